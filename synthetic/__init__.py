@@ -1,0 +1,164 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds no arithmetic of the method: it only draws parameters,
+poses and images from seeded numpy generators, in the shapes of the scenes the
+paper evaluates on (Replica-sized 1200x680 monocular frames, TUM-sized 640x480
+RGB-D frames).  The datasets themselves are not available; these scenes stand
+in for them.
+
+Scene recipe (every count, distribution and seed is fixed here):
+  tiny       4,096 Gaussians, means uniform in a 2 m cube centred at (0, 0, 3),
+             160x120 camera, fx = fy = 150, identity pose.
+  room       Gaussians uniform in a 6 x 3 x 4 m room centred at the origin
+             (x in [-3, 3], y in [-1.5, 1.5], z in [-2, 2]).
+  common     log-scales N(-4, 0.5); unit quaternions = normalised N(0, I4);
+             opacity logits N(0, 1); SH DC U(-1, 1), higher bands N(0, 0.1).
+  perturbed  every parameter + N(0, 0.05) (seed 1); targets render the
+             unperturbed set.
+  trajectory Lissajous path inside the central 2 x 1 x 1 m, yaw within +-60
+             degrees (seed 2), 50 poses.
+Seeds: scene 0, perturbation 1, trajectory 2.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+SH_PLANES = 12  # 48 floats per Gaussian as 12 float4 planes
+
+
+@dataclass
+class Params:
+    mean_op: np.ndarray   # (N, 4) float32: x, y, z, opacity logit
+    quat: np.ndarray      # (N, 4) float32: w, x, y, z
+    logscale: np.ndarray  # (N, 4) float32: 3 log-scales + zero pad
+    sh: np.ndarray        # (12, N, 4) float32: coefficient-major SH
+
+    @property
+    def n(self) -> int:
+        return self.mean_op.shape[0]
+
+    def copy(self) -> "Params":
+        return Params(self.mean_op.copy(), self.quat.copy(), self.logscale.copy(), self.sh.copy())
+
+
+@dataclass
+class Camera:
+    R: np.ndarray  # (3, 3) world -> camera rotation
+    t: np.ndarray  # (3,) world -> camera translation
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+
+    def as_array(self) -> np.ndarray:
+        """16 float32: R row-major, t, fx, fy, cx, cy."""
+        return np.concatenate([self.R.reshape(9), self.t.reshape(3),
+                               [self.fx, self.fy, self.cx, self.cy]]).astype(np.float32)
+
+
+def _draw(rng: np.random.Generator, n: int, lo, hi) -> Params:
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    mean = lo + (hi - lo) * rng.random((n, 3))
+    opac = rng.standard_normal(n)
+    ls = rng.normal(-4.0, 0.5, (n, 3))
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    sh48 = np.empty((n, 48))
+    sh48[:, 0:3] = rng.uniform(-1.0, 1.0, (n, 3))
+    sh48[:, 3:] = rng.normal(0.0, 0.1, (n, 45))
+    return Params(
+        mean_op=np.concatenate([mean, opac[:, None]], 1).astype(np.float32),
+        quat=q.astype(np.float32),
+        logscale=np.concatenate([ls, np.zeros((n, 1))], 1).astype(np.float32),
+        sh=np.ascontiguousarray(sh48.reshape(n, SH_PLANES, 4).transpose(1, 0, 2)).astype(np.float32),
+    )
+
+
+def tiny_scene(n: int = 4096, seed: int = 0) -> Params:
+    rng = np.random.default_rng(seed)
+    return _draw(rng, n, (-1.0, -1.0, 2.0), (1.0, 1.0, 4.0))
+
+
+def room_scene(n: int, seed: int = 0) -> Params:
+    rng = np.random.default_rng(seed)
+    return _draw(rng, n, (-3.0, -1.5, -2.0), (3.0, 1.5, 2.0))
+
+
+def perturb(p: Params, sigma: float = 0.05, seed: int = 1) -> Params:
+    rng = np.random.default_rng(seed)
+    q = p.copy()
+    q.mean_op += rng.normal(0, sigma, q.mean_op.shape).astype(np.float32)
+    q.quat += rng.normal(0, sigma, q.quat.shape).astype(np.float32)
+    q.logscale[:, :3] += rng.normal(0, sigma, (p.n, 3)).astype(np.float32)
+    q.sh += rng.normal(0, sigma, q.sh.shape).astype(np.float32)
+    return q
+
+
+def tiny_camera() -> Camera:
+    return Camera(np.eye(3), np.zeros(3), 150.0, 150.0, 80.0, 60.0, 160, 120)
+
+
+def _yaw(theta: float) -> np.ndarray:
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def pose_camera(position, yaw, fx, fy, width, height) -> Camera:
+    """Camera at `position` looking along +z rotated by `yaw` about +y."""
+    Rcw = _yaw(yaw)               # camera -> world
+    R = Rcw.T                     # world -> camera
+    t = -R @ np.asarray(position, np.float64)
+    return Camera(R, t, float(fx), float(fy), width / 2.0, height / 2.0, int(width), int(height))
+
+
+def trajectory(k: int, n_poses: int = 50, seed: int = 2):
+    """(position, yaw) of pose k on the seeded Lissajous path."""
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0, 2 * np.pi, 4)
+    s = 2 * np.pi * (k % n_poses) / n_poses
+    pos = np.array([1.0 * np.sin(s + ph[0]), 0.5 * np.sin(2 * s + ph[1]), 0.5 * np.sin(3 * s + ph[2])])
+    yaw = (np.pi / 3) * np.sin(s + ph[3])
+    return pos, yaw
+
+
+def replica_camera(k: int = 0) -> Camera:
+    """1200x680, fx = fy = 600: the Replica frame shape, on the trajectory."""
+    pos, yaw = trajectory(k)
+    return pose_camera(pos, yaw, 600.0, 600.0, 1200, 680)
+
+
+def tum_camera(k: int = 0) -> Camera:
+    """640x480, fx = fy = 525: the TUM RGB-D frame shape, on the trajectory."""
+    pos, yaw = trajectory(k)
+    return pose_camera(pos, yaw, 525.0, 525.0, 640, 480)
+
+
+def camera_at_level(cam: Camera, level: int) -> Camera:
+    """Intrinsics of pyramid level `level` (each level halves, sizes round up)."""
+    s = 2 ** level
+    w, h = cam.width, cam.height
+    for _ in range(level):
+        w, h = (w + 1) // 2, (h + 1) // 2
+    return Camera(cam.R, cam.t, cam.fx / s, cam.fy / s, cam.cx / s, cam.cy / s, w, h)
+
+
+def random_image(C: int, H: int, W: int, seed: int = 5, smooth: int = 2) -> np.ndarray:
+    """Seeded image in [0, 1], box-smoothed noise (float32, planar C x H x W)."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((C, H + 2 * smooth, W + 2 * smooth))
+    if smooth > 0:
+        k = 2 * smooth + 1
+        c = np.cumsum(np.cumsum(np.pad(x, ((0, 0), (1, 0), (1, 0))), 1), 2)
+        x = (c[:, k:, k:] - c[:, :-k, k:] - c[:, k:, :-k] + c[:, :-k, :-k]) / (k * k)
+    return np.ascontiguousarray(x[:, :H, :W]).astype(np.float32)
+
+
+def random_grad_image(C: int, H: int, W: int, seed: int = 6) -> np.ndarray:
+    """Seeded upstream gradient dL/dimage, N(0, 1) (float32, planar)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((C, H, W)).astype(np.float32)
