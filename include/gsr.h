@@ -1,0 +1,252 @@
+/*
+ * gsr.h -- C ABI of libgsr, the B300 (sm_103a) differentiable 3D-Gaussian
+ * rasteriser behind Photo-SLAM-style photorealistic mapping
+ * (arXiv 2311.16728, Sec. 3.3 "Photorealistic Mapping" and Sec. 3.4
+ * "Gaussian-Pyramid-Based Learning").
+ *
+ * The problem every call serves (Sec. 3.3, Eq. 3 and Eq. 4): given hyper
+ * primitives (position P, rotation r, scaling s, density sigma, SH colour),
+ * a keyframe pose (R, t) with its intrinsics and a ground-truth image at a
+ * pyramid level, compute the rendered image C(R, t), the photometric loss L
+ * and dL/d(P, r, s, sigma, SH).  Poses are inputs only.
+ *
+ * Conventions shared by every entry point:
+ *  - Every pointer named d_* or documented "device" is CUDA device memory
+ *    owned by the caller.  No entry point allocates, frees or synchronises the
+ *    device; scratch memory is a caller buffer sized by the matching
+ *    *_workspace_size query.  Structs and scalars are read on the host during
+ *    the call and may be freed on return.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and runs asynchronously; outputs are valid once the stream has
+ *    reached that point.
+ *  - The return value is a gsr_status.  Argument errors are detected on the
+ *    host before anything is enqueued (GSR_ERR_INVALID_ARG) and leave every
+ *    output untouched.  GSR_ERR_CUDA means a launch failed; gsr_last_error()
+ *    gives the message.  Data-dependent errors found on the device (too many
+ *    (Gaussian, tile) pairs for the caller's capacity, a bounded wait that ran
+ *    out) are OR-ed as bit flags (1 << code) into the caller's device status
+ *    word d_status, which the caller zeroes and reads after synchronising.
+ *  - Layout of the parameter store (SoA, 16-byte aligned float4 planes):
+ *      mean_op  float4[n]      x, y, z, opacity logit
+ *      quat     float4[n]      w, x, y, z (need not be normalised)
+ *      logscale float4[n]      log s_x, log s_y, log s_z, pad (pad kept 0)
+ *      sh       float4[12][n]  48 SH coefficients per Gaussian,
+ *                              coefficient-major: float f of the 48 is SH
+ *                              coefficient f / 3 of colour channel f % 3
+ *    Gradients and Adam moments use the same layout.
+ *  - Images are planar float32 C x H x W (C = 3 for colour).
+ *  - Pixel (px, py) is sampled at integer coordinates; cx = W/2, cy = H/2
+ *    makes pyramid intrinsics exact (level l divides fx, fy, cx, cy by 2^l).
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gsr_stream_t; /* binary-compatible with cudaStream_t */
+
+typedef enum {
+    GSR_OK = 0,
+    GSR_ERR_INVALID_ARG = 1, /* bad pointer / size / alignment / enum     */
+    GSR_ERR_CAPACITY = 2,    /* pair or workspace capacity too small       */
+    GSR_ERR_CUDA = 3,        /* a CUDA launch or copy failed               */
+    GSR_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up         */
+    GSR_ERR_UNSUPPORTED = 5  /* a configuration this build does not serve  */
+} gsr_status;
+
+/* Read-only parameter store (layout above).  sh_degree in 0..3: only the
+ * first (sh_degree + 1)^2 coefficients take part. */
+typedef struct {
+    const float *mean_op;
+    const float *quat;
+    const float *logscale;
+    const float *sh;
+    int64_t n;
+    int32_t sh_degree;
+} gsr_gaussians;
+
+/* Writable buffers in the parameter-store layout: gradients (accumulated
+ * with +=), parameters and Adam moments. */
+typedef struct {
+    float *mean_op;
+    float *quat;
+    float *logscale;
+    float *sh;
+} gsr_param_buffers;
+
+/* Pinhole camera at one pyramid level.  R is the row-major world-to-camera
+ * rotation and t the translation (x_cam = R x_world + t); fx, fy, cx, cy in
+ * pixels of this level; width x height pixels (Sec. 3.2 pi_m projection). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gsr_camera;
+
+/* Screen tiling.  tile_w x tile_h pixels per tile, tile_w * tile_h <= 1024
+ * and a multiple of 32.  The rendered image does not depend on the tiling:
+ * each Gaussian only reaches the pixels of its own 3-sigma pixel box. */
+typedef struct {
+    int32_t tile_w, tile_h;
+} gsr_tiling;
+
+/* Per-Gaussian screen-space record written by gsr_preprocess (caller-owned,
+ * n entries each, 16-byte aligned):
+ *   xy_conic  float4  u, v, conic A, conic B   (Sigma'^-1 = [[A, B], [B, C]])
+ *   c_op_box  float4  conic C, opacity, box x (u32 bits: x0 | x1 << 16),
+ *                     box y (u32 bits: y0 | y1 << 16); inclusive pixel box
+ *   rgb_depth float4  r, g, b (SH colour, clamped at 0), camera depth z
+ *   ntiles    u32     tiles the box touches; 0 = culled
+ * Records of culled Gaussians (ntiles == 0) are left unwritten. */
+typedef struct {
+    float *xy_conic;
+    float *c_op_box;
+    float *rgb_depth;
+    uint32_t *ntiles;
+} gsr_proj;
+
+/* Screen-space gradient buffer (caller-owned, 3 float4 per Gaussian):
+ *   g0 = dL/d(u, v, A, B), g1 = dL/d(C, opacity, r, g), g2 = dL/d(b), 0, 0, 0
+ * Written by gsr_render_bwd. */
+typedef struct {
+    float *g0, *g1, *g2;
+} gsr_grad2d;
+
+/* ---------------------------------------------------------------- */
+/* Library facts                                                     */
+/* ---------------------------------------------------------------- */
+
+/* Version string, e.g. "gsr 0.1 sm_103a". */
+const char *gsr_version(void);
+
+/* Message of the last host-side error on the calling thread ("" if none). */
+const char *gsr_last_error(void);
+
+/* Copy the device status word to *h_status (synchronises `stream`). */
+int32_t gsr_status_read(const int32_t *d_status, int32_t *h_status, gsr_stream_t stream);
+
+/* Intrinsics of pyramid level `level` (Sec. 3.4, Eq. 5): fx, fy, cx, cy
+ * divided by 2^level, width and height halved `level` times rounding up.
+ * Host-only arithmetic on the struct; no device work. */
+int32_t gsr_camera_at_level(const gsr_camera *in, int32_t level, gsr_camera *out);
+
+/* ---------------------------------------------------------------- */
+/* Hot path (Sec. 3.3): preprocess -> bin/sort -> render -> loss -> backward */
+/* ---------------------------------------------------------------- */
+
+/* EWA projection of every Gaussian (the splatting G of Eq. 3): camera-space
+ * mean, near cull z > 0.2, 2D covariance J W Sigma W^T J^T + 0.3 I, its
+ * inverse (conic), 3-sigma radius, clipped pixel box, tiles touched,
+ * opacity = sigmoid(logit), colour = max(0, SH(view dir) + 0.5).  Cull,
+ * depth, radius and box follow a fixed FP32 operation sequence so that tile
+ * keys are reproducible bit for bit.  One thread per Gaussian. */
+int32_t gsr_preprocess(const gsr_gaussians *g, const gsr_camera *cam, const gsr_tiling *tiling,
+                       const gsr_proj *out, int32_t *d_status, gsr_stream_t stream);
+
+/* Bytes of scratch gsr_bin_sort needs for n Gaussians, pair_capacity pairs
+ * and the tiles of (cam, tiling). */
+int32_t gsr_bin_sort_workspace_size(int64_t n, int64_t pair_capacity, const gsr_camera *cam,
+                                    const gsr_tiling *tiling, size_t *bytes);
+
+/* Tile binning (Sec. 3.3 "tile-based renderer"): an exclusive scan of
+ * ntiles gives each visible Gaussian its slots; one (key, gid) pair is
+ * emitted per tile its box touches, key = tile << 32 | bits(depth); an
+ * in-house stable LSD radix sort orders the pairs by key over the
+ * 32 + ceil(log2 tiles) significant bits (equal keys keep Gaussian order);
+ * tile_ranges[2 t], [2 t + 1] = [begin, end) of tile t in the sorted arrays
+ * (empty tiles [0, 0)).  keys/vals hold pair_capacity entries; the pair
+ * count is written to *d_num_pairs.  If it exceeds pair_capacity, the
+ * GSR_ERR_CAPACITY bit is set in *d_status, *d_num_pairs holds the count
+ * needed and the output is truncated (never written out of bounds). */
+int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camera *cam, const gsr_tiling *tiling,
+                     uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
+                     int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,
+                     gsr_stream_t stream);
+
+/* Forward render, Eq. 3 read as C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j)
+ * + T_final * bg, front to back over each tile's depth-sorted list, with
+ * alpha_i = min(0.99, sigma_i exp(-d^T Sigma'^-1 d / 2)), Gaussians skipped
+ * where alpha < 1/255 or the pixel is outside their box, and the walk stopped
+ * before a Gaussian that would take T below 1e-4.  Writes img (3 x H x W),
+ * T_final (H x W) and n_contrib (H x W: 1 + position in the tile list of the
+ * last Gaussian blended, 0 if none).  bg is a host array of 3 floats. */
+int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, const uint32_t *tile_ranges,
+                       const gsr_camera *cam, const gsr_tiling *tiling, const float *bg, float *img,
+                       float *T_final, uint32_t *n_contrib, gsr_stream_t stream);
+
+/* Bytes of scratch gsr_loss_fwd_bwd needs for a C x H x W image. */
+int32_t gsr_loss_workspace_size(int32_t C, int32_t H, int32_t W, size_t *bytes);
+
+/* Eq. 4: L = (1 - lambda) mean|img - gt| + lambda (1 - mean SSIM(img, gt)),
+ * SSIM per channel with an 11 x 11 Gaussian window (sigma 1.5), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2, averaged over all pixels and channels;
+ * the paper's lambda is 0.2 (Sec. 4.1).  Writes the scalar *d_loss and
+ * dL_dimg (C x H x W).  The sum reductions run in a fixed order, so the
+ * result is deterministic. */
+int32_t gsr_loss_fwd_bwd(const float *img, const float *gt, int32_t C, int32_t H, int32_t W,
+                         float lambda, float *d_loss, float *dL_dimg, void *workspace,
+                         size_t workspace_bytes, gsr_stream_t stream);
+
+/* Backward of Eq. 3 then of the projection.  Replays each pixel back to
+ * front from T_final and n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i)
+ * instead of storing per-pixel lists; per-Gaussian screen-space gradients are
+ * pre-reduced across each warp with shuffles before the global atomics into
+ * grad2d (zeroed by this call).  Then chains them, per Gaussian, to mean
+ * (through the projection, the Jacobian and the SH view direction),
+ * quaternion (through its normalisation), log-scale, opacity logit and SH,
+ * ADDING (+=) into `grads` so several views accumulate.  dL_dimg is
+ * 3 x H x W.  If densify_stat is not NULL, |dL/d(u, v)| of each visible
+ * Gaussian is added to densify_stat[gid] (the 3DGS densification statistic)
+ * and 1 to densify_count[gid]. */
+int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint32_t *vals,
+                       const uint32_t *tile_ranges, const gsr_camera *cam, const gsr_tiling *tiling,
+                       const float *bg, const float *T_final, const uint32_t *n_contrib,
+                       const float *dL_dimg, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
+                       float *densify_stat, float *densify_count, gsr_stream_t stream);
+
+/* ---------------------------------------------------------------- */
+/* Optimiser, pyramid and metrics                                    */
+/* ---------------------------------------------------------------- */
+
+/* Learning rates per parameter group (the paper's optimiser is plain SGD
+ * with a fixed rate, Sec. 4.1; this is its Adam variant). */
+typedef struct {
+    float lr_mean, lr_opacity, lr_quat, lr_scale, lr_sh;
+    float beta1, beta2, eps;
+} gsr_adam_config;
+
+/* One fused Adam step over all n Gaussians' 60-float records (the log-scale
+ * pad has zero gradient and never moves): m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * with t = *d_step + 1, then zeroes the gradients and increments *d_step
+ * (device int32) so that a captured graph can replay it. */
+int32_t gsr_adam_step(const gsr_param_buffers *params, const gsr_param_buffers *grads,
+                      const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
+                      const gsr_adam_config *cfg, int32_t *d_step, gsr_stream_t stream);
+
+/* One Gaussian-pyramid step down (Sec. 3.4, Eq. 5 GP^l): separable binomial
+ * [1 4 6 4 1]/16 blur with reflect-101 borders, keeping even pixels.
+ * in is C x H x W, out is C x ceil(H/2) x ceil(W/2). */
+int32_t gsr_pyramid_down(const float *in, int32_t C, int32_t H, int32_t W, float *out,
+                         gsr_stream_t stream);
+
+/* Bytes of scratch gsr_psnr needs for `count` values. */
+int32_t gsr_psnr_workspace_size(int64_t count, size_t *bytes);
+
+/* PSNR (Sec. 4.1 metric) of img clamped to [0, 1] against gt, peak 1:
+ * 10 log10(1 / MSE), written to *d_psnr (device float); FP64 sum in a fixed
+ * order. */
+int32_t gsr_psnr(const float *img, const float *gt, int64_t count, float *d_psnr, void *workspace,
+                 size_t workspace_bytes, gsr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H */

@@ -1,0 +1,64 @@
+"""Shared plumbing for the GPU-vs-oracle parity tests (inputs come from
+`synthetic`, expected values from `oracle`; nothing here computes the method)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import synthetic as S
+
+# Tolerances (stated per result by the tests):
+IMG_ATOL = 1e-4           # rendered image, max abs on [0, 1]
+GRAD_RTOL = 1e-3          # gradients: |g - g*| <= max(GRAD_RTOL |g*|, GRAD_ATOL)
+GRAD_ATOL = 1e-6
+MARGIN_FLAG = 1e-5        # oracle decision margin below which FP32 and FP64 may disagree
+
+
+def oracle_scene(p: S.Params, sh_degree: int = 3):
+    return oracle.Scene64(p.mean_op, p.quat, p.logscale, p.sh, sh_degree)
+
+
+def to_gpu(p: S.Params, sh_degree: int = 3):
+    import paper_2311_16728_b300 as gsr
+    return gsr.Gaussians.from_arrays(p.mean_op, p.quat, p.logscale, p.sh, sh_degree)
+
+
+def gpu_view(p: S.Params, cam: S.Camera, tile=(16, 16), sh_degree: int = 3, cap=None, bg=(0.0, 0.0, 0.0)):
+    """Runs preprocess -> bin/sort -> render on the GPU; returns (ViewBuffers, Gaussians)."""
+    import paper_2311_16728_b300 as gsr
+    g = to_gpu(p, sh_degree)
+    vb = gsr.ViewBuffers(p.n, gsr.camera_from(cam), gsr.tiling_struct(*tile), cap or max(1024, 64 * p.n))
+    if cap is None:
+        gsr.ensure_capacity(vb, g, bg)
+    vb.forward(g, bg)
+    import torch
+    torch.cuda.synchronize()
+    return vb, g
+
+
+def unpack_box(c_op_box: np.ndarray) -> np.ndarray:
+    bx = c_op_box[:, 2].view(np.uint32)
+    by = c_op_box[:, 3].view(np.uint32)
+    return np.stack([bx & 0xFFFF, bx >> 16, by & 0xFFFF, by >> 16], 1).astype(np.int32)
+
+
+def grad_planes_gpu(grads) -> np.ndarray:
+    """GPU gradient store -> (N, 60) in the oracle's layout."""
+    n = grads.n
+    mo = grads.mean_op.cpu().numpy()
+    q = grads.quat.cpu().numpy()
+    ls = grads.logscale.cpu().numpy()
+    sh = grads.sh.cpu().numpy().transpose(1, 0, 2).reshape(n, 48)
+    return np.concatenate([mo, q, ls, sh], 1).astype(np.float64)
+
+
+def grad_report(g: np.ndarray, ref: np.ndarray, rtol=GRAD_RTOL, atol=GRAD_ATOL):
+    """Per-element pass mask, worst excess and normwise relative error per group."""
+    err = np.abs(g - ref)
+    bound = np.maximum(rtol * np.abs(ref), atol)
+    ok = err <= bound
+    groups = {"mean": slice(0, 3), "opacity": slice(3, 4), "quat": slice(4, 8), "logscale": slice(8, 11),
+              "sh": slice(12, 60)}
+    norms = {k: float(np.linalg.norm((g - ref)[:, s]) / max(np.linalg.norm(ref[:, s]), 1e-30))
+             for k, s in groups.items()}
+    return ok, float((err / bound).max()), norms

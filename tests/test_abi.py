@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/gsr.h declares, and rejects bad arguments on the
+host before touching the device."""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gsr():
+    from paper_2311_16728_b300 import _build
+    _build.build()
+    import paper_2311_16728_b300 as pkg
+    return pkg
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gsr_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported_and_bound(gsr):
+    lib = ctypes.CDLL(gsr._lib.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert name in gsr._lib.EXPORTED, f"{name} has no Python binding"
+
+
+def test_version_and_last_error(gsr):
+    assert gsr._lib.gsr_version().decode().startswith("gsr")
+    assert isinstance(gsr._lib.gsr_last_error(), bytes)
+
+
+def test_camera_at_level_matches_pyramid_intrinsics(gsr):
+    import synthetic as S
+    cam = S.replica_camera(3)
+    c = gsr.camera_from(cam)
+    for lvl in range(3):
+        got = gsr.camera_at_level(c, lvl)
+        ref = S.camera_at_level(cam, lvl)
+        assert (got.width, got.height) == (ref.width, ref.height)
+        assert got.fx == pytest.approx(ref.fx) and got.cx == pytest.approx(ref.cx)
+        assert got.cy == pytest.approx(ref.cy) and got.fy == pytest.approx(ref.fy)
+    assert [gsr.camera_at_level(c, l).width for l in range(3)] == [1200, 600, 300]
+    assert [gsr.camera_at_level(c, l).height for l in range(3)] == [680, 340, 170]
+
+
+def test_bad_arguments_are_rejected_on_the_host(gsr):
+    L = gsr._lib
+    cam = gsr.camera_struct(np.eye(3), np.zeros(3), 100, 100, 50, 40, 100, 80)
+    good_tiling = gsr.tiling_struct(16, 16)
+    g = L.gsr_gaussians(16, 16, 16, 16, 10, 3)
+    proj = L.gsr_proj(16, 16, 16, 16)
+    # NULL outputs
+    rc = L.gsr_preprocess.raw(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(good_tiling), None, None, None)
+    assert rc == L.GSR_ERR_INVALID_ARG
+    # unaligned parameter plane
+    g_bad = L.gsr_gaussians(18, 16, 16, 16, 10, 3)
+    rc = L.gsr_preprocess.raw(ctypes.byref(g_bad), ctypes.byref(cam), ctypes.byref(good_tiling), ctypes.byref(proj),
+                              None, None)
+    assert rc == L.GSR_ERR_INVALID_ARG and b"aligned" in L.gsr_last_error()
+    # SH degree out of range
+    g_deg = L.gsr_gaussians(16, 16, 16, 16, 10, 4)
+    rc = L.gsr_preprocess.raw(ctypes.byref(g_deg), ctypes.byref(cam), ctypes.byref(good_tiling), ctypes.byref(proj),
+                              None, None)
+    assert rc == L.GSR_ERR_INVALID_ARG
+    # tiling that is not a multiple of a warp
+    bad_tiling = gsr.tiling_struct(5, 5)
+    rc = L.gsr_preprocess.raw(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(bad_tiling), ctypes.byref(proj),
+                              None, None)
+    assert rc == L.GSR_ERR_INVALID_ARG
+    # workspace too small
+    rc = L.gsr_bin_sort.raw(ctypes.byref(proj), 10, ctypes.byref(cam), ctypes.byref(good_tiling), 16, 16, 100, 16, 16,
+                            16, 1, None, None)
+    assert rc == L.GSR_ERR_CAPACITY
+    # loss: lambda outside [0, 1]
+    rc = L.gsr_loss_fwd_bwd.raw(16, 16, 3, 8, 8, ctypes.c_float(1.5), 16, 16, 16, 1 << 20, None)
+    assert rc == L.GSR_ERR_INVALID_ARG
+
+
+def test_workspace_queries(gsr):
+    L = gsr._lib
+    sz = ctypes.c_size_t()
+    cam = gsr.camera_struct(np.eye(3), np.zeros(3), 600, 600, 600, 340, 1200, 680)
+    t = gsr.tiling_struct(16, 16)
+    L.gsr_bin_sort_workspace_size(300000, 2_000_000, ctypes.byref(cam), ctypes.byref(t), ctypes.byref(sz))
+    assert sz.value >= 12 * 2_000_000
+    L.gsr_loss_workspace_size(3, 680, 1200, ctypes.byref(sz))
+    assert sz.value >= 3 * 3 * 680 * 1200 * 4
+
+
+def test_defaults_match_paper_hyperparameters(gsr):
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_hyperparameters.json")))
+    assert gsr.LAMBDA_DSSIM == gold["lambda_dssim"]["value"]
+    assert gsr.PYRAMID_LEVELS == gold["pyramid_levels"]["value"]
+    assert 48 // 3 == gold["sh_coeffs_per_channel"]["value"]  # 12 float4 planes = 16 coefficients x RGB
