@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(1024) render_bwd_kernel(RenderArgs a, const fl
         if (threadIdx.x == 0) s_max[0] = v;
     }
     __syncthreads();
-    const int stop = begin + (int)s_max[0];
+    // never past the tile's own list, whatever n_contrib holds
+    const int stop = min(begin + (int)s_max[0], (int)rg.y);
     const int lane = threadIdx.x & 31;
     for (int bend = stop; bend > begin; bend -= nthr) {
         const int bstart = max(begin, bend - nthr);
