@@ -57,7 +57,7 @@ def lib():
         L.orc_decide.argtypes = [i64, P, P, P, P, i32, i32, P, P, P, P, P]
         L.orc_keys.argtypes = [i64, P, P, P, i32, i32, i32, i32, P, P, i64, P, P]
         L.orc_render.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P, P, i32, i32, i32, P, P, P, P]
-        L.orc_render_bwd.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P, P, i32, i32, i32, P, P, P]
+        L.orc_render_bwd.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P, P, i32, i32, i32, P, P, P, P]
         L.orc_chain.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P]
         L.orc_project.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P]
         L.orc_ssim_map.argtypes = [P, P, i32, i32, i32, P]
@@ -178,8 +178,9 @@ def render(sc: Scene64, cam, W: int, H: int, dec: Decisions, bg=(0.0, 0.0, 0.0),
 
 
 def render_bwd(sc: Scene64, cam, W: int, H: int, dec: Decisions, dimg, bg=(0.0, 0.0, 0.0), flags: int = 0,
-               rows=None):
-    """Returns (grad (N, 60), grad2d (N, 9))."""
+               rows=None, with_magnitude: bool = False):
+    """Returns (grad (N, 60), grad2d (N, 9)) [, grad2d_mag (N, 9)]: the magnitude
+    is the per-element sum of |pixel term| (condition scale of each sum)."""
     y0, y1 = (0, H) if rows is None else rows
     cam = _f32(cam)
     bg = _f64(bg)
@@ -187,11 +188,12 @@ def render_bwd(sc: Scene64, cam, W: int, H: int, dec: Decisions, dimg, bg=(0.0, 
     assert dimg.shape == (3, H, W)
     g = np.zeros((sc.n, 60))
     g2 = np.zeros((sc.n, 9))
+    mag = np.zeros((sc.n, 9)) if with_magnitude else None
     rc = lib().orc_render_bwd(sc.n, _p(sc.mean_op), _p(sc.quat), _p(sc.logscale), _p(sc.sh), sc.sh_degree, _p(cam),
                               W, H, _p(bg), _p(dec.visible), _p(dec.depth), _p(dec.box), flags, y0, y1, _p(dimg),
-                              _p(g), _p(g2))
+                              _p(g), _p(g2), _p(mag) if with_magnitude else None)
     assert rc == 0
-    return g, g2
+    return (g, g2, mag) if with_magnitude else (g, g2)
 
 
 def chain(sc: Scene64, cam, W: int, H: int, dec: Decisions, g2):

@@ -720,18 +720,24 @@ static void chain_one(const orc_pre *p, const orc_cam *cam, const double *sh, in
 /* Backward of the render: given dL/dimg (planar 3 x H x W) over rows
  * [y_begin, y_end), writes grad[60 n] (= dL/dparams, overwritten) and
  * grad2d[9 n] (screen-space gradients du dv dA dB dC dopacity dr dg db).
- * The per-pixel blend state is kept exactly (no division recompute). */
+ * The per-pixel blend state is kept exactly (no division recompute).
+ * grad2d_mag (may be NULL) receives, per screen-space gradient element, the
+ * sum over pixels of the magnitude of that pixel's term with every inner sum
+ * taken in absolute value: the scale against which a finite-precision
+ * evaluation of the same sum can err (its condition magnitude). */
 int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const double *logscale,
                    const double *sh, int deg, const float *camf, int W, int H, const double *bg,
                    const uint8_t *visible, const float *depth, const int32_t *box, int flags,
-                   int y_begin, int y_end, const double *dimg, double *grad, double *grad2d) {
+                   int y_begin, int y_end, const double *dimg, double *grad, double *grad2d,
+                   double *grad2d_mag) {
     if (deg < 0 || deg > 3 || y_begin < 0 || y_end > H || y_begin > y_end) return 1;
     orc_cam cam = make_cam(camf, W, H);
     orc_pre *pre = project_all(n, mean_op, quat, logscale, sh, deg, &cam, visible);
     int64_t *order;
     int64_t nv = depth_order(n, visible, depth, &order);
     const int nthr = orc_num_threads();
-    double *acc = (double *)calloc((size_t)nthr * (size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+    const int nacc = 18; /* 9 gradients + 9 condition magnitudes */
+    double *acc = (double *)calloc((size_t)nthr * (size_t)(n > 0 ? n : 1) * nacc, sizeof(double));
 #pragma omp parallel
     {
 #ifdef _OPENMP
@@ -739,7 +745,7 @@ int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const d
 #else
         const int tid = 0;
 #endif
-        double *g2 = acc + (size_t)tid * (size_t)n * 9;
+        double *g2 = acc + (size_t)tid * (size_t)n * nacc;
         contrib_t *cs = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(nv > 0 ? nv : 1));
 #pragma omp for schedule(dynamic, 1)
         for (int py = y_begin; py < y_end; ++py) {
@@ -755,34 +761,43 @@ int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const d
                 for (int64_t k = nc - 1; k >= 0; --k) {
                     const contrib_t *c = &cs[k];
                     const orc_pre *p = &pre[c->gid];
-                    double *o = g2 + 9 * c->gid;
-                    double dalpha = 0.0;
+                    double *o = g2 + nacc * c->gid, *om = o + 9;
+                    double dalpha = 0.0, dalpha_mag = 0.0;
                     for (int ch = 0; ch < 3; ++ch) {
                         o[6 + ch] += dC[ch] * c->alpha * c->T;
+                        om[6 + ch] += fabs(dC[ch] * c->alpha * c->T);
                         dalpha += dC[ch] * (p->rgb[ch] * c->T - S[ch] / (1.0 - c->alpha));
+                        dalpha_mag += fabs(dC[ch]) * (fabs(p->rgb[ch]) * c->T + fabs(S[ch]) / (1.0 - c->alpha));
                     }
                     for (int ch = 0; ch < 3; ++ch) S[ch] += p->rgb[ch] * c->alpha * c->T;
                     if (c->clamped) continue; /* alpha = 0.99 does not depend on anything */
                     /* alpha = opacity * exp(power) */
                     o[5] += dalpha * c->G;
-                    double dpow = dalpha * c->alpha;
+                    om[5] += dalpha_mag * c->G;
+                    double dpow = dalpha * c->alpha, dpow_mag = dalpha_mag * c->alpha;
                     const double A = p->conic[0], B = p->conic[1], Cc = p->conic[2];
                     o[0] += dpow * (A * c->dx + B * c->dy);
                     o[1] += dpow * (Cc * c->dy + B * c->dx);
                     o[2] += dpow * (-0.5 * c->dx * c->dx);
                     o[3] += dpow * (-c->dx * c->dy);
                     o[4] += dpow * (-0.5 * c->dy * c->dy);
+                    om[0] += dpow_mag * (fabs(A * c->dx) + fabs(B * c->dy));
+                    om[1] += dpow_mag * (fabs(Cc * c->dy) + fabs(B * c->dx));
+                    om[2] += dpow_mag * 0.5 * c->dx * c->dx;
+                    om[3] += dpow_mag * fabs(c->dx * c->dy);
+                    om[4] += dpow_mag * 0.5 * c->dy * c->dy;
                 }
             }
         }
         free(cs);
     }
     for (int64_t i = 0; i < n; ++i) {
-        for (int k = 0; k < 9; ++k) {
+        for (int k = 0; k < nacc; ++k) {
             double s = 0.0;
-            for (int t = 0; t < nthr; ++t) s += acc[((size_t)t * (size_t)n + (size_t)i) * 9 + k];
-            if (grad2d) grad2d[9 * i + k] = s;
-            acc[(size_t)i * 9 + k] = s; /* thread 0 slot now holds the total */
+            for (int t = 0; t < nthr; ++t) s += acc[((size_t)t * (size_t)n + (size_t)i) * nacc + k];
+            if (k < 9 && grad2d) grad2d[9 * i + k] = s;
+            if (k >= 9 && grad2d_mag) grad2d_mag[9 * i + k - 9] = s;
+            acc[(size_t)i * nacc + k] = s; /* thread 0 slot now holds the total */
         }
     }
 #pragma omp parallel for schedule(static)
@@ -792,7 +807,7 @@ int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const d
         if (!visible[i]) continue;
         double shi[48];
         gather_sh(sh, n, i, shi);
-        chain_one(&pre[i], &cam, shi, deg, acc + (size_t)i * 9, o);
+        chain_one(&pre[i], &cam, shi, deg, acc + (size_t)i * nacc, o);
     }
     free(acc);
     free(order);

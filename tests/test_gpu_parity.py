@@ -1,8 +1,11 @@
 """GPU (libgsr, sm_103a) against the FP64 oracle, element by element, through the C ABI.
 
 Bars: tile keys, sort order, per-tile ranges, cull set, depth bits and pixel
-boxes bit-exact; image <= 1e-4 max abs; gradients |g - g*| <=
-max(1e-3 |g*|, 1e-6) per element.  Pixels where an alpha / transmittance
+boxes bit-exact; image <= 1e-4 max abs; gradients per element
+|g - g*| <= max(1e-3 |g*|, 1e-6) + 2^-15 C, where C is the element's
+condition magnitude (the oracle's sum of |terms|): the allowance only
+matters where the exact sum cancels, and the number of elements that use it
+is printed.  Pixels where an alpha / transmittance
 decision lies within 1e-5 (relative) of its threshold may legitimately flip
 between FP32 and FP64: the oracle flags them, the tests count them and keep
 them out of the element-wise image bar (their upstream gradient is zeroed in
@@ -13,8 +16,8 @@ import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import (GRAD_ATOL, GRAD_RTOL, IMG_ATOL, MARGIN_FLAG, gpu_view, grad_planes_gpu, grad_report,
-                            oracle_scene, to_gpu, unpack_box)
+from parity_helpers import (GRAD_TAU, IMG_ATOL, MARGIN_FLAG, gpu_view, grad_check, grad_planes_gpu, grad_report,
+                            oracle_scene, param_condition, to_gpu, unpack_box)
 
 pytestmark = pytest.mark.gpu
 
@@ -120,23 +123,27 @@ def test_loss_matches_oracle(H, W):
 def test_render_backward_matches_oracle_tiny():
     p, cam = S.perturb(S.tiny_scene()), S.tiny_camera()
     vb, g = gpu_view(p, cam)
+    ca = cam.as_array()
     dec, _, sc, (img, T, nc, mg) = _oracle_all(p, cam)
     dimg = S.random_grad_image(3, cam.height, cam.width, seed=3)
     dimg[:, mg < MARGIN_FLAG] = 0.0
-    gref, g2ref = oracle.render_bwd(sc, cam.as_array(), cam.width, cam.height, dec, dimg.astype(np.float64))
+    gref, g2ref, mag = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, dimg.astype(np.float64),
+                                         with_magnitude=True)
     grads = g.zeros_like()
     vb.render_bwd(g, grads, dimg=torch.tensor(dimg, device="cuda"))
     torch.cuda.synchronize()
     g2 = vb.g2.cpu().numpy()
     g2gpu = np.concatenate([g2[0], g2[1], g2[2][:, :1]], 1).astype(np.float64)
-    ok2, worst2, _ = grad_report(np.pad(g2gpu, ((0, 0), (0, 51))), np.pad(g2ref, ((0, 0), (0, 51))))
-    pr = oracle.project(sc, cam.as_array(), cam.width, cam.height, dec.visible)
+    ok2, used2, worst2 = grad_check(g2gpu, g2ref, mag)
+    pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
     near_clamp = (np.abs(pr[:, 13:16]) < 1e-4).any(1)
     gg = grad_planes_gpu(grads)
-    ok, worst, norms = grad_report(gg, gref)
+    ok, used, worst = grad_check(gg, gref, param_condition(sc, ca, cam.width, cam.height, dec, mag))
     ok[near_clamp] = True
-    print(f"screen-space grads: worst |err|/bound {worst2:.3f}; param grads worst {worst:.3f}, "
-          f"normwise {norms}; colour-clamp-adjacent Gaussians excluded: {near_clamp.sum()}")
+    _, _, norms = grad_report(gg, gref)
+    print(f"screen-space grads: worst err/bound {worst2:.3f} ({used2} of {g2gpu.size} use the FP32 allowance); "
+          f"param grads worst {worst:.3f} ({used} use it), normwise {norms}; "
+          f"colour-clamp-adjacent Gaussians excluded: {near_clamp.sum()}")
     assert ok2.all(), f"{(~ok2).sum()} screen-space gradient elements out of tolerance"
     assert ok.all(), f"{(~ok).sum()} of {ok.size} parameter gradient elements out of tolerance"
 
@@ -198,7 +205,9 @@ def test_adam_matches_oracle():
     lr = np.zeros((n, 60))
     lr[:, 0:3], lr[:, 3], lr[:, 4:8], lr[:, 8:12], lr[:, 12:] = cfg.lr_mean, cfg.lr_opacity, cfg.lr_quat, \
         cfg.lr_scale, cfg.lr_sh
-    p1, m1, v1 = oracle.adam(p0, g0, m0, v0, lr, 5, cfg.beta1, cfg.beta2, cfg.eps)
+    f32 = lambda x: float(np.float32(x))  # the kernel receives FP32 hyper-parameters
+    lr = lr.astype(np.float32).astype(np.float64)
+    p1, m1, v1 = oracle.adam(p0, g0, m0, v0, lr, 5, f32(cfg.beta1), f32(cfg.beta2), f32(cfg.eps))
     opt.step(grads)
     torch.cuda.synchronize()
     assert int(opt.step_count.item()) == 5
@@ -303,16 +312,22 @@ def test_full_size_keys_and_sampled_rows():
         ww[:, fl] = 0
         w[:, r[0]:r[1]] = ww
     gref = np.zeros((p.n, 60))
+    mag = np.zeros((p.n, 9))
     for r in rows:
-        gr, _ = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, w.astype(np.float64), rows=r)
+        gr, _, mg2 = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, w.astype(np.float64), rows=r,
+                                       with_magnitude=True)
         gref += gr
+        mag += mg2
     grads = g.zeros_like()
     vb.render_bwd(g, grads, dimg=torch.tensor(w, device="cuda"))
     torch.cuda.synchronize()
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
-    ok, worst, norms = grad_report(grad_planes_gpu(grads), gref)
+    gg = grad_planes_gpu(grads)
+    ok, used, worst = grad_check(gg, gref, param_condition(sc, ca, cam.width, cam.height, dec, mag))
     ok[(np.abs(pr[:, 13:16]) < 1e-4).any(1)] = True
-    print(f"full size: pairs {len(ks)}, grad worst {worst:.3f}, normwise {norms}")
+    _, _, norms = grad_report(gg, gref)
+    print(f"full size: pairs {len(ks)}, grad worst err/bound {worst:.3f} ({used} use the FP32 allowance), "
+          f"normwise {norms}")
     assert ok.all(), f"{(~ok).sum()} gradient elements out of tolerance"
 
 
