@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamK a, const int32_t *__res
     else if (which == 2) lr = make_float4(a.lr_scale, a.lr_scale, a.lr_scale, a.lr_scale);
     else lr = make_float4(a.lr_sh, a.lr_sh, a.lr_sh, a.lr_sh);
     const int t = *d_step + 1;
-    const float bc1 = 1.0f - powf(a.b1, (float)t), bc2 = 1.0f - powf(a.b2, (float)t);
+    // 1 - b^t = -expm1(t log1p(b - 1)): no cancellation for b near 1 (b - 1 is exact)
+    const float bc1 = -expm1f((float)t * log1pf(a.b1 - 1.0f));
+    const float bc2 = -expm1f((float)t * log1pf(a.b2 - 1.0f));
     const float ibc1 = 1.0f / bc1, ibc2 = 1.0f / bc2;
     float4 *pp = a.p[which] + off, *gp = a.g[which] + off, *mp = a.m[which] + off, *vp = a.v[which] + off;
     float4 p = *pp, g = *gp, m = *mp, v = *vp;

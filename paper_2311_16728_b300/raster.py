@@ -200,11 +200,11 @@ def ensure_capacity(vb: ViewBuffers, g: Gaussians, bg=(0.0, 0.0, 0.0), margin: f
     vb.preprocess(g)
     vb.bin_sort()
     need = vb.pairs_needed()
-    if need > vb.pair_capacity:
+    grown = need > vb.pair_capacity
+    if grown:
         vb.set_pair_capacity(int(need * margin) + 1024)
-        vb.status.zero_()
-        return True
-    return False
+    vb.status.zero_()
+    return grown
 
 
 # ---------------------------------------------------------------- autograd
@@ -321,6 +321,7 @@ class MappingStep:
                 self.vb.bin_sort()
                 need = max(need, self.vb.pairs_needed())
             self.vb.set_pair_capacity(int(need * margin) + 4096)
+        self.vb.status.zero_()  # the sizing passes may have flagged overflow
         self.vb.cam = cam0
         self.graphs = None
         self.k = 0
