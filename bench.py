@@ -47,11 +47,11 @@ def _config(extra=None):
     return c
 
 
-def _scene():
+def _scene(poses: int = N_POSES):
     import synthetic as S
     target = S.room_scene(N_GAUSS, seed=0)
     start = S.perturb(target, 0.05, seed=1)
-    cams = [S.replica_camera(k) for k in range(N_POSES)]
+    cams = [S.replica_camera(k) for k in range(poses)]
     return target, start, cams
 
 
@@ -140,7 +140,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms",
-                                       "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
@@ -188,12 +188,13 @@ def count_kernel_nodes(graphs) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
     ap.add_argument("--cpu-rows", type=int, default=16, help="image rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--poses", type=int, default=N_POSES, help="trajectory poses trained on (profiling uses fewer)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -210,7 +211,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     import paper_2311_16728_b300 as gsr
-    target, start, cams = _scene()
+    target, start, cams = _scene(args.poses)
 
     # targets: renders of the unperturbed set at every pose (setup, untimed)
     g_tgt = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
@@ -296,7 +297,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; Replica-shaped)",
-            "config": _config({"pairs_last_step": pairs}),
+            "config": _config({"pairs_last_step": pairs, "poses": len(cams)}),
             "roofline": roof, "stages_ms": stage_ms, "gpu_launches": launches, "clocks": clk,
             "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "iters/s",
                     "h2d_bytes_per_step": 3 * WIDTH * HEIGHT * 4, "d2h_bytes_per_step": 4}}
