@@ -210,6 +210,29 @@ int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint3
                        const float *dL_dimg, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
                        float *densify_stat, float *densify_count, gsr_stream_t stream);
 
+/* Allocation-free variant of gsr_loss_fwd_bwd, for callers that cannot
+ * allocate device memory at the point where they evaluate the loss -- for
+ * example code that runs while a stream is being captured in the global
+ * capture mode (where cudaMalloc is an error), or a host application that
+ * owns every allocation itself and hands this library only its images.
+ * There is no counterpart in the paper: it is a packaging of Eq. 4.
+ *
+ * Computes exactly what gsr_loss_fwd_bwd computes (same kernels), but its
+ * scratch lives in one fixed array in device memory that the library defines
+ * (29.6 MB, held by every GPU that loads the library until the process
+ * exits).  Limits: C * H * W <= 2,457,600 values (a 3 x 1200 x 680 frame fits)
+ * and at most 16,384 blocks of 32 x 8 pixels summed over channels; larger
+ * images return GSR_ERR_CAPACITY with a message and enqueue nothing.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  It never calls cudaMalloc or cudaFree.
+ * All calls on a device share the array and it keeps the last call's
+ * contents (nothing in it needs clearing between calls): calls whose work
+ * overlaps on the GPU -- on different streams, or from different host
+ * threads -- race on it and must be serialised by the caller. */
+int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, int32_t C, int32_t H, int32_t W,
+                                float lambda, float *d_loss, float *dL_dimg, gsr_stream_t stream);
+
 /* ---------------------------------------------------------------- */
 /* Optimiser, pyramid and metrics                                    */
 /* ---------------------------------------------------------------- */

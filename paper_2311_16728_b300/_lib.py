@@ -70,6 +70,8 @@ _SIGNATURES = {
     "gsr_loss_workspace_size": ([c_int32, c_int32, c_int32, P(c_size_t)], c_int32),
     "gsr_loss_fwd_bwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p,
                           c_size_t, c_void_p], c_int32),
+    "gsr_loss_fwd_bwd_static": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p,
+                                 c_void_p], c_int32),
     "gsr_render_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_void_p, P(gsr_camera), P(gsr_tiling), c_void_p,
                         c_void_p, c_void_p, c_void_p, P(gsr_grad2d), P(gsr_param_buffers), c_void_p, c_void_p,
                         c_void_p], c_int32),
@@ -127,6 +129,7 @@ gsr_bin_sort = _wrap("gsr_bin_sort")
 gsr_render_fwd = _wrap("gsr_render_fwd")
 gsr_loss_workspace_size = _wrap("gsr_loss_workspace_size")
 gsr_loss_fwd_bwd = _wrap("gsr_loss_fwd_bwd")
+gsr_loss_fwd_bwd_static = _wrap("gsr_loss_fwd_bwd_static")
 gsr_render_bwd = _wrap("gsr_render_bwd")
 gsr_adam_step = _wrap("gsr_adam_step")
 gsr_pyramid_down = _wrap("gsr_pyramid_down")

@@ -13,6 +13,8 @@
 // partial sums in a fixed order.
 #include <math.h>
 
+#include <mutex>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -313,4 +315,75 @@ extern "C" int32_t gsr_psnr(const float *img, const float *gt, int64_t count, fl
     psnr_partial_kernel<<<kPsnrBlocks, 256, 0, st>>>(img, gt, count, part);
     psnr_final_kernel<<<1, 256, 0, st>>>(part, kPsnrBlocks, count, d_psnr);
     return check_launch("psnr kernels");
+}
+
+// ---------------------------------------------------------------- allocation-free loss
+// gsr_loss_fwd_bwd_static: the same two kernels as gsr_loss_fwd_bwd, with the
+// scratch (the three SSIM partial-derivative maps and the per-CTA partial
+// sums) taken from a fixed array in device memory instead of a caller buffer.
+// The array is defined at file scope, so every GPU that loads this library
+// holds it (about 29.6 MB) until the process exits.
+namespace gsr {
+
+constexpr int64_t kStaticLossMaxElems = 2457600;  // C x H x W, e.g. 3 x 1200 x 680 (Replica frame) fits
+constexpr int64_t kStaticLossMaxBlocks = 16384;   // CTAs of 32 x 8 pixels per channel, summed over channels
+
+static __device__ __align__(256) float g_loss_scratch[3 * kStaticLossMaxElems + 2 * kStaticLossMaxBlocks];
+
+// Device address of g_loss_scratch, looked up once per device.  In host code
+// the symbol names a host-side stand-in, not device memory, so it is never
+// passed to a kernel directly.
+constexpr int kMaxDevices = 64;
+static float *g_loss_scratch_ptr[kMaxDevices];
+static std::mutex g_loss_scratch_mu;
+
+static int32_t static_loss_scratch(float **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_error("gsr_loss_fwd_bwd_static: no usable current device");
+        return GSR_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_loss_scratch_mu);
+    if (!g_loss_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_loss_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("gsr_loss_fwd_bwd_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return GSR_ERR_CUDA;
+        }
+        g_loss_scratch_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_loss_scratch_ptr[dev];
+    return GSR_OK;
+}
+
+}  // namespace gsr
+
+extern "C" int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, int32_t C, int32_t H, int32_t W,
+                                           float lambda, float *d_loss, float *dL_dimg, gsr_stream_t stream) {
+    if (!img || !gt || !d_loss || !dL_dimg || C <= 0 || H <= 0 || W <= 0 || !(lambda >= 0.f && lambda <= 1.f)) {
+        set_error("gsr_loss_fwd_bwd_static: bad arguments");
+        return GSR_ERR_INVALID_ARG;
+    }
+    const int64_t elems = (int64_t)C * H * W;
+    const int64_t nblocks = (int64_t)((W + kLTW - 1) / kLTW) * ((H + kLTH - 1) / kLTH) * C;
+    if (elems > kStaticLossMaxElems || nblocks > kStaticLossMaxBlocks) {
+        set_error("gsr_loss_fwd_bwd_static: image %d x %d x %d exceeds the fixed scratch (at most %lld values "
+                  "and %lld 32x8 pixel blocks); use gsr_loss_fwd_bwd with a workspace",
+                  (int)C, (int)H, (int)W, (long long)kStaticLossMaxElems, (long long)kStaticLossMaxBlocks);
+        return GSR_ERR_CAPACITY;
+    }
+    float *base = nullptr;
+    int32_t rc = static_loss_scratch(&base);
+    if (rc) return rc;
+    // every map entry the second pass reads and every partial sum is written
+    // by the first pass of the same call, so nothing needs clearing
+    float *mA = base, *mB = base + kStaticLossMaxElems, *mC = base + 2 * kStaticLossMaxElems;
+    float *part = base + 3 * kStaticLossMaxElems;
+    const Win win = ssim_window();
+    const dim3 grid((W + kLTW - 1) / kLTW, (H + kLTH - 1) / kLTH, C);
+    cudaStream_t st = as_cuda(stream);
+    ssim_pass1_kernel<<<grid, 256, 0, st>>>(img, gt, H, W, win, mA, mB, mC, part);
+    ssim_pass2_kernel<<<grid, 256, 0, st>>>(img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda, d_loss, dL_dimg);
+    return check_launch("ssim kernels (static scratch)");
 }
