@@ -54,8 +54,11 @@ def lib():
         L.orc_chain_exp.restype = ctypes.c_float
         L.orc_sh_basis.argtypes = [P, i32, P, P]
         L.orc_sh_basis.restype = None
-        L.orc_decide.argtypes = [i64, P, P, P, P, i32, i32, P, P, P, P, P]
-        L.orc_keys.argtypes = [i64, P, P, P, i32, i32, i32, i32, P, P, i64, P, P]
+        L.orc_decide.argtypes = [i64, P, P, P, P, i32, i32, P, P, P, P, P, P, P]
+        L.orc_keys.argtypes = [i64, P, P, P, P, P, P, i32, i32, i32, i32, P, P, i64, P, P]
+        L.orc_tile_keep.argtypes = [ctypes.c_float, ctypes.c_float, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float]
+        L.orc_tile_keep.restype = i32
         L.orc_render.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P, P, i32, i32, i32, P, P, P, P]
         L.orc_render_bwd.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P, P, i32, i32, i32, P, P, P, P]
         L.orc_chain.argtypes = [i64, P, P, P, P, i32, P, i32, i32, P, P, P]
@@ -107,10 +110,12 @@ def camera_array(R, t, fx, fy, cx, cy) -> np.ndarray:
 
 
 class Decisions:
-    """FP32 decision chain outputs: visible, depth, pixel box, uv, radius."""
+    """FP32 decision chain outputs: visible, depth, pixel box, uv, radius,
+    conic (A, B, C) and opacity."""
 
-    def __init__(self, visible, depth, box, uv, radius):
+    def __init__(self, visible, depth, box, uv, radius, conic, opacity):
         self.visible, self.depth, self.box, self.uv, self.radius = visible, depth, box, uv, radius
+        self.conic, self.opacity = conic, opacity
 
 
 def decide(mean_op, quat, logscale, cam, W: int, H: int) -> Decisions:
@@ -121,14 +126,23 @@ def decide(mean_op, quat, logscale, cam, W: int, H: int) -> Decisions:
     box = np.zeros((n, 4), np.int32)
     uv = np.zeros((n, 2), np.float32)
     rad = np.zeros(n, np.int32)
+    conic = np.zeros((n, 3), np.float32)
+    op = np.zeros(n, np.float32)
     rc = lib().orc_decide(n, _p(mean_op), _p(quat), _p(logscale), _p(cam), W, H, _p(vis), _p(depth), _p(box),
-                          _p(uv), _p(rad))
+                          _p(uv), _p(rad), _p(conic), _p(op))
     assert rc == 0
-    return Decisions(vis, depth, box, uv, rad)
+    return Decisions(vis, depth, box, uv, rad, conic, op)
+
+
+def tile_keep(u, v, conic, opacity, x0, x1, y0, y1) -> bool:
+    c = np.ascontiguousarray(conic, np.float32)
+    f = ctypes.c_float
+    return bool(lib().orc_tile_keep(f(u), f(v), _p(c), f(opacity), f(x0), f(x1), f(y0), f(y1)))
 
 
 def keys(dec: Decisions, W: int, H: int, tile_w: int = 16, tile_h: int = 16):
-    """Sorted (key, gid) pairs and per-tile ranges (2 * tiles u32)."""
+    """Sorted (key, gid) pairs of the kept (Gaussian, tile) pairs and per-tile
+    ranges (2 * tiles u32)."""
     n = dec.visible.shape[0]
     gx, gy = (W + tile_w - 1) // tile_w, (H + tile_h - 1) // tile_h
     npairs = np.zeros(1, np.int64)
@@ -136,13 +150,12 @@ def keys(dec: Decisions, W: int, H: int, tile_w: int = 16, tile_h: int = 16):
     # first call sizes the pair buffer
     k0 = np.zeros(1, np.uint64)
     v0 = np.zeros(1, np.uint32)
-    rc = lib().orc_keys(n, _p(dec.visible), _p(dec.depth), _p(dec.box), W, H, tile_w, tile_h, _p(k0), _p(v0), 0,
-                        _p(npairs), _p(ranges))
+    args = (_p(dec.visible), _p(dec.depth), _p(dec.box), _p(dec.uv), _p(dec.conic), _p(dec.opacity))
+    rc = lib().orc_keys(n, *args, W, H, tile_w, tile_h, _p(k0), _p(v0), 0, _p(npairs), _p(ranges))
     cap = int(npairs[0])
     ks = np.zeros(max(cap, 1), np.uint64)
     vs = np.zeros(max(cap, 1), np.uint32)
-    rc = lib().orc_keys(n, _p(dec.visible), _p(dec.depth), _p(dec.box), W, H, tile_w, tile_h, _p(ks), _p(vs), cap,
-                        _p(npairs), _p(ranges))
+    rc = lib().orc_keys(n, *args, W, H, tile_w, tile_h, _p(ks), _p(vs), cap, _p(npairs), _p(ranges))
     assert rc == 0
     return ks[:cap], vs[:cap], ranges
 

@@ -188,7 +188,9 @@ typedef struct {
     float depth;
     float u, v;
     int radius;
-    int box[4]; /* x0, x1, y0, y1 inclusive, clipped to the image */
+    int box[4];     /* x0, x1, y0, y1 inclusive, clipped to the image */
+    float conic[3]; /* A, B, C of Sigma'^-1 in the chain's FP32        */
+    float opacity;  /* sigmoid(logit) in the chain's FP32               */
 } orc_decision;
 
 /* cam layout (floats): R[9] row-major world->camera, t[3], fx, fy, cx, cy */
@@ -278,12 +280,16 @@ static orc_decision decide_one(const float *mo, const float *q, const float *ls,
     d.box[2] = y0;
     d.box[3] = y1;
     d.visible = 1;
+    d.conic[0] = c / det;
+    d.conic[1] = -(b / det);
+    d.conic[2] = a / det;
+    d.opacity = 1.0f / (1.0f + orc_chain_exp(-mo[3]));
     return d;
 }
 
 int orc_decide(int64_t n, const float *mean_op, const float *quat, const float *logscale,
                const float *cam, int W, int H, uint8_t *visible, float *depth, int32_t *box,
-               float *uv, int32_t *radius) {
+               float *uv, int32_t *radius, float *conic, float *opacity) {
     if (n < 0 || W <= 0 || H <= 0) return 1;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
@@ -293,14 +299,63 @@ int orc_decide(int64_t n, const float *mean_op, const float *quat, const float *
         for (int k = 0; k < 4; ++k) box[4 * i + k] = d.box[k];
         if (uv) { uv[2 * i] = d.u; uv[2 * i + 1] = d.v; }
         if (radius) radius[i] = d.radius;
+        if (conic) for (int k = 0; k < 3; ++k) conic[3 * i + k] = d.conic[k];
+        if (opacity) opacity[i] = d.opacity;
     }
     return 0;
 }
 
+/* Tile cull of the decision chain.  A (Gaussian, tile) pair is kept when the
+ * Gaussian's largest alpha over the rectangle R = tile x pixel box, computed
+ * from the continuous minimum q_min of d^T Sigma'^-1 d over R, reaches
+ * half of the 1/255 skip threshold:  opacity exp(-q_min / 2) >= 0.5 / 255.
+ * Pixels of a dropped pair would all have alpha < 1/255 by a factor-two
+ * margin, so they are skipped by the per-pixel rule anyway: the image does
+ * not change and stays independent of the tile shape.  q_min is 0 when the
+ * projected mean lies in R, else the smallest value over R's four edges,
+ * each minimised in closed form (the 1D quadratic's vertex, clamped). */
+#define ORC_TILE_ALPHA_MIN 0x1.010102p-9f /* 0.5 / 255 in binary32 */
+
+static float qform32(float A, float B, float C, float dx, float dy) {
+    return ((A * dx) * dx + ((2.0f * B) * dx) * dy) + (C * dy) * dy;
+}
+
+static int tile_keep(float u, float v, const float *conic, float op, float x0, float x1, float y0,
+                     float y1) {
+    const float A = conic[0], B = conic[1], C = conic[2];
+    float q;
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
+        q = 0.0f;
+    } else {
+        q = INFINITY;
+        for (int e = 0; e < 2; ++e) {
+            const float xe = e ? x1 : x0;
+            const float dx = xe - u;
+            float ys = v - (B * dx) / C;
+            ys = fminf(fmaxf(ys, y0), y1);
+            const float dy = ys - v;
+            q = fminf(q, qform32(A, B, C, dx, dy));
+        }
+        for (int e = 0; e < 2; ++e) {
+            const float ye = e ? y1 : y0;
+            const float dy = ye - v;
+            float xs = u - (B * dy) / A;
+            xs = fminf(fmaxf(xs, x0), x1);
+            const float dx = xs - u;
+            q = fminf(q, qform32(A, B, C, dx, dy));
+        }
+    }
+    return op * orc_chain_exp(-0.5f * q) >= ORC_TILE_ALPHA_MIN;
+}
+
+int orc_tile_keep(float u, float v, const float *conic, float op, float x0, float x1, float y0, float y1) {
+    return tile_keep(u, v, conic, op, x0, x1, y0, y1);
+}
+
 /* ------------------------------------------------------------------------- */
-/* Tile keys: one (key, gid) pair per (visible Gaussian, tile its pixel box   */
-/* touches); key = tile << 32 | bits(depth).  Sorted by (key, gid) and        */
-/* per-tile [begin, end) ranges; empty tiles get [0, 0).                      */
+/* Tile keys: one (key, gid) pair per (visible Gaussian, tile of its pixel    */
+/* box that survives the tile cull above); key = tile << 32 | bits(depth).    */
+/* Sorted by (key, gid) and per-tile [begin, end) ranges; empty tiles [0, 0). */
 /* ------------------------------------------------------------------------- */
 
 typedef struct { uint64_t key; uint32_t val; } kv_t;
@@ -318,32 +373,49 @@ static uint32_t float_bits(float f) {
     return u;
 }
 
-int orc_keys(int64_t n, const uint8_t *visible, const float *depth, const int32_t *box, int W, int H,
-             int tw, int th, uint64_t *keys, uint32_t *vals, int64_t cap, int64_t *npairs,
-             uint32_t *ranges) {
+/* keep[tile-in-box] decisions of Gaussian i, row-major over its box's tiles */
+static int64_t gaussian_tiles(const int32_t *b, const float *uv, const float *conic, float op, int tw,
+                              int th, int gx, uint32_t *tiles_out) {
+    int64_t k = 0;
+    for (int ty = b[2] / th; ty <= b[3] / th; ++ty)
+        for (int tx = b[0] / tw; tx <= b[1] / tw; ++tx) {
+            const int rx0 = tx * tw > b[0] ? tx * tw : b[0];
+            const int rx1 = tx * tw + tw - 1 < b[1] ? tx * tw + tw - 1 : b[1];
+            const int ry0 = ty * th > b[2] ? ty * th : b[2];
+            const int ry1 = ty * th + th - 1 < b[3] ? ty * th + th - 1 : b[3];
+            if (!tile_keep(uv[0], uv[1], conic, op, (float)rx0, (float)rx1, (float)ry0, (float)ry1)) continue;
+            if (tiles_out) tiles_out[k] = (uint32_t)(ty * gx + tx);
+            ++k;
+        }
+    return k;
+}
+
+int orc_keys(int64_t n, const uint8_t *visible, const float *depth, const int32_t *box, const float *uv,
+             const float *conic, const float *opacity, int W, int H, int tw, int th, uint64_t *keys,
+             uint32_t *vals, int64_t cap, int64_t *npairs, uint32_t *ranges) {
     if (tw <= 0 || th <= 0) return 1;
     const int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
     int64_t total = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (!visible[i]) continue;
-        const int32_t *b = box + 4 * i;
-        total += (int64_t)(b[1] / tw - b[0] / tw + 1) * (b[3] / th - b[2] / th + 1);
+        total += gaussian_tiles(box + 4 * i, uv + 2 * i, conic + 3 * i, opacity[i], tw, th, gx, NULL);
     }
     *npairs = total;
     if (total > cap) return 2;
     kv_t *kv = (kv_t *)malloc(sizeof(kv_t) * (size_t)(total > 0 ? total : 1));
-    if (!kv) return 3;
+    uint32_t *tl = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(gx * gy));
+    if (!kv || !tl) return 3;
     int64_t k = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (!visible[i]) continue;
-        const int32_t *b = box + 4 * i;
-        for (int ty = b[2] / th; ty <= b[3] / th; ++ty)
-            for (int tx = b[0] / tw; tx <= b[1] / tw; ++tx) {
-                kv[k].key = ((uint64_t)(uint32_t)(ty * gx + tx) << 32) | float_bits(depth[i]);
-                kv[k].val = (uint32_t)i;
-                ++k;
-            }
+        const int64_t m = gaussian_tiles(box + 4 * i, uv + 2 * i, conic + 3 * i, opacity[i], tw, th, gx, tl);
+        for (int64_t j = 0; j < m; ++j) {
+            kv[k].key = ((uint64_t)tl[j] << 32) | float_bits(depth[i]);
+            kv[k].val = (uint32_t)i;
+            ++k;
+        }
     }
+    free(tl);
     qsort(kv, (size_t)total, sizeof(kv_t), kv_cmp);
     for (int t = 0; t < gx * gy; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
     for (int64_t j = 0; j < total; ++j) {

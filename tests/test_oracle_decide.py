@@ -70,6 +70,32 @@ def test_near_plane_and_offscreen_cull():
     assert list(dec.visible) == [0, 1, 0, 0, 1]
 
 
+F = np.float32
+
+
+def _py_tile_keep(u, v, conic, op, x0, x1, y0, y1):
+    """The tile cull restated with numpy binary32 scalars (one rounding per op)."""
+    A, B, C = (F(c) for c in conic)
+    u, v, x0, x1, y0, y1 = F(u), F(v), F(x0), F(x1), F(y0), F(y1)
+
+    def qf(dx, dy):
+        return (A * dx * dx + F(2) * B * dx * dy) + C * dy * dy
+
+    if x0 <= u <= x1 and y0 <= v <= y1:
+        q = F(0)
+    else:
+        q = F(np.inf)
+        for xe in (x0, x1):
+            dx = xe - u
+            ys = min(max(v - (B * dx) / C, y0), y1)
+            q = min(q, qf(dx, ys - v))
+        for ye in (y0, y1):
+            dy = ye - v
+            xs = min(max(u - (B * dy) / A, x0), x1)
+            q = min(q, qf(xs - u, dy))
+    return F(op) * F(oracle.chain_exp(float(F(-0.5) * q))) >= F(0.5) / F(255)
+
+
 def _python_keys(dec, W, H, tw, th):
     gx = (W + tw - 1) // tw
     gy = (H + th - 1) // th
@@ -81,7 +107,9 @@ def _python_keys(dec, W, H, tw, th):
         x0, x1, y0, y1 = (int(t) for t in dec.box[i])
         for ty in range(y0 // th, y1 // th + 1):
             for tx in range(x0 // tw, x1 // tw + 1):
-                pairs.append((((ty * gx + tx) << 32) | int(dbits[i]), i))
+                r = (max(tx * tw, x0), min(tx * tw + tw - 1, x1), max(ty * th, y0), min(ty * th + th - 1, y1))
+                if _py_tile_keep(dec.uv[i, 0], dec.uv[i, 1], dec.conic[i], dec.opacity[i], *r):
+                    pairs.append((((ty * gx + tx) << 32) | int(dbits[i]), i))
     pairs.sort()
     ranges = np.zeros(2 * gx * gy, np.uint32)
     for j, (k, _) in enumerate(pairs):
@@ -116,3 +144,43 @@ def test_depth_ties_ordered_by_index():
     for t in range(len(rg) // 2):
         seg = vs[rg[2 * t]:rg[2 * t + 1]]
         assert list(seg) == sorted(seg)
+
+
+def test_chain_conic_and_opacity_match_fp64():
+    p, cam, ca = _scene()
+    dec = oracle.decide(p.mean_op, p.quat, p.logscale, ca, cam.width, cam.height)
+    sc = oracle.Scene64(p.mean_op, p.quat, p.logscale, p.sh)
+    pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
+    v = dec.visible > 0
+    np.testing.assert_allclose(dec.conic[v], pr[v, 2:5], rtol=1e-4, atol=1e-6 * np.abs(pr[v, 2:5]).max())
+    np.testing.assert_allclose(dec.opacity[v], pr[v, 5], rtol=1e-6)
+
+
+def test_dropped_tiles_never_reach_the_alpha_threshold():
+    """Every pixel of a dropped (Gaussian, tile) pair has FP64 alpha < 1/255 by a
+    wide margin: the cull cannot change the image (so the image stays
+    independent of the tile shape)."""
+    p, cam, ca = _scene()
+    W, H = cam.width, cam.height
+    dec = oracle.decide(p.mean_op, p.quat, p.logscale, ca, W, H)
+    sc = oracle.Scene64(p.mean_op, p.quat, p.logscale, p.sh)
+    pr = oracle.project(sc, ca, W, H, dec.visible)
+    dropped = kept = 0
+    worst = 0.0
+    for tw, th in [(16, 16), (8, 32)]:
+        for i in np.flatnonzero(dec.visible):
+            x0, x1, y0, y1 = (int(t) for t in dec.box[i])
+            u, v, A, B, C, op = pr[i, :6]
+            for ty in range(y0 // th, y1 // th + 1):
+                for tx in range(x0 // tw, x1 // tw + 1):
+                    r = (max(tx * tw, x0), min(tx * tw + tw - 1, x1), max(ty * th, y0), min(ty * th + th - 1, y1))
+                    if oracle.tile_keep(dec.uv[i, 0], dec.uv[i, 1], dec.conic[i], dec.opacity[i], *r):
+                        kept += 1
+                        continue
+                    dropped += 1
+                    xs, ys = np.meshgrid(np.arange(r[0], r[1] + 1), np.arange(r[2], r[3] + 1))
+                    dx, dy = xs - u, ys - v
+                    a = op * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+                    worst = max(worst, float(a.max()) * 255)
+    assert dropped > 0 and kept > 0
+    assert worst < 0.51, worst  # max alpha of any dropped pixel, in units of 1/255
