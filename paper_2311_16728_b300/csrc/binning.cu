@@ -1,24 +1,33 @@
 // binning.cu -- tile binning for the tile-based renderer of Photo-SLAM
-// (arXiv 2311.16728) Sec. 3.3: one (key, Gaussian) pair per tile a
-// Gaussian's pixel box touches, key = tile << 32 | bits(depth), sorted by an
-// in-house stable LSD radix sort, then per-tile [begin, end) ranges.
+// (arXiv 2311.16728) Sec. 3.3: one (tile, Gaussian) pair per kept tile of a
+// Gaussian's pixel box, ordered by the 64-bit key tile << 32 | bits(depth)
+// (ties by Gaussian index), plus per-tile [begin, end) ranges.
 //
-// The pair count is data dependent; every kernel reads it from device memory
-// (clamped to the caller's capacity) so the whole sequence can be captured
-// in a CUDA graph with fixed launch shapes.
+// The order is produced by an in-house stable LSD radix sort in two stages
+// that together sort the full 64-bit key:
+//   1. the ~10^5 visible Gaussians are sorted once by their 32 depth bits
+//      (4 passes of 8 bits over N_visible, not over the pairs);
+//   2. pairs are emitted in that depth order and stably sorted by the tile
+//      bits only (ceil(log2 tiles) bits, one or two passes over the pairs).
+// Stable passes over the low 32 bits followed by stable passes over the high
+// bits are exactly an LSD sort of the 64-bit key; doing the low passes
+// before duplication sorts 10^5 items instead of 10^6.
+//
+// Counts are data dependent: every kernel reads them from device memory
+// (clamped to capacity) so the whole sequence has fixed launch shapes and can
+// be captured in a CUDA graph.
 #include "gsr_internal.cuh"
 
 namespace gsr {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;  // Gaussians per thread in the scan / emit kernels
+constexpr int kScanItems = 8;  // Gaussians per thread in the scan / compaction / emit kernels
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;  // pairs per thread per block tile
+constexpr int kSortItems = 16;  // elements per thread per block tile
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRadix = 256;     // bins of one pass (a pass uses at most 8 bits)
 
 __device__ __forceinline__ int64_t clamp_count(const int64_t *d_count, int64_t cap) {
     const int64_t c = *d_count;
@@ -50,103 +59,199 @@ __device__ __forceinline__ uint32_t block_incl_scan_256(uint32_t v, uint32_t *s_
     return v + add;
 }
 
-// ---------------------------------------------------------------- K2: scan + emit
-__global__ void __launch_bounds__(kScanThreads) tiles_reduce_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
-                                                                    uint32_t *__restrict__ block_sums) {
+// Sum of block_sums[0 .. b) (the exclusive prefix of block b) and, when
+// `total` is not NULL, of all of them.  Block-cooperative; few hundred blocks.
+__device__ __forceinline__ int64_t block_prefix(const uint32_t *block_sums, int64_t nblocks, int64_t b,
+                                                int64_t *total, int64_t *s_red) {
+    int64_t pre = 0, all = 0;
+    for (int64_t k = threadIdx.x; k < nblocks; k += kScanThreads) {
+        const uint32_t v = block_sums[k];
+        all += v;
+        if (k < b) pre += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pre += __shfl_xor_sync(0xffffffffu, pre, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_red[wid] = pre;
+        s_red[8 + wid] = all;
+    }
+    __syncthreads();
+    int64_t p = 0, a = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        p += s_red[w];
+        a += s_red[8 + w];
+    }
+    __syncthreads();
+    if (total) *total = a;
+    return p;
+}
+
+// ---------------------------------------------------------------- visible compaction
+__global__ void __launch_bounds__(kScanThreads) vis_count_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
+                                                                 uint32_t *__restrict__ block_sums) {
     __shared__ uint32_t s_warp[8];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) s += ntiles[base + k];
+        if (base + k < n) s += ntiles[base + k] > 0u ? 1u : 0u;
     s = block_incl_scan_256(s, s_warp);
     if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
 }
 
-// one block: exclusive scan of the per-block sums (64-bit), total -> *d_num_pairs
-__global__ void __launch_bounds__(1024) tiles_scan_blocks_kernel(const uint32_t *__restrict__ block_sums,
-                                                                 int64_t nblocks, int64_t *__restrict__ block_offsets,
-                                                                 int64_t *__restrict__ d_num_pairs, int64_t cap,
-                                                                 int32_t *__restrict__ d_status) {
-    __shared__ int64_t s_part[1024];
-    const int t = threadIdx.x;
-    const int64_t per = (nblocks + 1023) / 1024;
-    const int64_t b0 = t * per;
-    int64_t s = 0;
-    for (int64_t k = 0; k < per; ++k)
-        if (b0 + k < nblocks) s += block_sums[b0 + k];
-    s_part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int64_t v = t >= o ? s_part[t - o] : 0;
-        __syncthreads();
-        s_part[t] += v;
-        __syncthreads();
+// visible Gaussians in index order -> (depth bits, index), count -> *d_nvis
+__global__ void __launch_bounds__(kScanThreads) vis_compact_kernel(
+    const uint32_t *__restrict__ ntiles, const float4 *__restrict__ rgb_depth, int64_t n,
+    const uint32_t *__restrict__ block_sums, int64_t nblocks, uint32_t *__restrict__ dkey,
+    uint32_t *__restrict__ dval, int64_t *__restrict__ d_nvis) {
+    __shared__ uint32_t s_warp[8];
+    __shared__ int64_t s_red[16];
+    int64_t total;
+    const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_nvis = total;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    bool vis[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        vis[k] = base + k < n && ntiles[base + k] > 0u;
+        s += vis[k] ? 1u : 0u;
     }
-    int64_t run = s_part[t] - s;  // exclusive prefix of this thread's chunk
-    for (int64_t k = 0; k < per; ++k)
-        if (b0 + k < nblocks) {
-            block_offsets[b0 + k] = run;
-            run += block_sums[b0 + k];
+    const uint32_t incl = block_incl_scan_256(s, s_warp);
+    int64_t pos = pre + (int64_t)(incl - s);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (vis[k]) {
+            dkey[pos] = __float_as_uint(__ldg(&rgb_depth[base + k].w));
+            dval[pos] = (uint32_t)(base + k);
+            ++pos;
         }
-    if (t == 1023) {
-        const int64_t total = s_part[1023];
+}
+
+// ---------------------------------------------------------------- pair emission
+__global__ void __launch_bounds__(kScanThreads) pairs_count_kernel(const uint32_t *__restrict__ ntiles,
+                                                                   const uint32_t *__restrict__ order,
+                                                                   const int64_t *__restrict__ d_nvis, int64_t cap_n,
+                                                                   uint32_t *__restrict__ block_sums) {
+    __shared__ uint32_t s_warp[8];
+    const int64_t nv = clamp_count(d_nvis, cap_n);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < nv) s += ntiles[order[base + k]];
+    s = block_incl_scan_256(s, s_warp);
+    if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
+}
+
+// Emits (tile, gid) for the kept tiles of every visible Gaussian, in depth
+// order; boxes with more than kSmallBoxTiles tiles are emitted by the whole
+// warp (ballot-prefix positions keep the row-major tile order).
+__global__ void __launch_bounds__(kScanThreads) pairs_emit_kernel(
+    const uint32_t *__restrict__ ntiles, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
+    const float4 *__restrict__ c_op_box, const int64_t *__restrict__ d_nvis, int64_t cap_n,
+    const uint32_t *__restrict__ block_sums, int64_t nblocks, int tw, int th, int gx, int64_t cap,
+    uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval, int64_t *__restrict__ d_num_pairs,
+    int32_t *__restrict__ d_status) {
+    __shared__ uint32_t s_warp[8];
+    __shared__ int64_t s_red[16];
+    int64_t total;
+    const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *d_num_pairs = total;
         if (total > cap) raise_status(d_status, GSR_ERR_CAPACITY);
     }
-}
-
-__global__ void __launch_bounds__(kScanThreads) emit_pairs_kernel(
-    const uint32_t *__restrict__ ntiles, const float4 *__restrict__ c_op_box, const float4 *__restrict__ rgb_depth,
-    int64_t n, const int64_t *__restrict__ block_offsets, int tw, int th, int gx, int64_t cap,
-    uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    __shared__ uint32_t s_warp[8];
+    const int64_t nv = clamp_count(d_nvis, cap_n);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t cnt[kScanItems];
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        cnt[k] = (base + k < n) ? ntiles[base + k] : 0u;
+        cnt[k] = base + k < nv ? ntiles[order[base + k]] : 0u;
         s += cnt[k];
     }
     const uint32_t incl = block_incl_scan_256(s, s_warp);
-    int64_t off = block_offsets[blockIdx.x] + (int64_t)(incl - s);
+    int64_t off = pre + (int64_t)(incl - s);
+    const int lane = threadIdx.x & 31;
 #pragma unroll 1
     for (int k = 0; k < kScanItems; ++k) {
-        if (cnt[k] == 0u) continue;
-        const int64_t i = base + k;
-        const float4 cb = __ldg(c_op_box + i);
-        const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
-        const int tx0 = (int)(bx & 0xffffu) / tw, tx1 = (int)(bx >> 16) / tw;
-        const int ty0 = (int)(by & 0xffffu) / th, ty1 = (int)(by >> 16) / th;
-        const uint32_t dbits = __float_as_uint(__ldg(&rgb_depth[i].w));
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                if (off < cap) {
-                    keys[off] = ((uint64_t)(uint32_t)(ty * gx + tx) << 32) | dbits;
-                    vals[off] = (uint32_t)i;
+        const bool has = cnt[k] > 0u;
+        Splat sp{};
+        uint32_t gid = 0;
+        int nbt = 0;
+        if (has) {
+            gid = order[base + k];
+            sp = load_splat(xy_conic, c_op_box, gid);
+            nbt = (sp.x1 / tw - sp.x0 / tw + 1) * (sp.y1 / th - sp.y0 / th + 1);
+        }
+        if (has && nbt <= kSmallBoxTiles) {
+            int64_t o = off;
+            for (int ty = sp.y0 / th; ty <= sp.y1 / th; ++ty)
+                for (int tx = sp.x0 / tw; tx <= sp.x1 / tw; ++tx)
+                    if (tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0,
+                                     sp.y1)) {
+                        if (o < cap) {
+                            tkey[o] = (uint32_t)(ty * gx + tx);
+                            tval[o] = gid;
+                        }
+                        ++o;
+                    }
+        }
+        uint32_t big = __ballot_sync(0xffffffffu, has && nbt > kSmallBoxTiles);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const Splat w = shfl_splat(sp, src);
+            const uint32_t wgid = __shfl_sync(0xffffffffu, gid, src);
+            int64_t o = __shfl_sync(0xffffffffu, off, src);
+            const int tx0 = w.x0 / tw, ty0 = w.y0 / th;
+            const int ntx = w.x1 / tw - tx0 + 1, tot = ntx * (w.y1 / th - ty0 + 1);
+            for (int kb = 0; kb < tot; kb += 32) {
+                const int kk = kb + lane;
+                const int tx = tx0 + kk % ntx, ty = ty0 + kk / ntx;
+                const bool keep =
+                    kk < tot && tile_keep_at(tx, ty, tw, th, w.u, w.v, w.A, w.B, w.C, w.op, w.x0, w.x1, w.y0, w.y1);
+                const uint32_t m = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int64_t p = o + __popc(m & ((1u << lane) - 1u));
+                    if (p < cap) {
+                        tkey[p] = (uint32_t)(ty * gx + tx);
+                        tval[p] = wgid;
+                    }
                 }
-                ++off;
+                o += __popc(m);
             }
+        }
+        off += cnt[k];
     }
 }
 
-// ---------------------------------------------------------------- K3: radix sort
-// One pass = histogram of the digit per block tile, per-digit scan over
-// blocks, then a stable scatter (warp match_any ranks, warps in order).
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *__restrict__ keys,
+// ---------------------------------------------------------------- radix sort passes
+// One stable pass on u32 keys (digit = (key >> shift) & mask, <= 8 bits) with
+// u32 values: per-block digit histogram, per-digit scan over blocks, scatter
+// (warp match_any ranks, warps in order).
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys,
                                                                   const int64_t *__restrict__ d_count, int64_t cap,
-                                                                  int shift, int nblocks,
+                                                                  int shift, uint32_t mask, int nblocks,
                                                                   uint32_t *__restrict__ hist) {
     __shared__ uint32_t s_hist[kRadix];
     s_hist[threadIdx.x] = 0u;
     __syncthreads();
     const int64_t count = clamp_count(d_count, cap);
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const uint32_t lane_lt = (1u << (threadIdx.x & 31)) - 1u;
 #pragma unroll 4
     for (int k = 0; k < kSortItems; ++k) {
         const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (idx < count) atomicAdd(&s_hist[(uint32_t)(keys[idx] >> shift) & (kRadix - 1)], 1u);
+        const bool valid = idx < count;
+        const uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lane_lt) == 0u) atomicAdd(&s_hist[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
@@ -174,9 +279,9 @@ __global__ void __launch_bounds__(256) radix_digit_scan_kernel(uint32_t *__restr
 }
 
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
-    const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint64_t *__restrict__ keys_out,
-    uint32_t *__restrict__ vals_out, const int64_t *__restrict__ d_count, int64_t cap, int shift, int nblocks,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ digit_total) {
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, const int64_t *__restrict__ d_count, int64_t cap, int shift, uint32_t mask,
+    int nblocks, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ digit_total) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t s_base[kRadix];            // running output position per digit
     __shared__ uint32_t s_wcount[kWarps][kRadix];  // per-warp digit counts of one sub-tile
@@ -196,20 +301,19 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll 1
     for (int k = 0; k < kSortItems; ++k) {
+        if (base + (int64_t)k * kSortThreads >= count) break;  // block-uniform
         const int64_t idx = base + (int64_t)k * kSortThreads + t;
         const bool valid = idx < count;
-        uint64_t key = 0;
-        uint32_t val = 0, d = kRadix;  // sentinel digit for the tail
+        uint32_t key = 0, val = 0, d = kRadix;  // sentinel digit for the tail
         if (valid) {
             key = keys_in[idx];
             val = vals_in[idx];
-            d = (uint32_t)(key >> shift) & (kRadix - 1);
+            d = (key >> shift) & mask;
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & lt_mask);
         if (valid && rank == 0) s_wcount[wid][d] = __popc(peers);
         __syncthreads();
-        // digit t: exclusive prefix over warps, advance the running base
         uint32_t run = s_base[t];
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
@@ -231,65 +335,76 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     }
 }
 
-// ---------------------------------------------------------------- K4: tile ranges
-__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t *__restrict__ keys,
-                                                          const int64_t *__restrict__ d_count, int64_t cap,
-                                                          uint2 *__restrict__ ranges) {
+// ---------------------------------------------------------------- ranges + 64-bit keys
+__global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *__restrict__ tkey,
+                                                       const uint32_t *__restrict__ vals,
+                                                       const float4 *__restrict__ rgb_depth,
+                                                       const int64_t *__restrict__ d_count, int64_t cap,
+                                                       uint64_t *__restrict__ keys, uint2 *__restrict__ ranges) {
     const int64_t count = clamp_count(d_count, cap);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const uint32_t tile = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != tile) ranges[tile].x = (uint32_t)i;
-    if (i == count - 1 || (uint32_t)(keys[i + 1] >> 32) != tile) ranges[tile].y = (uint32_t)(i + 1);
+    const uint32_t tile = tkey[i];
+    keys[i] = ((uint64_t)tile << 32) | __float_as_uint(__ldg(&rgb_depth[vals[i]].w));
+    if (i == 0 || tkey[i - 1] != tile) ranges[tile].x = (uint32_t)i;
+    if (i == count - 1 || tkey[i + 1] != tile) ranges[tile].y = (uint32_t)(i + 1);
 }
 
 // ---------------------------------------------------------------- host side
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SortLayout {
-    size_t keys_alt, vals_alt, block_sums, block_offsets, hist, digit_total, total;
-    int64_t scan_blocks, sort_blocks;
+    size_t block_sums, dkey, dval, dkey2, dval2, nvis, tkey, tkey2, tval2, hist, digit_total, total;
+    int64_t scan_blocks, nsort_blocks, psort_blocks;
 };
 
 static SortLayout sort_layout(int64_t n, int64_t cap) {
     SortLayout L;
-    L.scan_blocks = (n + kScanTile - 1) / kScanTile;
-    L.sort_blocks = (cap + kSortTile - 1) / kSortTile;
+    const int64_t n1 = n > 0 ? n : 1, c1 = cap > 0 ? cap : 1;
+    L.scan_blocks = (n1 + kScanTile - 1) / kScanTile;
+    L.nsort_blocks = (n1 + kSortTile - 1) / kSortTile;
+    L.psort_blocks = (c1 + kSortTile - 1) / kSortTile;
+    const int64_t hist_blocks = L.nsort_blocks > L.psort_blocks ? L.nsort_blocks : L.psort_blocks;
     size_t off = 0;
-    L.keys_alt = off; off += align256(sizeof(uint64_t) * (size_t)(cap > 0 ? cap : 1));
-    L.vals_alt = off; off += align256(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
-    L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)(L.scan_blocks > 0 ? L.scan_blocks : 1));
-    L.block_offsets = off; off += align256(sizeof(int64_t) * (size_t)(L.scan_blocks > 0 ? L.scan_blocks : 1));
-    L.hist = off; off += align256(sizeof(uint32_t) * kRadix * (size_t)(L.sort_blocks > 0 ? L.sort_blocks : 1));
+    L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
+    L.dkey = off; off += align256(sizeof(uint32_t) * (size_t)n1);
+    L.dval = off; off += align256(sizeof(uint32_t) * (size_t)n1);
+    L.dkey2 = off; off += align256(sizeof(uint32_t) * (size_t)n1);
+    L.dval2 = off; off += align256(sizeof(uint32_t) * (size_t)n1);
+    L.nvis = off; off += align256(sizeof(int64_t));
+    L.tkey = off; off += align256(sizeof(uint32_t) * (size_t)c1);
+    L.tkey2 = off; off += align256(sizeof(uint32_t) * (size_t)c1);
+    L.tval2 = off; off += align256(sizeof(uint32_t) * (size_t)c1);
+    L.hist = off; off += align256(sizeof(uint32_t) * kRadix * (size_t)hist_blocks);
     L.digit_total = off; off += align256(sizeof(uint32_t) * kRadix);
     L.total = off;
     return L;
 }
 
-static int radix_passes(int64_t tiles) {
-    int bits = 0;
-    while ((int64_t(1) << bits) < tiles) ++bits;
-    return (32 + bits + kRadixBits - 1) / kRadixBits;
+static int ceil_log2(int64_t x) {
+    int b = 0;
+    while ((int64_t(1) << b) < x) ++b;
+    return b;
 }
 
-// Sort (keys, vals) of *d_count pairs in place on 64-bit keys over `passes`
-// 8-bit digits.  The data start in the buffer pair selected by `start_in_alt`
-// and end in (keys, vals).
-static int32_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                                const int64_t *d_count, int64_t cap, int passes, uint32_t *hist,
-                                uint32_t *digit_total, int nblocks, cudaStream_t st) {
-    uint64_t *kin = (passes & 1) ? keys_alt : keys, *kout = (passes & 1) ? keys : keys_alt;
-    uint32_t *vin = (passes & 1) ? vals_alt : vals, *vout = (passes & 1) ? vals : vals_alt;
+// Stable LSD passes over `bits` bits starting at `shift0`: `passes` passes
+// of ceil(bits / passes) bits.  Data start in (k, v); after an odd number of
+// passes they end in (k2, v2), after an even number back in (k, v).
+static void radix_passes(uint32_t *k, uint32_t *v, uint32_t *k2, uint32_t *v2, const int64_t *d_count, int64_t cap,
+                         int shift0, int bits, int passes, uint32_t *hist, uint32_t *digit_total, int nblocks,
+                         cudaStream_t st) {
+    const int per = passes > 0 ? (bits + passes - 1) / passes : 0;
     for (int p = 0; p < passes; ++p) {
-        const int shift = p * kRadixBits;
-        radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(kin, d_count, cap, shift, nblocks, hist);
+        const int shift = shift0 + p * per;
+        const int b = (shift0 + bits - shift) < per ? (shift0 + bits - shift) : per;
+        const uint32_t mask = (1u << b) - 1u;
+        radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(k, d_count, cap, shift, mask, nblocks, hist);
         radix_digit_scan_kernel<<<kRadix, 256, 0, st>>>(hist, nblocks, digit_total);
-        radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_count, cap, shift, nblocks,
-                                                               hist, digit_total);
-        uint64_t *tk = kin; kin = kout; kout = tk;
-        uint32_t *tv = vin; vin = vout; vout = tv;
+        radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(k, v, k2, v2, d_count, cap, shift, mask, nblocks, hist,
+                                                               digit_total);
+        uint32_t *t = k; k = k2; k2 = t;
+        t = v; v = v2; v2 = t;
     }
-    return check_launch("radix sort");
 }
 
 }  // namespace gsr
@@ -314,8 +429,8 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
                                 gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
-    if (!proj || (n > 0 && (!proj->ntiles || !proj->c_op_box || !proj->rgb_depth)) || n < 0 || pair_capacity < 0 ||
-        !tile_ranges || !d_num_pairs || (pair_capacity > 0 && (!keys || !vals))) {
+    if (!proj || (n > 0 && (!proj->ntiles || !proj->xy_conic || !proj->c_op_box || !proj->rgb_depth)) || n < 0 ||
+        pair_capacity < 0 || !tile_ranges || !d_num_pairs || (pair_capacity > 0 && (!keys || !vals))) {
         set_error("gsr_bin_sort: NULL pointer or negative size");
         return GSR_ERR_INVALID_ARG;
     }
@@ -330,12 +445,11 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
     }
     cudaStream_t st = as_cuda(stream);
     char *ws = static_cast<char *>(workspace);
-    uint64_t *keys_alt = reinterpret_cast<uint64_t *>(ws + L.keys_alt);
-    uint32_t *vals_alt = reinterpret_cast<uint32_t *>(ws + L.vals_alt);
-    uint32_t *block_sums = reinterpret_cast<uint32_t *>(ws + L.block_sums);
-    int64_t *block_offsets = reinterpret_cast<int64_t *>(ws + L.block_offsets);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
-    uint32_t *digit_total = reinterpret_cast<uint32_t *>(ws + L.digit_total);
+    auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(ws + off); };
+    uint32_t *block_sums = u32(L.block_sums), *hist = u32(L.hist), *digit_total = u32(L.digit_total);
+    uint32_t *dkey = u32(L.dkey), *dval = u32(L.dval), *dkey2 = u32(L.dkey2), *dval2 = u32(L.dval2);
+    uint32_t *tkey = u32(L.tkey), *tkey2 = u32(L.tkey2), *tval2 = u32(L.tval2);
+    int64_t *d_nvis = reinterpret_cast<int64_t *>(ws + L.nvis);
     const int gx = grid_x(cam, tiling), gy = grid_y(cam, tiling);
     const int64_t tiles = (int64_t)gx * gy;
     if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st) != cudaSuccess)
@@ -345,24 +459,30 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
             return check_launch("memset pair count");
         return GSR_OK;
     }
-    const int passes = radix_passes(tiles);
-    // emit into the buffer that makes the last pass land in (keys, vals)
-    uint64_t *emit_k = (passes & 1) ? keys_alt : keys;
-    uint32_t *emit_v = (passes & 1) ? vals_alt : vals;
-    const int64_t sb = L.scan_blocks;
-    tiles_reduce_kernel<<<(unsigned)sb, kScanThreads, 0, st>>>(proj->ntiles, n, block_sums);
-    tiles_scan_blocks_kernel<<<1, 1024, 0, st>>>(block_sums, sb, block_offsets, d_num_pairs, pair_capacity,
-                                                 d_status);
-    emit_pairs_kernel<<<(unsigned)sb, kScanThreads, 0, st>>>(
-        proj->ntiles, reinterpret_cast<const float4 *>(proj->c_op_box),
-        reinterpret_cast<const float4 *>(proj->rgb_depth), n, block_offsets, tiling->tile_w, tiling->tile_h, gx,
-        pair_capacity, emit_k, emit_v);
-    if ((rc = check_launch("emit pairs"))) return rc;
+    const float4 *xy = reinterpret_cast<const float4 *>(proj->xy_conic);
+    const float4 *cb = reinterpret_cast<const float4 *>(proj->c_op_box);
+    const float4 *rd = reinterpret_cast<const float4 *>(proj->rgb_depth);
+    const unsigned sb = (unsigned)L.scan_blocks;
+    // 1. visible Gaussians -> (depth bits, index), then the four depth passes
+    vis_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, block_sums);
+    vis_compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, rd, n, block_sums, L.scan_blocks, dkey, dval, d_nvis);
+    radix_passes(dkey, dval, dkey2, dval2, d_nvis, n, 0, 32, 4, hist, digit_total, (int)L.nsort_blocks, st);
+    if ((rc = check_launch("depth sort"))) return rc;
+    // 2. pairs in depth order, then the tile passes (ending in tkey / vals)
+    const int tbits = ceil_log2(tiles);
+    const int tpasses = (tbits + 7) / 8;
+    uint32_t *ek = (tpasses & 1) ? tkey2 : tkey;
+    uint32_t *ev = (tpasses & 1) ? tval2 : vals;
+    pairs_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums);
+    pairs_emit_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, xy, cb, d_nvis, n, block_sums, L.scan_blocks,
+                                                   tiling->tile_w, tiling->tile_h, gx, pair_capacity, ek, ev,
+                                                   d_num_pairs, d_status);
+    if ((rc = check_launch("pair emission"))) return rc;
     if (pair_capacity == 0) return GSR_OK;
-    if ((rc = radix_sort_pairs(keys, vals, keys_alt, vals_alt, d_num_pairs, pair_capacity, passes, hist, digit_total,
-                               (int)L.sort_blocks, st)))
-        return rc;
+    radix_passes(ek, ev, (tpasses & 1) ? tkey : tkey2, (tpasses & 1) ? vals : tval2, d_num_pairs, pair_capacity, 0,
+                 tbits, tpasses, hist, digit_total, (int)L.psort_blocks, st);
     const unsigned rb = (unsigned)((pair_capacity + 255) / 256);
-    tile_ranges_kernel<<<rb, 256, 0, st>>>(keys, d_num_pairs, pair_capacity, reinterpret_cast<uint2 *>(tile_ranges));
-    return check_launch("tile_ranges_kernel");
+    finalize_kernel<<<rb, 256, 0, st>>>(tkey, vals, rd, d_num_pairs, pair_capacity, keys,
+                                        reinterpret_cast<uint2 *>(tile_ranges));
+    return check_launch("finalize_kernel");
 }

@@ -186,6 +186,104 @@ __device__ __forceinline__ bool decide_chain(const float4 mo, const float4 q, co
     return o.x0 <= o.x1 && o.y0 <= o.y1;
 }
 
+// Conic (inverse of the dilated 2D covariance) and opacity in the chain's
+// FP32: these feed the tile cull below and are the values the render uses.
+__device__ __forceinline__ void chain_conic_opacity(const Chain &c, float logit, float &A, float &B, float &C,
+                                                    float &op) {
+    A = FD(c.c, c.det);
+    B = -FD(c.b, c.det);
+    C = FD(c.a, c.det);
+    op = FD(1.0f, FA(1.0f, chain_exp(-logit)));
+}
+
+// Tile cull.  A (Gaussian, tile) pair is kept when opacity exp(-q_min / 2)
+// >= 0.5 / 255, q_min being the continuous minimum of d^T Sigma'^-1 d over
+// R = tile x pixel box (0 when the mean lies in R, else the least of R's four
+// edges, each minimised at its clamped 1D vertex).  A dropped pair has alpha
+// < 1/255 at every pixel by a factor-two margin, so the per-pixel skip would
+// drop it anyway: the image does not depend on this cull or on the tiling.
+constexpr float kTileAlphaMin = 0x1.010102p-9f;  // 0.5 / 255 in binary32
+
+__device__ __forceinline__ float qform32(float A, float B, float C, float dx, float dy) {
+    return FA(FA(FM(FM(A, dx), dx), FM(FM(FM(2.0f, B), dx), dy)), FM(FM(C, dy), dy));
+}
+
+__device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, float C, float op, float x0, float x1,
+                                          float y0, float y1) {
+    float q;
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
+        q = 0.0f;
+    } else {
+        q = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float dx = FS(e ? x1 : x0, u);
+            float ys = FS(v, FD(FM(B, dx), C));
+            ys = fminf(fmaxf(ys, y0), y1);
+            q = fminf(q, qform32(A, B, C, dx, FS(ys, v)));
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float dy = FS(e ? y1 : y0, v);
+            float xs = FS(u, FD(FM(B, dy), A));
+            xs = fminf(fmaxf(xs, x0), x1);
+            q = fminf(q, qform32(A, B, C, FS(xs, u), dy));
+        }
+    }
+    return FM(op, chain_exp(FM(-0.5f, q))) >= kTileAlphaMin;
+}
+
+// Tile (tx, ty) of a Gaussian with pixel box [x0, x1] x [y0, y1]: keep?
+__device__ __forceinline__ bool tile_keep_at(int tx, int ty, int tw, int th, float u, float v, float A, float B,
+                                             float C, float op, int x0, int x1, int y0, int y1) {
+    const int rx0 = max(tx * tw, x0), rx1 = min(tx * tw + tw - 1, x1);
+    const int ry0 = max(ty * th, y0), ry1 = min(ty * th + th - 1, y1);
+    return tile_keep(u, v, A, B, C, op, (float)rx0, (float)rx1, (float)ry0, (float)ry1);
+}
+
+// Record of one projected Gaussian as the binning kernels read it back.
+struct Splat {
+    float u, v, A, B, C, op;
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ Splat load_splat(const float4 *xy_conic, const float4 *c_op_box, int64_t i) {
+    const float4 a = xy_conic[i], b = c_op_box[i];
+    const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+    return Splat{a.x, a.y, a.z, a.w, b.x, b.y, (int)(bx & 0xffffu), (int)(bx >> 16), (int)(by & 0xffffu),
+                 (int)(by >> 16)};
+}
+
+// Number of kept tiles of one Gaussian, computed by the whole warp (every
+// lane passes the same splat; the result is returned to every lane).
+__device__ __forceinline__ uint32_t warp_count_tiles(const Splat &s, int tw, int th) {
+    const int tx0 = s.x0 / tw, ty0 = s.y0 / th;
+    const int ntx = s.x1 / tw - tx0 + 1, total = ntx * (s.y1 / th - ty0 + 1);
+    uint32_t c = 0;
+    for (int k = (int)(threadIdx.x & 31); k < total; k += 32)
+        c += tile_keep_at(tx0 + k % ntx, ty0 + k / ntx, tw, th, s.u, s.v, s.A, s.B, s.C, s.op, s.x0, s.x1, s.y0, s.y1)
+                 ? 1u
+                 : 0u;
+    return __reduce_add_sync(0xffffffffu, c);
+}
+
+__device__ __forceinline__ Splat shfl_splat(const Splat &s, int src) {
+    Splat o;
+    o.u = __shfl_sync(0xffffffffu, s.u, src);
+    o.v = __shfl_sync(0xffffffffu, s.v, src);
+    o.A = __shfl_sync(0xffffffffu, s.A, src);
+    o.B = __shfl_sync(0xffffffffu, s.B, src);
+    o.C = __shfl_sync(0xffffffffu, s.C, src);
+    o.op = __shfl_sync(0xffffffffu, s.op, src);
+    o.x0 = __shfl_sync(0xffffffffu, s.x0, src);
+    o.x1 = __shfl_sync(0xffffffffu, s.x1, src);
+    o.y0 = __shfl_sync(0xffffffffu, s.y0, src);
+    o.y1 = __shfl_sync(0xffffffffu, s.y1, src);
+    return o;
+}
+
+constexpr int kSmallBoxTiles = 8;  // boxes with more tiles are counted / emitted by a whole warp
+
 // ---------------------------------------------------------------- SH basis
 // Real orthonormal SH with the Condon-Shortley phase, index l*l + l + m,
 // written as the textbook polynomials in the unit direction (x, y, z).

@@ -47,40 +47,60 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussK g, CamK cam,
                                                              float4 *__restrict__ rgb_depth,
                                                              uint32_t *__restrict__ ntiles) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
-    const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+    const bool active = i < g.n;
     Chain c;
-    if (!decide_chain(mo, q, ls, cam, c)) {
-        ntiles[i] = 0u;
-        return;
-    }
-    const float inv_det = 1.0f / c.det;
-    const float A = c.c * inv_det, B = -c.b * inv_det, C = c.a * inv_det;
-    const float opacity = 1.0f / (1.0f + __expf(-mo.w));
-    // colour: SH at the unit view direction (mean - camera centre)
-    const float3 cc = cam_center(cam);
-    float dx = mo.x - cc.x, dy = mo.y - cc.y, dz = mo.z - cc.z;
-    const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= inv_len; dy *= inv_len; dz *= inv_len;
-    float sh[48];
-    load_sh(g.sh, g.n, i, g.deg, sh);
-    float Y[16];
-    sh_basis(dx, dy, dz, g.deg, Y, nullptr);
-    const int nc = (g.deg + 1) * (g.deg + 1);
-    float rgb[3];
+    bool vis = false;
+    Splat s{};
+    if (active) {
+        const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+        vis = decide_chain(mo, q, ls, cam, c);
+        if (vis) {
+            float A, B, C, op;
+            chain_conic_opacity(c, mo.w, A, B, C, op);
+            // colour: SH at the unit view direction (mean - camera centre)
+            const float3 cc = cam_center(cam);
+            float dx = mo.x - cc.x, dy = mo.y - cc.y, dz = mo.z - cc.z;
+            const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= inv_len; dy *= inv_len; dz *= inv_len;
+            float sh[48];
+            load_sh(g.sh, g.n, i, g.deg, sh);
+            float Y[16];
+            sh_basis(dx, dy, dz, g.deg, Y, nullptr);
+            const int nc = (g.deg + 1) * (g.deg + 1);
+            float rgb[3];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.5f;
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < nc) acc += sh[3 * k + ch] * Y[k];
-        rgb[ch] = fmaxf(acc, 0.0f);
+                for (int k = 0; k < 16; ++k)
+                    if (k < nc) acc += sh[3 * k + ch] * Y[k];
+                rgb[ch] = fmaxf(acc, 0.0f);
+            }
+            const uint32_t bx = (uint32_t)c.x0 | ((uint32_t)c.x1 << 16), by = (uint32_t)c.y0 | ((uint32_t)c.y1 << 16);
+            xy_conic[i] = make_float4(c.u, c.v, A, B);
+            c_op_box[i] = make_float4(C, op, __uint_as_float(bx), __uint_as_float(by));
+            rgb_depth[i] = make_float4(rgb[0], rgb[1], rgb[2], c.zc);
+            s = Splat{c.u, c.v, A, B, C, op, c.x0, c.x1, c.y0, c.y1};
+        }
     }
-    xy_conic[i] = make_float4(c.u, c.v, A, B);
-    c_op_box[i] = make_float4(C, opacity, __uint_as_float((uint32_t)c.x0 | ((uint32_t)c.x1 << 16)),
-                              __uint_as_float((uint32_t)c.y0 | ((uint32_t)c.y1 << 16)));
-    rgb_depth[i] = make_float4(rgb[0], rgb[1], rgb[2], c.zc);
-    ntiles[i] = (uint32_t)((c.x1 / cam.tw - c.x0 / cam.tw + 1) * (c.y1 / cam.th - c.y0 / cam.th + 1));
+    // kept tiles: small boxes in the thread, large ones by the whole warp
+    const int nbt = vis ? (s.x1 / cam.tw - s.x0 / cam.tw + 1) * (s.y1 / cam.th - s.y0 / cam.th + 1) : 0;
+    uint32_t cnt = 0;
+    if (vis && nbt <= kSmallBoxTiles) {
+        for (int ty = s.y0 / cam.th; ty <= s.y1 / cam.th; ++ty)
+            for (int tx = s.x0 / cam.tw; tx <= s.x1 / cam.tw; ++tx)
+                cnt += tile_keep_at(tx, ty, cam.tw, cam.th, s.u, s.v, s.A, s.B, s.C, s.op, s.x0, s.x1, s.y0, s.y1)
+                           ? 1u
+                           : 0u;
+    }
+    uint32_t big = __ballot_sync(0xffffffffu, vis && nbt > kSmallBoxTiles);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t c2 = warp_count_tiles(shfl_splat(s, src), cam.tw, cam.th);
+        if ((int)(threadIdx.x & 31) == src) cnt = c2;
+    }
+    if (active) ntiles[i] = vis ? cnt : 0u;
 }
 
 // K8: screen-space gradients (du, dv, dA, dB, dC, dopacity, dr, dg, db) of one
@@ -145,12 +165,11 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussK g, CamK cam,
     }
     const float vd = dvh.x * vx + dvh.y * vy + dvh.z * vz;
     float dmx = (dvh.x - vx * vd) * inv_len, dmy = (dvh.y - vy * vd) * inv_len, dmz = (dvh.z - vz * vd) * inv_len;
-    // ---- opacity
-    const float sig = 1.0f / (1.0f + __expf(-mo.w));
+    // ---- opacity (the same FP32 conic and opacity the forward used)
+    float A, B, C, sig;
+    chain_conic_opacity(c, mo.w, A, B, C, sig);
     const float dlogit = dop * sig * (1.0f - sig);
     // ---- conic -> Sigma':  G_S' = -Q G_Q Q,  G_Q = [[dA, dB/2], [dB/2, dC]]
-    const float inv_det = 1.0f / c.det;
-    const float A = c.c * inv_det, B = -c.b * inv_det, C = c.a * inv_det;
     const float hB = 0.5f * dB;
     const float t00 = A * dA + B * hB, t01 = A * hB + B * dC;
     const float t10 = B * dA + C * hB, t11 = B * hB + C * dC;

@@ -49,8 +49,11 @@ def _check_keys(vb, dec, keys_ref):
     assert np.array_equal(gk, ks), "tile|depth keys differ"
     assert np.array_equal(gv, vs), "sorted Gaussian order differs"
     assert np.array_equal(grg, rg), "per-tile ranges differ"
-    vis = vb.ntiles.cpu().numpy() > 0
-    assert np.array_equal(vis, dec.visible > 0), "cull set differs"
+    ntiles = vb.ntiles.cpu().numpy().view(np.uint32)[:len(dec.visible)]
+    kept = np.bincount(vs, minlength=len(dec.visible))
+    assert np.array_equal(ntiles, kept), "kept-tile counts per Gaussian differ"
+    vis = ntiles > 0
+    assert np.array_equal(vis, (dec.visible > 0) & (kept > 0)), "cull set differs"
     rd = vb.rgb_depth.cpu().numpy()
     assert np.array_equal(rd[vis, 3].view(np.uint32), dec.depth[vis].view(np.uint32)), "depth bits differ"
     cb = vb.c_op_box.cpu().numpy()
