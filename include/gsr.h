@@ -154,16 +154,20 @@ int32_t gsr_preprocess(const gsr_gaussians *g, const gsr_camera *cam, const gsr_
 int32_t gsr_bin_sort_workspace_size(int64_t n, int64_t pair_capacity, const gsr_camera *cam,
                                     const gsr_tiling *tiling, size_t *bytes);
 
-/* Tile binning (Sec. 3.3 "tile-based renderer"): an exclusive scan of
- * ntiles gives each visible Gaussian its slots; one (key, gid) pair is
- * emitted per tile its box touches, key = tile << 32 | bits(depth); an
- * in-house stable LSD radix sort orders the pairs by key over the
- * 32 + ceil(log2 tiles) significant bits (equal keys keep Gaussian order);
- * tile_ranges[2 t], [2 t + 1] = [begin, end) of tile t in the sorted arrays
- * (empty tiles [0, 0)).  keys/vals hold pair_capacity entries; the pair
- * count is written to *d_num_pairs.  If it exceeds pair_capacity, the
- * GSR_ERR_CAPACITY bit is set in *d_status, *d_num_pairs holds the count
- * needed and the output is truncated (never written out of bounds). */
+/* Tile binning (Sec. 3.3 "tile-based renderer").  Every visible Gaussian's
+ * box tiles are candidates; a candidate survives when the Gaussian's largest
+ * alpha over (tile x pixel box) reaches 0.5/255 -- half the per-pixel skip
+ * threshold, so a dropped pair would never blend at any pixel and the image
+ * is unchanged.  One (key, gid) pair is output per kept tile, key =
+ * tile << 32 | bits(depth), sorted by key with equal keys in Gaussian order
+ * (an in-house stable LSD radix sort: the visible Gaussians by depth first,
+ * then the pairs by tile bits); tile_ranges[2 t], [2 t + 1] = [begin, end)
+ * of tile t (empty tiles [0, 0)).  keys/vals hold pair_capacity entries; the
+ * pair count is written to *d_num_pairs.  If it exceeds pair_capacity (or
+ * the candidates exceed 2 x pair_capacity), the GSR_ERR_CAPACITY bit is set
+ * in *d_status and *d_num_pairs holds a capacity that suffices for a retry
+ * (the pair count, or the candidate count); outputs are then truncated but
+ * nothing is written out of bounds. */
 int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camera *cam, const gsr_tiling *tiling,
                      uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
                      int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,

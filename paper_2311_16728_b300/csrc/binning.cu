@@ -7,7 +7,8 @@
 // that together sort the full 64-bit key:
 //   1. the ~10^5 visible Gaussians are sorted once by their 32 depth bits
 //      (4 passes of 8 bits over N_visible, not over the pairs);
-//   2. pairs are emitted in that depth order and stably sorted by the tile
+//   2. their box tiles are expanded in that depth order, culled (see
+//      tile_keep) and compacted, and the pairs are stably sorted by the tile
 //      bits only (ceil(log2 tiles) bits, one or two passes over the pairs).
 // Stable passes over the low 32 bits followed by stable passes over the high
 // bits are exactly an LSD sort of the 64-bit key; doing the low passes
@@ -133,11 +134,16 @@ __global__ void __launch_bounds__(kScanThreads) vis_compact_kernel(
         }
 }
 
-// ---------------------------------------------------------------- pair emission
-__global__ void __launch_bounds__(kScanThreads) pairs_count_kernel(const uint32_t *__restrict__ ntiles,
-                                                                   const uint32_t *__restrict__ order,
-                                                                   const int64_t *__restrict__ d_nvis, int64_t cap_n,
-                                                                   uint32_t *__restrict__ block_sums) {
+// ---------------------------------------------------------------- pair expansion
+// Candidates are the (Gaussian, box tile) slots of the depth-ordered visible
+// list.  One thread per candidate runs the tile cull, so a few near-camera
+// Gaussians with thousands of box tiles spread over the whole GPU instead of
+// serialising in the warps that hold them; an ordered compaction of the kept
+// candidates then yields the pairs in depth order (row-major within a box).
+__global__ void __launch_bounds__(kScanThreads) cand_count_kernel(const uint32_t *__restrict__ ntiles,
+                                                                  const uint32_t *__restrict__ order,
+                                                                  const int64_t *__restrict__ d_nvis, int64_t cap_n,
+                                                                  uint32_t *__restrict__ block_sums) {
     __shared__ uint32_t s_warp[8];
     const int64_t nv = clamp_count(d_nvis, cap_n);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
@@ -149,24 +155,27 @@ __global__ void __launch_bounds__(kScanThreads) pairs_count_kernel(const uint32_
     if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
 }
 
-// Emits (tile, gid) for the kept tiles of every visible Gaussian, in depth
-// order; boxes with more than kSmallBoxTiles tiles are emitted by the whole
-// warp (ballot-prefix positions keep the row-major tile order).
-__global__ void __launch_bounds__(kScanThreads) pairs_emit_kernel(
-    const uint32_t *__restrict__ ntiles, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
-    const float4 *__restrict__ c_op_box, const int64_t *__restrict__ d_nvis, int64_t cap_n,
-    const uint32_t *__restrict__ block_sums, int64_t nblocks, int tw, int th, int gx, int64_t cap,
-    uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval, int64_t *__restrict__ d_num_pairs,
+// coff[i] = first candidate slot of item i; coff[nv] = *d_ncand = total.  If
+// the candidates exceed their capacity, the GSR_ERR_CAPACITY bit is set and
+// *d_num_pairs receives the candidate count (an upper bound on the pairs).
+__global__ void __launch_bounds__(kScanThreads) cand_offsets_kernel(
+    const uint32_t *__restrict__ ntiles, const uint32_t *__restrict__ order, const int64_t *__restrict__ d_nvis,
+    int64_t cap_n, const uint32_t *__restrict__ block_sums, int64_t nblocks, int64_t cand_cap,
+    uint32_t *__restrict__ coff, int64_t *__restrict__ d_ncand, int64_t *__restrict__ d_num_pairs,
     int32_t *__restrict__ d_status) {
     __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_red[16];
     int64_t total;
     const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *d_num_pairs = total;
-        if (total > cap) raise_status(d_status, GSR_ERR_CAPACITY);
-    }
     const int64_t nv = clamp_count(d_nvis, cap_n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *d_ncand = total;
+        coff[nv] = (uint32_t)total;
+        if (total > cand_cap) {
+            *d_num_pairs = total;
+            raise_status(d_status, GSR_ERR_CAPACITY);
+        }
+    }
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t cnt[kScanItems];
     uint32_t s = 0;
@@ -177,58 +186,137 @@ __global__ void __launch_bounds__(kScanThreads) pairs_emit_kernel(
     }
     const uint32_t incl = block_incl_scan_256(s, s_warp);
     int64_t off = pre + (int64_t)(incl - s);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < nv) {
+            coff[base + k] = (uint32_t)off;
+            off += cnt[k];
+        }
+}
+
+constexpr int kExpandThreads = 256;
+constexpr int kExpandItems = 4;
+constexpr int kExpandTile = kExpandThreads * kExpandItems;
+
+// largest i in [0, n) with a[i] <= x (a ascending, a[0] <= x), by one warp
+__device__ __forceinline__ int64_t warp_upper_index(const uint32_t *a, int64_t n, uint32_t x) {
+    int64_t lo = 0, hi = n;  // answer in [lo, hi)
     const int lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int k = 0; k < kScanItems; ++k) {
-        const bool has = cnt[k] > 0u;
-        Splat sp{};
-        uint32_t gid = 0;
-        int nbt = 0;
-        if (has) {
-            gid = order[base + k];
-            sp = load_splat(xy_conic, c_op_box, gid);
-            nbt = (sp.x1 / tw - sp.x0 / tw + 1) * (sp.y1 / th - sp.y0 / th + 1);
-        }
-        if (has && nbt <= kSmallBoxTiles) {
-            int64_t o = off;
-            for (int ty = sp.y0 / th; ty <= sp.y1 / th; ++ty)
-                for (int tx = sp.x0 / tw; tx <= sp.x1 / tw; ++tx)
-                    if (tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0,
-                                     sp.y1)) {
-                        if (o < cap) {
-                            tkey[o] = (uint32_t)(ty * gx + tx);
-                            tval[o] = gid;
-                        }
-                        ++o;
-                    }
-        }
-        uint32_t big = __ballot_sync(0xffffffffu, has && nbt > kSmallBoxTiles);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const Splat w = shfl_splat(sp, src);
-            const uint32_t wgid = __shfl_sync(0xffffffffu, gid, src);
-            int64_t o = __shfl_sync(0xffffffffu, off, src);
-            const int tx0 = w.x0 / tw, ty0 = w.y0 / th;
-            const int ntx = w.x1 / tw - tx0 + 1, tot = ntx * (w.y1 / th - ty0 + 1);
-            for (int kb = 0; kb < tot; kb += 32) {
-                const int kk = kb + lane;
-                const int tx = tx0 + kk % ntx, ty = ty0 + kk / ntx;
-                const bool keep =
-                    kk < tot && tile_keep_at(tx, ty, tw, th, w.u, w.v, w.A, w.B, w.C, w.op, w.x0, w.x1, w.y0, w.y1);
-                const uint32_t m = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int64_t p = o + __popc(m & ((1u << lane) - 1u));
-                    if (p < cap) {
-                        tkey[p] = (uint32_t)(ty * gx + tx);
-                        tval[p] = wgid;
-                    }
-                }
-                o += __popc(m);
-            }
-        }
-        off += cnt[k];
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t probe = lo + (int64_t)lane * step;
+        const bool le = probe < hi && a[probe] <= x;
+        const uint32_t m = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(m);  // highest lane whose probe is <= x (lane 0 always is)
+        const int64_t nlo = lo + (int64_t)last * step;
+        hi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
     }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kExpandThreads) expand_kernel(
+    const uint32_t *__restrict__ coff, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
+    const float4 *__restrict__ c_op_box, const int64_t *__restrict__ d_nvis, int64_t cap_n,
+    const int64_t *__restrict__ d_ncand, int64_t cand_cap, int tw, int th, int gx, uint8_t *__restrict__ flag,
+    uint32_t *__restrict__ ctile, uint32_t *__restrict__ cgid) {
+    __shared__ uint32_t s_off[kExpandTile + 1];
+    __shared__ int64_t s_i0;
+    __shared__ int s_m;
+    const int64_t ncand = clamp_count(d_ncand, cand_cap);
+    const int64_t nv = clamp_count(d_nvis, cap_n);
+    const int64_t s0 = (int64_t)blockIdx.x * kExpandTile;
+    if (s0 >= ncand) return;
+    const int64_t s_last = (s0 + kExpandTile < ncand ? s0 + kExpandTile : ncand) - 1;
+    if (threadIdx.x < 32) {
+        const int64_t i0 = warp_upper_index(coff, nv, (uint32_t)s0);
+        const int64_t i1 = warp_upper_index(coff, nv, (uint32_t)s_last);
+        if (threadIdx.x == 0) {
+            s_i0 = i0;
+            s_m = (int)(i1 - i0 + 1);  // every item owns >= 1 slot, so m <= kExpandTile
+        }
+    }
+    __syncthreads();
+    const int64_t i0 = s_i0;
+    const int m = s_m;
+    for (int j = threadIdx.x; j <= m; j += kExpandThreads) s_off[j] = coff[i0 + j];
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < kExpandItems; ++r) {
+        const int64_t slot = s0 + (int64_t)r * kExpandThreads + threadIdx.x;
+        if (slot >= ncand) break;
+        int lo = 0, hi = m;  // s_off[lo] <= slot < s_off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= (uint32_t)slot) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t gid = order[i0 + lo];
+        const int k = (int)((uint32_t)slot - s_off[lo]);
+        const Splat sp = load_splat(xy_conic, c_op_box, gid);
+        const int tx0 = sp.x0 / tw, ntx = sp.x1 / tw - tx0 + 1;
+        const int tx = tx0 + k % ntx, ty = sp.y0 / th + k / ntx;
+        flag[slot] = tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1)
+                         ? 1
+                         : 0;
+        ctile[slot] = (uint32_t)(ty * gx + tx);
+        cgid[slot] = gid;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) kept_count_kernel(const uint8_t *__restrict__ flag,
+                                                                  const int64_t *__restrict__ d_ncand,
+                                                                  int64_t cand_cap,
+                                                                  uint32_t *__restrict__ block_sums) {
+    __shared__ uint32_t s_warp[8];
+    const int64_t nc = clamp_count(d_ncand, cand_cap);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < nc) s += flag[base + k];
+    s = block_incl_scan_256(s, s_warp);
+    if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kScanThreads) kept_compact_kernel(
+    const uint8_t *__restrict__ flag, const uint32_t *__restrict__ ctile, const uint32_t *__restrict__ cgid,
+    const int64_t *__restrict__ d_ncand, int64_t cand_cap, const uint32_t *__restrict__ block_sums,
+    int64_t nblocks, int64_t cap, uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
+    int64_t *__restrict__ d_num_pairs, int64_t *__restrict__ d_written, int32_t *__restrict__ d_status) {
+    __shared__ uint32_t s_warp[8];
+    __shared__ int64_t s_red[16];
+    int64_t total;
+    const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
+    const int64_t nc_raw = *d_ncand;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // pairs actually present for the sort, whatever overflowed upstream
+        *d_written = total < cap ? total : cap;
+        if (nc_raw <= cand_cap) {
+            *d_num_pairs = total;
+            if (total > cap) raise_status(d_status, GSR_ERR_CAPACITY);
+        }
+    }
+    const int64_t nc = nc_raw < cand_cap ? nc_raw : cand_cap;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+    uint8_t f[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        f[k] = base + k < nc ? flag[base + k] : 0;
+        s += f[k];
+    }
+    const uint32_t incl = block_incl_scan_256(s, s_warp);
+    int64_t pos = pre + (int64_t)(incl - s);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (f[k]) {
+            if (pos < cap) {
+                tkey[pos] = ctile[base + k];
+                tval[pos] = cgid[base + k];
+            }
+            ++pos;
+        }
 }
 
 // ---------------------------------------------------------------- radix sort passes
@@ -340,11 +428,13 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *__restric
                                                        const uint32_t *__restrict__ vals,
                                                        const float4 *__restrict__ rgb_depth,
                                                        const int64_t *__restrict__ d_count, int64_t cap,
-                                                       uint64_t *__restrict__ keys, uint2 *__restrict__ ranges) {
+                                                       uint32_t ntiles_total, uint64_t *__restrict__ keys,
+                                                       uint2 *__restrict__ ranges) {
     const int64_t count = clamp_count(d_count, cap);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const uint32_t tile = tkey[i];
+    if (tile >= ntiles_total) return;  // cannot happen for emitted pairs; keeps every write in bounds
     keys[i] = ((uint64_t)tile << 32) | __float_as_uint(__ldg(&rgb_depth[vals[i]].w));
     if (i == 0 || tkey[i - 1] != tile) ranges[tile].x = (uint32_t)i;
     if (i == count - 1 || tkey[i + 1] != tile) ranges[tile].y = (uint32_t)(i + 1);
@@ -354,18 +444,30 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *__restric
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SortLayout {
-    size_t block_sums, dkey, dval, dkey2, dval2, nvis, tkey, tkey2, tval2, hist, digit_total, total;
-    int64_t scan_blocks, nsort_blocks, psort_blocks;
+    size_t block_sums, dkey, dval, dkey2, dval2, nvis, tkey, tkey2, tval2, hist, digit_total;
+    size_t coff, ncand, written, flag, ctile, cgid, cblock_sums, total;
+    int64_t scan_blocks, nsort_blocks, psort_blocks, cand_cap, cand_blocks, expand_blocks;
 };
 
+// Candidates (box tiles before the cull) get twice the pair capacity.
 static SortLayout sort_layout(int64_t n, int64_t cap) {
     SortLayout L;
     const int64_t n1 = n > 0 ? n : 1, c1 = cap > 0 ? cap : 1;
+    L.cand_cap = 2 * c1 > 1024 ? 2 * c1 : 1024;
     L.scan_blocks = (n1 + kScanTile - 1) / kScanTile;
     L.nsort_blocks = (n1 + kSortTile - 1) / kSortTile;
     L.psort_blocks = (c1 + kSortTile - 1) / kSortTile;
+    L.cand_blocks = (L.cand_cap + kScanTile - 1) / kScanTile;
+    L.expand_blocks = (L.cand_cap + kExpandTile - 1) / kExpandTile;
     const int64_t hist_blocks = L.nsort_blocks > L.psort_blocks ? L.nsort_blocks : L.psort_blocks;
     size_t off = 0;
+    L.coff = off; off += align256(sizeof(uint32_t) * (size_t)(n1 + 1));
+    L.ncand = off; off += align256(sizeof(int64_t));
+    L.written = off; off += align256(sizeof(int64_t));
+    L.flag = off; off += align256(sizeof(uint8_t) * (size_t)L.cand_cap);
+    L.ctile = off; off += align256(sizeof(uint32_t) * (size_t)L.cand_cap);
+    L.cgid = off; off += align256(sizeof(uint32_t) * (size_t)L.cand_cap);
+    L.cblock_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.cand_blocks);
     L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
     L.dkey = off; off += align256(sizeof(uint32_t) * (size_t)n1);
     L.dval = off; off += align256(sizeof(uint32_t) * (size_t)n1);
@@ -473,16 +575,25 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
     const int tpasses = (tbits + 7) / 8;
     uint32_t *ek = (tpasses & 1) ? tkey2 : tkey;
     uint32_t *ev = (tpasses & 1) ? tval2 : vals;
-    pairs_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums);
-    pairs_emit_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, xy, cb, d_nvis, n, block_sums, L.scan_blocks,
-                                                   tiling->tile_w, tiling->tile_h, gx, pair_capacity, ek, ev,
-                                                   d_num_pairs, d_status);
-    if ((rc = check_launch("pair emission"))) return rc;
+    uint32_t *coff = u32(L.coff), *ctile = u32(L.ctile), *cgid = u32(L.cgid), *cblock_sums = u32(L.cblock_sums);
+    uint8_t *flag = reinterpret_cast<uint8_t *>(ws + L.flag);
+    int64_t *d_ncand = reinterpret_cast<int64_t *>(ws + L.ncand);
+    int64_t *d_written = reinterpret_cast<int64_t *>(ws + L.written);
+    cand_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums);
+    cand_offsets_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums, L.scan_blocks,
+                                                     L.cand_cap, coff, d_ncand, d_num_pairs, d_status);
+    expand_kernel<<<(unsigned)L.expand_blocks, kExpandThreads, 0, st>>>(
+        coff, dval, xy, cb, d_nvis, n, d_ncand, L.cand_cap, tiling->tile_w, tiling->tile_h, gx, flag, ctile, cgid);
+    kept_count_kernel<<<(unsigned)L.cand_blocks, kScanThreads, 0, st>>>(flag, d_ncand, L.cand_cap, cblock_sums);
+    kept_compact_kernel<<<(unsigned)L.cand_blocks, kScanThreads, 0, st>>>(flag, ctile, cgid, d_ncand, L.cand_cap,
+                                                                          cblock_sums, L.cand_blocks, pair_capacity,
+                                                                          ek, ev, d_num_pairs, d_written, d_status);
+    if ((rc = check_launch("pair expansion"))) return rc;
     if (pair_capacity == 0) return GSR_OK;
-    radix_passes(ek, ev, (tpasses & 1) ? tkey : tkey2, (tpasses & 1) ? vals : tval2, d_num_pairs, pair_capacity, 0,
+    radix_passes(ek, ev, (tpasses & 1) ? tkey : tkey2, (tpasses & 1) ? vals : tval2, d_written, pair_capacity, 0,
                  tbits, tpasses, hist, digit_total, (int)L.psort_blocks, st);
     const unsigned rb = (unsigned)((pair_capacity + 255) / 256);
-    finalize_kernel<<<rb, 256, 0, st>>>(tkey, vals, rd, d_num_pairs, pair_capacity, keys,
+    finalize_kernel<<<rb, 256, 0, st>>>(tkey, vals, rd, d_written, pair_capacity, (uint32_t)tiles, keys,
                                         reinterpret_cast<uint2 *>(tile_ranges));
     return check_launch("finalize_kernel");
 }

@@ -83,23 +83,9 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussK g, CamK cam,
             s = Splat{c.u, c.v, A, B, C, op, c.x0, c.x1, c.y0, c.y1};
         }
     }
-    // kept tiles: small boxes in the thread, large ones by the whole warp
-    const int nbt = vis ? (s.x1 / cam.tw - s.x0 / cam.tw + 1) * (s.y1 / cam.th - s.y0 / cam.th + 1) : 0;
-    uint32_t cnt = 0;
-    if (vis && nbt <= kSmallBoxTiles) {
-        for (int ty = s.y0 / cam.th; ty <= s.y1 / cam.th; ++ty)
-            for (int tx = s.x0 / cam.tw; tx <= s.x1 / cam.tw; ++tx)
-                cnt += tile_keep_at(tx, ty, cam.tw, cam.th, s.u, s.v, s.A, s.B, s.C, s.op, s.x0, s.x1, s.y0, s.y1)
-                           ? 1u
-                           : 0u;
-    }
-    uint32_t big = __ballot_sync(0xffffffffu, vis && nbt > kSmallBoxTiles);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const uint32_t c2 = warp_count_tiles(shfl_splat(s, src), cam.tw, cam.th);
-        if ((int)(threadIdx.x & 31) == src) cnt = c2;
-    }
+    // tiles the pixel box touches (the tile cull runs during pair expansion)
+    const uint32_t cnt =
+        vis ? (uint32_t)((s.x1 / cam.tw - s.x0 / cam.tw + 1) * (s.y1 / cam.th - s.y0 / cam.th + 1)) : 0u;
     if (active) ntiles[i] = vis ? cnt : 0u;
 }
 
