@@ -89,9 +89,11 @@ typedef struct {
     int32_t width, height;
 } gsr_camera;
 
-/* Screen tiling.  tile_w x tile_h pixels per tile, tile_w * tile_h <= 1024
- * and a multiple of 32.  The rendered image does not depend on the tiling:
- * each Gaussian only reaches the pixels of its own 3-sigma pixel box. */
+/* Screen tiling.  tile_w x tile_h pixels per tile: tile_h even, tile_w a
+ * divisor or a multiple of 32, tile_w * tile_h a multiple of 64 and at most
+ * 1024 (the blend kernels run one thread per two vertically adjacent pixels).
+ * The rendered image does not depend on the tiling: each Gaussian only
+ * reaches the pixels of its own 3-sigma pixel box. */
 typedef struct {
     int32_t tile_w, tile_h;
 } gsr_tiling;

@@ -52,8 +52,11 @@ int32_t validate_camera(const gsr_camera *c) {
 }
 
 int32_t validate_tiling(const gsr_tiling *t) {
-    if (!t || t->tile_w <= 0 || t->tile_h <= 0 || t->tile_w * t->tile_h > 1024 || (t->tile_w * t->tile_h) % 32 != 0) {
-        set_error("tiling: tile_w * tile_h must be a positive multiple of 32, at most 1024");
+    // two pixels per thread (rows 2k, 2k + 1) and whole thread rows per warp
+    if (!t || t->tile_w <= 0 || t->tile_h <= 0 || t->tile_w * t->tile_h > 1024 || (t->tile_w * t->tile_h) % 64 != 0 ||
+        t->tile_h % 2 != 0 || (t->tile_w % 32 != 0 && 32 % t->tile_w != 0)) {
+        set_error("tiling: need tile_h even, tile_w dividing 32 or a multiple of 32, and tile_w * tile_h a multiple "
+                  "of 64, at most 1024");
         return GSR_ERR_INVALID_ARG;
     }
     return GSR_OK;

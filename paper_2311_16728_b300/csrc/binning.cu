@@ -26,7 +26,7 @@ constexpr int kScanItems = 8;  // Gaussians per thread in the scan / compaction 
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;  // elements per thread per block tile
+constexpr int kSortItems = 4;   // elements per thread per block tile (short per-block chains)
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadix = 256;     // bins of one pass (a pass uses at most 8 bits)
 
