@@ -227,7 +227,7 @@ int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint3
  * scratch lives in one fixed array in device memory that the library defines
  * (29.6 MB, held by every GPU that loads the library until the process
  * exits).  Limits: C * H * W <= 2,457,600 values (a 3 x 1200 x 680 frame fits)
- * and at most 16,384 blocks of 32 x 8 pixels summed over channels; larger
+ * and at most 16,384 blocks of 32 x 32 pixels summed over channels; larger
  * images return GSR_ERR_CAPACITY with a message and enqueue nothing.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -19,8 +19,11 @@
 
 namespace gsr {
 
-constexpr int kLTW = 32, kLTH = 8, kLR = 5;
+constexpr int kLTW = 32, kLTH = 32, kLR = 5;       // output tile and window radius
 constexpr int kRW = kLTW + 2 * kLR, kRH = kLTH + 2 * kLR;
+constexpr int kRS = 45;                            // row stride of the staged region (conflict-free)
+constexpr int kRun = 4;                            // outputs per thread along a row / column
+constexpr int kLThreads = 256;
 
 struct Win {
     float w[11];
@@ -52,141 +55,183 @@ __device__ __forceinline__ float block_sum_256(float v, float *s_red) {
     return r;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) ssim_pass1_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                                         int H, int W, Win win, float *__restrict__ mapA,
-                                                         float *__restrict__ mapB, float *__restrict__ mapC,
-                                                         float *__restrict__ partials) {
-    __shared__ float sX[kRH][kRW], sY[kRH][kRW];
-    __shared__ float sH[5][kRH][kLTW];
-    __shared__ float s_red[8];
-    const int c = blockIdx.z, ox = blockIdx.x * kLTW, oy = blockIdx.y * kLTH, t = threadIdx.x;
-    const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
-    for (int idx = t; idx < kRH * kRW; idx += 256) {
+// Stages a (kRH x kRW) region of plane `src` around the tile (zero outside).
+__device__ __forceinline__ void stage_region(const float *__restrict__ src, int H, int W, int ox, int oy, float *dst) {
+    for (int idx = threadIdx.x; idx < kRH * kRW; idx += kLThreads) {
         const int r = idx / kRW, q = idx % kRW;
         const int gy = oy - kLR + r, gx = ox - kLR + q;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        sX[r][q] = in ? x[cb + (int64_t)gy * W + gx] : 0.f;
-        sY[r][q] = in ? y[cb + (int64_t)gy * W + gx] : 0.f;
+        dst[r * kRS + q] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? src[(int64_t)gy * W + gx] : 0.f;
     }
+}
+
+// Pass 1: windowed moments (separable: rows then columns, kRun outputs per
+// thread from kRun + 10 staged values), SSIM map, its partials (a, b, c) and
+// per-CTA sums of |x - y| and SSIM.
+__global__ void __launch_bounds__(kLThreads) ssim_pass1_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                                               int H, int W, Win win, float *__restrict__ mapA,
+                                                               float *__restrict__ mapB, float *__restrict__ mapC,
+                                                               float *__restrict__ partials) {
+    extern __shared__ float sm[];
+    float *sX = sm, *sY = sm + kRH * kRS;
+    float *sH = sm + 2 * kRH * kRS;  // [5][kRH][kLTW]
+    __shared__ float s_red[8];
+    const int c = blockIdx.z, ox = blockIdx.x * kLTW, oy = blockIdx.y * kLTH;
+    const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
+    stage_region(x + cb, H, W, ox, oy, sX);
+    stage_region(y + cb, H, W, ox, oy, sY);
     __syncthreads();
-    for (int idx = t; idx < kRH * kLTW; idx += 256) {
-        const int r = idx / kLTW, j = idx % kLTW;
-        float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+    // rows: kRH rows x (kLTW / kRun) runs
+    for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += kLThreads) {
+        const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
+        float a[kRun + 10], b[kRun + 10];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float a = sX[r][j + k], b = sY[r][j + k], w = win.w[k];
-            mx += w * a;
-            my += w * b;
-            xx += w * a * a;
-            yy += w * b * b;
-            xy += w * a * b;
+        for (int k = 0; k < kRun + 10; ++k) {
+            a[k] = sX[r * kRS + j0 + k];
+            b[k] = sY[r * kRS + j0 + k];
         }
-        sH[0][r][j] = mx; sH[1][r][j] = my; sH[2][r][j] = xx; sH[3][r][j] = yy; sH[4][r][j] = xy;
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                const float w = win.w[k], av = a[o + k], bv = b[o + k];
+                mx += w * av;
+                my += w * bv;
+                xx += w * av * av;
+                yy += w * bv * bv;
+                xy += w * av * bv;
+            }
+            float *h = sH + r * kLTW + j0 + o;
+            h[0] = mx;
+            h[kRH * kLTW] = my;
+            h[2 * kRH * kLTW] = xx;
+            h[3 * kRH * kLTW] = yy;
+            h[4 * kRH * kLTW] = xy;
+        }
     }
     __syncthreads();
-    const int tx = t % kLTW, ty = t / kLTW;
-    float mx = 0.f, my = 0.f, ex2 = 0.f, ey2 = 0.f, exy = 0.f;
+    // columns: thread = (column, run of kRun rows)
+    const int tx = threadIdx.x % kLTW, i0 = (threadIdx.x / kLTW) * kRun;
+    float m[5][kRun];
 #pragma unroll
-    for (int k = 0; k < 11; ++k) {
-        const float w = win.w[k];
-        mx += w * sH[0][ty + k][tx];
-        my += w * sH[1][ty + k][tx];
-        ex2 += w * sH[2][ty + k][tx];
-        ey2 += w * sH[3][ty + k][tx];
-        exy += w * sH[4][ty + k][tx];
+    for (int q = 0; q < 5; ++q) {
+        float col[kRun + 10];
+#pragma unroll
+        for (int k = 0; k < kRun + 10; ++k) col[k] = sH[q * kRH * kLTW + (i0 + k) * kLTW + tx];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) s += win.w[k] * col[o + k];
+            m[q][o] = s;
+        }
     }
-    const int gx = ox + tx, gy = oy + ty;
     float l1 = 0.f, ssim = 0.f;
-    if (gx < W && gy < H) {
-        const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-        const float sxx = ex2 - mx * mx, syy = ey2 - my * my, sxy = exy - mx * my;
-        const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
-        const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-        const float iB = 1.0f / (B1 * B2);
-        const float S = A1 * A2 * iB;
-        const float dS_dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-        const float dS_dsxx = -S / B2;
-        const float dS_dsxy = 2.f * A1 * iB;
-        const int64_t o = cb + (int64_t)gy * W + gx;
-        mapA[o] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
-        mapB[o] = dS_dsxx;
-        mapC[o] = dS_dsxy;
-        l1 = fabsf(sX[ty + kLR][tx + kLR] - sY[ty + kLR][tx + kLR]);
-        ssim = S;
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+        const int gx = ox + tx, gy = oy + i0 + o;
+        if (gx < W && gy < H) {
+            const float mx = m[0][o], my = m[1][o];
+            const float sxx = m[2][o] - mx * mx, syy = m[3][o] - my * my, sxy = m[4][o] - mx * my;
+            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+            const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+            const float iB = 1.0f / (B1 * B2);
+            const float S = A1 * A2 * iB;
+            const float dS_dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
+            const float dS_dsxx = -S / B2;
+            const float dS_dsxy = 2.f * A1 * iB;
+            const int64_t idx = cb + (int64_t)gy * W + gx;
+            mapA[idx] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
+            mapB[idx] = dS_dsxx;
+            mapC[idx] = dS_dsxy;
+            const int rr = i0 + o + kLR, qq = tx + kLR;
+            l1 += fabsf(sX[rr * kRS + qq] - sY[rr * kRS + qq]);
+            ssim += S;
+        }
     }
     const float s1 = block_sum_256(l1, s_red);
     const float s2 = block_sum_256(ssim, s_red);
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         partials[2 * b] = s1;
         partials[2 * b + 1] = s2;
     }
 }
 
-__global__ void __launch_bounds__(256) ssim_pass2_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                                         int H, int W, Win win, const float *__restrict__ mapA,
-                                                         const float *__restrict__ mapB,
-                                                         const float *__restrict__ mapC,
-                                                         const float *__restrict__ partials, int64_t npartials,
-                                                         float lambda, float *__restrict__ d_loss,
-                                                         float *__restrict__ dx_out) {
-    __shared__ float sM[3][kRH][kRW];
-    __shared__ float sH[3][kRH][kLTW];
-    const int c = blockIdx.z, ox = blockIdx.x * kLTW, oy = blockIdx.y * kLTH, t = threadIdx.x;
+// Pass 2: blur (a, b, c) (the adjoint of the symmetric window), then
+// dL/dx = ((1 - lambda) sign(x - y) - lambda (G*a + 2 x G*b + y G*c)) / (C H W).
+// The first CTA also folds the per-CTA sums into the loss, in a fixed order.
+__global__ void __launch_bounds__(kLThreads) ssim_pass2_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                                               int H, int W, Win win, const float *__restrict__ mapA,
+                                                               const float *__restrict__ mapB,
+                                                               const float *__restrict__ mapC,
+                                                               const float *__restrict__ partials, int64_t npartials,
+                                                               float lambda, float *__restrict__ d_loss,
+                                                               float *__restrict__ dx_out) {
+    extern __shared__ float sm[];
+    float *sM = sm;                  // [3][kRH][kRS]
+    float *sH = sm + 3 * kRH * kRS;  // [3][kRH][kLTW]
+    const int c = blockIdx.z, ox = blockIdx.x * kLTW, oy = blockIdx.y * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     const float inv_n = (float)(1.0 / ((double)gridDim.z * (double)plane));  // 1 / (C H W)
-    for (int idx = t; idx < kRH * kRW; idx += 256) {
-        const int r = idx / kRW, q = idx % kRW;
-        const int gy = oy - kLR + r, gx = ox - kLR + q;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const int64_t o = cb + (int64_t)gy * W + gx;
-        sM[0][r][q] = in ? mapA[o] : 0.f;
-        sM[1][r][q] = in ? mapB[o] : 0.f;
-        sM[2][r][q] = in ? mapC[o] : 0.f;
+    stage_region(mapA + cb, H, W, ox, oy, sM);
+    stage_region(mapB + cb, H, W, ox, oy, sM + kRH * kRS);
+    stage_region(mapC + cb, H, W, ox, oy, sM + 2 * kRH * kRS);
+    __syncthreads();
+    for (int item = threadIdx.x; item < 3 * kRH * (kLTW / kRun); item += kLThreads) {
+        const int q = item / (kRH * (kLTW / kRun)), rem = item % (kRH * (kLTW / kRun));
+        const int r = rem / (kLTW / kRun), j0 = (rem % (kLTW / kRun)) * kRun;
+        float a[kRun + 10];
+#pragma unroll
+        for (int k = 0; k < kRun + 10; ++k) a[k] = sM[q * kRH * kRS + r * kRS + j0 + k];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) s += win.w[k] * a[o + k];
+            sH[q * kRH * kLTW + r * kLTW + j0 + o] = s;
+        }
     }
     __syncthreads();
-    for (int idx = t; idx < kRH * kLTW; idx += 256) {
-        const int r = idx / kLTW, j = idx % kLTW;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const int tx = threadIdx.x % kLTW, i0 = (threadIdx.x / kLTW) * kRun;
+    float g[3][kRun];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.w[k];
-            s0 += w * sM[0][r][j + k];
-            s1 += w * sM[1][r][j + k];
-            s2 += w * sM[2][r][j + k];
-        }
-        sH[0][r][j] = s0; sH[1][r][j] = s1; sH[2][r][j] = s2;
-    }
-    __syncthreads();
-    const int tx = t % kLTW, ty = t / kLTW;
-    const int gx = ox + tx, gy = oy + ty;
-    if (gx < W && gy < H) {
-        float ga = 0.f, gb = 0.f, gc = 0.f;
+    for (int q = 0; q < 3; ++q) {
+        float col[kRun + 10];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.w[k];
-            ga += w * sH[0][ty + k][tx];
-            gb += w * sH[1][ty + k][tx];
-            gc += w * sH[2][ty + k][tx];
+        for (int k = 0; k < kRun + 10; ++k) col[k] = sH[q * kRH * kLTW + (i0 + k) * kLTW + tx];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) s += win.w[k] * col[o + k];
+            g[q][o] = s;
         }
-        const int64_t o = cb + (int64_t)gy * W + gx;
-        const float xv = x[o], yv = y[o];
-        const float d = xv - yv;
-        const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        dx_out[o] = ((1.f - lambda) * sg - lambda * (ga + 2.f * xv * gb + yv * gc)) * inv_n;
     }
-    // the first CTA folds the per-CTA partial sums, always in the same order
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+        const int gx = ox + tx, gy = oy + i0 + o;
+        if (gx < W && gy < H) {
+            const int64_t idx = cb + (int64_t)gy * W + gx;
+            const float xv = x[idx], yv = y[idx];
+            const float d = xv - yv;
+            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+            dx_out[idx] = ((1.f - lambda) * sg - lambda * (g[0][o] + 2.f * xv * g[1][o] + yv * g[2][o])) * inv_n;
+        }
+    }
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
-        __shared__ double s_l1[256], s_ss[256];
+        __shared__ double s_l1[kLThreads], s_ss[kLThreads];
+        const int t = threadIdx.x;
         double a = 0.0, b = 0.0;
-        for (int64_t k = t; k < npartials; k += 256) {
+        for (int64_t k = t; k < npartials; k += kLThreads) {
             a += (double)partials[2 * k];
             b += (double)partials[2 * k + 1];
         }
         s_l1[t] = a;
         s_ss[t] = b;
         __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
+        for (int o = kLThreads / 2; o > 0; o >>= 1) {
             if (t < o) {
                 s_l1[t] += s_l1[t + o];
                 s_ss[t] += s_ss[t + o];
@@ -198,6 +243,22 @@ __global__ void __launch_bounds__(256) ssim_pass2_kernel(const float *__restrict
             *d_loss = (float)((1.0 - lambda) * s_l1[0] / cnt + lambda * (1.0 - s_ss[0] / cnt));
         }
     }
+}
+
+constexpr size_t kPass1Smem = sizeof(float) * (2 * kRH * kRS + 5 * kRH * kLTW);
+constexpr size_t kPass2Smem = sizeof(float) * (3 * kRH * kRS + 3 * kRH * kLTW);
+
+static void launch_ssim(const float *img, const float *gt, int C, int H, int W, float lambda, float *d_loss,
+                        float *dL_dimg, float *mA, float *mB, float *mC, float *part, int64_t nblocks,
+                        cudaStream_t st) {
+    // (per device, cheap, and not a stream operation: fine during capture)
+    cudaFuncSetAttribute(ssim_pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem);
+    cudaFuncSetAttribute(ssim_pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass2Smem);
+    const Win win = ssim_window();
+    const dim3 grid((W + kLTW - 1) / kLTW, (H + kLTH - 1) / kLTH, C);
+    ssim_pass1_kernel<<<grid, kLThreads, kPass1Smem, st>>>(img, gt, H, W, win, mA, mB, mC, part);
+    ssim_pass2_kernel<<<grid, kLThreads, kPass2Smem, st>>>(img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda,
+                                                            d_loss, dL_dimg);
 }
 
 // ---------------------------------------------------------------- PSNR
@@ -283,11 +344,7 @@ extern "C" int32_t gsr_loss_fwd_bwd(const float *img, const float *gt, int32_t C
     char *ws = static_cast<char *>(workspace);
     float *mA = reinterpret_cast<float *>(ws + L.a), *mB = reinterpret_cast<float *>(ws + L.b);
     float *mC = reinterpret_cast<float *>(ws + L.c), *part = reinterpret_cast<float *>(ws + L.partials);
-    const Win win = ssim_window();
-    const dim3 grid((W + kLTW - 1) / kLTW, (H + kLTH - 1) / kLTH, C);
-    cudaStream_t st = as_cuda(stream);
-    ssim_pass1_kernel<<<grid, 256, 0, st>>>(img, gt, H, W, win, mA, mB, mC, part);
-    ssim_pass2_kernel<<<grid, 256, 0, st>>>(img, gt, H, W, win, mA, mB, mC, part, L.nblocks, lambda, d_loss, dL_dimg);
+    launch_ssim(img, gt, C, H, W, lambda, d_loss, dL_dimg, mA, mB, mC, part, L.nblocks, as_cuda(stream));
     return check_launch("ssim kernels");
 }
 
@@ -326,7 +383,7 @@ extern "C" int32_t gsr_psnr(const float *img, const float *gt, int64_t count, fl
 namespace gsr {
 
 constexpr int64_t kStaticLossMaxElems = 2457600;  // C x H x W, e.g. 3 x 1200 x 680 (Replica frame) fits
-constexpr int64_t kStaticLossMaxBlocks = 16384;   // CTAs of 32 x 8 pixels per channel, summed over channels
+constexpr int64_t kStaticLossMaxBlocks = 16384;   // CTAs of 32 x 32 pixels per channel, summed over channels
 
 static __device__ __align__(256) float g_loss_scratch[3 * kStaticLossMaxElems + 2 * kStaticLossMaxBlocks];
 
@@ -369,7 +426,7 @@ extern "C" int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, in
     const int64_t nblocks = (int64_t)((W + kLTW - 1) / kLTW) * ((H + kLTH - 1) / kLTH) * C;
     if (elems > kStaticLossMaxElems || nblocks > kStaticLossMaxBlocks) {
         set_error("gsr_loss_fwd_bwd_static: image %d x %d x %d exceeds the fixed scratch (at most %lld values "
-                  "and %lld 32x8 pixel blocks); use gsr_loss_fwd_bwd with a workspace",
+                  "and %lld 32x32 pixel blocks); use gsr_loss_fwd_bwd with a workspace",
                   (int)C, (int)H, (int)W, (long long)kStaticLossMaxElems, (long long)kStaticLossMaxBlocks);
         return GSR_ERR_CAPACITY;
     }
@@ -380,10 +437,6 @@ extern "C" int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, in
     // by the first pass of the same call, so nothing needs clearing
     float *mA = base, *mB = base + kStaticLossMaxElems, *mC = base + 2 * kStaticLossMaxElems;
     float *part = base + 3 * kStaticLossMaxElems;
-    const Win win = ssim_window();
-    const dim3 grid((W + kLTW - 1) / kLTW, (H + kLTH - 1) / kLTH, C);
-    cudaStream_t st = as_cuda(stream);
-    ssim_pass1_kernel<<<grid, 256, 0, st>>>(img, gt, H, W, win, mA, mB, mC, part);
-    ssim_pass2_kernel<<<grid, 256, 0, st>>>(img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda, d_loss, dL_dimg);
+    launch_ssim(img, gt, C, H, W, lambda, d_loss, dL_dimg, mA, mB, mC, part, nblocks, as_cuda(stream));
     return check_launch("ssim kernels (static scratch)");
 }

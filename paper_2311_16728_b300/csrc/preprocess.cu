@@ -91,63 +91,77 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussK g, CamK cam,
 
 // K8: screen-space gradients (du, dv, dA, dB, dC, dopacity, dr, dg, db) of one
 // Gaussian -> dL/d(mean, opacity logit, quaternion, log-scale, SH), added to
-// the gradient planes.
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussK g, CamK cam, const uint32_t *__restrict__ ntiles,
-                                                             const float4 *__restrict__ g0,
-                                                             const float4 *__restrict__ g1,
-                                                             const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
-                                                             float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
-                                                             float4 *__restrict__ d_sh, float *__restrict__ dstat,
-                                                             float *__restrict__ dcount) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
-    if (ntiles[i] == 0u) return;
+// the gradient planes.  Only visible Gaussians have work, and they are a
+// small fraction of the map, so each CTA first compacts the visible indices
+// of its chunk in shared memory and then runs the chain on full warps.
+constexpr int kBwdThreads = 128;
+constexpr int kBwdChunk = 1024;  // Gaussians per CTA
+
+__device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &cam, int64_t i,
+                                                   const float4 *__restrict__ g0, const float4 *__restrict__ g1,
+                                                   const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
+                                                   float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
+                                                   float4 *__restrict__ d_sh, float *__restrict__ dstat,
+                                                   float *__restrict__ dcount) {
     const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
     Chain c;
-    if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen when ntiles > 0
+    if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
     const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
     const float du = G0.x, dv = G0.y, dA = G0.z, dB = G0.w, dC = G1.x, dop = G1.y;
-    const float dcol_in[3] = {G1.z, G1.w, G2.x};
     if (dstat) {
         dstat[i] += sqrtf(du * du + dv * dv);
         dcount[i] += 1.0f;
     }
     const float *W = cam.R;
-    // ---- colour and SH
+    // ---- colour and SH, streamed one float4 plane at a time
     const float3 cc = cam_center(cam);
     const float dirx = mo.x - cc.x, diry = mo.y - cc.y, dirz = mo.z - cc.z;
-    const float len = sqrtf(dirx * dirx + diry * diry + dirz * dirz);
-    const float inv_len = 1.0f / len;
+    const float inv_len = 1.0f / sqrtf(dirx * dirx + diry * diry + dirz * dirz);
     const float vx = dirx * inv_len, vy = diry * inv_len, vz = dirz * inv_len;
-    float sh[48];
-    load_sh(g.sh, g.n, i, g.deg, sh);
     float Y[16];
     float3 dY[16];
     sh_basis(vx, vy, vz, g.deg, Y, dY);
     const int nc = (g.deg + 1) * (g.deg + 1);
-    float dcol[3];
+    const int planes = sh_planes(g.deg);
+    // raw colour decides the clamp: first pass over the planes
+    float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float raw = 0.5f;
+    for (int j = 0; j < kShPlanes; ++j) {
+        if (j >= planes) break;
+        const float4 v = __ldg(g.sh + (int64_t)j * g.n + i);
+        const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < nc) raw += sh[3 * k + ch] * Y[k];
-        dcol[ch] = raw > 0.0f ? dcol_in[ch] : 0.0f;
+        for (int t = 0; t < 4; ++t) {
+            const int f = 4 * j + t, k = f / 3, ch = f % 3;
+            if (k < nc) raw[ch] += e[t] * Y[k];
+        }
     }
-    float dsh[48];
+    const float dcol[3] = {raw[0] > 0.0f ? G1.z : 0.0f, raw[1] > 0.0f ? G1.w : 0.0f, raw[2] > 0.0f ? G2.x : 0.0f};
     float3 dvh = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int j = 0; j < kShPlanes; ++j) {
+        if (j >= planes) break;
+        const float4 v = __ldg(g.sh + (int64_t)j * g.n + i);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+        float d[4];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            dsh[3 * k + ch] = (k < nc) ? dcol[ch] * Y[k] : 0.0f;
+        for (int t = 0; t < 4; ++t) {
+            const int f = 4 * j + t, k = f / 3, ch = f % 3;
+            d[t] = 0.0f;
             if (k < nc) {
-                const float w = dcol[ch] * sh[3 * k + ch];
+                d[t] = dcol[ch] * Y[k];
+                const float w = dcol[ch] * e[t];
                 dvh.x += w * dY[k].x;
                 dvh.y += w * dY[k].y;
                 dvh.z += w * dY[k].z;
             }
         }
+        float4 s = d_sh[(int64_t)j * g.n + i];
+        s.x += d[0];
+        s.y += d[1];
+        s.z += d[2];
+        s.w += d[3];
+        d_sh[(int64_t)j * g.n + i] = s;
     }
     const float vd = dvh.x * vx + dvh.y * vy + dvh.z * vz;
     float dmx = (dvh.x - vx * vd) * inv_len, dmy = (dvh.y - vy * vd) * inv_len, dmz = (dvh.z - vz * vd) * inv_len;
@@ -264,18 +278,35 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussK g, CamK cam,
     d_q[i] = make_float4(a.x + dw, a.y + dx2, a.z + dy2, a.w + dz2);
     a = d_ls[i];
     d_ls[i] = make_float4(a.x + dls[0], a.y + dls[1], a.z + dls[2], a.w);
-    const int planes = sh_planes(g.deg);
-#pragma unroll
-    for (int j = 0; j < kShPlanes; ++j) {
-        if (j < planes) {
-            float4 s = d_sh[(int64_t)j * g.n + i];
-            s.x += dsh[4 * j];
-            s.y += dsh[4 * j + 1];
-            s.z += dsh[4 * j + 2];
-            s.w += dsh[4 * j + 3];
-            d_sh[(int64_t)j * g.n + i] = s;
-        }
+}
+
+__global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, CamK cam, const uint32_t *__restrict__ ntiles,
+                                                                     const float4 *__restrict__ g0,
+                                                                     const float4 *__restrict__ g1,
+                                                                     const float4 *__restrict__ g2,
+                                                                     float4 *__restrict__ d_mo, float4 *__restrict__ d_q,
+                                                                     float4 *__restrict__ d_ls, float4 *__restrict__ d_sh,
+                                                                     float *__restrict__ dstat,
+                                                                     float *__restrict__ dcount) {
+    __shared__ uint32_t s_idx[kBwdChunk];
+    __shared__ uint32_t s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < kBwdChunk; k += kBwdThreads) {
+        const int64_t i = base + k;
+        const bool vis = i < g.n && ntiles[i] > 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        uint32_t slot = 0;
+        if (lane == 0 && m) slot = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
     }
+    __syncthreads();
+    const uint32_t cnt = s_cnt;
+    for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads)
+        chain_one_gaussian(g, cam, base + s_idx[k], g0, g1, g2, d_mo, d_q, d_ls, d_sh, dstat, dcount);
 }
 
 }  // namespace gsr
@@ -309,9 +340,8 @@ int32_t launch_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, cons
                               float *dstat, float *dcount, cudaStream_t stream) {
     if (g->n == 0) return GSR_OK;
     const CamK ck = make_camk(cam, tiling);
-    const int threads = 128;
-    const int64_t blocks = (g->n + threads - 1) / threads;
-    preprocess_bwd_kernel<<<(unsigned)blocks, threads, 0, stream>>>(
+    const int64_t blocks = (g->n + kBwdChunk - 1) / kBwdChunk;
+    preprocess_bwd_kernel<<<(unsigned)blocks, kBwdThreads, 0, stream>>>(
         make_gk(g), ck, proj->ntiles, reinterpret_cast<const float4 *>(g2d->g0),
         reinterpret_cast<const float4 *>(g2d->g1), reinterpret_cast<const float4 *>(g2d->g2),
         reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),
