@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
-    ap.add_argument("--cpu-rows", type=int, default=16, help="image rows of the cpu_baseline sample")
+    ap.add_argument("--cpu-rows", type=int, default=160, help="image rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--poses", type=int, default=N_POSES, help="trajectory poses trained on (profiling uses fewer)")
     args = ap.parse_args()
@@ -287,24 +287,39 @@ def main():
         per_iter = None
     launches = per_iter * args.steps if per_iter is not None else None
 
-    # ---- roofline of the dominant stage's kernel
+    # ---- work counters at the final state (outside the timed region): visible
+    # Gaussians, pairs, and (pixel, Gaussian) blends over the first poses
+    vb = ms.vb
+    nblend = torch.zeros(HEIGHT, WIDTH, dtype=torch.int32, device="cuda")
+    blends, nvis = [], []
+    for k in range(min(5, len(ms.views))):
+        vb.cam = ms.views[k][0]
+        vb.preprocess(params)
+        vb.bin_sort()
+        vb.render_fwd(n_blended=nblend)
+        blends.append(int(nblend.sum().item()))
+        nvis.append(int((vb.ntiles > 0).sum().item()))
+    work = {"blends": statistics.mean(blends), "visible": statistics.mean(nvis), "pairs": pairs}
+
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm = peaks.get("hbm_gbs", 6400.0)
+    stages = stage_rooflines(stage_ms, work, peaks, clk)
     dom = max(stage_ms, key=stage_ms.get)
-    roof = roofline_for(dom, stage_ms[dom], pairs, hbm, clk, peaks)
+    roof = dict(stages[dom])
 
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; Replica-shaped)",
             "config": _config({"pairs_last_step": pairs, "poses": len(cams)}),
-            "roofline": roof, "stages_ms": stage_ms, "gpu_launches": launches, "clocks": clk,
+            "roofline": roof, "stages_ms": stage_ms, "stage_rooflines": stages, "work": work,
+            "gpu_launches": launches, "clocks": clk,
             "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "iters/s",
                     "h2d_bytes_per_step": 3 * WIDTH * HEIGHT * 4, "d2h_bytes_per_step": 4}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         import synthetic as S
-        rows, row0 = args.cpu_rows, 330
+        rows = min(args.cpu_rows, HEIGHT)
+        row0 = (HEIGHT - rows) // 2
         cam = cams[0]
         dt = oracle.decide(target.mean_op, target.quat, target.logscale, cam.as_array(), WIDTH, HEIGHT)
         st = oracle.Scene64(target.mean_op, target.quat, target.logscale, target.sh)
@@ -321,27 +336,59 @@ def main():
         dist.destroy_process_group()
 
 
-# Algorithmic bytes / flops per launch of each stage's dominant kernel.
-def roofline_for(stage, ms, pairs, hbm_gbs, clk, peaks):
-    sec = ms * 1e-3
-    n = N_GAUSS
-    if stage == "adam":
-        # 15 float4 planes x (param r+w, grad r+w, m r+w, v r+w)
-        alg = 15 * 16 * 8 * n
-        return {"kernel": "adam_kernel", "bound": "hbm", "achieved": alg / sec / 1e9, "peak": hbm_gbs,
-                "unit": "GB/s", "frac": alg / sec / 1e9 / hbm_gbs, "traffic": None,
-                "alg_bytes_per_launch": alg, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    if stage == "bin_sort":
-        passes = 6
-        alg = pairs * (12 + passes * 32 + 8) + 4 * n
-        return {"kernel": "radix sort passes", "bound": "hbm", "achieved": alg / sec / 1e9, "peak": hbm_gbs,
-                "unit": "GB/s", "frac": alg / sec / 1e9 / hbm_gbs, "traffic": None, "alg_bytes_per_launch": alg,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    # blend kernels: FP32-pipe bound; peak = 148 SMs x 128 FP32 lanes x 2 flop x median SM clock
+# DRAM bytes per launch of a kernel from one ncu capture of this workload
+# (profiles/blend_kernels_300k_1200x680.md); None when not captured for the
+# current kernel version.
+NCU_TRAFFIC = {"blend_bwd": 28.203264e6, "render_fwd": 11.310336e6}
+
+# FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
+FLOPS_PER_BLEND_FWD = 20
+FLOPS_PER_BLEND_BWD = 60
+
+
+def stage_rooflines(stage_ms, work, peaks, clk):
+    """Roofline entry of each stage's dominant kernel: algorithmic work per
+    launch / measured stage time against the measured HBM copy bandwidth or
+    the FP32 peak (148 SMs x 128 lanes x 2 flops x median SM clock)."""
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6400 GB/s (of fallback)"
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    peak = 148 * 128 * 2 * mhz * 1e6 / 1e12
-    return {"kernel": stage, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
-            "traffic": None, "note": "FP32 peak at the sampled median SM clock"}
+    fp32 = 148 * 128 * 2 * mhz * 1e6 / 1e12
+    n, nv, K, E = N_GAUSS, work["visible"], work["pairs"], work["blends"]
+    px = 3 * WIDTH * HEIGHT
+
+    def hbm_entry(kernel, alg):
+        sec = stage_ms[st] * 1e-3
+        return {"kernel": kernel, "bound": "hbm", "achieved": alg / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": alg / sec / 1e9 / hbm, "traffic": NCU_TRAFFIC.get(st), "alg_per_launch": alg,
+                "peak_source": hbm_src}
+
+    def alu_entry(kernel, flops):
+        sec = stage_ms[st] * 1e-3
+        return {"kernel": kernel, "bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32, "unit": "TFLOP/s",
+                "frac": flops / sec / 1e12 / fp32, "traffic": NCU_TRAFFIC.get(st), "alg_per_launch": flops,
+                "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"}
+
+    out = {}
+    for st in stage_ms:
+        if st == "preprocess":
+            out[st] = hbm_entry("preprocess_fwd_kernel", 48 * n + 4 * n + (192 + 48) * nv)
+        elif st == "bin_sort":
+            # depth passes 4 x 16 B per visible, tile passes 2 x 16 B per pair, keys + values out 12 B per pair
+            out[st] = hbm_entry("binning + radix passes", 4 * 16 * nv + 2 * 16 * K + 12 * K)
+        elif st == "render_fwd":
+            out[st] = alu_entry("render_fwd_kernel", FLOPS_PER_BLEND_FWD * E)
+        elif st == "loss":
+            # x, y read twice, three maps written and read, dL/dx written
+            out[st] = hbm_entry("ssim_pass1/2_kernel", 4 * px * (2 + 3 + 3 + 2 + 1))
+        elif st == "blend_bwd":
+            out[st] = alu_entry("render_bwd_kernel", FLOPS_PER_BLEND_BWD * E)
+        elif st == "preprocess_bwd":
+            out[st] = hbm_entry("preprocess_bwd_kernel", (240 + 48 + 480) * nv)
+        elif st == "adam":
+            # 15 float4 planes x (param r+w, grad r+w, m r+w, v r+w)
+            out[st] = hbm_entry("adam_kernel", 15 * 16 * 8 * n)
+    return out
 
 
 if __name__ == "__main__":

@@ -181,10 +181,12 @@ int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camera *cam, con
  * where alpha < 1/255 or the pixel is outside their box, and the walk stopped
  * before a Gaussian that would take T below 1e-4.  Writes img (3 x H x W),
  * T_final (H x W) and n_contrib (H x W: 1 + position in the tile list of the
- * last Gaussian blended, 0 if none).  bg is a host array of 3 floats. */
+ * last Gaussian blended, 0 if none).  bg is a host array of 3 floats.
+ * n_blended (H x W, may be NULL) receives the number of Gaussians blended
+ * at each pixel (a work statistic; the render does not depend on it). */
 int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, const uint32_t *tile_ranges,
                        const gsr_camera *cam, const gsr_tiling *tiling, const float *bg, float *img,
-                       float *T_final, uint32_t *n_contrib, gsr_stream_t stream);
+                       float *T_final, uint32_t *n_contrib, uint32_t *n_blended, gsr_stream_t stream);
 
 /* Bytes of scratch gsr_loss_fwd_bwd needs for a C x H x W image. */
 int32_t gsr_loss_workspace_size(int32_t C, int32_t H, int32_t W, size_t *bytes);
@@ -198,6 +200,20 @@ int32_t gsr_loss_workspace_size(int32_t C, int32_t H, int32_t W, size_t *bytes);
 int32_t gsr_loss_fwd_bwd(const float *img, const float *gt, int32_t C, int32_t H, int32_t W,
                          float lambda, float *d_loss, float *dL_dimg, void *workspace,
                          size_t workspace_bytes, gsr_stream_t stream);
+
+/* Backward of Eq. 3 alone (the first half of gsr_render_bwd): zeroes grad2d
+ * (n Gaussians) and accumulates the screen-space gradients into it. */
+int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t *vals, const uint32_t *tile_ranges,
+                      const gsr_camera *cam, const gsr_tiling *tiling, const float *bg, const float *T_final,
+                      const uint32_t *n_contrib, const float *dL_dimg, const gsr_grad2d *grad2d,
+                      gsr_stream_t stream);
+
+/* Backward of the projection alone (the second half of gsr_render_bwd):
+ * chains grad2d to the parameter gradients, adding (+=) into `grads`, for
+ * the Gaussians with ntiles > 0; densify statistics as in gsr_render_bwd. */
+int32_t gsr_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                           const gsr_tiling *tiling, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
+                           float *densify_stat, float *densify_count, gsr_stream_t stream);
 
 /* Backward of Eq. 3 then of the projection.  Replays each pixel back to
  * front from T_final and n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i)

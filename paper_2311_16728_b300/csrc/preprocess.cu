@@ -333,19 +333,30 @@ extern "C" int32_t gsr_preprocess(const gsr_gaussians *g, const gsr_camera *cam,
     return check_launch("preprocess_fwd_kernel");
 }
 
-namespace gsr {
-// Launched by gsr_render_bwd after the per-pixel backward.
-int32_t launch_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
-                              const gsr_tiling *tiling, const gsr_grad2d *g2d, const gsr_param_buffers *grads,
-                              float *dstat, float *dcount, cudaStream_t stream) {
+extern "C" int32_t gsr_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                                      const gsr_tiling *tiling, const gsr_grad2d *g2d,
+                                      const gsr_param_buffers *grads, float *densify_stat, float *densify_count,
+                                      gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_gaussians(g)) || (rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
     if (g->n == 0) return GSR_OK;
+    if (!proj || !proj->ntiles || !g2d || !g2d->g0 || !g2d->g1 || !g2d->g2 || !grads || !grads->mean_op ||
+        !grads->quat || !grads->logscale || !grads->sh || (densify_stat != nullptr) != (densify_count != nullptr)) {
+        set_error("gsr_preprocess_bwd: NULL pointer");
+        return GSR_ERR_INVALID_ARG;
+    }
+    if (!aligned16(g2d->g0) || !aligned16(g2d->g1) || !aligned16(g2d->g2) || !aligned16(grads->mean_op) ||
+        !aligned16(grads->quat) || !aligned16(grads->logscale) || !aligned16(grads->sh)) {
+        set_error("gsr_preprocess_bwd: gradient buffers must be 16-byte aligned");
+        return GSR_ERR_INVALID_ARG;
+    }
     const CamK ck = make_camk(cam, tiling);
     const int64_t blocks = (g->n + kBwdChunk - 1) / kBwdChunk;
-    preprocess_bwd_kernel<<<(unsigned)blocks, kBwdThreads, 0, stream>>>(
+    preprocess_bwd_kernel<<<(unsigned)blocks, kBwdThreads, 0, as_cuda(stream)>>>(
         make_gk(g), ck, proj->ntiles, reinterpret_cast<const float4 *>(g2d->g0),
         reinterpret_cast<const float4 *>(g2d->g1), reinterpret_cast<const float4 *>(g2d->g2),
         reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),
-        reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh), dstat, dcount);
+        reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh), densify_stat,
+        densify_count);
     return check_launch("preprocess_bwd_kernel");
 }
-}  // namespace gsr

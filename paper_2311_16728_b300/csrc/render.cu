@@ -25,7 +25,6 @@ struct RenderArgs {
     float bg0, bg1, bg2;
 };
 
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kHalfLog2e = -0.5f * 1.4426950408889634f;  // exponent of 2 = kHalfLog2e * (d^T Q d)
 
 // pixel (px, py0) and (px, py0 + 1) of this thread; origin of the tile
@@ -92,7 +91,8 @@ __device__ __forceinline__ bool splat_alpha(float e2, float op, Eval &r) {
 // ---------------------------------------------------------------- K5
 __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__restrict__ img,
                                                          float *__restrict__ T_final,
-                                                         uint32_t *__restrict__ n_contrib) {
+                                                         uint32_t *__restrict__ n_contrib,
+                                                         uint32_t *__restrict__ n_blended) {
     extern __shared__ float4 smem[];
     const int nthr = blockDim.x, nwarps = nthr >> 5;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__
     const int begin = (int)rg.x, end = (int)rg.y;
     const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)(py0 + 1);
     float T0 = 1.0f, T1 = 1.0f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
-    uint32_t last0 = 0, last1 = 0;
+    uint32_t last0 = 0, last1 = 0, nb0 = 0, nb1 = 0;
     bool done0 = !in0, done1 = !in1;
     for (int base = begin; base < end; base += nthr) {
         // stop the whole tile once every pixel has terminated
@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__
                             C02 += col.z * w;
                             T0 = tn;
                             last0 = pos;
+                            ++nb0;
                         }
                     }
                 }
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__
                             C12 += col.z * w;
                             T1 = tn;
                             last1 = pos;
+                            ++nb1;
                         }
                     }
                 }
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__
         img[2 * plane + pix] = C02 + T0 * a.bg2;
         T_final[pix] = T0;
         n_contrib[pix] = last0;
+        if (n_blended) n_blended[pix] = nb0;
     }
     if (in1) {
         const int64_t pix = (int64_t)(py0 + 1) * a.W + px;
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__
         img[2 * plane + pix] = C12 + T1 * a.bg2;
         T_final[pix] = T1;
         n_contrib[pix] = last1;
+        if (n_blended) n_blended[pix] = nb1;
     }
 }
 
@@ -384,17 +388,13 @@ static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const ui
     return a;
 }
 
-int32_t launch_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
-                              const gsr_tiling *tiling, const gsr_grad2d *g2d, const gsr_param_buffers *grads,
-                              float *dstat, float *dcount, cudaStream_t stream);
-
 }  // namespace gsr
 
 using namespace gsr;
 
 extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, const uint32_t *tile_ranges,
                                   const gsr_camera *cam, const gsr_tiling *tiling, const float *bg, float *img,
-                                  float *T_final, uint32_t *n_contrib, gsr_stream_t stream) {
+                                  float *T_final, uint32_t *n_contrib, uint32_t *n_blended, gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
     if (!proj || !proj->xy_conic || !proj->c_op_box || !proj->rgb_depth || !tile_ranges || !img || !T_final ||
@@ -406,32 +406,28 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
     const size_t shm = (3 * sizeof(float4) + sizeof(uint32_t)) * (size_t)nthr;
-    render_fwd_kernel<<<tiles, nthr, shm, as_cuda(stream)>>>(a, img, T_final, n_contrib);
+    render_fwd_kernel<<<tiles, nthr, shm, as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
     return check_launch("render_fwd_kernel");
 }
 
-extern "C" int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint32_t *vals,
-                                  const uint32_t *tile_ranges, const gsr_camera *cam, const gsr_tiling *tiling,
-                                  const float *bg, const float *T_final, const uint32_t *n_contrib,
-                                  const float *dL_dimg, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
-                                  float *densify_stat, float *densify_count, gsr_stream_t stream) {
+extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t *vals, const uint32_t *tile_ranges,
+                                 const gsr_camera *cam, const gsr_tiling *tiling, const float *bg,
+                                 const float *T_final, const uint32_t *n_contrib, const float *dL_dimg,
+                                 const gsr_grad2d *grad2d, gsr_stream_t stream) {
     int32_t rc;
-    if ((rc = validate_gaussians(g)) || (rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
-    if (!proj || !proj->xy_conic || !proj->c_op_box || !proj->rgb_depth || !proj->ntiles || !tile_ranges ||
-        !T_final || !n_contrib || !dL_dimg || !grad2d || !grad2d->g0 || !grad2d->g1 || !grad2d->g2 || !grads ||
-        !grads->mean_op || !grads->quat || !grads->logscale || !grads->sh ||
-        (densify_stat != nullptr) != (densify_count != nullptr)) {
-        set_error("gsr_render_bwd: NULL pointer");
+    if ((rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
+    if (n < 0 || !proj || (n > 0 && (!proj->xy_conic || !proj->c_op_box || !proj->rgb_depth)) || !tile_ranges ||
+        !T_final || !n_contrib || !dL_dimg || !grad2d || !grad2d->g0 || !grad2d->g1 || !grad2d->g2) {
+        set_error("gsr_blend_bwd: NULL pointer or negative count");
         return GSR_ERR_INVALID_ARG;
     }
-    if (!aligned16(grad2d->g0) || !aligned16(grad2d->g1) || !aligned16(grad2d->g2) || !aligned16(grads->mean_op) ||
-        !aligned16(grads->quat) || !aligned16(grads->logscale) || !aligned16(grads->sh)) {
-        set_error("gsr_render_bwd: gradient buffers must be 16-byte aligned");
+    if (!aligned16(grad2d->g0) || !aligned16(grad2d->g1) || !aligned16(grad2d->g2)) {
+        set_error("gsr_blend_bwd: screen-space gradient planes must be 16-byte aligned");
         return GSR_ERR_INVALID_ARG;
     }
     cudaStream_t st = as_cuda(stream);
-    const size_t g2bytes = sizeof(float4) * (size_t)g->n;
-    if (g->n > 0) {
+    const size_t g2bytes = sizeof(float4) * (size_t)n;
+    if (n > 0) {
         if (cudaMemsetAsync(grad2d->g0, 0, g2bytes, st) != cudaSuccess ||
             cudaMemsetAsync(grad2d->g1, 0, g2bytes, st) != cudaSuccess ||
             cudaMemsetAsync(grad2d->g2, 0, g2bytes, st) != cudaSuccess)
@@ -442,6 +438,18 @@ extern "C" int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, 
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
     const size_t shm = (3 * sizeof(float4) + 2 * sizeof(uint32_t)) * (size_t)nthr;
     render_bwd_kernel<<<tiles, nthr, shm, st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0, grad2d->g1, grad2d->g2);
-    if ((rc = check_launch("render_bwd_kernel"))) return rc;
-    return launch_preprocess_bwd(g, proj, cam, tiling, grad2d, grads, densify_stat, densify_count, st);
+    return check_launch("render_bwd_kernel");
+}
+
+extern "C" int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint32_t *vals,
+                                  const uint32_t *tile_ranges, const gsr_camera *cam, const gsr_tiling *tiling,
+                                  const float *bg, const float *T_final, const uint32_t *n_contrib,
+                                  const float *dL_dimg, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
+                                  float *densify_stat, float *densify_count, gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_gaussians(g))) return rc;
+    if ((rc = gsr_blend_bwd(proj, g->n, vals, tile_ranges, cam, tiling, bg, T_final, n_contrib, dL_dimg, grad2d,
+                            stream)))
+        return rc;
+    return gsr_preprocess_bwd(g, proj, cam, tiling, grad2d, grads, densify_stat, densify_count, stream);
 }

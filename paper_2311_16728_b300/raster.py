@@ -160,12 +160,12 @@ class ViewBuffers:
                        _p(self.vals), self.pair_capacity, _p(self.ranges), _p(self.num_pairs), _p(self.sort_ws),
                        self.sort_ws.numel(), _p(self.status), _stream(stream))
 
-    def render_fwd(self, bg: Sequence[float] = (0.0, 0.0, 0.0), stream=None):
+    def render_fwd(self, bg: Sequence[float] = (0.0, 0.0, 0.0), stream=None, n_blended=None):
         proj = self.proj_struct()
         bga = (ctypes.c_float * 3)(*bg)
         L.gsr_render_fwd(ctypes.byref(proj), _p(self.vals), _p(self.ranges), ctypes.byref(self.cam),
                          ctypes.byref(self.tiling), bga, _p(self.img), _p(self.T_final), _p(self.n_contrib),
-                         _stream(stream))
+                         _p(n_blended), _stream(stream))
 
     def loss_fwd_bwd(self, gt: torch.Tensor, lam: float = LAMBDA_DSSIM, stream=None):
         H, W = self.cam.height, self.cam.width
@@ -180,6 +180,20 @@ class ViewBuffers:
         L.gsr_render_bwd(ctypes.byref(gs), ctypes.byref(proj), _p(self.vals), _p(self.ranges), ctypes.byref(self.cam),
                          ctypes.byref(self.tiling), bga, _p(self.T_final), _p(self.n_contrib), _p(d),
                          ctypes.byref(g2), ctypes.byref(gb), _p(densify_stat), _p(densify_count), _stream(stream))
+
+    def blend_bwd(self, dimg: Optional[torch.Tensor] = None, bg: Sequence[float] = (0.0, 0.0, 0.0), stream=None):
+        proj, g2 = self.proj_struct(), self.grad2d_struct()
+        bga = (ctypes.c_float * 3)(*bg)
+        d = self.dimg if dimg is None else dimg
+        L.gsr_blend_bwd(ctypes.byref(proj), self.n, _p(self.vals), _p(self.ranges), ctypes.byref(self.cam),
+                        ctypes.byref(self.tiling), bga, _p(self.T_final), _p(self.n_contrib), _p(d), ctypes.byref(g2),
+                        _stream(stream))
+
+    def preprocess_bwd(self, g: Gaussians, grads: Gaussians, densify_stat=None, densify_count=None, stream=None):
+        gs, proj, g2, gb = g.gaussians_struct(), self.proj_struct(), self.grad2d_struct(), grads.buffers_struct()
+        L.gsr_preprocess_bwd(ctypes.byref(gs), ctypes.byref(proj), ctypes.byref(self.cam), ctypes.byref(self.tiling),
+                             ctypes.byref(g2), ctypes.byref(gb), _p(densify_stat), _p(densify_count),
+                             _stream(stream))
 
     def forward(self, g: Gaussians, bg=(0.0, 0.0, 0.0), stream=None):
         self.preprocess(g, stream)
@@ -289,7 +303,7 @@ def psnr(img: torch.Tensor, gt: torch.Tensor, stream=None) -> torch.Tensor:
 
 
 # ---------------------------------------------------------------- mapping step
-STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "adam")
+STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "preprocess_bwd", "adam")
 
 
 class MappingStep:
@@ -338,8 +352,10 @@ class MappingStep:
             vb.render_fwd(stream=stream)
         elif name == "loss":
             vb.loss_fwd_bwd(gt, self.lam, stream)
-        elif name == "render_bwd":
-            vb.render_bwd(self.params, self.grads, stream=stream)
+        elif name == "blend_bwd":
+            vb.blend_bwd(stream=stream)
+        elif name == "preprocess_bwd":
+            vb.preprocess_bwd(self.params, self.grads, stream=stream)
         elif name == "adam":
             self.adam.step(self.grads, stream)
 
