@@ -256,6 +256,29 @@ int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, int32_t C, in
                                 float lambda, float *d_loss, float *dL_dimg, gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */
+/* Learned initialiser (tensor-core MLP)                             */
+/* ---------------------------------------------------------------- */
+
+/* BF16 GEMM on the tcgen05 tensor cores with an FP32 accumulator in tensor
+ * memory: D = A B^T, A [M x K] and B [N x K] row-major BF16 with K
+ * contiguous (row strides lda, ldb elements, multiples of 8, base pointers
+ * 16-byte aligned); M % 128 == 0, N % 64 == 0, K % 64 == 0 (callers pad).
+ * Epilogue, applied in this order to each FP32 element (n = column, m = row):
+ * += bias[n] (if bias), max(., 0) (if relu), zeroed where mask[m * ldm + n]
+ * (BF16) is not positive (if mask).  Outputs (any subset, at least one):
+ * out_bf16[m * ldo + n] (BF16, round to nearest even), out_bf16_t[n * ldt + m]
+ * (transposed BF16), out_f32[m * ldf + n] (FP32, 16-byte aligned, ldf % 4 ==
+ * 0; added with atomics when atomic_f32), colsum[n] += sum over rows
+ * m < valid_rows (FP32 atomics).  ksplit > 1 splits K over that many CTAs per
+ * output tile and needs an atomic FP32 output and no element-wise epilogue.
+ * A tensor-core wait that gives up sets the GSR_ERR_TIMEOUT bit in *d_status.
+ * Used by the MLP calls below; exposed so it can be checked on its own. */
+int32_t gsr_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int32_t M, int32_t N, int32_t K,
+                      const float *bias, int32_t relu, const void *mask, int32_t ldm, void *out_bf16, int32_t ldo,
+                      void *out_bf16_t, int32_t ldt, float *out_f32, int32_t ldf, int32_t atomic_f32, float *colsum,
+                      int64_t valid_rows, int32_t ksplit, int32_t *d_status, gsr_stream_t stream);
+
+/* ---------------------------------------------------------------- */
 /* Optimiser, pyramid and metrics                                    */
 /* ---------------------------------------------------------------- */
 

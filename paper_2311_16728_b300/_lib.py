@@ -79,6 +79,9 @@ _SIGNATURES = {
     "gsr_render_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_void_p, P(gsr_camera), P(gsr_tiling), c_void_p,
                         c_void_p, c_void_p, c_void_p, P(gsr_grad2d), P(gsr_param_buffers), c_void_p, c_void_p,
                         c_void_p], c_int32),
+    "gsr_gemm_bf16": ([c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
+                       c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int64,
+                       c_int32, c_void_p, c_void_p], c_int32),
     "gsr_adam_step": ([P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers),
                        c_int64, P(gsr_adam_config), c_void_p, c_void_p], c_int32),
     "gsr_pyramid_down": ([c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p], c_int32),
@@ -137,6 +140,7 @@ gsr_loss_workspace_size = _wrap("gsr_loss_workspace_size")
 gsr_loss_fwd_bwd = _wrap("gsr_loss_fwd_bwd")
 gsr_loss_fwd_bwd_static = _wrap("gsr_loss_fwd_bwd_static")
 gsr_render_bwd = _wrap("gsr_render_bwd")
+gsr_gemm_bf16 = _wrap("gsr_gemm_bf16")
 gsr_adam_step = _wrap("gsr_adam_step")
 gsr_pyramid_down = _wrap("gsr_pyramid_down")
 gsr_psnr_workspace_size = _wrap("gsr_psnr_workspace_size")

@@ -1,0 +1,315 @@
+// umma_gemm.cuh -- BF16 x BF16 -> FP32 GEMM on the sm_100-family tensor cores
+// (tcgen05.mma, accumulator in tensor memory), operands staged by TMA.
+//
+//   D[M x N] = A[M x K] * B[N x K]^T      (both operands K-major, row-major
+//                                           storage with K contiguous)
+//
+// CTA tile 128 x BN (BN = 64, 128 or 256), K step 64 (one 128-byte swizzled
+// row per operand row).  Warp 0 issues the TMA loads into an mbarrier ring of
+// shared-memory stages, warp 1 issues the MMAs (one elected thread), warps
+// 2..5 drain the accumulator from tensor memory and apply the epilogue.
+// Every wait is bounded; a wait that gives up raises GSR_ERR_TIMEOUT in the
+// status word and the CTA winds down (its copies and MMAs are still waited
+// for, with a bound, before tensor memory is released).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace umma {
+
+constexpr int BM = 128, BK = 64;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart (stride
+// dimension byte offset), leading-dimension offset unused (1), version bits
+// 46-48 = 0b001, swizzle mode 2 (128 B).  The tile base is 1024-B aligned.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit words: this thread's row, 16 columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue of one GEMM (all pointers optional; M, N are the padded extents).
+struct Epilogue {
+    const float *bias;            // [N]        v += bias[n]
+    int relu;                     //            v = max(v, 0)
+    const __nv_bfloat16 *mask;    // [M x ldm]  v = mask[m][n] > 0 ? v : 0 (ReLU derivative)
+    int ldm;
+    __nv_bfloat16 *out_bf16;      // [M x ldo]  row-major BF16
+    int ldo;
+    __nv_bfloat16 *out_bf16_t;    // [N x ldt]  transposed BF16 (element (n, m))
+    int ldt;
+    float *out_f32;               // [M x ldf]  FP32 (added atomically when atomic_f32)
+    int ldf;
+    int atomic_f32;
+    float *colsum;                // [N]        colsum[n] += sum over valid rows of v (after mask / relu)
+    int64_t valid_rows;           //            rows >= valid_rows are padding: not summed
+};
+
+template <int BN>
+struct Config {
+    static constexpr int kStages = BN == 256 ? 4 : 6;
+    static constexpr int kABytes = BM * BK * 2;
+    static constexpr int kBBytes = BN * BK * 2;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kTmemCols = BN < 32 ? 32 : BN;
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
+};
+
+// grid: (N / BN, M / BM, ksplit); K tiles of this CTA: the z-th slice.
+template <int BN>
+__global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, int K, Epilogue ep,
+                                                      int32_t *d_status) {
+    using Cfg = Config<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-B aligned stages
+    uint8_t *bar_area = smem + (size_t)Cfg::kStages * Cfg::kStageBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(bar_area);
+    uint64_t *empty = full + Cfg::kStages;
+    uint64_t *tmem_full = empty + Cfg::kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_full + 1);
+    __shared__ int s_err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int ktiles = K / BK;
+    const int kz = gridDim.z, z = blockIdx.z;
+    const int kt0 = (int)((int64_t)ktiles * z / kz), kt1 = (int)((int64_t)ktiles * (z + 1) / kz);
+    const int nk = kt1 - kt0;
+
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < Cfg::kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tmem_full, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % Cfg::kStages;
+                if (i >= Cfg::kStages && !mbar_wait(&empty[s], ((i / Cfg::kStages) - 1) & 1)) {
+                    atomicExch(&s_err, 1);
+                    break;
+                }
+                uint8_t *sa = smem + (size_t)s * Cfg::kStageBytes;
+                mbar_expect_tx(&full[s], Cfg::kStageBytes);
+                tma_load_2d(sa, &tmA, (kt0 + i) * BK, m0, &full[s]);
+                tma_load_2d(sa + Cfg::kABytes, &tmB, (kt0 + i) * BK, n0, &full[s]);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % Cfg::kStages;
+                if (!mbar_wait(&full[s], (i / Cfg::kStages) & 1)) {
+                    atomicExch(&s_err, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + (size_t)s * Cfg::kStageBytes);
+                const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + Cfg::kABytes);
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)  // 16 BF16 = 32 B per MMA step along K
+                    mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (i > 0 || k > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+            }
+            mma_commit(tmem_full);  // all MMAs issued so far, done or not, are tracked
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, lane quarter = warp % 4
+        const int q = warp & 3;
+        const int m = m0 + 32 * q + lane;
+        const bool ok = mbar_wait(tmem_full, 0);
+        if (!ok) atomicExch(&s_err, 1);
+        tc_fence_after();
+        if (ok && nk > 0) {
+            const bool row_valid = m < ep.valid_rows;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+                const int nb = n0 + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (ep.bias) v[j] += ep.bias[nb + j];
+                    if (ep.relu) v[j] = fmaxf(v[j], 0.0f);
+                }
+                if (ep.mask) {
+                    const __nv_bfloat16 *mr = ep.mask + (int64_t)m * ep.ldm + nb;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (!(__bfloat162float(mr[j]) > 0.0f)) v[j] = 0.0f;
+                }
+                if (ep.out_bf16) {
+                    __nv_bfloat16 *o = ep.out_bf16 + (int64_t)m * ep.ldo + nb;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) *reinterpret_cast<__nv_bfloat162 *>(o + j) =
+                        __floats2bfloat162_rn(v[j], v[j + 1]);
+                }
+                if (ep.out_bf16_t) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) ep.out_bf16_t[(int64_t)(nb + j) * ep.ldt + m] = __float2bfloat16_rn(v[j]);
+                }
+                if (ep.out_f32) {
+                    float *o = ep.out_f32 + (int64_t)m * ep.ldf + nb;
+                    if (ep.atomic_f32) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) atomicAdd(o + j, v[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(o + j) =
+                            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    }
+                }
+                if (ep.colsum) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float s = row_valid ? v[j] : 0.0f;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        if (lane == 0) atomicAdd(ep.colsum + nb + j, s);
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (s_err) {
+        // wind down: the last copies of the ring and the MMAs must have landed
+        // before the shared memory and the tensor memory are given back
+        if (threadIdx.x == 0) {
+            raise_status(d_status, GSR_ERR_TIMEOUT);
+            for (int s = 0; s < Cfg::kStages && s < nk; ++s) {
+                const int i = nk - 1 - s;
+                mbar_wait(&full[i % Cfg::kStages], (i / Cfg::kStages) & 1);
+            }
+            mbar_wait(tmem_full, 0);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, Cfg::kTmemCols);
+    }
+}
+
+}  // namespace umma
+}  // namespace gsr
