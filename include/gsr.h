@@ -278,6 +278,72 @@ int32_t gsr_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, in
                       void *out_bf16_t, int32_t ldt, float *out_f32, int32_t ldf, int32_t atomic_f32, float *colsum,
                       int64_t valid_rows, int32_t ksplit, int32_t *d_status, gsr_stream_t stream);
 
+/* MLP weights (caller-owned device memory).  FP32 masters, row-major:
+ * W1 [256 x 2368] (inputs padded from 2308 to 2368 with zero columns), b1
+ * [256], W2 [256 x 256], b2 [256], W3 [64 x 256] (56 outputs + 8 zero rows),
+ * b3 [64]; BF16 working copies W1h (as W1), W2h (as W2), W2hT (W2
+ * transposed), W3h (as W3), W3hT (W3 transposed, [256 x 64]).  The same
+ * struct holds the Adam moments, where only the FP32 pointers are used. */
+typedef struct {
+    float *W1, *b1, *W2, *b2, *W3, *b3;
+    void *W1h, *W2h, *W2hT, *W3h, *W3hT;
+} gsr_mlp_weights;
+
+/* Bytes of scratch for a batch padded to Mpad rows (Mpad % 128 == 0). */
+int32_t gsr_mlp_workspace_size(int64_t Mpad, size_t *bytes);
+
+/* Writes the BF16 copies of the FP32 master weights (after initialising or
+ * loading them). */
+int32_t gsr_mlp_sync_weights(const gsr_mlp_weights *w, gsr_stream_t stream);
+
+/* Input rows of the initialiser (the patches of Sec. 3.3.1's densification
+ * keypoints): for keypoint m (keypoints[5 m ..] = u, v at level 0, depth,
+ * log keypoint scale, angle) row m of x (BF16 [Mpad x 2368]) is the 16 x 16
+ * RGB patch of each of the three pyramid levels around (u, v) / 2^l (nearest
+ * pixel, clamped; index l * 768 + (16 row + col) * 3 + channel), then depth,
+ * log scale, cos, sin of the angle, then zeros; rows >= M are zero.  Level l
+ * is a planar 3 x H_l x W_l image with W_l, H_l halved l times rounding up.
+ * xT (may be NULL) receives the transpose [2368 x Mpad] for training. */
+int32_t gsr_patch_gather(const float *level0, const float *level1, const float *level2, int32_t W0, int32_t H0,
+                         const float *keypoints, int64_t M, int64_t Mpad, void *x, void *xT, gsr_stream_t stream);
+
+/* y [Mpad x 64] FP32 = W3 relu(W2 relu(W1 x + b1) + b2) + b3 on the tensor
+ * cores (BF16 operands, FP32 accumulation; hidden activations rounded to
+ * BF16). */
+int32_t gsr_mlp_forward(const gsr_mlp_weights *w, const void *x, int64_t Mpad, float *y, void *workspace,
+                        size_t workspace_bytes, int32_t *d_status, gsr_stream_t stream);
+
+/* One training step on M valid rows: forward, L = sum_{m < M, j < 56}
+ * out_weight[j] (y - target)^2 / M into *d_loss, backward by the five
+ * tensor-core GEMMs (weight gradients split over the batch), then Adam
+ * (step t = *d_step + 1, bias-corrected) on every FP32 master with m and v
+ * as moments, refreshed BF16 copies, and *d_step += 1.  target is FP32
+ * [Mpad x 64]; y receives the forward output. */
+int32_t gsr_mlp_train_step(const gsr_mlp_weights *w, const gsr_mlp_weights *m, const gsr_mlp_weights *v,
+                           const void *x, const void *xT, const float *target, const float *out_weight, int64_t M,
+                           int64_t Mpad, float lr, float beta1, float beta2, float eps, int32_t *d_step,
+                           float *d_loss, float *y, void *workspace, size_t workspace_bytes, int32_t *d_status,
+                           gsr_stream_t stream);
+
+/* Addresses, inside a training workspace for Mpad rows, of the FP32
+ * gradients of the last gsr_mlp_train_step (valid until the next step
+ * clears them): W1 [256 x 2368], b1, W2 [256 x 256], b2, W3 TRANSPOSED
+ * [256 x 64], b3 [64]; the BF16 pointers are set to NULL.  Host-only. */
+int32_t gsr_mlp_gradients(void *workspace, int64_t Mpad, gsr_mlp_weights *grads);
+
+/* Training targets for keypoints whose primitive is known (gids[m]): log-scale
+ * minus log(depth / fx), rotation in the camera frame (unit quaternion with
+ * w >= 0), opacity logit, the 48 SH coefficients; columns 56..63 zero.  Rows
+ * M .. Mpad - 1 are zeroed. */
+int32_t gsr_mlp_encode_targets(const gsr_gaussians *g, const uint32_t *gids, const float *keypoints, int64_t M,
+                               int64_t Mpad, const gsr_camera *cam, float *target, gsr_stream_t stream);
+
+/* Inverse of the encoding: writes Gaussians offset .. offset + M - 1 of a
+ * store of n Gaussians, the mean back-projected from the keypoint at its
+ * depth (R^T (depth K^-1 [u v 1] - t)). */
+int32_t gsr_mlp_decode(const float *y, const float *keypoints, int64_t M, const gsr_camera *cam,
+                       const gsr_param_buffers *out, int64_t n, int64_t offset, gsr_stream_t stream);
+
 /* ---------------------------------------------------------------- */
 /* Optimiser, pyramid and metrics                                    */
 /* ---------------------------------------------------------------- */

@@ -50,6 +50,12 @@ class gsr_grad2d(ctypes.Structure):
     _fields_ = [("g0", c_void_p), ("g1", c_void_p), ("g2", c_void_p)]
 
 
+class gsr_mlp_weights(ctypes.Structure):
+    _fields_ = [("W1", c_void_p), ("b1", c_void_p), ("W2", c_void_p), ("b2", c_void_p), ("W3", c_void_p),
+                ("b3", c_void_p), ("W1h", c_void_p), ("W2h", c_void_p), ("W2hT", c_void_p), ("W3h", c_void_p),
+                ("W3hT", c_void_p)]
+
+
 class gsr_adam_config(ctypes.Structure):
     _fields_ = [("lr_mean", c_float), ("lr_opacity", c_float), ("lr_quat", c_float), ("lr_scale", c_float),
                 ("lr_sh", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
@@ -82,6 +88,20 @@ _SIGNATURES = {
     "gsr_gemm_bf16": ([c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
                        c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int64,
                        c_int32, c_void_p, c_void_p], c_int32),
+    "gsr_mlp_workspace_size": ([c_int64, P(c_size_t)], c_int32),
+    "gsr_mlp_sync_weights": ([P(gsr_mlp_weights), c_void_p], c_int32),
+    "gsr_patch_gather": ([c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int64, c_int64, c_void_p,
+                          c_void_p, c_void_p], c_int32),
+    "gsr_mlp_forward": ([P(gsr_mlp_weights), c_void_p, c_int64, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p],
+                        c_int32),
+    "gsr_mlp_train_step": ([P(gsr_mlp_weights), P(gsr_mlp_weights), P(gsr_mlp_weights), c_void_p, c_void_p, c_void_p,
+                            c_void_p, c_int64, c_int64, c_float, c_float, c_float, c_float, c_void_p, c_void_p,
+                            c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "gsr_mlp_gradients": ([c_void_p, c_int64, P(gsr_mlp_weights)], c_int32),
+    "gsr_mlp_encode_targets": ([P(gsr_gaussians), c_void_p, c_void_p, c_int64, c_int64, P(gsr_camera), c_void_p,
+                                c_void_p], c_int32),
+    "gsr_mlp_decode": ([c_void_p, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64, c_int64,
+                        c_void_p], c_int32),
     "gsr_adam_step": ([P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers),
                        c_int64, P(gsr_adam_config), c_void_p, c_void_p], c_int32),
     "gsr_pyramid_down": ([c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p], c_int32),
@@ -141,6 +161,14 @@ gsr_loss_fwd_bwd = _wrap("gsr_loss_fwd_bwd")
 gsr_loss_fwd_bwd_static = _wrap("gsr_loss_fwd_bwd_static")
 gsr_render_bwd = _wrap("gsr_render_bwd")
 gsr_gemm_bf16 = _wrap("gsr_gemm_bf16")
+gsr_mlp_workspace_size = _wrap("gsr_mlp_workspace_size")
+gsr_mlp_sync_weights = _wrap("gsr_mlp_sync_weights")
+gsr_patch_gather = _wrap("gsr_patch_gather")
+gsr_mlp_forward = _wrap("gsr_mlp_forward")
+gsr_mlp_train_step = _wrap("gsr_mlp_train_step")
+gsr_mlp_gradients = _wrap("gsr_mlp_gradients")
+gsr_mlp_encode_targets = _wrap("gsr_mlp_encode_targets")
+gsr_mlp_decode = _wrap("gsr_mlp_decode")
 gsr_adam_step = _wrap("gsr_adam_step")
 gsr_pyramid_down = _wrap("gsr_pyramid_down")
 gsr_psnr_workspace_size = _wrap("gsr_psnr_workspace_size")

@@ -1,0 +1,156 @@
+"""The learned initialiser on the GPU (tcgen05 MLP) against the FP64 oracle of oracle/mlp.py."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2311_16728_b300 as gsr  # noqa: E402
+from paper_2311_16728_b300.learned_init import LearnedInit  # noqa: E402
+
+
+def _levels(seed=3, H=120, W=160):
+    img = torch.tensor(S.random_image(3, H, W, seed=seed), device="cuda")
+    return gsr.pyramid(img, 3)
+
+
+def _keypoints(M, W=160, H=120, seed=4):
+    rng = np.random.default_rng(seed)
+    kp = np.stack([rng.uniform(0, W - 1, M), rng.uniform(0, H - 1, M), rng.uniform(0.5, 5, M),
+                   rng.normal(0, 1, M), rng.uniform(-np.pi, np.pi, M)], 1).astype(np.float32)
+    return kp
+
+
+def _np_gather(levels, kp):
+    M = kp.shape[0]
+    x = np.zeros((M, omlp.K0))
+    for m in range(M):
+        u, v, d, s, th = kp[m]
+        for l, img in enumerate(levels):
+            _, Hl, Wl = img.shape
+            cx, cy = int(np.rint(np.float32(u) * np.float32(2.0 ** -l))), int(np.rint(np.float32(v) * np.float32(2.0 ** -l)))
+            for p in range(256):
+                px = min(max(cx - 8 + p % 16, 0), Wl - 1)
+                py = min(max(cy - 8 + p // 16, 0), Hl - 1)
+                x[m, l * 768 + 3 * p:l * 768 + 3 * p + 3] = img[:, py, px]
+        x[m, 2304:2308] = [d, s, np.cos(np.float32(th)), np.sin(np.float32(th))]
+    return x
+
+
+def test_patch_gather_matches_numpy():
+    levels = _levels()
+    kp = _keypoints(37)
+    li = LearnedInit(omlp.init_params(3), 37)
+    li.gather(levels, torch.tensor(kp, device="cuda"), transpose=True)
+    torch.cuda.synchronize()
+    ref = omlp.bf16_round(_np_gather([l.cpu().numpy() for l in levels], kp))
+    got = li.x[:37].float().cpu().numpy()
+    np.testing.assert_allclose(got[:, :2306], ref[:, :2306], rtol=0, atol=0)
+    np.testing.assert_allclose(got[:, 2306:2308], ref[:, 2306:2308], atol=2 ** -7)  # device cos / sin
+    assert (li.x[37:].float().abs().max().item() == 0) and torch.equal(li.xT, li.x.t())
+
+
+def _batch(M, seed=5):
+    rng = np.random.default_rng(seed)
+    p = omlp.init_params(seed)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(0, 0.05, p[k].shape).astype(np.float32)
+    x = np.zeros((M, omlp.K0), np.float32)
+    x[:, :omlp.K_IN] = rng.uniform(0, 1, (M, omlp.K_IN))
+    t = rng.normal(0, 1, (M, omlp.N3)).astype(np.float32)
+    t[:, omlp.N_OUT:] = 0
+    return p, x, t
+
+
+def _load(li, x):
+    xb = torch.tensor(x, device="cuda").to(torch.bfloat16)
+    li.x.zero_()
+    li.x[:x.shape[0]] = xb
+    li.xT.copy_(li.x.t())
+
+
+@pytest.mark.parametrize("M", [100, 300])
+def test_forward_matches_oracle(M):
+    p, x, t = _batch(M)
+    li = LearnedInit(p, M)
+    _load(li, x)
+    y = li.forward()
+    torch.cuda.synchronize()
+    assert int(li.status.item()) == 0
+    fw = omlp.forward(p, x)
+    got = y[:M].cpu().numpy()
+    err = np.abs(got - fw["y"])
+    # the hidden activations are rounded to BF16 on both sides; an FP32/FP64
+    # difference can move one of them by an ulp, so bound through |W| |h|
+    scale = np.abs(fw["W3"]) @ np.abs(fw["h2"]).T
+    assert (err <= 2 ** -7 * scale.T + 1e-4).all(), (err / (scale.T + 1e-9)).max()
+    assert np.linalg.norm(err) / np.linalg.norm(fw["y"]) < 1e-3
+
+
+def test_training_gradients_match_oracle():
+    M = 200
+    p, x, t = _batch(M, seed=7)
+    li = LearnedInit(p, M, lr=1e-4)
+    _load(li, x)
+    target = torch.zeros(li.mpad, omlp.N3, device="cuda")
+    target[:M] = torch.tensor(t, device="cuda")
+    li.train_step(target, M)
+    torch.cuda.synchronize()
+    assert int(li.status.item()) == 0
+    fw = omlp.forward(p, x)
+    L_ref, dy = omlp.loss_and_dy(fw["y"], t, np.ones(omlp.N3))
+    g_ref = omlp.backward(fw, dy)
+    assert float(li.loss.item()) == pytest.approx(L_ref, rel=1e-3)
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in li.gradients().items()}
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        rel = np.linalg.norm(g[k] - g_ref[k]) / max(np.linalg.norm(g_ref[k]), 1e-30)
+        assert rel < 2e-2, (k, rel)
+    # one Adam step moved the masters and refreshed the BF16 copies
+    assert int(li.step_count.item()) == 1
+    assert torch.equal(li.w.h["W1h"], li.w.t["W1"].to(torch.bfloat16))
+    assert torch.equal(li.w.h["W3hT"], li.w.t["W3"].t().contiguous().to(torch.bfloat16))
+
+
+def test_training_reduces_the_loss():
+    M = 256
+    p, x, t = _batch(M, seed=9)
+    li = LearnedInit(p, M, lr=1e-3)
+    _load(li, x)
+    target = torch.zeros(li.mpad, omlp.N3, device="cuda")
+    target[:M] = torch.tensor(t, device="cuda")
+    losses = []
+    for _ in range(60):
+        li.train_step(target, M)
+        losses.append(float(li.loss.item()))
+    assert losses[-1] < 0.5 * losses[0], losses[::10]
+
+
+def test_encode_decode_round_trip():
+    p = S.tiny_scene(64, seed=2)
+    cam = S.pose_camera(*S.trajectory(3), 150.0, 150.0, 160, 120)
+    g = gsr.Gaussians.from_arrays(p.mean_op, p.quat, p.logscale, p.sh)
+    # keypoints = projections of the Gaussians themselves, at their depth
+    pc = (cam.R @ p.mean_op[:, :3].T.astype(np.float64)).T + cam.t
+    kp = np.stack([cam.fx * pc[:, 0] / pc[:, 2] + cam.cx, cam.fy * pc[:, 1] / pc[:, 2] + cam.cy, pc[:, 2],
+                   np.zeros(64), np.zeros(64)], 1).astype(np.float32)
+    li = LearnedInit(omlp.init_params(1), 64)
+    kpt = torch.tensor(kp, device="cuda")
+    target = torch.zeros(li.mpad, omlp.N3, device="cuda")
+    li.encode_targets(g, torch.arange(64, dtype=torch.int32, device="cuda"), kpt, cam, target)
+    li.y.copy_(target)
+    out = gsr.Gaussians.zeros(100)
+    li.decode(kpt, cam, out, 10)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.mean_op[10:74, :3].cpu().numpy(), p.mean_op[:, :3], atol=2e-5)
+    np.testing.assert_allclose(out.mean_op[10:74, 3].cpu().numpy(), p.mean_op[:, 3], atol=1e-6)
+    np.testing.assert_allclose(out.logscale[10:74, :3].cpu().numpy(), p.logscale[:, :3], atol=2e-5)
+    q = out.quat[10:74].cpu().numpy()
+    q0 = p.quat / np.linalg.norm(p.quat, axis=1, keepdims=True)
+    assert np.allclose(np.abs((q * q0).sum(1)), 1.0, atol=1e-5)  # same rotation up to sign
+    np.testing.assert_allclose(out.sh[:, 10:74].cpu().numpy(), p.sh, atol=1e-6)
