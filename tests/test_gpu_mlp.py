@@ -118,22 +118,26 @@ def test_training_gradients_match_oracle():
 
 
 def test_training_reduces_the_loss():
+    """Targets from a fixed teacher network are learnable: the loss must fall."""
     M = 256
-    p, x, t = _batch(M, seed=9)
+    p, x, _ = _batch(M, seed=9)
+    teacher, _, _ = _batch(M, seed=10)
+    t = omlp.forward(teacher, x)["y"].astype(np.float32)
+    t[:, omlp.N_OUT:] = 0
     li = LearnedInit(p, M, lr=1e-3)
     _load(li, x)
     target = torch.zeros(li.mpad, omlp.N3, device="cuda")
     target[:M] = torch.tensor(t, device="cuda")
     losses = []
-    for _ in range(60):
+    for _ in range(100):
         li.train_step(target, M)
         losses.append(float(li.loss.item()))
-    assert losses[-1] < 0.5 * losses[0], losses[::10]
+    assert losses[-1] < 0.3 * losses[0], losses[::10]
 
 
 def test_encode_decode_round_trip():
     p = S.tiny_scene(64, seed=2)
-    cam = S.pose_camera(*S.trajectory(3), 150.0, 150.0, 160, 120)
+    cam = S.tiny_camera()  # identity pose: every Gaussian is 2-4 m in front
     g = gsr.Gaussians.from_arrays(p.mean_op, p.quat, p.logscale, p.sh)
     # keypoints = projections of the Gaussians themselves, at their depth
     pc = (cam.R @ p.mean_op[:, :3].T.astype(np.float64)).T + cam.t
