@@ -1,0 +1,36 @@
+"""The autotuner: every candidate tiling renders the identical image; the
+winner is one of them and is cached."""
+import json
+
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2311_16728_b300 as gsr  # noqa: E402
+from paper_2311_16728_b300.autotune import CANDIDATES, autotune  # noqa: E402
+
+
+def test_autotune_picks_a_candidate_and_caches(tmp_path):
+    base = S.tiny_scene(4096, seed=3)
+    cam = S.tiny_camera()
+    g = gsr.Gaussians.from_arrays(base.mean_op, base.quat, base.logscale, base.sh)
+    vb = gsr.ViewBuffers(base.n, gsr.camera_from(cam), gsr.tiling_struct(16, 16), 1 << 16)
+    vb.forward(g)
+    gt = vb.img.clone()
+    p = S.perturb(base)
+    gp = gsr.Gaussians.from_arrays(p.mean_op, p.quat, p.logscale, p.sh)
+    before = [t.clone() for t in gp.tensors()]
+    cache = tmp_path / "tiles.json"
+    tile, report = autotune(gp, [(cam, gt)], steps=3, warmup=1, cache_path=str(cache))
+    assert tuple(tile) in CANDIDATES
+    assert all(report["identical_image"].values()) and len(report["ms_per_step"]) == len(CANDIDATES)
+    assert all(torch.equal(a, b) for a, b in zip(before, gp.tensors()))  # caller's parameters untouched
+    tile2, _ = autotune(gp, [(cam, gt)], cache_path=str(cache))
+    assert tuple(tile2) == tuple(tile)
+    assert json.load(open(cache))
