@@ -256,6 +256,57 @@ int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, int32_t C, in
                                 float lambda, float *d_loss, float *dL_dimg, gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */
+/* Batched Gaussian-pyramid window (Sec. 3.4, Eq. 5)                 */
+/* ---------------------------------------------------------------- */
+/* Eq. 5 supervises pyramid level l with GP^l(I_gt), one level after the
+ * other.  These calls evaluate the levels of a whole window of keyframes in
+ * one iteration instead: views v = 0 .. nviews - 1 (nviews <= 64), each a
+ * (keyframe, level) camera with its GP^l image, L = sum_v weight_v L_v and a
+ * gradient equal to the sum of the single-view gradients.  Per-view records
+ * are stored view-major: record r = v n + i is Gaussian i seen from view v
+ * (the proj arrays hold nviews x n entries), and tiles are numbered view
+ * after view. */
+
+/* Projects every Gaussian into every view (parameters read once). */
+int32_t gsr_batched_preprocess(const gsr_gaussians *g, const gsr_camera *cams, int32_t nviews,
+                               const gsr_tiling *tiling, const gsr_proj *out, gsr_stream_t stream);
+
+/* gsr_bin_sort over all views' records (n_per_view each); tile ranges for the
+ * sum over views of their tiles.  Workspace: gsr_bin_sort_workspace_size with
+ * n = n_per_view x nviews. */
+int32_t gsr_batched_bin_sort(const gsr_proj *proj, int64_t n_per_view, const gsr_camera *cams, int32_t nviews,
+                             const gsr_tiling *tiling, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
+                             uint32_t *tile_ranges, int64_t *d_num_pairs, void *workspace, size_t workspace_bytes,
+                             int32_t *d_status, gsr_stream_t stream);
+
+/* Bytes of scratch for gsr_batched_iterate over these views. */
+int32_t gsr_batched_iterate_workspace_size(const gsr_camera *cams, int32_t nviews, size_t *bytes);
+
+/* ONE persistent cooperative launch over the whole window: forward blend of
+ * every (view, tile), both SSIM passes of every (view, channel, 32 x 32
+ * block), the per-view losses (d_losses[v]), dL_dimg[v] = weight_v dL_v/dI_v,
+ * and the backward blend of every (view, tile), accumulating into grad2d
+ * (nviews x n records; must be zero on entry -- gsr_batched_preprocess_bwd
+ * leaves it zero).  Work is pulled from atomic queues so uneven resolutions
+ * balance; the phases are separated by grid-wide barriers whose waits are
+ * bounded (about a second): a wait that gives up sets GSR_ERR_TIMEOUT in
+ * *d_status and the launch winds down.  img, T_final, n_contrib, gt, dL_dimg
+ * are arrays of nviews device pointers (host arrays); weights (host, may be
+ * NULL = all 1).  Tiles must hold 256 pixels (16 x 16, 32 x 8 or 8 x 32). */
+int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *vals, const uint32_t *tile_ranges,
+                            const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling, const float *bg,
+                            float *const *img, float *const *T_final, uint32_t *const *n_contrib,
+                            const float *const *gt, float *const *dL_dimg, const float *weights, float lambda,
+                            float *d_losses, const gsr_grad2d *grad2d, void *workspace, size_t workspace_bytes,
+                            int32_t *d_status, gsr_stream_t stream);
+
+/* Chains every view's screen-space gradient into `grads` (+=), one thread per
+ * Gaussian summing over the views that see it, and zeroes grad2d again. */
+int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
+                                   int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
+                                   const gsr_param_buffers *grads, gsr_stream_t stream);
+
+/* ---------------------------------------------------------------- */
 /* Learned initialiser (tensor-core MLP)                             */
 /* ---------------------------------------------------------------- */
 

@@ -85,6 +85,15 @@ _SIGNATURES = {
     "gsr_render_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_void_p, P(gsr_camera), P(gsr_tiling), c_void_p,
                         c_void_p, c_void_p, c_void_p, P(gsr_grad2d), P(gsr_param_buffers), c_void_p, c_void_p,
                         c_void_p], c_int32),
+    "gsr_batched_preprocess": ([P(gsr_gaussians), c_void_p, c_int32, P(gsr_tiling), P(gsr_proj), c_void_p], c_int32),
+    "gsr_batched_bin_sort": ([P(gsr_proj), c_int64, c_void_p, c_int32, P(gsr_tiling), c_void_p, c_void_p, c_int64,
+                              c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "gsr_batched_iterate_workspace_size": ([c_void_p, c_int32, P(c_size_t)], c_int32),
+    "gsr_batched_iterate": ([P(gsr_proj), c_void_p, c_void_p, c_void_p, c_int32, P(gsr_tiling), c_void_p, c_void_p,
+                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, P(gsr_grad2d),
+                             c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "gsr_batched_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_int32, P(gsr_tiling), P(gsr_grad2d),
+                                    P(gsr_param_buffers), c_void_p], c_int32),
     "gsr_gemm_bf16": ([c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
                        c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int64,
                        c_int32, c_void_p, c_void_p], c_int32),
@@ -160,6 +169,11 @@ gsr_loss_workspace_size = _wrap("gsr_loss_workspace_size")
 gsr_loss_fwd_bwd = _wrap("gsr_loss_fwd_bwd")
 gsr_loss_fwd_bwd_static = _wrap("gsr_loss_fwd_bwd_static")
 gsr_render_bwd = _wrap("gsr_render_bwd")
+gsr_batched_preprocess = _wrap("gsr_batched_preprocess")
+gsr_batched_bin_sort = _wrap("gsr_batched_bin_sort")
+gsr_batched_iterate_workspace_size = _wrap("gsr_batched_iterate_workspace_size")
+gsr_batched_iterate = _wrap("gsr_batched_iterate")
+gsr_batched_preprocess_bwd = _wrap("gsr_batched_preprocess_bwd")
 gsr_gemm_bf16 = _wrap("gsr_gemm_bf16")
 gsr_mlp_workspace_size = _wrap("gsr_mlp_workspace_size")
 gsr_mlp_sync_weights = _wrap("gsr_mlp_sync_weights")

@@ -1,0 +1,150 @@
+"""Batched Gaussian-pyramid window (Sec. 3.4, Eq. 5) as one captured iteration.
+
+All (keyframe, level) views of a window are optimised together: one batched
+projection, one binning, ONE persistent launch for the forward blend, the
+Eq. 4 loss and its gradient, and the backward blend of every view, then the
+summed chain rule and Adam -- captured once as a CUDA graph and replayed.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib as L
+from .raster import (LAMBDA_DSSIM, PYRAMID_LEVELS, Adam, AdamConfig, Gaussians, _p, _stream, camera_at_level,
+                     camera_from, n_tiles, pyramid, tiling_struct)
+
+
+class BatchedWindow:
+    """views: every (keyframe, level) of `keyframes` = [(camera, level-0 gt)],
+    ordered level 0 first (largest images first balances the work queues)."""
+
+    def __init__(self, params: Gaussians, keyframes: Sequence, levels: int = PYRAMID_LEVELS,
+                 weights: Optional[Sequence[float]] = None, adam_cfg: AdamConfig = AdamConfig(),
+                 lam: float = LAMBDA_DSSIM, pair_capacity: Optional[int] = None, margin: float = 1.5):
+        self.params = params
+        self.tiling = tiling_struct(16, 16)
+        self.lam = lam
+        dev = params.mean_op.device
+        pyr = [pyramid(gt.contiguous(), levels) for _, gt in keyframes]
+        views = []
+        for l in range(levels):
+            for k, (cam, _) in enumerate(keyframes):
+                views.append((camera_at_level(camera_from(cam), l), pyr[k][l], l, k))
+        self.views = views
+        V = len(views)
+        assert V <= 64, "at most 64 views per window"
+        self.V = V
+        self.cams = (L.gsr_camera * V)(*[v[0] for v in views])
+        n = params.n
+        self.n = n
+        f32 = dict(dtype=torch.float32, device=dev)
+        m = max(n, 1) * V
+        self.xy_conic = torch.empty(m, 4, **f32)
+        self.c_op_box = torch.empty(m, 4, **f32)
+        self.rgb_depth = torch.empty(m, 4, **f32)
+        self.ntiles = torch.zeros(m, dtype=torch.int32, device=dev)
+        self.tiles = sum(n_tiles(v[0], self.tiling) for v in views)
+        self.ranges = torch.zeros(self.tiles, 2, dtype=torch.int32, device=dev)
+        self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.imgs = [torch.empty(3, v[0].height, v[0].width, **f32) for v in views]
+        self.T = [torch.empty(v[0].height, v[0].width, **f32) for v in views]
+        self.nc = [torch.empty(v[0].height, v[0].width, dtype=torch.int32, device=dev) for v in views]
+        self.dimg = [torch.empty(3, v[0].height, v[0].width, **f32) for v in views]
+        self.gts = [v[1].contiguous() for v in views]
+        self.losses = torch.zeros(V, **f32)
+        self.g2 = torch.zeros(3, m, 4, **f32)  # zero on entry; the chain step leaves it zero
+        self.grads = params.zeros_like()
+        self.adam = Adam(params, adam_cfg)
+        self.weights = (ctypes.c_float * V)(*(weights if weights is not None else [1.0] * V))
+        ptrs = lambda ts: (ctypes.c_void_p * V)(*[t.data_ptr() for t in ts])
+        self.p_img, self.p_T, self.p_nc = ptrs(self.imgs), ptrs(self.T), ptrs(self.nc)
+        self.p_gt, self.p_dimg = ptrs(self.gts), ptrs(self.dimg)
+        sz = ctypes.c_size_t()
+        L.gsr_batched_iterate_workspace_size(self.cams, V, ctypes.byref(sz))
+        self.iter_ws = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+        self.bg = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+        self._set_capacity(pair_capacity or 1 << 20)
+        if pair_capacity is None:
+            self.preprocess()
+            self.bin_sort()
+            need = int(self.num_pairs.item())
+            self._set_capacity(int(need * margin) + 4096)
+            self.status.zero_()
+        self.graph = None
+
+    def _set_capacity(self, cap: int):
+        dev = self.params.mean_op.device
+        self.cap = int(cap)
+        self.keys = torch.empty(self.cap, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(self.cap, dtype=torch.int32, device=dev)
+        sz = ctypes.c_size_t()
+        L.gsr_bin_sort_workspace_size(self.n * self.V, self.cap, None, ctypes.byref(self.tiling), ctypes.byref(sz))
+        self.sort_ws = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+
+    def proj(self) -> L.gsr_proj:
+        return L.gsr_proj(self.xy_conic.data_ptr(), self.c_op_box.data_ptr(), self.rgb_depth.data_ptr(),
+                          self.ntiles.data_ptr())
+
+    def grad2d(self) -> L.gsr_grad2d:
+        return L.gsr_grad2d(self.g2[0].data_ptr(), self.g2[1].data_ptr(), self.g2[2].data_ptr())
+
+    # -- the calls of one iteration ------------------------------------------
+    def preprocess(self, stream=None):
+        gs, pr = self.params.gaussians_struct(), self.proj()
+        L.gsr_batched_preprocess(ctypes.byref(gs), self.cams, self.V, ctypes.byref(self.tiling), ctypes.byref(pr),
+                                 _stream(stream))
+
+    def bin_sort(self, stream=None):
+        pr = self.proj()
+        L.gsr_batched_bin_sort(ctypes.byref(pr), self.n, self.cams, self.V, ctypes.byref(self.tiling), _p(self.keys),
+                               _p(self.vals), self.cap, _p(self.ranges), _p(self.num_pairs), _p(self.sort_ws),
+                               self.sort_ws.numel(), _p(self.status), _stream(stream))
+
+    def iterate(self, stream=None):
+        pr, g2 = self.proj(), self.grad2d()
+        L.gsr_batched_iterate(ctypes.byref(pr), _p(self.vals), _p(self.ranges), self.cams, self.V,
+                              ctypes.byref(self.tiling), self.bg, self.p_img, self.p_T, self.p_nc, self.p_gt,
+                              self.p_dimg, self.weights, self.lam, _p(self.losses), ctypes.byref(g2), _p(self.iter_ws),
+                              self.iter_ws.numel(), _p(self.status), _stream(stream))
+
+    def chain(self, stream=None):
+        gs, pr, g2, gb = self.params.gaussians_struct(), self.proj(), self.grad2d(), self.grads.buffers_struct()
+        L.gsr_batched_preprocess_bwd(ctypes.byref(gs), ctypes.byref(pr), self.cams, self.V, ctypes.byref(self.tiling),
+                                     ctypes.byref(g2), ctypes.byref(gb), _stream(stream))
+
+    def _run(self, stream=None, with_adam: bool = True):
+        self.preprocess(stream)
+        self.bin_sort(stream)
+        self.iterate(stream)
+        self.chain(stream)
+        if with_adam:
+            self.adam.step(self.grads, stream)
+
+    def capture(self):
+        """One CUDA graph for the whole iteration (after one eager warm-up whose
+        parameter update is undone)."""
+        saved = [t.clone() for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()]
+        step0 = self.adam.step_count.clone()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._run(s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        for dst, src in zip([t for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()], saved):
+            dst.copy_(src)
+        self.adam.step_count.copy_(step0)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._run(torch.cuda.current_stream())
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._run()

@@ -1,0 +1,463 @@
+// batched.cu -- a window of keyframes at every Gaussian-pyramid level in one
+// optimisation iteration (Photo-SLAM, arXiv 2311.16728, Sec. 3.4, Eq. 5):
+// instead of supervising one level at a time, all (keyframe, level) views of a
+// window are rendered, compared with GP^l(I_gt) (Eq. 4) and back-propagated
+// together, L = sum_v w_v L_v, so the gradient is the sum of the single-view
+// gradients.
+//
+//  - gsr_batched_preprocess: one thread per Gaussian projects it into every
+//    view (parameters read once; SH read once, coloured per view).
+//  - gsr_batched_bin_sort (binning.cu): one binning over all views' records
+//    with tiles numbered across views.
+//  - gsr_batched_iterate: ONE persistent cooperative launch runs, for every
+//    (view, tile) and every (view, channel, 32 x 32 block), the forward
+//    blend, both SSIM passes and the backward blend, pulling work from atomic
+//    queues; phases are separated by grid barriers whose waits are bounded.
+//  - gsr_batched_preprocess_bwd: one thread per Gaussian chains every view's
+//    screen-space gradient into the parameter gradient and clears it.
+#include "chain_impl.cuh"
+#include "render_impl.cuh"
+#include "ssim_impl.cuh"
+
+namespace gsr {
+
+struct ViewsK {
+    int nviews;
+    CamK cam[kMaxViews];
+};
+
+__global__ void __launch_bounds__(128) batched_preprocess_kernel(GaussK g, const __grid_constant__ ViewsK V,
+                                                                 float4 *__restrict__ xy_conic,
+                                                                 float4 *__restrict__ c_op_box,
+                                                                 float4 *__restrict__ rgb_depth,
+                                                                 uint32_t *__restrict__ ntiles) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+    float sh[48];
+    bool have_sh = false;
+    const int nc = (g.deg + 1) * (g.deg + 1);
+    for (int v = 0; v < V.nviews; ++v) {
+        const CamK &cam = V.cam[v];
+        const int64_t r = (int64_t)v * g.n + i;
+        Chain c;
+        if (!decide_chain(mo, q, ls, cam, c)) {
+            ntiles[r] = 0u;
+            continue;
+        }
+        float A, B, C, op;
+        chain_conic_opacity(c, mo.w, A, B, C, op);
+        if (!have_sh) {
+            load_sh(g.sh, g.n, i, g.deg, sh);
+            have_sh = true;
+        }
+        const float3 cc = cam_center(cam);
+        float dx = mo.x - cc.x, dy = mo.y - cc.y, dz = mo.z - cc.z;
+        const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv_len; dy *= inv_len; dz *= inv_len;
+        float Y[16];
+        sh_basis(dx, dy, dz, g.deg, Y, nullptr);
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < nc) acc += sh[3 * k + ch] * Y[k];
+            rgb[ch] = fmaxf(acc, 0.0f);
+        }
+        const uint32_t bx = (uint32_t)c.x0 | ((uint32_t)c.x1 << 16), by = (uint32_t)c.y0 | ((uint32_t)c.y1 << 16);
+        xy_conic[r] = make_float4(c.u, c.v, A, B);
+        c_op_box[r] = make_float4(C, op, __uint_as_float(bx), __uint_as_float(by));
+        rgb_depth[r] = make_float4(rgb[0], rgb[1], rgb[2], c.zc);
+        ntiles[r] = (uint32_t)((c.x1 / cam.tw - c.x0 / cam.tw + 1) * (c.y1 / cam.th - c.y0 / cam.th + 1));
+    }
+}
+
+// ---------------------------------------------------------------- persistent iteration
+constexpr int kIterThreads = 128;  // 256-pixel tiles (16 x 16, 32 x 8, 8 x 32) at two pixels per thread
+constexpr uint32_t kBarrierSpin = 1u << 24;  // x ~64 ns sleep: about a second
+
+struct IterView {
+    float *img, *T_final, *dimg, *mapA, *mapB, *mapC;
+    const float *gt;
+    uint32_t *n_contrib;
+    int W, H, gx, tile_off, loss_off, lbx, lby;
+    float weight;
+};
+
+struct IterArgs {
+    const float4 *xy, *cb, *rd;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    int tw, th;
+    float bg0, bg1, bg2;
+    int nviews, tiles_total, loss_items;
+    float lambda;
+    Win win;
+    float *g0, *g1, *g2;
+    float *partials, *losses;
+    unsigned *sync;  // [0..3] phase queues, [4] arrivals, [5] generation, [6] abort
+    int32_t *d_status;
+    IterView view[kMaxViews];
+};
+
+__device__ __forceinline__ int next_item(unsigned *counter, int *s_item) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *s_item;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  Returns
+// false when the run was aborted: a wait that exceeded its bound sets the
+// abort flag and the timeout status, and every later barrier and phase is
+// skipped.
+__device__ bool grid_barrier(unsigned *sync, unsigned nblocks, int32_t *status, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = sync + 5, *vabort = sync + 6;
+        int ok = *vabort == 0u;
+        if (ok) {
+            const unsigned g0 = *vgen;
+            __threadfence();
+            const unsigned arrived = atomicAdd(sync + 4, 1u) + 1u;
+            if (arrived == nblocks) {
+                atomicExch(sync + 4, 0u);
+                __threadfence();
+                atomicAdd(sync + 5, 1u);
+            } else {
+                uint32_t it = 0;
+                while (*vgen == g0) {
+                    if (*vabort) {
+                        ok = 0;
+                        break;
+                    }
+                    if (++it > kBarrierSpin) {
+                        atomicExch(sync + 6, 1u);
+                        raise_status(status, GSR_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        *s_ok = ok && *vabort == 0u;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__device__ __forceinline__ RenderArgs view_args(const IterArgs &a, const IterView &v) {
+    RenderArgs r;
+    r.xy_conic = a.xy;
+    r.c_op_box = a.cb;
+    r.rgb_depth = a.rd;
+    r.vals = a.vals;
+    r.ranges = a.ranges;
+    r.W = v.W;
+    r.H = v.H;
+    r.tw = a.tw;
+    r.th = a.th;
+    r.gx = v.gx;
+    r.tile_off = v.tile_off;
+    r.bg0 = a.bg0;
+    r.bg1 = a.bg1;
+    r.bg2 = a.bg2;
+    return r;
+}
+
+__device__ __forceinline__ int view_of_tile(const IterArgs &a, int t) {
+    int v = 0;
+    while (v + 1 < a.nviews && a.view[v + 1].tile_off <= t) ++v;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
+    int v = 0;
+    while (v + 1 < a.nviews && a.view[v + 1].loss_off <= t) ++v;
+    return v;
+}
+
+__global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
+    extern __shared__ float4 smem4[];
+    float *smf = reinterpret_cast<float *>(smem4);
+    __shared__ int s_item, s_ok;
+    __shared__ float s_red[32];
+    __shared__ double s_dbl[2 * kIterThreads];
+    const unsigned nb = gridDim.x;
+    // ---- phase 1: forward blend of every (view, tile)
+    for (int it = next_item(a.sync + 0, &s_item); it < a.tiles_total; it = next_item(a.sync + 0, &s_item)) {
+        const int v = view_of_tile(a, it);
+        const IterView &w = a.view[v];
+        render_fwd_tile(view_args(a, w), it - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
+    }
+    if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
+    // ---- phase 2: SSIM moments of every (view, channel, 32 x 32 block)
+    for (int it = next_item(a.sync + 1, &s_item); it < a.loss_items; it = next_item(a.sync + 1, &s_item)) {
+        const int v = view_of_loss(a, it);
+        const IterView &w = a.view[v];
+        const int local = it - w.loss_off, per = w.lbx * w.lby;
+        const int c = local / per, rem = local - c * per;
+        ssim_pass1_block<kIterThreads>(w.img, w.gt, w.H, w.W, a.win, w.mapA, w.mapB, w.mapC, a.partials + 2 * it,
+                                       rem % w.lbx, rem / w.lbx, c, smf, s_red);
+    }
+    if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
+    // ---- phase 3: dL/dI of every view, scaled by its weight; per-view losses
+    for (int it = next_item(a.sync + 2, &s_item); it < a.loss_items; it = next_item(a.sync + 2, &s_item)) {
+        const int v = view_of_loss(a, it);
+        const IterView &w = a.view[v];
+        const int local = it - w.loss_off, per = w.lbx * w.lby;
+        const int c = local / per, rem = local - c * per;
+        ssim_pass2_block<kIterThreads>(w.img, w.gt, w.H, w.W, 3, a.win, w.mapA, w.mapB, w.mapC, a.lambda, w.weight,
+                                       w.dimg, rem % w.lbx, rem / w.lbx, c, smf);
+    }
+    for (int v = blockIdx.x; v < a.nviews; v += gridDim.x) {
+        const IterView &w = a.view[v];
+        const float L = loss_from_partials<kIterThreads>(a.partials + 2 * w.loss_off, 3 * w.lbx * w.lby,
+                                                         3.0 * w.W * w.H, a.lambda, s_dbl);
+        if (threadIdx.x == 0) a.losses[v] = L;
+    }
+    if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
+    // ---- phase 4: backward blend of every (view, tile)
+    for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
+        const int v = view_of_tile(a, it);
+        const IterView &w = a.view[v];
+        render_bwd_tile(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1, a.g2, smem4);
+    }
+}
+
+static size_t iterate_smem() {
+    size_t s = render_bwd_smem(kIterThreads);
+    if (render_fwd_smem(kIterThreads) > s) s = render_fwd_smem(kIterThreads);
+    if (sizeof(float) * kPass1Floats > s) s = sizeof(float) * kPass1Floats;
+    if (sizeof(float) * kPass2Floats > s) s = sizeof(float) * kPass2Floats;
+    return s;
+}
+
+// ---------------------------------------------------------------- batched chain rule
+__global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, const __grid_constant__ ViewsK V,
+                                                                    const uint32_t *__restrict__ ntiles,
+                                                                    float4 *__restrict__ g0, float4 *__restrict__ g1,
+                                                                    float4 *__restrict__ g2, float4 *__restrict__ d_mo,
+                                                                    float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
+                                                                    float4 *__restrict__ d_sh) {
+    __shared__ uint32_t s_idx[kBwdChunk];
+    __shared__ uint32_t s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < kBwdChunk; k += kBwdThreads) {
+        const int64_t i = base + k;
+        bool vis = false;
+        if (i < g.n)
+            for (int v = 0; v < V.nviews && !vis; ++v) vis = ntiles[(int64_t)v * g.n + i] > 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        uint32_t slot = 0;
+        if (lane == 0 && m) slot = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+    }
+    __syncthreads();
+    const uint32_t cnt = s_cnt;
+    for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
+        const int64_t i = base + s_idx[k];
+        for (int v = 0; v < V.nviews; ++v) {
+            const int64_t r = (int64_t)v * g.n + i;
+            if (ntiles[r] == 0u) continue;
+            const int64_t off = (int64_t)v * g.n;
+            chain_one_gaussian(g, V.cam[v], i, g0 + off, g1 + off, g2 + off, d_mo, d_q, d_ls, d_sh, nullptr, nullptr);
+            // leave the screen-space gradient zeroed for the next iteration
+            g0[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            g1[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            g2[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+static int32_t views_k(const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling, ViewsK &V) {
+    int32_t rc;
+    if (!cams || nviews <= 0 || nviews > kMaxViews) {
+        set_error("batched: need 1 .. %d views", kMaxViews);
+        return GSR_ERR_INVALID_ARG;
+    }
+    V.nviews = nviews;
+    for (int v = 0; v < nviews; ++v) {
+        if ((rc = validate_camera(&cams[v]))) return rc;
+        V.cam[v] = make_camk(&cams[v], tiling);
+    }
+    return GSR_OK;
+}
+
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" int32_t gsr_batched_preprocess(const gsr_gaussians *g, const gsr_camera *cams, int32_t nviews,
+                                          const gsr_tiling *tiling, const gsr_proj *out, gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_gaussians(g)) || (rc = validate_tiling(tiling))) return rc;
+    ViewsK V;
+    if ((rc = views_k(cams, nviews, tiling, V))) return rc;
+    if (g->n == 0) return GSR_OK;
+    if (!out || !out->xy_conic || !out->c_op_box || !out->rgb_depth || !out->ntiles || !aligned16(out->xy_conic) ||
+        !aligned16(out->c_op_box) || !aligned16(out->rgb_depth)) {
+        set_error("gsr_batched_preprocess: output records must be non-NULL and 16-byte aligned");
+        return GSR_ERR_INVALID_ARG;
+    }
+    batched_preprocess_kernel<<<(unsigned)((g->n + 127) / 128), 128, 0, as_cuda(stream)>>>(
+        make_gk(g), V, reinterpret_cast<float4 *>(out->xy_conic), reinterpret_cast<float4 *>(out->c_op_box),
+        reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles);
+    return check_launch("batched_preprocess_kernel");
+}
+
+extern "C" int32_t gsr_batched_iterate_workspace_size(const gsr_camera *cams, int32_t nviews, size_t *bytes) {
+    if (!cams || nviews <= 0 || nviews > kMaxViews || !bytes) {
+        set_error("gsr_batched_iterate_workspace_size: bad arguments");
+        return GSR_ERR_INVALID_ARG;
+    }
+    size_t items = 0, px = 0;
+    for (int v = 0; v < nviews; ++v) {
+        items += 3 * (size_t)((cams[v].width + kLTW - 1) / kLTW) * ((cams[v].height + kLTH - 1) / kLTH);
+        px += 3 * (size_t)cams[v].width * cams[v].height;
+    }
+    // three SSIM maps per pixel-channel, two partial sums per block, sync words
+    *bytes = ((3 * px * sizeof(float) + 255) & ~size_t(255)) + ((2 * items * sizeof(float) + 255) & ~size_t(255)) + 256;
+    return GSR_OK;
+}
+
+extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *vals, const uint32_t *tile_ranges,
+                                       const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling,
+                                       const float *bg, float *const *img, float *const *T_final,
+                                       uint32_t *const *n_contrib, const float *const *gt, float *const *dL_dimg,
+                                       const float *weights, float lambda, float *d_losses, const gsr_grad2d *grad2d,
+                                       void *workspace, size_t workspace_bytes, int32_t *d_status,
+                                       gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_tiling(tiling))) return rc;
+    if (tiling->tile_w * tiling->tile_h != 2 * kIterThreads) {
+        set_error("gsr_batched_iterate: the persistent kernel runs 256-pixel tiles (tile_w * tile_h = 256)");
+        return GSR_ERR_UNSUPPORTED;
+    }
+    if (!proj || !tile_ranges || !cams || nviews <= 0 || nviews > kMaxViews || !img || !T_final || !n_contrib ||
+        !gt || !dL_dimg || !d_losses || !grad2d || !grad2d->g0 || !grad2d->g1 || !grad2d->g2 ||
+        !(lambda >= 0.f && lambda <= 1.f)) {
+        set_error("gsr_batched_iterate: bad arguments");
+        return GSR_ERR_INVALID_ARG;
+    }
+    size_t need;
+    if ((rc = gsr_batched_iterate_workspace_size(cams, nviews, &need))) return rc;
+    if (!workspace || workspace_bytes < need) {
+        set_error("gsr_batched_iterate: workspace of %zu bytes needed", need);
+        return GSR_ERR_CAPACITY;
+    }
+    IterArgs a{};  // passed by value as the kernel parameter
+    a.xy = reinterpret_cast<const float4 *>(proj->xy_conic);
+    a.cb = reinterpret_cast<const float4 *>(proj->c_op_box);
+    a.rd = reinterpret_cast<const float4 *>(proj->rgb_depth);
+    a.vals = vals;
+    a.ranges = reinterpret_cast<const uint2 *>(tile_ranges);
+    a.tw = tiling->tile_w;
+    a.th = tiling->tile_h;
+    a.bg0 = bg ? bg[0] : 0.f;
+    a.bg1 = bg ? bg[1] : 0.f;
+    a.bg2 = bg ? bg[2] : 0.f;
+    a.nviews = nviews;
+    a.lambda = lambda;
+    a.win = ssim_window();
+    a.g0 = grad2d->g0;
+    a.g1 = grad2d->g1;
+    a.g2 = grad2d->g2;
+    a.losses = d_losses;
+    a.d_status = d_status;
+    size_t px = 0;
+    int tiles = 0, items = 0;
+    for (int v = 0; v < nviews; ++v) {
+        if ((rc = validate_camera(&cams[v]))) return rc;
+        if (!img[v] || !T_final[v] || !n_contrib[v] || !gt[v] || !dL_dimg[v]) {
+            set_error("gsr_batched_iterate: NULL image pointer of view %d", v);
+            return GSR_ERR_INVALID_ARG;
+        }
+        IterView &w = a.view[v];
+        w.img = img[v];
+        w.T_final = T_final[v];
+        w.n_contrib = n_contrib[v];
+        w.gt = gt[v];
+        w.dimg = dL_dimg[v];
+        w.W = cams[v].width;
+        w.H = cams[v].height;
+        w.gx = grid_x(&cams[v], tiling);
+        w.tile_off = tiles;
+        tiles += grid_x(&cams[v], tiling) * grid_y(&cams[v], tiling);
+        w.lbx = (w.W + kLTW - 1) / kLTW;
+        w.lby = (w.H + kLTH - 1) / kLTH;
+        w.loss_off = items;
+        items += 3 * w.lbx * w.lby;
+        w.weight = weights ? weights[v] : 1.0f;
+        px += 3 * (size_t)w.W * w.H;
+    }
+    char *ws = static_cast<char *>(workspace);
+    float *maps = reinterpret_cast<float *>(ws);
+    size_t off = 0;
+    for (int v = 0; v < nviews; ++v) {
+        const size_t p = 3 * (size_t)a.view[v].W * a.view[v].H;
+        a.view[v].mapA = maps + off;
+        a.view[v].mapB = maps + px + off;
+        a.view[v].mapC = maps + 2 * px + off;
+        off += p;
+    }
+    const size_t maps_bytes = (3 * px * sizeof(float) + 255) & ~size_t(255);
+    a.partials = reinterpret_cast<float *>(ws + maps_bytes);
+    const size_t part_bytes = (2 * (size_t)items * sizeof(float) + 255) & ~size_t(255);
+    a.sync = reinterpret_cast<unsigned *>(ws + maps_bytes + part_bytes);
+    a.tiles_total = tiles;
+    a.loss_items = items;
+    cudaStream_t st = as_cuda(stream);
+    if (cudaMemsetAsync(a.sync, 0, 8 * sizeof(unsigned), st) != cudaSuccess) return check_launch("memset sync");
+    const size_t smem = iterate_smem();
+    cudaFuncSetAttribute(batched_iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_iterate_kernel, kIterThreads, smem);
+    if (per_sm < 1) {
+        set_error("gsr_batched_iterate: the persistent kernel does not fit on an SM");
+        return GSR_ERR_UNSUPPORTED;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(sms * per_sm));
+    cfg.blockDim = dim3(kIterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, batched_iterate_kernel, a) != cudaSuccess) return check_launch("batched_iterate_kernel");
+    return check_launch("batched_iterate_kernel");
+}
+
+extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
+                                              int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
+                                              const gsr_param_buffers *grads, gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_gaussians(g)) || (rc = validate_tiling(tiling))) return rc;
+    ViewsK V;
+    if ((rc = views_k(cams, nviews, tiling, V))) return rc;
+    if (g->n == 0) return GSR_OK;
+    if (!proj || !proj->ntiles || !grad2d || !grad2d->g0 || !grad2d->g1 || !grad2d->g2 || !grads ||
+        !grads->mean_op || !grads->quat || !grads->logscale || !grads->sh) {
+        set_error("gsr_batched_preprocess_bwd: NULL pointer");
+        return GSR_ERR_INVALID_ARG;
+    }
+    batched_chain_kernel<<<(unsigned)((g->n + kBwdChunk - 1) / kBwdChunk), kBwdThreads, 0, as_cuda(stream)>>>(
+        make_gk(g), V, proj->ntiles, reinterpret_cast<float4 *>(grad2d->g0), reinterpret_cast<float4 *>(grad2d->g1),
+        reinterpret_cast<float4 *>(grad2d->g2), reinterpret_cast<float4 *>(grads->mean_op),
+        reinterpret_cast<float4 *>(grads->quat), reinterpret_cast<float4 *>(grads->logscale),
+        reinterpret_cast<float4 *>(grads->sh));
+    return check_launch("batched_chain_kernel");
+}

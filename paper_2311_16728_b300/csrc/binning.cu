@@ -218,8 +218,8 @@ __device__ __forceinline__ int64_t warp_upper_index(const uint32_t *a, int64_t n
 __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     const uint32_t *__restrict__ coff, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
     const float4 *__restrict__ c_op_box, const int64_t *__restrict__ d_nvis, int64_t cap_n,
-    const int64_t *__restrict__ d_ncand, int64_t cand_cap, int tw, int th, int gx, uint8_t *__restrict__ flag,
-    uint32_t *__restrict__ ctile, uint32_t *__restrict__ cgid) {
+    const int64_t *__restrict__ d_ncand, int64_t cand_cap, int tw, int th, const ViewTiles vt,
+    uint8_t *__restrict__ flag, uint32_t *__restrict__ ctile, uint32_t *__restrict__ cgid) {
     __shared__ uint32_t s_off[kExpandTile + 1];
     __shared__ int64_t s_i0;
     __shared__ int s_m;
@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
         flag[slot] = tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1)
                          ? 1
                          : 0;
-        ctile[slot] = (uint32_t)(ty * gx + tx);
+        const int v = (int)((int64_t)gid / vt.n_per_view);  // view of this record
+        ctile[slot] = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
         cgid[slot] = gid;
     }
 }
@@ -525,12 +526,13 @@ extern "C" int32_t gsr_bin_sort_workspace_size(int64_t n, int64_t pair_capacity,
     return GSR_OK;
 }
 
-extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camera *cam, const gsr_tiling *tiling,
-                                uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
-                                int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,
-                                gsr_stream_t stream) {
+namespace gsr {
+// Binning of n records spread over the views of vt (tiles numbered 0 .. tiles - 1).
+int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int64_t tiles, const gsr_tiling *tiling,
+                      uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
+                      int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,
+                      gsr_stream_t stream) {
     int32_t rc;
-    if ((rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
     if (!proj || (n > 0 && (!proj->ntiles || !proj->xy_conic || !proj->c_op_box || !proj->rgb_depth)) || n < 0 ||
         pair_capacity < 0 || !tile_ranges || !d_num_pairs || (pair_capacity > 0 && (!keys || !vals))) {
         set_error("gsr_bin_sort: NULL pointer or negative size");
@@ -552,8 +554,6 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
     uint32_t *dkey = u32(L.dkey), *dval = u32(L.dval), *dkey2 = u32(L.dkey2), *dval2 = u32(L.dval2);
     uint32_t *tkey = u32(L.tkey), *tkey2 = u32(L.tkey2), *tval2 = u32(L.tval2);
     int64_t *d_nvis = reinterpret_cast<int64_t *>(ws + L.nvis);
-    const int gx = grid_x(cam, tiling), gy = grid_y(cam, tiling);
-    const int64_t tiles = (int64_t)gx * gy;
     if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st) != cudaSuccess)
         return check_launch("memset tile ranges");
     if (n == 0) {
@@ -583,7 +583,7 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
     cand_offsets_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums, L.scan_blocks,
                                                      L.cand_cap, coff, d_ncand, d_num_pairs, d_status);
     expand_kernel<<<(unsigned)L.expand_blocks, kExpandThreads, 0, st>>>(
-        coff, dval, xy, cb, d_nvis, n, d_ncand, L.cand_cap, tiling->tile_w, tiling->tile_h, gx, flag, ctile, cgid);
+        coff, dval, xy, cb, d_nvis, n, d_ncand, L.cand_cap, tiling->tile_w, tiling->tile_h, vt, flag, ctile, cgid);
     kept_count_kernel<<<(unsigned)L.cand_blocks, kScanThreads, 0, st>>>(flag, d_ncand, L.cand_cap, cblock_sums);
     kept_compact_kernel<<<(unsigned)L.cand_blocks, kScanThreads, 0, st>>>(flag, ctile, cgid, d_ncand, L.cand_cap,
                                                                           cblock_sums, L.cand_blocks, pair_capacity,
@@ -596,4 +596,50 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
     finalize_kernel<<<rb, 256, 0, st>>>(tkey, vals, rd, d_written, pair_capacity, (uint32_t)tiles, keys,
                                         reinterpret_cast<uint2 *>(tile_ranges));
     return check_launch("finalize_kernel");
+}
+}  // namespace gsr
+
+extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camera *cam, const gsr_tiling *tiling,
+                                uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
+                                int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,
+                                gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
+    ViewTiles vt{};
+    vt.nviews = 1;
+    vt.n_per_view = n > 0 ? n : 1;
+    vt.gx[0] = grid_x(cam, tiling);
+    vt.toff[0] = 0;
+    const int64_t tiles = (int64_t)grid_x(cam, tiling) * grid_y(cam, tiling);
+    return bin_sort_impl(proj, n, vt, tiles, tiling, keys, vals, pair_capacity, tile_ranges, d_num_pairs, workspace,
+                         workspace_bytes, d_status, stream);
+}
+
+extern "C" int32_t gsr_batched_bin_sort(const gsr_proj *proj, int64_t n_per_view, const gsr_camera *cams,
+                                        int32_t nviews, const gsr_tiling *tiling, uint64_t *keys, uint32_t *vals,
+                                        int64_t pair_capacity, uint32_t *tile_ranges, int64_t *d_num_pairs,
+                                        void *workspace, size_t workspace_bytes, int32_t *d_status,
+                                        gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_tiling(tiling))) return rc;
+    if (!cams || nviews <= 0 || nviews > kMaxViews || n_per_view < 0) {
+        set_error("gsr_batched_bin_sort: need 1 .. %d views and n_per_view >= 0", kMaxViews);
+        return GSR_ERR_INVALID_ARG;
+    }
+    ViewTiles vt{};
+    vt.nviews = nviews;
+    vt.n_per_view = n_per_view > 0 ? n_per_view : 1;
+    int64_t tiles = 0;
+    for (int v = 0; v < nviews; ++v) {
+        if ((rc = validate_camera(&cams[v]))) return rc;
+        vt.gx[v] = grid_x(&cams[v], tiling);
+        vt.toff[v] = (uint32_t)tiles;
+        tiles += (int64_t)grid_x(&cams[v], tiling) * grid_y(&cams[v], tiling);
+    }
+    if (n_per_view * nviews > 0xffffffffLL) {
+        set_error("gsr_batched_bin_sort: n_per_view x views must fit in 32 bits");
+        return GSR_ERR_UNSUPPORTED;
+    }
+    return bin_sort_impl(proj, n_per_view * nviews, vt, tiles, tiling, keys, vals, pair_capacity, tile_ranges,
+                         d_num_pairs, workspace, workspace_bytes, d_status, stream);
 }

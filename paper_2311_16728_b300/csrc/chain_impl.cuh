@@ -1,0 +1,234 @@
+// chain_impl.cuh -- parameter access and the per-Gaussian chain rule (K8)
+// from screen-space gradients to the 59 parameters, for the EWA splatting
+// cited by Eq. 3 of Photo-SLAM (arXiv 2311.16728, Sec. 3.3); shared by the
+// one-view kernels (preprocess.cu) and the multi-view ones (batched.cu).
+#pragma once
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+struct GaussK {
+    const float4 *mean_op, *quat, *logscale, *sh;
+    int64_t n;
+    int deg;
+};
+
+inline GaussK make_gk(const gsr_gaussians *g) {
+    return GaussK{reinterpret_cast<const float4 *>(g->mean_op), reinterpret_cast<const float4 *>(g->quat),
+                  reinterpret_cast<const float4 *>(g->logscale), reinterpret_cast<const float4 *>(g->sh), g->n,
+                  g->sh_degree};
+}
+
+// camera centre C = -R^T t
+__device__ __forceinline__ float3 cam_center(const CamK &cam) {
+    const float *R = cam.R, *t = cam.t;
+    return make_float3(-(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]), -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]),
+                       -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]));
+}
+
+__device__ __forceinline__ void load_sh(const float4 *__restrict__ sh, int64_t n, int64_t i, int deg, float out[48]) {
+    const int planes = sh_planes(deg);
+#pragma unroll
+    for (int j = 0; j < kShPlanes; ++j) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < planes) v = __ldg(sh + (int64_t)j * n + i);
+        out[4 * j + 0] = v.x;
+        out[4 * j + 1] = v.y;
+        out[4 * j + 2] = v.z;
+        out[4 * j + 3] = v.w;
+    }
+}
+
+// K8: screen-space gradients (du, dv, dA, dB, dC, dopacity, dr, dg, db) of one
+// Gaussian -> dL/d(mean, opacity logit, quaternion, log-scale, SH), added to
+// the gradient planes.  Only visible Gaussians have work, and they are a
+// small fraction of the map, so each CTA first compacts the visible indices
+// of its chunk in shared memory and then runs the chain on full warps.
+constexpr int kBwdThreads = 128;
+constexpr int kBwdChunk = 1024;  // Gaussians per CTA
+
+__device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &cam, int64_t i,
+                                                   const float4 *__restrict__ g0, const float4 *__restrict__ g1,
+                                                   const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
+                                                   float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
+                                                   float4 *__restrict__ d_sh, float *__restrict__ dstat,
+                                                   float *__restrict__ dcount) {
+    const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+    Chain c;
+    if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
+    const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
+    const float du = G0.x, dv = G0.y, dA = G0.z, dB = G0.w, dC = G1.x, dop = G1.y;
+    if (dstat) {
+        dstat[i] += sqrtf(du * du + dv * dv);
+        dcount[i] += 1.0f;
+    }
+    const float *W = cam.R;
+    // ---- colour and SH, streamed one float4 plane at a time
+    const float3 cc = cam_center(cam);
+    const float dirx = mo.x - cc.x, diry = mo.y - cc.y, dirz = mo.z - cc.z;
+    const float inv_len = 1.0f / sqrtf(dirx * dirx + diry * diry + dirz * dirz);
+    const float vx = dirx * inv_len, vy = diry * inv_len, vz = dirz * inv_len;
+    float Y[16];
+    float3 dY[16];
+    sh_basis(vx, vy, vz, g.deg, Y, dY);
+    const int nc = (g.deg + 1) * (g.deg + 1);
+    const int planes = sh_planes(g.deg);
+    // raw colour decides the clamp: first pass over the planes
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int j = 0; j < kShPlanes; ++j) {
+        if (j >= planes) break;
+        const float4 v = __ldg(g.sh + (int64_t)j * g.n + i);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int f = 4 * j + t, k = f / 3, ch = f % 3;
+            if (k < nc) raw[ch] += e[t] * Y[k];
+        }
+    }
+    const float dcol[3] = {raw[0] > 0.0f ? G1.z : 0.0f, raw[1] > 0.0f ? G1.w : 0.0f, raw[2] > 0.0f ? G2.x : 0.0f};
+    float3 dvh = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kShPlanes; ++j) {
+        if (j >= planes) break;
+        const float4 v = __ldg(g.sh + (int64_t)j * g.n + i);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+        float d[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int f = 4 * j + t, k = f / 3, ch = f % 3;
+            d[t] = 0.0f;
+            if (k < nc) {
+                d[t] = dcol[ch] * Y[k];
+                const float w = dcol[ch] * e[t];
+                dvh.x += w * dY[k].x;
+                dvh.y += w * dY[k].y;
+                dvh.z += w * dY[k].z;
+            }
+        }
+        float4 s = d_sh[(int64_t)j * g.n + i];
+        s.x += d[0];
+        s.y += d[1];
+        s.z += d[2];
+        s.w += d[3];
+        d_sh[(int64_t)j * g.n + i] = s;
+    }
+    const float vd = dvh.x * vx + dvh.y * vy + dvh.z * vz;
+    float dmx = (dvh.x - vx * vd) * inv_len, dmy = (dvh.y - vy * vd) * inv_len, dmz = (dvh.z - vz * vd) * inv_len;
+    // ---- opacity (the same FP32 conic and opacity the forward used)
+    float A, B, C, sig;
+    chain_conic_opacity(c, mo.w, A, B, C, sig);
+    const float dlogit = dop * sig * (1.0f - sig);
+    // ---- conic -> Sigma':  G_S' = -Q G_Q Q,  G_Q = [[dA, dB/2], [dB/2, dC]]
+    const float hB = 0.5f * dB;
+    const float t00 = A * dA + B * hB, t01 = A * hB + B * dC;
+    const float t10 = B * dA + C * hB, t11 = B * hB + C * dC;
+    const float Gs00 = -(t00 * A + t01 * B);
+    const float Gs11 = -(t10 * B + t11 * C);
+    const float Gs01 = -0.5f * ((t00 * B + t01 * C) + (t10 * A + t11 * B));
+    // ---- T = J W, J with the clamped x/z, y/z
+    const float limx = 1.3f * (0.5f * (float)cam.W / cam.fx), limy = 1.3f * (0.5f * (float)cam.H / cam.fy);
+    const bool clx = c.txz < -limx || c.txz > limx, cly = c.tyz < -limy || c.tyz > limy;
+    const float qx = fminf(limx, fmaxf(-limx, c.txz)), qy = fminf(limy, fmaxf(-limy, c.tyz));
+    const float iz = 1.0f / c.zc, iz2 = iz * iz;
+    const float J00 = cam.fx * iz, J02 = -cam.fx * qx * iz, J11 = cam.fy * iz, J12 = -cam.fy * qy * iz;
+    float T[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T[j] = J00 * W[j] + J02 * W[6 + j];
+        T[3 + j] = J11 * W[3 + j] + J12 * W[6 + j];
+    }
+    const float S[9] = {c.Sig[0], c.Sig[1], c.Sig[2], c.Sig[1], c.Sig[3], c.Sig[4], c.Sig[2], c.Sig[4], c.Sig[5]};
+    const float Gs[4] = {Gs00, Gs01, Gs01, Gs11};
+    // G_Sig = T^T G_S' T
+    float GS[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            GS[3 * k + l] = T[k] * (Gs[0] * T[l] + Gs[1] * T[3 + l]) + T[3 + k] * (Gs[2] * T[l] + Gs[3] * T[3 + l]);
+    // G_T = 2 G_S' T Sig
+    float TS[6];
+#pragma unroll
+    for (int i2 = 0; i2 < 2; ++i2)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            TS[3 * i2 + l] = T[3 * i2] * S[l] + T[3 * i2 + 1] * S[3 + l] + T[3 * i2 + 2] * S[6 + l];
+    float GT[6];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        GT[l] = 2.0f * (Gs[0] * TS[l] + Gs[1] * TS[3 + l]);
+        GT[3 + l] = 2.0f * (Gs[2] * TS[l] + Gs[3] * TS[3 + l]);
+    }
+    // G_J = G_T W^T (entries 00, 02, 11, 12 are the only live ones of J)
+    const float GJ00 = GT[0] * W[0] + GT[1] * W[1] + GT[2] * W[2];
+    const float GJ02 = GT[0] * W[6] + GT[1] * W[7] + GT[2] * W[8];
+    const float GJ11 = GT[3] * W[3] + GT[4] * W[4] + GT[5] * W[5];
+    const float GJ12 = GT[3] * W[6] + GT[4] * W[7] + GT[5] * W[8];
+    const float X = c.xc, Yc = c.yc;
+    float dpx = 0.f, dpy = 0.f, dpz = 0.f;
+    dpz += -(GJ00 * cam.fx + GJ11 * cam.fy) * iz2;
+    // J02 = -fx qx / z with qx = clamp(x / z)
+    if (!clx) {
+        dpx += -GJ02 * cam.fx * iz2;
+        dpz += GJ02 * cam.fx * (qx * iz2 + X * iz2 * iz);
+    } else {
+        dpz += GJ02 * cam.fx * qx * iz2;
+    }
+    if (!cly) {
+        dpy += -GJ12 * cam.fy * iz2;
+        dpz += GJ12 * cam.fy * (qy * iz2 + Yc * iz2 * iz);
+    } else {
+        dpz += GJ12 * cam.fy * qy * iz2;
+    }
+    // u = fx x / z + cx, v = fy y / z + cy
+    dpx += du * cam.fx * iz;
+    dpy += dv * cam.fy * iz;
+    dpz += -(du * cam.fx * X + dv * cam.fy * Yc) * iz2;
+    dmx += W[0] * dpx + W[3] * dpy + W[6] * dpz;
+    dmy += W[1] * dpx + W[4] * dpy + W[7] * dpz;
+    dmz += W[2] * dpx + W[5] * dpy + W[8] * dpz;
+    // ---- Sig = M M^T, M = Rq diag(s):  G_M = 2 G_Sig M
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * r + j] = c.Rq[3 * r + j] * c.s[j];
+    float GR[9], dls[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float ds = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float gm = 2.0f * (GS[3 * r] * M[j] + GS[3 * r + 1] * M[3 + j] + GS[3 * r + 2] * M[6 + j]);
+            ds += gm * c.Rq[3 * r + j];
+            GR[3 * r + j] = gm * c.s[j];
+        }
+        dls[j] = ds * c.s[j];
+    }
+    // rotation entries -> normalised quaternion (w, x, y, z)
+    const float w = c.qn[0], x = c.qn[1], y = c.qn[2], z = c.qn[3];
+    float dw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+    float dx2 = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] -
+                       2.f * x * GR[8]);
+    float dy2 = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] -
+                       2.f * y * GR[8]);
+    float dz2 = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] +
+                       x * GR[6] + y * GR[7]);
+    const float qd = dw * w + dx2 * x + dy2 * y + dz2 * z;
+    const float iq = 1.0f / c.qnorm;
+    dw = (dw - w * qd) * iq;
+    dx2 = (dx2 - x * qd) * iq;
+    dy2 = (dy2 - y * qd) * iq;
+    dz2 = (dz2 - z * qd) * iq;
+    // ---- accumulate (+=)
+    float4 a = d_mo[i];
+    d_mo[i] = make_float4(a.x + dmx, a.y + dmy, a.z + dmz, a.w + dlogit);
+    a = d_q[i];
+    d_q[i] = make_float4(a.x + dw, a.y + dx2, a.z + dy2, a.w + dz2);
+    a = d_ls[i];
+    d_ls[i] = make_float4(a.x + dls[0], a.y + dls[1], a.z + dls[2], a.w);
+}
+
+}  // namespace gsr

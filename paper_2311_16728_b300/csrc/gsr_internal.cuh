@@ -36,6 +36,16 @@ constexpr float kAlphaMin = 1.0f / 255.0f;  // alpha skip threshold
 constexpr float kTMin = 1e-4f;       // stop before T drops below this
 constexpr int kShPlanes = 12;        // 48 SH floats as 12 float4 planes
 
+// Views of a batched call: records of view v are [v n_per_view, (v + 1)
+// n_per_view); its tiles are numbered from toff[v] (row-major, gx[v] wide).
+constexpr int kMaxViews = 64;
+struct ViewTiles {
+    int nviews;
+    int64_t n_per_view;
+    int gx[kMaxViews];
+    uint32_t toff[kMaxViews];
+};
+
 // Camera as a kernel argument (by value).
 struct CamK {
     float R[9], t[3];

@@ -15,153 +15,21 @@
 
 #include <mutex>
 
-#include "gsr_internal.cuh"
+#include "ssim_impl.cuh"
 
 namespace gsr {
 
-constexpr int kLTW = 32, kLTH = 32, kLR = 5;       // output tile and window radius
-constexpr int kRW = kLTW + 2 * kLR, kRH = kLTH + 2 * kLR;
-constexpr int kRS = 45;                            // row stride of the staged region (conflict-free)
-constexpr int kRun = 4;                            // outputs per thread along a row / column
-constexpr int kLThreads = 256;
-
-struct Win {
-    float w[11];
-};
-
-static Win ssim_window() {
-    Win k;
-    double s = 0, v[11];
-    for (int i = 0; i < 11; ++i) {
-        v[i] = exp(-((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5));
-        s += v[i];
-    }
-    for (int i = 0; i < 11; ++i) k.w[i] = (float)(v[i] / s);
-    return k;
-}
-
-__device__ __forceinline__ float block_sum_256(float v, float *s_red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float r = 0.f;
-    if (threadIdx.x < 32) {
-        r = threadIdx.x < 8 ? s_red[threadIdx.x] : 0.f;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
-}
-
-// Stages a (kRH x kRW) region of plane `src` around the tile (zero outside).
-__device__ __forceinline__ void stage_region(const float *__restrict__ src, int H, int W, int ox, int oy, float *dst) {
-    for (int idx = threadIdx.x; idx < kRH * kRW; idx += kLThreads) {
-        const int r = idx / kRW, q = idx % kRW;
-        const int gy = oy - kLR + r, gx = ox - kLR + q;
-        dst[r * kRS + q] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? src[(int64_t)gy * W + gx] : 0.f;
-    }
-}
-
-// Pass 1: windowed moments (separable: rows then columns, kRun outputs per
-// thread from kRun + 10 staged values), SSIM map, its partials (a, b, c) and
-// per-CTA sums of |x - y| and SSIM.
 __global__ void __launch_bounds__(kLThreads) ssim_pass1_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                                                int H, int W, Win win, float *__restrict__ mapA,
                                                                float *__restrict__ mapB, float *__restrict__ mapC,
                                                                float *__restrict__ partials) {
     extern __shared__ float sm[];
-    float *sX = sm, *sY = sm + kRH * kRS;
-    float *sH = sm + 2 * kRH * kRS;  // [5][kRH][kLTW]
-    __shared__ float s_red[8];
-    const int c = blockIdx.z, ox = blockIdx.x * kLTW, oy = blockIdx.y * kLTH;
-    const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
-    stage_region(x + cb, H, W, ox, oy, sX);
-    stage_region(y + cb, H, W, ox, oy, sY);
-    __syncthreads();
-    // rows: kRH rows x (kLTW / kRun) runs
-    for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += kLThreads) {
-        const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
-        float a[kRun + 10], b[kRun + 10];
-#pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) {
-            a[k] = sX[r * kRS + j0 + k];
-            b[k] = sY[r * kRS + j0 + k];
-        }
-#pragma unroll
-        for (int o = 0; o < kRun; ++o) {
-            float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                const float w = win.w[k], av = a[o + k], bv = b[o + k];
-                mx += w * av;
-                my += w * bv;
-                xx += w * av * av;
-                yy += w * bv * bv;
-                xy += w * av * bv;
-            }
-            float *h = sH + r * kLTW + j0 + o;
-            h[0] = mx;
-            h[kRH * kLTW] = my;
-            h[2 * kRH * kLTW] = xx;
-            h[3 * kRH * kLTW] = yy;
-            h[4 * kRH * kLTW] = xy;
-        }
-    }
-    __syncthreads();
-    // columns: thread = (column, run of kRun rows)
-    const int tx = threadIdx.x % kLTW, i0 = (threadIdx.x / kLTW) * kRun;
-    float m[5][kRun];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        float col[kRun + 10];
-#pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) col[k] = sH[q * kRH * kLTW + (i0 + k) * kLTW + tx];
-#pragma unroll
-        for (int o = 0; o < kRun; ++o) {
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) s += win.w[k] * col[o + k];
-            m[q][o] = s;
-        }
-    }
-    float l1 = 0.f, ssim = 0.f;
-    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-#pragma unroll
-    for (int o = 0; o < kRun; ++o) {
-        const int gx = ox + tx, gy = oy + i0 + o;
-        if (gx < W && gy < H) {
-            const float mx = m[0][o], my = m[1][o];
-            const float sxx = m[2][o] - mx * mx, syy = m[3][o] - my * my, sxy = m[4][o] - mx * my;
-            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
-            const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-            const float iB = 1.0f / (B1 * B2);
-            const float S = A1 * A2 * iB;
-            const float dS_dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-            const float dS_dsxx = -S / B2;
-            const float dS_dsxy = 2.f * A1 * iB;
-            const int64_t idx = cb + (int64_t)gy * W + gx;
-            mapA[idx] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
-            mapB[idx] = dS_dsxx;
-            mapC[idx] = dS_dsxy;
-            const int rr = i0 + o + kLR, qq = tx + kLR;
-            l1 += fabsf(sX[rr * kRS + qq] - sY[rr * kRS + qq]);
-            ssim += S;
-        }
-    }
-    const float s1 = block_sum_256(l1, s_red);
-    const float s2 = block_sum_256(ssim, s_red);
-    if (threadIdx.x == 0) {
-        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[2 * b] = s1;
-        partials[2 * b + 1] = s2;
-    }
+    __shared__ float s_red[32];
+    const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    ssim_pass1_block<kLThreads>(x, y, H, W, win, mapA, mapB, mapC, partials + 2 * b, blockIdx.x, blockIdx.y,
+                                blockIdx.z, sm, s_red);
 }
 
-// Pass 2: blur (a, b, c) (the adjoint of the symmetric window), then
-// dL/dx = ((1 - lambda) sign(x - y) - lambda (G*a + 2 x G*b + y G*c)) / (C H W).
-// The first CTA also folds the per-CTA sums into the loss, in a fixed order.
 __global__ void __launch_bounds__(kLThreads) ssim_pass2_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                                                int H, int W, Win win, const float *__restrict__ mapA,
                                                                const float *__restrict__ mapB,
@@ -170,83 +38,18 @@ __global__ void __launch_bounds__(kLThreads) ssim_pass2_kernel(const float *__re
                                                                float lambda, float *__restrict__ d_loss,
                                                                float *__restrict__ dx_out) {
     extern __shared__ float sm[];
-    float *sM = sm;                  // [3][kRH][kRS]
-    float *sH = sm + 3 * kRH * kRS;  // [3][kRH][kLTW]
-    const int c = blockIdx.z, ox = blockIdx.x * kLTW, oy = blockIdx.y * kLTH;
-    const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
-    const float inv_n = (float)(1.0 / ((double)gridDim.z * (double)plane));  // 1 / (C H W)
-    stage_region(mapA + cb, H, W, ox, oy, sM);
-    stage_region(mapB + cb, H, W, ox, oy, sM + kRH * kRS);
-    stage_region(mapC + cb, H, W, ox, oy, sM + 2 * kRH * kRS);
-    __syncthreads();
-    for (int item = threadIdx.x; item < 3 * kRH * (kLTW / kRun); item += kLThreads) {
-        const int q = item / (kRH * (kLTW / kRun)), rem = item % (kRH * (kLTW / kRun));
-        const int r = rem / (kLTW / kRun), j0 = (rem % (kLTW / kRun)) * kRun;
-        float a[kRun + 10];
-#pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) a[k] = sM[q * kRH * kRS + r * kRS + j0 + k];
-#pragma unroll
-        for (int o = 0; o < kRun; ++o) {
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) s += win.w[k] * a[o + k];
-            sH[q * kRH * kLTW + r * kLTW + j0 + o] = s;
-        }
-    }
-    __syncthreads();
-    const int tx = threadIdx.x % kLTW, i0 = (threadIdx.x / kLTW) * kRun;
-    float g[3][kRun];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        float col[kRun + 10];
-#pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) col[k] = sH[q * kRH * kLTW + (i0 + k) * kLTW + tx];
-#pragma unroll
-        for (int o = 0; o < kRun; ++o) {
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) s += win.w[k] * col[o + k];
-            g[q][o] = s;
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < kRun; ++o) {
-        const int gx = ox + tx, gy = oy + i0 + o;
-        if (gx < W && gy < H) {
-            const int64_t idx = cb + (int64_t)gy * W + gx;
-            const float xv = x[idx], yv = y[idx];
-            const float d = xv - yv;
-            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            dx_out[idx] = ((1.f - lambda) * sg - lambda * (g[0][o] + 2.f * xv * g[1][o] + yv * g[2][o])) * inv_n;
-        }
-    }
+    __shared__ double s_dbl[2 * kLThreads];
+    ssim_pass2_block<kLThreads>(x, y, H, W, gridDim.z, win, mapA, mapB, mapC, lambda, 1.0f, dx_out, blockIdx.x,
+                                blockIdx.y, blockIdx.z, sm);
+    // the first CTA folds the per-CTA partial sums, always in the same order
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
-        __shared__ double s_l1[kLThreads], s_ss[kLThreads];
-        const int t = threadIdx.x;
-        double a = 0.0, b = 0.0;
-        for (int64_t k = t; k < npartials; k += kLThreads) {
-            a += (double)partials[2 * k];
-            b += (double)partials[2 * k + 1];
-        }
-        s_l1[t] = a;
-        s_ss[t] = b;
-        __syncthreads();
-        for (int o = kLThreads / 2; o > 0; o >>= 1) {
-            if (t < o) {
-                s_l1[t] += s_l1[t + o];
-                s_ss[t] += s_ss[t + o];
-            }
-            __syncthreads();
-        }
-        if (t == 0) {
-            const double cnt = (double)gridDim.z * (double)plane;
-            *d_loss = (float)((1.0 - lambda) * s_l1[0] / cnt + lambda * (1.0 - s_ss[0] / cnt));
-        }
+        const float L = loss_from_partials<kLThreads>(partials, npartials, (double)gridDim.z * H * W, lambda, s_dbl);
+        if (threadIdx.x == 0) *d_loss = L;
     }
 }
 
-constexpr size_t kPass1Smem = sizeof(float) * (2 * kRH * kRS + 5 * kRH * kLTW);
-constexpr size_t kPass2Smem = sizeof(float) * (3 * kRH * kRS + 3 * kRH * kLTW);
+constexpr size_t kPass1Smem = sizeof(float) * kPass1Floats;
+constexpr size_t kPass2Smem = sizeof(float) * kPass2Floats;
 
 static void launch_ssim(const float *img, const float *gt, int C, int H, int W, float lambda, float *d_loss,
                         float *dL_dimg, float *mA, float *mB, float *mC, float *part, int64_t nblocks,

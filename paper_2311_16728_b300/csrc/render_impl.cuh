@@ -1,0 +1,368 @@
+// render_impl.cuh -- per-tile routines of the forward blend (K5) and its
+// backward (K7) for the tile-based renderer of Photo-SLAM (arXiv 2311.16728)
+// Sec. 3.3, Eq. 3, shared by the one-view kernels (render.cu) and the
+// persistent multi-view kernel (batched.cu).  See render.cu for the design.
+#pragma once
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+struct RenderArgs {
+    const float4 *xy_conic, *c_op_box, *rgb_depth;
+    const uint32_t *vals;
+    const uint2 *ranges;  // indexed by tile_off + local tile
+    int W, H, tw, th, gx, tile_off;
+    float bg0, bg1, bg2;
+};
+
+constexpr float kHalfLog2e = -0.5f * 1.4426950408889634f;  // exponent of 2 = kHalfLog2e * (d^T Q d)
+
+// pixel (px, py0) and (px, py0 + 1) of this thread; origin of the tile
+__device__ __forceinline__ void thread_pixels(const RenderArgs &a, int tile, int &px, int &py0, int &ox, int &oy) {
+    ox = (tile % a.gx) * a.tw;
+    oy = (tile / a.gx) * a.th;
+    px = ox + (int)threadIdx.x % a.tw;
+    py0 = oy + 2 * ((int)threadIdx.x / a.tw);
+}
+
+// Stages Gaussian gid: exponent coefficients pre-scaled so that
+// exponent_2 = a2 dx^2 + b2 dx dy + c2 dy^2 (= -log2(e) d^T Q d / 2), and the
+// mask of warps (of a block of nwarps) that can see it.
+__device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, int ox, int oy, int nwarps,
+                                            float4 &s_xy, float4 &s_cb, float4 &s_rgb, uint32_t &s_mask) {
+    const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
+    s_rgb = __ldg(a.rgb_depth + gid);
+    const float A = g.z, B = g.w, C = c.x, op = c.y;
+    s_xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
+    s_cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
+    uint32_t mask = 0u;
+    const float tau = 2.0f * __logf(255.0f * op);  // alpha >= 1/255  <=>  d^T Q d <= tau
+    if (tau > 0.0f) {
+        // A C - B^2 with Kahan's two-FMA scheme: accurate even when the
+        // splat is very elongated and the difference cancels
+        const float bb = B * B;
+        const float det = __fmaf_rn(A, C, -bb) + __fmaf_rn(-B, B, bb);
+        const float ex = sqrtf(tau * C / det) * 1.001f + 0.01f;
+        const float ey = sqrtf(tau * A / det) * 1.001f + 0.01f;
+        const uint32_t bx = __float_as_uint(c.z), by = __float_as_uint(c.w);
+        const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+        for (int w = 0; w < nwarps; ++w) {
+            // pixel rectangle of warp w: threads [32 w, 32 w + 32) of the tile
+            const int t0 = 32 * w, t1 = 32 * w + 31;
+            const int rx0 = a.tw >= 32 ? ox + t0 % a.tw : ox;
+            const int rx1 = a.tw >= 32 ? rx0 + 31 : ox + a.tw - 1;
+            const int ry0 = oy + 2 * (t0 / a.tw), ry1 = oy + 2 * (t1 / a.tw) + 1;
+            const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
+            const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
+            const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
+            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey) mask |= 1u << w;
+        }
+    }
+    s_mask = mask;
+}
+
+// alpha of a staged splat at offset (dx, dy); false when the pixel skips it
+// (outside the box, positive exponent, or alpha < 1/255).
+struct Eval {
+    float G, alpha;
+    bool clamped;
+};
+
+__device__ __forceinline__ bool splat_alpha(float e2, float op, Eval &r) {
+    if (e2 > 0.0f) return false;
+    r.G = ex2_approx(e2);
+    const float raw = FM(op, r.G);
+    r.clamped = raw > kAlphaMax;
+    r.alpha = fminf(kAlphaMax, raw);
+    return r.alpha >= kAlphaMin;
+}
+
+// ---------------------------------------------------------------- K5
+// One tile (local index `tile` of the view in `a`), by the whole block.
+__device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, float *__restrict__ img,
+                                                float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
+                                                uint32_t *__restrict__ n_blended, float4 *smem) {
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
+    float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(smem + 3 * nthr);
+    int px, py0, ox, oy;
+    thread_pixels(a, tile, px, py0, ox, oy);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py0 + 1 < a.H;
+    const uint2 rg = a.ranges[a.tile_off + tile];
+    const int begin = (int)rg.x, end = (int)rg.y;
+    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)(py0 + 1);
+    float T0 = 1.0f, T1 = 1.0f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+    uint32_t last0 = 0, last1 = 0, nb0 = 0, nb1 = 0;
+    bool done0 = !in0, done1 = !in1;
+    for (int base = begin; base < end; base += nthr) {
+        // stop the whole tile once every pixel has terminated
+        if (__syncthreads_count(done0 && done1) == nthr) break;
+        const int idx = base + (int)threadIdx.x;
+        if (idx < end) stage_splat(a, a.vals[idx], ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x],
+                                   s_rgb[threadIdx.x], s_mask[threadIdx.x]);
+        else s_mask[threadIdx.x] = 0u;
+        __syncthreads();
+        const int cnt = min(nthr, end - base);
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            // warp-ballot early termination: leave once no pixel of the warp accumulates
+            if (__all_sync(0xffffffffu, done0 && done1)) break;
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            while (bits) {
+                const int j = c0 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const float4 g = s_xy[j], cb = s_cb[j];
+                const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
+                if (px < (int)(bx & 0xffffu) || px > (int)(bx >> 16)) continue;
+                const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+                const float dx = fpx - g.x;
+                const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
+                const uint32_t pos = (uint32_t)(base - begin + j + 1);
+                if (!done0 && py0 >= y0 && py0 <= y1) {
+                    const float dy = fpy0 - g.y;
+                    const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
+                    Eval ev;
+                    if (splat_alpha(e2, cb.y, ev)) {
+                        const float tn = FM(T0, FS(1.0f, ev.alpha));
+                        if (tn < kTMin) {
+                            done0 = true;
+                        } else {
+                            const float4 col = s_rgb[j];
+                            const float w = ev.alpha * T0;
+                            C00 += col.x * w;
+                            C01 += col.y * w;
+                            C02 += col.z * w;
+                            T0 = tn;
+                            last0 = pos;
+                            ++nb0;
+                        }
+                    }
+                }
+                if (!done1 && py0 + 1 >= y0 && py0 + 1 <= y1) {
+                    const float dy = fpy1 - g.y;
+                    const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
+                    Eval ev;
+                    if (splat_alpha(e2, cb.y, ev)) {
+                        const float tn = FM(T1, FS(1.0f, ev.alpha));
+                        if (tn < kTMin) {
+                            done1 = true;
+                        } else {
+                            const float4 col = s_rgb[j];
+                            const float w = ev.alpha * T1;
+                            C10 += col.x * w;
+                            C11 += col.y * w;
+                            C12 += col.z * w;
+                            T1 = tn;
+                            last1 = pos;
+                            ++nb1;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    const int64_t plane = (int64_t)a.W * a.H;
+    if (in0) {
+        const int64_t pix = (int64_t)py0 * a.W + px;
+        img[pix] = C00 + T0 * a.bg0;
+        img[plane + pix] = C01 + T0 * a.bg1;
+        img[2 * plane + pix] = C02 + T0 * a.bg2;
+        T_final[pix] = T0;
+        n_contrib[pix] = last0;
+        if (n_blended) n_blended[pix] = nb0;
+    }
+    if (in1) {
+        const int64_t pix = (int64_t)(py0 + 1) * a.W + px;
+        img[pix] = C10 + T1 * a.bg0;
+        img[plane + pix] = C11 + T1 * a.bg1;
+        img[2 * plane + pix] = C12 + T1 * a.bg2;
+        T_final[pix] = T1;
+        n_contrib[pix] = last1;
+        if (n_blended) n_blended[pix] = nb1;
+    }
+}
+
+
+// ---------------------------------------------------------------- K7
+// Back to front from each pixel's last contributor.  T_i = T_{i+1} / (1 -
+// alpha_i) recovers the transmittance in front of each Gaussian; the colour
+// behind it, normalised by T_{i+1}, follows acc <- acc (1 - alpha) + c alpha.
+//   dL/dc_i     = dL/dC alpha_i T_i
+//   dL/dalpha_i = T_i sum_ch dL/dC_ch (c_i,ch - acc_ch)
+// then through alpha = opacity exp(power) (zero where the 0.99 clamp holds).
+struct PixelBwd {
+    float T, acc0, acc1, acc2, dC0, dC1, dC2;
+    uint32_t last;
+};
+
+// Adds this pixel's contribution of splat j to v[9]; returns whether it had one.
+__device__ __forceinline__ bool pixel_bwd(PixelBwd &p, float e2, float op, float dx, float dy, float A, float B,
+                                          float C, const float4 &col, float v[9]) {
+    Eval ev;
+    if (!splat_alpha(e2, op, ev)) return false;
+    const float one_m = 1.0f - ev.alpha;
+    p.T = __fdividef(p.T, one_m);  // transmittance in front of this Gaussian
+    const float aT = ev.alpha * p.T;
+    v[6] += p.dC0 * aT;
+    v[7] += p.dC1 * aT;
+    v[8] += p.dC2 * aT;
+    const float dalpha = p.T * (p.dC0 * (col.x - p.acc0) + p.dC1 * (col.y - p.acc1) + p.dC2 * (col.z - p.acc2));
+    p.acc0 = p.acc0 * one_m + col.x * ev.alpha;
+    p.acc1 = p.acc1 * one_m + col.y * ev.alpha;
+    p.acc2 = p.acc2 * one_m + col.z * ev.alpha;
+    if (!ev.clamped) {
+        const float dpow = dalpha * ev.alpha;
+        v[5] += dalpha * ev.G;
+        v[0] += dpow * (A * dx + B * dy);
+        v[1] += dpow * (C * dy + B * dx);
+        v[2] += -0.5f * dx * dx * dpow;
+        v[3] += -dx * dy * dpow;
+        v[4] += -0.5f * dy * dy * dpow;
+    }
+    return true;
+}
+
+// Sums v[0..8] over the warp without broadcasting every value: each halving
+// step keeps half of the values in each lane of a pair and swaps the other
+// half (9 shuffles for v[0..7], 5 for v[8]).  Afterwards lane l holds the
+// warp total of value (l >> 2) & 7 and every lane holds the total of v[8].
+__device__ __forceinline__ float warp_transpose_sum(float v[9], float &v8) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? v[k] : v[k + 4];
+        const float keep = b4 ? v[k + 4] : v[k];
+        w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? w[k] : w[k + 2];
+        const float keep = b3 ? w[k + 2] : w[k];
+        x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    v8 = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(0xffffffffu, v8, o);
+    return y;
+}
+
+__device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, const float *__restrict__ T_final,
+                                                const uint32_t *__restrict__ n_contrib,
+                                                const float *__restrict__ dL_dimg, float *__restrict__ g0,
+                                                float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
+    float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(smem + 3 * nthr);
+    uint32_t *s_gid = s_mask + nthr;
+    uint32_t *s_max = s_gid + nthr;  // 32 entries
+    int px, py0, ox, oy;
+    thread_pixels(a, tile, px, py0, ox, oy);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py0 + 1 < a.H;
+    const uint2 rg = a.ranges[a.tile_off + tile];
+    const int begin = (int)rg.x;
+    const int64_t plane = (int64_t)a.W * a.H;
+    PixelBwd p0{0.f, a.bg0, a.bg1, a.bg2, 0.f, 0.f, 0.f, 0u}, p1 = p0;
+    if (in0) {
+        const int64_t pix = (int64_t)py0 * a.W + px;
+        p0.T = T_final[pix];
+        p0.last = n_contrib[pix];
+        p0.dC0 = dL_dimg[pix];
+        p0.dC1 = dL_dimg[plane + pix];
+        p0.dC2 = dL_dimg[2 * plane + pix];
+    }
+    if (in1) {
+        const int64_t pix = (int64_t)(py0 + 1) * a.W + px;
+        p1.T = T_final[pix];
+        p1.last = n_contrib[pix];
+        p1.dC0 = dL_dimg[pix];
+        p1.dC1 = dL_dimg[plane + pix];
+        p1.dC2 = dL_dimg[2 * plane + pix];
+    }
+    // block-wide max of n_contrib: positions at or beyond it are never used
+    const uint32_t m = __reduce_max_sync(0xffffffffu, max(p0.last, p1.last));
+    if (lane == 0) s_max[wid] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < (unsigned)nwarps ? s_max[threadIdx.x] : 0u;
+        v = __reduce_max_sync(0xffffffffu, v);
+        if (threadIdx.x == 0) s_max[0] = v;
+    }
+    __syncthreads();
+    // never past the tile's own list, whatever n_contrib holds
+    const int stop = min(begin + (int)s_max[0], (int)rg.y);
+    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)(py0 + 1);
+    // value k of the transposed reduction lands in lane 4k: its gradient slot
+    const int kval = (lane >> 2) & 7;
+    float *const gk = (kval < 4 ? g0 : g1) + (kval & 3);
+    for (int bend = stop; bend > begin; bend -= nthr) {
+        const int bstart = max(begin, bend - nthr);
+        __syncthreads();
+        const int idx = bstart + (int)threadIdx.x;
+        if (idx < bend) {
+            const uint32_t gid = a.vals[idx];
+            s_gid[threadIdx.x] = gid;
+            stage_splat(a, gid, ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x],
+                        s_mask[threadIdx.x]);
+        } else {
+            s_mask[threadIdx.x] = 0u;
+        }
+        __syncthreads();
+        const int cnt = bend - bstart;
+        for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            while (bits) {
+                const int jj = 31 - __clz(bits);
+                bits &= ~(1u << jj);
+                const int j = c0 + jj;
+                const uint32_t pos = (uint32_t)(bstart + j - begin);  // 0-based position in the tile list
+                float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                bool any = false;
+                const float4 g = s_xy[j], cb = s_cb[j];
+                const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
+                if (px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16) && (pos < p0.last || pos < p1.last)) {
+                    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+                    const float dx = fpx - g.x;
+                    const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
+                    // original conic for the gradient formulas
+                    const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e),
+                                C = cb.x * (1.0f / kHalfLog2e);
+                    const float4 col = s_rgb[j];
+                    if (pos < p0.last && py0 >= y0 && py0 <= y1) {
+                        const float dy = fpy0 - g.y;
+                        const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
+                        any |= pixel_bwd(p0, e2, cb.y, dx, dy, A, B, C, col, v);
+                    }
+                    if (pos < p1.last && py0 + 1 >= y0 && py0 + 1 <= y1) {
+                        const float dy = fpy1 - g.y;
+                        const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
+                        any |= pixel_bwd(p1, e2, cb.y, dx, dy, A, B, C, col, v);
+                    }
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    float v8;
+                    const float y = warp_transpose_sum(v, v8);
+                    const uint32_t gid = s_gid[j];
+                    if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
+                    else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+                }
+            }
+        }
+    }
+}
+
+
+// dynamic shared memory of the two tile routines for `nthr` threads
+__host__ __device__ inline size_t render_fwd_smem(int nthr) { return (3 * sizeof(float4) + sizeof(uint32_t)) * nthr; }
+__host__ __device__ inline size_t render_bwd_smem(int nthr) {
+    return (3 * sizeof(float4) + 2 * sizeof(uint32_t)) * nthr + 32 * sizeof(uint32_t);
+}
+
+}  // namespace gsr

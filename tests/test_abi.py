@@ -107,3 +107,33 @@ def test_defaults_match_paper_hyperparameters(gsr):
     assert gsr.LAMBDA_DSSIM == gold["lambda_dssim"]["value"]
     assert gsr.PYRAMID_LEVELS == gold["pyramid_levels"]["value"]
     assert 48 // 3 == gold["sh_coeffs_per_channel"]["value"]  # 12 float4 planes = 16 coefficients x RGB
+
+
+def test_batched_arguments_are_rejected_on_the_host(gsr):
+    L = gsr._lib
+    cam = gsr.camera_struct(np.eye(3), np.zeros(3), 100, 100, 50, 40, 100, 80)
+    sz = ctypes.c_size_t()
+    cams65 = (L.gsr_camera * 65)(*([cam] * 65))
+    assert L.gsr_batched_iterate_workspace_size.raw(cams65, 65, ctypes.byref(sz)) == L.GSR_ERR_INVALID_ARG
+    assert L.gsr_batched_iterate_workspace_size.raw(cams65, 0, ctypes.byref(sz)) == L.GSR_ERR_INVALID_ARG
+    assert L.gsr_batched_iterate_workspace_size.raw(cams65, 2, ctypes.byref(sz)) == L.GSR_OK
+    # three SSIM maps of 3 x 100 x 80 per view, 2 partials per 32 x 32 block (4 x 3 blocks x 3 channels)
+    assert sz.value >= 2 * (3 * 3 * 100 * 80 * 4 + 2 * 36 * 4)
+    # the persistent kernel runs 256-pixel tiles only
+    proj = L.gsr_proj(16, 16, 16, 16)
+    g2 = L.gsr_grad2d(16, 16, 16)
+    ptrs = (ctypes.c_void_p * 1)(16)
+    rc = L.gsr_batched_iterate.raw(ctypes.byref(proj), None, 16, cams65, 1, ctypes.byref(gsr.tiling_struct(16, 8)),
+                                   None, ptrs, ptrs, ptrs, ptrs, ptrs, None, 0.2, 16, ctypes.byref(g2), 16, 1 << 30,
+                                   None, None)
+    assert rc == L.GSR_ERR_UNSUPPORTED and b"256-pixel" in L.gsr_last_error()
+    # lambda outside [0, 1]
+    rc = L.gsr_batched_iterate.raw(ctypes.byref(proj), None, 16, cams65, 1, ctypes.byref(gsr.tiling_struct(16, 16)),
+                                   None, ptrs, ptrs, ptrs, ptrs, ptrs, None, 1.5, 16, ctypes.byref(g2), 16, 1 << 30,
+                                   None, None)
+    assert rc == L.GSR_ERR_INVALID_ARG
+    # too many views for the batched binning
+    g = L.gsr_gaussians(16, 16, 16, 16, 10, 3)
+    rc = L.gsr_batched_preprocess.raw(ctypes.byref(g), cams65, 65, ctypes.byref(gsr.tiling_struct(16, 16)),
+                                      ctypes.byref(proj), None)
+    assert rc == L.GSR_ERR_INVALID_ARG
