@@ -9,9 +9,15 @@ dataset itself is not available).  The path does not shard: with --gpus N
 every rank runs an independent replica (weak scaling, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--mode mapping|window|mlp]
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this path) on the host cores, on a bounded band of image rows per step.
+--mode window times the batched Gaussian-pyramid window (500k Gaussians,
+8 keyframes of 640 x 480 x 3 levels, one persistent launch per iteration,
+whole iteration in one CUDA graph); --mode mlp times the learned
+initialiser's tensor-core forward and training step at 2k and 20k rows.
+The default (mapping) line is the headline.
 """
 from __future__ import annotations
 
@@ -185,6 +191,178 @@ def count_kernel_nodes(graphs) -> int:
     return total
 
 
+# ---------------------------------------------------------------- batched window (pattern 2)
+WIN_N = 500_000
+WIN_KF = 8
+WIN_LEVELS = 3
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def run_window(args):
+    import torch
+    import synthetic as S
+    import paper_2311_16728_b300 as gsr
+    from paper_2311_16728_b300.autotune import autotune_window
+    from paper_2311_16728_b300.batched import BatchedWindow
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    target = S.room_scene(WIN_N, seed=0)
+    start = S.perturb(target, 0.05, seed=1)
+    cams = [S.tum_camera(k * N_POSES // WIN_KF) for k in range(WIN_KF)]
+    g_tgt = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
+    vb = gsr.ViewBuffers(WIN_N, gsr.camera_from(cams[0]), gsr.tiling_struct(16, 16), 1024)
+    kf = []
+    for cam in cams:
+        vb.cam = gsr.camera_from(cam)
+        gsr.ensure_capacity(vb, g_tgt)
+        vb.forward(g_tgt)
+        kf.append((cam, vb.img.clone()))
+    del vb, g_tgt
+    params = gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh)
+    tile, report = autotune_window(params, kf, levels=WIN_LEVELS, steps=5, warmup=2)
+    bw = BatchedWindow(params, kf, levels=WIN_LEVELS, tiling=gsr.tiling_struct(*tile))
+    bw.capture()
+    for _ in range(args.warmup):
+        bw.step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler()
+    clocks.start()
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(args.steps):
+        bw.step()
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop(int(os.environ.get("LOCAL_RANK", "0")))
+    if bw.status.item() != 0:
+        raise RuntimeError(f"device status {bw.status.item():#x} during the timed region")
+    ms_per_step = t0.elapsed_time(t1) / args.steps
+    launches_per_iter = count_kernel_nodes([bw.graph])
+    # end to end: every view's target image from pinned host memory in, the per-view losses out
+    host_gts = [g.cpu().pin_memory() for g in bw.gts]
+    host_loss = torch.empty(bw.V, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(args.steps):
+        for d, h in zip(bw.gts, host_gts):
+            d.copy_(h, non_blocking=True)
+        bw.step()
+        host_loss.copy_(bw.losses, non_blocking=True)
+    t1.record()
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / args.steps
+    h2d = sum(g.numel() * 4 for g in bw.gts)
+    # stage breakdown: the same iteration captured one graph per stage
+    bw.capture(per_stage=True)
+    nst = len(bw.STAGES)
+    ksteps = min(args.steps, 200)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)] for _ in range(ksteps)]
+    for k in range(ksteps):
+        bw.step(events=evs[k])
+    torch.cuda.synchronize()
+    stage_ms = {nm: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, nm in enumerate(bw.STAGES)}
+    # work counters (outside the timed region): blends of every view at the final parameters
+    blends = 0
+    nblend = None
+    for cam_v, _, _, _ in bw.views:
+        vbv = gsr.ViewBuffers(WIN_N, cam_v, bw.tiling, 1024)
+        gsr.ensure_capacity(vbv, params)
+        nblend = torch.zeros(cam_v.height, cam_v.width, dtype=torch.int32, device="cuda")
+        vbv.preprocess(params)
+        vbv.bin_sort()
+        vbv.render_fwd(n_blended=nblend)
+        blends += int(nblend.sum().item())
+        del vbv
+    peaks = _peaks()
+    mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    fp32 = 148 * 128 * 2 * mhz * 1e6 / 1e12
+    flops = (FLOPS_PER_BLEND_FWD + FLOPS_PER_BLEND_BWD) * blends
+    it_s = stage_ms["iterate"] * 1e-3
+    px = sum(c.width * c.height for c, _, _, _ in bw.views)
+    line = {"metric": f"window iters/s @{WIN_N // 1000}k Gaussians, {WIN_KF} keyframes 640x480 x {WIN_LEVELS} levels",
+            "value": 1000.0 / ms_per_step, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; TUM-shaped keyframes)",
+            "views_per_s": bw.V * 1000.0 / ms_per_step,
+            "config": {"workload": f"batched Gaussian-pyramid window: {WIN_N} Gaussians in a 6x3x4 m room, "
+                                   f"{WIN_KF} keyframes 640x480 fx=fy=525 x {WIN_LEVELS} levels = {bw.V} views, "
+                                   f"{bw.tiles} tiles, {px} px; one persistent launch per iteration; whole "
+                                   "iteration (preprocess, binning, persistent fwd/loss/bwd, chain, Adam) in one "
+                                   "CUDA graph", "tile": f"{tile[0]}x{tile[1]} (autotuned)",
+                       "autotune_ms": report["ms_per_step"], "pairs": int(bw.num_pairs.item()),
+                       "l2": "inputs larger than L2 (4 x 120 MB of params, grads, moments per step)"},
+            "roofline": {"kernel": "batched_iterate_kernel (fwd + bwd blends)", "bound": "alu",
+                         "achieved": flops / it_s / 1e12, "peak": fp32, "unit": "TFLOP/s",
+                         "frac": flops / it_s / 1e12 / fp32, "traffic": None, "alg_per_launch": flops,
+                         "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"},
+            "stages_ms": stage_ms, "work": {"blends": blends, "views": bw.V},
+            "gpu_launches": launches_per_iter * args.steps, "clocks": clk,
+            "e2e": {"value": 1000.0 / e2e_ms, "unit": "iters/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 4 * bw.V}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- learned initialiser (cfg5)
+def run_mlp(args):
+    import torch
+    from paper_2311_16728_b300.learned_init import LearnedInit, init_weights, pad_rows, K_IN, H, N_OUT, N3
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peaks = _peaks()
+    out = []
+    for M in (2048, 20000):
+        li = LearnedInit(init_weights(3), M, lr=1e-4)
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        li.x[:M, :K_IN] = torch.rand(M, K_IN, device="cuda", generator=gen).to(torch.bfloat16)
+        li.xT.copy_(li.x.t())
+        tgt = torch.zeros(li.mpad, N3, device="cuda")
+        tgt[:M, :N_OUT] = torch.randn(M, N_OUT, device="cuda", generator=gen)
+        fwd_flop = 2.0 * M * (K_IN * H + H * H + H * N_OUT)
+        res = {"rows": M, "padded_rows": li.mpad}
+        for name, fn, flop in (("forward", lambda: li.forward(), fwd_flop),
+                               ("train_step", lambda: li.train_step(tgt, M), 3 * fwd_flop)):
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                fn()
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            for _ in range(max(args.warmup, 3)):
+                g.replay()
+            reps = 200
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": ms, "tflops": flop / ms / 1e9,
+                         "frac_of_bf16_burst": flop / ms / 1e9 / peaks.get("bf16_tflops", 1800.0)}
+        if li.status.item() != 0:
+            raise RuntimeError(f"MLP device status {li.status.item():#x}")
+        out.append(res)
+    big = out[-1]["train_step"]
+    line = {"metric": "learned-initialiser training step TFLOP/s @20k rows (2308-256-256-56, BF16 x BF16 -> FP32)",
+            "value": big["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": 200, "warmup": max(args.warmup, 3),
+            "ms_per_step": big["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic (seeded uniform patches, Gaussian targets)",
+            "config": {"workload": "MLP forward / training step (5 tcgen05 GEMMs + fused epilogues + Adam) on "
+                                   "2k and 20k rows", "results": out},
+            "roofline": {"kernel": "training step (all GEMMs)", "bound": "tensor", "achieved": big["tflops"],
+                         "peak": peaks.get("bf16_tflops", 1800.0), "unit": "TFLOP/s",
+                         "frac": big["frac_of_bf16_burst"], "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; of measured)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,13 +370,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
-    ap.add_argument("--cpu-rows", type=int, default=160, help="image rows of the cpu_baseline sample")
+    ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
+    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--poses", type=int, default=N_POSES, help="trajectory poses trained on (profiling uses fewer)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "window":
+        run_window(args)
+        return
+    if args.mode == "mlp":
+        run_mlp(args)
         return
 
     import torch

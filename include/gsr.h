@@ -300,8 +300,12 @@ int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *vals, const ui
                             float *d_losses, const gsr_grad2d *grad2d, void *workspace, size_t workspace_bytes,
                             int32_t *d_status, gsr_stream_t stream);
 
-/* Chains every view's screen-space gradient into `grads` (+=), one thread per
- * Gaussian summing over the views that see it, and zeroes grad2d again. */
+/* Chains every view's screen-space gradient into `grads` (+=, atomically)
+ * and zeroes grad2d again.  Views that are exact power-of-two scalings of one
+ * camera (the pyramid levels of a keyframe: same pose, fx, fy, cx, cy, width
+ * and height all scaled by 2^-k) are merged before the chain rule, which then
+ * runs once per (Gaussian, keyframe): u, v scale by 2^-k, the dilated
+ * covariance is 4^-k M + 0.3 I, and opacity and colour are shared. */
 int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
                                    int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
                                    const gsr_param_buffers *grads, gsr_stream_t stream);

@@ -23,9 +23,10 @@ class BatchedWindow:
 
     def __init__(self, params: Gaussians, keyframes: Sequence, levels: int = PYRAMID_LEVELS,
                  weights: Optional[Sequence[float]] = None, adam_cfg: AdamConfig = AdamConfig(),
-                 lam: float = LAMBDA_DSSIM, pair_capacity: Optional[int] = None, margin: float = 1.5):
+                 lam: float = LAMBDA_DSSIM, pair_capacity: Optional[int] = None, margin: float = 1.5,
+                 tiling: Optional[L.gsr_tiling] = None):
         self.params = params
-        self.tiling = tiling_struct(16, 16)
+        self.tiling = tiling or tiling_struct(16, 16)
         self.lam = lam
         dev = params.mean_op.device
         pyr = [pyramid(gt.contiguous(), levels) for _, gt in keyframes]
@@ -75,6 +76,7 @@ class BatchedWindow:
             self._set_capacity(int(need * margin) + 4096)
             self.status.zero_()
         self.graph = None
+        self.stage_graphs = None
 
     def _set_capacity(self, cap: int):
         dev = self.params.mean_op.device
@@ -116,35 +118,72 @@ class BatchedWindow:
         L.gsr_batched_preprocess_bwd(ctypes.byref(gs), ctypes.byref(pr), self.cams, self.V, ctypes.byref(self.tiling),
                                      ctypes.byref(g2), ctypes.byref(gb), _stream(stream))
 
-    def _run(self, stream=None, with_adam: bool = True):
-        self.preprocess(stream)
-        self.bin_sort(stream)
-        self.iterate(stream)
-        self.chain(stream)
-        if with_adam:
-            self.adam.step(self.grads, stream)
+    STAGES = ("preprocess", "bin_sort", "iterate", "chain", "adam")
 
-    def capture(self):
-        """One CUDA graph for the whole iteration (after one eager warm-up whose
-        parameter update is undone)."""
-        saved = [t.clone() for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()]
-        step0 = self.adam.step_count.clone()
+    def _stage(self, name: str, stream=None):
+        if name == "adam":
+            self.adam.step(self.grads, stream)
+        else:
+            getattr(self, name)(stream)
+
+    def _run(self, stream=None):
+        for name in self.STAGES:
+            self._stage(name, stream)
+
+    def _snapshot(self):
+        return [t.clone() for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()], \
+            self.adam.step_count.clone()
+
+    def _restore(self, snap):
+        saved, step0 = snap
+        for dst, src in zip([t for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()], saved):
+            dst.copy_(src)
+        self.adam.step_count.copy_(step0)
+
+    def capture(self, per_stage: bool = False):
+        """Captures the whole iteration as ONE CUDA graph (per_stage=False) or
+        one graph per stage, so that events between stages time them live.
+        One eager warm-up iteration loads the kernels first; its effect on the
+        parameters, moments and step counter is undone."""
+        snap = self._snapshot()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             self._run(s)
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
-        for dst, src in zip([t for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()], saved):
-            dst.copy_(src)
-        self.adam.step_count.copy_(step0)
+        self._restore(snap)
         torch.cuda.synchronize()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self._run(torch.cuda.current_stream())
+        if per_stage:
+            self.graph = None
+            self.stage_graphs = []
+            for name in self.STAGES:
+                gph = torch.cuda.CUDAGraph(keep_graph=True)
+                with torch.cuda.graph(gph):
+                    self._stage(name, torch.cuda.current_stream())
+                gph.instantiate()
+                self.stage_graphs.append(gph)
+        else:
+            self.stage_graphs = None
+            self.graph = torch.cuda.CUDAGraph(keep_graph=True)  # kept for kernel-node counting
+            with torch.cuda.graph(self.graph):
+                self._run(torch.cuda.current_stream())
+            self.graph.instantiate()
 
-    def step(self):
-        if self.graph is not None:
+    def graphs(self):
+        return [self.graph] if self.graph is not None else list(self.stage_graphs or [])
+
+    def step(self, events=None):
+        """One iteration over the whole window.  `events` (per-stage capture
+        only): len(STAGES) + 1 CUDA events recorded around the stages."""
+        if getattr(self, "stage_graphs", None):
+            if events is not None:
+                events[0].record()
+            for i, gph in enumerate(self.stage_graphs):
+                gph.replay()
+                if events is not None:
+                    events[i + 1].record()
+        elif self.graph is not None:
             self.graph.replay()
         else:
             self._run()

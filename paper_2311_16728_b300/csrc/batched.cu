@@ -15,6 +15,9 @@
 //    queues; phases are separated by grid barriers whose waits are bounded.
 //  - gsr_batched_preprocess_bwd: one thread per Gaussian chains every view's
 //    screen-space gradient into the parameter gradient and clears it.
+#include <algorithm>
+#include <cmath>
+
 #include "chain_impl.cuh"
 #include "render_impl.cuh"
 #include "ssim_impl.cuh"
@@ -238,44 +241,132 @@ static size_t iterate_smem() {
 }
 
 // ---------------------------------------------------------------- batched chain rule
+// The pyramid levels of one keyframe are exact power-of-two scalings of one
+// camera (same pose; fx, fy, cx, cy, W, H all scaled by s = 2^-k), so with
+// M = J W Sigma W^T J^T at the finest level, level k sees u_k = s u,
+// v_k = s v and Sigma'_k = s^2 M + 0.3 I, while the opacity, the view
+// direction (hence the colour and its clamp) and the near-plane test are the
+// same.  The screen-space gradients of such views therefore merge exactly
+// into one view before the chain rule: dL/du += s dL/du_k, dL/dv += s dL/dv_k,
+// dL/dM += s^2 dL/dSigma'_k (with dL/dSigma' = -Q dL/dQ Q per view), and the
+// opacity and colour gradients add.  The expensive chain then runs once per
+// (Gaussian, keyframe) instead of once per (Gaussian, view).
+constexpr int kGroupMax = 8;     // views per group
+constexpr int kChainChunk = 128; // Gaussians per CTA
+
+struct ChainGroups {
+    int ngroups;
+    int count[kMaxViews];
+    int member[kMaxViews][kGroupMax];   // view index, finest level first
+    float scale[kMaxViews][kGroupMax];  // relative to the group's first view (1, 1/2, 1/4, ...)
+};
+
 __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, const __grid_constant__ ViewsK V,
+                                                                    const __grid_constant__ ChainGroups CG,
+                                                                    const float4 *__restrict__ xy_conic,
+                                                                    const float4 *__restrict__ c_op_box,
                                                                     const uint32_t *__restrict__ ntiles,
                                                                     float4 *__restrict__ g0, float4 *__restrict__ g1,
                                                                     float4 *__restrict__ g2, float4 *__restrict__ d_mo,
                                                                     float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
                                                                     float4 *__restrict__ d_sh) {
-    __shared__ uint32_t s_idx[kBwdChunk];
+    extern __shared__ uint32_t s_rec[];  // kChainChunk x ngroups candidates
     __shared__ uint32_t s_cnt;
     if (threadIdx.x == 0) s_cnt = 0u;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
+    const int64_t base = (int64_t)blockIdx.x * kChainChunk;
     const int lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < kBwdChunk; k += kBwdThreads) {
-        const int64_t i = base + k;
+    const int total = kChainChunk * CG.ngroups;  // a multiple of 32: whole warps take part in each ballot
+    for (int k = threadIdx.x; k < total; k += kBwdThreads) {
+        const int il = k % kChainChunk, grp = k / kChainChunk;
+        const int64_t i = base + il;
         bool vis = false;
         if (i < g.n)
-            for (int v = 0; v < V.nviews && !vis; ++v) vis = ntiles[(int64_t)v * g.n + i] > 0u;
-        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+            for (int m = 0; m < CG.count[grp] && !vis; ++m) vis = ntiles[(int64_t)CG.member[grp][m] * g.n + i] > 0u;
+        const uint32_t msk = __ballot_sync(0xffffffffu, vis);
         uint32_t slot = 0;
-        if (lane == 0 && m) slot = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+        if (lane == 0 && msk) slot = atomicAdd(&s_cnt, (uint32_t)__popc(msk));
         slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+        if (vis) s_rec[slot + __popc(msk & ((1u << lane) - 1u))] = ((uint32_t)grp << 16) | (uint32_t)il;
     }
     __syncthreads();
     const uint32_t cnt = s_cnt;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
-        const int64_t i = base + s_idx[k];
-        for (int v = 0; v < V.nviews; ++v) {
-            const int64_t r = (int64_t)v * g.n + i;
+        const int grp = (int)(s_rec[k] >> 16);
+        const int64_t i = base + (s_rec[k] & 0xFFFFu);
+        // the finest visible view of the group is the base of the merge
+        int mb = 0;
+        while (mb + 1 < CG.count[grp] && ntiles[(int64_t)CG.member[grp][mb] * g.n + i] == 0u) ++mb;
+        const int vb = CG.member[grp][mb];
+        const CamK &cam = V.cam[vb];
+        const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+        Chain c;
+        if (!decide_chain(mo, q, ls, cam, c)) continue;  // cannot happen for a visible record
+        ScreenGrad sg = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float sb = CG.scale[grp][mb];
+        for (int m = mb; m < CG.count[grp]; ++m) {
+            const int64_t r = (int64_t)CG.member[grp][m] * g.n + i;
             if (ntiles[r] == 0u) continue;
-            const int64_t off = (int64_t)v * g.n;
-            chain_one_gaussian(g, V.cam[v], i, g0 + off, g1 + off, g2 + off, d_mo, d_q, d_ls, d_sh, nullptr, nullptr);
+            const float4 G0 = g0[r], G1 = g1[r], G2 = g2[r];
+            const float4 xc = __ldg(xy_conic + r), cb = __ldg(c_op_box + r);
+            const float s = CG.scale[grp][m] / sb;  // exact: both are powers of two
+            float h00, h01, h11;
+            conic_grad_to_cov(xc.z, xc.w, cb.x, G0.z, G0.w, G1.x, h00, h01, h11);
+            const float s2 = s * s;
+            sg.du += s * G0.x;
+            sg.dv += s * G0.y;
+            sg.Gs00 += s2 * h00;
+            sg.Gs01 += s2 * h01;
+            sg.Gs11 += s2 * h11;
+            sg.dop += G1.y;
+            sg.dr += G1.z;
+            sg.dg += G1.w;
+            sg.db += G2.x;
             // leave the screen-space gradient zeroed for the next iteration
             g0[r] = make_float4(0.f, 0.f, 0.f, 0.f);
             g1[r] = make_float4(0.f, 0.f, 0.f, 0.f);
             g2[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        chain_core(g, cam, i, mo, c, sg, d_mo, d_q, d_ls, d_sh, true);
     }
+}
+
+// Groups of views that are exact power-of-two scalings of one camera.
+static bool is_scaling(const gsr_camera &a, const gsr_camera &b, float &s) {
+    for (int k = 0; k < 9; ++k)
+        if (a.R[k] != b.R[k]) return false;
+    for (int k = 0; k < 3; ++k)
+        if (a.t[k] != b.t[k]) return false;
+    s = b.fx / a.fx;
+    int e;
+    if (!(s > 0.f) || std::frexp(s, &e) != 0.5f) return false;
+    return b.fy == a.fy * s && b.cx == a.cx * s && b.cy == a.cy * s && (float)b.width == (float)a.width * s &&
+           (float)b.height == (float)a.height * s;
+}
+
+static void make_groups(const gsr_camera *cams, int nviews, ChainGroups &G) {
+    G.ngroups = 0;
+    for (int v = 0; v < nviews; ++v) {
+        int found = -1;
+        float s = 1.f;
+        for (int q = 0; q < G.ngroups && found < 0; ++q)
+            if (G.count[q] < kGroupMax && is_scaling(cams[G.member[q][0]], cams[v], s)) found = q;
+        if (found < 0) {
+            found = G.ngroups++;
+            G.count[found] = 0;
+            s = 1.f;
+        }
+        G.member[found][G.count[found]] = v;
+        G.scale[found][G.count[found]] = s;
+        G.count[found]++;
+    }
+    // finest first within each group (insertion sort by descending scale)
+    for (int q = 0; q < G.ngroups; ++q)
+        for (int a = 1; a < G.count[q]; ++a)
+            for (int b = a; b > 0 && G.scale[q][b] > G.scale[q][b - 1]; --b) {
+                std::swap(G.scale[q][b], G.scale[q][b - 1]);
+                std::swap(G.member[q][b], G.member[q][b - 1]);
+            }
 }
 
 static int32_t views_k(const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling, ViewsK &V) {
@@ -454,10 +545,18 @@ extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_
         set_error("gsr_batched_preprocess_bwd: NULL pointer");
         return GSR_ERR_INVALID_ARG;
     }
-    batched_chain_kernel<<<(unsigned)((g->n + kBwdChunk - 1) / kBwdChunk), kBwdThreads, 0, as_cuda(stream)>>>(
-        make_gk(g), V, proj->ntiles, reinterpret_cast<float4 *>(grad2d->g0), reinterpret_cast<float4 *>(grad2d->g1),
-        reinterpret_cast<float4 *>(grad2d->g2), reinterpret_cast<float4 *>(grads->mean_op),
-        reinterpret_cast<float4 *>(grads->quat), reinterpret_cast<float4 *>(grads->logscale),
-        reinterpret_cast<float4 *>(grads->sh));
+    if (!proj->xy_conic || !proj->c_op_box) {
+        set_error("gsr_batched_preprocess_bwd: NULL record pointer");
+        return GSR_ERR_INVALID_ARG;
+    }
+    ChainGroups CG;
+    make_groups(cams, nviews, CG);
+    const size_t smem = sizeof(uint32_t) * kChainChunk * CG.ngroups;
+    batched_chain_kernel<<<(unsigned)((g->n + kChainChunk - 1) / kChainChunk), kBwdThreads, smem, as_cuda(stream)>>>(
+        make_gk(g), V, CG, reinterpret_cast<const float4 *>(proj->xy_conic),
+        reinterpret_cast<const float4 *>(proj->c_op_box), proj->ntiles, reinterpret_cast<float4 *>(grad2d->g0),
+        reinterpret_cast<float4 *>(grad2d->g1), reinterpret_cast<float4 *>(grad2d->g2),
+        reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),
+        reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh));
     return check_launch("batched_chain_kernel");
 }

@@ -48,21 +48,41 @@ __device__ __forceinline__ void load_sh(const float4 *__restrict__ sh, int64_t n
 constexpr int kBwdThreads = 128;
 constexpr int kBwdChunk = 1024;  // Gaussians per CTA
 
-__device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &cam, int64_t i,
-                                                   const float4 *__restrict__ g0, const float4 *__restrict__ g1,
-                                                   const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
-                                                   float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
-                                                   float4 *__restrict__ d_sh, float *__restrict__ dstat,
-                                                   float *__restrict__ dcount) {
-    const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
-    Chain c;
-    if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
-    const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
-    const float du = G0.x, dv = G0.y, dA = G0.z, dB = G0.w, dC = G1.x, dop = G1.y;
-    if (dstat) {
-        dstat[i] += sqrtf(du * du + dv * dv);
-        dcount[i] += 1.0f;
+// Screen-space gradient of one Gaussian in one view, with the conic part
+// already taken to the dilated 2D covariance: Gs = dL/dSigma' (symmetric).
+struct ScreenGrad {
+    float du, dv, Gs00, Gs01, Gs11, dop, dr, dg, db;
+};
+
+// conic Q = Sigma'^-1 = [[A, B], [B, C]] and G_Q = [[dA, dB/2], [dB/2, dC]]
+// -> G_Sigma' = -Q G_Q Q
+__device__ __forceinline__ void conic_grad_to_cov(float A, float B, float C, float dA, float dB, float dC, float &Gs00,
+                                                  float &Gs01, float &Gs11) {
+    const float hB = 0.5f * dB;
+    const float t00 = A * dA + B * hB, t01 = A * hB + B * dC;
+    const float t10 = B * dA + C * hB, t11 = B * hB + C * dC;
+    Gs00 = -(t00 * A + t01 * B);
+    Gs11 = -(t10 * B + t11 * C);
+    Gs01 = -0.5f * ((t00 * B + t01 * C) + (t10 * A + t11 * B));
+}
+
+__device__ __forceinline__ void add4(float4 *p, float4 v, bool atomic) {
+    if (atomic) {
+        atomicAdd(p, v);  // 128-bit global float atomic (sm_90 and later)
+    } else {
+        const float4 a = *p;
+        *p = make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w);
     }
+}
+
+// Chain rule of one Gaussian from its screen-space gradient in camera `cam`
+// (c = the forward chain of that camera) to the 59 parameters, added to the
+// gradient planes (atomically when several threads may add to the same
+// Gaussian).
+__device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int64_t i, const float4 mo, const Chain &c,
+                                           const ScreenGrad &sg, float4 *__restrict__ d_mo, float4 *__restrict__ d_q,
+                                           float4 *__restrict__ d_ls, float4 *__restrict__ d_sh, bool atomic) {
+    const float du = sg.du, dv = sg.dv, dop = sg.dop;
     const float *W = cam.R;
     // ---- colour and SH, streamed one float4 plane at a time
     const float3 cc = cam_center(cam);
@@ -87,7 +107,7 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
             if (k < nc) raw[ch] += e[t] * Y[k];
         }
     }
-    const float dcol[3] = {raw[0] > 0.0f ? G1.z : 0.0f, raw[1] > 0.0f ? G1.w : 0.0f, raw[2] > 0.0f ? G2.x : 0.0f};
+    const float dcol[3] = {raw[0] > 0.0f ? sg.dr : 0.0f, raw[1] > 0.0f ? sg.dg : 0.0f, raw[2] > 0.0f ? sg.db : 0.0f};
     float3 dvh = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < kShPlanes; ++j) {
@@ -107,26 +127,14 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
                 dvh.z += w * dY[k].z;
             }
         }
-        float4 s = d_sh[(int64_t)j * g.n + i];
-        s.x += d[0];
-        s.y += d[1];
-        s.z += d[2];
-        s.w += d[3];
-        d_sh[(int64_t)j * g.n + i] = s;
+        add4(d_sh + (int64_t)j * g.n + i, make_float4(d[0], d[1], d[2], d[3]), atomic);
     }
     const float vd = dvh.x * vx + dvh.y * vy + dvh.z * vz;
     float dmx = (dvh.x - vx * vd) * inv_len, dmy = (dvh.y - vy * vd) * inv_len, dmz = (dvh.z - vz * vd) * inv_len;
-    // ---- opacity (the same FP32 conic and opacity the forward used)
-    float A, B, C, sig;
-    chain_conic_opacity(c, mo.w, A, B, C, sig);
+    // ---- opacity (the same FP32 opacity the forward used)
+    const float sig = FD(1.0f, FA(1.0f, chain_exp(-mo.w)));
     const float dlogit = dop * sig * (1.0f - sig);
-    // ---- conic -> Sigma':  G_S' = -Q G_Q Q,  G_Q = [[dA, dB/2], [dB/2, dC]]
-    const float hB = 0.5f * dB;
-    const float t00 = A * dA + B * hB, t01 = A * hB + B * dC;
-    const float t10 = B * dA + C * hB, t11 = B * hB + C * dC;
-    const float Gs00 = -(t00 * A + t01 * B);
-    const float Gs11 = -(t10 * B + t11 * C);
-    const float Gs01 = -0.5f * ((t00 * B + t01 * C) + (t10 * A + t11 * B));
+    const float Gs00 = sg.Gs00, Gs01 = sg.Gs01, Gs11 = sg.Gs11;
     // ---- T = J W, J with the clamped x/z, y/z
     const float limx = 1.3f * (0.5f * (float)cam.W / cam.fx), limy = 1.3f * (0.5f * (float)cam.H / cam.fy);
     const bool clx = c.txz < -limx || c.txz > limx, cly = c.tyz < -limy || c.tyz > limy;
@@ -223,12 +231,38 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
     dy2 = (dy2 - y * qd) * iq;
     dz2 = (dz2 - z * qd) * iq;
     // ---- accumulate (+=)
-    float4 a = d_mo[i];
-    d_mo[i] = make_float4(a.x + dmx, a.y + dmy, a.z + dmz, a.w + dlogit);
-    a = d_q[i];
-    d_q[i] = make_float4(a.x + dw, a.y + dx2, a.z + dy2, a.w + dz2);
-    a = d_ls[i];
-    d_ls[i] = make_float4(a.x + dls[0], a.y + dls[1], a.z + dls[2], a.w);
+    add4(d_mo + i, make_float4(dmx, dmy, dmz, dlogit), atomic);
+    add4(d_q + i, make_float4(dw, dx2, dy2, dz2), atomic);
+    add4(d_ls + i, make_float4(dls[0], dls[1], dls[2], 0.0f), atomic);
+}
+
+// One view: the screen-space gradient of record i (g0, g1, g2) chained into
+// the parameter gradients of Gaussian i (one thread per Gaussian).
+__device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &cam, int64_t i,
+                                                   const float4 *__restrict__ g0, const float4 *__restrict__ g1,
+                                                   const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
+                                                   float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
+                                                   float4 *__restrict__ d_sh, float *__restrict__ dstat,
+                                                   float *__restrict__ dcount) {
+    const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+    Chain c;
+    if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
+    const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
+    if (dstat) {
+        dstat[i] += sqrtf(G0.x * G0.x + G0.y * G0.y);
+        dcount[i] += 1.0f;
+    }
+    float A, B, C, sig;
+    chain_conic_opacity(c, mo.w, A, B, C, sig);
+    ScreenGrad sg;
+    sg.du = G0.x;
+    sg.dv = G0.y;
+    conic_grad_to_cov(A, B, C, G0.z, G0.w, G1.x, sg.Gs00, sg.Gs01, sg.Gs11);
+    sg.dop = G1.y;
+    sg.dr = G1.z;
+    sg.dg = G1.w;
+    sg.db = G2.x;
+    chain_core(g, cam, i, mo, c, sg, d_mo, d_q, d_ls, d_sh, false);
 }
 
 }  // namespace gsr

@@ -25,6 +25,21 @@ def pad_rows(m: int) -> int:
     return max(128, (m + 127) // 128 * 128)
 
 
+def init_weights(seed: int = 3) -> dict:
+    """He-uniform FP32 weights (limit sqrt(6 / fan_in)) on the valid block of
+    each layer, zero padding and zero biases."""
+    rng = np.random.default_rng(seed)
+
+    def layer(rows_valid, fan_in, rows, cols):
+        w = np.zeros((rows, cols), np.float32)
+        bound = np.sqrt(6.0 / fan_in)
+        w[:rows_valid, :fan_in] = rng.uniform(-bound, bound, (rows_valid, fan_in))
+        return w
+
+    return {"W1": layer(H, K_IN, H, K0), "b1": np.zeros(H, np.float32), "W2": layer(H, H, H, H),
+            "b2": np.zeros(H, np.float32), "W3": layer(N_OUT, H, N3, H), "b3": np.zeros(N3, np.float32)}
+
+
 class MLPWeights:
     """FP32 masters + BF16 copies (or FP32-only moments) on the device."""
 
