@@ -197,6 +197,17 @@ WIN_KF = 8
 WIN_LEVELS = 3
 
 
+def _profile_steps(step, k):
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profiled_steps": k}), flush=True)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(path)) if os.path.exists(path) else {}
@@ -222,12 +233,19 @@ def run_window(args):
         kf.append((cam, vb.img.clone()))
     del vb, g_tgt
     params = gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh)
-    tile, report = autotune_window(params, kf, levels=WIN_LEVELS, steps=5, warmup=2)
+    if args.tile == "auto":
+        tile, report = autotune_window(params, kf, levels=WIN_LEVELS, steps=5, warmup=2)
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
+        report = {"ms_per_step": {}}
     bw = BatchedWindow(params, kf, levels=WIN_LEVELS, tiling=gsr.tiling_struct(*tile))
     bw.capture()
     for _ in range(args.warmup):
         bw.step()
     torch.cuda.synchronize()
+    if args.profile:
+        _profile_steps(bw.step, args.steps)
+        return
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler()
     clocks.start()
@@ -265,17 +283,40 @@ def run_window(args):
         bw.step(events=evs[k])
     torch.cuda.synchronize()
     stage_ms = {nm: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, nm in enumerate(bw.STAGES)}
+    phases = bw.phase_ms()
+    phases["bwd_blend"] = stage_ms["iterate"] - phases.pop("entry_to_bwd")
     # work counters (outside the timed region): blends of every view at the final parameters
+    # and the same views through the one-view kernels, timed one by one
     blends = 0
-    nblend = None
-    for cam_v, _, _, _ in bw.views:
+    single = {"render_fwd": 0.0, "loss": 0.0, "blend_bwd": 0.0}
+    per_level = {}
+    for cam_v, gt_v, lvl, _ in bw.views:
         vbv = gsr.ViewBuffers(WIN_N, cam_v, bw.tiling, 1024)
         gsr.ensure_capacity(vbv, params)
         nblend = torch.zeros(cam_v.height, cam_v.width, dtype=torch.int32, device="cuda")
         vbv.preprocess(params)
         vbv.bin_sort()
         vbv.render_fwd(n_blended=nblend)
-        blends += int(nblend.sum().item())
+        nb = int(nblend.sum().item())
+        blends += nb
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        vbv.render_fwd()
+        ev[1].record()
+        vbv.loss_fwd_bwd(gt_v, 0.2)
+        ev[2].record()
+        vbv.blend_bwd()
+        ev[3].record()
+        torch.cuda.synchronize()
+        for j, nm in enumerate(("render_fwd", "loss", "blend_bwd")):
+            single[nm] += ev[j].elapsed_time(ev[j + 1])
+        pl = per_level.setdefault(str(lvl), {"views": 0, "blends": 0, "pairs": 0, "render_fwd_ms": 0.0,
+                                             "blend_bwd_ms": 0.0})
+        pl["views"] += 1
+        pl["blends"] += nb
+        pl["pairs"] += int(vbv.num_pairs.item())
+        pl["render_fwd_ms"] += ev[0].elapsed_time(ev[1])
+        pl["blend_bwd_ms"] += ev[2].elapsed_time(ev[3])
         del vbv
     peaks = _peaks()
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
@@ -292,14 +333,15 @@ def run_window(args):
                                    f"{WIN_KF} keyframes 640x480 fx=fy=525 x {WIN_LEVELS} levels = {bw.V} views, "
                                    f"{bw.tiles} tiles, {px} px; one persistent launch per iteration; whole "
                                    "iteration (preprocess, binning, persistent fwd/loss/bwd, chain, Adam) in one "
-                                   "CUDA graph", "tile": f"{tile[0]}x{tile[1]} (autotuned)",
+                                   "CUDA graph", "tile": f"{tile[0]}x{tile[1]}" + (" (autotuned)" if args.tile == "auto" else " (given)"),
                        "autotune_ms": report["ms_per_step"], "pairs": int(bw.num_pairs.item()),
                        "l2": "inputs larger than L2 (4 x 120 MB of params, grads, moments per step)"},
             "roofline": {"kernel": "batched_iterate_kernel (fwd + bwd blends)", "bound": "alu",
                          "achieved": flops / it_s / 1e12, "peak": fp32, "unit": "TFLOP/s",
                          "frac": flops / it_s / 1e12 / fp32, "traffic": None, "alg_per_launch": flops,
                          "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"},
-            "stages_ms": stage_ms, "work": {"blends": blends, "views": bw.V},
+            "stages_ms": stage_ms, "iterate_phases_ms": phases,
+            "one_view_kernels_ms": single, "per_level": per_level, "work": {"blends": blends, "views": bw.V},
             "gpu_launches": launches_per_iter * args.steps, "clocks": clk,
             "e2e": {"value": 1000.0 / e2e_ms, "unit": "iters/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 4 * bw.V}}
@@ -373,6 +415,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
     ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
+    ap.add_argument("--profile", action="store_true",
+                    help="run --steps iterations between cudaProfilerStart/Stop after the warm-up and exit "
+                         "(for ncu --profile-from-start off); prints no bench line")
     ap.add_argument("--poses", type=int, default=N_POSES, help="trajectory poses trained on (profiling uses fewer)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -415,6 +461,9 @@ def main():
     for _ in range(args.warmup):
         ms.step()
     torch.cuda.synchronize()
+    if args.profile:
+        _profile_steps(ms.step, args.steps)
+        return
     if world > 1:
         dist.barrier()
 
@@ -505,16 +554,22 @@ def main():
         import synthetic as S
         rows = min(args.cpu_rows, HEIGHT)
         row0 = (HEIGHT - rows) // 2
-        cam = cams[0]
-        dt = oracle.decide(target.mean_op, target.quat, target.logscale, cam.as_array(), WIDTH, HEIGHT)
         st = oracle.Scene64(target.mean_op, target.quat, target.logscale, target.sh)
-        im, _, _, _ = oracle.render(st, cam.as_array(), WIDTH, HEIGHT, dt, rows=(row0, row0 + rows))
-        full, det = oracle_sample(start, im[:, row0:row0 + rows].copy(), cams, 0, rows, row0)
-        line["cpu_baseline"] = {"value": 1.0 / full, "unit": "iters/s", "cores": oracle.num_threads(),
+        total, measured = 0.0, 0.0
+        poses = (0, 1)
+        for pose in poses:
+            cam = cams[pose]
+            dt = oracle.decide(target.mean_op, target.quat, target.logscale, cam.as_array(), WIDTH, HEIGHT)
+            im, _, _, _ = oracle.render(st, cam.as_array(), WIDTH, HEIGHT, dt, rows=(row0, row0 + rows))
+            full, det = oracle_sample(start, im[:, row0:row0 + rows].copy(), cams, pose, rows, row0)
+            total += full
+            measured += det["measured_s"]
+        line["cpu_baseline"] = {"value": len(poses) / total, "unit": "iters/s", "cores": oracle.num_threads(),
                                 "kind": "oracle",
-                                "sample": f"one iteration at pose 0: decide+Adam over all {N_GAUSS} Gaussians, "
-                                          f"render+loss+backward on rows {row0}-{row0 + rows} of 680, "
-                                          f"extrapolated to the full frame ({det['measured_s']:.1f} s measured)"}
+                                "sample": f"{len(poses)} iterations (poses 0, 1): decide+Adam over all {N_GAUSS} "
+                                          f"Gaussians, render+loss+backward on rows {row0}-{row0 + rows} of 680"
+                                          + (", extrapolated to the full frame" if rows < HEIGHT else "")
+                                          + f" ({measured:.1f} s measured)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

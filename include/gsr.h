@@ -292,7 +292,10 @@ int32_t gsr_batched_iterate_workspace_size(const gsr_camera *cams, int32_t nview
  * bounded (about a second): a wait that gives up sets GSR_ERR_TIMEOUT in
  * *d_status and the launch winds down.  img, T_final, n_contrib, gt, dL_dimg
  * are arrays of nviews device pointers (host arrays); weights (host, may be
- * NULL = all 1).  Tiles must hold 256 pixels (16 x 16, 32 x 8 or 8 x 32). */
+ * NULL = all 1).  Tiles must hold 256 pixels (16 x 16, 32 x 8 or 8 x 32).
+ * The last 256 bytes of the workspace hold the launch's queue and barrier
+ * words; its bytes 64 .. 95 receive four uint64 global-timer stamps (ns) taken
+ * by block 0 at entry and after each of the three barriers (phase split). */
 int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *vals, const uint32_t *tile_ranges,
                             const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling, const float *bg,
                             float *const *img, float *const *T_final, uint32_t *const *n_contrib,

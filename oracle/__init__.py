@@ -68,6 +68,7 @@ def lib():
         L.orc_pyramid_down.argtypes = [P, i32, i32, i32, P]
         L.orc_adam.argtypes = [i64, P, P, P, P, P, i32, dbl, dbl, dbl]
         L.orc_psnr.argtypes = [P, P, i64]
+        L.orc_default_init.argtypes = [P, i32, i32, P, i64, P, P, i64, i64, P, P, P, P, P]
         L.orc_psnr.restype = dbl
         _lib = L
     return _lib
@@ -268,6 +269,24 @@ def adam(p, g, m, v, lr, step: int, b1=0.9, b2=0.999, eps=1e-15):
 def psnr(img, gt) -> float:
     img, gt = _f64(img), _f64(gt)
     return float(lib().orc_psnr(_p(img), _p(gt), img.size))
+
+
+def default_init(img, keypoints, cam, ref_xyz, offset: int):
+    """Default initialisation of M new primitives (see orc_default_init).
+    keypoints (M, 5) float32; ref_xyz (N, 3) map means, rows offset ..
+    offset + M - 1 being the new primitives.  Returns a dict of FP64 arrays:
+    mean (M,3), logscale (M,3), quat (M,4), logit (M,), sh (M,48)."""
+    img = _f64(img)
+    C, H, W = img.shape
+    kp = np.ascontiguousarray(keypoints, np.float32)
+    M = kp.shape[0]
+    ref = _f64(ref_xyz)
+    out = {"mean": np.zeros((M, 3)), "logscale": np.zeros((M, 3)), "quat": np.zeros((M, 4)),
+           "logit": np.zeros(M), "sh": np.zeros((M, 48))}
+    rc = lib().orc_default_init(_p(img), W, H, _p(kp), M, _p(_f32(cam)), _p(ref), ref.shape[0], int(offset),
+                                _p(out["mean"]), _p(out["logscale"]), _p(out["quat"]), _p(out["logit"]), _p(out["sh"]))
+    assert rc == 0
+    return out
 
 
 def grad_to_planes(g60: np.ndarray):

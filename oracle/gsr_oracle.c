@@ -18,6 +18,9 @@
  *   - Sec. 3.3, Eq. 4  L = (1-lambda)|I_r - I_gt|_1 + lambda (1 - SSIM).
  *   - Sec. 3.4, Eq. 5  Gaussian pyramid levels GP^l(I_gt).
  *   - Sec. 4.1  lambda = 0.2, three pyramid levels.
+ *   - Sec. 3.3.1  new primitives at keypoints (their default initial shape
+ *               is a reading: 3-nearest-neighbour scale, identity rotation,
+ *               opacity 0.1, DC colour of the keypoint pixel).
  * Where the paper is silent the readings are the ones listed in the design
  * notes: EWA splat with 0.3 px dilation, 3-sigma pixel-square footprint,
  * alpha clamp 0.99, skip below 1/255, stop before T(1-alpha) < 1e-4, near
@@ -1096,4 +1099,79 @@ double orc_psnr(const double *img, const double *gt, int64_t count) {
     }
     double mse = se / (double)count;
     return 10.0 * log10(1.0 / mse);
+}
+
+/* Default initialisation of new primitives created at keypoints.  Photo-SLAM
+ * adds primitives at inactive ORB keypoints (Sec. 3.3.1, geometry-based
+ * densification) without stating their initial shape; the reading is the
+ * 3D-Gaussian-splatting convention:
+ *   mean      = R^T (d K^-1 [u v 1]^T - t)      (keypoint u, v at depth d)
+ *   log-scale = log sqrt(mean squared distance to the 3 nearest other map
+ *               points), the same on all three axes (mean squared distance
+ *               floored at 1e-7 m^2; 1e-4 m^2 when the map has no other point)
+ *   rotation  = identity, opacity logit = logit(0.1)
+ *   SH        = DC (I(p) - 0.5) / Y_00 at the keypoint's nearest pixel p of
+ *               the level-0 image, higher bands 0.
+ * kp: M x 5 floats (u, v, depth, log keypoint scale, angle); cam: R (9),
+ * t (3), fx, fy, cx, cy as floats; ref: the map's means (n_ref x 3 doubles),
+ * of which entries offset .. offset + M - 1 are the new primitives and are
+ * replaced by their back-projected means; each primitive's own entry is not
+ * its neighbour.  Outputs are M x 3, M x 3, M x 4, M, M x 48 (coefficient-
+ * major: 16 coefficients x RGB). */
+int orc_default_init(const double *img, int W, int H, const float *kp, int64_t M, const float *cam,
+                     const double *ref, int64_t n_ref, int64_t offset, double *mean, double *logscale, double *quat,
+                     double *logit, double *sh) {
+    if (M < 0 || n_ref < offset + M) return 1;
+    double R[9], t[3];
+    for (int k = 0; k < 9; ++k) R[k] = cam[k];
+    for (int k = 0; k < 3; ++k) t[k] = cam[9 + k];
+    const double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
+    for (int64_t m = 0; m < M; ++m) {
+        const double u = kp[5 * m], v = kp[5 * m + 1], d = kp[5 * m + 2];
+        const double pc[3] = {(u - cx) / fx * d - t[0], (v - cy) / fy * d - t[1], d - t[2]};
+        for (int r = 0; r < 3; ++r) mean[3 * m + r] = R[r] * pc[0] + R[3 + r] * pc[1] + R[6 + r] * pc[2];
+    }
+    const double y00 = 0.5 / sqrt(M_PI);
+    const double lg = log(0.1 / 0.9);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t m = 0; m < M; ++m) {
+        double best[3] = {INFINITY, INFINITY, INFINITY};
+        int found = 0;
+        for (int64_t j = 0; j < n_ref; ++j) {
+            if (j == offset + m) continue;
+            const double *q = (j >= offset && j < offset + M) ? mean + 3 * (j - offset) : ref + 3 * j;
+            const double dx = q[0] - mean[3 * m], dy = q[1] - mean[3 * m + 1], dz = q[2] - mean[3 * m + 2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            ++found;
+            if (d2 < best[2]) {
+                best[2] = d2;
+                if (best[2] < best[1]) { double s = best[1]; best[1] = best[2]; best[2] = s; }
+                if (best[1] < best[0]) { double s = best[0]; best[0] = best[1]; best[1] = s; }
+            }
+        }
+        const int k = found < 3 ? found : 3;
+        double msd = 1e-4;
+        if (k > 0) {
+            msd = 0;
+            for (int a = 0; a < k; ++a) msd += best[a];
+            msd /= k;
+            if (msd < 1e-7) msd = 1e-7;
+        }
+        const double ls = 0.5 * log(msd);
+        for (int a = 0; a < 3; ++a) logscale[3 * m + a] = ls;
+        quat[4 * m] = 1.0;
+        quat[4 * m + 1] = quat[4 * m + 2] = quat[4 * m + 3] = 0.0;
+        logit[m] = lg;
+        /* nearest pixel: round half up, clamped to the image */
+        const float uf = kp[5 * m], vf = kp[5 * m + 1];
+        int px = (int)floor((double)uf) + ((double)uf - floor((double)uf) >= 0.5);
+        int py = (int)floor((double)vf) + ((double)vf - floor((double)vf) >= 0.5);
+        px = px < 0 ? 0 : (px > W - 1 ? W - 1 : px);
+        py = py < 0 ? 0 : (py > H - 1 ? H - 1 : py);
+        for (int c = 0; c < 48; ++c) sh[48 * m + c] = 0.0;
+        for (int ch = 0; ch < 3; ++ch) sh[48 * m + ch] = (img[((int64_t)ch * H + py) * W + px] - 0.5) / y00;
+    }
+    return 0;
 }

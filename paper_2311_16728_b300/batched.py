@@ -19,7 +19,7 @@ from .raster import (LAMBDA_DSSIM, PYRAMID_LEVELS, Adam, AdamConfig, Gaussians, 
 
 class BatchedWindow:
     """views: every (keyframe, level) of `keyframes` = [(camera, level-0 gt)],
-    ordered level 0 first (largest images first balances the work queues)."""
+    coarsest level first; `views[v]` = (camera, gt, level, keyframe index)."""
 
     def __init__(self, params: Gaussians, keyframes: Sequence, levels: int = PYRAMID_LEVELS,
                  weights: Optional[Sequence[float]] = None, adam_cfg: AdamConfig = AdamConfig(),
@@ -31,7 +31,9 @@ class BatchedWindow:
         dev = params.mean_op.device
         pyr = [pyramid(gt.contiguous(), levels) for _, gt in keyframes]
         views = []
-        for l in range(levels):
+        # coarsest level first: its tiles carry the longest lists, and taking
+        # the longest work items first keeps the tail of each phase short
+        for l in reversed(range(levels)):
             for k, (cam, _) in enumerate(keyframes):
                 views.append((camera_at_level(camera_from(cam), l), pyr[k][l], l, k))
         self.views = views
@@ -112,6 +114,15 @@ class BatchedWindow:
                               ctypes.byref(self.tiling), self.bg, self.p_img, self.p_T, self.p_nc, self.p_gt,
                               self.p_dimg, self.weights, self.lam, _p(self.losses), ctypes.byref(g2), _p(self.iter_ws),
                               self.iter_ws.numel(), _p(self.status), _stream(stream))
+
+    def phase_ms(self):
+        """Phase split of the last persistent launch (ms): forward blend,
+        SSIM moments, dL/dI, and (entry to barrier 3) for the backward's start
+        (the backward's end is the launch's end, timed by the caller)."""
+        tail = self.iter_ws[self.iter_ws.numel() - 256 + 64:self.iter_ws.numel() - 256 + 96]
+        t = tail.view(torch.int64).cpu().tolist()
+        return {"fwd_blend": (t[1] - t[0]) * 1e-6, "ssim_moments": (t[2] - t[1]) * 1e-6,
+                "ssim_grad": (t[3] - t[2]) * 1e-6, "entry_to_bwd": (t[3] - t[0]) * 1e-6}
 
     def chain(self, stream=None):
         gs, pr, g2, gb = self.params.gaussians_struct(), self.proj(), self.grad2d(), self.grads.buffers_struct()

@@ -100,7 +100,7 @@ struct IterArgs {
     Win win;
     float *g0, *g1, *g2;
     float *partials, *losses;
-    unsigned *sync;  // [0..3] phase queues, [4] arrivals, [5] generation, [6] abort
+    unsigned *sync;  // [0..3] phase queues, [4] arrivals, [5] generation, [6] abort, [16..23] 4 u64 stamps
     int32_t *d_status;
     IterView view[kMaxViews];
 };
@@ -153,6 +153,17 @@ __device__ bool grid_barrier(unsigned *sync, unsigned nblocks, int32_t *status, 
     return *s_ok != 0;
 }
 
+// Block 0 records the global timer when it enters the kernel and when it
+// leaves each barrier (u64 words at byte 64 of the sync area): a cheap view
+// of the phase split of one launch, read back by the host on demand.
+__device__ __forceinline__ void phase_stamp(unsigned *sync, int k) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        reinterpret_cast<unsigned long long *>(sync + 16)[k] = t;
+    }
+}
+
 __device__ __forceinline__ RenderArgs view_args(const IterArgs &a, const IterView &v) {
     RenderArgs r;
     r.xy_conic = a.xy;
@@ -184,13 +195,14 @@ __device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
     return v;
 }
 
-__global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
+__global__ void __launch_bounds__(kIterThreads, 8) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
     extern __shared__ float4 smem4[];
     float *smf = reinterpret_cast<float *>(smem4);
     __shared__ int s_item, s_ok;
     __shared__ float s_red[32];
     __shared__ double s_dbl[2 * kIterThreads];
     const unsigned nb = gridDim.x;
+    phase_stamp(a.sync, 0);
     // ---- phase 1: forward blend of every (view, tile)
     for (int it = next_item(a.sync + 0, &s_item); it < a.tiles_total; it = next_item(a.sync + 0, &s_item)) {
         const int v = view_of_tile(a, it);
@@ -198,6 +210,7 @@ __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __g
         render_fwd_tile(view_args(a, w), it - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
+    phase_stamp(a.sync, 1);
     // ---- phase 2: SSIM moments of every (view, channel, 32 x 32 block)
     for (int it = next_item(a.sync + 1, &s_item); it < a.loss_items; it = next_item(a.sync + 1, &s_item)) {
         const int v = view_of_loss(a, it);
@@ -208,6 +221,7 @@ __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __g
                                        rem % w.lbx, rem / w.lbx, c, smf, s_red);
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
+    phase_stamp(a.sync, 2);
     // ---- phase 3: dL/dI of every view, scaled by its weight; per-view losses
     for (int it = next_item(a.sync + 2, &s_item); it < a.loss_items; it = next_item(a.sync + 2, &s_item)) {
         const int v = view_of_loss(a, it);
@@ -224,6 +238,7 @@ __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __g
         if (threadIdx.x == 0) a.losses[v] = L;
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
+    phase_stamp(a.sync, 3);
     // ---- phase 4: backward blend of every (view, tile)
     for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
         const int v = view_of_tile(a, it);

@@ -142,7 +142,7 @@ def test_window_matches_oracle_tiny():
         L_ref, dimg = oracle.loss(img, gt_l, 0.2)
         gv, _ = oracle.render_bwd(sc, ca, cl.width, cl.height, dec, dimg)
         gref += gv
-        L = float(bw.losses[lvl].item())
+        L = float(bw.losses[[v[2] for v in bw.views].index(lvl)].item())
         print(f"level {lvl}: loss {L:.7f} vs oracle {L_ref:.7f}")
         assert abs(L - L_ref) <= 1e-5 * L_ref
     _, _, norms = grad_report(grad_planes_gpu(bw.grads), gref)
