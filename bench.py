@@ -9,15 +9,18 @@ dataset itself is not available).  The path does not shard: with --gpus N
 every rank runs an independent replica (weak scaling, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode mapping|window|mlp]
+                  [--mode mapping|window|mlp|ttp]
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this path) on the host cores, on a bounded band of image rows per step.
 --mode window times the batched Gaussian-pyramid window (500k Gaussians,
 8 keyframes of 640 x 480 x 3 levels, one persistent launch per iteration,
 whole iteration in one CUDA graph); --mode mlp times the learned
-initialiser's tensor-core forward and training step at 2k and 20k rows.
-The default (mapping) line is the headline.
+initialiser's tensor-core forward and training step at 2k and 20k rows;
+--mode ttp runs the time-to-PSNR experiment (plain single-view path with
+default initialisation against the batched window with the learned
+initialiser, and with the default one).  The default (mapping) line is the
+headline.
 """
 from __future__ import annotations
 
@@ -405,6 +408,149 @@ def run_mlp(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- time to PSNR
+TTP_N = 200_000
+TTP_KF = 8
+TTP_NEW = 20_000         # at most this many new primitives per keyframe (all in-view centres, first keyframe first)
+TTP_BUDGET = 3000        # plain-path iterations fixing the target PSNR
+TTP_WINDOW_MAX = 1500    # window iterations at most
+TTP_TRAIN_SEEDS = (10, 11)
+TTP_HARVEST_ITERS = 400  # window iterations of the harvesting run
+TTP_MLP_STEPS = 6000
+
+
+def _ttp_setup(seed, gsr, torch):
+    """Scene `seed`, its keyframes (images rendered from the true map) and the
+    keypoints of the held-out primitives, with ORB-style angles."""
+    import synthetic as S
+    cams = [S.tum_camera(k * N_POSES // TTP_KF) for k in range(TTP_KF)]
+    truth, offsets, kps = S.densify_scene(S.room_scene(TTP_N, seed=seed), cams, TTP_NEW, seed=seed + 1)
+    g = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
+    vb = gsr.ViewBuffers(TTP_N, gsr.camera_from(cams[0]), gsr.tiling_struct(16, 16), 1024)
+    keyframes = []
+    for cam, kp in zip(cams, kps):
+        vb.cam = gsr.camera_from(cam)
+        gsr.ensure_capacity(vb, g)
+        vb.forward(g)
+        img = vb.img.clone()
+        host = img.cpu().numpy()
+        kp[:, 4] = [S.orb_angle(host, u, v) for u, v in kp[:, :2]]
+        keyframes.append((cam, img))
+    del vb
+    return truth, keyframes, [torch.tensor(k, device="cuda") for k in kps], offsets
+
+
+def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, every, gsr, torch):
+    """One arm: fresh map = truth with the held-out primitives initialised by
+    `init`; iterate until `target` PSNR (if given) or `budget` iterations.
+    Returns the PSNR curve [(iterations, training ms, PSNR)]."""
+    from paper_2311_16728_b300.batched import BatchedWindow
+    from paper_2311_16728_b300.mapping import Evaluator, PlainMapper, densify_default, densify_learned
+    params = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
+    if init == "learned":
+        densify_learned(li, params, keyframes, kps, offsets)
+    else:
+        densify_default(params, keyframes, kps, offsets)
+    ev = Evaluator(TTP_N, keyframes)
+    mapper = PlainMapper(params, keyframes) if kind == "plain" else BatchedWindow(params, keyframes)
+    mapper.capture()
+    curve = [(0, 0.0, ev(params))]
+    it, wall = 0, 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while it < budget and not (target is not None and curve[-1][2] >= target):
+        k = min(every, budget - it)
+        e0.record()
+        for _ in range(k):
+            mapper.step()
+        e1.record()
+        torch.cuda.synchronize()
+        it += k
+        wall += e0.elapsed_time(e1)
+        curve.append((it, wall, ev(params)))
+    status = mapper.status() if kind == "plain" else int(mapper.status.item())
+    if status != 0:
+        raise RuntimeError(f"{kind} arm: device status {status:#x}")
+    return curve
+
+
+def _first_at(curve, target):
+    for it, ms, ps in curve:
+        if ps >= target:
+            return it, ms
+    return None, None
+
+
+def run_ttp(args):
+    import torch
+    import paper_2311_16728_b300 as gsr
+    from paper_2311_16728_b300.batched import BatchedWindow
+    from paper_2311_16728_b300.learned_init import LearnedInit, init_weights
+    from paper_2311_16728_b300.mapping import densify_default, harvest, train_initialiser
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.time()
+    li = LearnedInit(init_weights(3), TTP_NEW, lr=1e-3)  # batches of up to one keyframe's new primitives
+    # ---- harvest (patch, converged parameter) pairs from window runs on training scenes
+    batches = []
+    for seed in TTP_TRAIN_SEEDS:
+        truth, keyframes, kps, offsets = _ttp_setup(seed, gsr, torch)
+        params = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
+        densify_default(params, keyframes, kps, offsets)
+        initial = gsr.Gaussians(*(t.clone() for t in params.tensors()), params.sh_degree)
+        bw = BatchedWindow(params, keyframes)
+        bw.capture()
+        for _ in range(TTP_HARVEST_ITERS):
+            bw.step()
+        torch.cuda.synchronize()
+        batches += harvest(li, params, initial, keyframes, kps, offsets)
+        del bw, params, initial
+    losses = train_initialiser(li, batches, TTP_MLP_STEPS)
+    t_train = time.time() - t0
+    # ---- held-out scenes: plain + default init fixes the target, then the window arms race to it
+    seeds = [int(x) for x in args.ttp_seeds.split(",") if x]
+    per_seed = []
+    for seed in seeds:
+        truth, keyframes, kps, offsets = _ttp_setup(seed, gsr, torch)
+        plain = _ttp_run("plain", truth, keyframes, kps, offsets, "default", li, TTP_BUDGET, None, 100, gsr, torch)
+        target = plain[-1][2]
+        res = {"seed": seed, "target_psnr": target, "plain": {"curve": plain},
+               "new": sum(int(k.shape[0]) for k in kps)}
+        res["plain"]["iters"], res["plain"]["ms"] = _first_at(plain, target)
+        for name, init in (("window_learned", "learned"), ("window_default", "default")):
+            c = _ttp_run("window", truth, keyframes, kps, offsets, init, li, TTP_WINDOW_MAX, target, 10, gsr, torch)
+            it, ms = _first_at(c, target)
+            res[name] = {"curve": c, "iters": it, "ms": ms, "psnr0": c[0][2]}
+        res["plain"]["psnr0"] = plain[0][2]
+        per_seed.append(res)
+    speed = [r["plain"]["ms"] / r["window_learned"]["ms"] for r in per_seed if r["window_learned"]["ms"]]
+    speed_def = [r["plain"]["ms"] / r["window_default"]["ms"] for r in per_seed if r["window_default"]["ms"]]
+    summary = [{"seed": r["seed"], "new_primitives": r["new"], "target_psnr": r["target_psnr"],
+                "plain_ms": r["plain"]["ms"], "plain_iters": r["plain"]["iters"],
+                "learned_window_ms": r["window_learned"]["ms"], "learned_window_iters": r["window_learned"]["iters"],
+                "default_window_ms": r["window_default"]["ms"], "default_window_iters": r["window_default"]["iters"],
+                "psnr0": {"default": r["plain"]["psnr0"], "learned": r["window_learned"]["psnr0"]}}
+               for r in per_seed]
+    line = {"metric": "time-to-PSNR speed-up, learned initialiser + batched window vs plain single-view path",
+            "value": statistics.mean(speed) if speed else None, "unit": "x (plain ms / learned+batched ms)",
+            "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; held-out scenes)",
+            "config": {"workload": f"{TTP_N} Gaussians in a 6x3x4 m room, {TTP_KF} keyframes 640x480 fx=fy=525, "
+                                   "every Gaussian whose centre a keyframe sees (at most "
+                                   f"{TTP_NEW} per keyframe) re-created at its keypoint (known depth, unknown shape, "
+                                   "opacity and colour); target = PSNR of the plain path (default init, sequential "
+                                   f"pyramid, tau_u 30) after {TTP_BUDGET} iterations; wall time = CUDA-event time "
+                                   "of the training iterations (evaluation excluded)",
+                       "train_seeds": list(TTP_TRAIN_SEEDS), "eval_seeds": seeds,
+                       "harvest": f"{TTP_HARVEST_ITERS} window iterations per training scene, "
+                                  f"{sum(b.M for b in batches)} pairs", "mlp_steps": TTP_MLP_STEPS,
+                       "mlp_loss_first_last": [losses[0], losses[-1]] if losses else None,
+                       "setup_s": round(t_train, 1)},
+            "speedup_default_window": statistics.mean(speed_def) if speed_def else None,
+            "per_seed": summary, "curves": {str(r["seed"]): {k: r[k]["curve"] for k in
+                                                            ("plain", "window_learned", "window_default")}
+                                           for r in per_seed}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,7 +559,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
     ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
-    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp"])
+    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp", "ttp"])
+    ap.add_argument("--ttp-seeds", default="100,101,102,103,104", help="ttp mode: held-out evaluation scenes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
     ap.add_argument("--profile", action="store_true",
@@ -430,6 +577,9 @@ def main():
         return
     if args.mode == "mlp":
         run_mlp(args)
+        return
+    if args.mode == "ttp":
+        run_ttp(args)
         return
 
     import torch

@@ -314,6 +314,29 @@ int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj,
                                    const gsr_param_buffers *grads, gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */
+/* Default initialisation of new primitives (Sec. 3.3.1)             */
+/* ---------------------------------------------------------------- */
+/* Photo-SLAM creates primitives at inactive ORB keypoints (geometry-based
+ * densification, Sec. 3.3.1) without stating their initial shape.  The
+ * default (3D Gaussian splatting's convention; the learned initialiser's
+ * fallback) writes Gaussians offset .. offset + M - 1 of the map (n Gaussians,
+ * planes of n entries):
+ *   mean      = R^T (d K^-1 [u v 1]^T - t) for keypoint m = keypoints[5 m ..]
+ *               = (u, v, d, log keypoint scale, angle) in camera `cam`
+ *   log-scale = log sqrt(mean squared distance to the 3 nearest other map
+ *               points) on all axes (floored at 1e-7 m^2; 1e-4 m^2 when the
+ *               map holds no other point; every map mean takes part)
+ *   rotation  = (1, 0, 0, 0), opacity logit = logit(0.1)
+ *   SH        = DC (I(p) - 0.5) / Y_00 at the keypoint's nearest pixel p
+ *               (half up, clamped) of img0 (planar 3 x H x W), others 0.
+ * Brute-force neighbour search (M x n distances).  Scratch from the caller:
+ * gsr_default_init_workspace_size. */
+int32_t gsr_default_init_workspace_size(int64_t M, int64_t n, size_t *bytes);
+int32_t gsr_default_init(const float *img0, int32_t W, int32_t H, const float *keypoints, int64_t M,
+                         const gsr_camera *cam, const gsr_param_buffers *map, int64_t n, int64_t offset,
+                         void *workspace, size_t workspace_bytes, gsr_stream_t stream);
+
+/* ---------------------------------------------------------------- */
 /* Learned initialiser (tensor-core MLP)                             */
 /* ---------------------------------------------------------------- */
 
@@ -391,15 +414,19 @@ int32_t gsr_mlp_gradients(void *workspace, int64_t Mpad, gsr_mlp_weights *grads)
 
 /* Training targets for keypoints whose primitive is known (gids[m]): log-scale
  * minus log(depth / fx), rotation in the camera frame (unit quaternion with
- * w >= 0), opacity logit, the 48 SH coefficients; columns 56..63 zero.  Rows
+ * w >= 0), opacity logit, the 48 SH coefficients; columns 56..63 zero.  With
+ * `base` (FP32 [Mpad x 64], may be NULL) the row minus base's row is written
+ * (the initialiser learns a correction of a base initialisation).  Rows
  * M .. Mpad - 1 are zeroed. */
 int32_t gsr_mlp_encode_targets(const gsr_gaussians *g, const uint32_t *gids, const float *keypoints, int64_t M,
-                               int64_t Mpad, const gsr_camera *cam, float *target, gsr_stream_t stream);
+                               int64_t Mpad, const gsr_camera *cam, const float *base, float *target,
+                               gsr_stream_t stream);
 
-/* Inverse of the encoding: writes Gaussians offset .. offset + M - 1 of a
- * store of n Gaussians, the mean back-projected from the keypoint at its
- * depth (R^T (depth K^-1 [u v 1] - t)). */
-int32_t gsr_mlp_decode(const float *y, const float *keypoints, int64_t M, const gsr_camera *cam,
+/* Inverse of the encoding applied to y + base (base may be NULL): writes
+ * Gaussians offset .. offset + M - 1 of a store of n Gaussians, the mean
+ * back-projected from the keypoint at its depth (R^T (depth K^-1 [u v 1] -
+ * t)). */
+int32_t gsr_mlp_decode(const float *y, const float *base, const float *keypoints, int64_t M, const gsr_camera *cam,
                        const gsr_param_buffers *out, int64_t n, int64_t offset, gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */

@@ -94,6 +94,9 @@ _SIGNATURES = {
                              c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "gsr_batched_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_int32, P(gsr_tiling), P(gsr_grad2d),
                                     P(gsr_param_buffers), c_void_p], c_int32),
+    "gsr_default_init_workspace_size": ([c_int64, c_int64, P(c_size_t)], c_int32),
+    "gsr_default_init": ([c_void_p, c_int32, c_int32, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64,
+                          c_int64, c_void_p, c_size_t, c_void_p], c_int32),
     "gsr_gemm_bf16": ([c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
                        c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int64,
                        c_int32, c_void_p, c_void_p], c_int32),
@@ -108,9 +111,9 @@ _SIGNATURES = {
                             c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "gsr_mlp_gradients": ([c_void_p, c_int64, P(gsr_mlp_weights)], c_int32),
     "gsr_mlp_encode_targets": ([P(gsr_gaussians), c_void_p, c_void_p, c_int64, c_int64, P(gsr_camera), c_void_p,
-                                c_void_p], c_int32),
-    "gsr_mlp_decode": ([c_void_p, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64, c_int64,
-                        c_void_p], c_int32),
+                                c_void_p, c_void_p], c_int32),
+    "gsr_mlp_decode": ([c_void_p, c_void_p, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64,
+                        c_int64, c_void_p], c_int32),
     "gsr_adam_step": ([P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers),
                        c_int64, P(gsr_adam_config), c_void_p, c_void_p], c_int32),
     "gsr_pyramid_down": ([c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p], c_int32),
@@ -174,6 +177,8 @@ gsr_batched_bin_sort = _wrap("gsr_batched_bin_sort")
 gsr_batched_iterate_workspace_size = _wrap("gsr_batched_iterate_workspace_size")
 gsr_batched_iterate = _wrap("gsr_batched_iterate")
 gsr_batched_preprocess_bwd = _wrap("gsr_batched_preprocess_bwd")
+gsr_default_init_workspace_size = _wrap("gsr_default_init_workspace_size")
+gsr_default_init = _wrap("gsr_default_init")
 gsr_gemm_bf16 = _wrap("gsr_gemm_bf16")
 gsr_mlp_workspace_size = _wrap("gsr_mlp_workspace_size")
 gsr_mlp_sync_weights = _wrap("gsr_mlp_sync_weights")

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(64) mlp_encode_kernel(const float4 *__restrict
                                                         const float4 *__restrict__ sh, int64_t n,
                                                         const uint32_t *__restrict__ gids,
                                                         const float *__restrict__ kp, int64_t M, CamMLP cam,
-                                                        float *__restrict__ target) {
+                                                        const float *__restrict__ base, float *__restrict__ target) {
     const int64_t m = blockIdx.x;
     const int j = threadIdx.x;
     float val = 0.0f;
@@ -319,20 +319,24 @@ __global__ void __launch_bounds__(64) mlp_encode_kernel(const float4 *__restrict
             val = (f & 3) == 0 ? s.x : ((f & 3) == 1 ? s.y : ((f & 3) == 2 ? s.z : s.w));
         }
     }
+    if (base && m < M && j < kOut) val -= base[m * kN3 + j];
     target[m * kN3 + j] = val;
 }
 
 // New Gaussian out_offset + m from row m: mean = back-projection of the
 // keypoint at its depth, parameters from the row (inverse of the encoding).
-__global__ void __launch_bounds__(64) mlp_decode_kernel(const float *__restrict__ y, const float *__restrict__ kp,
-                                                        int64_t M, CamMLP cam, float4 *__restrict__ mean_op,
-                                                        float4 *__restrict__ quat, float4 *__restrict__ logscale,
-                                                        float4 *__restrict__ sh, int64_t n, int64_t off) {
+__global__ void __launch_bounds__(64) mlp_decode_kernel(const float *__restrict__ y, const float *__restrict__ base,
+                                                        const float *__restrict__ kp, int64_t M, CamMLP cam,
+                                                        float4 *__restrict__ mean_op, float4 *__restrict__ quat,
+                                                        float4 *__restrict__ logscale, float4 *__restrict__ sh,
+                                                        int64_t n, int64_t off) {
+    __shared__ float row[kN3];
     const int64_t m = blockIdx.x;
     if (m >= M) return;
     const int64_t g = off + m;
-    const float *row = y + m * kN3;
     const int j = threadIdx.x;
+    row[j] = y[m * kN3 + j] + (base ? base[m * kN3 + j] : 0.0f);
+    __syncthreads();
     if (j == 0) {
         const float *k = kp + 5 * m;
         const float d = k[2];
@@ -569,8 +573,8 @@ extern "C" int32_t gsr_mlp_train_step(const gsr_mlp_weights *w, const gsr_mlp_we
 }
 
 extern "C" int32_t gsr_mlp_encode_targets(const gsr_gaussians *g, const uint32_t *gids, const float *keypoints,
-                                          int64_t M, int64_t Mpad, const gsr_camera *cam, float *target,
-                                          gsr_stream_t stream) {
+                                          int64_t M, int64_t Mpad, const gsr_camera *cam, const float *base,
+                                          float *target, gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_gaussians(g)) || (rc = validate_camera(cam))) return rc;
     if (M < 0 || Mpad < M || !target || (M > 0 && (!gids || !keypoints))) {
@@ -581,12 +585,13 @@ extern "C" int32_t gsr_mlp_encode_targets(const gsr_gaussians *g, const uint32_t
     mlp_encode_kernel<<<(unsigned)Mpad, kN3, 0, as_cuda(stream)>>>(
         reinterpret_cast<const float4 *>(g->mean_op), reinterpret_cast<const float4 *>(g->quat),
         reinterpret_cast<const float4 *>(g->logscale), reinterpret_cast<const float4 *>(g->sh), g->n, gids, keypoints,
-        M, cam_mlp(cam), target);
+        M, cam_mlp(cam), base, target);
     return check_launch("mlp_encode_kernel");
 }
 
-extern "C" int32_t gsr_mlp_decode(const float *y, const float *keypoints, int64_t M, const gsr_camera *cam,
-                                  const gsr_param_buffers *out, int64_t n, int64_t offset, gsr_stream_t stream) {
+extern "C" int32_t gsr_mlp_decode(const float *y, const float *base, const float *keypoints, int64_t M,
+                                  const gsr_camera *cam, const gsr_param_buffers *out, int64_t n, int64_t offset,
+                                  gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_camera(cam))) return rc;
     if (M < 0 || !out || !out->mean_op || !out->quat || !out->logscale || !out->sh || offset < 0 || offset + M > n ||
@@ -596,7 +601,7 @@ extern "C" int32_t gsr_mlp_decode(const float *y, const float *keypoints, int64_
     }
     if (M == 0) return GSR_OK;
     mlp_decode_kernel<<<(unsigned)M, 64, 0, as_cuda(stream)>>>(
-        y, keypoints, M, cam_mlp(cam), reinterpret_cast<float4 *>(out->mean_op), reinterpret_cast<float4 *>(out->quat),
+        y, base, keypoints, M, cam_mlp(cam), reinterpret_cast<float4 *>(out->mean_op), reinterpret_cast<float4 *>(out->quat),
         reinterpret_cast<float4 *>(out->logscale), reinterpret_cast<float4 *>(out->sh), n, offset);
     return check_launch("mlp_decode_kernel");
 }

@@ -66,6 +66,21 @@ class MLPWeights:
         L.gsr_mlp_sync_weights(ctypes.byref(s), _stream(stream))
 
 
+def default_init(map_params: Gaussians, img0: torch.Tensor, keypoints: torch.Tensor, cam, offset: int,
+                 stream=None):
+    """The fallback initialiser: writes Gaussians offset .. offset + M - 1 of
+    `map_params` from keypoints (M, 5) = (u, v, depth, log scale, angle) seen in
+    `cam` with level-0 image img0 (3, H, W)."""
+    M = keypoints.shape[0]
+    sz = ctypes.c_size_t()
+    L.gsr_default_init_workspace_size(M, map_params.n, ctypes.byref(sz))
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=img0.device)
+    c, o = camera_from(cam), map_params.buffers_struct()
+    _, H0, W0 = img0.shape
+    L.gsr_default_init(_p(img0.contiguous()), W0, H0, _p(keypoints.contiguous()), M, ctypes.byref(c), ctypes.byref(o),
+                       map_params.n, offset, _p(ws), ws.numel(), _stream(stream))
+
+
 class LearnedInit:
     def __init__(self, weights: dict, batch_capacity: int, lr: float = 1e-3, device="cuda"):
         self.w = MLPWeights(weights, device)
@@ -102,9 +117,14 @@ class LearnedInit:
                           _p(self.status), _stream(stream))
         return self.y
 
-    def train_step(self, target: torch.Tensor, M: int, stream=None):
+    def train_step(self, target: torch.Tensor, M: int, stream=None, x: torch.Tensor = None, xT: torch.Tensor = None):
+        """One training step on rows 0 .. M - 1 of x (default: the gather
+        buffers; any [Mpad, 2368] BF16 input with its transpose)."""
         w, m, v = self.w.struct(), self.m.struct(), self.v.struct()
-        L.gsr_mlp_train_step(ctypes.byref(w), ctypes.byref(m), ctypes.byref(v), _p(self.x), _p(self.xT),
+        x = self.x if x is None else x
+        xT = self.xT if xT is None else xT
+        assert x.shape == self.x.shape and xT.shape == self.xT.shape
+        L.gsr_mlp_train_step(ctypes.byref(w), ctypes.byref(m), ctypes.byref(v), _p(x), _p(xT),
                              _p(target), _p(self.out_weight), M, self.mpad, self.lr, 0.9, 0.999, 1e-8,
                              _p(self.step_count), _p(self.loss), _p(self.y), _p(self.ws), self.ws.numel(),
                              _p(self.status), _stream(stream))
@@ -124,12 +144,15 @@ class LearnedInit:
         return out
 
     def encode_targets(self, g: Gaussians, gids: torch.Tensor, keypoints: torch.Tensor, cam, target: torch.Tensor,
-                       stream=None):
+                       stream=None, base: torch.Tensor = None):
+        """Encoded parameters of Gaussians gids[m] (minus `base` rows if given)."""
         gs, c = g.gaussians_struct(), camera_from(cam)
         L.gsr_mlp_encode_targets(ctypes.byref(gs), _p(gids), _p(keypoints), keypoints.shape[0], self.mpad,
-                                 ctypes.byref(c), _p(target), _stream(stream))
+                                 ctypes.byref(c), _p(base), _p(target), _stream(stream))
 
-    def decode(self, keypoints: torch.Tensor, cam, out: Gaussians, offset: int, stream=None):
+    def decode(self, keypoints: torch.Tensor, cam, out: Gaussians, offset: int, stream=None,
+               base: torch.Tensor = None):
+        """Writes Gaussians offset .. offset + M - 1 from y (+ `base`)."""
         c, o = camera_from(cam), out.buffers_struct()
-        L.gsr_mlp_decode(_p(self.y), _p(keypoints), keypoints.shape[0], ctypes.byref(c), ctypes.byref(o), out.n,
-                         offset, _stream(stream))
+        L.gsr_mlp_decode(_p(self.y), _p(base), _p(keypoints), keypoints.shape[0], ctypes.byref(c), ctypes.byref(o),
+                         out.n, offset, _stream(stream))

@@ -317,13 +317,16 @@ class MappingStep:
     """
 
     def __init__(self, params: Gaussians, views, tiling: L.gsr_tiling = None, adam_cfg: AdamConfig = AdamConfig(),
-                 lam: float = LAMBDA_DSSIM, pair_capacity: Optional[int] = None, margin: float = 1.5):
+                 lam: float = LAMBDA_DSSIM, pair_capacity: Optional[int] = None, margin: float = 1.5,
+                 adam: Optional[Adam] = None, grads: Optional[Gaussians] = None):
+        """`adam` and `grads` may be shared with other steps over the same
+        parameters (e.g. one step per pyramid level)."""
         self.params = params
         self.tiling = tiling or tiling_struct(16, 16)
         self.views = [(camera_from(c), gt.contiguous()) for c, gt in views]
         self.lam = lam
-        self.grads = params.zeros_like()
-        self.adam = Adam(params, adam_cfg)
+        self.grads = grads if grads is not None else params.zeros_like()
+        self.adam = adam if adam is not None else Adam(params, adam_cfg)
         cam0 = self.views[0][0]
         self.vb = ViewBuffers(params.n, cam0, self.tiling, pair_capacity or 1024)
         if pair_capacity is None:
@@ -402,7 +405,10 @@ class MappingStep:
         """One iteration on the next view.  `events` (optional) is a list of
         len(STAGES) + 1 CUDA events recorded before the first and after every
         stage on the current stream."""
-        i = self.k % len(self.views)
+        self.step_view(self.k % len(self.views), events)
+
+    def step_view(self, i: int, events=None):
+        """One iteration on view i."""
         if events is not None:
             events[0].record()
         for si, name in enumerate(STAGES):

@@ -162,3 +162,69 @@ def random_grad_image(C: int, H: int, W: int, seed: int = 6) -> np.ndarray:
     """Seeded upstream gradient dL/dimage, N(0, 1) (float32, planar)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((C, H, W)).astype(np.float32)
+
+
+# ---------------------------------------------------------------- keypoints
+def project_points(xyz: np.ndarray, cam: Camera):
+    """(u, v, depth) of world points in `cam` (FP64)."""
+    pc = np.asarray(xyz, np.float64) @ np.asarray(cam.R, np.float64).T + np.asarray(cam.t, np.float64)
+    z = pc[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = cam.fx * pc[:, 0] / z + cam.cx
+        v = cam.fy * pc[:, 1] / z + cam.cy
+    return u, v, z
+
+
+def orb_angle(img: np.ndarray, u: float, v: float, half: int = 8) -> float:
+    """Orientation of a keypoint by the intensity centroid of the 16 x 16
+    luminance patch around it (the ORB definition): atan2(m01, m10)."""
+    C, H, W = img.shape
+    lum = 0.299 * img[0] + 0.587 * img[1] + 0.114 * img[2]
+    cx, cy = int(round(u)), int(round(v))
+    ys = np.clip(np.arange(cy - half, cy + half), 0, H - 1)
+    xs = np.clip(np.arange(cx - half, cx + half), 0, W - 1)
+    patch = lum[np.ix_(ys, xs)]
+    off = np.arange(-half, half) + 0.5
+    m10 = float((patch * off[None, :]).sum())
+    m01 = float((patch * off[:, None]).sum())
+    return float(np.arctan2(m01, m10))
+
+
+def held_out_keypoints(p: Params, cams, per_keyframe: int, seed: int = 5, margin: float = 8.0,
+                       min_depth: float = 0.5):
+    """Seeded held-out primitives for densification tests: for each keyframe in
+    turn, `per_keyframe` (None: all) not-yet-chosen Gaussians whose centre
+    projects inside the image (with a margin) in front of the camera.  Returns a list of
+    (indices, keypoints (M, 5) float32 without angles) per keyframe; the
+    keypoint is the exact projection of the centre, with its depth."""
+    rng = np.random.default_rng(seed)
+    taken = np.zeros(p.n, bool)
+    out = []
+    for cam in cams:
+        u, v, z = project_points(p.mean_op[:, :3], cam)
+        ok = (~taken) & (z > min_depth) & (u >= margin) & (u <= cam.width - 1 - margin) & (v >= margin) & \
+             (v <= cam.height - 1 - margin)
+        cand = np.flatnonzero(ok)
+        take = len(cand) if per_keyframe is None else min(per_keyframe, len(cand))
+        pick = np.sort(rng.choice(cand, size=take, replace=False))
+        taken[pick] = True
+        kp = np.stack([u[pick], v[pick], z[pick], np.zeros(len(pick)), np.zeros(len(pick))], 1).astype(np.float32)
+        out.append((pick, kp))
+    return out
+
+
+def densify_scene(p: Params, cams, per_keyframe: int, seed: int):
+    """The map layout of a densification experiment: `p` permuted so that the
+    held-out primitives of keyframe k (chosen by held_out_keypoints) occupy
+    slots offsets[k] .. offsets[k] + M_k - 1 at the end of the map.  Returns
+    (permuted params, offsets, keypoints per keyframe (M_k, 5) float32)."""
+    held = held_out_keypoints(p, cams, per_keyframe, seed=seed)
+    new = np.concatenate([h[0] for h in held]) if held else np.zeros(0, np.int64)
+    rest = np.setdiff1d(np.arange(p.n), new)
+    order = np.concatenate([rest, new]).astype(np.int64)
+    q = Params(p.mean_op[order].copy(), p.quat[order].copy(), p.logscale[order].copy(), p.sh[:, order].copy())
+    offsets, off = [], len(rest)
+    for idx, _ in held:
+        offsets.append(off)
+        off += len(idx)
+    return q, offsets, [h[1] for h in held]

@@ -137,3 +137,17 @@ def test_batched_arguments_are_rejected_on_the_host(gsr):
     rc = L.gsr_batched_preprocess.raw(ctypes.byref(g), cams65, 65, ctypes.byref(gsr.tiling_struct(16, 16)),
                                       ctypes.byref(proj), None)
     assert rc == L.GSR_ERR_INVALID_ARG
+
+
+def test_default_init_sizes_and_arguments(gsr):
+    L = gsr._lib
+    sz = ctypes.c_size_t()
+    for M, n in ((0, 5000), (1, 1), (700, 20000), (20000, 500000)):
+        assert L.gsr_default_init_workspace_size.raw(M, n, ctypes.byref(sz)) == L.GSR_OK
+        assert sz.value >= 12 * M
+    assert L.gsr_default_init_workspace_size.raw(-1, 10, ctypes.byref(sz)) == L.GSR_ERR_INVALID_ARG
+    cam = gsr.camera_struct(np.eye(3), np.zeros(3), 100, 100, 50, 40, 100, 80)
+    buf = L.gsr_param_buffers(16, 16, 16, 16)
+    # slots beyond the map
+    rc = L.gsr_default_init.raw(16, 100, 80, 16, 10, ctypes.byref(cam), ctypes.byref(buf), 5, 0, 16, 1 << 20, None)
+    assert rc == L.GSR_ERR_INVALID_ARG

@@ -158,3 +158,55 @@ def test_encode_decode_round_trip():
     q0 = p.quat / np.linalg.norm(p.quat, axis=1, keepdims=True)
     assert np.allclose(np.abs((q * q0).sum(1)), 1.0, atol=1e-5)  # same rotation up to sign
     np.testing.assert_allclose(out.sh[:, 10:74].cpu().numpy(), p.sh, atol=1e-6)
+
+
+def test_residual_encode_decode_round_trip():
+    """target = enc(g) - enc(h); decoding target + enc(h) gives g back."""
+    p, h = S.tiny_scene(64, seed=2), S.tiny_scene(64, seed=9)
+    h.mean_op[:, :3] = p.mean_op[:, :3]  # same centres (the keypoints), other shapes and colours
+    cam = S.tiny_camera()
+    g = gsr.Gaussians.from_arrays(p.mean_op, p.quat, p.logscale, p.sh)
+    gh = gsr.Gaussians.from_arrays(h.mean_op, h.quat, h.logscale, h.sh)
+    u, v, z = S.project_points(p.mean_op[:, :3], cam)
+    kpt = torch.tensor(np.stack([u, v, z, np.zeros(64), np.zeros(64)], 1).astype(np.float32), device="cuda")
+    li = LearnedInit(omlp.init_params(1), 64)
+    ids = torch.arange(64, dtype=torch.int32, device="cuda")
+    base = torch.zeros(li.mpad, omlp.N3, device="cuda")
+    res = torch.zeros(li.mpad, omlp.N3, device="cuda")
+    li.encode_targets(gh, ids, kpt, cam, base)
+    li.encode_targets(g, ids, kpt, cam, res, base=base)
+    li.y.copy_(res)
+    out = gsr.Gaussians.zeros(64)
+    li.decode(kpt, cam, out, 0, base=base)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.mean_op[:, 3].cpu().numpy(), p.mean_op[:, 3], atol=2e-6)
+    np.testing.assert_allclose(out.logscale[:, :3].cpu().numpy(), p.logscale[:, :3], atol=3e-5)
+    np.testing.assert_allclose(out.sh.cpu().numpy(), p.sh, atol=2e-6)
+    q = out.quat.cpu().numpy()
+    q0 = p.quat / np.linalg.norm(p.quat, axis=1, keepdims=True)
+    assert np.allclose(np.abs((q * q0).sum(1)), 1.0, atol=1e-5)
+
+
+def test_learned_init_with_zero_correction_is_the_default():
+    """A network whose last layer is zero predicts no correction: the learned
+    initialiser then writes the default initialisation."""
+    from paper_2311_16728_b300.learned_init import init_weights
+    from paper_2311_16728_b300.mapping import densify_default, densify_learned
+    p = S.room_scene(20000, seed=3)
+    cams = [S.tum_camera(4), S.tum_camera(20)]
+    q, offs, kps = S.densify_scene(p, cams, 500, seed=6)
+    w = init_weights(3)
+    w["W3"][:] = 0.0
+    w["b3"][:] = 0.0
+    li = LearnedInit(w, 500)
+    rng = np.random.default_rng(1)
+    keyframes = [(c, torch.tensor(rng.uniform(0, 1, (3, c.height, c.width)).astype(np.float32), device="cuda"))
+                 for c in cams]
+    kpt = [torch.tensor(k, device="cuda") for k in kps]
+    a = gsr.Gaussians.from_arrays(q.mean_op, q.quat, q.logscale, q.sh)
+    b = gsr.Gaussians.from_arrays(q.mean_op, q.quat, q.logscale, q.sh)
+    densify_default(a, keyframes, kpt, offs)
+    densify_learned(li, b, keyframes, kpt, offs)
+    torch.cuda.synchronize()
+    for x, y in zip(a.tensors(), b.tensors()):
+        torch.testing.assert_close(y, x, rtol=0, atol=5e-5)
