@@ -162,14 +162,13 @@ int32_t gsr_bin_sort_workspace_size(int64_t n, int64_t pair_capacity, const gsr_
  * threshold, so a dropped pair would never blend at any pixel and the image
  * is unchanged.  One (key, gid) pair is output per kept tile, key =
  * tile << 32 | bits(depth), sorted by key with equal keys in Gaussian order
- * (an in-house stable LSD radix sort: the visible Gaussians by depth first,
- * then the pairs by tile bits); tile_ranges[2 t], [2 t + 1] = [begin, end)
- * of tile t (empty tiles [0, 0)).  keys/vals hold pair_capacity entries; the
- * pair count is written to *d_num_pairs.  If it exceeds pair_capacity (or
- * the candidates exceed 2 x pair_capacity), the GSR_ERR_CAPACITY bit is set
- * in *d_status and *d_num_pairs holds a capacity that suffices for a retry
- * (the pair count, or the candidate count); outputs are then truncated but
- * nothing is written out of bounds. */
+ * (an in-house bucket sort by tile followed by a sort of each tile's segment
+ * on depth and index); tile_ranges[2 t], [2 t + 1] = [begin, end) of tile t
+ * (empty tiles [0, 0)).  keys/vals hold pair_capacity entries; the pair count
+ * is written to *d_num_pairs.  If it exceeds pair_capacity, the
+ * GSR_ERR_CAPACITY bit is set in *d_status, every range is empty and
+ * *d_num_pairs is the capacity a retry needs; nothing is written out of
+ * bounds.  A frame with 2^32 or more candidates sets GSR_ERR_UNSUPPORTED. */
 int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camera *cam, const gsr_tiling *tiling,
                      uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
                      int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,

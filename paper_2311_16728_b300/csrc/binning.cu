@@ -3,20 +3,23 @@
 // Gaussian's pixel box, ordered by the 64-bit key tile << 32 | bits(depth)
 // (ties by Gaussian index), plus per-tile [begin, end) ranges.
 //
-// The order is produced by an in-house stable LSD radix sort in two stages
-// that together sort the full 64-bit key:
-//   1. the ~10^5 visible Gaussians are sorted once by their 32 depth bits
-//      (4 passes of 8 bits over N_visible, not over the pairs);
-//   2. their box tiles are expanded in that depth order, culled (see
-//      tile_keep) and compacted, and the pairs are stably sorted by the tile
-//      bits only (ceil(log2 tiles) bits, one or two passes over the pairs).
-// Stable passes over the low 32 bits followed by stable passes over the high
-// bits are exactly an LSD sort of the 64-bit key; doing the low passes
-// before duplication sorts 10^5 items instead of 10^6.
-//
-// Counts are data dependent: every kernel reads them from device memory
-// (clamped to capacity) so the whole sequence has fixed launch shapes and can
-// be captured in a CUDA graph.
+// In-house bucket sort by tile, then a sort inside each tile:
+//   1. the visible records are compacted in index order;
+//   2. an exclusive scan of their box-tile counts numbers the candidates
+//      (record, box tile);
+//   3. expansion: one thread per candidate runs the tile cull (tile_keep); a
+//      kept pair is appended to an unordered list (one atomic per warp) and
+//      counted in its tile (an atomic on the tile's range word);
+//   4. one CTA scans the tile counts into [begin, end) ranges, seeds each
+//      tile's cursor, and lists the non-empty tiles by length class;
+//   5. scatter: every kept pair takes the next slot of its tile's segment;
+//   6. each segment is sorted on (depth bits << 32 | index) -- unique keys --
+//      in shared memory by a bitonic network (a stable LSD radix sort in
+//      global memory for the rare segment longer than shared memory), and
+//      written out as key = tile << 32 | depth bits, value = index.
+// The result is exactly the order of a stable sort of all pairs by the
+// 64-bit key.  Counts stay on the device (kernels read them back), so the
+// whole sequence has fixed launch shapes and can be captured in a CUDA graph.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -25,10 +28,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;  // Gaussians per thread in the scan / compaction / emit kernels
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 4;   // elements per thread per block tile (short per-block chains)
-constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadix = 256;     // bins of one pass (a pass uses at most 8 bits)
+constexpr int kRadix = 256;  // digits of one pass of the long-segment radix sort
 
 __device__ __forceinline__ int64_t clamp_count(const int64_t *d_count, int64_t cap) {
     const int64_t c = *d_count;
@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(kScanThreads) vis_count_kernel(const uint32_t 
     if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
 }
 
-// visible Gaussians in index order -> (depth bits, index), count -> *d_nvis
-__global__ void __launch_bounds__(kScanThreads) vis_compact_kernel(
-    const uint32_t *__restrict__ ntiles, const float4 *__restrict__ rgb_depth, int64_t n,
-    const uint32_t *__restrict__ block_sums, int64_t nblocks, uint32_t *__restrict__ dkey,
-    uint32_t *__restrict__ dval, int64_t *__restrict__ d_nvis) {
+// visible records in index order -> order[], count -> *d_nvis
+__global__ void __launch_bounds__(kScanThreads) vis_compact_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
+                                                                   const uint32_t *__restrict__ block_sums,
+                                                                   int64_t nblocks, uint32_t *__restrict__ order,
+                                                                   int64_t *__restrict__ d_nvis) {
     __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_red[16];
     int64_t total;
@@ -127,19 +127,14 @@ __global__ void __launch_bounds__(kScanThreads) vis_compact_kernel(
     int64_t pos = pre + (int64_t)(incl - s);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
-        if (vis[k]) {
-            dkey[pos] = __float_as_uint(__ldg(&rgb_depth[base + k].w));
-            dval[pos] = (uint32_t)(base + k);
-            ++pos;
-        }
+        if (vis[k]) order[pos++] = (uint32_t)(base + k);
 }
 
-// ---------------------------------------------------------------- pair expansion
-// Candidates are the (Gaussian, box tile) slots of the depth-ordered visible
-// list.  One thread per candidate runs the tile cull, so a few near-camera
-// Gaussians with thousands of box tiles spread over the whole GPU instead of
-// serialising in the warps that hold them; an ordered compaction of the kept
-// candidates then yields the pairs in depth order (row-major within a box).
+
+// ---------------------------------------------------------------- candidates
+// Candidates are the (record, box tile) slots of the visible list; one thread
+// per candidate runs the tile cull, so a few near-camera Gaussians with
+// thousands of box tiles spread over the whole GPU.
 __global__ void __launch_bounds__(kScanThreads) cand_count_kernel(const uint32_t *__restrict__ ntiles,
                                                                   const uint32_t *__restrict__ order,
                                                                   const int64_t *__restrict__ d_nvis, int64_t cap_n,
@@ -155,26 +150,23 @@ __global__ void __launch_bounds__(kScanThreads) cand_count_kernel(const uint32_t
     if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
 }
 
-// coff[i] = first candidate slot of item i; coff[nv] = *d_ncand = total.  If
-// the candidates exceed their capacity, the GSR_ERR_CAPACITY bit is set and
-// *d_num_pairs receives the candidate count (an upper bound on the pairs).
+// coff[i] = first candidate slot of visible item i; coff[nv] = total =
+// *d_ncand.  Candidate numbers are 32-bit: a frame with 2^32 or more
+// candidates sets GSR_ERR_UNSUPPORTED and expands nothing.
 __global__ void __launch_bounds__(kScanThreads) cand_offsets_kernel(
     const uint32_t *__restrict__ ntiles, const uint32_t *__restrict__ order, const int64_t *__restrict__ d_nvis,
-    int64_t cap_n, const uint32_t *__restrict__ block_sums, int64_t nblocks, int64_t cand_cap,
-    uint32_t *__restrict__ coff, int64_t *__restrict__ d_ncand, int64_t *__restrict__ d_num_pairs,
-    int32_t *__restrict__ d_status) {
+    int64_t cap_n, const uint32_t *__restrict__ block_sums, int64_t nblocks, uint32_t *__restrict__ coff,
+    int64_t *__restrict__ d_ncand, int32_t *__restrict__ d_status) {
     __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_red[16];
     int64_t total;
     const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
     const int64_t nv = clamp_count(d_nvis, cap_n);
+    const bool too_many = total > (int64_t)0xffffffffLL;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *d_ncand = total;
+        *d_ncand = too_many ? 0 : total;
         coff[nv] = (uint32_t)total;
-        if (total > cand_cap) {
-            *d_num_pairs = total;
-            raise_status(d_status, GSR_ERR_CAPACITY);
-        }
+        if (too_many) raise_status(d_status, GSR_ERR_UNSUPPORTED);
     }
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t cnt[kScanItems];
@@ -194,10 +186,6 @@ __global__ void __launch_bounds__(kScanThreads) cand_offsets_kernel(
         }
 }
 
-constexpr int kExpandThreads = 256;
-constexpr int kExpandItems = 4;
-constexpr int kExpandTile = kExpandThreads * kExpandItems;
-
 // largest i in [0, n) with a[i] <= x (a ascending, a[0] <= x), by one warp
 __device__ __forceinline__ int64_t warp_upper_index(const uint32_t *a, int64_t n, uint32_t x) {
     int64_t lo = 0, hi = n;  // answer in [lo, hi)
@@ -215,299 +203,342 @@ __device__ __forceinline__ int64_t warp_upper_index(const uint32_t *a, int64_t n
     return lo;
 }
 
+constexpr int kExpandThreads = 256;
+constexpr int kExpandItems = 4;
+constexpr int kExpandTile = kExpandThreads * kExpandItems;
+constexpr int kExpandGrid = 148 * 8;  // grid-stride over chunks of kExpandTile candidates
+
+// Kept pairs: kept_tile[p] = global tile, kept_sk[p] = depth bits << 32 |
+// record (p from one atomic per warp on *d_kept; pairs beyond `cap` are
+// counted but not stored), and counts[2 t] += 1 per kept pair of tile t.
 __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     const uint32_t *__restrict__ coff, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
-    const float4 *__restrict__ c_op_box, const int64_t *__restrict__ d_nvis, int64_t cap_n,
-    const int64_t *__restrict__ d_ncand, int64_t cand_cap, int tw, int th, const ViewTiles vt,
-    uint8_t *__restrict__ flag, uint32_t *__restrict__ ctile, uint32_t *__restrict__ cgid) {
+    const float4 *__restrict__ c_op_box, const float4 *__restrict__ rgb_depth, const int64_t *__restrict__ d_nvis,
+    int64_t cap_n, const int64_t *__restrict__ d_ncand, int tw, int th, const ViewTiles vt, uint32_t ntiles_total,
+    uint32_t *__restrict__ counts, uint32_t *__restrict__ kept_tile, uint64_t *__restrict__ kept_sk, int64_t cap,
+    unsigned long long *__restrict__ d_kept) {
     __shared__ uint32_t s_off[kExpandTile + 1];
     __shared__ int64_t s_i0;
     __shared__ int s_m;
-    const int64_t ncand = clamp_count(d_ncand, cand_cap);
+    const int64_t ncand = *d_ncand;
     const int64_t nv = clamp_count(d_nvis, cap_n);
-    const int64_t s0 = (int64_t)blockIdx.x * kExpandTile;
-    if (s0 >= ncand) return;
-    const int64_t s_last = (s0 + kExpandTile < ncand ? s0 + kExpandTile : ncand) - 1;
-    if (threadIdx.x < 32) {
-        const int64_t i0 = warp_upper_index(coff, nv, (uint32_t)s0);
-        const int64_t i1 = warp_upper_index(coff, nv, (uint32_t)s_last);
-        if (threadIdx.x == 0) {
-            s_i0 = i0;
-            s_m = (int)(i1 - i0 + 1);  // every item owns >= 1 slot, so m <= kExpandTile
-        }
-    }
-    __syncthreads();
-    const int64_t i0 = s_i0;
-    const int m = s_m;
-    for (int j = threadIdx.x; j <= m; j += kExpandThreads) s_off[j] = coff[i0 + j];
-    __syncthreads();
-#pragma unroll 1
-    for (int r = 0; r < kExpandItems; ++r) {
-        const int64_t slot = s0 + (int64_t)r * kExpandThreads + threadIdx.x;
-        if (slot >= ncand) break;
-        int lo = 0, hi = m;  // s_off[lo] <= slot < s_off[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= (uint32_t)slot) lo = mid;
-            else hi = mid;
-        }
-        const uint32_t gid = order[i0 + lo];
-        const int k = (int)((uint32_t)slot - s_off[lo]);
-        const Splat sp = load_splat(xy_conic, c_op_box, gid);
-        const int tx0 = sp.x0 / tw, ntx = sp.x1 / tw - tx0 + 1;
-        const int tx = tx0 + k % ntx, ty = sp.y0 / th + k / ntx;
-        flag[slot] = tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1)
-                         ? 1
-                         : 0;
-        const int v = (int)((int64_t)gid / vt.n_per_view);  // view of this record
-        ctile[slot] = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
-        cgid[slot] = gid;
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) kept_count_kernel(const uint8_t *__restrict__ flag,
-                                                                  const int64_t *__restrict__ d_ncand,
-                                                                  int64_t cand_cap,
-                                                                  uint32_t *__restrict__ block_sums) {
-    __shared__ uint32_t s_warp[8];
-    const int64_t nc = clamp_count(d_ncand, cand_cap);
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < nc) s += flag[base + k];
-    s = block_incl_scan_256(s, s_warp);
-    if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(kScanThreads) kept_compact_kernel(
-    const uint8_t *__restrict__ flag, const uint32_t *__restrict__ ctile, const uint32_t *__restrict__ cgid,
-    const int64_t *__restrict__ d_ncand, int64_t cand_cap, const uint32_t *__restrict__ block_sums,
-    int64_t nblocks, int64_t cap, uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
-    int64_t *__restrict__ d_num_pairs, int64_t *__restrict__ d_written, int32_t *__restrict__ d_status) {
-    __shared__ uint32_t s_warp[8];
-    __shared__ int64_t s_red[16];
-    int64_t total;
-    const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
-    const int64_t nc_raw = *d_ncand;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // pairs actually present for the sort, whatever overflowed upstream
-        *d_written = total < cap ? total : cap;
-        if (nc_raw <= cand_cap) {
-            *d_num_pairs = total;
-            if (total > cap) raise_status(d_status, GSR_ERR_CAPACITY);
-        }
-    }
-    const int64_t nc = nc_raw < cand_cap ? nc_raw : cand_cap;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t s = 0;
-    uint8_t f[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        f[k] = base + k < nc ? flag[base + k] : 0;
-        s += f[k];
-    }
-    const uint32_t incl = block_incl_scan_256(s, s_warp);
-    int64_t pos = pre + (int64_t)(incl - s);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (f[k]) {
-            if (pos < cap) {
-                tkey[pos] = ctile[base + k];
-                tval[pos] = cgid[base + k];
+    const int lane = threadIdx.x & 31;
+    for (int64_t s0 = (int64_t)blockIdx.x * kExpandTile; s0 < ncand; s0 += (int64_t)gridDim.x * kExpandTile) {
+        const int64_t s_last = (s0 + kExpandTile < ncand ? s0 + kExpandTile : ncand) - 1;
+        __syncthreads();  // the previous chunk is done with s_off
+        if (threadIdx.x < 32) {
+            const int64_t i0 = warp_upper_index(coff, nv, (uint32_t)s0);
+            const int64_t i1 = warp_upper_index(coff, nv, (uint32_t)s_last);
+            if (threadIdx.x == 0) {
+                s_i0 = i0;
+                s_m = (int)(i1 - i0 + 1);  // every visible item owns >= 1 slot, so m <= kExpandTile
             }
-            ++pos;
         }
-}
-
-// ---------------------------------------------------------------- radix sort passes
-// One stable pass on u32 keys (digit = (key >> shift) & mask, <= 8 bits) with
-// u32 values: per-block digit histogram, per-digit scan over blocks, scatter
-// (warp match_any ranks, warps in order).
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys,
-                                                                  const int64_t *__restrict__ d_count, int64_t cap,
-                                                                  int shift, uint32_t mask, int nblocks,
-                                                                  uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_hist[kRadix];
-    s_hist[threadIdx.x] = 0u;
-    __syncthreads();
-    const int64_t count = clamp_count(d_count, cap);
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const uint32_t lane_lt = (1u << (threadIdx.x & 31)) - 1u;
-#pragma unroll 4
-    for (int k = 0; k < kSortItems; ++k) {
-        const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
-        const bool valid = idx < count;
-        const uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lane_lt) == 0u) atomicAdd(&s_hist[d], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
-}
-
-// grid = 256 blocks (one per digit): exclusive scan over blocks, digit total
-__global__ void __launch_bounds__(256) radix_digit_scan_kernel(uint32_t *__restrict__ hist, int nblocks,
-                                                               uint32_t *__restrict__ digit_total) {
-    __shared__ uint32_t s_warp[8];
-    uint32_t *row = hist + (int64_t)blockIdx.x * nblocks;
-    const int per = (nblocks + 255) / 256;
-    const int b0 = threadIdx.x * per;
-    uint32_t s = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nblocks) s += row[b0 + k];
-    const uint32_t incl = block_incl_scan_256(s, s_warp);
-    uint32_t run = incl - s;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nblocks) {
-            const uint32_t v = row[b0 + k];
-            row[b0 + k] = run;
-            run += v;
-        }
-    if (threadIdx.x == 255) digit_total[blockIdx.x] = incl;
-}
-
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
-    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
-    uint32_t *__restrict__ vals_out, const int64_t *__restrict__ d_count, int64_t cap, int shift, uint32_t mask,
-    int nblocks, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ digit_total) {
-    constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t s_base[kRadix];            // running output position per digit
-    __shared__ uint32_t s_wcount[kWarps][kRadix];  // per-warp digit counts of one sub-tile
-    __shared__ uint32_t s_warp[8];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int64_t count = clamp_count(d_count, cap);
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    if (base >= count) return;
-    {
-        const uint32_t tot = digit_total[t];
-        const uint32_t incl = block_incl_scan_256(tot, s_warp);
-        s_base[t] = (incl - tot) + hist[(int64_t)t * nblocks + blockIdx.x];
-    }
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s_wcount[w][t] = 0u;
-    __syncthreads();
-    const uint32_t lt_mask = (1u << lane) - 1u;
+        __syncthreads();
+        const int64_t i0 = s_i0;
+        const int m = s_m;
+        for (int j = threadIdx.x; j <= m; j += kExpandThreads) s_off[j] = coff[i0 + j];
+        __syncthreads();
 #pragma unroll 1
-    for (int k = 0; k < kSortItems; ++k) {
-        if (base + (int64_t)k * kSortThreads >= count) break;  // block-uniform
-        const int64_t idx = base + (int64_t)k * kSortThreads + t;
-        const bool valid = idx < count;
-        uint32_t key = 0, val = 0, d = kRadix;  // sentinel digit for the tail
-        if (valid) {
-            key = keys_in[idx];
-            val = vals_in[idx];
-            d = (key >> shift) & mask;
+        for (int r = 0; r < kExpandItems; ++r) {
+            // every lane runs every round: the ballot below needs the whole warp
+            const int64_t slot = s0 + (int64_t)r * kExpandThreads + threadIdx.x;
+            bool keep = false;
+            uint32_t tile = 0, gid = 0;
+            if (slot < ncand) {
+                int lo = 0, hi = m;  // s_off[lo] <= slot < s_off[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= (uint32_t)slot) lo = mid;
+                    else hi = mid;
+                }
+                gid = order[i0 + lo];
+                const int k = (int)((uint32_t)slot - s_off[lo]);
+                const Splat sp = load_splat(xy_conic, c_op_box, gid);
+                const int tx0 = sp.x0 / tw, ntx = sp.x1 / tw - tx0 + 1;
+                const int tx = tx0 + k % ntx, ty = sp.y0 / th + k / ntx;
+                const int v = (int)((int64_t)gid / vt.n_per_view);  // view of this record
+                tile = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
+                keep = tile < ntiles_total &&
+                       tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1);
+            }
+            const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
+            if (ballot == 0u) continue;  // warp-uniform
+            const int leader = __ffs(ballot) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(d_kept, (unsigned long long)__popc(ballot));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (keep) {
+                const unsigned long long pos = base + (unsigned long long)__popc(ballot & ((1u << lane) - 1u));
+                if (pos < (unsigned long long)cap) {
+                    kept_tile[pos] = tile;
+                    kept_sk[pos] = ((uint64_t)__float_as_uint(__ldg(&rgb_depth[gid].w)) << 32) | gid;
+                }
+                atomicAdd(&counts[2 * (size_t)tile], 1u);
+            }
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) s_wcount[wid][d] = __popc(peers);
-        __syncthreads();
-        uint32_t run = s_base[t];
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = s_wcount[w][t];
-            s_wcount[w][t] = run;
-            run += c;
-        }
-        s_base[t] = run;
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_wcount[wid][d] + rank;
-            keys_out[pos] = key;
-            vals_out[pos] = val;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s_wcount[w][t] = 0u;
-        __syncthreads();
     }
 }
 
-// ---------------------------------------------------------------- ranges + 64-bit keys
-__global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *__restrict__ tkey,
-                                                       const uint32_t *__restrict__ vals,
-                                                       const float4 *__restrict__ rgb_depth,
-                                                       const int64_t *__restrict__ d_count, int64_t cap,
-                                                       uint32_t ntiles_total, uint64_t *__restrict__ keys,
-                                                       uint2 *__restrict__ ranges) {
-    const int64_t count = clamp_count(d_count, cap);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const uint32_t tile = tkey[i];
-    if (tile >= ntiles_total) return;  // cannot happen for emitted pairs; keeps every write in bounds
-    keys[i] = ((uint64_t)tile << 32) | __float_as_uint(__ldg(&rgb_depth[vals[i]].w));
-    if (i == 0 || tkey[i - 1] != tile) ranges[tile].x = (uint32_t)i;
-    if (i == count - 1 || tkey[i + 1] != tile) ranges[tile].y = (uint32_t)(i + 1);
+// ---------------------------------------------------------------- tile scan
+constexpr int kTileScanThreads = 1024;
+constexpr uint32_t kSmallTile = 1024;    // longest segment of the small-tile sort
+constexpr uint32_t kLargeTile = 16384;   // longest segment sorted in shared memory
+
+__device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t add = wid > 0 ? s_warp[wid - 1] : 0u;
+    __syncthreads();
+    return v + add;
+}
+
+// One CTA.  ranges[2 t] holds tile t's pair count on entry; on exit
+// ranges[2 t] = begin and ranges[2 t + 1] = begin (the scatter cursor, which
+// ends at the segment's end), or [0, 0) for an empty tile.  Non-empty tiles
+// are listed for the sort: length <= kSmallTile from the front of `list`,
+// longer ones from its back.  On pair overflow every range is empty.
+__global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
+    uint32_t *__restrict__ ranges, uint32_t T, const unsigned long long *__restrict__ d_kept, int64_t cap,
+    uint32_t *__restrict__ list, uint32_t *__restrict__ list_counts, int64_t *__restrict__ d_written,
+    int64_t *__restrict__ d_num_pairs, int32_t *__restrict__ d_status) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_small, s_large;
+    const unsigned long long K = *d_kept;
+    const bool overflow = K > (unsigned long long)cap;
+    if (threadIdx.x == 0) {
+        s_small = 0u;
+        s_large = 0u;
+        *d_num_pairs = (int64_t)K;
+        *d_written = overflow ? 0 : (int64_t)K;
+        if (overflow) raise_status(d_status, GSR_ERR_CAPACITY);
+    }
+    __syncthreads();
+    const uint32_t per = (T + kTileScanThreads - 1) / kTileScanThreads;
+    const uint32_t t0 = threadIdx.x * per, t1 = min(T, t0 + per);
+    uint32_t sum = 0;
+    if (!overflow)
+        for (uint32_t t = t0; t < t1; ++t) sum += ranges[2 * (size_t)t];
+    const uint32_t incl = block_incl_scan_1024(sum, s_warp);
+    uint32_t off = incl - sum;
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t c = overflow ? 0u : ranges[2 * (size_t)t];
+        if (c == 0u) {
+            ranges[2 * (size_t)t] = 0u;
+            ranges[2 * (size_t)t + 1] = 0u;
+            continue;
+        }
+        ranges[2 * (size_t)t] = off;
+        ranges[2 * (size_t)t + 1] = off;
+        if (c <= kSmallTile) list[atomicAdd(&s_small, 1u)] = t;
+        else list[(size_t)cap - 1 - atomicAdd(&s_large, 1u)] = t;
+        off += c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        list_counts[0] = s_small;
+        list_counts[1] = s_large;
+    }
+}
+
+// every stored kept pair takes the next slot of its tile's segment
+__global__ void __launch_bounds__(256) scatter_kernel(const uint32_t *__restrict__ kept_tile,
+                                                      const uint64_t *__restrict__ kept_sk,
+                                                      const int64_t *__restrict__ d_written, int64_t cap,
+                                                      uint32_t *__restrict__ ranges, uint64_t *__restrict__ seg) {
+    const int64_t w = *d_written;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < w; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pos = atomicAdd(&ranges[2 * (size_t)kept_tile[i] + 1], 1u);
+        if (pos < (uint64_t)cap) seg[pos] = kept_sk[i];
+    }
+}
+
+// ---------------------------------------------------------------- per-tile sort
+// Ascending bitonic network over s[0, P) (P a power of two) by NT threads.
+template <int NT>
+__device__ __forceinline__ void bitonic_sort(uint64_t *s, uint32_t P) {
+    for (uint32_t k = 2; k <= P; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P / 2; i += NT) {
+                const uint32_t a = 2 * j * (i / j) + (i % j), b = a + j;
+                const uint64_t x = s[a], y = s[b];
+                const bool up = (a & k) == 0;
+                if ((x > y) == up) {
+                    s[a] = y;
+                    s[b] = x;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// sorted (depth << 32 | index) of tile t -> keys (tile << 32 | depth), vals
+template <int NT>
+__device__ __forceinline__ void emit_sorted(const uint64_t *s, uint32_t L, uint32_t tile, uint32_t begin,
+                                            uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (uint32_t i = threadIdx.x; i < L; i += NT) {
+        const uint64_t v = s[i];
+        keys[begin + i] = ((uint64_t)tile << 32) | (v >> 32);
+        vals[begin + i] = (uint32_t)v;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void smem_tile_sort(const uint64_t *__restrict__ seg, uint32_t tile, uint32_t begin,
+                                               uint32_t L, uint64_t *s, uint64_t *__restrict__ keys,
+                                               uint32_t *__restrict__ vals) {
+    uint32_t P = 1;
+    while (P < L) P <<= 1;
+    for (uint32_t i = threadIdx.x; i < P; i += NT) s[i] = i < L ? seg[begin + i] : ~0ull;
+    __syncthreads();
+    bitonic_sort<NT>(s, P);
+    emit_sorted<NT>(s, L, tile, begin, keys, vals);
+    __syncthreads();
+}
+
+constexpr int kSmallSortThreads = 256;
+constexpr int kLargeSortThreads = 1024;
+constexpr int kSortGrid = 148 * 8;
+
+__global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uint32_t *__restrict__ list,
+                                                                       const uint32_t *__restrict__ list_counts,
+                                                                       const uint32_t *__restrict__ ranges,
+                                                                       const uint64_t *__restrict__ seg,
+                                                                       uint64_t *__restrict__ keys,
+                                                                       uint32_t *__restrict__ vals) {
+    __shared__ uint64_t s[kSmallTile];
+    const uint32_t cnt = list_counts[0];
+    for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+        const uint32_t t = list[e];
+        const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
+        smem_tile_sort<kSmallSortThreads>(seg, t, b, L, s, keys, vals);
+    }
+}
+
+// Stable LSD radix sort of a[0, L) (64-bit keys, 8 passes of 8 bits) through
+// b[0, L), by one CTA of NT threads; the result ends in a.  Shared memory:
+// kRadix digit bases + (NT / 32) x kRadix per-warp counts.
+template <int NT>
+__device__ void cta_radix_sort64(uint64_t *a, uint64_t *b, uint32_t L, uint32_t *s_base, uint32_t *s_wcount,
+                                 uint32_t *s_warp) {
+    constexpr int kWarps = NT / 32;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        for (int d = t; d < kRadix; d += NT) s_base[d] = 0u;
+        __syncthreads();
+        for (uint32_t i = t; i < L; i += NT) atomicAdd(&s_base[(a[i] >> shift) & 0xffu], 1u);
+        __syncthreads();
+        if (t == 0) {  // exclusive scan of 256 digit counts (once per pass)
+            uint32_t run = 0;
+            for (int d = 0; d < kRadix; ++d) {
+                const uint32_t c = s_base[d];
+                s_base[d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (uint32_t c0 = 0; c0 < L; c0 += NT) {
+            for (int k = t; k < kWarps * kRadix; k += NT) s_wcount[k] = 0u;
+            __syncthreads();
+            const uint32_t i = c0 + t;
+            const bool valid = i < L;
+            const uint64_t key = valid ? a[i] : 0ull;
+            const uint32_t d = valid ? (uint32_t)((key >> shift) & 0xffu) : (uint32_t)kRadix;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t rank = __popc(peers & lt);
+            if (valid && rank == 0) s_wcount[wid * kRadix + d] = __popc(peers);
+            __syncthreads();
+            for (int dd = t; dd < kRadix; dd += NT) {  // per-warp offsets within the chunk, warps in order
+                uint32_t run = s_base[dd];
+                for (int w = 0; w < kWarps; ++w) {
+                    const uint32_t c = s_wcount[w * kRadix + dd];
+                    s_wcount[w * kRadix + dd] = run;
+                    run += c;
+                }
+                s_base[dd] = run;
+            }
+            __syncthreads();
+            if (valid) b[s_wcount[wid * kRadix + d] + rank] = key;
+            __syncthreads();
+        }
+        uint64_t *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    (void)s_warp;
+}
+
+// Segments longer than kSmallTile: in shared memory up to kLargeTile, else
+// the radix sort in global memory with `spare` (the kept-pair list, free by
+// now, indexed like the segments) as the second buffer.
+__global__ void __launch_bounds__(kLargeSortThreads) sort_large_kernel(const uint32_t *__restrict__ list,
+                                                                       const uint32_t *__restrict__ list_counts,
+                                                                       int64_t cap,
+                                                                       const uint32_t *__restrict__ ranges,
+                                                                       uint64_t *__restrict__ seg,
+                                                                       uint64_t *__restrict__ spare,
+                                                                       uint64_t *__restrict__ keys,
+                                                                       uint32_t *__restrict__ vals) {
+    extern __shared__ uint64_t s_big[];  // kLargeTile entries
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t cnt = list_counts[1];
+    for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+        const uint32_t t = list[(size_t)cap - 1 - e];
+        const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
+        if (L <= kLargeTile) {
+            smem_tile_sort<kLargeSortThreads>(seg, t, b, L, s_big, keys, vals);
+        } else {
+            // s_big serves as the per-warp digit counts (32 x 256 words)
+            cta_radix_sort64<kLargeSortThreads>(seg + b, spare + b, L, s_base,
+                                                reinterpret_cast<uint32_t *>(s_big), s_warp);
+            emit_sorted<kLargeSortThreads>(seg + b, L, t, b, keys, vals);  // 8 passes end in seg
+            __syncthreads();
+        }
+    }
 }
 
 // ---------------------------------------------------------------- host side
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SortLayout {
-    size_t block_sums, dkey, dval, dkey2, dval2, nvis, tkey, tkey2, tval2, hist, digit_total;
-    size_t coff, ncand, written, flag, ctile, cgid, cblock_sums, total;
-    int64_t scan_blocks, nsort_blocks, psort_blocks, cand_cap, cand_blocks, expand_blocks;
+    size_t order, block_sums, coff, counters, kept_tile, kept_sk, seg, list, total;
+    int64_t scan_blocks;
 };
 
-// Candidates (box tiles before the cull) get twice the pair capacity.
 static SortLayout sort_layout(int64_t n, int64_t cap) {
     SortLayout L;
     const int64_t n1 = n > 0 ? n : 1, c1 = cap > 0 ? cap : 1;
-    L.cand_cap = 2 * c1 > 1024 ? 2 * c1 : 1024;
     L.scan_blocks = (n1 + kScanTile - 1) / kScanTile;
-    L.nsort_blocks = (n1 + kSortTile - 1) / kSortTile;
-    L.psort_blocks = (c1 + kSortTile - 1) / kSortTile;
-    L.cand_blocks = (L.cand_cap + kScanTile - 1) / kScanTile;
-    L.expand_blocks = (L.cand_cap + kExpandTile - 1) / kExpandTile;
-    const int64_t hist_blocks = L.nsort_blocks > L.psort_blocks ? L.nsort_blocks : L.psort_blocks;
     size_t off = 0;
-    L.coff = off; off += align256(sizeof(uint32_t) * (size_t)(n1 + 1));
-    L.ncand = off; off += align256(sizeof(int64_t));
-    L.written = off; off += align256(sizeof(int64_t));
-    L.flag = off; off += align256(sizeof(uint8_t) * (size_t)L.cand_cap);
-    L.ctile = off; off += align256(sizeof(uint32_t) * (size_t)L.cand_cap);
-    L.cgid = off; off += align256(sizeof(uint32_t) * (size_t)L.cand_cap);
-    L.cblock_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.cand_blocks);
+    L.order = off; off += align256(sizeof(uint32_t) * (size_t)n1);
     L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
-    L.dkey = off; off += align256(sizeof(uint32_t) * (size_t)n1);
-    L.dval = off; off += align256(sizeof(uint32_t) * (size_t)n1);
-    L.dkey2 = off; off += align256(sizeof(uint32_t) * (size_t)n1);
-    L.dval2 = off; off += align256(sizeof(uint32_t) * (size_t)n1);
-    L.nvis = off; off += align256(sizeof(int64_t));
-    L.tkey = off; off += align256(sizeof(uint32_t) * (size_t)c1);
-    L.tkey2 = off; off += align256(sizeof(uint32_t) * (size_t)c1);
-    L.tval2 = off; off += align256(sizeof(uint32_t) * (size_t)c1);
-    L.hist = off; off += align256(sizeof(uint32_t) * kRadix * (size_t)hist_blocks);
-    L.digit_total = off; off += align256(sizeof(uint32_t) * kRadix);
+    L.coff = off; off += align256(sizeof(uint32_t) * (size_t)(n1 + 1));
+    L.counters = off; off += 256;  // nvis, ncand, kept, written (int64) + 2 list counts (u32)
+    L.kept_tile = off; off += align256(sizeof(uint32_t) * (size_t)c1);
+    L.kept_sk = off; off += align256(sizeof(uint64_t) * (size_t)c1);
+    L.seg = off; off += align256(sizeof(uint64_t) * (size_t)c1);
+    L.list = off; off += align256(sizeof(uint32_t) * (size_t)c1);
     L.total = off;
     return L;
-}
-
-static int ceil_log2(int64_t x) {
-    int b = 0;
-    while ((int64_t(1) << b) < x) ++b;
-    return b;
-}
-
-// Stable LSD passes over `bits` bits starting at `shift0`: `passes` passes
-// of ceil(bits / passes) bits.  Data start in (k, v); after an odd number of
-// passes they end in (k2, v2), after an even number back in (k, v).
-static void radix_passes(uint32_t *k, uint32_t *v, uint32_t *k2, uint32_t *v2, const int64_t *d_count, int64_t cap,
-                         int shift0, int bits, int passes, uint32_t *hist, uint32_t *digit_total, int nblocks,
-                         cudaStream_t st) {
-    const int per = passes > 0 ? (bits + passes - 1) / passes : 0;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = shift0 + p * per;
-        const int b = (shift0 + bits - shift) < per ? (shift0 + bits - shift) : per;
-        const uint32_t mask = (1u << b) - 1u;
-        radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(k, d_count, cap, shift, mask, nblocks, hist);
-        radix_digit_scan_kernel<<<kRadix, 256, 0, st>>>(hist, nblocks, digit_total);
-        radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(k, v, k2, v2, d_count, cap, shift, mask, nblocks, hist,
-                                                               digit_total);
-        uint32_t *t = k; k = k2; k2 = t;
-        t = v; v = v2; v2 = t;
-    }
 }
 
 }  // namespace gsr
@@ -538,8 +569,8 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
         set_error("gsr_bin_sort: NULL pointer or negative size");
         return GSR_ERR_INVALID_ARG;
     }
-    if (n > 0xffffffffLL || pair_capacity > 0xffffffffLL) {
-        set_error("gsr_bin_sort: n and pair_capacity must fit in 32 bits");
+    if (n > 0xffffffffLL || pair_capacity > 0xffffffffLL || tiles > 0xffffffffLL) {
+        set_error("gsr_bin_sort: n, pair_capacity and the tile count must fit in 32 bits");
         return GSR_ERR_UNSUPPORTED;
     }
     const SortLayout L = sort_layout(n, pair_capacity);
@@ -549,11 +580,6 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     }
     cudaStream_t st = as_cuda(stream);
     char *ws = static_cast<char *>(workspace);
-    auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(ws + off); };
-    uint32_t *block_sums = u32(L.block_sums), *hist = u32(L.hist), *digit_total = u32(L.digit_total);
-    uint32_t *dkey = u32(L.dkey), *dval = u32(L.dval), *dkey2 = u32(L.dkey2), *dval2 = u32(L.dval2);
-    uint32_t *tkey = u32(L.tkey), *tkey2 = u32(L.tkey2), *tval2 = u32(L.tval2);
-    int64_t *d_nvis = reinterpret_cast<int64_t *>(ws + L.nvis);
     if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st) != cudaSuccess)
         return check_launch("memset tile ranges");
     if (n == 0) {
@@ -561,41 +587,48 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
             return check_launch("memset pair count");
         return GSR_OK;
     }
+    uint32_t *order = reinterpret_cast<uint32_t *>(ws + L.order);
+    uint32_t *block_sums = reinterpret_cast<uint32_t *>(ws + L.block_sums);
+    uint32_t *coff = reinterpret_cast<uint32_t *>(ws + L.coff);
+    int64_t *d_nvis = reinterpret_cast<int64_t *>(ws + L.counters);
+    int64_t *d_ncand = d_nvis + 1;
+    unsigned long long *d_kept = reinterpret_cast<unsigned long long *>(d_nvis + 2);
+    int64_t *d_written = d_nvis + 3;
+    uint32_t *list_counts = reinterpret_cast<uint32_t *>(d_nvis + 4);
+    uint32_t *kept_tile = reinterpret_cast<uint32_t *>(ws + L.kept_tile);
+    uint64_t *kept_sk = reinterpret_cast<uint64_t *>(ws + L.kept_sk);
+    uint64_t *seg = reinterpret_cast<uint64_t *>(ws + L.seg);
+    uint32_t *list = reinterpret_cast<uint32_t *>(ws + L.list);
+    if (cudaMemsetAsync(d_kept, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return check_launch("memset pair counter");
     const float4 *xy = reinterpret_cast<const float4 *>(proj->xy_conic);
     const float4 *cb = reinterpret_cast<const float4 *>(proj->c_op_box);
     const float4 *rd = reinterpret_cast<const float4 *>(proj->rgb_depth);
     const unsigned sb = (unsigned)L.scan_blocks;
-    // 1. visible Gaussians -> (depth bits, index), then the four depth passes
+    // 1-2. visible records in index order, their candidate offsets
     vis_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, block_sums);
-    vis_compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, rd, n, block_sums, L.scan_blocks, dkey, dval, d_nvis);
-    radix_passes(dkey, dval, dkey2, dval2, d_nvis, n, 0, 32, 4, hist, digit_total, (int)L.nsort_blocks, st);
-    if ((rc = check_launch("depth sort"))) return rc;
-    // 2. pairs in depth order, then the tile passes (ending in tkey / vals)
-    const int tbits = ceil_log2(tiles);
-    const int tpasses = (tbits + 7) / 8;
-    uint32_t *ek = (tpasses & 1) ? tkey2 : tkey;
-    uint32_t *ev = (tpasses & 1) ? tval2 : vals;
-    uint32_t *coff = u32(L.coff), *ctile = u32(L.ctile), *cgid = u32(L.cgid), *cblock_sums = u32(L.cblock_sums);
-    uint8_t *flag = reinterpret_cast<uint8_t *>(ws + L.flag);
-    int64_t *d_ncand = reinterpret_cast<int64_t *>(ws + L.ncand);
-    int64_t *d_written = reinterpret_cast<int64_t *>(ws + L.written);
-    cand_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums);
-    cand_offsets_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, dval, d_nvis, n, block_sums, L.scan_blocks,
-                                                     L.cand_cap, coff, d_ncand, d_num_pairs, d_status);
-    expand_kernel<<<(unsigned)L.expand_blocks, kExpandThreads, 0, st>>>(
-        coff, dval, xy, cb, d_nvis, n, d_ncand, L.cand_cap, tiling->tile_w, tiling->tile_h, vt, flag, ctile, cgid);
-    kept_count_kernel<<<(unsigned)L.cand_blocks, kScanThreads, 0, st>>>(flag, d_ncand, L.cand_cap, cblock_sums);
-    kept_compact_kernel<<<(unsigned)L.cand_blocks, kScanThreads, 0, st>>>(flag, ctile, cgid, d_ncand, L.cand_cap,
-                                                                          cblock_sums, L.cand_blocks, pair_capacity,
-                                                                          ek, ev, d_num_pairs, d_written, d_status);
+    vis_compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, block_sums, L.scan_blocks, order, d_nvis);
+    cand_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, order, d_nvis, n, block_sums);
+    cand_offsets_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, order, d_nvis, n, block_sums, L.scan_blocks, coff,
+                                                     d_ncand, d_status);
+    // 3. cull + unordered kept list + tile counts (in the range words)
+    expand_kernel<<<kExpandGrid, kExpandThreads, 0, st>>>(coff, order, xy, cb, rd, d_nvis, n, d_ncand,
+                                                          tiling->tile_w, tiling->tile_h, vt, (uint32_t)tiles,
+                                                          tile_ranges, kept_tile, kept_sk, pair_capacity, d_kept);
     if ((rc = check_launch("pair expansion"))) return rc;
-    if (pair_capacity == 0) return GSR_OK;
-    radix_passes(ek, ev, (tpasses & 1) ? tkey : tkey2, (tpasses & 1) ? vals : tval2, d_written, pair_capacity, 0,
-                 tbits, tpasses, hist, digit_total, (int)L.psort_blocks, st);
-    const unsigned rb = (unsigned)((pair_capacity + 255) / 256);
-    finalize_kernel<<<rb, 256, 0, st>>>(tkey, vals, rd, d_written, pair_capacity, (uint32_t)tiles, keys,
-                                        reinterpret_cast<uint2 *>(tile_ranges));
-    return check_launch("finalize_kernel");
+    // 4-6. ranges, scatter into tile segments, sort each segment
+    tile_scan_kernel<<<1, kTileScanThreads, 0, st>>>(tile_ranges, (uint32_t)tiles, d_kept, pair_capacity, list,
+                                                      list_counts, d_written, d_num_pairs, d_status);
+    if (pair_capacity == 0) return check_launch("tile_scan_kernel");
+    scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_tile, kept_sk, d_written, pair_capacity, tile_ranges, seg);
+    sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list_counts, tile_ranges, seg, keys, vals);
+    const size_t big = sizeof(uint64_t) * kLargeTile;
+    static_assert(sizeof(uint64_t) * kLargeTile >= sizeof(uint32_t) * (kLargeSortThreads / 32) * kRadix,
+                  "the long-segment sort reuses the shared array for its per-warp counts");
+    cudaFuncSetAttribute(sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    sort_large_kernel<<<148, kLargeSortThreads, big, st>>>(list, list_counts, pair_capacity, tile_ranges, seg, kept_sk,
+                                                          keys, vals);
+    return check_launch("tile sort");
 }
 }  // namespace gsr
 

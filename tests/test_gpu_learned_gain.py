@@ -1,0 +1,87 @@
+"""What the trained initialiser gains over the method without it.
+
+A small version of the time-to-PSNR experiment: the MLP is trained on the GPU
+(its own tensor-core kernels) on (patch, converged parameter) pairs that a
+mapping run produces on one seeded scene, then a held-out scene's keyframes
+are mapped by the batched window from the default initialisation and from the
+learned one.  The learned start must be at least as good and must lead after
+a fixed number of iterations (both arms see identical work per iteration).
+"""
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2311_16728_b300 as gsr  # noqa: E402
+from paper_2311_16728_b300.batched import BatchedWindow  # noqa: E402
+from paper_2311_16728_b300.learned_init import LearnedInit, init_weights  # noqa: E402
+from paper_2311_16728_b300.mapping import (Evaluator, densify_default, densify_learned, harvest,  # noqa: E402
+                                           train_initialiser)
+
+N = 60_000
+CAMS = [S.tum_camera(k * 50 // 4) for k in range(4)]
+
+
+def _scene(seed):
+    truth, offsets, kps = S.densify_scene(S.room_scene(N, seed=seed), CAMS, 20_000, seed=seed + 1)
+    g = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
+    vb = gsr.ViewBuffers(N, gsr.camera_from(CAMS[0]), gsr.tiling_struct(16, 16), 1024)
+    keyframes = []
+    for cam, kp in zip(CAMS, kps):
+        vb.cam = gsr.camera_from(cam)
+        gsr.ensure_capacity(vb, g)
+        vb.forward(g)
+        img = vb.img.clone()
+        host = img.cpu().numpy()
+        kp[:, 4] = [S.orb_angle(host, u, v) for u, v in kp[:, :2]]
+        keyframes.append((cam, img))
+    return truth, keyframes, [torch.tensor(k, device="cuda") for k in kps], offsets
+
+
+def _fresh(truth):
+    return gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
+
+
+def test_learned_initialiser_beats_default():
+    li = LearnedInit(init_weights(3), 20_000, lr=1e-3)
+    truth, keyframes, kps, offsets = _scene(10)
+    params = _fresh(truth)
+    densify_default(params, keyframes, kps, offsets)
+    initial = gsr.Gaussians(*(t.clone() for t in params.tensors()), params.sh_degree)
+    bw = BatchedWindow(params, keyframes)
+    bw.capture()
+    for _ in range(150):
+        bw.step()
+    torch.cuda.synchronize()
+    assert bw.status.item() == 0
+    batches = harvest(li, params, initial, keyframes, kps, offsets)
+    losses = train_initialiser(li, batches, 1500)
+    assert losses[-1] < 0.5 * losses[0]
+    del bw, params, initial
+    truth, keyframes, kps, offsets = _scene(100)
+    ev = Evaluator(N, keyframes)
+    curves = {}
+    for name in ("default", "learned"):
+        params = _fresh(truth)
+        if name == "learned":
+            densify_learned(li, params, keyframes, kps, offsets)
+        else:
+            densify_default(params, keyframes, kps, offsets)
+        bw = BatchedWindow(params, keyframes)
+        bw.capture()
+        c = [ev(params)]
+        for _ in range(3):
+            for _ in range(10):
+                bw.step()
+            c.append(ev(params))
+        assert bw.status.item() == 0
+        curves[name] = c
+        del bw, params
+    print(f"MLP loss {losses[0]:.3f} -> {losses[-1]:.3f}; PSNR every 10 window iterations: {curves}")
+    assert curves["learned"][0] >= curves["default"][0] - 0.05
+    assert curves["learned"][-1] > curves["default"][-1] + 0.5

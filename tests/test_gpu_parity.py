@@ -381,3 +381,23 @@ def test_graph_replay_matches_eager():
     diff = np.linalg.norm(grads[1] - grads[0]) / np.linalg.norm(grads[0])
     assert diff <= 1e-6, diff
     np.testing.assert_allclose(losses[1], losses[0], rtol=1e-5)
+
+
+@pytest.mark.parametrize("n", [4000, 20000])
+def test_long_tile_segments_bit_exact(n):
+    """Large Gaussians covering most of a 160 x 120 frame with 32 x 32 tiles:
+    every tile holds ~n pairs, so the per-tile sort takes its shared-memory
+    path for long segments (n = 4000) and its global-memory radix path beyond
+    shared memory (n = 20000).  Keys, order and ranges stay bit-exact."""
+    rng = np.random.default_rng(11)
+    p = S.tiny_scene(n, seed=12)
+    p.mean_op[:, 0] = rng.uniform(-0.4, 0.4, n)
+    p.mean_op[:, 1] = rng.uniform(-0.3, 0.3, n)
+    p.logscale[:, :3] = np.log(rng.uniform(0.3, 0.6, (n, 3))).astype(np.float32)
+    cam = S.tiny_camera()
+    vb, g = gpu_view(p, cam, tile=(32, 32))
+    dec, keys_ref, _, _ = _oracle_all(p, cam, tile=(32, 32), rows=(0, 0))
+    lengths = np.diff(keys_ref[2].reshape(-1, 2), axis=1)
+    print(f"n {n}: pairs {len(keys_ref[0])}, longest tile segment {lengths.max()}")
+    assert lengths.max() > (16384 if n == 20000 else 1024)
+    _check_keys(vb, dec, keys_ref)
