@@ -209,8 +209,9 @@ constexpr int kExpandTile = kExpandThreads * kExpandItems;
 constexpr int kExpandGrid = 148 * 8;  // grid-stride over chunks of kExpandTile candidates
 
 // Kept pairs: kept_tile[p] = global tile, kept_sk[p] = depth bits << 32 |
-// record (p from one atomic per warp on *d_kept; pairs beyond `cap` are
-// counted but not stored), and counts[2 t] += 1 per kept pair of tile t.
+// record (positions from one atomic per block and chunk on *d_kept; pairs
+// beyond `cap` are counted but not stored), and counts[2 t] += 1 per kept
+// pair of tile t.
 __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     const uint32_t *__restrict__ coff, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
     const float4 *__restrict__ c_op_box, const float4 *__restrict__ rgb_depth, const int64_t *__restrict__ d_nvis,
@@ -218,14 +219,15 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     uint32_t *__restrict__ counts, uint32_t *__restrict__ kept_tile, uint64_t *__restrict__ kept_sk, int64_t cap,
     unsigned long long *__restrict__ d_kept) {
     __shared__ uint32_t s_off[kExpandTile + 1];
+    __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_i0;
+    __shared__ unsigned long long s_base;
     __shared__ int s_m;
     const int64_t ncand = *d_ncand;
     const int64_t nv = clamp_count(d_nvis, cap_n);
-    const int lane = threadIdx.x & 31;
     for (int64_t s0 = (int64_t)blockIdx.x * kExpandTile; s0 < ncand; s0 += (int64_t)gridDim.x * kExpandTile) {
         const int64_t s_last = (s0 + kExpandTile < ncand ? s0 + kExpandTile : ncand) - 1;
-        __syncthreads();  // the previous chunk is done with s_off
+        __syncthreads();  // the previous chunk is done with the shared words
         if (threadIdx.x < 32) {
             const int64_t i0 = warp_upper_index(coff, nv, (uint32_t)s0);
             const int64_t i1 = warp_upper_index(coff, nv, (uint32_t)s_last);
@@ -239,12 +241,13 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
         const int m = s_m;
         for (int j = threadIdx.x; j <= m; j += kExpandThreads) s_off[j] = coff[i0 + j];
         __syncthreads();
-#pragma unroll 1
+        uint32_t tiles[kExpandItems], gids[kExpandItems];
+        uint32_t mine = 0;  // bit r: this thread's candidate of round r is kept
+#pragma unroll
         for (int r = 0; r < kExpandItems; ++r) {
-            // every lane runs every round: the ballot below needs the whole warp
             const int64_t slot = s0 + (int64_t)r * kExpandThreads + threadIdx.x;
-            bool keep = false;
-            uint32_t tile = 0, gid = 0;
+            tiles[r] = 0;
+            gids[r] = 0;
             if (slot < ncand) {
                 int lo = 0, hi = m;  // s_off[lo] <= slot < s_off[hi]
                 while (hi - lo > 1) {
@@ -252,31 +255,37 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
                     if (s_off[mid] <= (uint32_t)slot) lo = mid;
                     else hi = mid;
                 }
-                gid = order[i0 + lo];
+                const uint32_t gid = order[i0 + lo];
                 const int k = (int)((uint32_t)slot - s_off[lo]);
                 const Splat sp = load_splat(xy_conic, c_op_box, gid);
                 const int tx0 = sp.x0 / tw, ntx = sp.x1 / tw - tx0 + 1;
                 const int tx = tx0 + k % ntx, ty = sp.y0 / th + k / ntx;
                 const int v = (int)((int64_t)gid / vt.n_per_view);  // view of this record
-                tile = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
-                keep = tile < ntiles_total &&
-                       tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1);
-            }
-            const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
-            if (ballot == 0u) continue;  // warp-uniform
-            const int leader = __ffs(ballot) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(d_kept, (unsigned long long)__popc(ballot));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (keep) {
-                const unsigned long long pos = base + (unsigned long long)__popc(ballot & ((1u << lane) - 1u));
-                if (pos < (unsigned long long)cap) {
-                    kept_tile[pos] = tile;
-                    kept_sk[pos] = ((uint64_t)__float_as_uint(__ldg(&rgb_depth[gid].w)) << 32) | gid;
+                const uint32_t tile = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
+                if (tile < ntiles_total &&
+                    tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1)) {
+                    mine |= 1u << r;
+                    tiles[r] = tile;
+                    gids[r] = gid;
                 }
-                atomicAdd(&counts[2 * (size_t)tile], 1u);
             }
         }
+        // one atomic per block and chunk reserves the block's slots
+        const uint32_t c = (uint32_t)__popc(mine);
+        const uint32_t incl = block_incl_scan_256(c, s_warp);
+        if (threadIdx.x == kExpandThreads - 1) s_base = incl ? atomicAdd(d_kept, (unsigned long long)incl) : 0ull;
+        __syncthreads();
+        unsigned long long pos = s_base + (unsigned long long)(incl - c);
+#pragma unroll
+        for (int r = 0; r < kExpandItems; ++r)
+            if (mine & (1u << r)) {
+                if (pos < (unsigned long long)cap) {
+                    kept_tile[pos] = tiles[r];
+                    kept_sk[pos] = ((uint64_t)__float_as_uint(__ldg(&rgb_depth[gids[r]].w)) << 32) | gids[r];
+                }
+                atomicAdd(&counts[2 * (size_t)tiles[r]], 1u);
+                ++pos;
+            }
     }
 }
 
@@ -371,20 +380,46 @@ __global__ void __launch_bounds__(256) scatter_kernel(const uint32_t *__restrict
 
 // ---------------------------------------------------------------- per-tile sort
 // Ascending bitonic network over s[0, P) (P a power of two) by NT threads.
+// Stages whose partner distance j is below 32 stay inside aligned chunks of
+// 64 entries, so each warp runs them on its own chunks with warp barriers;
+// only the wider stages take a block barrier.
+__device__ __forceinline__ void cmp_swap(uint64_t *s, uint32_t a, uint32_t j, uint32_t k) {
+    const uint32_t b = a + j;
+    const uint64_t x = s[a], y = s[b];
+    if ((x > y) == ((a & k) == 0)) {
+        s[a] = y;
+        s[b] = x;
+    }
+}
+
 template <int NT>
 __device__ __forceinline__ void bitonic_sort(uint64_t *s, uint32_t P) {
+    constexpr int kWarps = NT / 32;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t C = P < 64 ? P : 64;  // chunk of the warp-local stages
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        uint32_t j = k >> 1;
+        for (; j >= 32; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P / 2; i += NT) cmp_swap(s, 2 * j * (i / j) + (i % j), j, k);
+            __syncthreads();
+        }
+        for (uint32_t c = wid; c < P / C; c += kWarps) {
+            for (uint32_t jj = j; jj > 0; jj >>= 1) {
+                if (lane < C / 2) cmp_swap(s, c * C + 2 * jj * (lane / jj) + (lane % jj), jj, k);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// the same network over at most 64 entries by one warp
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t *s, uint32_t P) {
+    const uint32_t lane = threadIdx.x & 31;
     for (uint32_t k = 2; k <= P; k <<= 1)
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P / 2; i += NT) {
-                const uint32_t a = 2 * j * (i / j) + (i % j), b = a + j;
-                const uint64_t x = s[a], y = s[b];
-                const bool up = (a & k) == 0;
-                if ((x > y) == up) {
-                    s[a] = y;
-                    s[b] = x;
-                }
-            }
-            __syncthreads();
+            if (lane < P / 2) cmp_swap(s, 2 * j * (lane / j) + (lane % j), j, k);
+            __syncwarp();
         }
 }
 
@@ -416,18 +451,45 @@ constexpr int kSmallSortThreads = 256;
 constexpr int kLargeSortThreads = 1024;
 constexpr int kSortGrid = 148 * 8;
 
+constexpr uint32_t kWarpTile = 64;  // segments this short are sorted by one warp
+
 __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uint32_t *__restrict__ list,
                                                                        const uint32_t *__restrict__ list_counts,
                                                                        const uint32_t *__restrict__ ranges,
                                                                        const uint64_t *__restrict__ seg,
                                                                        uint64_t *__restrict__ keys,
                                                                        uint32_t *__restrict__ vals) {
+    constexpr int kWarps = kSmallSortThreads / 32;
+    static_assert(kWarps * kWarpTile <= kSmallTile, "one warp-sized slice per warp");
     __shared__ uint64_t s[kSmallTile];
     const uint32_t cnt = list_counts[0];
-    for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
-        const uint32_t t = list[e];
-        const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
-        smem_tile_sort<kSmallSortThreads>(seg, t, b, L, s, keys, vals);
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // each block takes kWarps list entries at a time: the short ones one per
+    // warp, then the others one after another by the whole block
+    for (uint32_t e0 = blockIdx.x * kWarps; e0 < cnt; e0 += gridDim.x * kWarps) {
+        const uint32_t e = e0 + wid;
+        if (e < cnt) {
+            const uint32_t t = list[e];
+            const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
+            if (L <= kWarpTile) {
+                uint64_t *w = s + wid * kWarpTile;
+                uint32_t P = 1;
+                while (P < L) P <<= 1;
+                for (uint32_t i = lane; i < P; i += 32) w[i] = i < L ? seg[b + i] : ~0ull;
+                __syncwarp();
+                warp_bitonic_sort(w, P);
+                for (uint32_t i = lane; i < L; i += 32) {
+                    keys[b + i] = ((uint64_t)t << 32) | (w[i] >> 32);
+                    vals[b + i] = (uint32_t)w[i];
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t q = 0; q < (uint32_t)kWarps && e0 + q < cnt; ++q) {
+            const uint32_t t = list[e0 + q];
+            const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
+            if (L > kWarpTile) smem_tile_sort<kSmallSortThreads>(seg, t, b, L, s, keys, vals);
+        }
     }
 }
 
