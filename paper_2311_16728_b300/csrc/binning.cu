@@ -8,11 +8,13 @@
 //   2. an exclusive scan of their box-tile counts numbers the candidates
 //      (record, box tile);
 //   3. expansion: one thread per candidate runs the tile cull (tile_keep); a
-//      kept pair is appended to an unordered list (one atomic per warp) and
-//      counted in its tile (an atomic on the tile's range word);
-//   4. one CTA scans the tile counts into [begin, end) ranges, seeds each
-//      tile's cursor, and lists the non-empty tiles by length class;
-//   5. scatter: every kept pair takes the next slot of its tile's segment;
+//      kept pair is appended to an unordered list (one atomic per block and
+//      chunk of candidates) and counted in its tile (an atomic on the tile's
+//      range word, whose return value is the pair's rank in the tile);
+//   4. one CTA scans the tile counts into [begin, end) ranges and lists the
+//      non-empty tiles by length class;
+//   5. scatter: every kept pair goes to its tile's segment at the rank the
+//      counting atomic returned;
 //   6. each segment is sorted on (depth bits << 32 | index) -- unique keys --
 //      in shared memory by a bitonic network (a stable LSD radix sort in
 //      global memory for the rare segment longer than shared memory), and
@@ -208,15 +210,15 @@ constexpr int kExpandItems = 4;
 constexpr int kExpandTile = kExpandThreads * kExpandItems;
 constexpr int kExpandGrid = 148 * 8;  // grid-stride over chunks of kExpandTile candidates
 
-// Kept pairs: kept_tile[p] = global tile, kept_sk[p] = depth bits << 32 |
-// record (positions from one atomic per block and chunk on *d_kept; pairs
-// beyond `cap` are counted but not stored), and counts[2 t] += 1 per kept
-// pair of tile t.
+// Kept pairs: kept_ts[p] = global tile << 32 | rank of the pair within its
+// tile (from the atomic that counts the tile's pairs in counts[2 t]),
+// kept_sk[p] = depth bits << 32 | record; positions p from one atomic per
+// block and chunk on *d_kept (pairs beyond `cap` are counted, not stored).
 __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     const uint32_t *__restrict__ coff, const uint32_t *__restrict__ order, const float4 *__restrict__ xy_conic,
     const float4 *__restrict__ c_op_box, const float4 *__restrict__ rgb_depth, const int64_t *__restrict__ d_nvis,
     int64_t cap_n, const int64_t *__restrict__ d_ncand, int tw, int th, const ViewTiles vt, uint32_t ntiles_total,
-    uint32_t *__restrict__ counts, uint32_t *__restrict__ kept_tile, uint64_t *__restrict__ kept_sk, int64_t cap,
+    uint32_t *__restrict__ counts, uint64_t *__restrict__ kept_ts, uint64_t *__restrict__ kept_sk, int64_t cap,
     unsigned long long *__restrict__ d_kept) {
     __shared__ uint32_t s_off[kExpandTile + 1];
     __shared__ uint32_t s_warp[8];
@@ -279,11 +281,11 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
 #pragma unroll
         for (int r = 0; r < kExpandItems; ++r)
             if (mine & (1u << r)) {
+                const uint32_t rank = atomicAdd(&counts[2 * (size_t)tiles[r]], 1u);
                 if (pos < (unsigned long long)cap) {
-                    kept_tile[pos] = tiles[r];
+                    kept_ts[pos] = ((uint64_t)tiles[r] << 32) | rank;
                     kept_sk[pos] = ((uint64_t)__float_as_uint(__ldg(&rgb_depth[gids[r]].w)) << 32) | gids[r];
                 }
-                atomicAdd(&counts[2 * (size_t)tiles[r]], 1u);
                 ++pos;
             }
     }
@@ -291,7 +293,8 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
 
 // ---------------------------------------------------------------- tile scan
 constexpr int kTileScanThreads = 1024;
-constexpr uint32_t kSmallTile = 1024;    // longest segment of the small-tile sort
+constexpr uint32_t kWarpTile = 256;      // segments this short are sorted by one warp, in registers
+constexpr uint32_t kSmallTile = 1024;    // longest segment of the one-block shared-memory sort
 constexpr uint32_t kLargeTile = 16384;   // longest segment sorted in shared memory
 
 __device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s_warp) {
@@ -319,21 +322,22 @@ __device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s
 }
 
 // One CTA.  ranges[2 t] holds tile t's pair count on entry; on exit
-// ranges[2 t] = begin and ranges[2 t + 1] = begin (the scatter cursor, which
-// ends at the segment's end), or [0, 0) for an empty tile.  Non-empty tiles
-// are listed for the sort: length <= kSmallTile from the front of `list`,
-// longer ones from its back.  On pair overflow every range is empty.
+// ranges[2 t], [2 t + 1] = [begin, end) of its segment, or [0, 0) for an
+// empty tile.  Non-empty tiles are listed for the sort by length: up to
+// kWarpTile from the front of `list`, up to kSmallTile in `list2`, longer
+// ones from the back of `list`.  On pair overflow every range is empty.
 __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     uint32_t *__restrict__ ranges, uint32_t T, const unsigned long long *__restrict__ d_kept, int64_t cap,
-    uint32_t *__restrict__ list, uint32_t *__restrict__ list_counts, int64_t *__restrict__ d_written,
-    int64_t *__restrict__ d_num_pairs, int32_t *__restrict__ d_status) {
+    uint32_t *__restrict__ list, uint32_t *__restrict__ list2, uint32_t *__restrict__ list_counts,
+    int64_t *__restrict__ d_written, int64_t *__restrict__ d_num_pairs, int32_t *__restrict__ d_status) {
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_small, s_large;
+    __shared__ uint32_t s_small, s_large, s_mid;
     const unsigned long long K = *d_kept;
     const bool overflow = K > (unsigned long long)cap;
     if (threadIdx.x == 0) {
         s_small = 0u;
         s_large = 0u;
+        s_mid = 0u;
         *d_num_pairs = (int64_t)K;
         *d_written = overflow ? 0 : (int64_t)K;
         if (overflow) raise_status(d_status, GSR_ERR_CAPACITY);
@@ -354,8 +358,9 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
             continue;
         }
         ranges[2 * (size_t)t] = off;
-        ranges[2 * (size_t)t + 1] = off;
-        if (c <= kSmallTile) list[atomicAdd(&s_small, 1u)] = t;
+        ranges[2 * (size_t)t + 1] = off + c;
+        if (c <= kWarpTile) list[atomicAdd(&s_small, 1u)] = t;
+        else if (c <= kSmallTile) list2[atomicAdd(&s_mid, 1u)] = t;
         else list[(size_t)cap - 1 - atomicAdd(&s_large, 1u)] = t;
         off += c;
     }
@@ -363,17 +368,21 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     if (threadIdx.x == 0) {
         list_counts[0] = s_small;
         list_counts[1] = s_large;
+        list_counts[2] = s_mid;
     }
 }
 
-// every stored kept pair takes the next slot of its tile's segment
-__global__ void __launch_bounds__(256) scatter_kernel(const uint32_t *__restrict__ kept_tile,
+// every stored kept pair goes to its tile's segment at its rank
+__global__ void __launch_bounds__(256) scatter_kernel(const uint64_t *__restrict__ kept_ts,
                                                       const uint64_t *__restrict__ kept_sk,
                                                       const int64_t *__restrict__ d_written, int64_t cap,
-                                                      uint32_t *__restrict__ ranges, uint64_t *__restrict__ seg) {
+                                                      const uint32_t *__restrict__ ranges,
+                                                      uint64_t *__restrict__ seg) {
     const int64_t w = *d_written;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < w; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t pos = atomicAdd(&ranges[2 * (size_t)kept_tile[i] + 1], 1u);
+        const uint64_t ts = kept_ts[i];
+        const uint32_t t = (uint32_t)(ts >> 32);
+        const uint64_t pos = (uint64_t)ranges[2 * (size_t)t] + (uint32_t)ts;
         if (pos < (uint64_t)cap) seg[pos] = kept_sk[i];
     }
 }
@@ -413,14 +422,41 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *s, uint32_t P) {
     }
 }
 
-// the same network over at most 64 entries by one warp
-__device__ __forceinline__ void warp_bitonic_sort(uint64_t *s, uint32_t P) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t k = 2; k <= P; k <<= 1)
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            if (lane < P / 2) cmp_swap(s, 2 * j * (lane / j) + (lane % j), j, k);
-            __syncwarp();
+// The same network over 256 entries held in one warp's registers: entry
+// i = 32 e + lane sits in v[e] of that lane, so partners at distance J < 32
+// are a lane apart (shuffle) and partners at J >= 32 are registers of the
+// same lane.  Stages are unrolled at compile time; sizes above P are skipped.
+template <uint32_t K, uint32_t J>
+__device__ __forceinline__ void warp_stage(uint64_t (&v)[8], uint32_t lane) {
+    if constexpr (J >= 32) {
+        constexpr uint32_t EJ = J / 32;
+#pragma unroll
+        for (uint32_t e = 0; e < 8; ++e)
+            if ((e & EJ) == 0) {
+                const bool up = ((32 * e + lane) & K) == 0;
+                const uint64_t a = v[e], b = v[e | EJ];
+                if ((a > b) == up) {
+                    v[e] = b;
+                    v[e | EJ] = a;
+                }
+            }
+    } else {
+        const bool lower = (lane & J) == 0;
+#pragma unroll
+        for (uint32_t e = 0; e < 8; ++e) {
+            const bool up = ((32 * e + lane) & K) == 0;
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], J);
+            v[e] = (lower == up) ? (v[e] < o ? v[e] : o) : (v[e] < o ? o : v[e]);
         }
+    }
+    if constexpr (J > 1) warp_stage<K, J / 2>(v, lane);
+}
+
+template <uint32_t K>
+__device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[8], uint32_t lane, uint32_t P) {
+    if (K > P) return;
+    warp_stage<K, K / 2>(v, lane);
+    if constexpr (K < 256) warp_sort_regs<2 * K>(v, lane, P);
 }
 
 // sorted (depth << 32 | index) of tile t -> keys (tile << 32 | depth), vals
@@ -451,45 +487,46 @@ constexpr int kSmallSortThreads = 256;
 constexpr int kLargeSortThreads = 1024;
 constexpr int kSortGrid = 148 * 8;
 
-constexpr uint32_t kWarpTile = 64;  // segments this short are sorted by one warp
 
+// Segments up to kWarpTile: one warp each, in registers; segments up to
+// kSmallTile: one block each, in shared memory.  Both classes are spread
+// over the whole grid.
 __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uint32_t *__restrict__ list,
+                                                                       const uint32_t *__restrict__ list2,
                                                                        const uint32_t *__restrict__ list_counts,
                                                                        const uint32_t *__restrict__ ranges,
                                                                        const uint64_t *__restrict__ seg,
                                                                        uint64_t *__restrict__ keys,
                                                                        uint32_t *__restrict__ vals) {
     constexpr int kWarps = kSmallSortThreads / 32;
-    static_assert(kWarps * kWarpTile <= kSmallTile, "one warp-sized slice per warp");
     __shared__ uint64_t s[kSmallTile];
-    const uint32_t cnt = list_counts[0];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // each block takes kWarps list entries at a time: the short ones one per
-    // warp, then the others one after another by the whole block
-    for (uint32_t e0 = blockIdx.x * kWarps; e0 < cnt; e0 += gridDim.x * kWarps) {
-        const uint32_t e = e0 + wid;
-        if (e < cnt) {
-            const uint32_t t = list[e];
-            const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
-            if (L <= kWarpTile) {
-                uint64_t *w = s + wid * kWarpTile;
-                uint32_t P = 1;
-                while (P < L) P <<= 1;
-                for (uint32_t i = lane; i < P; i += 32) w[i] = i < L ? seg[b + i] : ~0ull;
-                __syncwarp();
-                warp_bitonic_sort(w, P);
-                for (uint32_t i = lane; i < L; i += 32) {
-                    keys[b + i] = ((uint64_t)t << 32) | (w[i] >> 32);
-                    vals[b + i] = (uint32_t)w[i];
-                }
+    const uint32_t n_warp = list_counts[0], n_block = list_counts[2];
+    for (uint32_t e = blockIdx.x * kWarps + wid; e < n_warp; e += gridDim.x * kWarps) {
+        const uint32_t t = list[e];
+        const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
+        uint32_t P = 1;
+        while (P < L) P <<= 1;
+        uint64_t v[8];
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+            const uint32_t i = 32 * q + lane;
+            v[q] = i < L ? seg[b + i] : ~0ull;
+        }
+        warp_sort_regs<2>(v, lane, P);
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+            const uint32_t i = 32 * q + lane;
+            if (i < L) {
+                keys[b + i] = ((uint64_t)t << 32) | (v[q] >> 32);
+                vals[b + i] = (uint32_t)v[q];
             }
         }
-        __syncthreads();
-        for (uint32_t q = 0; q < (uint32_t)kWarps && e0 + q < cnt; ++q) {
-            const uint32_t t = list[e0 + q];
-            const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
-            if (L > kWarpTile) smem_tile_sort<kSmallSortThreads>(seg, t, b, L, s, keys, vals);
-        }
+    }
+    for (uint32_t e = blockIdx.x; e < n_block; e += gridDim.x) {
+        const uint32_t t = list2[e];
+        const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
+        smem_tile_sort<kSmallSortThreads>(seg, t, b, L, s, keys, vals);
     }
 }
 
@@ -582,7 +619,7 @@ __global__ void __launch_bounds__(kLargeSortThreads) sort_large_kernel(const uin
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SortLayout {
-    size_t order, block_sums, coff, counters, kept_tile, kept_sk, seg, list, total;
+    size_t order, block_sums, coff, counters, kept_ts, kept_sk, seg, list, list2, total;
     int64_t scan_blocks;
 };
 
@@ -594,11 +631,12 @@ static SortLayout sort_layout(int64_t n, int64_t cap) {
     L.order = off; off += align256(sizeof(uint32_t) * (size_t)n1);
     L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
     L.coff = off; off += align256(sizeof(uint32_t) * (size_t)(n1 + 1));
-    L.counters = off; off += 256;  // nvis, ncand, kept, written (int64) + 2 list counts (u32)
-    L.kept_tile = off; off += align256(sizeof(uint32_t) * (size_t)c1);
+    L.counters = off; off += 256;  // nvis, ncand, kept, written (int64) + 3 list counts (u32)
+    L.kept_ts = off; off += align256(sizeof(uint64_t) * (size_t)c1);
     L.kept_sk = off; off += align256(sizeof(uint64_t) * (size_t)c1);
     L.seg = off; off += align256(sizeof(uint64_t) * (size_t)c1);
     L.list = off; off += align256(sizeof(uint32_t) * (size_t)c1);
+    L.list2 = off; off += align256(sizeof(uint32_t) * (size_t)c1);
     L.total = off;
     return L;
 }
@@ -657,10 +695,11 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     unsigned long long *d_kept = reinterpret_cast<unsigned long long *>(d_nvis + 2);
     int64_t *d_written = d_nvis + 3;
     uint32_t *list_counts = reinterpret_cast<uint32_t *>(d_nvis + 4);
-    uint32_t *kept_tile = reinterpret_cast<uint32_t *>(ws + L.kept_tile);
+    uint64_t *kept_ts = reinterpret_cast<uint64_t *>(ws + L.kept_ts);
     uint64_t *kept_sk = reinterpret_cast<uint64_t *>(ws + L.kept_sk);
     uint64_t *seg = reinterpret_cast<uint64_t *>(ws + L.seg);
     uint32_t *list = reinterpret_cast<uint32_t *>(ws + L.list);
+    uint32_t *list2 = reinterpret_cast<uint32_t *>(ws + L.list2);
     if (cudaMemsetAsync(d_kept, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return check_launch("memset pair counter");
     const float4 *xy = reinterpret_cast<const float4 *>(proj->xy_conic);
@@ -676,14 +715,15 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     // 3. cull + unordered kept list + tile counts (in the range words)
     expand_kernel<<<kExpandGrid, kExpandThreads, 0, st>>>(coff, order, xy, cb, rd, d_nvis, n, d_ncand,
                                                           tiling->tile_w, tiling->tile_h, vt, (uint32_t)tiles,
-                                                          tile_ranges, kept_tile, kept_sk, pair_capacity, d_kept);
+                                                          tile_ranges, kept_ts, kept_sk, pair_capacity, d_kept);
     if ((rc = check_launch("pair expansion"))) return rc;
     // 4-6. ranges, scatter into tile segments, sort each segment
     tile_scan_kernel<<<1, kTileScanThreads, 0, st>>>(tile_ranges, (uint32_t)tiles, d_kept, pair_capacity, list,
-                                                      list_counts, d_written, d_num_pairs, d_status);
+                                                      list2, list_counts, d_written, d_num_pairs, d_status);
     if (pair_capacity == 0) return check_launch("tile_scan_kernel");
-    scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_tile, kept_sk, d_written, pair_capacity, tile_ranges, seg);
-    sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list_counts, tile_ranges, seg, keys, vals);
+    scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_ts, kept_sk, d_written, pair_capacity, tile_ranges, seg);
+    sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list2, list_counts, tile_ranges, seg, keys,
+                                                                 vals);
     const size_t big = sizeof(uint64_t) * kLargeTile;
     static_assert(sizeof(uint64_t) * kLargeTile >= sizeof(uint32_t) * (kLargeSortThreads / 32) * kRadix,
                   "the long-segment sort reuses the shared array for its per-warp counts");
