@@ -776,8 +776,9 @@ def stage_rooflines(stage_ms, work, peaks, clk):
         elif st == "preprocess_bwd":
             out[st] = hbm_entry("preprocess_bwd_kernel", (240 + 48 + 480) * nv)
         elif st == "adam":
-            # 15 float4 planes x (param r+w, grad r+w, m r+w, v r+w)
-            out[st] = hbm_entry("adam_kernel", 15 * 16 * 8 * n)
+            # 15 float4 planes: param, m, v read + written for every Gaussian, the
+            # gradient read + zeroed only where the view flag (4 B) is set
+            out[st] = hbm_entry("adam_kernel", (15 * 16 * 6 + 4) * n + 15 * 16 * 2 * nv)
     return out
 
 

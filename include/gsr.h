@@ -307,10 +307,12 @@ int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *vals, const ui
  * camera (the pyramid levels of a keyframe: same pose, fx, fy, cx, cy, width
  * and height all scaled by 2^-k) are merged before the chain rule, which then
  * runs once per (Gaussian, keyframe): u, v scale by 2^-k, the dilated
- * covariance is 4^-k M + 0.3 I, and opacity and colour are shared. */
+ * covariance is 4^-k M + 0.3 I, and opacity and colour are shared.
+ * touched (n u32, may be NULL) receives 1 for every Gaussian some view saw,
+ * else 0: the flags gsr_adam_step_touched takes. */
 int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
                                    int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
-                                   const gsr_param_buffers *grads, gsr_stream_t stream);
+                                   const gsr_param_buffers *grads, uint32_t *touched, gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */
 /* Default initialisation of new primitives (Sec. 3.3.1)             */
@@ -447,6 +449,18 @@ typedef struct {
 int32_t gsr_adam_step(const gsr_param_buffers *params, const gsr_param_buffers *grads,
                       const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
                       const gsr_adam_config *cfg, int32_t *d_step, gsr_stream_t stream);
+
+/* gsr_adam_step for gradients that are zero wherever touched[i] == 0 (n
+ * flags, device): such Gaussians' gradients are neither read nor rewritten
+ * (their moments decay and their parameters move as Adam prescribes for a
+ * zero gradient), which saves a quarter of the step's HBM bytes for every
+ * Gaussian the iteration did not see.  A one-view iteration passes its
+ * proj.ntiles (non-zero exactly for the Gaussians whose gradient it wrote);
+ * the batched window passes the flags gsr_batched_preprocess_bwd writes. */
+int32_t gsr_adam_step_touched(const gsr_param_buffers *params, const gsr_param_buffers *grads,
+                              const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
+                              const gsr_adam_config *cfg, const uint32_t *touched, int32_t *d_step,
+                              gsr_stream_t stream);
 
 /* One Gaussian-pyramid step down (Sec. 3.4, Eq. 5 GP^l): separable binomial
  * [1 4 6 4 1]/16 blur with reflect-101 borders, keeping even pixels.

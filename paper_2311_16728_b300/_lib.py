@@ -93,7 +93,7 @@ _SIGNATURES = {
                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, P(gsr_grad2d),
                              c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "gsr_batched_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_int32, P(gsr_tiling), P(gsr_grad2d),
-                                    P(gsr_param_buffers), c_void_p], c_int32),
+                                    P(gsr_param_buffers), c_void_p, c_void_p], c_int32),
     "gsr_default_init_workspace_size": ([c_int64, c_int64, P(c_size_t)], c_int32),
     "gsr_default_init": ([c_void_p, c_int32, c_int32, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64,
                           c_int64, c_void_p, c_size_t, c_void_p], c_int32),
@@ -116,6 +116,8 @@ _SIGNATURES = {
                         c_int64, c_void_p], c_int32),
     "gsr_adam_step": ([P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers),
                        c_int64, P(gsr_adam_config), c_void_p, c_void_p], c_int32),
+    "gsr_adam_step_touched": ([P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers),
+                               c_int64, P(gsr_adam_config), c_void_p, c_void_p, c_void_p], c_int32),
     "gsr_pyramid_down": ([c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p], c_int32),
     "gsr_psnr_workspace_size": ([c_int64, P(c_size_t)], c_int32),
     "gsr_psnr": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
@@ -189,6 +191,7 @@ gsr_mlp_gradients = _wrap("gsr_mlp_gradients")
 gsr_mlp_encode_targets = _wrap("gsr_mlp_encode_targets")
 gsr_mlp_decode = _wrap("gsr_mlp_decode")
 gsr_adam_step = _wrap("gsr_adam_step")
+gsr_adam_step_touched = _wrap("gsr_adam_step_touched")
 gsr_pyramid_down = _wrap("gsr_pyramid_down")
 gsr_psnr_workspace_size = _wrap("gsr_psnr_workspace_size")
 gsr_psnr = _wrap("gsr_psnr")

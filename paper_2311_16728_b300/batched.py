@@ -61,6 +61,7 @@ class BatchedWindow:
         self.losses = torch.zeros(V, **f32)
         self.g2 = torch.zeros(3, m, 4, **f32)  # zero on entry; the chain step leaves it zero
         self.grads = params.zeros_like()
+        self.touched = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)  # Gaussians some view saw
         self.adam = Adam(params, adam_cfg)
         self.weights = (ctypes.c_float * V)(*(weights if weights is not None else [1.0] * V))
         ptrs = lambda ts: (ctypes.c_void_p * V)(*[t.data_ptr() for t in ts])
@@ -127,13 +128,13 @@ class BatchedWindow:
     def chain(self, stream=None):
         gs, pr, g2, gb = self.params.gaussians_struct(), self.proj(), self.grad2d(), self.grads.buffers_struct()
         L.gsr_batched_preprocess_bwd(ctypes.byref(gs), ctypes.byref(pr), self.cams, self.V, ctypes.byref(self.tiling),
-                                     ctypes.byref(g2), ctypes.byref(gb), _stream(stream))
+                                     ctypes.byref(g2), ctypes.byref(gb), _p(self.touched), _stream(stream))
 
     STAGES = ("preprocess", "bin_sort", "iterate", "chain", "adam")
 
     def _stage(self, name: str, stream=None):
         if name == "adam":
-            self.adam.step(self.grads, stream)
+            self.adam.step(self.grads, stream, touched=self.touched)
         else:
             getattr(self, name)(stream)
 

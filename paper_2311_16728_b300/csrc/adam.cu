@@ -20,8 +20,12 @@ struct AdamK {
     float b1, b2, eps;
 };
 
-// one thread per float4 of the 15 planes (mean_op, quat, logscale, sh x 12)
-__global__ void __launch_bounds__(256) adam_kernel(AdamK a, const int32_t *__restrict__ d_step) {
+// One thread per float4 of the 15 planes (mean_op, quat, logscale, sh x 12).
+// With `touched` (n flags), a Gaussian whose flag is 0 has a zero gradient
+// by contract: its gradient is neither read nor rewritten (a quarter of the
+// step's bytes for every Gaussian no view saw).
+__global__ void __launch_bounds__(256) adam_kernel(AdamK a, const int32_t *__restrict__ d_step,
+                                                   const uint32_t *__restrict__ touched) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= 15 * a.n) return;
     const int plane = (int)(e / a.n);
@@ -39,7 +43,9 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamK a, const int32_t *__res
     const float bc2 = -expm1f((float)t * log1pf(a.b2 - 1.0f));
     const float ibc1 = 1.0f / bc1, ibc2 = 1.0f / bc2;
     float4 *pp = a.p[which] + off, *gp = a.g[which] + off, *mp = a.m[which] + off, *vp = a.v[which] + off;
-    float4 p = *pp, g = *gp, m = *mp, v = *vp;
+    const bool live = touched == nullptr || __ldg(touched + i) != 0u;
+    float4 p = *pp, m = *mp, v = *vp;
+    const float4 g = live ? *gp : make_float4(0.f, 0.f, 0.f, 0.f);
 #define ADAM_LANE(c)                                                       \
     m.c = a.b1 * m.c + (1.0f - a.b1) * g.c;                                \
     v.c = a.b2 * v.c + (1.0f - a.b2) * g.c * g.c;                          \
@@ -52,7 +58,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamK a, const int32_t *__res
     *pp = p;
     *mp = m;
     *vp = v;
-    *gp = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) *gp = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void step_advance_kernel(int32_t *d_step) { *d_step += 1; }
@@ -92,9 +98,9 @@ __global__ void __launch_bounds__(256) pyramid_down_kernel(const float *__restri
 
 using namespace gsr;
 
-extern "C" int32_t gsr_adam_step(const gsr_param_buffers *params, const gsr_param_buffers *grads,
-                                 const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
-                                 const gsr_adam_config *cfg, int32_t *d_step, gsr_stream_t stream) {
+static int32_t adam_step(const gsr_param_buffers *params, const gsr_param_buffers *grads,
+                         const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
+                         const gsr_adam_config *cfg, const uint32_t *touched, int32_t *d_step, gsr_stream_t stream) {
     const gsr_param_buffers *bufs[4] = {params, grads, m, v};
     if (!cfg || !d_step || n < 0) {
         set_error("gsr_adam_step: bad arguments");
@@ -126,10 +132,27 @@ extern "C" int32_t gsr_adam_step(const gsr_param_buffers *params, const gsr_para
         a.lr_scale = cfg->lr_scale; a.lr_sh = cfg->lr_sh;
         a.b1 = cfg->beta1; a.b2 = cfg->beta2; a.eps = cfg->eps;
         const int64_t total = 15 * n;
-        adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, d_step);
+        adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, d_step, touched);
     }
     step_advance_kernel<<<1, 1, 0, st>>>(d_step);
     return check_launch("adam_kernel");
+}
+
+extern "C" int32_t gsr_adam_step(const gsr_param_buffers *params, const gsr_param_buffers *grads,
+                                 const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
+                                 const gsr_adam_config *cfg, int32_t *d_step, gsr_stream_t stream) {
+    return adam_step(params, grads, m, v, n, cfg, nullptr, d_step, stream);
+}
+
+extern "C" int32_t gsr_adam_step_touched(const gsr_param_buffers *params, const gsr_param_buffers *grads,
+                                         const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
+                                         const gsr_adam_config *cfg, const uint32_t *touched, int32_t *d_step,
+                                         gsr_stream_t stream) {
+    if (!touched && n > 0) {
+        set_error("gsr_adam_step_touched: NULL flags");
+        return GSR_ERR_INVALID_ARG;
+    }
+    return adam_step(params, grads, m, v, n, cfg, touched, d_step, stream);
 }
 
 extern "C" int32_t gsr_pyramid_down(const float *in, int32_t C, int32_t H, int32_t W, float *out,

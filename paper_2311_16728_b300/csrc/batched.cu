@@ -284,10 +284,13 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
                                                                     float4 *__restrict__ g0, float4 *__restrict__ g1,
                                                                     float4 *__restrict__ g2, float4 *__restrict__ d_mo,
                                                                     float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
-                                                                    float4 *__restrict__ d_sh) {
+                                                                    float4 *__restrict__ d_sh,
+                                                                    uint32_t *__restrict__ touched) {
     extern __shared__ uint32_t s_rec[];  // kChainChunk x ngroups candidates
     __shared__ uint32_t s_cnt;
+    __shared__ uint32_t s_touch[kChainChunk];
     if (threadIdx.x == 0) s_cnt = 0u;
+    for (int k = threadIdx.x; k < kChainChunk; k += kBwdThreads) s_touch[k] = 0u;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kChainChunk;
     const int lane = threadIdx.x & 31;
@@ -302,9 +305,15 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
         uint32_t slot = 0;
         if (lane == 0 && msk) slot = atomicAdd(&s_cnt, (uint32_t)__popc(msk));
         slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (vis) s_rec[slot + __popc(msk & ((1u << lane) - 1u))] = ((uint32_t)grp << 16) | (uint32_t)il;
+        if (vis) {
+            s_rec[slot + __popc(msk & ((1u << lane) - 1u))] = ((uint32_t)grp << 16) | (uint32_t)il;
+            s_touch[il] = 1u;
+        }
     }
     __syncthreads();
+    if (touched)
+        for (int k = threadIdx.x; k < kChainChunk; k += kBwdThreads)
+            if (base + k < g.n) touched[base + k] = s_touch[k];
     const uint32_t cnt = s_cnt;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
         const int grp = (int)(s_rec[k] >> 16);
@@ -549,7 +558,8 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
 
 extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
                                               int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
-                                              const gsr_param_buffers *grads, gsr_stream_t stream) {
+                                              const gsr_param_buffers *grads, uint32_t *touched,
+                                              gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_gaussians(g)) || (rc = validate_tiling(tiling))) return rc;
     ViewsK V;
@@ -572,6 +582,6 @@ extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_
         reinterpret_cast<const float4 *>(proj->c_op_box), proj->ntiles, reinterpret_cast<float4 *>(grad2d->g0),
         reinterpret_cast<float4 *>(grad2d->g1), reinterpret_cast<float4 *>(grad2d->g2),
         reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),
-        reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh));
+        reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh), touched);
     return check_launch("batched_chain_kernel");
 }

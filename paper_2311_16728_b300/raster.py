@@ -276,10 +276,17 @@ class Adam:
         self.step_count = torch.zeros(1, dtype=torch.int32, device=params.mean_op.device)
         self._cfg = cfg.struct()
 
-    def step(self, grads: Gaussians, stream=None):
+    def step(self, grads: Gaussians, stream=None, touched: Optional[torch.Tensor] = None):
+        """One step; `touched` (n int32 flags, optional): Gaussians whose flag is
+        0 are known to have a zero gradient, which is then not read."""
         p, g, m, v = (x.buffers_struct() for x in (self.params, grads, self.m, self.v))
-        L.gsr_adam_step(ctypes.byref(p), ctypes.byref(g), ctypes.byref(m), ctypes.byref(v), self.params.n,
-                        ctypes.byref(self._cfg), _p(self.step_count), _stream(stream))
+        if touched is None:
+            L.gsr_adam_step(ctypes.byref(p), ctypes.byref(g), ctypes.byref(m), ctypes.byref(v), self.params.n,
+                            ctypes.byref(self._cfg), _p(self.step_count), _stream(stream))
+        else:
+            L.gsr_adam_step_touched(ctypes.byref(p), ctypes.byref(g), ctypes.byref(m), ctypes.byref(v),
+                                    self.params.n, ctypes.byref(self._cfg), _p(touched), _p(self.step_count),
+                                    _stream(stream))
 
 
 def pyramid(img: torch.Tensor, levels: int = PYRAMID_LEVELS, stream=None):
@@ -360,7 +367,8 @@ class MappingStep:
         elif name == "preprocess_bwd":
             vb.preprocess_bwd(self.params, self.grads, stream=stream)
         elif name == "adam":
-            self.adam.step(self.grads, stream)
+            # the one-view backward writes gradients exactly where ntiles > 0
+            self.adam.step(self.grads, stream, touched=vb.ntiles if self.params.n else None)
 
     def _run(self, idx: int, stream=None):
         for name in STAGES:

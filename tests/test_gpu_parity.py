@@ -222,6 +222,34 @@ def test_adam_matches_oracle():
     assert float(flat(grads).__abs__().max()) == 0.0  # gradients zeroed
 
 
+def test_adam_touched_flags_equal_dense_step():
+    """Gradients zero where the flag is 0: the flagged step skips them and must
+    leave parameters, moments and (zeroed) gradients bit-identical to the
+    dense step."""
+    rng = np.random.default_rng(4)
+    n = 3000
+    arr = lambda: (rng.standard_normal((n, 4)), rng.standard_normal((n, 4)), rng.standard_normal((n, 4)),
+                   rng.standard_normal((12, n, 4)))
+    p_arr, g_arr, m_arr, v_arr = arr(), list(arr()), arr(), arr()
+    flags = (rng.random(n) < 0.2).astype(np.int32)
+    for t in g_arr[:3]:
+        t[flags == 0] = 0.0
+    g_arr[3][:, flags == 0] = 0.0
+    outs = []
+    for touched in (None, torch.tensor(flags, device="cuda")):
+        params = gsr.Gaussians.from_arrays(*p_arr)
+        grads = gsr.Gaussians.from_arrays(*g_arr)
+        opt = gsr.Adam(params, gsr.AdamConfig())
+        opt.m = gsr.Gaussians.from_arrays(*m_arr)
+        opt.v = gsr.Gaussians(*(t.abs() for t in gsr.Gaussians.from_arrays(*v_arr).tensors()))
+        opt.step_count.fill_(2)
+        opt.step(grads, touched=touched)
+        torch.cuda.synchronize()
+        outs.append([t.clone() for x in (params, opt.m, opt.v, grads) for t in x.tensors()])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 def test_pyramid_and_psnr_match_oracle():
     x = S.random_image(3, 37, 53, seed=4)
     lv = gsr.pyramid(torch.tensor(x, device="cuda"), 3)
