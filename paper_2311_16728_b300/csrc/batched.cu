@@ -195,7 +195,7 @@ __device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
     return v;
 }
 
-__global__ void __launch_bounds__(kIterThreads, 8) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
+__global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
     extern __shared__ float4 smem4[];
     float *smf = reinterpret_cast<float *>(smem4);
     __shared__ int s_item, s_ok;

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__
     render_fwd_tile(a, blockIdx.x, img, T_final, n_contrib, n_blended, smem);
 }
 
-__global__ void __launch_bounds__(512) render_bwd_kernel(RenderArgs a, const float *__restrict__ T_final,
+__global__ void __maxnreg__(80) render_bwd_kernel(RenderArgs a, const float *__restrict__ T_final,
                                                          const uint32_t *__restrict__ n_contrib,
                                                          const float *__restrict__ dL_dimg, float *__restrict__ g0,
                                                          float *__restrict__ g1, float *__restrict__ g2) {

@@ -78,6 +78,49 @@ __device__ __forceinline__ bool splat_alpha(float e2, float op, Eval &r) {
     return r.alpha >= kAlphaMin;
 }
 
+// alpha of one staged splat at this thread's two pixels (px, py0), (px, py0 + 1);
+// ok = inside the pixel box and alpha >= 1/255
+struct PixAlpha {
+    float a0, a1;
+    bool ok0, ok1;
+};
+
+__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, int px, float fpx, float fpy0,
+                                                 float fpy1, int py0, PixAlpha &r) {
+    const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
+    const bool xin = px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16);
+    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+    const float dx = fpx - g.x;
+    const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
+    const float dy0 = fpy0 - g.y, dy1 = fpy1 - g.y;
+    const float e0 = __fmaf_rn(FM(cb.x, dy0), dy0, __fmaf_rn(bdx, dy0, t));
+    const float e1 = __fmaf_rn(FM(cb.x, dy1), dy1, __fmaf_rn(bdx, dy1, t));
+    Eval v0, v1;
+    r.ok0 = xin && py0 >= y0 && py0 <= y1 && splat_alpha(e0, cb.y, v0);
+    r.ok1 = xin && py0 + 1 >= y0 && py0 + 1 <= y1 && splat_alpha(e1, cb.y, v1);
+    r.a0 = v0.alpha;
+    r.a1 = v1.alpha;
+}
+
+// front-to-back blend of one evaluated splat into one pixel's state
+__device__ __forceinline__ void blend_fwd(bool ok, float alpha, const float4 *s_rgb, int j, uint32_t pos, bool &done,
+                                          float &T, float &C0, float &C1, float &C2, uint32_t &last, uint32_t &nb) {
+    if (!ok || done) return;
+    const float tn = FM(T, FS(1.0f, alpha));
+    if (tn < kTMin) {
+        done = true;
+        return;
+    }
+    const float4 col = s_rgb[j];
+    const float w = alpha * T;
+    C0 += col.x * w;
+    C1 += col.y * w;
+    C2 += col.z * w;
+    T = tn;
+    last = pos;
+    ++nb;
+}
+
 // ---------------------------------------------------------------- K5
 // One tile (local index `tile` of the view in `a`), by the whole block.
 __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, float *__restrict__ img,
@@ -109,56 +152,23 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
             // warp-ballot early termination: leave once no pixel of the warp accumulates
             if (__all_sync(0xffffffffu, done0 && done1)) break;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            // two splats per round: their alphas are independent, so both are
+            // evaluated before they are blended in list order
             while (bits) {
-                const int j = c0 + __ffs(bits) - 1;
+                const int ja = c0 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                const float4 g = s_xy[j], cb = s_cb[j];
-                const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
-                if (px < (int)(bx & 0xffffu) || px > (int)(bx >> 16)) continue;
-                const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
-                const float dx = fpx - g.x;
-                const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
-                const uint32_t pos = (uint32_t)(base - begin + j + 1);
-                if (!done0 && py0 >= y0 && py0 <= y1) {
-                    const float dy = fpy0 - g.y;
-                    const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
-                    Eval ev;
-                    if (splat_alpha(e2, cb.y, ev)) {
-                        const float tn = FM(T0, FS(1.0f, ev.alpha));
-                        if (tn < kTMin) {
-                            done0 = true;
-                        } else {
-                            const float4 col = s_rgb[j];
-                            const float w = ev.alpha * T0;
-                            C00 += col.x * w;
-                            C01 += col.y * w;
-                            C02 += col.z * w;
-                            T0 = tn;
-                            last0 = pos;
-                            ++nb0;
-                        }
-                    }
-                }
-                if (!done1 && py0 + 1 >= y0 && py0 + 1 <= y1) {
-                    const float dy = fpy1 - g.y;
-                    const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
-                    Eval ev;
-                    if (splat_alpha(e2, cb.y, ev)) {
-                        const float tn = FM(T1, FS(1.0f, ev.alpha));
-                        if (tn < kTMin) {
-                            done1 = true;
-                        } else {
-                            const float4 col = s_rgb[j];
-                            const float w = ev.alpha * T1;
-                            C10 += col.x * w;
-                            C11 += col.y * w;
-                            C12 += col.z * w;
-                            T1 = tn;
-                            last1 = pos;
-                            ++nb1;
-                        }
-                    }
-                }
+                const bool has_b = bits != 0u;
+                const int jb = has_b ? c0 + __ffs(bits) - 1 : ja;
+                if (has_b) bits &= bits - 1;
+                PixAlpha pa, pb;
+                pixel_pair_alpha(s_xy[ja], s_cb[ja], px, fpx, fpy0, fpy1, py0, pa);
+                pixel_pair_alpha(s_xy[jb], s_cb[jb], px, fpx, fpy0, fpy1, py0, pb);
+                if (!has_b) pb.ok0 = pb.ok1 = false;
+                const uint32_t posa = (uint32_t)(base - begin + ja + 1), posb = (uint32_t)(base - begin + jb + 1);
+                blend_fwd(pa.ok0, pa.a0, s_rgb, ja, posa, done0, T0, C00, C01, C02, last0, nb0);
+                blend_fwd(pb.ok0, pb.a0, s_rgb, jb, posb, done0, T0, C00, C01, C02, last0, nb0);
+                blend_fwd(pa.ok1, pa.a1, s_rgb, ja, posa, done1, T1, C10, C11, C12, last1, nb1);
+                blend_fwd(pb.ok1, pb.a1, s_rgb, jb, posb, done1, T1, C10, C11, C12, last1, nb1);
             }
         }
     }
@@ -196,11 +206,10 @@ struct PixelBwd {
     uint32_t last;
 };
 
-// Adds this pixel's contribution of splat j to v[9]; returns whether it had one.
-__device__ __forceinline__ bool pixel_bwd(PixelBwd &p, float e2, float op, float dx, float dy, float A, float B,
-                                          float C, const float4 &col, float v[9]) {
-    Eval ev;
-    if (!splat_alpha(e2, op, ev)) return false;
+// Adds the contribution of a splat with (already evaluated) alpha to this
+// pixel's state and to v[9].
+__device__ __forceinline__ void pixel_bwd_update(PixelBwd &p, const Eval &ev, float dx, float dy, float A, float B,
+                                                 float C, const float4 &col, float v[9]) {
     const float one_m = 1.0f - ev.alpha;
     p.T = __fdividef(p.T, one_m);  // transmittance in front of this Gaussian
     const float aT = ev.alpha * p.T;
@@ -220,7 +229,34 @@ __device__ __forceinline__ bool pixel_bwd(PixelBwd &p, float e2, float op, float
         v[3] += -dx * dy * dpow;
         v[4] += -0.5f * dy * dy * dpow;
     }
-    return true;
+}
+
+// A staged splat seen from this thread's two pixels: offsets, the original
+// conic for the gradient formulas, and each pixel's alpha (ok = the pixel
+// has a contribution: inside the box, before its last contributor, alpha
+// above the skip threshold).
+struct SplatBwd {
+    float dx, dy0, dy1, A, B, C;
+    Eval e0, e1;
+    bool ok0, ok1;
+};
+
+__device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, int px, float fpx, float fpy0,
+                                               float fpy1, int py0, bool live0, bool live1, SplatBwd &r) {
+    const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
+    const bool xin = px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16);
+    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+    r.dx = fpx - g.x;
+    const float t = FM(FM(g.z, r.dx), r.dx), bdx = FM(g.w, r.dx);
+    r.dy0 = fpy0 - g.y;
+    r.dy1 = fpy1 - g.y;
+    const float e0 = __fmaf_rn(FM(cb.x, r.dy0), r.dy0, __fmaf_rn(bdx, r.dy0, t));
+    const float e1 = __fmaf_rn(FM(cb.x, r.dy1), r.dy1, __fmaf_rn(bdx, r.dy1, t));
+    r.A = g.z * (1.0f / kHalfLog2e);
+    r.B = g.w * (0.5f / kHalfLog2e);
+    r.C = cb.x * (1.0f / kHalfLog2e);
+    r.ok0 = live0 && xin && py0 >= y0 && py0 <= y1 && splat_alpha(e0, cb.y, r.e0);
+    r.ok1 = live1 && xin && py0 + 1 >= y0 && py0 + 1 <= y1 && splat_alpha(e1, cb.y, r.e1);
 }
 
 // Sums v[0..8] over the warp without broadcasting every value: each halving
@@ -318,38 +354,41 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
         const int cnt = bend - bstart;
         for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            // two splats per round, back to front: both are evaluated first
+            // (independent), then applied in order, then reduced together
             while (bits) {
-                const int jj = 31 - __clz(bits);
-                bits &= ~(1u << jj);
-                const int j = c0 + jj;
-                const uint32_t pos = (uint32_t)(bstart + j - begin);  // 0-based position in the tile list
-                float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                bool any = false;
-                const float4 g = s_xy[j], cb = s_cb[j];
-                const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
-                if (px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16) && (pos < p0.last || pos < p1.last)) {
-                    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
-                    const float dx = fpx - g.x;
-                    const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
-                    // original conic for the gradient formulas
-                    const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e),
-                                C = cb.x * (1.0f / kHalfLog2e);
-                    const float4 col = s_rgb[j];
-                    if (pos < p0.last && py0 >= y0 && py0 <= y1) {
-                        const float dy = fpy0 - g.y;
-                        const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
-                        any |= pixel_bwd(p0, e2, cb.y, dx, dy, A, B, C, col, v);
-                    }
-                    if (pos < p1.last && py0 + 1 >= y0 && py0 + 1 <= y1) {
-                        const float dy = fpy1 - g.y;
-                        const float e2 = __fmaf_rn(FM(cb.x, dy), dy, __fmaf_rn(bdx, dy, t));
-                        any |= pixel_bwd(p1, e2, cb.y, dx, dy, A, B, C, col, v);
-                    }
+                const int ja = c0 + 31 - __clz(bits);
+                bits &= ~(1u << (ja - c0));
+                const bool has_b = bits != 0u;
+                const int jb = has_b ? c0 + 31 - __clz(bits) : ja;
+                if (has_b) bits &= ~(1u << (jb - c0));
+                const uint32_t posa = (uint32_t)(bstart + ja - begin), posb = (uint32_t)(bstart + jb - begin);
+                SplatBwd sa, sb;
+                splat_bwd_eval(s_xy[ja], s_cb[ja], px, fpx, fpy0, fpy1, py0, posa < p0.last, posa < p1.last, sa);
+                splat_bwd_eval(s_xy[jb], s_cb[jb], px, fpx, fpy0, fpy1, py0, has_b && posb < p0.last,
+                               has_b && posb < p1.last, sb);
+                float va[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float vb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (sa.ok0 || sa.ok1 || sb.ok0 || sb.ok1) {
+                    const float4 cola = s_rgb[ja], colb = s_rgb[jb];
+                    if (sa.ok0) pixel_bwd_update(p0, sa.e0, sa.dx, sa.dy0, sa.A, sa.B, sa.C, cola, va);
+                    if (sb.ok0) pixel_bwd_update(p0, sb.e0, sb.dx, sb.dy0, sb.A, sb.B, sb.C, colb, vb);
+                    if (sa.ok1) pixel_bwd_update(p1, sa.e1, sa.dx, sa.dy1, sa.A, sa.B, sa.C, cola, va);
+                    if (sb.ok1) pixel_bwd_update(p1, sb.e1, sb.dx, sb.dy1, sb.A, sb.B, sb.C, colb, vb);
                 }
-                if (__any_sync(0xffffffffu, any)) {
+                const bool anya = __any_sync(0xffffffffu, sa.ok0 || sa.ok1);
+                const bool anyb = __any_sync(0xffffffffu, sb.ok0 || sb.ok1);
+                if (anya) {
                     float v8;
-                    const float y = warp_transpose_sum(v, v8);
-                    const uint32_t gid = s_gid[j];
+                    const float y = warp_transpose_sum(va, v8);
+                    const uint32_t gid = s_gid[ja];
+                    if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
+                    else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+                }
+                if (anyb) {
+                    float v8;
+                    const float y = warp_transpose_sum(vb, v8);
+                    const uint32_t gid = s_gid[jb];
                     if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
                     else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
                 }
