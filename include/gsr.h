@@ -444,8 +444,10 @@ typedef struct {
 /* One fused Adam step over all n Gaussians' 60-float records (the log-scale
  * pad has zero gradient and never moves): m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
- * with t = *d_step + 1, then zeroes the gradients and increments *d_step
- * (device int32) so that a captured graph can replay it. */
+ * with t = *d_step + 1 (FP32; the square root and the division use the fast
+ * reciprocal square root and reciprocal, a few 1e-7 relative error on the
+ * update), then zeroes the gradients and increments *d_step (device int32)
+ * so that a captured graph can replay it. */
 int32_t gsr_adam_step(const gsr_param_buffers *params, const gsr_param_buffers *grads,
                       const gsr_param_buffers *m, const gsr_param_buffers *v, int64_t n,
                       const gsr_adam_config *cfg, int32_t *d_step, gsr_stream_t stream);

@@ -20,45 +20,76 @@ struct AdamK {
     float b1, b2, eps;
 };
 
-// One thread per float4 of the 15 planes (mean_op, quat, logscale, sh x 12).
-// With `touched` (n flags), a Gaussian whose flag is 0 has a zero gradient
-// by contract: its gradient is neither read nor rewritten (a quarter of the
+// blockIdx.y is the plane (mean_op, quat, logscale, sh x 12); each thread
+// updates the float4 of two Gaussians (i and i + 256), loading both before
+// computing.  The bias corrections are computed once per block.  With
+// `touched` (n flags), a Gaussian whose flag is 0 has a zero gradient by
+// contract: its gradient is neither read nor rewritten (a quarter of the
 // step's bytes for every Gaussian no view saw).
-__global__ void __launch_bounds__(256) adam_kernel(AdamK a, const int32_t *__restrict__ d_step,
-                                                   const uint32_t *__restrict__ touched) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 15 * a.n) return;
-    const int plane = (int)(e / a.n);
-    const int64_t i = e - (int64_t)plane * a.n;
+constexpr int kAdamThreads = 256;
+constexpr int kAdamPer = 2;
+
+__device__ __forceinline__ float adam_delta(float lr, float m, float v, float ibc1, float ibc2, float eps) {
+    // lr m_hat / (sqrt(v_hat) + eps), with sqrt(x) = x rsqrt(x) (x > 0) and a
+    // fast reciprocal: relative error a few 1e-7 on the update
+    const float vh = v * ibc2;
+    const float root = vh > 0.0f ? vh * rsqrtf(vh) : 0.0f;
+    return __fdividef(lr * (m * ibc1), root + eps);
+}
+
+__global__ void __launch_bounds__(kAdamThreads) adam_kernel(AdamK a, const int32_t *__restrict__ d_step,
+                                                            const uint32_t *__restrict__ touched) {
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) {
+        const int t = *d_step + 1;
+        // 1 - b^t = -expm1(t log1p(b - 1)): no cancellation for b near 1 (b - 1 is exact)
+        s_bc[0] = 1.0f / -expm1f((float)t * log1pf(a.b1 - 1.0f));
+        s_bc[1] = 1.0f / -expm1f((float)t * log1pf(a.b2 - 1.0f));
+    }
+    __syncthreads();
+    const int plane = (int)blockIdx.y;
     const int which = plane < 3 ? plane : 3;
-    const int64_t off = plane < 3 ? i : (int64_t)(plane - 3) * a.n + i;
     float4 lr;
     if (which == 0) lr = make_float4(a.lr_mean, a.lr_mean, a.lr_mean, a.lr_opacity);
     else if (which == 1) lr = make_float4(a.lr_quat, a.lr_quat, a.lr_quat, a.lr_quat);
     else if (which == 2) lr = make_float4(a.lr_scale, a.lr_scale, a.lr_scale, a.lr_scale);
     else lr = make_float4(a.lr_sh, a.lr_sh, a.lr_sh, a.lr_sh);
-    const int t = *d_step + 1;
-    // 1 - b^t = -expm1(t log1p(b - 1)): no cancellation for b near 1 (b - 1 is exact)
-    const float bc1 = -expm1f((float)t * log1pf(a.b1 - 1.0f));
-    const float bc2 = -expm1f((float)t * log1pf(a.b2 - 1.0f));
-    const float ibc1 = 1.0f / bc1, ibc2 = 1.0f / bc2;
-    float4 *pp = a.p[which] + off, *gp = a.g[which] + off, *mp = a.m[which] + off, *vp = a.v[which] + off;
-    const bool live = touched == nullptr || __ldg(touched + i) != 0u;
-    float4 p = *pp, m = *mp, v = *vp;
-    const float4 g = live ? *gp : make_float4(0.f, 0.f, 0.f, 0.f);
-#define ADAM_LANE(c)                                                       \
-    m.c = a.b1 * m.c + (1.0f - a.b1) * g.c;                                \
-    v.c = a.b2 * v.c + (1.0f - a.b2) * g.c * g.c;                          \
-    p.c -= lr.c * (m.c * ibc1) / (sqrtf(v.c * ibc2) + a.eps);
-    ADAM_LANE(x)
-    ADAM_LANE(y)
-    ADAM_LANE(z)
-    ADAM_LANE(w)
+    const float ibc1 = s_bc[0], ibc2 = s_bc[1], b1 = a.b1, b2 = a.b2, eps = a.eps;
+    const int64_t plane_off = plane < 3 ? 0 : (int64_t)(plane - 3) * a.n;
+    float4 *const P = a.p[which] + plane_off, *const G = a.g[which] + plane_off, *const M = a.m[which] + plane_off,
+                  *const V = a.v[which] + plane_off;
+    const int64_t i0 = (int64_t)blockIdx.x * (kAdamThreads * kAdamPer) + threadIdx.x;
+    float4 p[kAdamPer], g[kAdamPer], m[kAdamPer], v[kAdamPer];
+    bool in[kAdamPer], live[kAdamPer];
+#pragma unroll
+    for (int r = 0; r < kAdamPer; ++r) {
+        const int64_t i = i0 + r * kAdamThreads;
+        in[r] = i < a.n;
+        live[r] = in[r] && (touched == nullptr || __ldg(touched + i) != 0u);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        p[r] = in[r] ? P[i] : z;
+        m[r] = in[r] ? M[i] : z;
+        v[r] = in[r] ? V[i] : z;
+        g[r] = live[r] ? G[i] : z;
+    }
+#pragma unroll
+    for (int r = 0; r < kAdamPer; ++r) {
+        if (!in[r]) continue;
+        const int64_t i = i0 + r * kAdamThreads;
+#define ADAM_LANE(c)                                             \
+    m[r].c = b1 * m[r].c + (1.0f - b1) * g[r].c;                 \
+    v[r].c = b2 * v[r].c + (1.0f - b2) * g[r].c * g[r].c;        \
+    p[r].c -= adam_delta(lr.c, m[r].c, v[r].c, ibc1, ibc2, eps);
+        ADAM_LANE(x)
+        ADAM_LANE(y)
+        ADAM_LANE(z)
+        ADAM_LANE(w)
 #undef ADAM_LANE
-    *pp = p;
-    *mp = m;
-    *vp = v;
-    if (live) *gp = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[i] = p[r];
+        M[i] = m[r];
+        V[i] = v[r];
+        if (live[r]) G[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 __global__ void step_advance_kernel(int32_t *d_step) { *d_step += 1; }
@@ -131,8 +162,8 @@ static int32_t adam_step(const gsr_param_buffers *params, const gsr_param_buffer
         a.lr_mean = cfg->lr_mean; a.lr_opacity = cfg->lr_opacity; a.lr_quat = cfg->lr_quat;
         a.lr_scale = cfg->lr_scale; a.lr_sh = cfg->lr_sh;
         a.b1 = cfg->beta1; a.b2 = cfg->beta2; a.eps = cfg->eps;
-        const int64_t total = 15 * n;
-        adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, d_step, touched);
+        adam_kernel<<<dim3((unsigned)((n + kAdamThreads * kAdamPer - 1) / (kAdamThreads * kAdamPer)), 15),
+                      kAdamThreads, 0, st>>>(a, d_step, touched);
     }
     step_advance_kernel<<<1, 1, 0, st>>>(d_step);
     return check_launch("adam_kernel");

@@ -76,12 +76,13 @@ __device__ __forceinline__ void add4(float4 *p, float4 v, bool atomic) {
 }
 
 // Chain rule of one Gaussian from its screen-space gradient in camera `cam`
-// (c = the forward chain of that camera) to the 59 parameters, added to the
-// gradient planes (atomically when several threads may add to the same
-// Gaussian).
-__device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int64_t i, const float4 mo, const Chain &c,
-                                           const ScreenGrad &sg, float4 *__restrict__ d_mo, float4 *__restrict__ d_q,
-                                           float4 *__restrict__ d_ls, float4 *__restrict__ d_sh, bool atomic) {
+// (c = the forward chain of that camera) to the 59 parameters.  Each plane's
+// gradient goes to sink(plane, value): planes 3 .. 3 + sh_planes - 1 (SH) as
+// soon as that SH plane has been read, then 0 (mean, opacity logit), 1
+// (quaternion), 2 (log-scale).
+template <class Sink>
+__device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, int64_t i, const float4 mo,
+                                              const Chain &c, const ScreenGrad &sg, Sink &sink) {
     const float du = sg.du, dv = sg.dv, dop = sg.dop;
     const float *W = cam.R;
     // ---- colour and SH, streamed one float4 plane at a time
@@ -127,7 +128,7 @@ __device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int
                 dvh.z += w * dY[k].z;
             }
         }
-        add4(d_sh + (int64_t)j * g.n + i, make_float4(d[0], d[1], d[2], d[3]), atomic);
+        sink(3 + j, make_float4(d[0], d[1], d[2], d[3]));
     }
     const float vd = dvh.x * vx + dvh.y * vy + dvh.z * vz;
     float dmx = (dvh.x - vx * vd) * inv_len, dmy = (dvh.y - vy * vd) * inv_len, dmz = (dvh.z - vz * vd) * inv_len;
@@ -230,10 +231,28 @@ __device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int
     dx2 = (dx2 - x * qd) * iq;
     dy2 = (dy2 - y * qd) * iq;
     dz2 = (dz2 - z * qd) * iq;
-    // ---- accumulate (+=)
-    add4(d_mo + i, make_float4(dmx, dmy, dmz, dlogit), atomic);
-    add4(d_q + i, make_float4(dw, dx2, dy2, dz2), atomic);
-    add4(d_ls + i, make_float4(dls[0], dls[1], dls[2], 0.0f), atomic);
+    sink(0, make_float4(dmx, dmy, dmz, dlogit));
+    sink(1, make_float4(dw, dx2, dy2, dz2));
+    sink(2, make_float4(dls[0], dls[1], dls[2], 0.0f));
+}
+
+// sink that adds into the gradient planes (atomically when several threads
+// may add to the same Gaussian)
+struct AddSink {
+    float4 *d_mo, *d_q, *d_ls, *d_sh;
+    int64_t n, i;
+    bool atomic;
+    __device__ __forceinline__ void operator()(int plane, float4 v) const {
+        float4 *p = plane == 0 ? d_mo + i : (plane == 1 ? d_q + i : (plane == 2 ? d_ls + i : d_sh + (int64_t)(plane - 3) * n + i));
+        add4(p, v, atomic);
+    }
+};
+
+__device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int64_t i, const float4 mo, const Chain &c,
+                                           const ScreenGrad &sg, float4 *__restrict__ d_mo, float4 *__restrict__ d_q,
+                                           float4 *__restrict__ d_ls, float4 *__restrict__ d_sh, bool atomic) {
+    AddSink sink{d_mo, d_q, d_ls, d_sh, g.n, i, atomic};
+    chain_core_to(g, cam, i, mo, c, sg, sink);
 }
 
 // One view: the screen-space gradient of record i (g0, g1, g2) chained into
