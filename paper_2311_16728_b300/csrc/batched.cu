@@ -29,7 +29,18 @@ struct ViewsK {
     CamK cam[kMaxViews];
 };
 
+// Views that share a pose (the pyramid levels of one keyframe) share the
+// camera-space mean, the near-plane test and the colour; the 3D covariance is
+// shared by every view.  Each record is bit-identical to gsr_preprocess's.
+constexpr int kPoseMax = 8;  // views per pose group
+struct PoseGroups {
+    int ngroups;
+    int count[kMaxViews];
+    int member[kMaxViews][kPoseMax];
+};
+
 __global__ void __launch_bounds__(128) batched_preprocess_kernel(GaussK g, const __grid_constant__ ViewsK V,
+                                                                 const __grid_constant__ PoseGroups PG,
                                                                  float4 *__restrict__ xy_conic,
                                                                  float4 *__restrict__ c_op_box,
                                                                  float4 *__restrict__ rgb_depth,
@@ -37,43 +48,75 @@ __global__ void __launch_bounds__(128) batched_preprocess_kernel(GaussK g, const
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+    Chain shape;
+    const bool shape_ok = chain_shape(q, ls, shape);
+    const float op = FD(1.0f, FA(1.0f, chain_exp(-mo.w)));
     float sh[48];
     bool have_sh = false;
     const int nc = (g.deg + 1) * (g.deg + 1);
-    for (int v = 0; v < V.nviews; ++v) {
-        const CamK &cam = V.cam[v];
-        const int64_t r = (int64_t)v * g.n + i;
-        Chain c;
-        if (!decide_chain(mo, q, ls, cam, c)) {
-            ntiles[r] = 0u;
-            continue;
-        }
-        float A, B, C, op;
-        chain_conic_opacity(c, mo.w, A, B, C, op);
-        if (!have_sh) {
-            load_sh(g.sh, g.n, i, g.deg, sh);
-            have_sh = true;
-        }
-        const float3 cc = cam_center(cam);
-        float dx = mo.x - cc.x, dy = mo.y - cc.y, dz = mo.z - cc.z;
-        const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv_len; dy *= inv_len; dz *= inv_len;
-        float Y[16];
-        sh_basis(dx, dy, dz, g.deg, Y, nullptr);
-        float rgb[3];
+    for (int grp = 0; grp < PG.ngroups; ++grp) {
+        Chain pose = shape;
+        const bool front = shape_ok && chain_camera(mo, V.cam[PG.member[grp][0]], pose);
+        float rgb[3] = {0.f, 0.f, 0.f};
+        bool have_rgb = false;
+        for (int k = 0; k < PG.count[grp]; ++k) {
+            const int v = PG.member[grp][k];
+            const CamK &cam = V.cam[v];
+            const int64_t r = (int64_t)v * g.n + i;
+            Chain c = pose;
+            if (!front || !chain_screen(cam, c)) {
+                ntiles[r] = 0u;
+                continue;
+            }
+            const float A = FD(c.c, c.det), B = -FD(c.b, c.det), C = FD(c.a, c.det);
+            if (!have_rgb) {
+                if (!have_sh) {
+                    load_sh(g.sh, g.n, i, g.deg, sh);
+                    have_sh = true;
+                }
+                const float3 cc = cam_center(cam);
+                float dx = mo.x - cc.x, dy = mo.y - cc.y, dz = mo.z - cc.z;
+                const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
+                dx *= inv_len; dy *= inv_len; dz *= inv_len;
+                float Y[16];
+                sh_basis(dx, dy, dz, g.deg, Y, nullptr);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.5f;
+                for (int ch = 0; ch < 3; ++ch) {
+                    float acc = 0.5f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < nc) acc += sh[3 * k + ch] * Y[k];
-            rgb[ch] = fmaxf(acc, 0.0f);
+                    for (int kk = 0; kk < 16; ++kk)
+                        if (kk < nc) acc += sh[3 * kk + ch] * Y[kk];
+                    rgb[ch] = fmaxf(acc, 0.0f);
+                }
+                have_rgb = true;
+            }
+            const uint32_t bx = (uint32_t)c.x0 | ((uint32_t)c.x1 << 16), by = (uint32_t)c.y0 | ((uint32_t)c.y1 << 16);
+            xy_conic[r] = make_float4(c.u, c.v, A, B);
+            c_op_box[r] = make_float4(C, op, __uint_as_float(bx), __uint_as_float(by));
+            rgb_depth[r] = make_float4(rgb[0], rgb[1], rgb[2], c.zc);
+            ntiles[r] = (uint32_t)((c.x1 / cam.tw - c.x0 / cam.tw + 1) * (c.y1 / cam.th - c.y0 / cam.th + 1));
         }
-        const uint32_t bx = (uint32_t)c.x0 | ((uint32_t)c.x1 << 16), by = (uint32_t)c.y0 | ((uint32_t)c.y1 << 16);
-        xy_conic[r] = make_float4(c.u, c.v, A, B);
-        c_op_box[r] = make_float4(C, op, __uint_as_float(bx), __uint_as_float(by));
-        rgb_depth[r] = make_float4(rgb[0], rgb[1], rgb[2], c.zc);
-        ntiles[r] = (uint32_t)((c.x1 / cam.tw - c.x0 / cam.tw + 1) * (c.y1 / cam.th - c.y0 / cam.th + 1));
+    }
+}
+
+// views with identical pose (R and t bit for bit), at most kPoseMax a group
+static void pose_groups(const gsr_camera *cams, int nviews, PoseGroups &G) {
+    G.ngroups = 0;
+    for (int v = 0; v < nviews; ++v) {
+        int found = -1;
+        for (int q = 0; q < G.ngroups && found < 0; ++q) {
+            if (G.count[q] >= kPoseMax) continue;
+            const gsr_camera &a = cams[G.member[q][0]], &b = cams[v];
+            bool same = true;
+            for (int k = 0; k < 9; ++k) same = same && a.R[k] == b.R[k];
+            for (int k = 0; k < 3; ++k) same = same && a.t[k] == b.t[k];
+            if (same) found = q;
+        }
+        if (found < 0) {
+            found = G.ngroups++;
+            G.count[found] = 0;
+        }
+        G.member[found][G.count[found]++] = v;
     }
 }
 
@@ -423,8 +466,10 @@ extern "C" int32_t gsr_batched_preprocess(const gsr_gaussians *g, const gsr_came
         set_error("gsr_batched_preprocess: output records must be non-NULL and 16-byte aligned");
         return GSR_ERR_INVALID_ARG;
     }
+    PoseGroups PG;
+    pose_groups(cams, nviews, PG);
     batched_preprocess_kernel<<<(unsigned)((g->n + 127) / 128), 128, 0, as_cuda(stream)>>>(
-        make_gk(g), V, reinterpret_cast<float4 *>(out->xy_conic), reinterpret_cast<float4 *>(out->c_op_box),
+        make_gk(g), V, PG, reinterpret_cast<float4 *>(out->xy_conic), reinterpret_cast<float4 *>(out->c_op_box),
         reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles);
     return check_launch("batched_preprocess_kernel");
 }

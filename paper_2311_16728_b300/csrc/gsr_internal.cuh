@@ -107,15 +107,10 @@ struct Chain {
     int x0, x1, y0, y1;      // inclusive clipped pixel box
 };
 
-// Returns false when the Gaussian is culled (behind the near plane, zero
-// quaternion, degenerate covariance or a box that misses the image).
-__device__ __forceinline__ bool decide_chain(const float4 mo, const float4 q, const float4 ls, const CamK &cam,
-                                             Chain &o) {
-    const float *R = cam.R;
-    o.xc = FA(FA(FA(FM(R[0], mo.x), FM(R[1], mo.y)), FM(R[2], mo.z)), cam.t[0]);
-    o.yc = FA(FA(FA(FM(R[3], mo.x), FM(R[4], mo.y)), FM(R[5], mo.z)), cam.t[1]);
-    o.zc = FA(FA(FA(FM(R[6], mo.x), FM(R[7], mo.y)), FM(R[8], mo.z)), cam.t[2]);
-    if (!(o.zc > kNear)) return false;
+// The view-independent part of the decision chain: scales, normalised
+// quaternion, its rotation and the 3D covariance (false for a zero
+// quaternion).
+__device__ __forceinline__ bool chain_shape(const float4 q, const float4 ls, Chain &o) {
     o.s[0] = chain_exp(ls.x);
     o.s[1] = chain_exp(ls.y);
     o.s[2] = chain_exp(ls.z);
@@ -144,16 +139,34 @@ __device__ __forceinline__ bool decide_chain(const float4 mo, const float4 q, co
         M[3 * i + 1] = FM(Rq[3 * i + 1], o.s[1]);
         M[3 * i + 2] = FM(Rq[3 * i + 2], o.s[2]);
     }
-    float S[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
             const float v = FA(FA(FM(M[3 * i], M[3 * j]), FM(M[3 * i + 1], M[3 * j + 1])), FM(M[3 * i + 2], M[3 * j + 2]));
-            S[3 * i + j] = v;
-            S[3 * j + i] = v;
+            const int k = i == 0 ? j : (i == 1 ? 2 + j : 5);  // xx xy xz yy yz zz
+            o.Sig[k] = v;
         }
-    o.Sig[0] = S[0]; o.Sig[1] = S[1]; o.Sig[2] = S[2]; o.Sig[3] = S[4]; o.Sig[4] = S[5]; o.Sig[5] = S[8];
+    return true;
+}
+
+// Camera-space mean and near-plane test of the decision chain.
+__device__ __forceinline__ bool chain_camera(const float4 mo, const CamK &cam, Chain &o) {
+    const float *R = cam.R;
+    o.xc = FA(FA(FA(FM(R[0], mo.x), FM(R[1], mo.y)), FM(R[2], mo.z)), cam.t[0]);
+    o.yc = FA(FA(FA(FM(R[3], mo.x), FM(R[4], mo.y)), FM(R[5], mo.z)), cam.t[1]);
+    o.zc = FA(FA(FA(FM(R[6], mo.x), FM(R[7], mo.y)), FM(R[8], mo.z)), cam.t[2]);
+    return o.zc > kNear;
+}
+
+// The rest of the chain for one camera (intrinsics and image of `cam`), from
+// the shape part and the camera-space mean already in o.
+__device__ __forceinline__ bool chain_screen(const CamK &cam, Chain &o) {
+    const float *R = cam.R;
+    float S[9];
+    S[0] = o.Sig[0]; S[1] = o.Sig[1]; S[2] = o.Sig[2];
+    S[3] = o.Sig[1]; S[4] = o.Sig[3]; S[5] = o.Sig[4];
+    S[6] = o.Sig[2]; S[7] = o.Sig[4]; S[8] = o.Sig[5];
     const float limx = FM(1.3f, FD(FM(0.5f, (float)cam.W), cam.fx));
     const float limy = FM(1.3f, FD(FM(0.5f, (float)cam.H), cam.fy));
     o.txz = FD(o.xc, o.zc);
@@ -194,6 +207,17 @@ __device__ __forceinline__ bool decide_chain(const float4 mo, const float4 q, co
     o.y0 = fy0 < 0.0f ? 0 : (int)fy0;
     o.y1 = fy1 > (float)(cam.H - 1) ? cam.H - 1 : (int)fy1;
     return o.x0 <= o.x1 && o.y0 <= o.y1;
+}
+
+// The whole decision chain of one Gaussian in one view: camera-space mean,
+// near plane, 3D covariance, EWA projection, 3-sigma radius, pixel box.
+// Returns false when the Gaussian is culled (behind the near plane, zero
+// quaternion, degenerate covariance or a box that misses the image).
+__device__ __forceinline__ bool decide_chain(const float4 mo, const float4 q, const float4 ls, const CamK &cam,
+                                             Chain &o) {
+    if (!chain_camera(mo, cam, o)) return false;
+    if (!chain_shape(q, ls, o)) return false;
+    return chain_screen(cam, o);
 }
 
 // Conic (inverse of the dilated 2D covariance) and opacity in the chain's
