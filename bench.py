@@ -730,7 +730,7 @@ def main():
 # with the current kernels (profiles/blend_kernels_300k_1200x680.md; the loss
 # stage is its two SSIM passes); absent when not captured for the current
 # kernel version.
-NCU_TRAFFIC = {"blend_bwd": 27.780352e6, "render_fwd": 10.625024e6, "loss": 19.688e6 + 49.609e6}
+NCU_TRAFFIC = {}
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20

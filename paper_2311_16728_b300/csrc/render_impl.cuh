@@ -18,12 +18,41 @@ struct RenderArgs {
 
 constexpr float kHalfLog2e = -0.5f * 1.4426950408889634f;  // exponent of 2 = kHalfLog2e * (d^T Q d)
 
-// pixel (px, py0) and (px, py0 + 1) of this thread; origin of the tile
+// Pixel (px, py0) and (px, py0 + 1) of this thread; origin of the tile.  In
+// a 16 x 16 tile each warp covers one 8 x 8 quadrant (its lanes: 8 columns x
+// 4 pixel pairs), a squarer footprint than 16 x 4 rows, so fewer splats touch
+// it; other tile shapes take rows of the tile in thread order.
+__device__ __forceinline__ bool quadrant_warps(const RenderArgs &a) { return a.tw == 16 && a.th == 16; }
+
 __device__ __forceinline__ void thread_pixels(const RenderArgs &a, int tile, int &px, int &py0, int &ox, int &oy) {
     ox = (tile % a.gx) * a.tw;
     oy = (tile / a.gx) * a.th;
-    px = ox + (int)threadIdx.x % a.tw;
-    py0 = oy + 2 * ((int)threadIdx.x / a.tw);
+    const int t = (int)threadIdx.x;
+    if (quadrant_warps(a)) {
+        const int w = t >> 5, l = t & 31;
+        px = ox + 8 * (w & 1) + (l & 7);
+        py0 = oy + 8 * (w >> 1) + 2 * (l >> 3);
+    } else {
+        px = ox + t % a.tw;
+        py0 = oy + 2 * (t / a.tw);
+    }
+}
+
+// pixel rectangle [rx0, rx1] x [ry0, ry1] of warp w (as thread_pixels maps it)
+__device__ __forceinline__ void warp_rect(const RenderArgs &a, int w, int ox, int oy, int &rx0, int &rx1, int &ry0,
+                                          int &ry1) {
+    if (quadrant_warps(a)) {
+        rx0 = ox + 8 * (w & 1);
+        rx1 = rx0 + 7;
+        ry0 = oy + 8 * (w >> 1);
+        ry1 = ry0 + 7;
+        return;
+    }
+    const int t0 = 32 * w, t1 = 32 * w + 31;
+    rx0 = a.tw >= 32 ? ox + t0 % a.tw : ox;
+    rx1 = a.tw >= 32 ? rx0 + 31 : ox + a.tw - 1;
+    ry0 = oy + 2 * (t0 / a.tw);
+    ry1 = oy + 2 * (t1 / a.tw) + 1;
 }
 
 // Stages Gaussian gid: exponent coefficients pre-scaled so that
@@ -48,11 +77,8 @@ __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, i
         const uint32_t bx = __float_as_uint(c.z), by = __float_as_uint(c.w);
         const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
         for (int w = 0; w < nwarps; ++w) {
-            // pixel rectangle of warp w: threads [32 w, 32 w + 32) of the tile
-            const int t0 = 32 * w, t1 = 32 * w + 31;
-            const int rx0 = a.tw >= 32 ? ox + t0 % a.tw : ox;
-            const int rx1 = a.tw >= 32 ? rx0 + 31 : ox + a.tw - 1;
-            const int ry0 = oy + 2 * (t0 / a.tw), ry1 = oy + 2 * (t1 / a.tw) + 1;
+            int rx0, rx1, ry0, ry1;
+            warp_rect(a, w, ox, oy, rx0, rx1, ry0, ry1);
             const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
             const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
             const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
