@@ -214,6 +214,14 @@ int32_t gsr_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const g
                            const gsr_tiling *tiling, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
                            float *densify_stat, float *densify_count, gsr_stream_t stream);
 
+/* gsr_preprocess_bwd that stores (=) instead of adding: the gradients of the
+ * Gaussians with ntiles > 0 are replaced, all others are left as they are.
+ * For callers whose gradients are zero before the pass (an optimiser step
+ * that zeroes them, as gsr_adam_step does), it saves reading them back. */
+int32_t gsr_preprocess_bwd_store(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                                 const gsr_tiling *tiling, const gsr_grad2d *g2d, const gsr_param_buffers *grads,
+                                 float *densify_stat, float *densify_count, gsr_stream_t stream);
+
 /* Backward of Eq. 3 then of the projection.  Replays each pixel back to
  * front from T_final and n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i)
  * instead of storing per-pixel lists; per-Gaussian screen-space gradients are

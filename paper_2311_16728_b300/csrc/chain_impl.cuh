@@ -237,21 +237,23 @@ __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, 
 }
 
 // sink that adds into the gradient planes (atomically when several threads
-// may add to the same Gaussian)
+// may add to the same Gaussian), or stores into them (store: the caller's
+// gradients of this Gaussian are replaced)
 struct AddSink {
     float4 *d_mo, *d_q, *d_ls, *d_sh;
     int64_t n, i;
-    bool atomic;
+    bool atomic, store;
     __device__ __forceinline__ void operator()(int plane, float4 v) const {
         float4 *p = plane == 0 ? d_mo + i : (plane == 1 ? d_q + i : (plane == 2 ? d_ls + i : d_sh + (int64_t)(plane - 3) * n + i));
-        add4(p, v, atomic);
+        if (store) *p = v;
+        else add4(p, v, atomic);
     }
 };
 
 __device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int64_t i, const float4 mo, const Chain &c,
                                            const ScreenGrad &sg, float4 *__restrict__ d_mo, float4 *__restrict__ d_q,
                                            float4 *__restrict__ d_ls, float4 *__restrict__ d_sh, bool atomic) {
-    AddSink sink{d_mo, d_q, d_ls, d_sh, g.n, i, atomic};
+    AddSink sink{d_mo, d_q, d_ls, d_sh, g.n, i, atomic, false};
     chain_core_to(g, cam, i, mo, c, sg, sink);
 }
 
@@ -262,7 +264,7 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
                                                    const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
                                                    float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
                                                    float4 *__restrict__ d_sh, float *__restrict__ dstat,
-                                                   float *__restrict__ dcount) {
+                                                   float *__restrict__ dcount, bool store = false) {
     const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
     Chain c;
     if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
@@ -281,7 +283,8 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
     sg.dr = G1.z;
     sg.dg = G1.w;
     sg.db = G2.x;
-    chain_core(g, cam, i, mo, c, sg, d_mo, d_q, d_ls, d_sh, false);
+    AddSink sink{d_mo, d_q, d_ls, d_sh, g.n, i, false, store};
+    chain_core_to(g, cam, i, mo, c, sg, sink);
 }
 
 }  // namespace gsr

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussK g, CamK cam,
     if (active) ntiles[i] = vis ? cnt : 0u;
 }
 
+template <bool kStore>
 __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, CamK cam, const uint32_t *__restrict__ ntiles,
                                                                      const float4 *__restrict__ g0,
                                                                      const float4 *__restrict__ g1,
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, C
     __syncthreads();
     const uint32_t cnt = s_cnt;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads)
-        chain_one_gaussian(g, cam, base + s_idx[k], g0, g1, g2, d_mo, d_q, d_ls, d_sh, dstat, dcount);
+        chain_one_gaussian(g, cam, base + s_idx[k], g0, g1, g2, d_mo, d_q, d_ls, d_sh, dstat, dcount, kStore);
 }
 
 }  // namespace gsr
@@ -110,30 +111,44 @@ extern "C" int32_t gsr_preprocess(const gsr_gaussians *g, const gsr_camera *cam,
     return check_launch("preprocess_fwd_kernel");
 }
 
-extern "C" int32_t gsr_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
-                                      const gsr_tiling *tiling, const gsr_grad2d *g2d,
-                                      const gsr_param_buffers *grads, float *densify_stat, float *densify_count,
-                                      gsr_stream_t stream) {
+static int32_t preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                              const gsr_tiling *tiling, const gsr_grad2d *g2d, const gsr_param_buffers *grads,
+                              float *densify_stat, float *densify_count, bool store, gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_gaussians(g)) || (rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
     if (g->n == 0) return GSR_OK;
     if (!proj || !proj->ntiles || !g2d || !g2d->g0 || !g2d->g1 || !g2d->g2 || !grads || !grads->mean_op ||
         !grads->quat || !grads->logscale || !grads->sh || (densify_stat != nullptr) != (densify_count != nullptr)) {
-        set_error("gsr_preprocess_bwd: NULL pointer");
+        set_error("preprocess_bwd: NULL pointer");
         return GSR_ERR_INVALID_ARG;
     }
     if (!aligned16(g2d->g0) || !aligned16(g2d->g1) || !aligned16(g2d->g2) || !aligned16(grads->mean_op) ||
         !aligned16(grads->quat) || !aligned16(grads->logscale) || !aligned16(grads->sh)) {
-        set_error("gsr_preprocess_bwd: gradient buffers must be 16-byte aligned");
+        set_error("preprocess_bwd: gradient buffers must be 16-byte aligned");
         return GSR_ERR_INVALID_ARG;
     }
     const CamK ck = make_camk(cam, tiling);
     const int64_t blocks = (g->n + kBwdChunk - 1) / kBwdChunk;
-    preprocess_bwd_kernel<<<(unsigned)blocks, kBwdThreads, 0, as_cuda(stream)>>>(
+    auto kernel = store ? preprocess_bwd_kernel<true> : preprocess_bwd_kernel<false>;
+    kernel<<<(unsigned)blocks, kBwdThreads, 0, as_cuda(stream)>>>(
         make_gk(g), ck, proj->ntiles, reinterpret_cast<const float4 *>(g2d->g0),
         reinterpret_cast<const float4 *>(g2d->g1), reinterpret_cast<const float4 *>(g2d->g2),
         reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),
         reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh), densify_stat,
         densify_count);
     return check_launch("preprocess_bwd_kernel");
+}
+
+extern "C" int32_t gsr_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                                      const gsr_tiling *tiling, const gsr_grad2d *g2d,
+                                      const gsr_param_buffers *grads, float *densify_stat, float *densify_count,
+                                      gsr_stream_t stream) {
+    return preprocess_bwd(g, proj, cam, tiling, g2d, grads, densify_stat, densify_count, false, stream);
+}
+
+extern "C" int32_t gsr_preprocess_bwd_store(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                                            const gsr_tiling *tiling, const gsr_grad2d *g2d,
+                                            const gsr_param_buffers *grads, float *densify_stat,
+                                            float *densify_count, gsr_stream_t stream) {
+    return preprocess_bwd(g, proj, cam, tiling, g2d, grads, densify_stat, densify_count, true, stream);
 }

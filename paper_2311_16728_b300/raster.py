@@ -189,11 +189,14 @@ class ViewBuffers:
                         ctypes.byref(self.tiling), bga, _p(self.T_final), _p(self.n_contrib), _p(d), ctypes.byref(g2),
                         _stream(stream))
 
-    def preprocess_bwd(self, g: Gaussians, grads: Gaussians, densify_stat=None, densify_count=None, stream=None):
+    def preprocess_bwd(self, g: Gaussians, grads: Gaussians, densify_stat=None, densify_count=None, stream=None,
+                       store: bool = False):
+        """Chain rule into `grads`: += (default), or = for the visible
+        Gaussians when the caller knows their gradients are zero."""
         gs, proj, g2, gb = g.gaussians_struct(), self.proj_struct(), self.grad2d_struct(), grads.buffers_struct()
-        L.gsr_preprocess_bwd(ctypes.byref(gs), ctypes.byref(proj), ctypes.byref(self.cam), ctypes.byref(self.tiling),
-                             ctypes.byref(g2), ctypes.byref(gb), _p(densify_stat), _p(densify_count),
-                             _stream(stream))
+        fn = L.gsr_preprocess_bwd_store if store else L.gsr_preprocess_bwd
+        fn(ctypes.byref(gs), ctypes.byref(proj), ctypes.byref(self.cam), ctypes.byref(self.tiling), ctypes.byref(g2),
+           ctypes.byref(gb), _p(densify_stat), _p(densify_count), _stream(stream))
 
     def forward(self, g: Gaussians, bg=(0.0, 0.0, 0.0), stream=None):
         self.preprocess(g, stream)
@@ -365,7 +368,9 @@ class MappingStep:
         elif name == "blend_bwd":
             vb.blend_bwd(stream=stream)
         elif name == "preprocess_bwd":
-            vb.preprocess_bwd(self.params, self.grads, stream=stream)
+            # the gradients are zero here (Adam zeroes what it reads), so the
+            # chain rule stores them instead of adding
+            vb.preprocess_bwd(self.params, self.grads, stream=stream, store=True)
         elif name == "adam":
             # the one-view backward writes gradients exactly where ntiles > 0
             self.adam.step(self.grads, stream, touched=vb.ntiles if self.params.n else None)
