@@ -94,97 +94,80 @@ __device__ __forceinline__ int64_t block_prefix(const uint32_t *block_sums, int6
     return p;
 }
 
-// ---------------------------------------------------------------- visible compaction
-__global__ void __launch_bounds__(kScanThreads) vis_count_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
-                                                                 uint32_t *__restrict__ block_sums) {
+// ---------------------------------------------------------------- visible records and candidates
+// Pass 1: per block of kScanTile records, the number of visible records and
+// of their box tiles (the candidates).  It also zeroes the per-tile counters
+// (the range words) and the kept-pair counter for the passes that follow.
+__global__ void __launch_bounds__(kScanThreads) count_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
+                                                             uint32_t *__restrict__ vis_sums,
+                                                             uint32_t *__restrict__ cand_sums,
+                                                             uint32_t *__restrict__ ranges, int64_t range_words,
+                                                             unsigned long long *__restrict__ d_kept) {
     __shared__ uint32_t s_warp[8];
+    for (int64_t w = (int64_t)blockIdx.x * kScanThreads + threadIdx.x; w < range_words;
+         w += (int64_t)gridDim.x * kScanThreads)
+        ranges[w] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_kept = 0ull;
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t s = 0;
+    uint32_t v = 0, c = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) s += ntiles[base + k] > 0u ? 1u : 0u;
-    s = block_incl_scan_256(s, s_warp);
-    if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
-}
-
-// visible records in index order -> order[], count -> *d_nvis
-__global__ void __launch_bounds__(kScanThreads) vis_compact_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
-                                                                   const uint32_t *__restrict__ block_sums,
-                                                                   int64_t nblocks, uint32_t *__restrict__ order,
-                                                                   int64_t *__restrict__ d_nvis) {
-    __shared__ uint32_t s_warp[8];
-    __shared__ int64_t s_red[16];
-    int64_t total;
-    const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *d_nvis = total;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    bool vis[kScanItems];
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        vis[k] = base + k < n && ntiles[base + k] > 0u;
-        s += vis[k] ? 1u : 0u;
+        if (base + k < n) {
+            const uint32_t t = ntiles[base + k];
+            v += t > 0u ? 1u : 0u;
+            c += t;
+        }
+    v = block_incl_scan_256(v, s_warp);
+    c = block_incl_scan_256(c, s_warp);
+    if (threadIdx.x == kScanThreads - 1) {
+        vis_sums[blockIdx.x] = v;
+        cand_sums[blockIdx.x] = c;
     }
-    const uint32_t incl = block_incl_scan_256(s, s_warp);
-    int64_t pos = pre + (int64_t)(incl - s);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (vis[k]) order[pos++] = (uint32_t)(base + k);
 }
 
-
-// ---------------------------------------------------------------- candidates
-// Candidates are the (record, box tile) slots of the visible list; one thread
-// per candidate runs the tile cull, so a few near-camera Gaussians with
-// thousands of box tiles spread over the whole GPU.
-__global__ void __launch_bounds__(kScanThreads) cand_count_kernel(const uint32_t *__restrict__ ntiles,
-                                                                  const uint32_t *__restrict__ order,
-                                                                  const int64_t *__restrict__ d_nvis, int64_t cap_n,
-                                                                  uint32_t *__restrict__ block_sums) {
-    __shared__ uint32_t s_warp[8];
-    const int64_t nv = clamp_count(d_nvis, cap_n);
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < nv) s += ntiles[order[base + k]];
-    s = block_incl_scan_256(s, s_warp);
-    if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = s;
-}
-
-// coff[i] = first candidate slot of visible item i; coff[nv] = total =
+// Pass 2: the visible records in index order (order[]), the first candidate
+// slot of each (coff[], with coff[nv] = the candidate total), *d_nvis and
 // *d_ncand.  Candidate numbers are 32-bit: a frame with 2^32 or more
 // candidates sets GSR_ERR_UNSUPPORTED and expands nothing.
-__global__ void __launch_bounds__(kScanThreads) cand_offsets_kernel(
-    const uint32_t *__restrict__ ntiles, const uint32_t *__restrict__ order, const int64_t *__restrict__ d_nvis,
-    int64_t cap_n, const uint32_t *__restrict__ block_sums, int64_t nblocks, uint32_t *__restrict__ coff,
-    int64_t *__restrict__ d_ncand, int32_t *__restrict__ d_status) {
+__global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
+                                                               const uint32_t *__restrict__ vis_sums,
+                                                               const uint32_t *__restrict__ cand_sums,
+                                                               int64_t nblocks, uint32_t *__restrict__ order,
+                                                               uint32_t *__restrict__ coff,
+                                                               int64_t *__restrict__ d_nvis,
+                                                               int64_t *__restrict__ d_ncand,
+                                                               int32_t *__restrict__ d_status) {
     __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_red[16];
-    int64_t total;
-    const int64_t pre = block_prefix(block_sums, nblocks, blockIdx.x, &total, s_red);
-    const int64_t nv = clamp_count(d_nvis, cap_n);
-    const bool too_many = total > (int64_t)0xffffffffLL;
+    int64_t vis_total, cand_total;
+    const int64_t vis_pre = block_prefix(vis_sums, nblocks, blockIdx.x, &vis_total, s_red);
+    const int64_t cand_pre = block_prefix(cand_sums, nblocks, blockIdx.x, &cand_total, s_red);
+    const bool too_many = cand_total > (int64_t)0xffffffffLL;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *d_ncand = too_many ? 0 : total;
-        coff[nv] = (uint32_t)total;
+        *d_nvis = vis_total;
+        *d_ncand = too_many ? 0 : cand_total;
+        coff[vis_total] = (uint32_t)cand_total;
         if (too_many) raise_status(d_status, GSR_ERR_UNSUPPORTED);
     }
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t cnt[kScanItems];
-    uint32_t s = 0;
+    uint32_t t[kScanItems];
+    uint32_t v = 0, c = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        cnt[k] = base + k < nv ? ntiles[order[base + k]] : 0u;
-        s += cnt[k];
+        t[k] = base + k < n ? ntiles[base + k] : 0u;
+        v += t[k] > 0u ? 1u : 0u;
+        c += t[k];
     }
-    const uint32_t incl = block_incl_scan_256(s, s_warp);
-    int64_t off = pre + (int64_t)(incl - s);
+    const uint32_t vi = block_incl_scan_256(v, s_warp);
+    const uint32_t ci = block_incl_scan_256(c, s_warp);
+    int64_t pos = vis_pre + (int64_t)(vi - v), off = cand_pre + (int64_t)(ci - c);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
-        if (base + k < nv) {
-            coff[base + k] = (uint32_t)off;
-            off += cnt[k];
+        if (t[k] > 0u) {
+            order[pos] = (uint32_t)(base + k);
+            coff[pos] = (uint32_t)off;
+            ++pos;
+            off += t[k];
         }
 }
 
@@ -619,7 +602,7 @@ __global__ void __launch_bounds__(kLargeSortThreads) sort_large_kernel(const uin
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SortLayout {
-    size_t order, block_sums, coff, counters, kept_ts, kept_sk, seg, list, list2, total;
+    size_t order, block_sums, cand_sums, coff, counters, kept_ts, kept_sk, seg, list, list2, total;
     int64_t scan_blocks;
 };
 
@@ -630,6 +613,7 @@ static SortLayout sort_layout(int64_t n, int64_t cap) {
     size_t off = 0;
     L.order = off; off += align256(sizeof(uint32_t) * (size_t)n1);
     L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
+    L.cand_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
     L.coff = off; off += align256(sizeof(uint32_t) * (size_t)(n1 + 1));
     L.counters = off; off += 256;  // nvis, ncand, kept, written (int64) + 3 list counts (u32)
     L.kept_ts = off; off += align256(sizeof(uint64_t) * (size_t)c1);
@@ -680,15 +664,15 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     }
     cudaStream_t st = as_cuda(stream);
     char *ws = static_cast<char *>(workspace);
-    if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st) != cudaSuccess)
-        return check_launch("memset tile ranges");
     if (n == 0) {
-        if (cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st) != cudaSuccess)
-            return check_launch("memset pair count");
+        if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st) != cudaSuccess ||
+            cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st) != cudaSuccess)
+            return check_launch("memset ranges and pair count");
         return GSR_OK;
     }
     uint32_t *order = reinterpret_cast<uint32_t *>(ws + L.order);
-    uint32_t *block_sums = reinterpret_cast<uint32_t *>(ws + L.block_sums);
+    uint32_t *vis_sums = reinterpret_cast<uint32_t *>(ws + L.block_sums);
+    uint32_t *cand_sums = reinterpret_cast<uint32_t *>(ws + L.cand_sums);
     uint32_t *coff = reinterpret_cast<uint32_t *>(ws + L.coff);
     int64_t *d_nvis = reinterpret_cast<int64_t *>(ws + L.counters);
     int64_t *d_ncand = d_nvis + 1;
@@ -700,18 +684,15 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     uint64_t *seg = reinterpret_cast<uint64_t *>(ws + L.seg);
     uint32_t *list = reinterpret_cast<uint32_t *>(ws + L.list);
     uint32_t *list2 = reinterpret_cast<uint32_t *>(ws + L.list2);
-    if (cudaMemsetAsync(d_kept, 0, sizeof(unsigned long long), st) != cudaSuccess)
-        return check_launch("memset pair counter");
     const float4 *xy = reinterpret_cast<const float4 *>(proj->xy_conic);
     const float4 *cb = reinterpret_cast<const float4 *>(proj->c_op_box);
     const float4 *rd = reinterpret_cast<const float4 *>(proj->rgb_depth);
     const unsigned sb = (unsigned)L.scan_blocks;
-    // 1-2. visible records in index order, their candidate offsets
-    vis_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, block_sums);
-    vis_compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, block_sums, L.scan_blocks, order, d_nvis);
-    cand_count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, order, d_nvis, n, block_sums);
-    cand_offsets_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, order, d_nvis, n, block_sums, L.scan_blocks, coff,
-                                                     d_ncand, d_status);
+    // 1-2. visible records in index order and their candidate offsets (the
+    // first pass also zeroes the tile counters and the kept-pair counter)
+    count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, tile_ranges, 2 * tiles, d_kept);
+    compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, L.scan_blocks, order, coff,
+                                                d_nvis, d_ncand, d_status);
     // 3. cull + unordered kept list + tile counts (in the range words)
     expand_kernel<<<kExpandGrid, kExpandThreads, 0, st>>>(coff, order, xy, cb, rd, d_nvis, n, d_ncand,
                                                           tiling->tile_w, tiling->tile_h, vt, (uint32_t)tiles,
