@@ -730,7 +730,8 @@ def main():
 # with the current kernels (profiles/blend_kernels_300k_1200x680.md; the loss
 # stage is its two SSIM passes); absent when not captured for the current
 # kernel version.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"blend_bwd": 27.776256e6, "render_fwd": 10.62528e6, "loss": 69.339648e6, "adam": 442.247168e6,
+               "preprocess_bwd": 73.832448e6}
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20
