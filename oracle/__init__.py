@@ -69,6 +69,8 @@ def lib():
         L.orc_adam.argtypes = [i64, P, P, P, P, P, i32, dbl, dbl, dbl]
         L.orc_psnr.argtypes = [P, P, i64]
         L.orc_default_init.argtypes = [P, i32, i32, P, i64, P, P, i64, i64, P, P, P, P, P]
+        L.orc_densify.argtypes = [i64, P, P, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, i64, P, P, P, P, P]
         L.orc_psnr.restype = dbl
         _lib = L
     return _lib
@@ -287,6 +289,25 @@ def default_init(img, keypoints, cam, ref_xyz, offset: int):
                                 _p(out["mean"]), _p(out["logscale"]), _p(out["quat"]), _p(out["logit"]), _p(out["sh"]))
     assert rc == 0
     return out
+
+
+def densify(mean_op, quat, logscale, stat, count, eps, grad_thr, logit_min, logscale_split, shrink):
+    """Densification decisions and outputs (see orc_densify).  Returns a dict:
+    src (n_out,), kind (n_out,), mean (n_out, 3), logscale (n_out, 3)."""
+    mo, q, ls = _f32(mean_op), _f32(quat), _f32(logscale)
+    n = mo.shape[0]
+    cap = 2 * n
+    n_out = np.zeros(1, np.int64)
+    src = np.zeros(max(cap, 1), np.int64)
+    kind = np.zeros(max(cap, 1), np.int32)
+    mean = np.zeros((max(cap, 1), 3))
+    lso = np.zeros((max(cap, 1), 3))
+    rc = lib().orc_densify(n, _p(mo), _p(q), _p(ls), _p(_f32(stat)), _p(_f32(count)), _p(_f32(eps)),
+                           float(grad_thr), float(logit_min), float(logscale_split), float(shrink), cap, _p(n_out),
+                           _p(src), _p(kind), _p(mean), _p(lso))
+    assert rc == 0
+    k = int(n_out[0])
+    return {"src": src[:k], "kind": kind[:k], "mean": mean[:k], "logscale": lso[:k]}
 
 
 def grad_to_planes(g60: np.ndarray):

@@ -18,6 +18,9 @@
  *   - Sec. 3.3, Eq. 4  L = (1-lambda)|I_r - I_gt|_1 + lambda (1 - SSIM).
  *   - Sec. 3.4, Eq. 5  Gaussian pyramid levels GP^l(I_gt).
  *   - Sec. 4.1  lambda = 0.2, three pyramid levels.
+ *   - Sec. 3.3.1  densification: split or clone primitives with large
+ *               loss gradients, prune transparent ones (3DGS rules as the
+ *               reading; thresholds are parameters).
  *   - Sec. 3.3.1  new primitives at keypoints (their default initial shape
  *               is a reading: 3-nearest-neighbour scale, identity rotation,
  *               opacity 0.1, DC colour of the keypoint pixel).
@@ -1173,5 +1176,67 @@ int orc_default_init(const double *img, int W, int H, const float *kp, int64_t M
         for (int c = 0; c < 48; ++c) sh[48 * m + c] = 0.0;
         for (int ch = 0; ch < 3; ++ch) sh[48 * m + ch] = (img[((int64_t)ch * H + py) * W + px] - 0.5) / y00;
     }
+    return 0;
+}
+
+/* Gradient-driven densification and pruning of the map (Photo-SLAM Sec.
+ * 3.3.1: split or clone primitives with large loss gradients, after 3D
+ * Gaussian splatting; prune nearly transparent ones).  Decisions, per input
+ * Gaussian i, on FP32 values:
+ *   g_i = stat_i / count_i (0 if count_i = 0): the mean |dL/d(u, v)| in
+ *         normalised device coordinates over the iterations that saw it;
+ *   prune  when the opacity logit < logit_min (opacity below its sigmoid);
+ *   else densify when g_i >= grad_thr:
+ *     split when its largest log-scale > logscale_split: two children,
+ *           mean mu + R(q) (s * eps_k) (eps_k = eps[6 i + 3 k ..], s the
+ *           scales), log-scale - shrink, the rest copied; the parent goes;
+ *     clone otherwise: the Gaussian and a copy;
+ *   else keep.
+ * Outputs in input order (a clone: original first).  src[o] = input index,
+ * kind[o] = 0 kept, 1 clone copy, 2 / 3 split child 0 / 1; mean_out and
+ * logscale_out (o x 3) in FP64 (split means from FP64 arithmetic on the FP32
+ * inputs).  Returns 1 if the outputs exceed cap. */
+int orc_densify(int64_t n, const float *mean_op, const float *quat, const float *logscale, const float *stat,
+                const float *count, const float *eps, float grad_thr, float logit_min, float logscale_split,
+                float shrink, int64_t cap, int64_t *n_out, int64_t *src, int32_t *kind, double *mean_out,
+                double *logscale_out) {
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float g = count[i] > 0.0f ? stat[i] / count[i] : 0.0f;
+        const float *mo = mean_op + 4 * i, *q = quat + 4 * i, *ls = logscale + 4 * i;
+        if (mo[3] < logit_min) continue;
+        const int densify = g >= grad_thr;
+        const float lmax = ls[0] > ls[1] ? (ls[0] > ls[2] ? ls[0] : ls[2]) : (ls[1] > ls[2] ? ls[1] : ls[2]);
+        const int split = densify && lmax > logscale_split;
+        const int outs = split || densify ? 2 : 1;
+        if (o + outs > cap) return 1;
+        if (!split) {
+            for (int k = 0; k < outs; ++k, ++o) {
+                src[o] = i;
+                kind[o] = k;
+                for (int c = 0; c < 3; ++c) {
+                    mean_out[3 * o + c] = mo[c];
+                    logscale_out[3 * o + c] = ls[c];
+                }
+            }
+            continue;
+        }
+        /* rotation of the normalised quaternion (w, x, y, z) */
+        const double nq = sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3]);
+        const double w = q[0] / nq, x = q[1] / nq, y = q[2] / nq, z = q[3] / nq;
+        const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                             2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                             2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+        const double s[3] = {exp((double)ls[0]), exp((double)ls[1]), exp((double)ls[2])};
+        for (int k = 0; k < 2; ++k, ++o) {
+            const float *e = eps + 6 * i + 3 * k;
+            src[o] = i;
+            kind[o] = 2 + k;
+            for (int r = 0; r < 3; ++r)
+                mean_out[3 * o + r] = mo[r] + R[3 * r] * s[0] * e[0] + R[3 * r + 1] * s[1] * e[1] + R[3 * r + 2] * s[2] * e[2];
+            for (int c = 0; c < 3; ++c) logscale_out[3 * o + c] = (double)(float)(ls[c] - shrink);
+        }
+    }
+    *n_out = o;
     return 0;
 }
