@@ -9,7 +9,7 @@ dataset itself is not available).  The path does not shard: with --gpus N
 every rank runs an independent replica (weak scaling, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode mapping|window|mlp|ttp]
+                  [--mode mapping|window|mlp|ttp|densify]
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this path) on the host cores, on a bounded band of image rows per step.
@@ -19,7 +19,9 @@ whole iteration in one CUDA graph); --mode mlp times the learned
 initialiser's tensor-core forward and training step at 2k and 20k rows;
 --mode ttp runs the time-to-PSNR experiment (plain single-view path with
 default initialisation against the batched window with the learned
-initialiser, and with the default one).  The default (mapping) line is the
+initialiser, and with the default one); --mode densify runs mapping on a
+1M-Gaussian 1920 x 1080 scene with densification and pruning every 100
+iterations (uneven Gaussian counts).  The default (mapping) line is the
 headline.
 """
 from __future__ import annotations
@@ -551,6 +553,104 @@ def run_ttp(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- densify / prune (uneven counts)
+DENS_N = 1_000_000
+DENS_W, DENS_H, DENS_F = 1920, 1080, 1000.0
+DENS_EVERY = 100
+
+
+def run_densify(args):
+    import torch
+    import synthetic as S
+    import paper_2311_16728_b300 as gsr
+    from paper_2311_16728_b300.mapping import Densifier
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    target = S.room_scene(DENS_N, seed=0)
+    start = S.perturb(target, 0.05, seed=1)
+    cams = []
+    for k in range(N_POSES):
+        pos, yaw = S.trajectory(k)
+        cams.append(S.pose_camera(pos, yaw, DENS_F, DENS_F, DENS_W, DENS_H))
+    g_tgt = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
+    vb = gsr.ViewBuffers(DENS_N, gsr.camera_from(cams[0]), gsr.tiling_struct(16, 16), 1024)
+    gts = []
+    for cam in cams:
+        vb.cam = gsr.camera_from(cam)
+        gsr.ensure_capacity(vb, g_tgt)
+        vb.forward(g_tgt)
+        gts.append(vb.img.clone())
+    del vb, g_tgt
+    cap = int(DENS_N * 1.25)
+    params = gsr.Gaussians.zeros(cap)
+    for dst, src in ((params.mean_op, start.mean_op), (params.quat, start.quat), (params.logscale, start.logscale)):
+        dst[:DENS_N] = torch.tensor(src, device="cuda")
+    params.sh[:, :DENS_N] = torch.tensor(start.sh, device="cuda")
+    adam = gsr.Adam(params)
+    dens = Densifier(params, adam, DENS_N)
+    views = list(zip(cams, gts))
+
+    def build():
+        ms = gsr.MappingStep(dens.params, views, adam=dens.adam, densify_stat=dens.stat,
+                             densify_count=dens.count)
+        ms.capture()
+        return ms
+
+    t_build = time.time()
+    ms = build()
+    sized_for = DENS_N
+    build_s = [time.time() - t_build]
+    for _ in range(args.warmup):
+        ms.step()
+    torch.cuda.synchronize()
+    dens.stat.zero_()
+    dens.count.zero_()
+    segments = max(1, args.steps // DENS_EVERY)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, dens_ms, counts, rebuilds = 0.0, 0.0, [dens.n_live], 0
+    clocks = ClockSampler()
+    clocks.start()
+    for seg in range(segments):
+        e0.record()
+        for _ in range(DENS_EVERY):
+            ms.step()
+        e1.record()
+        torch.cuda.synchronize()
+        if ms.status() != 0:
+            raise RuntimeError(f"device status {ms.status():#x} in segment {seg} (pair capacity)")
+        step_ms += e0.elapsed_time(e1)
+        if seg == segments - 1:
+            break
+        t0 = time.time()
+        n_live, grown = dens.step()
+        counts.append(n_live)
+        # a new store, or a map grown by 30 % since the pair capacity was sized
+        # (it carries a 50 % margin), is captured again; a segment that still
+        # overflowed would stop the run above
+        if grown or n_live > 1.3 * sized_for:
+            ms = build()
+            sized_for = n_live
+            rebuilds += 1
+        torch.cuda.synchronize()
+        dens_ms += (time.time() - t0) * 1e3
+    clk = clocks.stop(int(os.environ.get("LOCAL_RANK", "0")))
+    iters = segments * DENS_EVERY
+    total_ms = step_ms + dens_ms
+    line = {"metric": f"mapping iters/s with densify / prune every {DENS_EVERY} @{DENS_N // 1000}k starting "
+                      f"Gaussians {DENS_W}x{DENS_H}",
+            "value": iters * 1000.0 / total_ms, "unit": "iters/s", "n_gpus": 1, "steps": iters,
+            "warmup": args.warmup, "ms_per_step": total_ms / iters, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; 1920x1080 frames)",
+            "config": {"workload": f"{DENS_N} Gaussians (perturbed room scene), {DENS_W}x{DENS_H} fx=fy={DENS_F:.0f}, "
+                                   f"{N_POSES}-pose trajectory; every {DENS_EVERY} iterations clone / split where the "
+                                   "mean NDC gradient norm >= 2e-4 (split above scale 0.03 m), prune opacity < 0.005; "
+                                   "store with 25 % spare capacity, re-captured when it overflows or the map grew "
+                                   "30 % since the pair capacity was sized", "gaussians_after_each_densify": counts,
+                       "rebuilds": rebuilds, "first_build_s": round(build_s[0], 1)},
+            "iteration_ms": step_ms / iters, "densify_ms_per_step": dens_ms / max(1, segments - 1),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,7 +659,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
     ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
-    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp", "ttp"])
+    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp", "ttp", "densify"])
     ap.add_argument("--ttp-seeds", default="100,101,102,103,104", help="ttp mode: held-out evaluation scenes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
@@ -580,6 +680,9 @@ def main():
         return
     if args.mode == "ttp":
         run_ttp(args)
+        return
+    if args.mode == "densify":
+        run_densify(args)
         return
 
     import torch

@@ -231,8 +231,9 @@ int32_t gsr_preprocess_bwd_store(const gsr_gaussians *g, const gsr_proj *proj, c
  * quaternion (through its normalisation), log-scale, opacity logit and SH,
  * ADDING (+=) into `grads` so several views accumulate.  dL_dimg is
  * 3 x H x W.  If densify_stat is not NULL, |dL/d(u, v)| of each visible
- * Gaussian is added to densify_stat[gid] (the 3DGS densification statistic)
- * and 1 to densify_count[gid]. */
+ * Gaussian, with (u, v) in normalised device coordinates (pixels scaled by
+ * 2 / W, 2 / H: the 3DGS densification statistic), is added to
+ * densify_stat[gid] and 1 to densify_count[gid]. */
 int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint32_t *vals,
                        const uint32_t *tile_ranges, const gsr_camera *cam, const gsr_tiling *tiling,
                        const float *bg, const float *T_final, const uint32_t *n_contrib,
@@ -344,6 +345,40 @@ int32_t gsr_default_init_workspace_size(int64_t M, int64_t n, size_t *bytes);
 int32_t gsr_default_init(const float *img0, int32_t W, int32_t H, const float *keypoints, int64_t M,
                          const gsr_camera *cam, const gsr_param_buffers *map, int64_t n, int64_t offset,
                          void *workspace, size_t workspace_bytes, gsr_stream_t stream);
+
+/* ---------------------------------------------------------------- */
+/* Gradient-driven densification and pruning (Sec. 3.3.1)           */
+/* ---------------------------------------------------------------- */
+/* Photo-SLAM splits or clones primitives with large loss gradients, as 3D
+ * Gaussian splatting does, and drops nearly transparent ones.  Thresholds
+ * (FP32; decisions are exact comparisons on FP32 values):
+ *   grad_thr       on g_i = stat_i / count_i, the mean |dL/d(u, v)| in
+ *                  normalised device coordinates that the chain rule
+ *                  accumulates (densify_stat / densify_count);
+ *   logit_min      prune when the opacity logit is below it;
+ *   logscale_split split (not clone) when the largest log-scale is above it;
+ *   shrink         log of the scale divisor of split children (log 1.6). */
+typedef struct {
+    float grad_thr, logit_min, logscale_split, shrink;
+} gsr_densify_config;
+
+int32_t gsr_densify_workspace_size(int64_t n, size_t *bytes);
+
+/* One densification step of n Gaussians (params, Adam moments m, v) into a
+ * second store of cap Gaussians (out_params, out_m, out_v; must not alias the
+ * inputs), in input order: prune (or padding: a zero quaternion) -> nothing; keep -> a copy; clone -> a copy
+ * and a second copy with zero moments; split -> two children with zero
+ * moments, mean mu + R(q) (s * eps_k) (eps: n x 6 floats, two standard normal
+ * 3-vectors per Gaussian, supplied by the caller), log-scale - shrink, rest
+ * copied.  *d_n_out (device) receives the output count; the tail [n_out, cap)
+ * becomes inert padding (all zero: a zero quaternion is never visible).  If
+ * n_out > cap, GSR_ERR_CAPACITY is set in *d_status, *d_n_out holds the
+ * count a retry needs and the outputs are incomplete. */
+int32_t gsr_densify(const gsr_param_buffers *params, const gsr_param_buffers *m, const gsr_param_buffers *v,
+                    int64_t n, const float *stat, const float *count, const float *eps,
+                    const gsr_densify_config *cfg, const gsr_param_buffers *out_params,
+                    const gsr_param_buffers *out_m, const gsr_param_buffers *out_v, int64_t cap, int64_t *d_n_out,
+                    void *workspace, size_t workspace_bytes, int32_t *d_status, gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */
 /* Learned initialiser (tensor-core MLP)                             */

@@ -1185,7 +1185,8 @@ int orc_default_init(const double *img, int W, int H, const float *kp, int64_t M
  * Gaussian i, on FP32 values:
  *   g_i = stat_i / count_i (0 if count_i = 0): the mean |dL/d(u, v)| in
  *         normalised device coordinates over the iterations that saw it;
- *   prune  when the opacity logit < logit_min (opacity below its sigmoid);
+ *   prune  when the opacity logit < logit_min (opacity below its sigmoid),
+ *          and drop padding (a zero quaternion: an empty slot of the store);
  *   else densify when g_i >= grad_thr:
  *     split when its largest log-scale > logscale_split: two children,
  *           mean mu + R(q) (s * eps_k) (eps_k = eps[6 i + 3 k ..], s the
@@ -1204,6 +1205,7 @@ int orc_densify(int64_t n, const float *mean_op, const float *quat, const float 
     for (int64_t i = 0; i < n; ++i) {
         const float g = count[i] > 0.0f ? stat[i] / count[i] : 0.0f;
         const float *mo = mean_op + 4 * i, *q = quat + 4 * i, *ls = logscale + 4 * i;
+        if (q[0] == 0.0f && q[1] == 0.0f && q[2] == 0.0f && q[3] == 0.0f) continue; /* padding */
         if (mo[3] < logit_min) continue;
         const int densify = g >= grad_thr;
         const float lmax = ls[0] > ls[1] ? (ls[0] > ls[2] ? ls[0] : ls[2]) : (ls[1] > ls[2] ? ls[1] : ls[2]);

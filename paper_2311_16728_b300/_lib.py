@@ -56,6 +56,10 @@ class gsr_mlp_weights(ctypes.Structure):
                 ("W3hT", c_void_p)]
 
 
+class gsr_densify_config(ctypes.Structure):
+    _fields_ = [("grad_thr", c_float), ("logit_min", c_float), ("logscale_split", c_float), ("shrink", c_float)]
+
+
 class gsr_adam_config(ctypes.Structure):
     _fields_ = [("lr_mean", c_float), ("lr_opacity", c_float), ("lr_quat", c_float), ("lr_scale", c_float),
                 ("lr_sh", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
@@ -99,6 +103,10 @@ _SIGNATURES = {
     "gsr_default_init_workspace_size": ([c_int64, c_int64, P(c_size_t)], c_int32),
     "gsr_default_init": ([c_void_p, c_int32, c_int32, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64,
                           c_int64, c_void_p, c_size_t, c_void_p], c_int32),
+    "gsr_densify_workspace_size": ([c_int64, P(c_size_t)], c_int32),
+    "gsr_densify": ([P(gsr_param_buffers), P(gsr_param_buffers), P(gsr_param_buffers), c_int64, c_void_p, c_void_p,
+                     c_void_p, P(gsr_densify_config), P(gsr_param_buffers), P(gsr_param_buffers),
+                     P(gsr_param_buffers), c_int64, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "gsr_gemm_bf16": ([c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
                        c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int64,
                        c_int32, c_void_p, c_void_p], c_int32),
@@ -184,6 +192,8 @@ gsr_batched_iterate = _wrap("gsr_batched_iterate")
 gsr_batched_preprocess_bwd = _wrap("gsr_batched_preprocess_bwd")
 gsr_default_init_workspace_size = _wrap("gsr_default_init_workspace_size")
 gsr_default_init = _wrap("gsr_default_init")
+gsr_densify_workspace_size = _wrap("gsr_densify_workspace_size")
+gsr_densify = _wrap("gsr_densify")
 gsr_gemm_bf16 = _wrap("gsr_gemm_bf16")
 gsr_mlp_workspace_size = _wrap("gsr_mlp_workspace_size")
 gsr_mlp_sync_weights = _wrap("gsr_mlp_sync_weights")

@@ -269,8 +269,9 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
     Chain c;
     if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
     const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
-    if (dstat) {
-        dstat[i] += sqrtf(G0.x * G0.x + G0.y * G0.y);
+    if (dstat) {  // |dL/d(u, v)| in normalised device coordinates
+        const float gu = G0.x * (0.5f * (float)cam.W), gv = G0.y * (0.5f * (float)cam.H);
+        dstat[i] += sqrtf(gu * gu + gv * gv);
         dcount[i] += 1.0f;
     }
     float A, B, C, sig;

@@ -14,15 +14,20 @@ Sec. 3.3-3.4).
 * `Evaluator`: PSNR of the map against level-0 keyframe images.
 * `harvest` / `train_initialiser`: (patch, converged parameter) pairs produced
   by a mapping run, and the MLP's training on them.
+* `Densifier`: gradient-driven densification and pruning (Sec. 3.3.1) of a
+  map kept in a padded store.
 """
 from __future__ import annotations
 
 from typing import List, Sequence
 
+import ctypes
+
 import torch
 
+from . import _lib as L
 from .learned_init import N3, LearnedInit, default_init
-from .raster import (PYRAMID_LEVELS, Adam, AdamConfig, Gaussians, MappingStep, ViewBuffers, camera_at_level,
+from .raster import (PYRAMID_LEVELS, Adam, AdamConfig, Gaussians, MappingStep, ViewBuffers, _p, camera_at_level,
                      camera_from, ensure_capacity, psnr, pyramid, tiling_struct)
 
 TAU_U = 30  # keyframe uses until level 0 (schedule reading)
@@ -156,3 +161,72 @@ def train_initialiser(li: LearnedInit, batches: Sequence[Batch], steps: int, see
         li.train_step(b.target, b.M, x=b.x, xT=b.xT)
         losses.append(li.loss.clone())
     return torch.cat(losses).cpu().tolist() if losses else []
+
+
+class Densifier:
+    """Gradient-driven densification and pruning (Sec. 3.3.1) of a map kept
+    in a store with spare capacity: the live Gaussians occupy the first
+    `n_live` slots and the rest is inert padding, so that captured
+    iterations over the whole store stay valid until the store is full.
+
+    Every mapping iteration adds each seen Gaussian's |dL/d(u, v)| (NDC) to
+    `stat` and 1 to `count` (pass them to MappingStep).  `step()` runs
+    gsr_densify with seeded standard normals for the split offsets and
+    writes the result back into the same store (the captured graphs keep
+    their pointers); when the result does not fit it returns a new, larger
+    store and the caller re-captures."""
+
+    def __init__(self, params: Gaussians, adam: Adam, n_live: int, grad_thr: float = 2e-4,
+                 min_opacity: float = 0.005, split_scale: float = 0.03, shrink: float = 1.6, seed: int = 0,
+                 growth: float = 1.25):
+        import math
+        self.params, self.adam, self.n_live, self.growth = params, adam, n_live, growth
+        dev = params.mean_op.device
+        self.stat = torch.zeros(params.n, dtype=torch.float32, device=dev)
+        self.count = torch.zeros(params.n, dtype=torch.float32, device=dev)
+        self.cfg = L.gsr_densify_config(grad_thr, math.log(min_opacity / (1.0 - min_opacity)), math.log(split_scale),
+                                        math.log(shrink))
+        self.gen = torch.Generator(device=dev).manual_seed(seed)
+        self.d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def _run(self, out: Gaussians, om: Gaussians, ov: Gaussians) -> int:
+        n = self.n_live
+        eps = torch.randn(max(n, 1), 6, generator=self.gen, device=self.params.mean_op.device)
+        sz = ctypes.c_size_t()
+        L.gsr_densify_workspace_size(n, ctypes.byref(sz))
+        ws = torch.empty(sz.value, dtype=torch.uint8, device=eps.device)
+        pb = [x.buffers_struct() for x in (self.params, self.adam.m, self.adam.v, out, om, ov)]
+        self.status.zero_()
+        L.gsr_densify(ctypes.byref(pb[0]), ctypes.byref(pb[1]), ctypes.byref(pb[2]), n, _p(self.stat), _p(self.count),
+                      _p(eps), ctypes.byref(self.cfg), ctypes.byref(pb[3]), ctypes.byref(pb[4]), ctypes.byref(pb[5]),
+                      out.n, _p(self.d_n), _p(ws), ws.numel(), _p(self.status), None)
+        return int(self.d_n.item())
+
+    def step(self):
+        """Densify and prune.  Returns (n_live, grown): grown is True when the
+        store was replaced by a larger one (self.params / self.adam are then
+        new objects and captured iterations must be rebuilt)."""
+        cap = self.params.n
+        out, om, ov = (Gaussians.zeros(cap, self.params.mean_op.device, self.params.sh_degree) for _ in range(3))
+        n_out = self._run(out, om, ov)
+        grown = n_out > cap
+        if grown:
+            cap = int(n_out * self.growth) + 1024
+            out, om, ov = (Gaussians.zeros(cap, self.params.mean_op.device, self.params.sh_degree) for _ in range(3))
+            n_out = self._run(out, om, ov)
+            adam = Adam(out, self.adam.cfg)
+            adam.m, adam.v = om, ov
+            adam.step_count.copy_(self.adam.step_count)
+            self.params, self.adam = out, adam
+            dev = out.mean_op.device
+            self.stat = torch.zeros(cap, dtype=torch.float32, device=dev)
+            self.count = torch.zeros(cap, dtype=torch.float32, device=dev)
+        else:
+            for dst, src in zip([t for x in (self.params, self.adam.m, self.adam.v) for t in x.tensors()],
+                                [t for x in (out, om, ov) for t in x.tensors()]):
+                dst.copy_(src)
+            self.stat.zero_()
+            self.count.zero_()
+        self.n_live = n_out
+        return n_out, grown

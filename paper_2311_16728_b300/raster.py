@@ -328,10 +328,14 @@ class MappingStep:
 
     def __init__(self, params: Gaussians, views, tiling: L.gsr_tiling = None, adam_cfg: AdamConfig = AdamConfig(),
                  lam: float = LAMBDA_DSSIM, pair_capacity: Optional[int] = None, margin: float = 1.5,
-                 adam: Optional[Adam] = None, grads: Optional[Gaussians] = None):
+                 adam: Optional[Adam] = None, grads: Optional[Gaussians] = None,
+                 densify_stat: Optional[torch.Tensor] = None, densify_count: Optional[torch.Tensor] = None):
         """`adam` and `grads` may be shared with other steps over the same
-        parameters (e.g. one step per pyramid level)."""
+        parameters (e.g. one step per pyramid level); with densify_stat /
+        densify_count (n floats each) every iteration accumulates the
+        densification statistic of the Gaussians it sees."""
         self.params = params
+        self.densify_stat, self.densify_count = densify_stat, densify_count
         self.tiling = tiling or tiling_struct(16, 16)
         self.views = [(camera_from(c), gt.contiguous()) for c, gt in views]
         self.lam = lam
@@ -370,7 +374,8 @@ class MappingStep:
         elif name == "preprocess_bwd":
             # the gradients are zero here (Adam zeroes what it reads), so the
             # chain rule stores them instead of adding
-            vb.preprocess_bwd(self.params, self.grads, stream=stream, store=True)
+            vb.preprocess_bwd(self.params, self.grads, self.densify_stat, self.densify_count, stream=stream,
+                              store=True)
         elif name == "adam":
             # the one-view backward writes gradients exactly where ntiles > 0
             self.adam.step(self.grads, stream, touched=vb.ntiles if self.params.n else None)

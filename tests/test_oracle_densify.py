@@ -36,6 +36,11 @@ def test_decision_table():
     out = oracle.densify(mo, q, ls, stat, count, eps, THR, LOGIT_MIN, SPLIT, SHRINK)
     assert out["src"].tolist() == [1, 1, 2, 3, 3, 4, 5]
     assert out["kind"].tolist() == [0, 1, 0, 2, 3, 0, 0]
+    # an empty slot (zero quaternion) is dropped even with a large gradient
+    q2 = q.copy()
+    q2[1] = 0
+    out = oracle.densify(mo, q2, ls, stat, count, eps, THR, LOGIT_MIN, SPLIT, SHRINK)
+    assert out["src"].tolist() == [2, 3, 3, 4, 5]
 
 
 def test_split_children_closed_forms():
