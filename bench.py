@@ -9,7 +9,7 @@ dataset itself is not available).  The path does not shard: with --gpus N
 every rank runs an independent replica (weak scaling, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode mapping|window|mlp|ttp|densify]
+                  [--mode mapping|window|mlp|ttp|densify|stereo]
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this path) on the host cores, on a bounded band of image rows per step.
@@ -21,8 +21,9 @@ initialiser's tensor-core forward and training step at 2k and 20k rows;
 default initialisation against the batched window with the learned
 initialiser, and with the default one); --mode densify runs mapping on a
 1M-Gaussian 1920 x 1080 scene with densification and pruning every 100
-iterations (uneven Gaussian counts).  The default (mapping) line is the
-headline.
+iterations (uneven Gaussian counts); --mode stereo maps 752 x 480 grayscale
+stereo pairs (0.11 m baseline, luminance loss).  The default (mapping) line
+is the headline.
 """
 from __future__ import annotations
 
@@ -651,6 +652,61 @@ def run_densify(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- stereo grayscale views
+STEREO_N = 300_000
+
+
+def run_stereo(args):
+    import torch
+    import synthetic as S
+    import paper_2311_16728_b300 as gsr
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    target = S.room_scene(STEREO_N, seed=0)
+    start = S.perturb(target, 0.05, seed=1)
+    cams = [c for k in range(N_POSES) for c in S.stereo_pair(k)]
+    g_tgt = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
+    vb = gsr.ViewBuffers(STEREO_N, gsr.camera_from(cams[0]), gsr.tiling_struct(16, 16), 1024)
+    views = []
+    for cam in cams:
+        vb.cam = gsr.camera_from(cam)
+        gsr.ensure_capacity(vb, g_tgt)
+        vb.forward(g_tgt)
+        # monochrome target: the luminance of the true render
+        views.append((cam, (0.299 * vb.img[0] + 0.587 * vb.img[1] + 0.114 * vb.img[2])[None].contiguous()))
+    del vb, g_tgt
+    params = gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh)
+    ms = gsr.MappingStep(params, views)
+    ms.capture()
+    for _ in range(args.warmup):
+        ms.step()
+    torch.cuda.synchronize()
+    nst = len(gsr.STAGES)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler()
+    clocks.start()
+    torch.cuda.synchronize()
+    t0.record()
+    for k in range(args.steps):
+        ms.step(events=evs[k])
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop(int(os.environ.get("LOCAL_RANK", "0")))
+    if ms.status() != 0:
+        raise RuntimeError(f"device status {ms.status():#x}")
+    ms_per = t0.elapsed_time(t1) / args.steps
+    stage_ms = {nm: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, nm in enumerate(gsr.STAGES)}
+    line = {"metric": f"stereo grayscale mapping iters/s @{STEREO_N // 1000}k Gaussians 752x480",
+            "value": 1000.0 / ms_per, "unit": "iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; EuRoC-shaped monochrome stereo)",
+            "config": {"workload": f"{STEREO_N} Gaussians in a 6x3x4 m room; {N_POSES} poses x 2 cameras "
+                                   "(0.11 m baseline) of 752x480 fx=fy=376, one view per iteration, Eq. 4 on the "
+                                   "luminance 0.299 R + 0.587 G + 0.114 B against monochrome targets, Adam"},
+            "stages_ms": stage_ms, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,7 +715,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
     ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
-    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp", "ttp", "densify"])
+    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp", "ttp", "densify", "stereo"])
     ap.add_argument("--ttp-seeds", default="100,101,102,103,104", help="ttp mode: held-out evaluation scenes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
@@ -683,6 +739,9 @@ def main():
         return
     if args.mode == "densify":
         run_densify(args)
+        return
+    if args.mode == "stereo":
+        run_stereo(args)
         return
 
     import torch

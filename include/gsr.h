@@ -200,6 +200,14 @@ int32_t gsr_loss_fwd_bwd(const float *img, const float *gt, int32_t C, int32_t H
                          float lambda, float *d_loss, float *dL_dimg, void *workspace,
                          size_t workspace_bytes, gsr_stream_t stream);
 
+/* Eq. 4 for a grayscale view (the monochrome stereo cameras of Sec. 4): the
+ * loss of the render's luminance Y = 0.299 R + 0.587 G + 0.114 B (img, 3 x H
+ * x W) against gt (1 x H x W), with dL_dimg (3 x H x W) = (0.299, 0.587,
+ * 0.114) dL/dY.  Scratch: gsr_loss_luma_workspace_size. */
+int32_t gsr_loss_luma_workspace_size(int32_t H, int32_t W, size_t *bytes);
+int32_t gsr_loss_luma_fwd_bwd(const float *img, const float *gt, int32_t H, int32_t W, float lambda, float *d_loss,
+                              float *dL_dimg, void *workspace, size_t workspace_bytes, gsr_stream_t stream);
+
 /* Backward of Eq. 3 alone (the first half of gsr_render_bwd): zeroes grad2d
  * (n Gaussians) and accumulates the screen-space gradients into it. */
 int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t *vals, const uint32_t *tile_ranges,

@@ -252,6 +252,13 @@ def loss(x, y, lam: float = 0.2, grad: bool = True):
     return (float(out[0]), d) if grad else float(out[0])
 
 
+def luma(img):
+    """Luminance of a 3 x H x W image (BT.601 weights, the reading for the
+    grayscale views): 0.299 R + 0.587 G + 0.114 B, as 1 x H x W (FP64)."""
+    img = _f64(img)
+    return (0.299 * img[0] + 0.587 * img[1] + 0.114 * img[2])[None]
+
+
 def pyramid_down(img):
     img = _f64(img)
     C, H, W = img.shape

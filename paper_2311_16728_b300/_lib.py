@@ -84,6 +84,9 @@ _SIGNATURES = {
     "gsr_preprocess_bwd_store": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d),
                             P(gsr_param_buffers), c_void_p, c_void_p, c_void_p], c_int32),
     "gsr_loss_workspace_size": ([c_int32, c_int32, c_int32, P(c_size_t)], c_int32),
+    "gsr_loss_luma_workspace_size": ([c_int32, c_int32, P(c_size_t)], c_int32),
+    "gsr_loss_luma_fwd_bwd": ([c_void_p, c_void_p, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p, c_size_t,
+                               c_void_p], c_int32),
     "gsr_loss_fwd_bwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p,
                           c_size_t, c_void_p], c_int32),
     "gsr_loss_fwd_bwd_static": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p,
@@ -208,5 +211,7 @@ gsr_adam_step_touched = _wrap("gsr_adam_step_touched")
 gsr_pyramid_down = _wrap("gsr_pyramid_down")
 gsr_psnr_workspace_size = _wrap("gsr_psnr_workspace_size")
 gsr_psnr = _wrap("gsr_psnr")
+gsr_loss_luma_workspace_size = _wrap("gsr_loss_luma_workspace_size")
+gsr_loss_luma_fwd_bwd = _wrap("gsr_loss_luma_fwd_bwd")
 
 EXPORTED = tuple(_SIGNATURES)

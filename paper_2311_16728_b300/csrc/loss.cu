@@ -151,6 +151,63 @@ extern "C" int32_t gsr_loss_fwd_bwd(const float *img, const float *gt, int32_t C
     return check_launch("ssim kernels");
 }
 
+// ---------------------------------------------------------------- luminance loss
+// Grayscale views (stereo rigs of Sec. 4): Eq. 4 on the luminance
+// Y = 0.299 R + 0.587 G + 0.114 B of the render against a grayscale target.
+constexpr float kLumaR = 0.299f, kLumaG = 0.587f, kLumaB = 0.114f;
+
+__global__ void __launch_bounds__(256) luma_kernel(const float *__restrict__ img, int64_t plane,
+                                                   float *__restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < plane) y[i] = kLumaR * img[i] + kLumaG * img[plane + i] + kLumaB * img[2 * plane + i];
+}
+
+__global__ void __launch_bounds__(256) luma_grad_kernel(const float *__restrict__ dy, int64_t plane,
+                                                        float *__restrict__ dimg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < plane) {
+        const float d = dy[i];
+        dimg[i] = kLumaR * d;
+        dimg[plane + i] = kLumaG * d;
+        dimg[2 * plane + i] = kLumaB * d;
+    }
+}
+
+extern "C" int32_t gsr_loss_luma_workspace_size(int32_t H, int32_t W, size_t *bytes) {
+    if (H <= 0 || W <= 0 || !bytes) {
+        set_error("gsr_loss_luma_workspace_size: bad arguments");
+        return GSR_ERR_INVALID_ARG;
+    }
+    *bytes = loss_layout(1, H, W).total + 2 * al256(sizeof(float) * (size_t)H * W);
+    return GSR_OK;
+}
+
+extern "C" int32_t gsr_loss_luma_fwd_bwd(const float *img, const float *gt, int32_t H, int32_t W, float lambda,
+                                         float *d_loss, float *dL_dimg, void *workspace, size_t workspace_bytes,
+                                         gsr_stream_t stream) {
+    if (!img || !gt || !d_loss || !dL_dimg || H <= 0 || W <= 0 || !(lambda >= 0.f && lambda <= 1.f)) {
+        set_error("gsr_loss_luma_fwd_bwd: bad arguments");
+        return GSR_ERR_INVALID_ARG;
+    }
+    const LossLayout L = loss_layout(1, H, W);
+    const size_t plane_bytes = al256(sizeof(float) * (size_t)H * W);
+    if (!workspace || workspace_bytes < L.total + 2 * plane_bytes) {
+        set_error("gsr_loss_luma_fwd_bwd: workspace of %zu bytes needed", L.total + 2 * plane_bytes);
+        return GSR_ERR_CAPACITY;
+    }
+    char *ws = static_cast<char *>(workspace);
+    float *mA = reinterpret_cast<float *>(ws + L.a), *mB = reinterpret_cast<float *>(ws + L.b);
+    float *mC = reinterpret_cast<float *>(ws + L.c), *part = reinterpret_cast<float *>(ws + L.partials);
+    float *y = reinterpret_cast<float *>(ws + L.total), *dy = reinterpret_cast<float *>(ws + L.total + plane_bytes);
+    const int64_t plane = (int64_t)H * W;
+    cudaStream_t st = as_cuda(stream);
+    const unsigned blocks = (unsigned)((plane + 255) / 256);
+    luma_kernel<<<blocks, 256, 0, st>>>(img, plane, y);
+    launch_ssim(y, gt, 1, H, W, lambda, d_loss, dy, mA, mB, mC, part, L.nblocks, st);
+    luma_grad_kernel<<<blocks, 256, 0, st>>>(dy, plane, dL_dimg);
+    return check_launch("luminance loss kernels");
+}
+
 extern "C" int32_t gsr_psnr_workspace_size(int64_t count, size_t *bytes) {
     if (count < 0 || !bytes) {
         set_error("gsr_psnr_workspace_size: bad arguments");

@@ -168,7 +168,17 @@ class ViewBuffers:
                          _p(n_blended), _stream(stream))
 
     def loss_fwd_bwd(self, gt: torch.Tensor, lam: float = LAMBDA_DSSIM, stream=None):
+        """Eq. 4 against gt: an RGB target (3 x H x W), or a grayscale one
+        (1 x H x W), then on the render's luminance."""
         H, W = self.cam.height, self.cam.width
+        if gt.shape[0] == 1:
+            sz = ctypes.c_size_t()
+            L.gsr_loss_luma_workspace_size(H, W, ctypes.byref(sz))
+            if self.loss_ws.numel() < sz.value:
+                self.loss_ws = torch.empty(int(sz.value), dtype=torch.uint8, device=self.img.device)
+            L.gsr_loss_luma_fwd_bwd(_p(self.img), _p(gt), H, W, float(lam), _p(self.loss), _p(self.dimg),
+                                    _p(self.loss_ws), self.loss_ws.numel(), _stream(stream))
+            return
         L.gsr_loss_fwd_bwd(_p(self.img), _p(gt), 3, H, W, float(lam), _p(self.loss), _p(self.dimg),
                            _p(self.loss_ws), self.loss_ws.numel(), _stream(stream))
 

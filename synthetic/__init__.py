@@ -228,3 +228,14 @@ def densify_scene(p: Params, cams, per_keyframe: int, seed: int):
         offsets.append(off)
         off += len(idx)
     return q, offsets, [h[1] for h in held]
+
+
+def stereo_pair(k: int, baseline: float = 0.11, f: float = 376.0, width: int = 752, height: int = 480):
+    """(left, right) cameras of a rectified stereo rig at pose k of the
+    trajectory: the right camera sits `baseline` metres along the left
+    camera's +x axis (EuRoC-shaped 752 x 480 monochrome views)."""
+    pos, yaw = trajectory(k)
+    left = pose_camera(pos, yaw, f, f, width, height)
+    right = Camera(left.R.copy(), left.t - np.array([baseline, 0.0, 0.0]), left.fx, left.fy, left.cx, left.cy,
+                   width, height)
+    return left, right

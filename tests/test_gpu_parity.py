@@ -429,3 +429,49 @@ def test_long_tile_segments_bit_exact(n):
     print(f"n {n}: pairs {len(keys_ref[0])}, longest tile segment {lengths.max()}")
     assert lengths.max() > (16384 if n == 20000 else 1024)
     _check_keys(vb, dec, keys_ref)
+
+
+@pytest.mark.parametrize("H,W", [(120, 160), (37, 53)])
+def test_luma_loss_matches_oracle(H, W):
+    """Grayscale target: Eq. 4 on the luminance, gradient spread over RGB by
+    the luminance weights."""
+    x = S.random_image(3, H, W, seed=5)
+    y = S.random_image(1, H, W, seed=6)
+    L_ref, dY = oracle.loss(oracle.luma(x), y, 0.2)
+    d_ref = np.concatenate([w * dY for w in (0.299, 0.587, 0.114)])
+    cam = gsr.camera_struct(np.eye(3), np.zeros(3), 100, 100, W / 2, H / 2, W, H)
+    vb = gsr.ViewBuffers(1, cam, gsr.tiling_struct(16, 16), 16)
+    vb.img.copy_(torch.tensor(x, device="cuda"))
+    vb.loss_fwd_bwd(torch.tensor(y, device="cuda"), 0.2)
+    torch.cuda.synchronize()
+    L = float(vb.loss.item())
+    d = vb.dimg.cpu().numpy().astype(np.float64)
+    assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
+    assert np.abs(d - d_ref).max() <= 1e-4 * np.abs(d_ref).max()
+
+
+def test_stereo_grayscale_mapping_reduces_the_loss():
+    """A mapping step over a stereo pair of grayscale views (luminance loss)
+    runs captured and lowers the loss of both views."""
+    base = S.room_scene(40000, seed=2)
+    left, right = S.stereo_pair(5, f=188.0, width=376, height=240)
+    g_ref = to_gpu(base)
+    views = []
+    for cam in (left, right):
+        vb = gsr.ViewBuffers(base.n, gsr.camera_from(cam), gsr.tiling_struct(16, 16), 1 << 16)
+        gsr.ensure_capacity(vb, g_ref)
+        vb.forward(g_ref)
+        y = (0.299 * vb.img[0] + 0.587 * vb.img[1] + 0.114 * vb.img[2])[None].contiguous()
+        views.append((cam, y))
+    ms = gsr.MappingStep(to_gpu(S.perturb(base)), views)
+    ms.capture()
+    first, last = [], []
+    for it in range(60):
+        ms.step()
+        if it < 2:
+            first.append(float(ms.vb.loss.item()))
+        if it >= 58:
+            last.append(float(ms.vb.loss.item()))
+    assert ms.status() == 0
+    print(f"stereo grayscale losses: first {first}, last {last}")
+    assert last[0] < first[0] and last[1] < first[1]

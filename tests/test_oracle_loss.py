@@ -68,3 +68,14 @@ def test_gradient_matches_central_differences():
         xm[idx] -= h
         fd[idx] = (oracle.loss(xp, y, 0.2, grad=False) - oracle.loss(xm, y, 0.2, grad=False)) / (2 * h)
     np.testing.assert_allclose(d, fd, rtol=1e-6, atol=1e-11)
+
+
+def test_luma_weights():
+    """Gray stays gray (the weights sum to one); each pure channel gives its
+    BT.601 weight."""
+    g = np.full((3, 4, 5), 0.37)
+    assert np.allclose(oracle.luma(g), 0.37, atol=1e-15)
+    for c, w in enumerate((0.299, 0.587, 0.114)):
+        e = np.zeros((3, 2, 2))
+        e[c] = 1.0
+        assert np.allclose(oracle.luma(e), w, atol=1e-15)

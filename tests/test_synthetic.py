@@ -30,3 +30,12 @@ def test_orb_angle_points_to_the_bright_side():
     img = np.zeros((3, 40, 40))
     img[:, 25:, :] = 1.0  # bright below
     assert abs(S.orb_angle(img, 20, 20) - np.pi / 2) < 1e-9
+
+
+def test_stereo_pair_baseline():
+    left, right = S.stereo_pair(3)
+    cl = -left.R.T @ left.t
+    cr = -right.R.T @ right.t
+    assert np.isclose(np.linalg.norm(cr - cl), 0.11)
+    # the right centre lies along the left camera's x axis
+    assert np.allclose(left.R @ (cr - cl), [0.11, 0.0, 0.0])
