@@ -9,7 +9,7 @@ dataset itself is not available).  The path does not shard: with --gpus N
 every rank runs an independent replica (weak scaling, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode mapping|window|mlp|ttp|densify|stereo]
+                  [--mode mapping|window|mlp|ttp|densify|stereo|gp_ablation]
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this path) on the host cores, on a bounded band of image rows per step.
@@ -22,8 +22,9 @@ default initialisation against the batched window with the learned
 initialiser, and with the default one); --mode densify runs mapping on a
 1M-Gaussian 1920 x 1080 scene with densification and pruning every 100
 iterations (uneven Gaussian counts); --mode stereo maps 752 x 480 grayscale
-stereo pairs (0.11 m baseline, luminance loss).  The default (mapping) line
-is the headline.
+stereo pairs (0.11 m baseline, luminance loss); --mode gp_ablation compares
+the final PSNR of the plain path with 1 to 4 pyramid levels (Sec. 4.4,
+Tab. 4).  The default (mapping) line is the headline.
 """
 from __future__ import annotations
 
@@ -707,6 +708,51 @@ def run_stereo(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- Gaussian-pyramid ablation
+def run_gp_ablation(args):
+    """Plain path with n + 1 = 1 .. 4 pyramid levels on the held-out
+    time-to-PSNR scenes, same iteration budget: final PSNR and time (the
+    paper's ablation of GP learning, Sec. 4.4, Tab. 4, and its remark that
+    more levels stop helping)."""
+    import torch
+    import paper_2311_16728_b300 as gsr
+    from paper_2311_16728_b300.mapping import Evaluator, PlainMapper, densify_default
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    seeds = [int(x) for x in args.ttp_seeds.split(",") if x][:3]
+    budget = TTP_BUDGET
+    rows = {}
+    for seed in seeds:
+        truth, keyframes, kps, offsets = _ttp_setup(seed, gsr, torch)
+        ev = Evaluator(TTP_N, keyframes)
+        for levels in (1, 2, 3, 4):
+            params = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
+            densify_default(params, keyframes, kps, offsets)
+            pm = PlainMapper(params, keyframes, levels=levels)
+            pm.capture()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(budget):
+                pm.step()
+            e1.record()
+            torch.cuda.synchronize()
+            if pm.status() != 0:
+                raise RuntimeError(f"device status {pm.status():#x}")
+            rows.setdefault(str(levels), []).append({"seed": seed, "psnr": ev(params), "ms": e0.elapsed_time(e1)})
+            del pm, params
+    summary = {k: {"psnr_mean": statistics.mean(r["psnr"] for r in v), "ms_mean": statistics.mean(r["ms"] for r in v)}
+               for k, v in rows.items()}
+    best = max(summary, key=lambda k: summary[k]["psnr_mean"])
+    line = {"metric": "Gaussian-pyramid ablation: final PSNR of the plain path with 1-4 levels",
+            "value": summary["3"]["psnr_mean"] - summary["1"]["psnr_mean"], "unit": "dB (3 levels minus 1)",
+            "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; held-out scenes)",
+            "config": {"workload": f"time-to-PSNR scenes {seeds}, default initialisation, {budget} iterations of the "
+                                   "plain path (one view per iteration, tau_u 30) with n + 1 pyramid levels",
+                       "best_levels": int(best)},
+            "levels": summary, "per_seed": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -715,7 +761,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8, help="image rows per oracle step (reference arm)")
     ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
-    ap.add_argument("--mode", default="mapping", choices=["mapping", "window", "mlp", "ttp", "densify", "stereo"])
+    ap.add_argument("--mode", default="mapping",
+                    choices=["mapping", "window", "mlp", "ttp", "densify", "stereo", "gp_ablation"])
     ap.add_argument("--ttp-seeds", default="100,101,102,103,104", help="ttp mode: held-out evaluation scenes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
@@ -742,6 +789,9 @@ def main():
         return
     if args.mode == "stereo":
         run_stereo(args)
+        return
+    if args.mode == "gp_ablation":
+        run_gp_ablation(args)
         return
 
     import torch
