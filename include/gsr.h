@@ -289,11 +289,17 @@ int32_t gsr_batched_preprocess(const gsr_gaussians *g, const gsr_camera *cams, i
 
 /* gsr_bin_sort over all views' records (n_per_view each); tile ranges for the
  * sum over views of their tiles.  Workspace: gsr_bin_sort_workspace_size with
- * n = n_per_view x nviews. */
+ * n = n_per_view x nviews.  With `compact` (may be NULL; arrays of
+ * n_per_view x nviews entries) the records of the visible list are first
+ * gathered in index order into compact->xy_conic, c_op_box, rgb_depth (the
+ * c-th visible record at position c), compact->ntiles[r] receives record r's
+ * position c (for records with proj->ntiles[r] > 0), and the pairs' values are
+ * these positions: the window's later passes then read records and
+ * accumulate gradients in dense arrays (the order of the pairs is the same). */
 int32_t gsr_batched_bin_sort(const gsr_proj *proj, int64_t n_per_view, const gsr_camera *cams, int32_t nviews,
                              const gsr_tiling *tiling, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
-                             uint32_t *tile_ranges, int64_t *d_num_pairs, void *workspace, size_t workspace_bytes,
-                             int32_t *d_status, gsr_stream_t stream);
+                             uint32_t *tile_ranges, int64_t *d_num_pairs, const gsr_proj *compact, void *workspace,
+                             size_t workspace_bytes, int32_t *d_status, gsr_stream_t stream);
 
 /* Bytes of scratch for gsr_batched_iterate over these views. */
 int32_t gsr_batched_iterate_workspace_size(const gsr_camera *cams, int32_t nviews, size_t *bytes);
@@ -302,7 +308,9 @@ int32_t gsr_batched_iterate_workspace_size(const gsr_camera *cams, int32_t nview
  * every (view, tile), both SSIM passes of every (view, channel, 32 x 32
  * block), the per-view losses (d_losses[v]), dL_dimg[v] = weight_v dL_v/dI_v,
  * and the backward blend of every (view, tile), accumulating into grad2d
- * (nviews x n records; must be zero on entry -- gsr_batched_preprocess_bwd
+ * (one entry per record that the pairs' values index: proj are the records
+ * the binning's values refer to, the compact ones when it gathered them;
+ * must be zero on entry -- gsr_batched_preprocess_bwd
  * leaves it zero).  Work is pulled from atomic queues so uneven resolutions
  * balance; the phases are separated by grid-wide barriers whose waits are
  * bounded (about a second): a wait that gives up sets GSR_ERR_TIMEOUT in
@@ -326,10 +334,13 @@ int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *vals, const ui
  * runs once per (Gaussian, keyframe): u, v scale by 2^-k, the dilated
  * covariance is 4^-k M + 0.3 I, and opacity and colour are shared.
  * touched (n u32, may be NULL) receives 1 for every Gaussian some view saw,
- * else 0: the flags gsr_adam_step_touched takes. */
-int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
-                                   int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
-                                   const gsr_param_buffers *grads, uint32_t *touched, gsr_stream_t stream);
+ * else 0: the flags gsr_adam_step_touched takes.  proj gives the records'
+ * visibility (ntiles); with `compact` (as passed to gsr_batched_bin_sort)
+ * the conics and grad2d are read at the compact positions. */
+int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_proj *compact,
+                                   const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling,
+                                   const gsr_grad2d *grad2d, const gsr_param_buffers *grads, uint32_t *touched,
+                                   gsr_stream_t stream);
 
 /* ---------------------------------------------------------------- */
 /* Default initialisation of new primitives (Sec. 3.3.1)             */

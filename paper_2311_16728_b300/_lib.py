@@ -96,13 +96,13 @@ _SIGNATURES = {
                         c_void_p], c_int32),
     "gsr_batched_preprocess": ([P(gsr_gaussians), c_void_p, c_int32, P(gsr_tiling), P(gsr_proj), c_void_p], c_int32),
     "gsr_batched_bin_sort": ([P(gsr_proj), c_int64, c_void_p, c_int32, P(gsr_tiling), c_void_p, c_void_p, c_int64,
-                              c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+                              c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "gsr_batched_iterate_workspace_size": ([c_void_p, c_int32, P(c_size_t)], c_int32),
     "gsr_batched_iterate": ([P(gsr_proj), c_void_p, c_void_p, c_void_p, c_int32, P(gsr_tiling), c_void_p, c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, P(gsr_grad2d),
                              c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
-    "gsr_batched_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_int32, P(gsr_tiling), P(gsr_grad2d),
-                                    P(gsr_param_buffers), c_void_p, c_void_p], c_int32),
+    "gsr_batched_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), c_void_p, c_void_p, c_int32, P(gsr_tiling),
+                                    P(gsr_grad2d), P(gsr_param_buffers), c_void_p, c_void_p], c_int32),
     "gsr_default_init_workspace_size": ([c_int64, c_int64, P(c_size_t)], c_int32),
     "gsr_default_init": ([c_void_p, c_int32, c_int32, c_void_p, c_int64, P(gsr_camera), P(gsr_param_buffers), c_int64,
                           c_int64, c_void_p, c_size_t, c_void_p], c_int32),

@@ -49,6 +49,13 @@ class BatchedWindow:
         self.c_op_box = torch.empty(m, 4, **f32)
         self.rgb_depth = torch.empty(m, 4, **f32)
         self.ntiles = torch.zeros(m, dtype=torch.int32, device=dev)
+        # the visible records gathered densely by the binning (the pairs'
+        # values index these; rec_to_c maps a record to its position), so the
+        # persistent launch and the chain rule touch arrays that stay in L2
+        self.cxy = torch.empty(m, 4, **f32)
+        self.ccb = torch.empty(m, 4, **f32)
+        self.crd = torch.empty(m, 4, **f32)
+        self.rec_to_c = torch.zeros(m, dtype=torch.int32, device=dev)
         self.tiles = sum(n_tiles(v[0], self.tiling) for v in views)
         self.ranges = torch.zeros(self.tiles, 2, dtype=torch.int32, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -94,6 +101,9 @@ class BatchedWindow:
         return L.gsr_proj(self.xy_conic.data_ptr(), self.c_op_box.data_ptr(), self.rgb_depth.data_ptr(),
                           self.ntiles.data_ptr())
 
+    def compact(self) -> L.gsr_proj:
+        return L.gsr_proj(self.cxy.data_ptr(), self.ccb.data_ptr(), self.crd.data_ptr(), self.rec_to_c.data_ptr())
+
     def grad2d(self) -> L.gsr_grad2d:
         return L.gsr_grad2d(self.g2[0].data_ptr(), self.g2[1].data_ptr(), self.g2[2].data_ptr())
 
@@ -104,13 +114,13 @@ class BatchedWindow:
                                  _stream(stream))
 
     def bin_sort(self, stream=None):
-        pr = self.proj()
+        pr, cp = self.proj(), self.compact()
         L.gsr_batched_bin_sort(ctypes.byref(pr), self.n, self.cams, self.V, ctypes.byref(self.tiling), _p(self.keys),
-                               _p(self.vals), self.cap, _p(self.ranges), _p(self.num_pairs), _p(self.sort_ws),
-                               self.sort_ws.numel(), _p(self.status), _stream(stream))
+                               _p(self.vals), self.cap, _p(self.ranges), _p(self.num_pairs), ctypes.byref(cp),
+                               _p(self.sort_ws), self.sort_ws.numel(), _p(self.status), _stream(stream))
 
     def iterate(self, stream=None):
-        pr, g2 = self.proj(), self.grad2d()
+        pr, g2 = self.compact(), self.grad2d()
         L.gsr_batched_iterate(ctypes.byref(pr), _p(self.vals), _p(self.ranges), self.cams, self.V,
                               ctypes.byref(self.tiling), self.bg, self.p_img, self.p_T, self.p_nc, self.p_gt,
                               self.p_dimg, self.weights, self.lam, _p(self.losses), ctypes.byref(g2), _p(self.iter_ws),
@@ -126,8 +136,9 @@ class BatchedWindow:
                 "ssim_grad": (t[3] - t[2]) * 1e-6, "entry_to_bwd": (t[3] - t[0]) * 1e-6}
 
     def chain(self, stream=None):
-        gs, pr, g2, gb = self.params.gaussians_struct(), self.proj(), self.grad2d(), self.grads.buffers_struct()
-        L.gsr_batched_preprocess_bwd(ctypes.byref(gs), ctypes.byref(pr), self.cams, self.V, ctypes.byref(self.tiling),
+        gs, pr, cp = self.params.gaussians_struct(), self.proj(), self.compact()
+        g2, gb = self.grad2d(), self.grads.buffers_struct()
+        L.gsr_batched_preprocess_bwd(ctypes.byref(gs), ctypes.byref(pr), ctypes.byref(cp), self.cams, self.V, ctypes.byref(self.tiling),
                                      ctypes.byref(g2), ctypes.byref(gb), _p(self.touched), _stream(stream))
 
     STAGES = ("preprocess", "bin_sort", "iterate", "chain", "adam")

@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
                                                                     const float4 *__restrict__ xy_conic,
                                                                     const float4 *__restrict__ c_op_box,
                                                                     const uint32_t *__restrict__ ntiles,
+                                                                    const uint32_t *__restrict__ rec_to_c,
                                                                     float4 *__restrict__ g0, float4 *__restrict__ g1,
                                                                     float4 *__restrict__ g2, float4 *__restrict__ d_mo,
                                                                     float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
@@ -372,8 +373,11 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
         ScreenGrad sg = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float sb = CG.scale[grp][mb];
         for (int m = mb; m < CG.count[grp]; ++m) {
-            const int64_t r = (int64_t)CG.member[grp][m] * g.n + i;
-            if (ntiles[r] == 0u) continue;
+            const int64_t rec = (int64_t)CG.member[grp][m] * g.n + i;
+            if (ntiles[rec] == 0u) continue;
+            // records and screen-space gradients: at the record, or at its
+            // compact position when the binning gathered the records
+            const int64_t r = rec_to_c ? (int64_t)rec_to_c[rec] : rec;
             const float4 G0 = g0[r], G1 = g1[r], G2 = g2[r];
             const float4 xc = __ldg(xy_conic + r), cb = __ldg(c_op_box + r);
             const float s = CG.scale[grp][m] / sb;  // exact: both are powers of two
@@ -601,10 +605,10 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     return check_launch("batched_iterate_kernel");
 }
 
-extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cams,
-                                              int32_t nviews, const gsr_tiling *tiling, const gsr_grad2d *grad2d,
-                                              const gsr_param_buffers *grads, uint32_t *touched,
-                                              gsr_stream_t stream) {
+extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_proj *compact,
+                                              const gsr_camera *cams, int32_t nviews, const gsr_tiling *tiling,
+                                              const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
+                                              uint32_t *touched, gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_gaussians(g)) || (rc = validate_tiling(tiling))) return rc;
     ViewsK V;
@@ -615,7 +619,8 @@ extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_
         set_error("gsr_batched_preprocess_bwd: NULL pointer");
         return GSR_ERR_INVALID_ARG;
     }
-    if (!proj->xy_conic || !proj->c_op_box) {
+    const gsr_proj *rp = compact ? compact : proj;
+    if (!rp->xy_conic || !rp->c_op_box || (compact && !compact->ntiles)) {
         set_error("gsr_batched_preprocess_bwd: NULL record pointer");
         return GSR_ERR_INVALID_ARG;
     }
@@ -623,8 +628,9 @@ extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_
     make_groups(cams, nviews, CG);
     const size_t smem = sizeof(uint32_t) * kChainChunk * CG.ngroups;
     batched_chain_kernel<<<(unsigned)((g->n + kChainChunk - 1) / kChainChunk), kBwdThreads, smem, as_cuda(stream)>>>(
-        make_gk(g), V, CG, reinterpret_cast<const float4 *>(proj->xy_conic),
-        reinterpret_cast<const float4 *>(proj->c_op_box), proj->ntiles, reinterpret_cast<float4 *>(grad2d->g0),
+        make_gk(g), V, CG, reinterpret_cast<const float4 *>(rp->xy_conic),
+        reinterpret_cast<const float4 *>(rp->c_op_box), proj->ntiles, compact ? compact->ntiles : nullptr,
+        reinterpret_cast<float4 *>(grad2d->g0),
         reinterpret_cast<float4 *>(grad2d->g1), reinterpret_cast<float4 *>(grad2d->g2),
         reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),
         reinterpret_cast<float4 *>(grads->logscale), reinterpret_cast<float4 *>(grads->sh), touched);

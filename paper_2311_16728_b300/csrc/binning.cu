@@ -125,10 +125,21 @@ __global__ void __launch_bounds__(kScanThreads) count_kernel(const uint32_t *__r
     }
 }
 
+// Records of the visible list gathered into dense arrays (position = rank in
+// index order) with rec_to_c[record] = position: the later passes then read
+// and accumulate into arrays that stay in L2 instead of the sparse
+// views x n ones.  All NULL: no gathering.
+struct Gather {
+    const float4 *xy, *cb, *rd;
+    float4 *cxy, *ccb, *crd;
+    uint32_t *rec_to_c;
+};
+
 // Pass 2: the visible records in index order (order[]), the first candidate
 // slot of each (coff[], with coff[nv] = the candidate total), *d_nvis and
-// *d_ncand.  Candidate numbers are 32-bit: a frame with 2^32 or more
-// candidates sets GSR_ERR_UNSUPPORTED and expands nothing.
+// *d_ncand, and the gathered records when gt.cxy is set.  Candidate numbers
+// are 32-bit: a frame with 2^32 or more candidates sets GSR_ERR_UNSUPPORTED
+// and expands nothing.
 __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
                                                                const uint32_t *__restrict__ vis_sums,
                                                                const uint32_t *__restrict__ cand_sums,
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t *_
                                                                uint32_t *__restrict__ coff,
                                                                int64_t *__restrict__ d_nvis,
                                                                int64_t *__restrict__ d_ncand,
-                                                               int32_t *__restrict__ d_status) {
+                                                               int32_t *__restrict__ d_status, Gather gt) {
     __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_red[16];
     int64_t vis_total, cand_total;
@@ -166,6 +177,12 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t *_
         if (t[k] > 0u) {
             order[pos] = (uint32_t)(base + k);
             coff[pos] = (uint32_t)off;
+            if (gt.cxy) {
+                gt.cxy[pos] = __ldg(gt.xy + base + k);
+                gt.ccb[pos] = __ldg(gt.cb + base + k);
+                gt.crd[pos] = __ldg(gt.rd + base + k);
+                gt.rec_to_c[base + k] = (uint32_t)pos;
+            }
             ++pos;
             off += t[k];
         }
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     const float4 *__restrict__ c_op_box, const float4 *__restrict__ rgb_depth, const int64_t *__restrict__ d_nvis,
     int64_t cap_n, const int64_t *__restrict__ d_ncand, int tw, int th, const ViewTiles vt, uint32_t ntiles_total,
     uint32_t *__restrict__ counts, uint64_t *__restrict__ kept_ts, uint64_t *__restrict__ kept_sk, int64_t cap,
-    unsigned long long *__restrict__ d_kept) {
+    unsigned long long *__restrict__ d_kept, bool compact) {
     __shared__ uint32_t s_off[kExpandTile + 1];
     __shared__ uint32_t s_warp[8];
     __shared__ int64_t s_i0;
@@ -240,12 +257,15 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
                     if (s_off[mid] <= (uint32_t)slot) lo = mid;
                     else hi = mid;
                 }
-                const uint32_t gid = order[i0 + lo];
+                const uint32_t rec = order[i0 + lo];
+                // the pair's value: the record, or its position in the visible
+                // list when the records were gathered into compact arrays
+                const uint32_t gid = compact ? (uint32_t)(i0 + lo) : rec;
                 const int k = (int)((uint32_t)slot - s_off[lo]);
                 const Splat sp = load_splat(xy_conic, c_op_box, gid);
                 const int tx0 = sp.x0 / tw, ntx = sp.x1 / tw - tx0 + 1;
                 const int tx = tx0 + k % ntx, ty = sp.y0 / th + k / ntx;
-                const int v = (int)((int64_t)gid / vt.n_per_view);  // view of this record
+                const int v = (int)((int64_t)rec / vt.n_per_view);  // view of this record
                 const uint32_t tile = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
                 if (tile < ntiles_total &&
                     tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1)) {
@@ -646,7 +666,7 @@ namespace gsr {
 int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int64_t tiles, const gsr_tiling *tiling,
                       uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *tile_ranges,
                       int64_t *d_num_pairs, void *workspace, size_t workspace_bytes, int32_t *d_status,
-                      gsr_stream_t stream) {
+                      gsr_stream_t stream, const gsr_proj *compact = nullptr) {
     int32_t rc;
     if (!proj || (n > 0 && (!proj->ntiles || !proj->xy_conic || !proj->c_op_box || !proj->rgb_depth)) || n < 0 ||
         pair_capacity < 0 || !tile_ranges || !d_num_pairs || (pair_capacity > 0 && (!keys || !vals))) {
@@ -684,19 +704,32 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     uint64_t *seg = reinterpret_cast<uint64_t *>(ws + L.seg);
     uint32_t *list = reinterpret_cast<uint32_t *>(ws + L.list);
     uint32_t *list2 = reinterpret_cast<uint32_t *>(ws + L.list2);
-    const float4 *xy = reinterpret_cast<const float4 *>(proj->xy_conic);
-    const float4 *cb = reinterpret_cast<const float4 *>(proj->c_op_box);
-    const float4 *rd = reinterpret_cast<const float4 *>(proj->rgb_depth);
+    if (compact && (!compact->xy_conic || !compact->c_op_box || !compact->rgb_depth || !compact->ntiles ||
+                    !aligned16(compact->xy_conic) || !aligned16(compact->c_op_box) || !aligned16(compact->rgb_depth))) {
+        set_error("gsr_batched_bin_sort: compact record arrays must be non-NULL and 16-byte aligned");
+        return GSR_ERR_INVALID_ARG;
+    }
+    const gsr_proj *rp = compact ? compact : proj;  // the records the pairs index
+    const float4 *xy = reinterpret_cast<const float4 *>(rp->xy_conic);
+    const float4 *cb = reinterpret_cast<const float4 *>(rp->c_op_box);
+    const float4 *rd = reinterpret_cast<const float4 *>(rp->rgb_depth);
     const unsigned sb = (unsigned)L.scan_blocks;
     // 1-2. visible records in index order and their candidate offsets (the
     // first pass also zeroes the tile counters and the kept-pair counter)
     count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, tile_ranges, 2 * tiles, d_kept);
+    Gather gt{};
+    if (compact)
+        gt = Gather{reinterpret_cast<const float4 *>(proj->xy_conic), reinterpret_cast<const float4 *>(proj->c_op_box),
+                    reinterpret_cast<const float4 *>(proj->rgb_depth), reinterpret_cast<float4 *>(compact->xy_conic),
+                    reinterpret_cast<float4 *>(compact->c_op_box), reinterpret_cast<float4 *>(compact->rgb_depth),
+                    compact->ntiles};
     compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, L.scan_blocks, order, coff,
-                                                d_nvis, d_ncand, d_status);
+                                                d_nvis, d_ncand, d_status, gt);
     // 3. cull + unordered kept list + tile counts (in the range words)
     expand_kernel<<<kExpandGrid, kExpandThreads, 0, st>>>(coff, order, xy, cb, rd, d_nvis, n, d_ncand,
                                                           tiling->tile_w, tiling->tile_h, vt, (uint32_t)tiles,
-                                                          tile_ranges, kept_ts, kept_sk, pair_capacity, d_kept);
+                                                          tile_ranges, kept_ts, kept_sk, pair_capacity, d_kept,
+                                                          compact != nullptr);
     if ((rc = check_launch("pair expansion"))) return rc;
     // 4-6. ranges, scatter into tile segments, sort each segment
     tile_scan_kernel<<<1, kTileScanThreads, 0, st>>>(tile_ranges, (uint32_t)tiles, d_kept, pair_capacity, list,
@@ -734,8 +767,8 @@ extern "C" int32_t gsr_bin_sort(const gsr_proj *proj, int64_t n, const gsr_camer
 extern "C" int32_t gsr_batched_bin_sort(const gsr_proj *proj, int64_t n_per_view, const gsr_camera *cams,
                                         int32_t nviews, const gsr_tiling *tiling, uint64_t *keys, uint32_t *vals,
                                         int64_t pair_capacity, uint32_t *tile_ranges, int64_t *d_num_pairs,
-                                        void *workspace, size_t workspace_bytes, int32_t *d_status,
-                                        gsr_stream_t stream) {
+                                        const gsr_proj *compact, void *workspace, size_t workspace_bytes,
+                                        int32_t *d_status, gsr_stream_t stream) {
     int32_t rc;
     if ((rc = validate_tiling(tiling))) return rc;
     if (!cams || nviews <= 0 || nviews > kMaxViews || n_per_view < 0) {
@@ -757,5 +790,5 @@ extern "C" int32_t gsr_batched_bin_sort(const gsr_proj *proj, int64_t n_per_view
         return GSR_ERR_UNSUPPORTED;
     }
     return bin_sort_impl(proj, n_per_view * nviews, vt, tiles, tiling, keys, vals, pair_capacity, tile_ranges,
-                         d_num_pairs, workspace, workspace_bytes, d_status, stream);
+                         d_num_pairs, workspace, workspace_bytes, d_status, stream, compact);
 }

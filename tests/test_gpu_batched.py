@@ -69,7 +69,12 @@ def test_one_view_equals_single_view_path():
     npairs = int(vb.num_pairs.item())
     assert int(bw.num_pairs.item()) == npairs
     assert torch.equal(bw.keys[:npairs], vb.keys[:npairs])
-    assert torch.equal(bw.vals[:npairs], vb.vals[:npairs])
+    # the window's values are compact positions of the gathered records
+    rec = vb.vals[:npairs].long()
+    assert torch.equal(bw.rec_to_c[rec], bw.vals[:npairs])
+    c = bw.vals[:npairs].long()
+    assert torch.equal(bw.cxy[c], bw.xy_conic[rec]) and torch.equal(bw.ccb[c], bw.c_op_box[rec])
+    assert torch.equal(bw.crd[c], bw.rgb_depth[rec])
     assert torch.equal(bw.ranges, vb.ranges)
     assert torch.equal(bw.imgs[0], vb.img), "image differs from the single-view path"
     assert torch.equal(bw.T[0], vb.T_final)
