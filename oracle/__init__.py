@@ -180,7 +180,7 @@ def render(sc: Scene64, cam, W: int, H: int, dec: Decisions, bg=(0.0, 0.0, 0.0),
            rows=None):
     """Returns (img (3,H,W), T_final (H,W), n_contrib (H,W), margin (H,W))."""
     y0, y1 = (0, H) if rows is None else rows
-    cam = _f32(cam)
+    cam = _f64(cam)
     bg = _f64(bg)
     img = np.zeros((3, H, W))
     T = np.zeros((H, W))
@@ -198,7 +198,7 @@ def render_bwd(sc: Scene64, cam, W: int, H: int, dec: Decisions, dimg, bg=(0.0, 
     """Returns (grad (N, 60), grad2d (N, 9)) [, grad2d_mag (N, 9)]: the magnitude
     is the per-element sum of |pixel term| (condition scale of each sum)."""
     y0, y1 = (0, H) if rows is None else rows
-    cam = _f32(cam)
+    cam = _f64(cam)
     bg = _f64(bg)
     dimg = _f64(dimg)
     assert dimg.shape == (3, H, W)
@@ -213,7 +213,7 @@ def render_bwd(sc: Scene64, cam, W: int, H: int, dec: Decisions, dimg, bg=(0.0, 
 
 
 def chain(sc: Scene64, cam, W: int, H: int, dec: Decisions, g2):
-    cam = _f32(cam)
+    cam = _f64(cam)
     g2 = _f64(g2)
     g = np.zeros((sc.n, 60))
     rc = lib().orc_chain(sc.n, _p(sc.mean_op), _p(sc.quat), _p(sc.logscale), _p(sc.sh), sc.sh_degree, _p(cam), W, H,
@@ -222,9 +222,23 @@ def chain(sc: Scene64, cam, W: int, H: int, dec: Decisions, g2):
     return g
 
 
+def pose_grad(sc: Scene64, cam, W: int, H: int, dec: Decisions, g2, with_magnitude: bool = False):
+    """Camera pose gradient from the screen-space gradients g2 (N, 9):
+    15 values dL/dR (row-major), dL/dt, dL/dphi (left rotation about the
+    camera centre) [, and the sums of their per-Gaussian parts' |.|]."""
+    cam = _f64(cam)
+    g2 = _f64(g2)
+    pose = np.zeros(15)
+    mag = np.zeros(15)
+    rc = lib().orc_pose_grad(sc.n, _p(sc.mean_op), _p(sc.quat), _p(sc.logscale), _p(sc.sh), sc.sh_degree, _p(cam),
+                             W, H, _p(dec.visible), _p(g2), _p(pose), _p(mag))
+    assert rc == 0
+    return (pose, mag) if with_magnitude else pose
+
+
 def project(sc: Scene64, cam, W: int, H: int, visible):
     """(N, 16): u, v, A, B, C, opacity, r, g, b, depth, a', b', c', raw r, g, b."""
-    cam = _f32(cam)
+    cam = _f64(cam)
     vis = np.ascontiguousarray(visible, np.uint8)
     out = np.zeros((sc.n, 16))
     rc = lib().orc_project(sc.n, _p(sc.mean_op), _p(sc.quat), _p(sc.logscale), _p(sc.sh), sc.sh_degree, _p(cam), W,

@@ -440,6 +440,7 @@ int orc_keys(int64_t n, const uint8_t *visible, const float *depth, const int32_
 /* ------------------------------------------------------------------------- */
 
 typedef struct {
+    double mu[3];          /* world-space mean                           */
     double pc[3];          /* camera-space mean                          */
     double s[3];           /* exp(logscale)                              */
     double qn[4], qnorm;   /* normalised quaternion (w,x,y,z), |q|       */
@@ -466,7 +467,9 @@ typedef struct {
     int W, H;
 } orc_cam;
 
-static orc_cam make_cam(const float *cam, int W, int H) {
+/* The FP64 path takes the camera in FP64 (an FP32 camera widens exactly);
+ * the decision chain keeps its FP32 copy. */
+static orc_cam make_cam(const double *cam, int W, int H) {
     orc_cam c;
     for (int i = 0; i < 9; ++i) c.R[i] = cam[i];
     for (int i = 0; i < 3; ++i) c.t[i] = cam[9 + i];
@@ -481,6 +484,7 @@ static orc_cam make_cam(const float *cam, int W, int H) {
 static void project_one(const double *mo, const double *q, const double *ls, const double *sh,
                         int deg, const orc_cam *cam, orc_pre *p) {
     const double *W = cam->R;
+    for (int i = 0; i < 3; ++i) p->mu[i] = mo[i];
     for (int i = 0; i < 3; ++i)
         p->pc[i] = W[3 * i] * mo[0] + W[3 * i + 1] * mo[1] + W[3 * i + 2] * mo[2] + cam->t[i];
     for (int i = 0; i < 3; ++i) p->s[i] = exp(ls[i]);
@@ -658,7 +662,7 @@ static int64_t pixel_walk(int px, int py, const int64_t *order, int64_t nv, cons
  * threshold (pixels with a tiny margin may legitimately differ between an
  * FP32 and an FP64 evaluation). */
 int orc_render(int64_t n, const double *mean_op, const double *quat, const double *logscale,
-               const double *sh, int deg, const float *camf, int W, int H, const double *bg,
+               const double *sh, int deg, const double *camf, int W, int H, const double *bg,
                const uint8_t *visible, const float *depth, const int32_t *box, int flags,
                int y_begin, int y_end, double *img, double *T_final, int32_t *n_contrib,
                double *margin) {
@@ -696,9 +700,14 @@ int orc_render(int64_t n, const double *mean_op, const double *quat, const doubl
 
 /* Chain the per-Gaussian screen-space gradients g2 = (du, dv, dA, dB, dC,
  * dopacity, dr, dg, db) to the 60-float parameter gradient layout
- * (mean x y z, opacity logit, quat w x y z, logscale 0 1 2, pad, sh[48]). */
+ * (mean x y z, opacity logit, quat w x y z, logscale 0 1 2, pad, sh[48]).
+ * pose (may be NULL) receives (+=) this Gaussian's part of the camera pose
+ * gradient, 15 values: dL/dR (row-major, R taken as a general 3 x 3 matrix),
+ * dL/dt, and dL/dphi for the left perturbation R <- exp([phi]x) R,
+ * t <- exp([phi]x) t (a rotation about the camera centre); pose_mag (may be
+ * NULL) the absolute values of the same parts. */
 static void chain_one(const orc_pre *p, const orc_cam *cam, const double *sh, int deg,
-                      const double *g2, double *out) {
+                      const double *g2, double *out, double *pose, double *pose_mag) {
     const double *W = cam->R;
     double dmean[3] = {0, 0, 0}, dpc[3] = {0, 0, 0};
     /* colour: c = max(0, sum_k sh_k Y_k(vhat) + 0.5) */
@@ -711,7 +720,9 @@ static void chain_one(const orc_pre *p, const orc_cam *cam, const double *sh, in
         for (int ch = 0; ch < 3; ++ch)
             for (int a = 0; a < 3; ++a) dvh[a] += dcol[ch] * sh[3 * k + ch] * p->dY[3 * k + a];
     double vd = dvh[0] * p->vh[0] + dvh[1] * p->vh[1] + dvh[2] * p->vh[2];
-    for (int a = 0; a < 3; ++a) dmean[a] += (dvh[a] - p->vh[a] * vd) / p->dirn;
+    double ddir[3]; /* dL/d(mean - camera centre) through the view direction */
+    for (int a = 0; a < 3; ++a) ddir[a] = (dvh[a] - p->vh[a] * vd) / p->dirn;
+    for (int a = 0; a < 3; ++a) dmean[a] += ddir[a];
     /* opacity */
     out[3] = g2[5] * p->opacity * (1.0 - p->opacity);
     /* conic -> Sigma' : G_S' = -Q G_Q Q with G_Q = [[dA, dB/2], [dB/2, dC]] */
@@ -763,6 +774,33 @@ static void chain_one(const orc_pre *p, const orc_cam *cam, const double *sh, in
     /* pc = W mean + t */
     for (int a = 0; a < 3; ++a) dmean[a] += W[a] * dpc[0] + W[3 + a] * dpc[1] + W[6 + a] * dpc[2];
     out[0] = dmean[0]; out[1] = dmean[1]; out[2] = dmean[2];
+    if (pose) {
+        /* the pose enters through pc = W mean + t, through T = J W (G_W = J^T G_T)
+         * and through the camera centre C = -W^T t of the view direction
+         * mean - C (G_C = -ddir) */
+        double c[15], GWc[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) GWc[3 * a + b] = p->J[a] * GT[b] + p->J[3 + a] * GT[3 + b];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                c[3 * a + b] = dpc[a] * p->mu[b] + GWc[3 * a + b] + ddir[b] * cam->t[a];
+        for (int a = 0; a < 3; ++a)
+            c[9 + a] = dpc[a] + W[3 * a] * ddir[0] + W[3 * a + 1] * ddir[1] + W[3 * a + 2] * ddir[2];
+        /* left rotation: d pc = phi x pc, d W = [phi]x W, the centre is fixed;
+         * <G, [phi]x W> = phi . (N21 - N12, N02 - N20, N10 - N01), N = G W^T */
+        double N[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                N[3 * a + b] = GWc[3 * a] * W[3 * b] + GWc[3 * a + 1] * W[3 * b + 1] + GWc[3 * a + 2] * W[3 * b + 2];
+        const double *pc = p->pc;
+        c[12] = pc[1] * dpc[2] - pc[2] * dpc[1] + N[7] - N[5];
+        c[13] = pc[2] * dpc[0] - pc[0] * dpc[2] + N[2] - N[6];
+        c[14] = pc[0] * dpc[1] - pc[1] * dpc[0] + N[3] - N[1];
+        for (int k = 0; k < 15; ++k) {
+            pose[k] += c[k];
+            if (pose_mag) pose_mag[k] += fabs(c[k]);
+        }
+    }
     /* Sig = M M^T, M = Rq diag(s) : G_M = 2 G_Sig M */
     double GM[9];
     for (int i = 0; i < 3; ++i)
@@ -804,7 +842,7 @@ static void chain_one(const orc_pre *p, const orc_cam *cam, const double *sh, in
  * taken in absolute value: the scale against which a finite-precision
  * evaluation of the same sum can err (its condition magnitude). */
 int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const double *logscale,
-                   const double *sh, int deg, const float *camf, int W, int H, const double *bg,
+                   const double *sh, int deg, const double *camf, int W, int H, const double *bg,
                    const uint8_t *visible, const float *depth, const int32_t *box, int flags,
                    int y_begin, int y_end, const double *dimg, double *grad, double *grad2d,
                    double *grad2d_mag) {
@@ -885,7 +923,7 @@ int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const d
         if (!visible[i]) continue;
         double shi[48];
         gather_sh(sh, n, i, shi);
-        chain_one(&pre[i], &cam, shi, deg, acc + (size_t)i * nacc, o);
+        chain_one(&pre[i], &cam, shi, deg, acc + (size_t)i * nacc, o, NULL, NULL);
     }
     free(acc);
     free(order);
@@ -896,7 +934,7 @@ int orc_render_bwd(int64_t n, const double *mean_op, const double *quat, const d
 /* Screen-space chain only (for checking the per-Gaussian chain rule by itself):
  * given g2[9n] computes grad[60n]. */
 int orc_chain(int64_t n, const double *mean_op, const double *quat, const double *logscale,
-              const double *sh, int deg, const float *camf, int W, int H, const uint8_t *visible,
+              const double *sh, int deg, const double *camf, int W, int H, const uint8_t *visible,
               const double *g2, double *grad) {
     orc_cam cam = make_cam(camf, W, H);
     orc_pre *pre = project_all(n, mean_op, quat, logscale, sh, deg, &cam, visible);
@@ -906,7 +944,33 @@ int orc_chain(int64_t n, const double *mean_op, const double *quat, const double
         if (!visible[i]) continue;
         double shi[48];
         gather_sh(sh, n, i, shi);
-        chain_one(&pre[i], &cam, shi, deg, g2 + 9 * i, o);
+        chain_one(&pre[i], &cam, shi, deg, g2 + 9 * i, o, NULL, NULL);
+    }
+    free(pre);
+    return 0;
+}
+
+/* Camera pose gradient (pose refinement against the map): given the
+ * screen-space gradients g2[9n] of the visible Gaussians, pose[15] receives
+ * the sum over them of their parts (chain_one): dL/dR (9, row-major), dL/dt
+ * (3), dL/dphi (3; the gradient along the translation of the same left
+ * perturbation is dL/dt).  pose_mag[15] (may be NULL) receives the sums of
+ * the parts' absolute values. */
+int orc_pose_grad(int64_t n, const double *mean_op, const double *quat, const double *logscale,
+                  const double *sh, int deg, const double *camf, int W, int H, const uint8_t *visible,
+                  const double *g2, double *pose, double *pose_mag) {
+    orc_cam cam = make_cam(camf, W, H);
+    orc_pre *pre = project_all(n, mean_op, quat, logscale, sh, deg, &cam, visible);
+    double o[60];
+    for (int k = 0; k < 15; ++k) {
+        pose[k] = 0.0;
+        if (pose_mag) pose_mag[k] = 0.0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (!visible[i]) continue;
+        double shi[48];
+        gather_sh(sh, n, i, shi);
+        chain_one(&pre[i], &cam, shi, deg, g2 + 9 * i, o, pose, pose_mag);
     }
     free(pre);
     return 0;
@@ -915,7 +979,7 @@ int orc_chain(int64_t n, const double *mean_op, const double *quat, const double
 /* Per-Gaussian FP64 screen-space quantities (for closed-form checks):
  * out[16 n] = u, v, A, B, C, opacity, r, g, b, depth, a', b', c', rgb_raw r g b */
 int orc_project(int64_t n, const double *mean_op, const double *quat, const double *logscale,
-                const double *sh, int deg, const float *camf, int W, int H, const uint8_t *visible,
+                const double *sh, int deg, const double *camf, int W, int H, const uint8_t *visible,
                 double *out) {
     orc_cam cam = make_cam(camf, W, H);
     orc_pre *pre = project_all(n, mean_op, quat, logscale, sh, deg, &cam, visible);
