@@ -222,6 +222,24 @@ int32_t gsr_preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, const g
                            const gsr_tiling *tiling, const gsr_grad2d *grad2d, const gsr_param_buffers *grads,
                            float *densify_stat, float *densify_count, gsr_stream_t stream);
 
+/* Camera pose gradient, for photometric pose refinement of a frame against
+ * a fixed map (the camera (R, t) of the Eq. 3 projection as the variable).
+ * From the screen-space gradients of the Gaussians with ntiles > 0 (grad2d
+ * as gsr_blend_bwd leaves it), adds (+=) into d_pose (15 floats, device):
+ *   d_pose[0..8]   dL/dR, row-major, R taken as a general 3 x 3 matrix;
+ *   d_pose[9..11]  dL/dt;
+ *   d_pose[12..14] dL/dphi for the left perturbation R <- exp([phi]x) R,
+ *                  t <- exp([phi]x) t (a rotation about the camera centre);
+ *                  the matching translation R, t <- R, t + rho has dL/drho =
+ *                  dL/dt, so (dL/drho, dL/dphi) is the se(3) gradient.
+ * The pose enters through the camera-space mean R mean + t, through the
+ * R of the projected covariance J R Sigma R^T J^T and through the camera
+ * centre -R^T t of the SH view direction.  The sums are FP32 atomics (their
+ * order, and so the last bits, vary from run to run).  Parameter gradients
+ * are not computed (gsr_preprocess_bwd does that). */
+int32_t gsr_pose_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam, const gsr_tiling *tiling,
+                     const gsr_grad2d *grad2d, float *d_pose, gsr_stream_t stream);
+
 /* gsr_preprocess_bwd that stores (=) instead of adding: the gradients of the
  * Gaussians with ntiles > 0 are replaced, all others are left as they are.
  * For callers whose gradients are zero before the pass (an optimiser step

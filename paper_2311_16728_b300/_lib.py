@@ -81,6 +81,8 @@ _SIGNATURES = {
                        c_void_p, c_void_p, P(gsr_grad2d), c_void_p], c_int32),
     "gsr_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d),
                             P(gsr_param_buffers), c_void_p, c_void_p, c_void_p], c_int32),
+    "gsr_pose_bwd": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d), c_void_p,
+                      c_void_p], c_int32),
     "gsr_preprocess_bwd_store": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d),
                             P(gsr_param_buffers), c_void_p, c_void_p, c_void_p], c_int32),
     "gsr_loss_workspace_size": ([c_int32, c_int32, c_int32, P(c_size_t)], c_int32),
@@ -184,6 +186,7 @@ gsr_render_fwd = _wrap("gsr_render_fwd")
 gsr_blend_bwd = _wrap("gsr_blend_bwd")
 gsr_preprocess_bwd = _wrap("gsr_preprocess_bwd")
 gsr_preprocess_bwd_store = _wrap("gsr_preprocess_bwd_store")
+gsr_pose_bwd = _wrap("gsr_pose_bwd")
 gsr_loss_workspace_size = _wrap("gsr_loss_workspace_size")
 gsr_loss_fwd_bwd = _wrap("gsr_loss_fwd_bwd")
 gsr_loss_fwd_bwd_static = _wrap("gsr_loss_fwd_bwd_static")

@@ -75,14 +75,21 @@ __device__ __forceinline__ void add4(float4 *p, float4 v, bool atomic) {
     }
 }
 
+// Number of camera pose gradient values: dL/dR (9, row-major, R taken as a
+// general 3 x 3 matrix), dL/dt (3), dL/dphi (3) for the left perturbation
+// R <- exp([phi]x) R, t <- exp([phi]x) t (a rotation about the camera centre).
+constexpr int kPoseGrad = 15;
+
 // Chain rule of one Gaussian from its screen-space gradient in camera `cam`
 // (c = the forward chain of that camera) to the 59 parameters.  Each plane's
 // gradient goes to sink(plane, value): planes 3 .. 3 + sh_planes - 1 (SH) as
 // soon as that SH plane has been read, then 0 (mean, opacity logit), 1
-// (quaternion), 2 (log-scale).
-template <class Sink>
+// (quaternion), 2 (log-scale).  kPose: this Gaussian's part of the camera pose
+// gradient is added to pose[kPoseGrad].
+template <class Sink, bool kPose = false>
 __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, int64_t i, const float4 mo,
-                                              const Chain &c, const ScreenGrad &sg, Sink &sink) {
+                                              const Chain &c, const ScreenGrad &sg, Sink &sink,
+                                              float *pose = nullptr) {
     const float du = sg.du, dv = sg.dv, dop = sg.dop;
     const float *W = cam.R;
     // ---- colour and SH, streamed one float4 plane at a time
@@ -131,7 +138,10 @@ __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, 
         sink(3 + j, make_float4(d[0], d[1], d[2], d[3]));
     }
     const float vd = dvh.x * vx + dvh.y * vy + dvh.z * vz;
-    float dmx = (dvh.x - vx * vd) * inv_len, dmy = (dvh.y - vy * vd) * inv_len, dmz = (dvh.z - vz * vd) * inv_len;
+    // dL/d(mean - camera centre) through the view direction
+    const float ddx = (dvh.x - vx * vd) * inv_len, ddy = (dvh.y - vy * vd) * inv_len,
+                ddz = (dvh.z - vz * vd) * inv_len;
+    float dmx = ddx, dmy = ddy, dmz = ddz;
     // ---- opacity (the same FP32 opacity the forward used)
     const float sig = FD(1.0f, FA(1.0f, chain_exp(-mo.w)));
     const float dlogit = dop * sig * (1.0f - sig);
@@ -198,6 +208,36 @@ __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, 
     dmx += W[0] * dpx + W[3] * dpy + W[6] * dpz;
     dmy += W[1] * dpx + W[4] * dpy + W[7] * dpz;
     dmz += W[2] * dpx + W[5] * dpy + W[8] * dpz;
+    if constexpr (kPose) {
+        // the pose enters through p = W mean + t, through T = J W
+        // (G_W = J^T G_T) and through the camera centre -W^T t of the view
+        // direction; under the left rotation dp = phi x p, dW = [phi]x W and
+        // the centre stays: <G_W, [phi]x W> = phi . (N21 - N12, N02 - N20,
+        // N10 - N01) with N = G_W W^T
+        float GW[9];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            GW[b] = J00 * GT[b];
+            GW[3 + b] = J11 * GT[3 + b];
+            GW[6 + b] = J02 * GT[b] + J12 * GT[3 + b];
+        }
+        const float mu[3] = {mo.x, mo.y, mo.z}, dp[3] = {dpx, dpy, dpz}, dd[3] = {ddx, ddy, ddz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) pose[3 * a + b] += dp[a] * mu[b] + GW[3 * a + b] + dd[b] * cam.t[a];
+            pose[9 + a] += dp[a] + W[3 * a] * dd[0] + W[3 * a + 1] * dd[1] + W[3 * a + 2] * dd[2];
+        }
+        float N[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                N[3 * a + b] = GW[3 * a] * W[3 * b] + GW[3 * a + 1] * W[3 * b + 1] + GW[3 * a + 2] * W[3 * b + 2];
+        pose[12] += Yc * dpz - c.zc * dpy + N[7] - N[5];
+        pose[13] += c.zc * dpx - X * dpz + N[2] - N[6];
+        pose[14] += X * dpy - Yc * dpx + N[3] - N[1];
+    }
     // ---- Sig = M M^T, M = Rq diag(s):  G_M = 2 G_Sig M
     float M[9];
 #pragma unroll
@@ -248,6 +288,11 @@ struct AddSink {
         if (store) *p = v;
         else add4(p, v, atomic);
     }
+};
+
+// sink that discards the parameter gradients (pose-only passes)
+struct NullSink {
+    __device__ __forceinline__ void operator()(int, float4) const {}
 };
 
 __device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int64_t i, const float4 mo, const Chain &c,

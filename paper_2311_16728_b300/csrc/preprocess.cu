@@ -87,6 +87,71 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, C
         chain_one_gaussian(g, cam, base + s_idx[k], g0, g1, g2, d_mo, d_q, d_ls, d_sh, dstat, dcount, kStore);
 }
 
+// Camera pose gradient: the chain of every visible Gaussian with its
+// parameter gradients discarded and its pose part summed -- per thread, then
+// per warp (shuffles), per CTA (shared memory) and one atomic per value and
+// CTA into d_pose.
+__global__ void __launch_bounds__(kBwdThreads) pose_bwd_kernel(GaussK g, CamK cam, const uint32_t *__restrict__ ntiles,
+                                                               const float4 *__restrict__ g0,
+                                                               const float4 *__restrict__ g1,
+                                                               const float4 *__restrict__ g2,
+                                                               float *__restrict__ d_pose) {
+    __shared__ uint32_t s_idx[kBwdChunk];
+    __shared__ uint32_t s_cnt;
+    __shared__ float s_pose[kBwdThreads / 32][kPoseGrad];
+    if (threadIdx.x == 0) s_cnt = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kBwdChunk; k += kBwdThreads) {
+        const int64_t i = base + k;
+        const bool vis = i < g.n && ntiles[i] > 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        uint32_t slot = 0;
+        if (lane == 0 && m) slot = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+    }
+    __syncthreads();
+    const uint32_t cnt = s_cnt;
+    float pose[kPoseGrad];
+#pragma unroll
+    for (int k = 0; k < kPoseGrad; ++k) pose[k] = 0.f;
+    NullSink sink;
+    for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
+        const int64_t i = base + s_idx[k];
+        const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+        Chain c;
+        if (!decide_chain(mo, q, ls, cam, c)) continue;  // cannot happen for a visible Gaussian
+        const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
+        float A, B, C, sig;
+        chain_conic_opacity(c, mo.w, A, B, C, sig);
+        ScreenGrad sg;
+        sg.du = G0.x;
+        sg.dv = G0.y;
+        conic_grad_to_cov(A, B, C, G0.z, G0.w, G1.x, sg.Gs00, sg.Gs01, sg.Gs11);
+        sg.dop = G1.y;
+        sg.dr = G1.z;
+        sg.dg = G1.w;
+        sg.db = G2.x;
+        chain_core_to<NullSink, true>(g, cam, i, mo, c, sg, sink, pose);
+    }
+#pragma unroll
+    for (int k = 0; k < kPoseGrad; ++k) {
+        float v = pose[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_pose[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPoseGrad && cnt > 0u) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < kBwdThreads / 32; ++w) v += s_pose[w][threadIdx.x];
+        atomicAdd(d_pose + threadIdx.x, v);
+    }
+}
+
 }  // namespace gsr
 
 using namespace gsr;
@@ -151,4 +216,30 @@ extern "C" int32_t gsr_preprocess_bwd_store(const gsr_gaussians *g, const gsr_pr
                                             const gsr_param_buffers *grads, float *densify_stat,
                                             float *densify_count, gsr_stream_t stream) {
     return preprocess_bwd(g, proj, cam, tiling, g2d, grads, densify_stat, densify_count, true, stream);
+}
+
+extern "C" int32_t gsr_pose_bwd(const gsr_gaussians *g, const gsr_proj *proj, const gsr_camera *cam,
+                                const gsr_tiling *tiling, const gsr_grad2d *g2d, float *d_pose,
+                                gsr_stream_t stream) {
+    int32_t rc;
+    if ((rc = validate_gaussians(g)) || (rc = validate_camera(cam)) || (rc = validate_tiling(tiling))) return rc;
+    if (!d_pose) {
+        set_error("gsr_pose_bwd: NULL d_pose");
+        return GSR_ERR_INVALID_ARG;
+    }
+    if (g->n == 0) return GSR_OK;
+    if (!proj || !proj->ntiles || !g2d || !g2d->g0 || !g2d->g1 || !g2d->g2) {
+        set_error("gsr_pose_bwd: NULL pointer");
+        return GSR_ERR_INVALID_ARG;
+    }
+    if (!aligned16(g2d->g0) || !aligned16(g2d->g1) || !aligned16(g2d->g2)) {
+        set_error("gsr_pose_bwd: screen-space gradient buffers must be 16-byte aligned");
+        return GSR_ERR_INVALID_ARG;
+    }
+    const CamK ck = make_camk(cam, tiling);
+    const int64_t blocks = (g->n + kBwdChunk - 1) / kBwdChunk;
+    pose_bwd_kernel<<<(unsigned)blocks, kBwdThreads, 0, as_cuda(stream)>>>(
+        make_gk(g), ck, proj->ntiles, reinterpret_cast<const float4 *>(g2d->g0),
+        reinterpret_cast<const float4 *>(g2d->g1), reinterpret_cast<const float4 *>(g2d->g2), d_pose);
+    return check_launch("pose_bwd_kernel");
 }

@@ -208,6 +208,14 @@ class ViewBuffers:
         fn(ctypes.byref(gs), ctypes.byref(proj), ctypes.byref(self.cam), ctypes.byref(self.tiling), ctypes.byref(g2),
            ctypes.byref(gb), _p(densify_stat), _p(densify_count), _stream(stream))
 
+    def pose_bwd(self, g: Gaussians, d_pose: torch.Tensor, stream=None):
+        """Camera pose gradient (+= into d_pose, 15 floats: dL/dR, dL/dt,
+        dL/dphi) from the screen-space gradients blend_bwd left in g2."""
+        assert d_pose.dtype == torch.float32 and d_pose.numel() >= 15
+        gs, proj, g2 = g.gaussians_struct(), self.proj_struct(), self.grad2d_struct()
+        L.gsr_pose_bwd(ctypes.byref(gs), ctypes.byref(proj), ctypes.byref(self.cam), ctypes.byref(self.tiling),
+                       ctypes.byref(g2), _p(d_pose), _stream(stream))
+
     def forward(self, g: Gaussians, bg=(0.0, 0.0, 0.0), stream=None):
         self.preprocess(g, stream)
         self.bin_sort(stream)

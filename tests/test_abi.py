@@ -67,6 +67,13 @@ def test_bad_arguments_are_rejected_on_the_host(gsr):
     # NULL outputs
     rc = L.gsr_preprocess.raw(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(good_tiling), None, None, None)
     assert rc == L.GSR_ERR_INVALID_ARG
+    g2d = L.gsr_grad2d(16, 16, 16)
+    rc = L.gsr_pose_bwd.raw(ctypes.byref(g), ctypes.byref(proj), ctypes.byref(cam), ctypes.byref(good_tiling),
+                            ctypes.byref(g2d), None, None)
+    assert rc == L.GSR_ERR_INVALID_ARG and b"d_pose" in L.gsr_last_error()
+    rc = L.gsr_pose_bwd.raw(ctypes.byref(g), ctypes.byref(proj), ctypes.byref(cam), ctypes.byref(good_tiling),
+                            ctypes.byref(L.gsr_grad2d(16, 24, 16)), 16, None)
+    assert rc == L.GSR_ERR_INVALID_ARG and b"aligned" in L.gsr_last_error()
     # unaligned parameter plane
     g_bad = L.gsr_gaussians(18, 16, 16, 16, 10, 3)
     rc = L.gsr_preprocess.raw(ctypes.byref(g_bad), ctypes.byref(cam), ctypes.byref(good_tiling), ctypes.byref(proj),
