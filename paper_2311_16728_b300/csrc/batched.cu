@@ -310,6 +310,7 @@ static size_t iterate_smem() {
 // opacity and colour gradients add.  The expensive chain then runs once per
 // (Gaussian, keyframe) instead of once per (Gaussian, view).
 constexpr int kGroupMax = 8;     // views per group
+static_assert(kGroupMax <= 8, "member masks are 8-bit");
 constexpr int kChainChunk = 128; // Gaussians per CTA
 
 struct ChainGroups {
@@ -330,21 +331,32 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
                                                                     float4 *__restrict__ d_q, float4 *__restrict__ d_ls,
                                                                     float4 *__restrict__ d_sh,
                                                                     uint32_t *__restrict__ touched) {
-    extern __shared__ uint32_t s_rec[];  // kChainChunk x ngroups candidates
+    extern __shared__ uint32_t s_rec[];  // kChainChunk x ngroups candidates, then as many member masks
     __shared__ uint32_t s_cnt;
     __shared__ uint32_t s_touch[kChainChunk];
+    const int total = kChainChunk * CG.ngroups;  // a multiple of 32: whole warps take part in each ballot
+    uint8_t *s_bits = reinterpret_cast<uint8_t *>(s_rec + total);  // members of the group that see the Gaussian
     if (threadIdx.x == 0) s_cnt = 0u;
     for (int k = threadIdx.x; k < kChainChunk; k += kBwdThreads) s_touch[k] = 0u;
-    __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kChainChunk;
     const int lane = threadIdx.x & 31;
-    const int total = kChainChunk * CG.ngroups;  // a multiple of 32: whole warps take part in each ballot
+    // every visibility word first (independent loads, no ballot in between)
+#pragma unroll 4
     for (int k = threadIdx.x; k < total; k += kBwdThreads) {
         const int il = k % kChainChunk, grp = k / kChainChunk;
         const int64_t i = base + il;
-        bool vis = false;
-        if (i < g.n)
-            for (int m = 0; m < CG.count[grp] && !vis; ++m) vis = ntiles[(int64_t)CG.member[grp][m] * g.n + i] > 0u;
+        uint32_t bits = 0u;
+        if (i < g.n) {
+#pragma unroll
+            for (int m = 0; m < kGroupMax; ++m)
+                if (m < CG.count[grp]) bits |= (ntiles[(int64_t)CG.member[grp][m] * g.n + i] > 0u ? 1u : 0u) << m;
+        }
+        s_bits[k] = (uint8_t)bits;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < total; k += kBwdThreads) {
+        const int il = k % kChainChunk, grp = k / kChainChunk;
+        const bool vis = s_bits[k] != 0u;
         const uint32_t msk = __ballot_sync(0xffffffffu, vis);
         uint32_t slot = 0;
         if (lane == 0 && msk) slot = atomicAdd(&s_cnt, (uint32_t)__popc(msk));
@@ -361,20 +373,23 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
     const uint32_t cnt = s_cnt;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
         const int grp = (int)(s_rec[k] >> 16);
-        const int64_t i = base + (s_rec[k] & 0xFFFFu);
+        const int il = (int)(s_rec[k] & 0xFFFFu);
+        const int64_t i = base + il;
+        const uint32_t bits = s_bits[grp * kChainChunk + il];
         // the finest visible view of the group is the base of the merge
-        int mb = 0;
-        while (mb + 1 < CG.count[grp] && ntiles[(int64_t)CG.member[grp][mb] * g.n + i] == 0u) ++mb;
+        const int mb = __ffs(bits) - 1;
         const int vb = CG.member[grp][mb];
         const CamK &cam = V.cam[vb];
         const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+        float4 shp[kShPlanes];  // in flight while the decision chain runs
+        load_sh_planes(g, i, shp);
         Chain c;
         if (!decide_chain(mo, q, ls, cam, c)) continue;  // cannot happen for a visible record
         ScreenGrad sg = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float sb = CG.scale[grp][mb];
         for (int m = mb; m < CG.count[grp]; ++m) {
+            if (!((bits >> m) & 1u)) continue;
             const int64_t rec = (int64_t)CG.member[grp][m] * g.n + i;
-            if (ntiles[rec] == 0u) continue;
             // records and screen-space gradients: at the record, or at its
             // compact position when the binning gathered the records
             const int64_t r = rec_to_c ? (int64_t)rec_to_c[rec] : rec;
@@ -398,7 +413,7 @@ __global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, co
             g1[r] = make_float4(0.f, 0.f, 0.f, 0.f);
             g2[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        chain_core(g, cam, i, mo, c, sg, d_mo, d_q, d_ls, d_sh, true);
+        chain_core(g, cam, i, mo, c, sg, d_mo, d_q, d_ls, d_sh, true, shp);
     }
 }
 
@@ -626,7 +641,7 @@ extern "C" int32_t gsr_batched_preprocess_bwd(const gsr_gaussians *g, const gsr_
     }
     ChainGroups CG;
     make_groups(cams, nviews, CG);
-    const size_t smem = sizeof(uint32_t) * kChainChunk * CG.ngroups;
+    const size_t smem = (sizeof(uint32_t) + sizeof(uint8_t)) * kChainChunk * CG.ngroups;
     batched_chain_kernel<<<(unsigned)((g->n + kChainChunk - 1) / kChainChunk), kBwdThreads, smem, as_cuda(stream)>>>(
         make_gk(g), V, CG, reinterpret_cast<const float4 *>(rp->xy_conic),
         reinterpret_cast<const float4 *>(rp->c_op_box), proj->ntiles, compact ? compact->ntiles : nullptr,

@@ -48,6 +48,31 @@ __device__ __forceinline__ void load_sh(const float4 *__restrict__ sh, int64_t n
 constexpr int kBwdThreads = 128;
 constexpr int kBwdChunk = 1024;  // Gaussians per CTA
 
+// Indices k (0 .. kBwdChunk-1) of the visible Gaussians base + k of this
+// CTA's chunk into s_idx[0 .. *s_cnt - 1] (s_cnt zero on entry; a barrier
+// must follow).  Every visibility word is loaded before the first ballot, so
+// the chunk costs one memory round trip, not one per iteration.
+__device__ __forceinline__ void compact_visible(const uint32_t *__restrict__ ntiles, int64_t n, int64_t base,
+                                                uint32_t *s_idx, uint32_t *s_cnt) {
+    constexpr int kIt = kBwdChunk / kBwdThreads;
+    const int lane = threadIdx.x & 31;
+    uint32_t nt[kIt];
+#pragma unroll
+    for (int j = 0; j < kIt; ++j) {
+        const int64_t i = base + j * kBwdThreads + (int)threadIdx.x;
+        nt[j] = i < n ? __ldg(ntiles + i) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kIt; ++j) {
+        const bool vis = nt[j] > 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        uint32_t slot = 0;
+        if (lane == 0 && m) slot = atomicAdd(s_cnt, (uint32_t)__popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(j * kBwdThreads + (int)threadIdx.x);
+    }
+}
+
 // Screen-space gradient of one Gaussian in one view, with the conic part
 // already taken to the dilated 2D covariance: Gs = dL/dSigma' (symmetric).
 struct ScreenGrad {
@@ -85,11 +110,12 @@ constexpr int kPoseGrad = 15;
 // gradient goes to sink(plane, value): planes 3 .. 3 + sh_planes - 1 (SH) as
 // soon as that SH plane has been read, then 0 (mean, opacity logit), 1
 // (quaternion), 2 (log-scale).  kPose: this Gaussian's part of the camera pose
-// gradient is added to pose[kPoseGrad].
+// gradient is added to pose[kPoseGrad].  shp (may be NULL): the Gaussian's SH
+// planes already in registers (load_sh_planes), else they are read here.
 template <class Sink, bool kPose = false>
 __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, int64_t i, const float4 mo,
                                               const Chain &c, const ScreenGrad &sg, Sink &sink,
-                                              float *pose = nullptr) {
+                                              float *pose = nullptr, const float4 *shp = nullptr) {
     const float du = sg.du, dv = sg.dv, dop = sg.dop;
     const float *W = cam.R;
     // ---- colour and SH, streamed one float4 plane at a time
@@ -107,7 +133,7 @@ __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, 
 #pragma unroll
     for (int j = 0; j < kShPlanes; ++j) {
         if (j >= planes) break;
-        const float4 v = __ldg(g.sh + (int64_t)j * g.n + i);
+        const float4 v = shp ? shp[j] : __ldg(g.sh + (int64_t)j * g.n + i);
         const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -120,7 +146,7 @@ __device__ __forceinline__ void chain_core_to(const GaussK &g, const CamK &cam, 
 #pragma unroll
     for (int j = 0; j < kShPlanes; ++j) {
         if (j >= planes) break;
-        const float4 v = __ldg(g.sh + (int64_t)j * g.n + i);
+        const float4 v = shp ? shp[j] : __ldg(g.sh + (int64_t)j * g.n + i);
         const float e[4] = {v.x, v.y, v.z, v.w};
         float d[4];
 #pragma unroll
@@ -297,13 +323,25 @@ struct NullSink {
 
 __device__ __forceinline__ void chain_core(const GaussK &g, const CamK &cam, int64_t i, const float4 mo, const Chain &c,
                                            const ScreenGrad &sg, float4 *__restrict__ d_mo, float4 *__restrict__ d_q,
-                                           float4 *__restrict__ d_ls, float4 *__restrict__ d_sh, bool atomic) {
+                                           float4 *__restrict__ d_ls, float4 *__restrict__ d_sh, bool atomic,
+                                           const float4 *shp = nullptr) {
     AddSink sink{d_mo, d_q, d_ls, d_sh, g.n, i, atomic, false};
-    chain_core_to(g, cam, i, mo, c, sg, sink);
+    chain_core_to(g, cam, i, mo, c, sg, sink, nullptr, shp);
+}
+
+// The SH planes of Gaussian i in registers (planes beyond the degree zero).
+__device__ __forceinline__ void load_sh_planes(const GaussK &g, int64_t i, float4 shp[kShPlanes]) {
+    const int planes = sh_planes(g.deg);
+#pragma unroll
+    for (int j = 0; j < kShPlanes; ++j)
+        shp[j] = j < planes ? __ldg(g.sh + (int64_t)j * g.n + i) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // One view: the screen-space gradient of record i (g0, g1, g2) chained into
-// the parameter gradients of Gaussian i (one thread per Gaussian).
+// the parameter gradients of Gaussian i (one thread per Gaussian).  Every
+// input of the Gaussian is loaded first, so its loads share one memory round
+// trip that overlaps the decision chain (these kernels run few warps per SM,
+// each bound by the latency of its own chain).
 __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &cam, int64_t i,
                                                    const float4 *__restrict__ g0, const float4 *__restrict__ g1,
                                                    const float4 *__restrict__ g2, float4 *__restrict__ d_mo,
@@ -311,9 +349,11 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
                                                    float4 *__restrict__ d_sh, float *__restrict__ dstat,
                                                    float *__restrict__ dcount, bool store = false) {
     const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+    const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
+    float4 shp[kShPlanes];
+    load_sh_planes(g, i, shp);
     Chain c;
     if (!decide_chain(mo, q, ls, cam, c)) return;  // cannot happen for a visible Gaussian
-    const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
     if (dstat) {  // |dL/d(u, v)| in normalised device coordinates
         const float gu = G0.x * (0.5f * (float)cam.W), gv = G0.y * (0.5f * (float)cam.H);
         dstat[i] += sqrtf(gu * gu + gv * gv);
@@ -330,7 +370,7 @@ __device__ __forceinline__ void chain_one_gaussian(const GaussK &g, const CamK &
     sg.dg = G1.w;
     sg.db = G2.x;
     AddSink sink{d_mo, d_q, d_ls, d_sh, g.n, i, false, store};
-    chain_core_to(g, cam, i, mo, c, sg, sink);
+    chain_core_to(g, cam, i, mo, c, sg, sink, nullptr, shp);
 }
 
 }  // namespace gsr

@@ -71,16 +71,7 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, C
     if (threadIdx.x == 0) s_cnt = 0u;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
-    const int lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < kBwdChunk; k += kBwdThreads) {
-        const int64_t i = base + k;
-        const bool vis = i < g.n && ntiles[i] > 0u;
-        const uint32_t m = __ballot_sync(0xffffffffu, vis);
-        uint32_t slot = 0;
-        if (lane == 0 && m) slot = atomicAdd(&s_cnt, (uint32_t)__popc(m));
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
-    }
+    compact_visible(ntiles, g.n, base, s_idx, &s_cnt);
     __syncthreads();
     const uint32_t cnt = s_cnt;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads)
@@ -103,15 +94,7 @@ __global__ void __launch_bounds__(kBwdThreads) pose_bwd_kernel(GaussK g, CamK ca
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < kBwdChunk; k += kBwdThreads) {
-        const int64_t i = base + k;
-        const bool vis = i < g.n && ntiles[i] > 0u;
-        const uint32_t m = __ballot_sync(0xffffffffu, vis);
-        uint32_t slot = 0;
-        if (lane == 0 && m) slot = atomicAdd(&s_cnt, (uint32_t)__popc(m));
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (vis) s_idx[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
-    }
+    compact_visible(ntiles, g.n, base, s_idx, &s_cnt);
     __syncthreads();
     const uint32_t cnt = s_cnt;
     float pose[kPoseGrad];
@@ -121,9 +104,11 @@ __global__ void __launch_bounds__(kBwdThreads) pose_bwd_kernel(GaussK g, CamK ca
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
         const int64_t i = base + s_idx[k];
         const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
+        const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
+        float4 shp[kShPlanes];
+        load_sh_planes(g, i, shp);
         Chain c;
         if (!decide_chain(mo, q, ls, cam, c)) continue;  // cannot happen for a visible Gaussian
-        const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
         float A, B, C, sig;
         chain_conic_opacity(c, mo.w, A, B, C, sig);
         ScreenGrad sg;
@@ -134,7 +119,7 @@ __global__ void __launch_bounds__(kBwdThreads) pose_bwd_kernel(GaussK g, CamK ca
         sg.dr = G1.z;
         sg.dg = G1.w;
         sg.db = G2.x;
-        chain_core_to<NullSink, true>(g, cam, i, mo, c, sg, sink, pose);
+        chain_core_to<NullSink, true>(g, cam, i, mo, c, sg, sink, pose, shp);
     }
 #pragma unroll
     for (int k = 0; k < kPoseGrad; ++k) {
