@@ -62,6 +62,33 @@ __device__ __forceinline__ uint32_t block_incl_scan_256(uint32_t v, uint32_t *s_
     return v + add;
 }
 
+// Exclusive running maximum over a block of 256 threads (0 for thread 0).
+__device__ __forceinline__ uint32_t block_excl_max_256(uint32_t v, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = max(incl, t);
+    }
+    const uint32_t prev_lane = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < 8 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w = max(w, t);
+        }
+        if (lane < 8) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = max(wid > 0 ? s_warp[wid - 1] : 0u, lane > 0 ? prev_lane : 0u);
+    __syncthreads();
+    return excl;
+}
+
 // Sum of block_sums[0 .. b) (the exclusive prefix of block b) and, when
 // `total` is not NULL, of all of them.  Block-cooperative; few hundred blocks.
 __device__ __forceinline__ int64_t block_prefix(const uint32_t *block_sums, int64_t nblocks, int64_t b,
@@ -209,6 +236,7 @@ constexpr int kExpandThreads = 256;
 constexpr int kExpandItems = 4;
 constexpr int kExpandTile = kExpandThreads * kExpandItems;
 constexpr int kExpandGrid = 148 * 8;  // grid-stride over chunks of kExpandTile candidates
+constexpr int kExpandGroup = 16;      // chunks of a block whose ends are searched together
 
 // Kept pairs: kept_ts[p] = global tile << 32 | rank of the pair within its
 // tile (from the atomic that counts the tile's pairs in counts[2 t]),
@@ -221,57 +249,109 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
     uint32_t *__restrict__ counts, uint64_t *__restrict__ kept_ts, uint64_t *__restrict__ kept_sk, int64_t cap,
     unsigned long long *__restrict__ d_kept, bool compact) {
     __shared__ uint32_t s_off[kExpandTile + 1];
+    __shared__ __align__(16) uint4 s_meta[kExpandTile];
+    __shared__ __align__(16) uint32_t s_map[kExpandTile];
+    __shared__ uint32_t s_depth[kExpandTile];
     __shared__ uint32_t s_warp[8];
-    __shared__ int64_t s_i0;
+    __shared__ int64_t s_ci[2 * kExpandGroup];
     __shared__ unsigned long long s_base;
-    __shared__ int s_m;
     const int64_t ncand = *d_ncand;
     const int64_t nv = clamp_count(d_nvis, cap_n);
-    for (int64_t s0 = (int64_t)blockIdx.x * kExpandTile; s0 < ncand; s0 += (int64_t)gridDim.x * kExpandTile) {
-        const int64_t s_last = (s0 + kExpandTile < ncand ? s0 + kExpandTile : ncand) - 1;
-        __syncthreads();  // the previous chunk is done with the shared words
-        if (threadIdx.x < 32) {
-            const int64_t i0 = warp_upper_index(coff, nv, (uint32_t)s0);
-            const int64_t i1 = warp_upper_index(coff, nv, (uint32_t)s_last);
-            if (threadIdx.x == 0) {
-                s_i0 = i0;
-                s_m = (int)(i1 - i0 + 1);  // every visible item owns >= 1 slot, so m <= kExpandTile
+    const int64_t nchunks = (ncand + kExpandTile - 1) / kExpandTile;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // this block's chunks are blockIdx.x + k gridDim.x; a group of up to
+    // kExpandGroup of them first finds the visible items at both ends of each
+    // chunk, one warp per search, all searches in flight together
+    for (int64_t cg = blockIdx.x; cg < nchunks; cg += (int64_t)gridDim.x * kExpandGroup) {
+        const int64_t left = (nchunks - cg + gridDim.x - 1) / gridDim.x;
+        const int kn = left < kExpandGroup ? (int)left : kExpandGroup;
+        __syncthreads();  // the previous group is done with the shared words
+        for (int q = wid; q < 2 * kn; q += kExpandThreads / 32) {
+            const int64_t c0 = (cg + (int64_t)(q >> 1) * gridDim.x) * kExpandTile;
+            const int64_t slot = (q & 1) ? (c0 + kExpandTile < ncand ? c0 + kExpandTile : ncand) - 1 : c0;
+            const int64_t idx = warp_upper_index(coff, nv, (uint32_t)slot);
+            if (lane == 0) s_ci[q] = idx;
+        }
+        __syncthreads();
+    for (int kc = 0; kc < kn; ++kc) {
+        const int64_t s0 = (cg + (int64_t)kc * gridDim.x) * kExpandTile;
+        const int64_t i0 = s_ci[2 * kc];
+        const int m = (int)(s_ci[2 * kc + 1] - i0 + 1);  // every visible item owns >= 1 slot, so m <= kExpandTile
+        __syncthreads();  // the previous chunk is done with s_off, s_meta, s_map
+        reinterpret_cast<uint4 *>(s_map)[threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        // per visible item of the chunk (once, not per candidate): its first
+        // slot, the pair value, its box in tiles and the index of its first
+        // tile; the first chunk slot of each item marks the slot map
+        for (int j = threadIdx.x; j <= m; j += kExpandThreads) {
+            const uint32_t off = coff[i0 + j];
+            s_off[j] = off;
+            if (j < m) {
+                const uint32_t rec = order[i0 + j];
+                // the pair's value: the record, or its position in the visible
+                // list when the records were gathered into compact arrays
+                const uint32_t gid = compact ? (uint32_t)(i0 + j) : rec;
+                const float4 b = __ldg(c_op_box + gid);
+                const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+                const int tx0 = (int)(bx & 0xffffu) / tw, ty0 = (int)(by & 0xffffu) / th;
+                const int ntx = (int)(bx >> 16) / tw - tx0 + 1;
+                const int v = vt.nviews > 1 ? (int)(rec / (uint32_t)vt.n_per_view) : 0;  // view of this record
+                s_meta[j] = make_uint4(gid, vt.toff[v] + (uint32_t)(ty0 * vt.gx[v] + tx0),
+                                       ((uint32_t)vt.gx[v] << 16) | (uint32_t)ntx, ((uint32_t)ty0 << 16) | (uint32_t)tx0);
+                s_depth[j] = __float_as_uint(__ldg(&rgb_depth[gid].w));
+                const int64_t start = (int64_t)off - s0;
+                if (start < kExpandTile) s_map[start > 0 ? start : 0] = (uint32_t)j;
             }
         }
         __syncthreads();
-        const int64_t i0 = s_i0;
-        const int m = s_m;
-        for (int j = threadIdx.x; j <= m; j += kExpandThreads) s_off[j] = coff[i0 + j];
+        {  // slot -> item: running maximum of the marks
+            uint4 q = reinterpret_cast<uint4 *>(s_map)[threadIdx.x];
+            q.y = max(q.y, q.x);
+            q.z = max(q.z, q.y);
+            q.w = max(q.w, q.z);
+            const uint32_t carry = block_excl_max_256(q.w, s_warp);
+            q.x = max(q.x, carry);
+            q.y = max(q.y, carry);
+            q.z = max(q.z, carry);
+            q.w = max(q.w, carry);
+            reinterpret_cast<uint4 *>(s_map)[threadIdx.x] = q;
+        }
         __syncthreads();
-        uint32_t tiles[kExpandItems], gids[kExpandItems];
+        uint32_t tiles[kExpandItems], gids[kExpandItems], depth[kExpandItems];
         uint32_t mine = 0;  // bit r: this thread's candidate of round r is kept
 #pragma unroll
         for (int r = 0; r < kExpandItems; ++r) {
-            const int64_t slot = s0 + (int64_t)r * kExpandThreads + threadIdx.x;
+            const int kl = r * kExpandThreads + (int)threadIdx.x;
+            const int64_t slot = s0 + kl;
             tiles[r] = 0;
             gids[r] = 0;
+            depth[r] = 0;
             if (slot < ncand) {
-                int lo = 0, hi = m;  // s_off[lo] <= slot < s_off[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_off[mid] <= (uint32_t)slot) lo = mid;
-                    else hi = mid;
-                }
-                const uint32_t rec = order[i0 + lo];
-                // the pair's value: the record, or its position in the visible
-                // list when the records were gathered into compact arrays
-                const uint32_t gid = compact ? (uint32_t)(i0 + lo) : rec;
+                const int lo = (int)s_map[kl];
+                const uint4 meta = s_meta[lo];
                 const int k = (int)((uint32_t)slot - s_off[lo]);
+                const int ntx = (int)(meta.z & 0xffffu), gxv = (int)(meta.z >> 16);
+                // k = q ntx + rr; q < 2^16, so the rounded quotient is off by
+                // at most one and one correction step makes it exact
+                int q = __float2int_rz(__fmul_rn(__int2float_rn(k), __frcp_rn(__int2float_rn(ntx))));
+                int rr = k - q * ntx;
+                if (rr < 0) {
+                    --q;
+                    rr += ntx;
+                } else if (rr >= ntx) {
+                    ++q;
+                    rr -= ntx;
+                }
+                const uint32_t gid = meta.x;
                 const Splat sp = load_splat(xy_conic, c_op_box, gid);
-                const int tx0 = sp.x0 / tw, ntx = sp.x1 / tw - tx0 + 1;
-                const int tx = tx0 + k % ntx, ty = sp.y0 / th + k / ntx;
-                const int v = (int)((int64_t)rec / vt.n_per_view);  // view of this record
-                const uint32_t tile = vt.toff[v] + (uint32_t)(ty * vt.gx[v] + tx);
+                const int tx = (int)(meta.w & 0xffffu) + rr, ty = (int)(meta.w >> 16) + q;
+                const uint32_t tile = meta.y + (uint32_t)(q * gxv + rr);
                 if (tile < ntiles_total &&
                     tile_keep_at(tx, ty, tw, th, sp.u, sp.v, sp.A, sp.B, sp.C, sp.op, sp.x0, sp.x1, sp.y0, sp.y1)) {
                     mine |= 1u << r;
                     tiles[r] = tile;
                     gids[r] = gid;
+                    depth[r] = s_depth[lo];
                 }
             }
         }
@@ -287,10 +367,11 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
                 const uint32_t rank = atomicAdd(&counts[2 * (size_t)tiles[r]], 1u);
                 if (pos < (unsigned long long)cap) {
                     kept_ts[pos] = ((uint64_t)tiles[r] << 32) | rank;
-                    kept_sk[pos] = ((uint64_t)__float_as_uint(__ldg(&rgb_depth[gids[r]].w)) << 32) | gids[r];
+                    kept_sk[pos] = ((uint64_t)depth[r] << 32) | gids[r];
                 }
                 ++pos;
             }
+    }
     }
 }
 
