@@ -225,47 +225,50 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
 // alpha_i) recovers the transmittance in front of each Gaussian; the colour
 // behind it, normalised by T_{i+1}, follows acc <- acc (1 - alpha) + c alpha.
 //   dL/dc_i     = dL/dC alpha_i T_i
-//   dL/dalpha_i = T_i sum_ch dL/dC_ch (c_i,ch - acc_ch)
+//   dL/dalpha_i = T_i dL/dC . (c_i - acc)
 // then through alpha = opacity exp(power) (zero where the 0.99 clamp holds).
+// Only dL/dC . acc enters, and it obeys the same recursion with dL/dC . c_i
+// in place of c_i, so the pixel keeps that one scalar (accd) instead of acc.
 struct PixelBwd {
-    float T, acc0, acc1, acc2, dC0, dC1, dC2;
+    float T, accd, dC0, dC1, dC2;
     uint32_t last;
 };
 
+// A staged splat seen from this thread's two pixels: offsets, the original
+// conic for the gradient formulas, the pixel-independent factors of the
+// exponent's gradient, and each pixel's alpha (ok = the pixel has a
+// contribution: inside the box, before its last contributor, alpha above
+// the skip threshold).
+struct SplatBwd {
+    float dx, dy0, dy1, A, B, C;
+    float Adx, Bdx, hdx2;  // A dx, B dx, -dx^2 / 2
+    Eval e0, e1;
+    bool ok0, ok1;
+};
+
 // Adds the contribution of a splat with (already evaluated) alpha to this
-// pixel's state and to v[9].
-__device__ __forceinline__ void pixel_bwd_update(PixelBwd &p, const Eval &ev, float dx, float dy, float A, float B,
-                                                 float C, const float4 &col, float v[9]) {
+// pixel's state and to v[9] (dy: this pixel's vertical offset).
+__device__ __forceinline__ void pixel_bwd_update(PixelBwd &p, const Eval &ev, const SplatBwd &s, float dy,
+                                                 const float4 &col, float v[9]) {
     const float one_m = 1.0f - ev.alpha;
     p.T = __fdividef(p.T, one_m);  // transmittance in front of this Gaussian
     const float aT = ev.alpha * p.T;
     v[6] += p.dC0 * aT;
     v[7] += p.dC1 * aT;
     v[8] += p.dC2 * aT;
-    const float dalpha = p.T * (p.dC0 * (col.x - p.acc0) + p.dC1 * (col.y - p.acc1) + p.dC2 * (col.z - p.acc2));
-    p.acc0 = p.acc0 * one_m + col.x * ev.alpha;
-    p.acc1 = p.acc1 * one_m + col.y * ev.alpha;
-    p.acc2 = p.acc2 * one_m + col.z * ev.alpha;
+    const float dc = p.dC0 * col.x + p.dC1 * col.y + p.dC2 * col.z;
+    const float dalpha = p.T * (dc - p.accd);
+    p.accd = p.accd * one_m + dc * ev.alpha;
     if (!ev.clamped) {
         const float dpow = dalpha * ev.alpha;
         v[5] += dalpha * ev.G;
-        v[0] += dpow * (A * dx + B * dy);
-        v[1] += dpow * (C * dy + B * dx);
-        v[2] += -0.5f * dx * dx * dpow;
-        v[3] += -dx * dy * dpow;
-        v[4] += -0.5f * dy * dy * dpow;
+        v[0] += dpow * (s.Adx + s.B * dy);
+        v[1] += dpow * (s.C * dy + s.Bdx);
+        v[2] += dpow * s.hdx2;
+        v[3] -= (dpow * s.dx) * dy;
+        v[4] += dpow * (-0.5f * dy * dy);
     }
 }
-
-// A staged splat seen from this thread's two pixels: offsets, the original
-// conic for the gradient formulas, and each pixel's alpha (ok = the pixel
-// has a contribution: inside the box, before its last contributor, alpha
-// above the skip threshold).
-struct SplatBwd {
-    float dx, dy0, dy1, A, B, C;
-    Eval e0, e1;
-    bool ok0, ok1;
-};
 
 __device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, int px, float fpx, float fpy0,
                                                float fpy1, int py0, bool live0, bool live1, SplatBwd &r) {
@@ -281,6 +284,9 @@ __device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, 
     r.A = g.z * (1.0f / kHalfLog2e);
     r.B = g.w * (0.5f / kHalfLog2e);
     r.C = cb.x * (1.0f / kHalfLog2e);
+    r.Adx = r.A * r.dx;
+    r.Bdx = r.B * r.dx;
+    r.hdx2 = -0.5f * r.dx * r.dx;
     r.ok0 = live0 && xin && py0 >= y0 && py0 <= y1 && splat_alpha(e0, cb.y, r.e0);
     r.ok1 = live1 && xin && py0 + 1 >= y0 && py0 + 1 <= y1 && splat_alpha(e1, cb.y, r.e1);
 }
@@ -331,7 +337,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
     const uint2 rg = a.ranges[a.tile_off + tile];
     const int begin = (int)rg.x;
     const int64_t plane = (int64_t)a.W * a.H;
-    PixelBwd p0{0.f, a.bg0, a.bg1, a.bg2, 0.f, 0.f, 0.f, 0u}, p1 = p0;
+    PixelBwd p0{0.f, 0.f, 0.f, 0.f, 0.f, 0u}, p1 = p0;
     if (in0) {
         const int64_t pix = (int64_t)py0 * a.W + px;
         p0.T = T_final[pix];
@@ -339,6 +345,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
         p0.dC0 = dL_dimg[pix];
         p0.dC1 = dL_dimg[plane + pix];
         p0.dC2 = dL_dimg[2 * plane + pix];
+        p0.accd = p0.dC0 * a.bg0 + p0.dC1 * a.bg1 + p0.dC2 * a.bg2;  // behind the last contributor: the background
     }
     if (in1) {
         const int64_t pix = (int64_t)(py0 + 1) * a.W + px;
@@ -347,6 +354,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
         p1.dC0 = dL_dimg[pix];
         p1.dC1 = dL_dimg[plane + pix];
         p1.dC2 = dL_dimg[2 * plane + pix];
+        p1.accd = p1.dC0 * a.bg0 + p1.dC1 * a.bg1 + p1.dC2 * a.bg2;
     }
     // block-wide max of n_contrib: positions at or beyond it are never used
     const uint32_t m = __reduce_max_sync(0xffffffffu, max(p0.last, p1.last));
@@ -397,10 +405,10 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                 float vb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (sa.ok0 || sa.ok1 || sb.ok0 || sb.ok1) {
                     const float4 cola = s_rgb[ja], colb = s_rgb[jb];
-                    if (sa.ok0) pixel_bwd_update(p0, sa.e0, sa.dx, sa.dy0, sa.A, sa.B, sa.C, cola, va);
-                    if (sb.ok0) pixel_bwd_update(p0, sb.e0, sb.dx, sb.dy0, sb.A, sb.B, sb.C, colb, vb);
-                    if (sa.ok1) pixel_bwd_update(p1, sa.e1, sa.dx, sa.dy1, sa.A, sa.B, sa.C, cola, va);
-                    if (sb.ok1) pixel_bwd_update(p1, sb.e1, sb.dx, sb.dy1, sb.A, sb.B, sb.C, colb, vb);
+                    if (sa.ok0) pixel_bwd_update(p0, sa.e0, sa, sa.dy0, cola, va);
+                    if (sb.ok0) pixel_bwd_update(p0, sb.e0, sb, sb.dy0, colb, vb);
+                    if (sa.ok1) pixel_bwd_update(p1, sa.e1, sa, sa.dy1, cola, va);
+                    if (sb.ok1) pixel_bwd_update(p1, sb.e1, sb, sb.dy1, colb, vb);
                 }
                 const bool anya = __any_sync(0xffffffffu, sa.ok0 || sa.ok1);
                 const bool anyb = __any_sync(0xffffffffu, sb.ok0 || sb.ok1);
