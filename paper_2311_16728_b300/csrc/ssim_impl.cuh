@@ -194,6 +194,16 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
     __syncthreads();
     for (int vt = threadIdx.x; vt < kLTW * (kLTH / kRun); vt += NT) {
         const int tx = vt % kLTW, i0 = (vt / kLTW) * kRun;
+        // this thread's rendered and target values, in flight during the blur
+        float xs[kRun], ys[kRun];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            const int gx = ox + tx, gy = oy + i0 + o;
+            const bool in = gx < W && gy < H;
+            const int64_t idx = cb + (int64_t)(in ? gy : 0) * W + (in ? gx : 0);
+            xs[o] = x[idx];
+            ys[o] = y[idx];
+        }
         float g[3][kRun];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -213,7 +223,7 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
             const int gx = ox + tx, gy = oy + i0 + o;
             if (gx < W && gy < H) {
                 const int64_t idx = cb + (int64_t)gy * W + gx;
-                const float xv = x[idx], yv = y[idx];
+                const float xv = xs[o], yv = ys[o];
                 const float d = xv - yv;
                 const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
                 dx_out[idx] = ((1.f - lambda) * sg - lambda * (g[0][o] + 2.f * xv * g[1][o] + yv * g[2][o])) * inv_n;
