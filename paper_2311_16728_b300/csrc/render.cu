@@ -17,12 +17,15 @@
 
 namespace gsr {
 
+// kCount: also write the per-pixel number of blended Gaussians (a work
+// counter); without it the counting is compiled out
+template <bool kCount>
 __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__restrict__ img,
                                                          float *__restrict__ T_final,
                                                          uint32_t *__restrict__ n_contrib,
                                                          uint32_t *__restrict__ n_blended) {
     extern __shared__ float4 smem[];
-    render_fwd_tile(a, blockIdx.x, img, T_final, n_contrib, n_blended, smem);
+    render_fwd_tile(a, blockIdx.x, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem);
 }
 
 __global__ void __maxnreg__(80) render_bwd_kernel(RenderArgs a, const float *__restrict__ T_final,
@@ -70,7 +73,8 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const RenderArgs a = make_args(proj, vals, tile_ranges, cam, tiling, bg);
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
-    render_fwd_kernel<<<tiles, nthr, render_fwd_smem(nthr), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
+    auto kernel = n_blended ? render_fwd_kernel<true> : render_fwd_kernel<false>;
+    kernel<<<tiles, nthr, render_fwd_smem(nthr), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
     return check_launch("render_fwd_kernel");
 }
 

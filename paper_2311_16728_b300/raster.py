@@ -340,8 +340,9 @@ class MappingStep:
 
     `views` is a list of (camera, gt image) pairs sharing one resolution; each
     call to `step()` trains on the next view.  `capture()` records every view's
-    iteration as CUDA graphs, one per stage (the camera struct is baked into
-    each launch), so that CUDA events between stages time them live.
+    iteration as one CUDA graph (the camera struct is baked into each launch),
+    and also as one graph per stage, so that CUDA events between stages can
+    time them live (`step(events=...)` replays those).
     """
 
     def __init__(self, params: Gaussians, views, tiling: L.gsr_tiling = None, adam_cfg: AdamConfig = AdamConfig(),
@@ -373,6 +374,7 @@ class MappingStep:
         self.vb.status.zero_()  # the sizing passes may have flagged overflow
         self.vb.cam = cam0
         self.graphs = None
+        self.whole = None
         self.k = 0
 
     def _stage(self, idx: int, name: str, stream=None):
@@ -413,7 +415,8 @@ class MappingStep:
         self.adam.step_count.copy_(step0)
 
     def capture(self):
-        """Capture one CUDA graph per (view, stage)."""
+        """Capture one CUDA graph per view (the whole iteration) and one per
+        (view, stage)."""
         # one eager iteration loads every kernel before capture; its effect on
         # the parameters, moments and step counter is undone afterwards
         snap = self._snapshot()
@@ -435,6 +438,13 @@ class MappingStep:
                 gph.instantiate()
                 per.append(gph)
             self.graphs.append(per)
+        self.whole = []
+        for i in range(len(self.views)):
+            gph = torch.cuda.CUDAGraph(keep_graph=True)
+            with torch.cuda.graph(gph):
+                self._run(i, torch.cuda.current_stream())
+            gph.instantiate()
+            self.whole.append(gph)
         self.vb.cam = self.views[0][0]
 
     def step(self, events=None):
@@ -444,7 +454,12 @@ class MappingStep:
         self.step_view(self.k % len(self.views), events)
 
     def step_view(self, i: int, events=None):
-        """One iteration on view i."""
+        """One iteration on view i: one graph replay, or (with events) one
+        replay per stage with the events between them."""
+        if events is None and self.whole is not None:
+            self.whole[i].replay()
+            self.k += 1
+            return
         if events is not None:
             events[0].record()
         for si, name in enumerate(STAGES):
