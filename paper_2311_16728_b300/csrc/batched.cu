@@ -238,6 +238,9 @@ __device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
     return v;
 }
 
+// kQuad: the views' tiles are 16 x 16 (quadrant warps; box tests from staged
+// lane masks), one instance per tiling so the blend loops carry no branch
+template <bool kQuad>
 __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
     extern __shared__ float4 smem4[];
     float *smf = reinterpret_cast<float *>(smem4);
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __g
     for (int it = next_item(a.sync + 0, &s_item); it < a.tiles_total; it = next_item(a.sync + 0, &s_item)) {
         const int v = view_of_tile(a, it);
         const IterView &w = a.view[v];
-        render_fwd_tile(view_args(a, w), it - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
+        render_fwd_tile<kQuad>(view_args(a, w), it - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
     phase_stamp(a.sync, 1);
@@ -286,7 +289,8 @@ __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __g
     for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
         const int v = view_of_tile(a, it);
         const IterView &w = a.view[v];
-        render_bwd_tile(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1, a.g2, smem4);
+        render_bwd_tile<kQuad>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1, a.g2,
+                               smem4);
     }
 }
 
@@ -597,11 +601,13 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     cudaStream_t st = as_cuda(stream);
     if (cudaMemsetAsync(a.sync, 0, 8 * sizeof(unsigned), st) != cudaSuccess) return check_launch("memset sync");
     const size_t smem = iterate_smem();
-    cudaFuncSetAttribute(batched_iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kernel = tiling->tile_w == 16 && tiling->tile_h == 16 ? batched_iterate_kernel<true>
+                                                               : batched_iterate_kernel<false>;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_iterate_kernel, kIterThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kIterThreads, smem);
     if (per_sm < 1) {
         set_error("gsr_batched_iterate: the persistent kernel does not fit on an SM");
         return GSR_ERR_UNSUPPORTED;
@@ -616,7 +622,7 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, batched_iterate_kernel, a) != cudaSuccess) return check_launch("batched_iterate_kernel");
+    if (cudaLaunchKernelEx(&cfg, kernel, a) != cudaSuccess) return check_launch("batched_iterate_kernel");
     return check_launch("batched_iterate_kernel");
 }
 

@@ -19,21 +19,23 @@ namespace gsr {
 
 // kCount: also write the per-pixel number of blended Gaussians (a work
 // counter); without it the counting is compiled out
-template <bool kCount>
+// kQuad: 16 x 16 tiles (quadrant warps, box tests from staged lane masks)
+template <bool kCount, bool kQuad>
 __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__restrict__ img,
                                                          float *__restrict__ T_final,
                                                          uint32_t *__restrict__ n_contrib,
                                                          uint32_t *__restrict__ n_blended) {
     extern __shared__ float4 smem[];
-    render_fwd_tile(a, blockIdx.x, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem);
+    render_fwd_tile<kQuad>(a, blockIdx.x, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem);
 }
 
+template <bool kQuad>
 __global__ void __maxnreg__(80) render_bwd_kernel(RenderArgs a, const float *__restrict__ T_final,
                                                          const uint32_t *__restrict__ n_contrib,
                                                          const float *__restrict__ dL_dimg, float *__restrict__ g0,
                                                          float *__restrict__ g1, float *__restrict__ g2) {
     extern __shared__ float4 smem[];
-    render_bwd_tile(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
+    render_bwd_tile<kQuad>(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
 static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const uint32_t *ranges,
@@ -73,7 +75,9 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const RenderArgs a = make_args(proj, vals, tile_ranges, cam, tiling, bg);
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
-    auto kernel = n_blended ? render_fwd_kernel<true> : render_fwd_kernel<false>;
+    const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
+    auto kernel = n_blended ? (quad ? render_fwd_kernel<true, true> : render_fwd_kernel<true, false>)
+                            : (quad ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
     kernel<<<tiles, nthr, render_fwd_smem(nthr), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
     return check_launch("render_fwd_kernel");
 }
@@ -104,7 +108,8 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
     const RenderArgs a = make_args(proj, vals, tile_ranges, cam, tiling, bg);
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
-    render_bwd_kernel<<<tiles, nthr, render_bwd_smem(nthr), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
+    auto kernel = tiling->tile_w == 16 && tiling->tile_h == 16 ? render_bwd_kernel<true> : render_bwd_kernel<false>;
+    kernel<<<tiles, nthr, render_bwd_smem(nthr), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
                                                                   grad2d->g1, grad2d->g2);
     return check_launch("render_bwd_kernel");
 }

@@ -55,11 +55,33 @@ __device__ __forceinline__ void warp_rect(const RenderArgs &a, int w, int ox, in
     ry1 = oy + 2 * (t1 / a.tw) + 1;
 }
 
+// Lanes of a quadrant warp (its 8 x 8 pixels at (rx0, ry0); lane l holds
+// column l & 7 of rows 2 (l >> 3) and 2 (l >> 3) + 1) whose first (.x) and
+// second (.y) pixel lie in the pixel box [x0, x1] x [y0, y1].
+__device__ __forceinline__ uint2 quad_box_lanes(int x0, int x1, int y0, int y1, int rx0, int ry0) {
+    const int c0 = max(x0 - rx0, 0), c1 = min(x1 - rx0, 7);
+    if (c0 > c1) return make_uint2(0u, 0u);
+    const uint32_t cm = (0xffu >> (7 - c1)) & (0xffu << c0);  // columns c0 .. c1
+    uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = ry0 + 2 * k;
+        if (r >= y0 && r <= y1) m0 |= cm << (8 * k);
+        if (r + 1 >= y0 && r + 1 <= y1) m1 |= cm << (8 * k);
+    }
+    return make_uint2(m0, m1);
+}
+
 // Stages Gaussian gid: exponent coefficients pre-scaled so that
 // exponent_2 = a2 dx^2 + b2 dx dy + c2 dy^2 (= -log2(e) d^T Q d / 2), and the
-// mask of warps (of a block of nwarps) that can see it.
+// mask of warps (of a block of nwarps) that can see it.  kQuad (16 x 16
+// tiles, quadrant warps): s_lanes[w] also receives, for every warp w that
+// can see it, the lanes whose pixels lie in its pixel box, so the blend
+// loops test one bit instead of the box.
+template <bool kQuad>
 __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, int ox, int oy, int nwarps,
-                                            float4 &s_xy, float4 &s_cb, float4 &s_rgb, uint32_t &s_mask) {
+                                            float4 &s_xy, float4 &s_cb, float4 &s_rgb, uint32_t &s_mask,
+                                            uint2 *s_lanes) {
     const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
     s_rgb = __ldg(a.rgb_depth + gid);
     const float A = g.z, B = g.w, C = c.x, op = c.y;
@@ -82,7 +104,10 @@ __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, i
             const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
             const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
             const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
-            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey) mask |= 1u << w;
+            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey) {
+                mask |= 1u << w;
+                if constexpr (kQuad) s_lanes[w] = quad_box_lanes(x0, x1, y0, y1, rx0, ry0);
+            }
         }
     }
     s_mask = mask;
@@ -111,19 +136,36 @@ struct PixAlpha {
     bool ok0, ok1;
 };
 
-__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, int px, float fpx, float fpy0,
-                                                 float fpy1, int py0, PixAlpha &r) {
-    const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
-    const bool xin = px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16);
-    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+// box test: the staged lane masks (kQuad) or the box itself
+template <bool kQuad>
+__device__ __forceinline__ void in_box(const float4 cb, const uint2 *lanes, int px, int py0, bool &in0, bool &in1) {
+    if constexpr (kQuad) {
+        const int lane = threadIdx.x & 31;
+        const uint2 m = lanes[threadIdx.x >> 5];
+        in0 = (m.x >> lane) & 1u;
+        in1 = (m.y >> lane) & 1u;
+    } else {
+        const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
+        const bool xin = px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16);
+        const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+        in0 = xin && py0 >= y0 && py0 <= y1;
+        in1 = xin && py0 + 1 >= y0 && py0 + 1 <= y1;
+    }
+}
+
+template <bool kQuad>
+__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, const uint2 *lanes, int px,
+                                                 float fpx, float fpy0, float fpy1, int py0, PixAlpha &r) {
+    bool b0, b1;
+    in_box<kQuad>(cb, lanes, px, py0, b0, b1);
     const float dx = fpx - g.x;
     const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
     const float dy0 = fpy0 - g.y, dy1 = fpy1 - g.y;
     const float e0 = __fmaf_rn(FM(cb.x, dy0), dy0, __fmaf_rn(bdx, dy0, t));
     const float e1 = __fmaf_rn(FM(cb.x, dy1), dy1, __fmaf_rn(bdx, dy1, t));
     Eval v0, v1;
-    r.ok0 = xin && py0 >= y0 && py0 <= y1 && splat_alpha(e0, cb.y, v0);
-    r.ok1 = xin && py0 + 1 >= y0 && py0 + 1 <= y1 && splat_alpha(e1, cb.y, v1);
+    r.ok0 = b0 && splat_alpha(e0, cb.y, v0);
+    r.ok1 = b1 && splat_alpha(e1, cb.y, v1);
     r.a0 = v0.alpha;
     r.a1 = v1.alpha;
 }
@@ -149,12 +191,14 @@ __device__ __forceinline__ void blend_fwd(bool ok, float alpha, const float4 *s_
 
 // ---------------------------------------------------------------- K5
 // One tile (local index `tile` of the view in `a`), by the whole block.
+template <bool kQuad>
 __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, float *__restrict__ img,
                                                 float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
                                                 uint32_t *__restrict__ n_blended, float4 *smem) {
     const int nthr = blockDim.x, nwarps = nthr >> 5;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(smem + 3 * nthr);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(smem + 3 * nthr);  // 4 per staged splat (kQuad)
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * nthr);
     int px, py0, ox, oy;
     thread_pixels(a, tile, px, py0, ox, oy);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -169,8 +213,8 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
         // stop the whole tile once every pixel has terminated
         if (__syncthreads_count(done0 && done1) == nthr) break;
         const int idx = base + (int)threadIdx.x;
-        if (idx < end) stage_splat(a, a.vals[idx], ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x],
-                                   s_rgb[threadIdx.x], s_mask[threadIdx.x]);
+        if (idx < end) stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x],
+                                          s_rgb[threadIdx.x], s_mask[threadIdx.x], s_lanes + 4 * threadIdx.x);
         else s_mask[threadIdx.x] = 0u;
         __syncthreads();
         const int cnt = min(nthr, end - base);
@@ -187,8 +231,8 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
                 const int jb = has_b ? c0 + __ffs(bits) - 1 : ja;
                 if (has_b) bits &= bits - 1;
                 PixAlpha pa, pb;
-                pixel_pair_alpha(s_xy[ja], s_cb[ja], px, fpx, fpy0, fpy1, py0, pa);
-                pixel_pair_alpha(s_xy[jb], s_cb[jb], px, fpx, fpy0, fpy1, py0, pb);
+                pixel_pair_alpha<kQuad>(s_xy[ja], s_cb[ja], s_lanes + 4 * ja, px, fpx, fpy0, fpy1, py0, pa);
+                pixel_pair_alpha<kQuad>(s_xy[jb], s_cb[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0, pb);
                 if (!has_b) pb.ok0 = pb.ok1 = false;
                 const uint32_t posa = (uint32_t)(base - begin + ja + 1), posb = (uint32_t)(base - begin + jb + 1);
                 blend_fwd(pa.ok0, pa.a0, s_rgb, ja, posa, done0, T0, C00, C01, C02, last0, nb0);
@@ -270,11 +314,12 @@ __device__ __forceinline__ void pixel_bwd_update(PixelBwd &p, const Eval &ev, co
     }
 }
 
-__device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, int px, float fpx, float fpy0,
-                                               float fpy1, int py0, bool live0, bool live1, SplatBwd &r) {
-    const uint32_t bx = __float_as_uint(cb.z), by = __float_as_uint(cb.w);
-    const bool xin = px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16);
-    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+template <bool kQuad>
+__device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, const uint2 *lanes, int px,
+                                               float fpx, float fpy0, float fpy1, int py0, bool live0, bool live1,
+                                               SplatBwd &r) {
+    bool b0, b1;
+    in_box<kQuad>(cb, lanes, px, py0, b0, b1);
     r.dx = fpx - g.x;
     const float t = FM(FM(g.z, r.dx), r.dx), bdx = FM(g.w, r.dx);
     r.dy0 = fpy0 - g.y;
@@ -287,8 +332,8 @@ __device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, 
     r.Adx = r.A * r.dx;
     r.Bdx = r.B * r.dx;
     r.hdx2 = -0.5f * r.dx * r.dx;
-    r.ok0 = live0 && xin && py0 >= y0 && py0 <= y1 && splat_alpha(e0, cb.y, r.e0);
-    r.ok1 = live1 && xin && py0 + 1 >= y0 && py0 + 1 <= y1 && splat_alpha(e1, cb.y, r.e1);
+    r.ok0 = live0 && b0 && splat_alpha(e0, cb.y, r.e0);
+    r.ok1 = live1 && b1 && splat_alpha(e1, cb.y, r.e1);
 }
 
 // Sums v[0..8] over the warp without broadcasting every value: each halving
@@ -321,13 +366,15 @@ __device__ __forceinline__ float warp_transpose_sum(float v[9], float &v8) {
     return y;
 }
 
+template <bool kQuad>
 __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, const float *__restrict__ T_final,
                                                 const uint32_t *__restrict__ n_contrib,
                                                 const float *__restrict__ dL_dimg, float *__restrict__ g0,
                                                 float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
     const int nthr = blockDim.x, nwarps = nthr >> 5;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(smem + 3 * nthr);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(smem + 3 * nthr);  // 4 per staged splat (kQuad)
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * nthr);
     uint32_t *s_gid = s_mask + nthr;
     uint32_t *s_max = s_gid + nthr;  // 32 entries
     int px, py0, ox, oy;
@@ -379,8 +426,8 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
         if (idx < bend) {
             const uint32_t gid = a.vals[idx];
             s_gid[threadIdx.x] = gid;
-            stage_splat(a, gid, ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x],
-                        s_mask[threadIdx.x]);
+            stage_splat<kQuad>(a, gid, ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x],
+                               s_mask[threadIdx.x], s_lanes + 4 * threadIdx.x);
         } else {
             s_mask[threadIdx.x] = 0u;
         }
@@ -398,9 +445,10 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                 if (has_b) bits &= ~(1u << (jb - c0));
                 const uint32_t posa = (uint32_t)(bstart + ja - begin), posb = (uint32_t)(bstart + jb - begin);
                 SplatBwd sa, sb;
-                splat_bwd_eval(s_xy[ja], s_cb[ja], px, fpx, fpy0, fpy1, py0, posa < p0.last, posa < p1.last, sa);
-                splat_bwd_eval(s_xy[jb], s_cb[jb], px, fpx, fpy0, fpy1, py0, has_b && posb < p0.last,
-                               has_b && posb < p1.last, sb);
+                splat_bwd_eval<kQuad>(s_xy[ja], s_cb[ja], s_lanes + 4 * ja, px, fpx, fpy0, fpy1, py0,
+                                      posa < p0.last, posa < p1.last, sa);
+                splat_bwd_eval<kQuad>(s_xy[jb], s_cb[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0,
+                                      has_b && posb < p0.last, has_b && posb < p1.last, sb);
                 float va[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float vb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (sa.ok0 || sa.ok1 || sb.ok0 || sb.ok1) {
@@ -433,9 +481,11 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
 
 
 // dynamic shared memory of the two tile routines for `nthr` threads
-__host__ __device__ inline size_t render_fwd_smem(int nthr) { return (3 * sizeof(float4) + sizeof(uint32_t)) * nthr; }
+__host__ __device__ inline size_t render_fwd_smem(int nthr) {
+    return (3 * sizeof(float4) + 4 * sizeof(uint2) + sizeof(uint32_t)) * nthr;
+}
 __host__ __device__ inline size_t render_bwd_smem(int nthr) {
-    return (3 * sizeof(float4) + 2 * sizeof(uint32_t)) * nthr + 32 * sizeof(uint32_t);
+    return (3 * sizeof(float4) + 4 * sizeof(uint2) + 2 * sizeof(uint32_t)) * nthr + 32 * sizeof(uint32_t);
 }
 
 }  // namespace gsr
