@@ -490,15 +490,17 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *s, uint32_t P) {
     constexpr int kWarps = NT / 32;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t C = P < 64 ? P : 64;  // chunk of the warp-local stages
+    // j is a power of two: the lower element of pair i is 2 j (i / j) + i % j,
+    // i.e. i with a zero bit inserted at bit log2(j)
     for (uint32_t k = 2; k <= P; k <<= 1) {
         uint32_t j = k >> 1;
         for (; j >= 32; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P / 2; i += NT) cmp_swap(s, 2 * j * (i / j) + (i % j), j, k);
+            for (uint32_t i = threadIdx.x; i < P / 2; i += NT) cmp_swap(s, ((i & ~(j - 1)) << 1) | (i & (j - 1)), j, k);
             __syncthreads();
         }
         for (uint32_t c = wid; c < P / C; c += kWarps) {
             for (uint32_t jj = j; jj > 0; jj >>= 1) {
-                if (lane < C / 2) cmp_swap(s, c * C + 2 * jj * (lane / jj) + (lane % jj), jj, k);
+                if (lane < C / 2) cmp_swap(s, c * C + (((lane & ~(jj - 1)) << 1) | (lane & (jj - 1))), jj, k);
                 __syncwarp();
             }
         }

@@ -125,9 +125,12 @@ def test_loss_matches_oracle(H, W):
     assert np.abs(d - d_ref).max() <= 1e-4 * scale
 
 
-def test_render_backward_matches_oracle_tiny():
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32)])
+def test_render_backward_matches_oracle_tiny(tile):
+    """16 x 16 tiles take the quadrant-warp path (staged lane masks), the
+    others the per-pixel box test."""
     p, cam = S.perturb(S.tiny_scene()), S.tiny_camera()
-    vb, g = gpu_view(p, cam)
+    vb, g = gpu_view(p, cam, tile=tile)
     ca = cam.as_array()
     dec, _, sc, (img, T, nc, mg) = _oracle_all(p, cam)
     dimg = S.random_grad_image(3, cam.height, cam.width, seed=3)
