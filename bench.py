@@ -1109,7 +1109,10 @@ def stage_rooflines(stage_ms, work, peaks, clk):
         elif st == "blend_bwd":
             out[st] = alu_entry("render_bwd_kernel", FLOPS_PER_BLEND_BWD * E)
         elif st == "preprocess_bwd":
-            out[st] = hbm_entry("preprocess_bwd_kernel", (240 + 48 + 480) * nv)
+            # per visible Gaussian: parameters 240 B and screen-space gradient
+            # 48 B read, gradients 240 B stored (they are zero before the pass),
+            # densify statistic and count 16 B; visibility word 4 B per Gaussian
+            out[st] = hbm_entry("preprocess_bwd_kernel", (240 + 48 + 240 + 16) * nv + 4 * n)
         elif st == "adam":
             # 15 float4 planes: param, m, v read + written for every Gaussian, the
             # gradient read + zeroed only where the view flag (4 B) is set
