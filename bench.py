@@ -346,7 +346,8 @@ def run_window(args):
                        "l2": "inputs larger than L2 (4 x 120 MB of params, grads, moments per step)"},
             "roofline": {"kernel": "batched_iterate_kernel (fwd + bwd blends)", "bound": "alu",
                          "achieved": flops / it_s / 1e12, "peak": fp32, "unit": "TFLOP/s",
-                         "frac": flops / it_s / 1e12 / fp32, "traffic": None, "alg_per_launch": flops,
+                         "frac": flops / it_s / 1e12 / fp32,
+                         "traffic": NCU_TRAFFIC_WINDOW_ITERATE if tile == (16, 16) else None, "alg_per_launch": flops,
                          "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"},
             "stages_ms": stage_ms, "iterate_phases_ms": phases,
             "one_view_kernels_ms": single, "per_level": per_level, "work": {"blends": blends, "views": bw.V},
@@ -1060,11 +1061,12 @@ def main():
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
-# with the current kernels (profiles/blend_kernels_300k_1200x680.md; the loss
-# stage is its two SSIM passes); absent when not captured for the current
-# kernel version.
-NCU_TRAFFIC = {"blend_bwd": 27.776256e6, "render_fwd": 10.62528e6, "loss": 69.339648e6, "adam": 442.247168e6,
-               "preprocess_bwd": 73.832448e6}
+# with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
+# loss stage is its two SSIM passes, the binning stage its seven kernels).
+NCU_TRAFFIC = {"preprocess": 49.497344e6, "bin_sort": 28.068096e6, "render_fwd": 10.619648e6, "loss": 69.054464e6,
+               "blend_bwd": 27.772672e6, "preprocess_bwd": 71.359744e6, "adam": 442.166528e6}
+# the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
+NCU_TRAFFIC_WINDOW_ITERATE = 681.693184e6
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20
