@@ -4,7 +4,8 @@
 // with the printed product index read as j.
 //
 // One CTA per screen tile; each thread owns two vertically adjacent pixels
-// (same column, so the x terms of the exponent are shared).  The tile's
+// (same column, so the x terms of the exponent are shared); the backward of
+// 16 x 16 tiles gives each thread four (render_q4.cuh).  The tile's
 // depth-sorted Gaussians are staged through shared memory one record per
 // thread per batch; while staging, each record gets a bit mask of the warps
 // whose pixel rectangle can see it at all (pixel box intersected with the
@@ -14,6 +15,7 @@
 // same instructions in both kernels, so the backward replays exactly the
 // forward's choices.
 #include "render_impl.cuh"
+#include "render_q4.cuh"
 
 namespace gsr {
 
@@ -36,6 +38,16 @@ __global__ void __maxnreg__(80) render_bwd_kernel(RenderArgs a, const float *__r
                                                          float *__restrict__ g1, float *__restrict__ g2) {
     extern __shared__ float4 smem[];
     render_bwd_tile<kQuad>(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
+}
+
+// 16 x 16 tiles: the backward with four pixels per thread (render_q4.cuh)
+__global__ void __launch_bounds__(kQ4Threads) render_bwd_q4_kernel(RenderArgs a, const float *__restrict__ T_final,
+                                                                   const uint32_t *__restrict__ n_contrib,
+                                                                   const float *__restrict__ dL_dimg,
+                                                                   float *__restrict__ g0, float *__restrict__ g1,
+                                                                   float *__restrict__ g2) {
+    extern __shared__ float4 smem[];
+    render_bwd_tile_q4(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
 static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const uint32_t *ranges,
@@ -108,7 +120,12 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
     const RenderArgs a = make_args(proj, vals, tile_ranges, cam, tiling, bg);
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
-    auto kernel = tiling->tile_w == 16 && tiling->tile_h == 16 ? render_bwd_kernel<true> : render_bwd_kernel<false>;
+    if (tiling->tile_w == 16 && tiling->tile_h == 16) {
+        render_bwd_q4_kernel<<<tiles, kQ4Threads, render_q4_smem(), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
+                                                                          grad2d->g1, grad2d->g2);
+        return check_launch("render_bwd_q4_kernel");
+    }
+    auto kernel = render_bwd_kernel<false>;
     kernel<<<tiles, nthr, render_bwd_smem(nthr), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
                                                                   grad2d->g1, grad2d->g2);
     return check_launch("render_bwd_kernel");

@@ -1,0 +1,194 @@
+// render_q4.cuh -- the backward blend (K7) of the tile-based renderer of
+// Photo-SLAM (arXiv 2311.16728) Sec. 3.3, Eq. 3, for 16 x 16 tiles with four
+// pixels per thread.
+//
+// 64 threads, two warps; warp w covers rows 8 w .. 8 w + 7 of the tile, lane l
+// column l & 15 and rows 8 w + 4 (l >> 4) + k, k < 4.  The x terms of a
+// splat's exponent are shared by a thread's four pixels, and every per-warp
+// cost (staging a splat, the warp's visibility test, the loop over visible
+// splats, the gradient reduction and its atomics) is paid once per 128
+// pixels instead of once per 64.  One splat per round: the four pixels are
+// four independent chains.  The per-pixel arithmetic is the two-pixel
+// routines' (render_impl.cuh).  (The forward blend keeps two pixels per
+// thread: its per-pixel work is small, and the coarser 16 x 8 warp regions
+// and later warp-level termination cost it more than the shared overhead
+// saves.)
+#pragma once
+
+#include "render_impl.cuh"
+
+namespace gsr {
+
+constexpr int kQ4Threads = 64;
+
+__device__ __forceinline__ void q4_pixels(const RenderArgs &a, int tile, int &px, int &py0, int &ox, int &oy) {
+    ox = (tile % a.gx) * 16;
+    oy = (tile / a.gx) * 16;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    px = ox + (l & 15);
+    py0 = oy + 8 * w + 4 * (l >> 4);
+}
+
+// Lanes of warp w (rows ry0 .. ry0 + 7 of the columns ox .. ox + 15) whose
+// k-th pixel lies in the pixel box [x0, x1] x [y0, y1], for k = 0 .. 3.
+__device__ __forceinline__ uint4 q4_box_lanes(int x0, int x1, int y0, int y1, int ox, int ry0) {
+    const int c0 = max(x0 - ox, 0), c1 = min(x1 - ox, 15);
+    if (c0 > c1) return make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t cm = (0xffffu >> (15 - c1)) & (0xffffu << c0);  // columns c0 .. c1
+    uint32_t m[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int lo = ry0 + k, hi = ry0 + 4 + k;
+        m[k] = ((lo >= y0 && lo <= y1) ? cm : 0u) | ((hi >= y0 && hi <= y1) ? (cm << 16) : 0u);
+    }
+    return make_uint4(m[0], m[1], m[2], m[3]);
+}
+
+// Stages Gaussian gid as stage_splat does, for the two 16 x 8 warps: the
+// mask of warps that can see it and, for those, the lanes of each pixel slot
+// inside its pixel box.
+__device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int ox, int oy, float4 &s_xy,
+                                         float4 &s_cb, float4 &s_rgb, uint32_t &s_mask, uint4 *s_lanes) {
+    const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
+    s_rgb = __ldg(a.rgb_depth + gid);
+    const float A = g.z, B = g.w, C = c.x, op = c.y;
+    s_xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
+    s_cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
+    uint32_t mask = 0u;
+    const float tau = 2.0f * __logf(255.0f * op);  // alpha >= 1/255  <=>  d^T Q d <= tau
+    if (tau > 0.0f) {
+        const float bb = B * B;
+        const float det = __fmaf_rn(A, C, -bb) + __fmaf_rn(-B, B, bb);
+        const float ex = sqrtf(tau * C / det) * 1.001f + 0.01f;
+        const float ey = sqrtf(tau * A / det) * 1.001f + 0.01f;
+        const uint32_t bx = __float_as_uint(c.z), by = __float_as_uint(c.w);
+        const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const int rx0 = ox, rx1 = ox + 15, ry0 = oy + 8 * w, ry1 = ry0 + 7;
+            const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
+            const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
+            const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
+            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey) {
+                mask |= 1u << w;
+                s_lanes[w] = q4_box_lanes(x0, x1, y0, y1, ox, ry0);
+            }
+        }
+    }
+    s_mask = mask;
+}
+
+__device__ __forceinline__ uint32_t q4_lane_bits(const uint4 m, int k) {
+    return k == 0 ? m.x : (k == 1 ? m.y : (k == 2 ? m.z : m.w));
+}
+
+// ---------------------------------------------------------------- K7
+__device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile, const float *__restrict__ T_final,
+                                                   const uint32_t *__restrict__ n_contrib,
+                                                   const float *__restrict__ dL_dimg, float *__restrict__ g0,
+                                                   float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
+    constexpr int nthr = kQ4Threads;
+    float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
+    uint4 *s_lanes = reinterpret_cast<uint4 *>(smem + 3 * nthr);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 2 * nthr);
+    uint32_t *s_gid = s_mask + nthr;
+    uint32_t *s_max = s_gid + nthr;  // 2 entries
+    int px, py0, ox, oy;
+    q4_pixels(a, tile, px, py0, ox, oy);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint2 rg = a.ranges[a.tile_off + tile];
+    const int begin = (int)rg.x;
+    const int64_t plane = (int64_t)a.W * a.H;
+    PixelBwd p[4];
+    uint32_t mlast = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        p[k] = PixelBwd{0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+        if (px < a.W && py0 + k < a.H) {
+            const int64_t pix = (int64_t)(py0 + k) * a.W + px;
+            p[k].T = T_final[pix];
+            p[k].last = n_contrib[pix];
+            p[k].dC0 = dL_dimg[pix];
+            p[k].dC1 = dL_dimg[plane + pix];
+            p[k].dC2 = dL_dimg[2 * plane + pix];
+            // behind the last contributor: the background
+            p[k].accd = p[k].dC0 * a.bg0 + p[k].dC1 * a.bg1 + p[k].dC2 * a.bg2;
+        }
+        mlast = max(mlast, p[k].last);
+    }
+    // block-wide max of n_contrib: positions at or beyond it are never used
+    const uint32_t m = __reduce_max_sync(0xffffffffu, mlast);
+    if (lane == 0) s_max[wid] = m;
+    __syncthreads();
+    // never past the tile's own list, whatever n_contrib holds
+    const int stop = min(begin + (int)max(s_max[0], s_max[1]), (int)rg.y);
+    const float fpx = (float)px;
+    // value k of the transposed reduction lands in lane 4k: its gradient slot
+    const int kval = (lane >> 2) & 7;
+    float *const gk = (kval < 4 ? g0 : g1) + (kval & 3);
+    for (int bend = stop; bend > begin; bend -= nthr) {
+        const int bstart = max(begin, bend - nthr);
+        __syncthreads();
+        const int idx = bstart + (int)threadIdx.x;
+        if (idx < bend) {
+            const uint32_t gid = a.vals[idx];
+            s_gid[threadIdx.x] = gid;
+            q4_stage(a, gid, ox, oy, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x], s_mask[threadIdx.x],
+                     s_lanes + 2 * threadIdx.x);
+        } else {
+            s_mask[threadIdx.x] = 0u;
+        }
+        __syncthreads();
+        const int cnt = bend - bstart;
+        for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            while (bits) {  // back to front
+                const int j = c0 + 31 - __clz(bits);
+                bits &= ~(1u << (j - c0));
+                const uint32_t pos = (uint32_t)(bstart + j - begin);
+                const float4 g = s_xy[j], cb = s_cb[j];
+                const uint4 lm = s_lanes[2 * j + wid];
+                SplatBwd s;
+                s.dx = fpx - g.x;
+                const float t = FM(FM(g.z, s.dx), s.dx), bdx = FM(g.w, s.dx);
+                s.A = g.z * (1.0f / kHalfLog2e);
+                s.B = g.w * (0.5f / kHalfLog2e);
+                s.C = cb.x * (1.0f / kHalfLog2e);
+                s.Adx = s.A * s.dx;
+                s.Bdx = s.B * s.dx;
+                s.hdx2 = -0.5f * s.dx * s.dx;
+                Eval ev[4];
+                float dy[4];
+                bool ok[4];
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    dy[k] = (float)(py0 + k) - g.y;
+                    const float e = __fmaf_rn(FM(cb.x, dy[k]), dy[k], __fmaf_rn(bdx, dy[k], t));
+                    ok[k] = pos < p[k].last && ((q4_lane_bits(lm, k) >> lane) & 1u) && splat_alpha(e, cb.y, ev[k]);
+                    any = any || ok[k];
+                }
+                float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (any) {
+                    const float4 col = s_rgb[j];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (ok[k]) pixel_bwd_update(p[k], ev[k], s, dy[k], col, v);
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    float v8;
+                    const float y = warp_transpose_sum(v, v8);
+                    const uint32_t gid = s_gid[j];
+                    if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
+                    else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+                }
+            }
+        }
+    }
+}
+
+__host__ __device__ inline size_t render_q4_smem() {
+    return (3 * sizeof(float4) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * kQ4Threads + 2 * sizeof(uint32_t);
+}
+
+}  // namespace gsr
