@@ -20,6 +20,7 @@
 
 #include "chain_impl.cuh"
 #include "render_impl.cuh"
+#include "render_q4.cuh"
 #include "ssim_impl.cuh"
 
 namespace gsr {
@@ -155,6 +156,14 @@ __device__ __forceinline__ int next_item(unsigned *counter, int *s_item) {
     return *s_item;
 }
 
+// next_item for one 64-thread half of the CTA (each half takes its own items)
+__device__ __forceinline__ int next_item_half(unsigned *counter, int *s_item) {
+    Q4Group<true>::sync();
+    if ((threadIdx.x & 63) == 0) *s_item = (int)atomicAdd(counter, 1u);
+    Q4Group<true>::sync();
+    return *s_item;
+}
+
 // Grid-wide barrier of a cooperative launch (all CTAs resident).  Returns
 // false when the run was aborted: a wait that exceeded its bound sets the
 // abort flag and the timeout status, and every later barrier and phase is
@@ -244,7 +253,7 @@ template <bool kQuad>
 __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
     extern __shared__ float4 smem4[];
     float *smf = reinterpret_cast<float *>(smem4);
-    __shared__ int s_item, s_ok;
+    __shared__ int s_item, s_ok, s_item2[2];
     __shared__ float s_red[32];
     __shared__ double s_dbl[2 * kIterThreads];
     const unsigned nb = gridDim.x;
@@ -285,17 +294,31 @@ __global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __g
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
     phase_stamp(a.sync, 3);
-    // ---- phase 4: backward blend of every (view, tile)
-    for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
-        const int v = view_of_tile(a, it);
-        const IterView &w = a.view[v];
-        render_bwd_tile<kQuad>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1, a.g2,
-                               smem4);
+    // ---- phase 4: backward blend of every (view, tile); 16 x 16 tiles run two
+    // at a time, one per 64-thread half of the CTA (four pixels per thread)
+    if constexpr (kQuad) {
+        const int half = (int)(threadIdx.x >> 6);
+        float4 *sm = smem4 + half * (render_q4_smem() / sizeof(float4));
+        for (int it = next_item_half(a.sync + 3, &s_item2[half]); it < a.tiles_total;
+             it = next_item_half(a.sync + 3, &s_item2[half])) {
+            const int v = view_of_tile(a, it);
+            const IterView &w = a.view[v];
+            render_bwd_tile_q4<true>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
+                                     a.g2, sm);
+        }
+    } else {
+        for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
+            const int v = view_of_tile(a, it);
+            const IterView &w = a.view[v];
+            render_bwd_tile<false>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
+                                   a.g2, smem4);
+        }
     }
 }
 
 static size_t iterate_smem() {
     size_t s = render_bwd_smem(kIterThreads);
+    if (2 * render_q4_smem() > s) s = 2 * render_q4_smem();
     if (render_fwd_smem(kIterThreads) > s) s = render_fwd_smem(kIterThreads);
     if (sizeof(float) * kPass1Floats > s) s = sizeof(float) * kPass1Floats;
     if (sizeof(float) * kPass2Floats > s) s = sizeof(float) * kPass2Floats;

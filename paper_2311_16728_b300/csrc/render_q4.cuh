@@ -21,10 +21,11 @@ namespace gsr {
 
 constexpr int kQ4Threads = 64;
 
-__device__ __forceinline__ void q4_pixels(const RenderArgs &a, int tile, int &px, int &py0, int &ox, int &oy) {
+__device__ __forceinline__ void q4_pixels(const RenderArgs &a, int tile, int ti, int &px, int &py0, int &ox,
+                                          int &oy) {
     ox = (tile % a.gx) * 16;
     oy = (tile / a.gx) * 16;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int w = ti >> 5, l = ti & 31;
     px = ox + (l & 15);
     py0 = oy + 8 * w + 4 * (l >> 4);
 }
@@ -82,20 +83,40 @@ __device__ __forceinline__ uint32_t q4_lane_bits(const uint4 m, int k) {
     return k == 0 ? m.x : (k == 1 ? m.y : (k == 2 ? m.z : m.w));
 }
 
+// The 64 threads of one tile: the whole CTA (kHalf false), or one half of a
+// 128-thread CTA that runs two tiles at once (kHalf: thread index modulo 64,
+// named barrier 1 + half over its 64 threads).
+template <bool kHalf>
+struct Q4Group {
+    __device__ __forceinline__ static int tid() { return kHalf ? (int)(threadIdx.x & 63) : (int)threadIdx.x; }
+    __device__ __forceinline__ static void sync() {
+        if constexpr (kHalf) {
+            // immediate barrier ids (1, 2): the CTA reserves only the ids it names
+            if (threadIdx.x < 64) asm volatile("bar.sync 1, 64;" ::: "memory");
+            else asm volatile("bar.sync 2, 64;" ::: "memory");
+        } else {
+            __syncthreads();
+        }
+    }
+};
+
 // ---------------------------------------------------------------- K7
+template <bool kHalf = false>
 __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile, const float *__restrict__ T_final,
                                                    const uint32_t *__restrict__ n_contrib,
                                                    const float *__restrict__ dL_dimg, float *__restrict__ g0,
                                                    float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
+    using G = Q4Group<kHalf>;
     constexpr int nthr = kQ4Threads;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
     uint4 *s_lanes = reinterpret_cast<uint4 *>(smem + 3 * nthr);
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 2 * nthr);
     uint32_t *s_gid = s_mask + nthr;
     uint32_t *s_max = s_gid + nthr;  // 2 entries
+    const int ti = G::tid();
     int px, py0, ox, oy;
-    q4_pixels(a, tile, px, py0, ox, oy);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    q4_pixels(a, tile, ti, px, py0, ox, oy);
+    const int lane = ti & 31, wid = ti >> 5;
     const uint2 rg = a.ranges[a.tile_off + tile];
     const int begin = (int)rg.x;
     const int64_t plane = (int64_t)a.W * a.H;
@@ -119,7 +140,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     // block-wide max of n_contrib: positions at or beyond it are never used
     const uint32_t m = __reduce_max_sync(0xffffffffu, mlast);
     if (lane == 0) s_max[wid] = m;
-    __syncthreads();
+    G::sync();
     // never past the tile's own list, whatever n_contrib holds
     const int stop = min(begin + (int)max(s_max[0], s_max[1]), (int)rg.y);
     const float fpx = (float)px;
@@ -128,17 +149,16 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     float *const gk = (kval < 4 ? g0 : g1) + (kval & 3);
     for (int bend = stop; bend > begin; bend -= nthr) {
         const int bstart = max(begin, bend - nthr);
-        __syncthreads();
-        const int idx = bstart + (int)threadIdx.x;
+        G::sync();
+        const int idx = bstart + ti;
         if (idx < bend) {
             const uint32_t gid = a.vals[idx];
-            s_gid[threadIdx.x] = gid;
-            q4_stage(a, gid, ox, oy, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x], s_mask[threadIdx.x],
-                     s_lanes + 2 * threadIdx.x);
+            s_gid[ti] = gid;
+            q4_stage(a, gid, ox, oy, s_xy[ti], s_cb[ti], s_rgb[ti], s_mask[ti], s_lanes + 2 * ti);
         } else {
-            s_mask[threadIdx.x] = 0u;
+            s_mask[ti] = 0u;
         }
-        __syncthreads();
+        G::sync();
         const int cnt = bend - bstart;
         for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
@@ -187,8 +207,10 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     }
 }
 
+// shared memory of one tile's 64 threads (a multiple of 16 bytes)
 __host__ __device__ inline size_t render_q4_smem() {
-    return (3 * sizeof(float4) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * kQ4Threads + 2 * sizeof(uint32_t);
+    return ((3 * sizeof(float4) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * kQ4Threads + 2 * sizeof(uint32_t) + 15) /
+           16 * 16;
 }
 
 }  // namespace gsr
