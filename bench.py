@@ -98,8 +98,10 @@ def oracle_sample(start, target_imgs_rows, cams, pose: int, rows: int, row0: int
     p = np.zeros((n, 60))
     oracle.adam(p, g, np.zeros_like(p), np.zeros_like(p), lr, 1)
     t7 = time.perf_counter()
+    # the band calls repeat their per-call fixed part (projection, depth
+    # sort): only the remainder scales with the number of rows
     fixed = (t1 - t0) + (t2 - t1) + (t5 - t4) + (t7 - t6)
-    per_band = (t3 - t2) + (t4 - t3) + (t6 - t5)
+    per_band = max(0.0, (t3 - t2) - (t2 - t1)) + (t4 - t3) + max(0.0, (t6 - t5) - (t5 - t4))
     full = fixed + per_band * (cam.height / rows)
     return full, {"measured_s": t7 - t0, "fixed_s": fixed, "band_s": per_band}
 
