@@ -986,16 +986,37 @@ def main():
     ms_per_step = ms_total / args.steps
     value = world * 1000.0 / ms_per_step
 
-    # ---- end to end: target image from pinned host memory in, loss out, every step
+    # ---- end to end: target image from pinned host memory in, loss out, every
+    # step.  Each step's target is copied on a second stream one step ahead,
+    # while the previous step computes (double buffering: each view has its
+    # own device buffer, last read 50 steps earlier; the copy waits for the
+    # step before the current one); every copy lies inside the timed region.
     host_gts = [g.cpu().pin_memory() for g in gts]
     host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    main, copy = torch.cuda.current_stream(), torch.cuda.Stream()
+    nv, k0 = len(ms.views), ms.k
+    ready = [torch.cuda.Event() for _ in range(args.steps)]
+    done = [torch.cuda.Event() for _ in range(args.steps)]
+
+    def fetch(k):  # the target of step k, on the copy stream
+        j = (k0 + k) % nv
+        with torch.cuda.stream(copy):
+            ms.views[j][1].copy_(host_gts[j], non_blocking=True)
+        ready[k].record(copy)
+
     torch.cuda.synchronize()
     e0.record()
+    copy.wait_stream(main)
+    fetch(0)
     for k in range(args.steps):
-        i = ms.k % len(ms.views)
-        ms.views[i][1].copy_(host_gts[i], non_blocking=True)
+        main.wait_event(ready[k])
+        if k + 1 < args.steps:
+            if k >= 1:
+                copy.wait_event(done[k - 1])
+            fetch(k + 1)
         ms.step()
+        done[k].record(main)
         host_loss.copy_(ms.vb.loss, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
