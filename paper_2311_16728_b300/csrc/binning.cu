@@ -569,6 +569,130 @@ __device__ __forceinline__ void smem_tile_sort(const uint64_t *__restrict__ seg,
     __syncthreads();
 }
 
+// Exclusive scan in place of the 256 words h[0 .. 255] by the first 256
+// threads of a block (NT >= 256; every thread calls it); s_tmp: 8 words.
+template <int NT>
+__device__ __forceinline__ void block_excl_scan_hist(uint32_t *h, uint32_t *s_tmp) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    uint32_t v = t < 256 ? h[t] : 0u, incl = v;
+    if (t < 256) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_tmp[wid] = incl;
+    }
+    __syncthreads();
+    if (t < 256) {
+        uint32_t add = 0;
+        for (int w = 0; w < wid; ++w) add += s_tmp[w];
+        h[t] = add + incl - v;
+    }
+    __syncthreads();
+}
+
+// Stable LSD radix sort of the entries a[0, L) (depth bits << 32 | value) by
+// their depth, 8 bits per pass over the depth bits that vary within the
+// segment, through b; returns the buffer that holds the result.  Entries of
+// equal depth keep their input order (fix_depth_ties orders them).  Shared
+// words: s_hist 256, s_wcnt (NT / 32) x 256, s_tmp 9.
+template <int NT>
+__device__ uint64_t *block_radix_sort_depth(uint64_t *a, uint64_t *b, uint32_t L, uint32_t *s_hist,
+                                            uint32_t *s_wcnt, uint32_t *s_tmp) {
+    constexpr int kWarps = NT / 32;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (t == 0) s_tmp[8] = 0u;
+    __syncthreads();
+    const uint32_t d0 = (uint32_t)(a[0] >> 32);
+    uint32_t x = 0;
+    for (uint32_t i = t; i < L; i += NT) x |= (uint32_t)(a[i] >> 32) ^ d0;
+    x = __reduce_or_sync(0xffffffffu, x);
+    if (lane == 0 && x) atomicOr(&s_tmp[8], x);
+    __syncthreads();
+    const uint32_t vary = s_tmp[8];
+    if (vary == 0u) return a;  // one depth: nothing to order here
+    const int lo = __ffs(vary) - 1, hi = 31 - __clz(vary);
+    for (int shift = 32 + (lo & ~7); shift <= 32 + hi; shift += 8) {
+        for (int d = t; d < 256; d += NT) s_hist[d] = 0u;
+        __syncthreads();
+        for (uint32_t i = t; i < L; i += NT) atomicAdd(&s_hist[(uint32_t)(a[i] >> shift) & 0xffu], 1u);
+        __syncthreads();
+        block_excl_scan_hist<NT>(s_hist, s_tmp);
+        // chunks of NT entries in index order: per-warp ranks by digit, warps
+        // in order within the chunk, chunks in order -> stable
+        for (uint32_t c0 = 0; c0 < L; c0 += NT) {
+            for (int k = t; k < kWarps * 256; k += NT) s_wcnt[k] = 0u;
+            __syncthreads();
+            const uint32_t i = c0 + (uint32_t)t;
+            const bool valid = i < L;
+            const uint64_t key = valid ? a[i] : 0ull;
+            const uint32_t d = valid ? (uint32_t)(key >> shift) & 0xffu : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t rank = __popc(peers & lt);
+            if (valid && rank == 0) s_wcnt[wid * 256 + d] = __popc(peers);
+            __syncthreads();
+            for (int dd = t; dd < 256; dd += NT) {
+                uint32_t run = s_hist[dd];
+                for (int w = 0; w < kWarps; ++w) {
+                    const uint32_t c = s_wcnt[w * 256 + dd];
+                    s_wcnt[w * 256 + dd] = run;
+                    run += c;
+                }
+                s_hist[dd] = run;
+            }
+            __syncthreads();
+            if (valid) b[s_wcnt[wid * 256 + d] + rank] = key;
+            __syncthreads();
+        }
+        uint64_t *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return a;
+}
+
+// r[0, L) sorted by depth: each run of equal depth is sorted by value (the
+// whole 64-bit entry) by the thread at its start.  Runs are rare and short;
+// the depth bits of a run are equal, so reordering one never changes what
+// the other threads compare.
+template <int NT>
+__device__ __forceinline__ void fix_depth_ties(uint64_t *r, uint32_t L) {
+    for (uint32_t i = threadIdx.x; i + 1 < L; i += NT) {
+        const uint32_t di = (uint32_t)(r[i] >> 32);
+        if ((uint32_t)(r[i + 1] >> 32) != di) continue;
+        if (i > 0 && (uint32_t)(r[i - 1] >> 32) == di) continue;
+        uint32_t j = i + 1;
+        while (j + 1 < L && (uint32_t)(r[j + 1] >> 32) == di) ++j;
+        for (uint32_t p = i + 1; p <= j; ++p) {
+            const uint64_t v = r[p];
+            uint32_t q = p;
+            while (q > i && r[q - 1] > v) {
+                r[q] = r[q - 1];
+                --q;
+            }
+            r[q] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// Tile t's segment seg[begin, begin + L) sorted in shared memory by the radix
+// sort (s_a, s_b: L entries each), then emitted.
+template <int NT>
+__device__ __forceinline__ void smem_tile_radix(const uint64_t *__restrict__ seg, uint32_t tile, uint32_t begin,
+                                                uint32_t L, uint64_t *s_a, uint64_t *s_b, uint32_t *s_hist,
+                                                uint32_t *s_wcnt, uint32_t *s_tmp, uint64_t *__restrict__ keys,
+                                                uint32_t *__restrict__ vals) {
+    for (uint32_t i = threadIdx.x; i < L; i += NT) s_a[i] = seg[begin + i];
+    __syncthreads();
+    uint64_t *r = block_radix_sort_depth<NT>(s_a, s_b, L, s_hist, s_wcnt, s_tmp);
+    fix_depth_ties<NT>(r, L);
+    emit_sorted<NT>(r, L, tile, begin, keys, vals);
+    __syncthreads();
+}
+
 constexpr int kSmallSortThreads = 256;
 constexpr int kLargeSortThreads = 1024;
 constexpr int kSortGrid = 148 * 8;
@@ -585,7 +709,8 @@ __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uin
                                                                        uint64_t *__restrict__ keys,
                                                                        uint32_t *__restrict__ vals) {
     constexpr int kWarps = kSmallSortThreads / 32;
-    __shared__ uint64_t s[kSmallTile];
+    __shared__ uint64_t s_a[kSmallTile], s_b[kSmallTile];
+    __shared__ uint32_t s_hist[256], s_wcnt[kWarps * 256], s_tmp[9];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t n_warp = list_counts[0], n_block = list_counts[2];
     for (uint32_t e = blockIdx.x * kWarps + wid; e < n_warp; e += gridDim.x * kWarps) {
@@ -612,7 +737,7 @@ __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uin
     for (uint32_t e = blockIdx.x; e < n_block; e += gridDim.x) {
         const uint32_t t = list2[e];
         const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
-        smem_tile_sort<kSmallSortThreads>(seg, t, b, L, s, keys, vals);
+        smem_tile_radix<kSmallSortThreads>(seg, t, b, L, s_a, s_b, s_hist, s_wcnt, s_tmp, keys, vals);
     }
 }
 
@@ -689,7 +814,12 @@ __global__ void __launch_bounds__(kLargeSortThreads) sort_large_kernel(const uin
     for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
         const uint32_t t = list[(size_t)cap - 1 - e];
         const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
-        if (L <= kLargeTile) {
+        if (L <= kLargeTile / 2) {
+            // s_big: two halves of kLargeTile / 2 entries, then the per-warp digit counts
+            uint32_t *s_w = reinterpret_cast<uint32_t *>(s_big + kLargeTile);
+            smem_tile_radix<kLargeSortThreads>(seg, t, b, L, s_big, s_big + kLargeTile / 2, s_base, s_w, s_warp,
+                                               keys, vals);
+        } else if (L <= kLargeTile) {
             smem_tile_sort<kLargeSortThreads>(seg, t, b, L, s_big, keys, vals);
         } else {
             // s_big serves as the per-warp digit counts (32 x 256 words)
@@ -821,7 +951,7 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_ts, kept_sk, d_written, pair_capacity, tile_ranges, seg);
     sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list2, list_counts, tile_ranges, seg, keys,
                                                                  vals);
-    const size_t big = sizeof(uint64_t) * kLargeTile;
+    const size_t big = sizeof(uint64_t) * kLargeTile + sizeof(uint32_t) * (kLargeSortThreads / 32) * 256;
     static_assert(sizeof(uint64_t) * kLargeTile >= sizeof(uint32_t) * (kLargeSortThreads / 32) * kRadix,
                   "the long-segment sort reuses the shared array for its per-warp counts");
     cudaFuncSetAttribute(sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
