@@ -88,6 +88,15 @@ class BatchedWindow:
         self.graph = None
         self.stage_graphs = None
 
+    def set_targets(self, gts):
+        """Points the window at another set of target images (one per view,
+        the same shapes); capture() afterwards bakes them into a new graph.
+        Two graphs over two target sets let one set be refilled while the
+        other is in use."""
+        assert len(gts) == self.V
+        self.gts = [g.contiguous() for g in gts]
+        self.p_gt = (ctypes.c_void_p * self.V)(*[t.data_ptr() for t in self.gts])
+
     def _set_capacity(self, cap: int):
         dev = self.params.mean_op.device
         self.cap = int(cap)
