@@ -61,9 +61,13 @@ def _config(extra=None):
     return c
 
 
-def _scene(poses: int = N_POSES):
+WORKLOAD_WALLS = WORKLOAD.replace("300k Gaussians in a 6x3x4 m room",
+                                  "300k Gaussians on the six walls of a 6x3x4 m room (surface-like; sensitivity variant)")
+
+
+def _scene(poses: int = N_POSES, kind: str = "room"):
     import synthetic as S
-    target = S.room_scene(N_GAUSS, seed=0)
+    target = S.room_scene(N_GAUSS, seed=0) if kind == "room" else S.wall_scene(N_GAUSS, seed=0)
     start = S.perturb(target, 0.05, seed=1)
     cams = [S.replica_camera(k) for k in range(poses)]
     return target, start, cams
@@ -916,6 +920,8 @@ def main():
                     help="run --steps iterations between cudaProfilerStart/Stop after the warm-up and exit "
                          "(for ncu --profile-from-start off); prints no bench line")
     ap.add_argument("--poses", type=int, default=N_POSES, help="trajectory poses trained on (profiling uses fewer)")
+    ap.add_argument("--scene", default="room", choices=["room", "walls"],
+                    help="mapping mode: Gaussians filling the room (headline) or on its six walls (sensitivity variant)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -953,7 +959,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     import paper_2311_16728_b300 as gsr
-    target, start, cams = _scene(args.poses)
+    target, start, cams = _scene(args.poses, args.scene)
 
     # targets: renders of the unperturbed set at every pose (setup, untimed)
     g_tgt = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
@@ -1082,7 +1088,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; Replica-shaped)",
-            "config": _config({"pairs_last_step": pairs, "poses": len(cams)}),
+            "config": _config({"pairs_last_step": pairs, "poses": len(cams), "scene": args.scene,
+                               **({"workload": WORKLOAD_WALLS} if args.scene == "walls" else {})}),
             "roofline": roof, "stages_ms": stage_ms, "stage_rooflines": stages, "work": work,
             "gpu_launches": launches, "clocks": clk,
             "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "iters/s",

@@ -86,7 +86,96 @@ def tiny_scene(n: int = 4096, seed: int = 0) -> Params:
 
 def room_scene(n: int, seed: int = 0) -> Params:
     rng = np.random.default_rng(seed)
-    return _draw(rng, n, (-3.0, -1.5, -2.0), (3.0, 1.5, 2.0))
+    return _draw(rng, n, (-3.0, -1.5, -2.0), (3.0, 1.5, 2.0))  # ROOM_LO, ROOM_HI
+
+
+ROOM_LO, ROOM_HI = (-3.0, -1.5, -2.0), (3.0, 1.5, 2.0)  # the 6 x 3 x 4 m room
+
+
+def _quat_from_matrix(R: np.ndarray) -> np.ndarray:
+    """(N, 3, 3) rotations -> (N, 4) unit quaternions (w, x, y, z), w >= 0."""
+    tr = R[:, 0, 0] + R[:, 1, 1] + R[:, 2, 2]
+    q = np.empty((R.shape[0], 4))
+    # Shepperd's method: take the largest of 4w^2, 4x^2, 4y^2, 4z^2
+    c = np.stack([tr, R[:, 0, 0], R[:, 1, 1], R[:, 2, 2]], 1)
+    k = c.argmax(1)
+    for i in range(R.shape[0]):
+        r = R[i]
+        if k[i] == 0:
+            w = np.sqrt(1.0 + tr[i]) / 2
+            q[i] = [w, (r[2, 1] - r[1, 2]) / (4 * w), (r[0, 2] - r[2, 0]) / (4 * w), (r[1, 0] - r[0, 1]) / (4 * w)]
+        elif k[i] == 1:
+            x = np.sqrt(1.0 + r[0, 0] - r[1, 1] - r[2, 2]) / 2
+            q[i] = [(r[2, 1] - r[1, 2]) / (4 * x), x, (r[0, 1] + r[1, 0]) / (4 * x), (r[0, 2] + r[2, 0]) / (4 * x)]
+        elif k[i] == 2:
+            y = np.sqrt(1.0 - r[0, 0] + r[1, 1] - r[2, 2]) / 2
+            q[i] = [(r[0, 2] - r[2, 0]) / (4 * y), (r[0, 1] + r[1, 0]) / (4 * y), y, (r[1, 2] + r[2, 1]) / (4 * y)]
+        else:
+            z = np.sqrt(1.0 - r[0, 0] - r[1, 1] + r[2, 2]) / 2
+            q[i] = [(r[1, 0] - r[0, 1]) / (4 * z), (r[0, 2] + r[2, 0]) / (4 * z), (r[1, 2] + r[2, 1]) / (4 * z), z]
+    q *= np.where(q[:, :1] < 0, -1.0, 1.0)
+    return q
+
+
+def wall_scene(n: int, seed: int = 0) -> Params:
+    """The room's Gaussians on its six walls instead of filling its volume
+    (surface-like, as indoor scenes are): faces drawn by area, positions
+    uniform on the face with 1 cm of normal jitter, two in-plane log-scales
+    N(-4, 0.5) and a 2 mm thickness along the wall normal (the local z axis,
+    turned onto the normal with a random spin about it), opacity logits
+    N(1, 1), colours as in room_scene."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(ROOM_LO), np.asarray(ROOM_HI)
+    size = hi - lo
+    faces = []  # (axis, side)
+    areas = []
+    for ax in range(3):
+        o = [a for a in range(3) if a != ax]
+        for side in (0, 1):
+            faces.append((ax, side))
+            areas.append(size[o[0]] * size[o[1]])
+    areas = np.asarray(areas) / np.sum(areas)
+    f = rng.choice(len(faces), size=n, p=areas)
+    mean = lo + size * rng.random((n, 3))
+    normal = np.zeros((n, 3))
+    for i, (ax, side) in enumerate(faces):
+        sel = f == i
+        mean[sel, ax] = (hi[ax] if side else lo[ax])
+        normal[sel, ax] = -1.0 if side else 1.0  # pointing into the room
+    mean += normal * rng.normal(0.0, 0.01, (n, 1))
+    # rotation taking e_z to the face normal (one per face), then a random
+    # spin about the normal: q = q_face * (cos(th/2), 0, 0, sin(th/2))
+    ez = np.array([0.0, 0.0, 1.0])
+    Rf = np.empty((len(faces), 3, 3))
+    for i, (ax, side) in enumerate(faces):
+        nz = np.zeros(3)
+        nz[ax] = -1.0 if side else 1.0
+        a = np.cross(ez, nz)
+        s_, c_ = np.linalg.norm(a), float(ez @ nz)
+        if s_ < 1e-12:
+            Rf[i] = np.eye(3) if c_ > 0 else np.diag([1.0, -1.0, -1.0])
+        else:
+            K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]]) / s_
+            ang = np.arctan2(s_, c_)
+            Rf[i] = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * (K @ K)
+    qf = _quat_from_matrix(Rf)[f]
+    th = rng.uniform(0, 2 * np.pi, n)
+    cs, sn = np.cos(th / 2), np.sin(th / 2)
+    w1, x1, y1, z1 = qf.T
+    q = np.stack([w1 * cs - z1 * sn, x1 * cs + y1 * sn, y1 * cs - x1 * sn, z1 * cs + w1 * sn], 1)
+    ls = np.empty((n, 3))
+    ls[:, :2] = rng.normal(-4.0, 0.5, (n, 2))
+    ls[:, 2] = np.log(0.002)
+    opac = rng.normal(1.0, 1.0, n)
+    sh48 = np.empty((n, 48))
+    sh48[:, 0:3] = rng.uniform(-1.0, 1.0, (n, 3))
+    sh48[:, 3:] = rng.normal(0.0, 0.1, (n, 45))
+    return Params(
+        mean_op=np.concatenate([mean, opac[:, None]], 1).astype(np.float32),
+        quat=q.astype(np.float32),
+        logscale=np.concatenate([ls, np.zeros((n, 1))], 1).astype(np.float32),
+        sh=np.ascontiguousarray(sh48.reshape(n, SH_PLANES, 4).transpose(1, 0, 2)).astype(np.float32),
+    )
 
 
 def perturb(p: Params, sigma: float = 0.05, seed: int = 1) -> Params:

@@ -39,3 +39,22 @@ def test_stereo_pair_baseline():
     assert np.isclose(np.linalg.norm(cr - cl), 0.11)
     # the right centre lies along the left camera's x axis
     assert np.allclose(left.R @ (cr - cl), [0.11, 0.0, 0.0])
+
+
+def test_wall_scene_lies_on_the_walls():
+    """The sensitivity variant: every mean within the 1 cm jitter (5 sigma) of
+    a wall of the room, the thin axis along that wall's normal (away from the
+    room's edges, where the nearest wall is ambiguous), unit quaternions."""
+    w = S.wall_scene(20000, seed=3)
+    m = w.mean_op[:, :3].astype(np.float64)
+    lo, hi = np.array(S.ROOM_LO), np.array(S.ROOM_HI)
+    d = np.minimum(np.abs(m - lo), np.abs(m - hi))
+    assert d.min(1).max() <= 0.05
+    q = w.quat.astype(np.float64)
+    np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-6)
+    qw, x, y, z = q.T
+    local_z = np.stack([2 * (x * z + qw * y), 2 * (y * z - qw * x), 1 - 2 * (x * x + y * y)], 1)
+    ax = d.argmin(1)
+    clear = np.sort(d, 1)[:, 1] > 0.1
+    assert np.abs(local_z[np.arange(len(ax)), ax])[clear].min() > 0.9999
+    assert np.allclose(w.logscale[:, 2], np.log(0.002))
