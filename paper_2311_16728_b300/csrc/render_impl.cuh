@@ -171,7 +171,7 @@ __device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb
 }
 
 // front-to-back blend of one evaluated splat into one pixel's state
-__device__ __forceinline__ void blend_fwd(bool ok, float alpha, const float4 *s_rgb, int j, uint32_t pos, bool &done,
+__device__ __forceinline__ void blend_fwd(bool ok, float alpha, const float4 &col, uint32_t pos, bool &done,
                                           float &T, float &C0, float &C1, float &C2, uint32_t &last, uint32_t &nb) {
     if (!ok || done) return;
     const float tn = FM(T, FS(1.0f, alpha));
@@ -179,7 +179,6 @@ __device__ __forceinline__ void blend_fwd(bool ok, float alpha, const float4 *s_
         done = true;
         return;
     }
-    const float4 col = s_rgb[j];
     const float w = alpha * T;
     C0 += col.x * w;
     C1 += col.y * w;
@@ -235,10 +234,11 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
                 pixel_pair_alpha<kQuad>(s_xy[jb], s_cb[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0, pb);
                 if (!has_b) pb.ok0 = pb.ok1 = false;
                 const uint32_t posa = (uint32_t)(base - begin + ja + 1), posb = (uint32_t)(base - begin + jb + 1);
-                blend_fwd(pa.ok0, pa.a0, s_rgb, ja, posa, done0, T0, C00, C01, C02, last0, nb0);
-                blend_fwd(pb.ok0, pb.a0, s_rgb, jb, posb, done0, T0, C00, C01, C02, last0, nb0);
-                blend_fwd(pa.ok1, pa.a1, s_rgb, ja, posa, done1, T1, C10, C11, C12, last1, nb1);
-                blend_fwd(pb.ok1, pb.a1, s_rgb, jb, posb, done1, T1, C10, C11, C12, last1, nb1);
+                const float4 cola = s_rgb[ja], colb = s_rgb[jb];
+                blend_fwd(pa.ok0, pa.a0, cola, posa, done0, T0, C00, C01, C02, last0, nb0);
+                blend_fwd(pb.ok0, pb.a0, colb, posb, done0, T0, C00, C01, C02, last0, nb0);
+                blend_fwd(pa.ok1, pa.a1, cola, posa, done1, T1, C10, C11, C12, last1, nb1);
+                blend_fwd(pb.ok1, pb.a1, colb, posb, done1, T1, C10, C11, C12, last1, nb1);
             }
         }
     }
