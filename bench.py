@@ -1124,10 +1124,10 @@ def main():
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
 # with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
 # loss stage is its two SSIM passes, the binning stage its seven kernels).
-NCU_TRAFFIC = {"preprocess": 49.497344e6, "bin_sort": 28.068096e6, "render_fwd": 10.619648e6, "loss": 69.054464e6,
-               "blend_bwd": 27.772672e6, "preprocess_bwd": 71.359744e6, "adam": 442.166528e6}
+NCU_TRAFFIC = {"preprocess": 49.481472e6, "bin_sort": 28.079104e6, "render_fwd": 10.620416e6, "loss": 69.09312e6,
+               "blend_bwd": 27.75424e6, "preprocess_bwd": 71.794176e6, "adam": 442.029312e6}
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
-NCU_TRAFFIC_WINDOW_ITERATE = 681.693184e6
+NCU_TRAFFIC_WINDOW_ITERATE = 682.628352e6
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20
@@ -1170,7 +1170,7 @@ def stage_rooflines(stage_ms, work, peaks, clk):
             # x, y read twice, three maps written and read, dL/dx written
             out[st] = hbm_entry("ssim_pass1/2_kernel", 4 * px * (2 + 3 + 3 + 2 + 1))
         elif st == "blend_bwd":
-            out[st] = alu_entry("render_bwd_kernel", FLOPS_PER_BLEND_BWD * E)
+            out[st] = alu_entry("render_bwd_q4_kernel", FLOPS_PER_BLEND_BWD * E)
         elif st == "preprocess_bwd":
             # per visible Gaussian: parameters 240 B and screen-space gradient
             # 48 B read, gradients 240 B stored (they are zero before the pass),
