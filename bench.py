@@ -401,7 +401,7 @@ def run_mlp(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peaks = _peaks()
     out = []
-    for M in (2048, 20000):
+    for M in ((20000,) if args.profile else (2048, 20000)):
         li = LearnedInit(init_weights(3), M, lr=1e-4)
         gen = torch.Generator(device="cuda").manual_seed(5)
         li.x[:M, :K_IN] = torch.rand(M, K_IN, device="cuda", generator=gen).to(torch.bfloat16)
@@ -423,6 +423,9 @@ def run_mlp(args):
                 fn()
             for _ in range(max(args.warmup, 3)):
                 g.replay()
+            if args.profile and name == "train_step":
+                _profile_steps(g.replay, args.steps)
+                return
             reps = 200
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()

@@ -49,23 +49,25 @@ static int32_t make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t 
     return GSR_OK;
 }
 
-template <int BN>
+template <int BN, int ST = (BN == 256 ? 4 : 6)>
 static int32_t launch_gemm_bn(const void *A, int64_t lda, const void *B, int64_t ldb, int M, int N, int K,
                               const umma::Epilogue &ep, int ksplit, int32_t *d_status, cudaStream_t st) {
-    using Cfg = umma::Config<BN>;
+    using Cfg = umma::Config<BN, ST>;
     CUtensorMap ma, mb;
     int32_t rc;
     if ((rc = make_map(&ma, A, M, K, lda, umma::BM)) || (rc = make_map(&mb, B, N, K, ldb, BN))) return rc;
-    cudaFuncSetAttribute(umma::gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    cudaFuncSetAttribute(umma::gemm_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     const dim3 grid(N / BN, M / umma::BM, ksplit);
-    umma::gemm_kernel<BN><<<grid, 192, Cfg::kSmem, st>>>(ma, mb, K, ep, d_status);
+    umma::gemm_kernel<BN, ST><<<grid, 192, Cfg::kSmem, st>>>(ma, mb, K, ep, d_status);
     return check_launch("umma gemm_kernel");
 }
 
 // D = A B^T with A [M x K], B [N x K] BF16 K-major; M % 128 == 0, N % 64 == 0,
-// K % 64 == 0; the widest BN in {256, 128, 64} that divides N.
+// K % 64 == 0; the widest BN in {256, 128, 64} that divides N, except that a
+// short reduction (K <= 256 without split, or bn64) takes BN = 64: there the
+// epilogue is most of the work and four times as many CTAs share it.
 int32_t gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int M, int N, int K,
-                  const umma::Epilogue &ep, int ksplit, int32_t *d_status, cudaStream_t st) {
+                  const umma::Epilogue &ep, int ksplit, int32_t *d_status, cudaStream_t st, bool bn64 = false) {
     if (M <= 0 || N <= 0 || K <= 0 || M % umma::BM || N % 64 || K % umma::BK || ksplit < 1 || !aligned16(A) ||
         !aligned16(B) || lda % 8 || ldb % 8) {
         set_error("gemm_bf16: need M %% 128 == 0, N %% 64 == 0, K %% 64 == 0, 16-byte aligned operands "
@@ -73,6 +75,14 @@ int32_t gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int M,
         return GSR_ERR_INVALID_ARG;
     }
     if (ksplit > K / umma::BK) ksplit = K / umma::BK;
+    // a reduction of at most 4 k-steps per CTA needs only a 2-stage ring (4 CTAs per SM)
+    if (ksplit == 1 && K <= 256) return launch_gemm_bn<64, 2>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
+    if (bn64) return launch_gemm_bn<64>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
+    // fewer 128 x 256 tiles than two per SM leave a ragged second wave (157
+    // tiles on 148 SMs take two tile times): 128 x 128 tiles on a 3-stage
+    // ring run two CTAs per SM instead
+    if (N % 256 == 0 && (int64_t)(N / 256) * (M / umma::BM) * ksplit < 2 * 148)
+        return launch_gemm_bn<128, 3>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     if (N % 256 == 0) return launch_gemm_bn<256>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     if (N % 128 == 0) return launch_gemm_bn<128>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     return launch_gemm_bn<64>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
@@ -184,24 +194,27 @@ __global__ void __launch_bounds__(256) mlp_loss_kernel(const float *__restrict__
                                                        const float *__restrict__ w, int64_t M, int64_t Mpad,
                                                        __nv_bfloat16 *__restrict__ dy, __nv_bfloat16 *__restrict__ dyT,
                                                        float *__restrict__ gb3, float *__restrict__ d_loss) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.0f, g = 0.0f;
-    int j = 0;
-    if (e < Mpad * kN3) {
-        const int64_t m = e / kN3;
-        j = (int)(e - m * kN3);
+    // thread: column j = tid % 64 of rows 4 k + tid / 64, grid-striding over
+    // the rows; the column sums and the loss stay in registers until one
+    // reduction and one atomic per column (and one for the loss) per block
+    const int j = (int)(threadIdx.x & 63), r0 = (int)(threadIdx.x >> 6);
+    float lsum = 0.0f, gsum = 0.0f;
+    const float wj = j < kOut ? w[j] : 0.0f;
+    for (int64_t m = 4 * (int64_t)blockIdx.x + r0; m < Mpad; m += 4 * (int64_t)gridDim.x) {
+        const int64_t e = m * kN3 + j;
+        float g = 0.0f;
         if (m < M && j < kOut) {
             const float d = y[e] - t[e];
-            l = w[j] * d * d / (float)M;
-            g = 2.0f * w[j] * d / (float)M;
+            lsum += wj * d * d / (float)M;
+            g = 2.0f * wj * d / (float)M;
         }
+        gsum += g;
         dy[e] = __float2bfloat16_rn(g);
         dyT[(int64_t)j * Mpad + m] = __float2bfloat16_rn(g);
     }
-    // 64 columns per 256 threads: four rows per block; reduce per column over the block
     __shared__ float s_g[256], s_l[256];
-    s_g[threadIdx.x] = g;
-    s_l[threadIdx.x] = l;
+    s_g[threadIdx.x] = gsum;
+    s_l[threadIdx.x] = lsum;
     __syncthreads();
     if (threadIdx.x < kN3) {
         const float s = s_g[threadIdx.x] + s_g[threadIdx.x + 64] + s_g[threadIdx.x + 128] + s_g[threadIdx.x + 192];
@@ -220,26 +233,42 @@ __global__ void __launch_bounds__(256) mlp_loss_kernel(const float *__restrict__
 // p, g, m, v FP32 [rows x cols]; g_t (if set) holds the gradient transposed
 // ([cols x rows]).  Writes the BF16 copy (and its transpose) of the updated
 // weights; the gradient stays readable until the next step clears it.
-__global__ void __launch_bounds__(256) mlp_adam_kernel(float *__restrict__ p, float *__restrict__ g, int g_t,
-                                                       float *__restrict__ m, float *__restrict__ v, int rows, int cols,
-                                                       float lr, float b1, float b2, float eps,
-                                                       const int32_t *__restrict__ d_step,
-                                                       __nv_bfloat16 *__restrict__ ph, __nv_bfloat16 *__restrict__ phT) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)rows * cols) return;
-    const int r = (int)(e / cols), c = (int)(e - (int64_t)r * cols);
-    const int64_t ge = g_t ? (int64_t)c * rows + r : e;
+
+// One tensor of the MLP's Adam step.
+struct MlpAdamT {
+    float *p, *g, *m, *v;
+    int g_t, rows, cols;
+    __nv_bfloat16 *ph, *phT;
+};
+struct MlpAdamSet {
+    MlpAdamT t[6];
+    int64_t off[7];  // element offsets of the tensors in one flat index space
+};
+
+// The six tensors' updates in one launch: thread f updates element f of the
+// flat index space.
+__global__ void __launch_bounds__(256) mlp_adam_all_kernel(const __grid_constant__ MlpAdamSet S, float lr, float b1,
+                                                           float b2, float eps, const int32_t *__restrict__ d_step) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= S.off[6]) return;
+    int k = 0;
+#pragma unroll
+    for (int q = 1; q < 6; ++q) k += f >= S.off[q] ? 1 : 0;
+    const MlpAdamT &T = S.t[k];
+    const int64_t e = f - S.off[k];
+    const int r = (int)(e / T.cols), c = (int)(e - (int64_t)r * T.cols);
+    const int64_t ge = T.g_t ? (int64_t)c * T.rows + r : e;
     const int t = *d_step + 1;
     const float bc1 = -expm1f((float)t * log1pf(b1 - 1.0f)), bc2 = -expm1f((float)t * log1pf(b2 - 1.0f));
-    const float gv = g[ge];
-    const float mv = b1 * m[e] + (1.0f - b1) * gv;
-    const float vv = b2 * v[e] + (1.0f - b2) * gv * gv;
-    const float pv = p[e] - lr * (mv / bc1) / (sqrtf(vv / bc2) + eps);
-    m[e] = mv;
-    v[e] = vv;
-    p[e] = pv;
-    if (ph) ph[e] = __float2bfloat16_rn(pv);
-    if (phT) phT[(int64_t)c * rows + r] = __float2bfloat16_rn(pv);
+    const float gv = T.g[ge];
+    const float mv = b1 * T.m[e] + (1.0f - b1) * gv;
+    const float vv = b2 * T.v[e] + (1.0f - b2) * gv * gv;
+    const float pv = T.p[e] - lr * (mv / bc1) / (sqrtf(vv / bc2) + eps);
+    T.m[e] = mv;
+    T.v[e] = vv;
+    T.p[e] = pv;
+    if (T.ph) T.ph[e] = __float2bfloat16_rn(pv);
+    if (T.phT) T.phT[(int64_t)c * T.rows + r] = __float2bfloat16_rn(pv);
 }
 
 __global__ void step_advance_mlp_kernel(int32_t *d_step) { *d_step += 1; }
@@ -521,14 +550,16 @@ extern "C" int32_t gsr_mlp_train_step(const gsr_mlp_weights *w, const gsr_mlp_we
         cudaMemsetAsync(d_loss, 0, sizeof(float), st) != cudaSuccess)
         return check_launch("mlp memset");
     if ((rc = mlp_forward_ws(w, x, Mpad, y, ws, L, true, d_status, st))) return rc;
-    const int64_t ty = Mpad * kN3;
-    mlp_loss_kernel<<<(unsigned)((ty + 255) / 256), 256, 0, st>>>(y, target, out_weight, M, Mpad, bf(L.dy),
-                                                                  bf(L.dyt), f32(L.gb3), d_loss);
+    const int64_t loss_blocks = Mpad / 4 < 2 * 148 ? Mpad / 4 : 2 * 148;
+    mlp_loss_kernel<<<(unsigned)loss_blocks, 256, 0, st>>>(y, target, out_weight, M, Mpad, bf(L.dy), bf(L.dyt),
+                                                           f32(L.gb3), d_loss);
     if ((rc = check_launch("mlp loss"))) return rc;
     // dW3^T = h2^T dy  (K = batch, split)
     umma::Epilogue g3{};
     g3.out_f32 = f32(L.gW3t); g3.ldf = kN3; g3.atomic_f32 = 1; g3.valid_rows = kH;
-    if ((rc = gemm_bf16(bf(L.h2t), Mpad, bf(L.dyt), Mpad, kH, kN3, (int)Mpad, g3, ksplit_for(Mpad, 2), d_status, st)))
+    // split-K over BN = 64 tiles: ~2 CTAs per SM, each split adds its partial tile atomically
+    if ((rc = gemm_bf16(bf(L.h2t), Mpad, bf(L.dyt), Mpad, kH, kN3, (int)Mpad, g3, ksplit_for(Mpad, 8), d_status, st,
+                        true)))
         return rc;
     // dpre2 = (dy W3) masked by h2 > 0; both layouts; gb2
     umma::Epilogue d2{};
@@ -540,8 +571,8 @@ extern "C" int32_t gsr_mlp_train_step(const gsr_mlp_weights *w, const gsr_mlp_we
     // dW2 = dpre2^T h1
     umma::Epilogue g2{};
     g2.out_f32 = f32(L.gW2); g2.ldf = kH; g2.atomic_f32 = 1; g2.valid_rows = kH;
-    if ((rc = gemm_bf16(bf(L.dpre2t), Mpad, bf(L.h1t), Mpad, kH, kH, (int)Mpad, g2, ksplit_for(Mpad, 2), d_status,
-                        st)))
+    if ((rc = gemm_bf16(bf(L.dpre2t), Mpad, bf(L.h1t), Mpad, kH, kH, (int)Mpad, g2, ksplit_for(Mpad, 8), d_status,
+                        st, true)))
         return rc;
     // dpre1^T = ((dpre2 W2) masked by h1 > 0)^T; gb1
     umma::Epilogue d1{};
@@ -555,19 +586,18 @@ extern "C" int32_t gsr_mlp_train_step(const gsr_mlp_weights *w, const gsr_mlp_we
     if ((rc = gemm_bf16(bf(L.dpre1t), Mpad, xT, Mpad, kH, kK0, (int)Mpad, g1, ksplit_for(Mpad, 2 * 37), d_status,
                         st)))
         return rc;
-    // Adam on every tensor (FP32 masters), refreshed BF16 copies
-    auto adam = [&](float *p, float *g, int gt, float *mm, float *vv, int rows, int cols, void *ph, void *phT) {
-        const int64_t tot = (int64_t)rows * cols;
-        mlp_adam_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p, g, gt, mm, vv, rows, cols, lr, beta1, beta2,
-                                                                       eps, d_step, (__nv_bfloat16 *)ph,
-                                                                       (__nv_bfloat16 *)phT);
-    };
-    adam(w->W1, f32(L.gW1), 0, m->W1, v->W1, kH, kK0, w->W1h, nullptr);
-    adam(w->b1, f32(L.gb1), 0, m->b1, v->b1, 1, kH, nullptr, nullptr);
-    adam(w->W2, f32(L.gW2), 0, m->W2, v->W2, kH, kH, w->W2h, w->W2hT);
-    adam(w->b2, f32(L.gb2), 0, m->b2, v->b2, 1, kH, nullptr, nullptr);
-    adam(w->W3, f32(L.gW3t), 1, m->W3, v->W3, kN3, kH, w->W3h, w->W3hT);
-    adam(w->b3, f32(L.gb3), 0, m->b3, v->b3, 1, kN3, nullptr, nullptr);
+    // Adam on every tensor (FP32 masters), refreshed BF16 copies, one launch
+    MlpAdamSet S{};
+    auto bfp = [](void *q) { return (__nv_bfloat16 *)q; };
+    S.t[0] = MlpAdamT{w->W1, f32(L.gW1), m->W1, v->W1, 0, kH, kK0, bfp(w->W1h), nullptr};
+    S.t[1] = MlpAdamT{w->b1, f32(L.gb1), m->b1, v->b1, 0, 1, kH, nullptr, nullptr};
+    S.t[2] = MlpAdamT{w->W2, f32(L.gW2), m->W2, v->W2, 0, kH, kH, bfp(w->W2h), bfp(w->W2hT)};
+    S.t[3] = MlpAdamT{w->b2, f32(L.gb2), m->b2, v->b2, 0, 1, kH, nullptr, nullptr};
+    S.t[4] = MlpAdamT{w->W3, f32(L.gW3t), m->W3, v->W3, 1, kN3, kH, bfp(w->W3h), bfp(w->W3hT)};
+    S.t[5] = MlpAdamT{w->b3, f32(L.gb3), m->b3, v->b3, 0, 1, kN3, nullptr, nullptr};
+    S.off[0] = 0;
+    for (int k = 0; k < 6; ++k) S.off[k + 1] = S.off[k] + (int64_t)S.t[k].rows * S.t[k].cols;
+    mlp_adam_all_kernel<<<(unsigned)((S.off[6] + 255) / 256), 256, 0, st>>>(S, lr, beta1, beta2, eps, d_step);
     step_advance_mlp_kernel<<<1, 1, 0, st>>>(d_step);
     return check_launch("mlp adam");
 }

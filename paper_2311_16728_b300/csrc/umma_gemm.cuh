@@ -149,9 +149,11 @@ struct Epilogue {
     int64_t valid_rows;           //            rows >= valid_rows are padding: not summed
 };
 
-template <int BN>
+// ST: stages of the shared-memory ring (default 4 for BN = 256, else 6); a
+// short reduction takes 2, so that several CTAs fit on an SM.
+template <int BN, int ST = (BN == 256 ? 4 : 6)>
 struct Config {
-    static constexpr int kStages = BN == 256 ? 4 : 6;
+    static constexpr int kStages = ST;
     static constexpr int kABytes = BM * BK * 2;
     static constexpr int kBBytes = BN * BK * 2;
     static constexpr int kStageBytes = kABytes + kBBytes;
@@ -160,11 +162,11 @@ struct Config {
 };
 
 // grid: (N / BN, M / BM, ksplit); K tiles of this CTA: the z-th slice.
-template <int BN>
+template <int BN, int ST = (BN == 256 ? 4 : 6)>
 __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, int K, Epilogue ep,
                                                       int32_t *d_status) {
-    using Cfg = Config<BN>;
+    using Cfg = Config<BN, ST>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-B aligned stages
@@ -279,13 +281,34 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CU
                     }
                 }
                 if (ep.colsum) {
+                    // column sums over the warp's 32 rows by a transposing
+                    // butterfly: each stage halves the values a lane keeps (16
+                    // shuffles in all); lane l ends with column
+                    // 8 b4 + 4 b3 + 2 b2 + b1 of its bits, lanes l and l ^ 1 alike
+                    float s16[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        float s = row_valid ? v[j] : 0.0f;
+                    for (int j = 0; j < 16; ++j) s16[j] = row_valid ? v[j] : 0.0f;
+                    float s8[8], s4[4], s2[2];
+                    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if (lane == 0) atomicAdd(ep.colsum + nb + j, s);
+                    for (int j = 0; j < 8; ++j) {
+                        const float keep = b4 ? s16[j + 8] : s16[j], send = b4 ? s16[j] : s16[j + 8];
+                        s8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                     }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float keep = b3 ? s8[j + 4] : s8[j], send = b3 ? s8[j] : s8[j + 4];
+                        s4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float keep = b2 ? s4[j + 2] : s4[j], send = b2 ? s4[j] : s4[j + 2];
+                        s2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    float s1 = (b1 ? s2[1] : s2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? s2[0] : s2[1], 2);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                    const int col = (b4 ? 8 : 0) + (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+                    if ((lane & 1) == 0) atomicAdd(ep.colsum + nb + col, s1);
                 }
             }
         }
