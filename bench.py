@@ -73,6 +73,15 @@ def _scene(poses: int = N_POSES, kind: str = "room"):
     return target, start, cams
 
 
+def _ordered(gsr, params, args):
+    """The map store in the order --order names (setup, untimed): Morton
+    order of the means over the room box, or the generator's order."""
+    if args.order == "input":
+        return params
+    import synthetic as S
+    return gsr.permuted(params, gsr.spatial_order(params, S.ROOM_LO, S.ROOM_HI))
+
+
 # ---------------------------------------------------------------- CPU oracle sample
 def oracle_sample(start, target_imgs_rows, cams, pose: int, rows: int, row0: int):
     """Time the oracle over one iteration restricted to `rows` image rows and
@@ -251,7 +260,7 @@ def run_window(args):
         vb.forward(g_tgt)
         kf.append((cam, vb.img.clone()))
     del vb, g_tgt
-    params = gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh)
+    params = _ordered(gsr, gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh), args)
     if args.tile == "auto":
         tile, report = autotune_window(params, kf, levels=WIN_LEVELS, steps=5, warmup=2)
     else:
@@ -380,6 +389,7 @@ def run_window(args):
                                    "iteration (preprocess, binning, persistent fwd/loss/bwd, chain, Adam) in one "
                                    "CUDA graph", "tile": f"{tile[0]}x{tile[1]}" + (" (autotuned)" if args.tile == "auto" else " (given)"),
                        "autotune_ms": report["ms_per_step"], "pairs": int(bw.num_pairs.item()),
+                       "map_order": args.order,
                        "l2": "inputs larger than L2 (4 x 120 MB of params, grads, moments per step)"},
             "roofline": {"kernel": "batched_iterate_kernel (fwd + bwd blends)", "bound": "alu",
                          "achieved": flops / it_s / 1e12, "peak": fp32, "unit": "TFLOP/s",
@@ -626,9 +636,11 @@ def run_densify(args):
     del vb, g_tgt
     cap = int(DENS_N * 1.25)
     params = gsr.Gaussians.zeros(cap)
-    for dst, src in ((params.mean_op, start.mean_op), (params.quat, start.quat), (params.logscale, start.logscale)):
-        dst[:DENS_N] = torch.tensor(src, device="cuda")
-    params.sh[:, :DENS_N] = torch.tensor(start.sh, device="cuda")
+    first = _ordered(gsr, gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh), args)
+    for dst, src in zip(params.tensors()[:3], first.tensors()[:3]):
+        dst[:DENS_N] = src
+    params.sh[:, :DENS_N] = first.sh
+    del first
     adam = gsr.Adam(params)
     dens = Densifier(params, adam, DENS_N)
     views = list(zip(cams, gts))
@@ -689,7 +701,7 @@ def run_densify(args):
                                    "mean NDC gradient norm >= 2e-4 (split above scale 0.03 m), prune opacity < 0.005; "
                                    "store with 25 % spare capacity, re-captured when it overflows or the map grew "
                                    "30 % since the pair capacity was sized", "gaussians_after_each_densify": counts,
-                       "rebuilds": rebuilds, "first_build_s": round(build_s[0], 1)},
+                       "rebuilds": rebuilds, "first_build_s": round(build_s[0], 1), "map_order": args.order},
             "iteration_ms": step_ms / iters, "densify_ms_per_step": dens_ms / max(1, segments - 1),
             "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -717,7 +729,7 @@ def run_stereo(args):
         # monochrome target: the luminance of the true render
         views.append((cam, (0.299 * vb.img[0] + 0.587 * vb.img[1] + 0.114 * vb.img[2])[None].contiguous()))
     del vb, g_tgt
-    params = gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh)
+    params = _ordered(gsr, gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh), args)
     ms = gsr.MappingStep(params, views)
     ms.capture()
     for _ in range(args.warmup):
@@ -745,7 +757,8 @@ def run_stereo(args):
             "data": "synthetic (seeded; EuRoC-shaped monochrome stereo)",
             "config": {"workload": f"{STEREO_N} Gaussians in a 6x3x4 m room; {N_POSES} poses x 2 cameras "
                                    "(0.11 m baseline) of 752x480 fx=fy=376, one view per iteration, Eq. 4 on the "
-                                   "luminance 0.299 R + 0.587 G + 0.114 B against monochrome targets, Adam"},
+                                   "luminance 0.299 R + 0.587 G + 0.114 B against monochrome targets, Adam",
+                       "map_order": args.order},
             "stages_ms": stage_ms, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -763,7 +776,7 @@ def run_pose(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     target, _, cams = _scene(1)
     true_cam = cams[0]
-    g = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
+    g = _ordered(gsr, gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh), args)
     vb = gsr.ViewBuffers(N_GAUSS, gsr.camera_from(true_cam), gsr.tiling_struct(16, 16), 1024)
     gsr.ensure_capacity(vb, g)
     vb.forward(g)
@@ -850,7 +863,7 @@ def run_pose(args):
                                    "6x3x4 m room, 1200x680 fx=fy=600, frame rendered from the true pose, camera "
                                    "1 degree / 3 cm off; preprocess, binning, forward blend, loss, backward blend "
                                    "and pose chain in one CUDA graph (fixed pose)",
-                       "visible": nv, "pairs": vb.pairs_needed()},
+                       "visible": nv, "pairs": vb.pairs_needed(), "map_order": args.order},
             "roofline": {"kernel": "pose_bwd_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "alg_bytes": alg,
                          "ms": ms_chain, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
@@ -925,6 +938,8 @@ def main():
     ap.add_argument("--poses", type=int, default=N_POSES, help="trajectory poses trained on (profiling uses fewer)")
     ap.add_argument("--scene", default="room", choices=["room", "walls"],
                     help="mapping mode: Gaussians filling the room (headline) or on its six walls (sensitivity variant)")
+    ap.add_argument("--order", default="morton", choices=["morton", "input"],
+                    help="map store in Morton order of the means (setup) or in generator order")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -975,7 +990,7 @@ def main():
         vb.forward(g_tgt)
         gts.append(vb.img.clone())
     del vb, g_tgt
-    params = gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh)
+    params = _ordered(gsr, gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh), args)
     ms = gsr.MappingStep(params, list(zip(cams, gts)), tiling)
     ms.capture()
     for _ in range(args.warmup):
@@ -1092,6 +1107,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; Replica-shaped)",
             "config": _config({"pairs_last_step": pairs, "poses": len(cams), "scene": args.scene,
+                               "map_order": args.order,
                                **({"workload": WORKLOAD_WALLS} if args.scene == "walls" else {})}),
             "roofline": roof, "stages_ms": stage_ms, "stage_rooflines": stages, "work": work,
             "gpu_launches": launches, "clocks": clk,
@@ -1127,10 +1143,10 @@ def main():
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
 # with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
 # loss stage is its two SSIM passes, the binning stage its seven kernels).
-NCU_TRAFFIC = {"preprocess": 49.481472e6, "bin_sort": 28.079104e6, "render_fwd": 10.620416e6, "loss": 69.09312e6,
-               "blend_bwd": 27.75424e6, "preprocess_bwd": 71.794176e6, "adam": 442.029312e6}
+NCU_TRAFFIC = {"preprocess": 15.451904e6, "bin_sort": 21.091328e6, "render_fwd": 4.220928e6, "loss": 69.118976e6,
+               "blend_bwd": 20.802304e6, "preprocess_bwd": 12.433920e6, "adam": 393.221632e6}
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
-NCU_TRAFFIC_WINDOW_ITERATE = 682.628352e6
+NCU_TRAFFIC_WINDOW_ITERATE = 606.532864e6
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20
@@ -1163,7 +1179,10 @@ def stage_rooflines(stage_ms, work, peaks, clk):
     out = {}
     for st in stage_ms:
         if st == "preprocess":
-            out[st] = hbm_entry("preprocess_fwd_kernel", 48 * n + 4 * n + (192 + 48) * nv)
+            # the frustum test reads the mean (16 B) and every Gaussian's tile
+            # count is written (4 B); a visible Gaussian also reads rotation
+            # and scale (32 B) and SH (192 B) and writes its record (48 B)
+            out[st] = hbm_entry("preprocess_fwd_kernel", (16 + 4) * n + (32 + 192 + 48) * nv)
         elif st == "bin_sort":
             # depth passes 4 x 16 B per visible, tile passes 2 x 16 B per pair, keys + values out 12 B per pair
             out[st] = hbm_entry("binning + radix passes", 4 * 16 * nv + 2 * 16 * K + 12 * K)

@@ -544,6 +544,29 @@ int32_t gsr_adam_step_touched(const gsr_param_buffers *params, const gsr_param_b
                               const gsr_adam_config *cfg, const uint32_t *touched, int32_t *d_step,
                               gsr_stream_t stream);
 
+/* ---------------------------------------------------------------- map order */
+
+/* Bytes of scratch for gsr_spatial_order over n Gaussians. */
+int32_t gsr_spatial_order_workspace_size(int64_t n, size_t *bytes);
+
+/* Spatial order of the map store (maintenance, outside the iteration):
+ * perm[i] (n uint32, device) = the index of the Gaussian that goes to place
+ * i when the Gaussians are sorted by the 30-bit Morton code of their means
+ * (each coordinate quantised to 10 bits over the box [lo, hi], host float[3],
+ * clamped; the three coordinates' bits interleaved), equal codes by index.
+ * With the store in this order the Gaussians a warp handles are spatial
+ * neighbours, which keeps the per-Gaussian kernels' visibility decisions
+ * coherent within a warp and their reads of visible Gaussians contiguous; it
+ * changes no result except the order of exactly equal depths.  n < 2^32. */
+int32_t gsr_spatial_order(const gsr_gaussians *g, const float *lo, const float *hi, uint32_t *perm,
+                          void *workspace, size_t workspace_bytes, gsr_stream_t stream);
+
+/* dst entry i = src entry perm[i] for every plane of n Gaussians' buffers
+ * (parameters, gradients or Adam moments; all 12 SH planes); src and dst
+ * must not overlap. */
+int32_t gsr_permute(const gsr_param_buffers *src, const gsr_param_buffers *dst, const uint32_t *perm, int64_t n,
+                    gsr_stream_t stream);
+
 /* One Gaussian-pyramid step down (Sec. 3.4, Eq. 5 GP^l): separable binomial
  * [1 4 6 4 1]/16 blur with reflect-101 borders, keeping even pixels.
  * in is C x H x W, out is C x ceil(H/2) x ceil(W/2). */

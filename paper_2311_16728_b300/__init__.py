@@ -10,9 +10,10 @@ from . import _lib
 from ._lib import GsrError
 from .raster import (LAMBDA_DSSIM, PYRAMID_LEVELS, STAGES, Adam, AdamConfig, Gaussians, MappingStep, RasterizeGaussians,
                      ViewBuffers, camera_at_level, camera_from, camera_struct, ensure_capacity, n_tiles, psnr,
-                     pyramid, rasterize, tiling_struct)
+                     permuted, pyramid, rasterize, spatial_order, tiling_struct)
 from .pose import PoseRefiner, so3_exp
 
 __all__ = ["_lib", "GsrError", "LAMBDA_DSSIM", "PYRAMID_LEVELS", "STAGES", "Adam", "AdamConfig", "Gaussians", "MappingStep",
            "RasterizeGaussians", "ViewBuffers", "camera_at_level", "camera_from", "camera_struct", "ensure_capacity",
-           "n_tiles", "psnr", "pyramid", "rasterize", "tiling_struct", "PoseRefiner", "so3_exp"]
+           "n_tiles", "psnr", "pyramid", "rasterize", "tiling_struct", "PoseRefiner", "so3_exp",
+           "spatial_order", "permuted"]

@@ -81,6 +81,9 @@ _SIGNATURES = {
                        c_void_p, c_void_p, P(gsr_grad2d), c_void_p], c_int32),
     "gsr_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d),
                             P(gsr_param_buffers), c_void_p, c_void_p, c_void_p], c_int32),
+    "gsr_spatial_order_workspace_size": ([c_int64, P(c_size_t)], c_int32),
+    "gsr_spatial_order": ([P(gsr_gaussians), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "gsr_permute": ([P(gsr_param_buffers), P(gsr_param_buffers), c_void_p, c_int64, c_void_p], c_int32),
     "gsr_pose_bwd": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d), c_void_p,
                       c_void_p], c_int32),
     "gsr_preprocess_bwd_store": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d),
@@ -187,6 +190,9 @@ gsr_blend_bwd = _wrap("gsr_blend_bwd")
 gsr_preprocess_bwd = _wrap("gsr_preprocess_bwd")
 gsr_preprocess_bwd_store = _wrap("gsr_preprocess_bwd_store")
 gsr_pose_bwd = _wrap("gsr_pose_bwd")
+gsr_spatial_order_workspace_size = _wrap("gsr_spatial_order_workspace_size")
+gsr_spatial_order = _wrap("gsr_spatial_order")
+gsr_permute = _wrap("gsr_permute")
 gsr_loss_workspace_size = _wrap("gsr_loss_workspace_size")
 gsr_loss_fwd_bwd = _wrap("gsr_loss_fwd_bwd")
 gsr_loss_fwd_bwd_static = _wrap("gsr_loss_fwd_bwd_static")

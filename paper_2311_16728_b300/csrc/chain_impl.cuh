@@ -48,18 +48,28 @@ __device__ __forceinline__ void load_sh(const float4 *__restrict__ sh, int64_t n
 constexpr int kBwdThreads = 128;
 constexpr int kBwdChunk = 1024;  // Gaussians per CTA
 
-// Indices k (0 .. kBwdChunk-1) of the visible Gaussians base + k of this
-// CTA's chunk into s_idx[0 .. *s_cnt - 1] (s_cnt zero on entry; a barrier
-// must follow).  Every visibility word is loaded before the first ballot, so
-// the chunk costs one memory round trip, not one per iteration.
-__device__ __forceinline__ void compact_visible(const uint32_t *__restrict__ ntiles, int64_t n, int64_t base,
-                                                uint32_t *s_idx, uint32_t *s_cnt) {
+// The CTA's chunk is kBwdChunk / kBwdThreads runs of kBwdThreads consecutive
+// Gaussians, run j starting at Gaussian (j * gridDim.x + blockIdx.x) *
+// kBwdThreads: every CTA samples the whole index range, so the visible
+// Gaussians spread over the CTAs even when the store is in a spatial order
+// (they are then contiguous, and whole chunks would be visible or not, with
+// the grid a single wave).  Slot k of the chunk is Gaussian chunk_index(k).
+__device__ __forceinline__ int64_t chunk_index(uint32_t k) {
+    return ((int64_t)(k / kBwdThreads) * gridDim.x + blockIdx.x) * kBwdThreads + (k % kBwdThreads);
+}
+
+// Slots k (0 .. kBwdChunk-1) of the visible Gaussians of this CTA's chunk
+// into s_idx[0 .. *s_cnt - 1] (s_cnt zero on entry; a barrier must follow).
+// Every visibility word is loaded before the first ballot, so the chunk costs
+// one memory round trip, not one per iteration.
+__device__ __forceinline__ void compact_visible(const uint32_t *__restrict__ ntiles, int64_t n, uint32_t *s_idx,
+                                                uint32_t *s_cnt) {
     constexpr int kIt = kBwdChunk / kBwdThreads;
     const int lane = threadIdx.x & 31;
     uint32_t nt[kIt];
 #pragma unroll
     for (int j = 0; j < kIt; ++j) {
-        const int64_t i = base + j * kBwdThreads + (int)threadIdx.x;
+        const int64_t i = chunk_index((uint32_t)(j * kBwdThreads) + threadIdx.x);
         nt[j] = i < n ? __ldg(ntiles + i) : 0u;
     }
 #pragma unroll

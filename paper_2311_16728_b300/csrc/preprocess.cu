@@ -70,12 +70,11 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, C
     __shared__ uint32_t s_cnt;
     if (threadIdx.x == 0) s_cnt = 0u;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
-    compact_visible(ntiles, g.n, base, s_idx, &s_cnt);
+    compact_visible(ntiles, g.n, s_idx, &s_cnt);
     __syncthreads();
     const uint32_t cnt = s_cnt;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads)
-        chain_one_gaussian(g, cam, base + s_idx[k], g0, g1, g2, d_mo, d_q, d_ls, d_sh, dstat, dcount, kStore);
+        chain_one_gaussian(g, cam, chunk_index(s_idx[k]), g0, g1, g2, d_mo, d_q, d_ls, d_sh, dstat, dcount, kStore);
 }
 
 // Camera pose gradient: the chain of every visible Gaussian with its
@@ -92,9 +91,8 @@ __global__ void __launch_bounds__(kBwdThreads) pose_bwd_kernel(GaussK g, CamK ca
     __shared__ float s_pose[kBwdThreads / 32][kPoseGrad];
     if (threadIdx.x == 0) s_cnt = 0u;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kBwdChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    compact_visible(ntiles, g.n, base, s_idx, &s_cnt);
+    compact_visible(ntiles, g.n, s_idx, &s_cnt);
     __syncthreads();
     const uint32_t cnt = s_cnt;
     float pose[kPoseGrad];
@@ -102,7 +100,7 @@ __global__ void __launch_bounds__(kBwdThreads) pose_bwd_kernel(GaussK g, CamK ca
     for (int k = 0; k < kPoseGrad; ++k) pose[k] = 0.f;
     NullSink sink;
     for (uint32_t k = threadIdx.x; k < cnt; k += kBwdThreads) {
-        const int64_t i = base + s_idx[k];
+        const int64_t i = chunk_index(s_idx[k]);
         const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
         const float4 G0 = g0[i], G1 = g1[i], G2 = g2[i];
         float4 shp[kShPlanes];

@@ -69,6 +69,28 @@ class Gaussians:
                                    self.sh.data_ptr())
 
 
+def spatial_order(params: Gaussians, lo, hi) -> torch.Tensor:
+    """Permutation (n int32, device) that sorts the Gaussians by the Morton
+    code of their means in the box [lo, hi] (gsr_spatial_order)."""
+    n = params.n
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=params.mean_op.device)
+    sz = ctypes.c_size_t()
+    L.gsr_spatial_order_workspace_size(n, ctypes.byref(sz))
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=params.mean_op.device)
+    gs = params.gaussians_struct()
+    lo3, hi3 = (ctypes.c_float * 3)(*[float(v) for v in lo]), (ctypes.c_float * 3)(*[float(v) for v in hi])
+    L.gsr_spatial_order(ctypes.byref(gs), lo3, hi3, _p(perm), _p(ws), ws.numel(), _stream(None))
+    return perm[:n]
+
+
+def permuted(x: Gaussians, perm: torch.Tensor) -> Gaussians:
+    """A new store with entry i = x's entry perm[i] (gsr_permute)."""
+    out = x.zeros_like()
+    src, dst = x.buffers_struct(), out.buffers_struct()
+    L.gsr_permute(ctypes.byref(src), ctypes.byref(dst), _p(perm), x.n, _stream(None))
+    return out
+
+
 def camera_struct(R, t, fx, fy, cx, cy, width, height) -> L.gsr_camera:
     c = L.gsr_camera()
     c.R[:] = [float(v) for v in np.asarray(R, np.float64).reshape(9)]

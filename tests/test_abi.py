@@ -74,6 +74,16 @@ def test_bad_arguments_are_rejected_on_the_host(gsr):
     rc = L.gsr_pose_bwd.raw(ctypes.byref(g), ctypes.byref(proj), ctypes.byref(cam), ctypes.byref(good_tiling),
                             ctypes.byref(L.gsr_grad2d(16, 24, 16)), 16, None)
     assert rc == L.GSR_ERR_INVALID_ARG and b"aligned" in L.gsr_last_error()
+    # spatial order: empty box axis, short workspace; permute: unaligned plane
+    lo3, hi3 = (ctypes.c_float * 3)(0, 0, 0), (ctypes.c_float * 3)(1, 0, 1)
+    rc = L.gsr_spatial_order.raw(ctypes.byref(g), lo3, hi3, 16, 16, 1 << 20, None)
+    assert rc == L.GSR_ERR_INVALID_ARG and b"hi > lo" in L.gsr_last_error()
+    hi3 = (ctypes.c_float * 3)(1, 1, 1)
+    rc = L.gsr_spatial_order.raw(ctypes.byref(g), lo3, hi3, 16, 16, 8, None)
+    assert rc == L.GSR_ERR_CAPACITY
+    pb, pb_bad = L.gsr_param_buffers(16, 16, 16, 16), L.gsr_param_buffers(16, 20, 16, 16)
+    rc = L.gsr_permute.raw(ctypes.byref(pb), ctypes.byref(pb_bad), 16, 10, None)
+    assert rc == L.GSR_ERR_INVALID_ARG and b"aligned" in L.gsr_last_error()
     # unaligned parameter plane
     g_bad = L.gsr_gaussians(18, 16, 16, 16, 10, 3)
     rc = L.gsr_preprocess.raw(ctypes.byref(g_bad), ctypes.byref(cam), ctypes.byref(good_tiling), ctypes.byref(proj),
