@@ -250,7 +250,7 @@ __device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
 // kQuad: the views' tiles are 16 x 16 (quadrant warps; box tests from staged
 // lane masks), one instance per tiling so the blend loops carry no branch
 template <bool kQuad>
-__global__ void __launch_bounds__(kIterThreads) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
+__global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
     extern __shared__ float4 smem4[];
     float *smf = reinterpret_cast<float *>(smem4);
     __shared__ int s_item, s_ok, s_item2[2];

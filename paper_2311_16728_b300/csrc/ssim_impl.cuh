@@ -48,13 +48,33 @@ __device__ __forceinline__ float block_sum(float v, float *s_red) {
     return r;  // valid in thread 0
 }
 
-// Stages a (kRH x kRW) region of plane `src` around the tile (zero outside).
+// Stages a (kRH x kRW) region of plane `src` around the tile (zero outside):
+// a thread's loads are issued in batches of up to 7 before the batch's
+// shared-memory stores (one memory round trip per batch: one for 256
+// threads, two for 128); a region inside the image skips the bounds tests.
 template <int NT>
 __device__ __forceinline__ void stage_region(const float *__restrict__ src, int H, int W, int ox, int oy, float *dst) {
-    for (int idx = threadIdx.x; idx < kRH * kRW; idx += NT) {
-        const int r = idx / kRW, q = idx % kRW;
-        const int gy = oy - kLR + r, gx = ox - kLR + q;
-        dst[r * kRS + q] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? src[(int64_t)gy * W + gx] : 0.f;
+    constexpr int kN = kRH * kRW, kPer = (kN + NT - 1) / NT, kBatch = 7;
+    const int gx0 = ox - kLR, gy0 = oy - kLR;
+    const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + kRW <= W && gy0 + kRH <= H;
+#pragma unroll
+    for (int j0 = 0; j0 < kPer; j0 += kBatch) {
+        float v[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = (int)threadIdx.x + (j0 + j) * NT;
+            const int r = idx / kRW, q = idx - r * kRW;
+            const int gy = gy0 + r, gx = gx0 + q;
+            v[j] = (j0 + j < kPer && idx < kN && (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)))
+                       ? src[(int64_t)gy * W + gx]
+                       : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = (int)threadIdx.x + (j0 + j) * NT;
+            const int r = idx / kRW, q = idx - r * kRW;
+            if (j0 + j < kPer && idx < kN) dst[r * kRS + q] = v[j];
+        }
     }
 }
 
@@ -81,23 +101,28 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
     __syncthreads();
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
         const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
-        float a[kRun + 10], b[kRun + 10];
+        // values and their products once per staged column, then five
+        // fused multiply-adds per tap
+        float a[kRun + 10], b[kRun + 10], aa[kRun + 10], bb[kRun + 10], ab[kRun + 10];
 #pragma unroll
         for (int k = 0; k < kRun + 10; ++k) {
             a[k] = sX[r * kRS + j0 + k];
             b[k] = sY[r * kRS + j0 + k];
+            aa[k] = a[k] * a[k];
+            bb[k] = b[k] * b[k];
+            ab[k] = a[k] * b[k];
         }
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
             float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
 #pragma unroll
             for (int k = 0; k < 11; ++k) {
-                const float w = win.w[k], av = a[o + k], bv = b[o + k];
-                mx += w * av;
-                my += w * bv;
-                xx += w * av * av;
-                yy += w * bv * bv;
-                xy += w * av * bv;
+                const float w = win.w[k];
+                mx = __fmaf_rn(w, a[o + k], mx);
+                my = __fmaf_rn(w, b[o + k], my);
+                xx = __fmaf_rn(w, aa[o + k], xx);
+                yy = __fmaf_rn(w, bb[o + k], yy);
+                xy = __fmaf_rn(w, ab[o + k], xy);
             }
             float *h = sH + r * kLTW + j0 + o;
             h[0] = mx;
@@ -137,8 +162,9 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
                 const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
                 const float iB = 1.0f / (B1 * B2);
                 const float S = A1 * A2 * iB;
-                const float dS_dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-                const float dS_dsxx = -S / B2;
+                // 1 / B1 = B2 iB and 1 / B2 = B1 iB: one division per pixel
+                const float dS_dmx = 2.f * my * A2 * iB - S * 2.f * mx * (B2 * iB);
+                const float dS_dsxx = -S * (B1 * iB);
                 const float dS_dsxy = 2.f * A1 * iB;
                 const int64_t idx = cb + (int64_t)gy * W + gx;
                 mapA[idx] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
