@@ -27,8 +27,11 @@
 namespace gsr {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;  // Gaussians per thread in the scan / compaction / emit kernels
-constexpr int kScanTile = kScanThreads * kScanItems;
+// records per thread in the count / compaction kernels: 8, or 32 when that
+// keeps the block count (whose prefix every compaction block sums) at most
+// kScanBlocksMax -- the batched window has views x n records
+constexpr int kScanItems = 8, kScanItemsBig = 32;
+constexpr int64_t kScanBlocksMax = 512;
 
 constexpr int kRadix = 256;  // digits of one pass of the long-segment radix sort
 
@@ -122,9 +125,12 @@ __device__ __forceinline__ int64_t block_prefix(const uint32_t *block_sums, int6
 }
 
 // ---------------------------------------------------------------- visible records and candidates
-// Pass 1: per block of kScanTile records, the number of visible records and
-// of their box tiles (the candidates).  It also zeroes the per-tile counters
-// (the range words) and the kept-pair counter for the passes that follow.
+// Pass 1: per block of kScanThreads x I records, the number of visible
+// records and of their box tiles (the candidates).  Warp w of block b takes
+// the 32 I records from (8 b + w) 32 I on, lane l record 32 j + l of them
+// (coalesced loads).  It also zeroes the per-tile counters (the range words)
+// and the kept-pair counter for the passes that follow.
+template <int I>
 __global__ void __launch_bounds__(kScanThreads) count_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
                                                              uint32_t *__restrict__ vis_sums,
                                                              uint32_t *__restrict__ cand_sums,
@@ -135,15 +141,16 @@ __global__ void __launch_bounds__(kScanThreads) count_kernel(const uint32_t *__r
          w += (int64_t)gridDim.x * kScanThreads)
         ranges[w] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_kept = 0ull;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t wbase = ((int64_t)blockIdx.x * (kScanThreads / 32) + wid) * (32 * I);
     uint32_t v = 0, c = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) {
-            const uint32_t t = ntiles[base + k];
-            v += t > 0u ? 1u : 0u;
-            c += t;
-        }
+    for (int j = 0; j < I; ++j) {
+        const int64_t e = wbase + 32 * j + lane;
+        const uint32_t t = e < n ? ntiles[e] : 0u;
+        v += t > 0u ? 1u : 0u;
+        c += t;
+    }
     v = block_incl_scan_256(v, s_warp);
     c = block_incl_scan_256(c, s_warp);
     if (threadIdx.x == kScanThreads - 1) {
@@ -167,7 +174,8 @@ struct Gather {
 // *d_ncand, and the gathered records when gt.cxy is set.  Candidate numbers
 // are 32-bit: a frame with 2^32 or more candidates sets GSR_ERR_UNSUPPORTED
 // and expands nothing.
-__global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
+template <int I>
+__global__ void __launch_bounds__(kScanThreads, 4) compact_kernel(const uint32_t *__restrict__ ntiles, int64_t n,
                                                                const uint32_t *__restrict__ vis_sums,
                                                                const uint32_t *__restrict__ cand_sums,
                                                                int64_t nblocks, uint32_t *__restrict__ order,
@@ -187,32 +195,50 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t *_
         coff[vis_total] = (uint32_t)cand_total;
         if (too_many) raise_status(d_status, GSR_ERR_UNSUPPORTED);
     }
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t t[kScanItems];
+    // the records of count_kernel's warp layout, in index order within the warp
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t wbase = ((int64_t)blockIdx.x * (kScanThreads / 32) + wid) * (32 * I);
+    uint32_t t[I];
     uint32_t v = 0, c = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        t[k] = base + k < n ? ntiles[base + k] : 0u;
-        v += t[k] > 0u ? 1u : 0u;
-        c += t[k];
+    for (int j = 0; j < I; ++j) {
+        const int64_t e = wbase + 32 * j + lane;
+        t[j] = e < n ? ntiles[e] : 0u;
+        v += t[j] > 0u ? 1u : 0u;
+        c += t[j];
     }
-    const uint32_t vi = block_incl_scan_256(v, s_warp);
-    const uint32_t ci = block_incl_scan_256(c, s_warp);
-    int64_t pos = vis_pre + (int64_t)(vi - v), off = cand_pre + (int64_t)(ci - c);
+    // warps' exclusive offsets within the block (lane 0 carries the warp's totals)
+    const uint32_t wv = __reduce_add_sync(0xffffffffu, v), wc = __reduce_add_sync(0xffffffffu, c);
+    const uint32_t vi = block_incl_scan_256(lane == 0 ? wv : 0u, s_warp);
+    const uint32_t ci = block_incl_scan_256(lane == 0 ? wc : 0u, s_warp);
+    int64_t pos = vis_pre + (int64_t)(__shfl_sync(0xffffffffu, vi, 0) - wv);
+    int64_t off = cand_pre + (int64_t)(__shfl_sync(0xffffffffu, ci, 0) - wc);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (t[k] > 0u) {
-            order[pos] = (uint32_t)(base + k);
-            coff[pos] = (uint32_t)off;
-            if (gt.cxy) {
-                gt.cxy[pos] = __ldg(gt.xy + base + k);
-                gt.ccb[pos] = __ldg(gt.cb + base + k);
-                gt.crd[pos] = __ldg(gt.rd + base + k);
-                gt.rec_to_c[base + k] = (uint32_t)pos;
-            }
-            ++pos;
-            off += t[k];
+    for (int j = 0; j < I; ++j) {
+        const uint32_t tj = t[j];
+        const bool vis = tj > 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        uint32_t inc = tj;  // inclusive warp scan of the candidate counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
         }
+        if (vis) {
+            const int64_t p = pos + __popc(m & lt), e = wbase + 32 * j + lane;
+            order[p] = (uint32_t)e;
+            coff[p] = (uint32_t)(off + (int64_t)(inc - tj));
+            if (gt.cxy) {
+                gt.cxy[p] = __ldg(gt.xy + e);
+                gt.ccb[p] = __ldg(gt.cb + e);
+                gt.crd[p] = __ldg(gt.rd + e);
+                gt.rec_to_c[e] = (uint32_t)p;
+            }
+        }
+        pos += __popc(m);
+        off += __shfl_sync(0xffffffffu, inc, 31);
+    }
 }
 
 // largest i in [0, n) with a[i] <= x (a ascending, a[0] <= x), by one warp
@@ -837,12 +863,16 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct SortLayout {
     size_t order, block_sums, cand_sums, coff, counters, kept_ts, kept_sk, seg, list, list2, total;
     int64_t scan_blocks;
+    int scan_items;
 };
 
 static SortLayout sort_layout(int64_t n, int64_t cap) {
     SortLayout L;
     const int64_t n1 = n > 0 ? n : 1, c1 = cap > 0 ? cap : 1;
-    L.scan_blocks = (n1 + kScanTile - 1) / kScanTile;
+    const int64_t small_tile = (int64_t)kScanThreads * kScanItems, big_tile = (int64_t)kScanThreads * kScanItemsBig;
+    L.scan_items = (n1 + small_tile - 1) / small_tile > kScanBlocksMax ? kScanItemsBig : kScanItems;
+    const int64_t tile = L.scan_items == kScanItems ? small_tile : big_tile;
+    L.scan_blocks = (n1 + tile - 1) / tile;
     size_t off = 0;
     L.order = off; off += align256(sizeof(uint32_t) * (size_t)n1);
     L.block_sums = off; off += align256(sizeof(uint32_t) * (size_t)L.scan_blocks);
@@ -929,15 +959,17 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     const unsigned sb = (unsigned)L.scan_blocks;
     // 1-2. visible records in index order and their candidate offsets (the
     // first pass also zeroes the tile counters and the kept-pair counter)
-    count_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, tile_ranges, 2 * tiles, d_kept);
+    auto count = L.scan_items == kScanItems ? count_kernel<kScanItems> : count_kernel<kScanItemsBig>;
+    count<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, tile_ranges, 2 * tiles, d_kept);
     Gather gt{};
     if (compact)
         gt = Gather{reinterpret_cast<const float4 *>(proj->xy_conic), reinterpret_cast<const float4 *>(proj->c_op_box),
                     reinterpret_cast<const float4 *>(proj->rgb_depth), reinterpret_cast<float4 *>(compact->xy_conic),
                     reinterpret_cast<float4 *>(compact->c_op_box), reinterpret_cast<float4 *>(compact->rgb_depth),
                     compact->ntiles};
-    compact_kernel<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, L.scan_blocks, order, coff,
-                                                d_nvis, d_ncand, d_status, gt);
+    auto compact_k = L.scan_items == kScanItems ? compact_kernel<kScanItems> : compact_kernel<kScanItemsBig>;
+    compact_k<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, L.scan_blocks, order, coff, d_nvis,
+                                           d_ncand, d_status, gt);
     // 3. cull + unordered kept list + tile counts (in the range words)
     expand_kernel<<<kExpandGrid, kExpandThreads, 0, st>>>(coff, order, xy, cb, rd, d_nvis, n, d_ncand,
                                                           tiling->tile_w, tiling->tile_h, vt, (uint32_t)tiles,
