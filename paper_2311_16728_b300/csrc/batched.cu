@@ -347,7 +347,7 @@ struct ChainGroups {
     float scale[kMaxViews][kGroupMax];  // relative to the group's first view (1, 1/2, 1/4, ...)
 };
 
-__global__ void __launch_bounds__(kBwdThreads) batched_chain_kernel(GaussK g, const __grid_constant__ ViewsK V,
+__global__ void __launch_bounds__(kBwdThreads, 4) batched_chain_kernel(GaussK g, const __grid_constant__ ViewsK V,
                                                                     const __grid_constant__ ChainGroups CG,
                                                                     const float4 *__restrict__ xy_conic,
                                                                     const float4 *__restrict__ c_op_box,

@@ -94,3 +94,28 @@ def grad_check(g: np.ndarray, ref: np.ndarray, cond: np.ndarray, rtol=GRAD_RTOL,
     base = np.maximum(rtol * np.abs(ref), atol)
     bound = base + tau * cond
     return err <= bound, int(((err > base) & (err <= bound)).sum()), float((err / bound).max())
+
+
+def morton_codes(mean, lo, hi):
+    """30-bit Morton codes of the means as the store-order kernel forms them:
+    each coordinate quantised to 10 bits (FP32 (v - lo) * (1024 / (hi - lo)),
+    clamped to [0, 1023], truncated), the bits interleaved x, y, z from bit 0
+    up."""
+    lo32, hi32 = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
+    q = []
+    for k in range(3):
+        s = np.float32(1024.0) / (hi32[k] - lo32[k])
+        t = (mean[:, k].astype(np.float32) - lo32[k]) * s
+        q.append(np.clip(t, 0.0, 1023.0).astype(np.uint32))
+    code = np.zeros(mean.shape[0], np.uint64)
+    for b in range(10):
+        for k in range(3):
+            code |= ((q[k].astype(np.uint64) >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + k)
+    return code
+
+
+def morton_permuted(p: S.Params, lo, hi) -> S.Params:
+    """The parameter set in the store order the benchmark uses (stable sort
+    by Morton code of the means), computed on the host."""
+    perm = np.lexsort((np.arange(p.n), morton_codes(p.mean_op[:, :3], lo, hi)))
+    return S.Params(p.mean_op[perm], p.quat[perm], p.logscale[perm], p.sh[:, perm])

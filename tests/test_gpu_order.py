@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from parity_helpers import to_gpu
+from parity_helpers import morton_codes, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -17,23 +17,6 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_2311_16728_b300 as gsr  # noqa: E402
-
-
-def _morton_ref(mean, lo, hi):
-    """30-bit Morton codes: each coordinate quantised to 10 bits as the
-    kernel does (FP32 (v - lo) * (1024 / (hi - lo)), clamped, truncated),
-    the bits interleaved x, y, z from bit 0 up."""
-    lo32, hi32 = np.float32(lo), np.float32(hi)
-    q = []
-    for k in range(3):
-        s = np.float32(1024.0) / (hi32[k] - lo32[k])
-        t = (mean[:, k].astype(np.float32) - lo32[k]) * s
-        q.append(np.clip(t, 0.0, 1023.0).astype(np.uint32))
-    code = np.zeros(mean.shape[0], np.uint64)
-    for b in range(10):
-        for k in range(3):
-            code |= ((q[k].astype(np.uint64) >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + k)
-    return code
 
 
 @pytest.mark.parametrize("n", [1, 1000, 70001])
@@ -45,7 +28,7 @@ def test_spatial_order_is_the_stable_morton_sort(n):
     g = to_gpu(p)
     perm = gsr.spatial_order(g, S.ROOM_LO, S.ROOM_HI).cpu().numpy().astype(np.int64)
     assert np.array_equal(np.sort(perm), np.arange(n))
-    code = _morton_ref(p.mean_op[:, :3], np.array(S.ROOM_LO), np.array(S.ROOM_HI))
+    code = morton_codes(p.mean_op[:, :3], S.ROOM_LO, S.ROOM_HI)
     ref = np.lexsort((np.arange(n), code))  # by code, then index
     assert np.array_equal(perm, ref)
 

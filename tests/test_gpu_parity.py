@@ -17,7 +17,7 @@ import pytest
 import oracle
 import synthetic as S
 from parity_helpers import (GRAD_TAU, IMG_ATOL, MARGIN_FLAG, gpu_view, grad_check, grad_planes_gpu, grad_report,
-                            oracle_scene, param_condition, to_gpu, unpack_box)
+                            morton_permuted, oracle_scene, param_condition, to_gpu, unpack_box)
 
 pytestmark = pytest.mark.gpu
 
@@ -364,10 +364,15 @@ def test_empty_and_degenerate_inputs():
     assert np.abs(vb.img.cpu().numpy() - img).max() <= IMG_ATOL
 
 
-def test_full_size_keys_and_sampled_rows():
-    """300k Gaussians, 1200 x 680, in the launch configuration the benchmark times:
-    keys bit-exact over the whole frame; image and gradients on sampled rows."""
+@pytest.mark.parametrize("order", ["morton", "input"])
+def test_full_size_keys_and_sampled_rows(order):
+    """300k Gaussians, 1200 x 680, in the launch configuration the benchmark times
+    (store in Morton order of the means, as the benchmark keeps it, or in the
+    generator's order): keys bit-exact over the whole frame; image and
+    gradients on sampled rows."""
     p = S.perturb(S.room_scene(300_000))
+    if order == "morton":
+        p = morton_permuted(p, S.ROOM_LO, S.ROOM_HI)
     cam = S.replica_camera(0)
     vb, g = gpu_view(p, cam)
     rows = [(0, 2), (339, 341), (678, 680)]
