@@ -10,7 +10,7 @@
 
 namespace gsr {
 
-__global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussK g, CamK cam, float4 *__restrict__ xy_conic,
+__global__ void __launch_bounds__(256, 3) preprocess_fwd_kernel(GaussK g, CamK cam, float4 *__restrict__ xy_conic,
                                                              float4 *__restrict__ c_op_box,
                                                              float4 *__restrict__ rgb_depth,
                                                              uint32_t *__restrict__ ntiles) {
