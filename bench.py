@@ -1143,10 +1143,10 @@ def main():
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
 # with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
 # loss stage is its two SSIM passes, the binning stage its seven kernels).
-NCU_TRAFFIC = {"preprocess": 15.451904e6, "bin_sort": 21.091328e6, "render_fwd": 4.220928e6, "loss": None,
-               "blend_bwd": 20.802304e6, "preprocess_bwd": 12.433920e6, "adam": 393.221632e6}
+NCU_TRAFFIC = {"preprocess": 15.452416e6, "bin_sort": 21.101056e6, "render_fwd": 4.218880e6, "loss": 69.143808e6,
+               "blend_bwd": 20.784896e6, "preprocess_bwd": 12.432128e6, "adam": 393.195520e6}
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
-NCU_TRAFFIC_WINDOW_ITERATE = None
+NCU_TRAFFIC_WINDOW_ITERATE = 604.977152e6
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20
