@@ -394,7 +394,8 @@ def run_window(args):
             "roofline": {"kernel": "batched_iterate_kernel (fwd + bwd blends)", "bound": "alu",
                          "achieved": flops / it_s / 1e12, "peak": fp32, "unit": "TFLOP/s",
                          "frac": flops / it_s / 1e12 / fp32,
-                         "traffic": NCU_TRAFFIC_WINDOW_ITERATE if tile == (16, 16) else None, "alg_per_launch": flops,
+                         "traffic": NCU_TRAFFIC_WINDOW_ITERATE if (tile == (16, 16) and args.order == "morton") else None,
+                         "alg_per_launch": flops,
                          "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"},
             "stages_ms": stage_ms, "iterate_phases_ms": phases,
             "one_view_kernels_ms": single, "per_level": per_level, "work": {"blends": blends, "views": bw.V},
@@ -1099,7 +1100,10 @@ def main():
 
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    stages = stage_rooflines(stage_ms, work, peaks, clk)
+    # the captured DRAM traffic is the room scene's in the Morton-ordered
+    # store; other scenes and orders report none
+    traffic = NCU_TRAFFIC if (args.scene == "room" and args.order == "morton") else {}
+    stages = stage_rooflines(stage_ms, work, peaks, clk, traffic)
     dom = max(stage_ms, key=stage_ms.get)
     roof = dict(stages[dom])
 
@@ -1153,7 +1157,7 @@ FLOPS_PER_BLEND_FWD = 20
 FLOPS_PER_BLEND_BWD = 60
 
 
-def stage_rooflines(stage_ms, work, peaks, clk):
+def stage_rooflines(stage_ms, work, peaks, clk, traffic):
     """Roofline entry of each stage's dominant kernel: algorithmic work per
     launch / measured stage time against the measured HBM copy bandwidth or
     the FP32 peak (148 SMs x 128 lanes x 2 flops x median SM clock)."""
@@ -1167,13 +1171,13 @@ def stage_rooflines(stage_ms, work, peaks, clk):
     def hbm_entry(kernel, alg):
         sec = stage_ms[st] * 1e-3
         return {"kernel": kernel, "bound": "hbm", "achieved": alg / sec / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": alg / sec / 1e9 / hbm, "traffic": NCU_TRAFFIC.get(st), "alg_per_launch": alg,
+                "frac": alg / sec / 1e9 / hbm, "traffic": traffic.get(st), "alg_per_launch": alg,
                 "peak_source": hbm_src}
 
     def alu_entry(kernel, flops):
         sec = stage_ms[st] * 1e-3
         return {"kernel": kernel, "bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32, "unit": "TFLOP/s",
-                "frac": flops / sec / 1e12 / fp32, "traffic": NCU_TRAFFIC.get(st), "alg_per_launch": flops,
+                "frac": flops / sec / 1e12 / fp32, "traffic": traffic.get(st), "alg_per_launch": flops,
                 "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"}
 
     out = {}
