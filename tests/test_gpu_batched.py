@@ -15,7 +15,8 @@ import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import grad_planes_gpu, grad_report, oracle_scene, to_gpu
+from parity_helpers import (IMG_ATOL, MARGIN_FLAG, grad_planes_gpu, grad_report, morton_permuted, oracle_scene,
+                            to_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -174,3 +175,59 @@ def test_window_graph_replay_matches_eager():
     print(f"eager {le}\ngraph {lg}")
     np.testing.assert_allclose(lg, le, rtol=1e-5)
     assert le[-1] < le[0], "window loss did not decrease"
+
+
+def test_window_full_size_keys_and_sampled_rows():
+    """The window as the benchmark runs it: 500k Gaussians in the Morton-ordered
+    store, 8 keyframes 640 x 480 x 3 levels, 16 x 16 tiles.  Keys, order and
+    ranges bit-exact against the oracle for all 24 views (values mapped back
+    from compact positions to Gaussian ids); images on sampled rows of one
+    view per level within the image bar."""
+    n = 500_000
+    p = morton_permuted(S.perturb(S.room_scene(n, seed=0), 0.05, seed=1), S.ROOM_LO, S.ROOM_HI)
+    cams = [S.tum_camera(k * 50 // 8) for k in range(8)]
+    gts = [torch.tensor(S.random_image(3, c.height, c.width, seed=30 + k), dtype=torch.float32, device="cuda")
+           for k, c in enumerate(cams)]
+    bw = BatchedWindow(to_gpu(p), list(zip(cams, gts)), levels=3)
+    assert bw.V == 24
+    _run_once(bw)
+    npairs = int(bw.num_pairs.item())
+    gk = bw.keys[:npairs].cpu().numpy().view(np.uint64)
+    gv = bw.vals[:npairs].cpu().numpy().view(np.uint32)
+    grg = bw.ranges.cpu().numpy().view(np.uint32).reshape(-1)
+    nt = bw.ntiles.cpu().numpy().view(np.uint32)
+    r2c = bw.rec_to_c.cpu().numpy().view(np.uint32)
+    vis_rec = np.nonzero(nt > 0)[0]
+    c2rec = np.zeros(len(vis_rec), np.int64)
+    c2rec[r2c[vis_rec]] = vis_rec
+    sc = oracle_scene(p)
+    toff, pos, sampled = 0, 0, set()
+    for v, (_, _, lvl, k) in enumerate(bw.views):
+        cl = S.camera_at_level(cams[k], lvl)
+        ca = cl.as_array()
+        dec = oracle.decide(p.mean_op, p.quat, p.logscale, ca, cl.width, cl.height)
+        ks, vs, rr = oracle.keys(dec, cl.width, cl.height)
+        T = len(rr) // 2
+        m = len(ks)
+        assert np.array_equal(gk[pos:pos + m], ks + (np.uint64(toff) << np.uint64(32))), f"view {v}: keys differ"
+        rec = c2rec[gv[pos:pos + m]]
+        assert np.array_equal(rec // n, np.full(m, v)), f"view {v}: records of another view"
+        assert np.array_equal((rec % n).astype(np.uint32), vs), f"view {v}: sorted Gaussian order differs"
+        wr = grg[2 * toff:2 * (toff + T)].astype(np.int64)
+        empty = rr[0::2] == rr[1::2]
+        assert np.array_equal(wr[0::2] == wr[1::2], empty), f"view {v}: empty tiles differ"
+        assert np.array_equal((wr[0::2] - pos)[~empty], rr[0::2][~empty].astype(np.int64))
+        assert np.array_equal((wr[1::2] - pos)[~empty], rr[1::2][~empty].astype(np.int64))
+        if lvl not in sampled and k == 3 * lvl:  # one view per level, from different keyframes
+            sampled.add(lvl)
+            gi = bw.imgs[v].cpu().numpy()
+            H = cl.height
+            for r in [(0, 2), (H // 2 - 1, H // 2 + 1), (H - 2, H)]:
+                img, _, _, mg = oracle.render(sc, ca, cl.width, H, dec, rows=r)
+                fl = mg[r[0]:r[1]] < MARGIN_FLAG
+                err = np.abs(gi[:, r[0]:r[1]] - img[:, r[0]:r[1]]).max(0)
+                assert err[~fl].max() <= IMG_ATOL, (v, r, err.max())
+        toff += T
+        pos += m
+    assert pos == npairs and toff == bw.tiles and sampled == {0, 1, 2}
+    print(f"window full size: {bw.V} views, {npairs} pairs, {len(vis_rec)} visible records")
