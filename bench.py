@@ -82,6 +82,24 @@ def _ordered(gsr, params, args):
     return gsr.permuted(params, gsr.spatial_order(params, S.ROOM_LO, S.ROOM_HI))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's value of a per-rank time (replicas: the job ends
+    when the last replica does); x itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ms_per_step: float, world: int) -> float:
+    """Whole-job iterations/s of `world` replicas that each ran one iteration
+    per ms_per_step (the max over ranks)."""
+    return world * 1000.0 / ms_per_step
+
+
 # ---------------------------------------------------------------- CPU oracle sample
 def oracle_sample(start, target_imgs_rows, cams, pose: int, rows: int, row0: int):
     """Time the oracle over one iteration restricted to `rows` image rows and
@@ -1030,12 +1048,9 @@ def main():
     pairs = int(ms.vb.num_pairs.item())
     if status != 0:
         raise RuntimeError(f"device status {status} during the timed region (pair capacity {ms.vb.pair_capacity})")
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, "cuda")
     ms_per_step = ms_total / args.steps
-    value = world * 1000.0 / ms_per_step
+    value = job_rate(ms_per_step, world)
 
     # ---- end to end: target image from pinned host memory in, loss out, every
     # step.  Each step's target is copied on a second stream one step ahead,
@@ -1072,10 +1087,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, "cuda")
 
     # ---- kernels launched per iteration (kernel nodes of one view's graph)
     try:
@@ -1115,7 +1127,7 @@ def main():
                                **({"workload": WORKLOAD_WALLS} if args.scene == "walls" else {})}),
             "roofline": roof, "stages_ms": stage_ms, "stage_rooflines": stages, "work": work,
             "gpu_launches": launches, "clocks": clk,
-            "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "iters/s",
+            "e2e": {"value": job_rate(e2e_ms, world), "unit": "iters/s",
                     "h2d_bytes_per_step": 3 * WIDTH * HEIGHT * 4, "d2h_bytes_per_step": 4}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
