@@ -67,7 +67,11 @@ static int32_t launch_gemm_bn(const void *A, int64_t lda, const void *B, int64_t
 // short reduction (K <= 256 without split, or bn64) takes BN = 64: there the
 // epilogue is most of the work and four times as many CTAs share it.
 int32_t gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int M, int N, int K,
-                  const umma::Epilogue &ep, int ksplit, int32_t *d_status, cudaStream_t st, bool bn64 = false) {
+                  const umma::Epilogue &ep_in, int ksplit, int32_t *d_status, cudaStream_t st, bool bn64 = false) {
+    umma::Epilogue ep = ep_in;
+    ep.vec_mask = ep.mask && aligned16(ep.mask) && ep.ldm % 8 == 0;
+    ep.vec_out = ep.out_bf16 && aligned16(ep.out_bf16) && ep.ldo % 8 == 0;
+    ep.vec_t = ep.out_bf16_t && aligned16(ep.out_bf16_t) && ep.ldt % 8 == 0;
     if (M <= 0 || N <= 0 || K <= 0 || M % umma::BM || N % 64 || K % umma::BK || ksplit < 1 || !aligned16(A) ||
         !aligned16(B) || lda % 8 || ldb % 8) {
         set_error("gemm_bf16: need M %% 128 == 0, N %% 64 == 0, K %% 64 == 0, 16-byte aligned operands "
@@ -78,11 +82,18 @@ int32_t gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int M,
     // a reduction of at most 4 k-steps per CTA needs only a 2-stage ring (4 CTAs per SM)
     if (ksplit == 1 && K <= 256) return launch_gemm_bn<64, 2>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     if (bn64) return launch_gemm_bn<64>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
+    // split-K over an N that 128 does not divide: 128 x 64 tiles on a 3-stage
+    // ring, three CTAs per SM, so the split's CTAs run in one wave
+    if (ksplit > 1 && N % 128 != 0) return launch_gemm_bn<64, 3>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     // fewer 128 x 256 tiles than two per SM leave a ragged second wave (157
-    // tiles on 148 SMs take two tile times): 128 x 128 tiles on a 3-stage
-    // ring run two CTAs per SM instead
-    if (N % 256 == 0 && (int64_t)(N / 256) * (M / umma::BM) * ksplit < 2 * 148)
-        return launch_gemm_bn<128, 3>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
+    // tiles on 148 SMs take two tile times): 128 x 128 tiles instead, on a
+    // 3-stage ring (two CTAs per SM) when they fit in one wave of those, else
+    // on a 2-stage ring (three CTAs per SM)
+    const int64_t t256 = (int64_t)(N / 256) * (M / umma::BM) * ksplit;
+    if (N % 256 == 0 && t256 < 2 * 148) {
+        if (2 * t256 <= 2 * 148) return launch_gemm_bn<128, 3>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
+        return launch_gemm_bn<128, 2>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
+    }
     if (N % 256 == 0) return launch_gemm_bn<256>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     if (N % 128 == 0) return launch_gemm_bn<128>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);
     return launch_gemm_bn<64>(A, lda, B, ldb, M, N, K, ep, ksplit, d_status, st);

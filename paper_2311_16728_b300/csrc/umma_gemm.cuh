@@ -147,7 +147,14 @@ struct Epilogue {
     int atomic_f32;
     float *colsum;                // [N]        colsum[n] += sum over valid rows of v (after mask / relu)
     int64_t valid_rows;           //            rows >= valid_rows are padding: not summed
+    int vec_mask, vec_out;        // set by the launcher: mask / out_bf16 rows are 16-byte aligned, so a
+                                  // lane moves its 16 columns as two 16-byte words
+    int vec_t;                    // set by the launcher: out_bf16_t columns are 16-byte aligned, so the
+                                  // warp transposes its 32 x 16 block through shared memory
 };
+
+// row stride (BF16 elements) of a warp's transposed 16 x 32 staging block
+constexpr int kTStride = 40;
 
 // ST: stages of the shared-memory ring (default 4 for BN = 256, else 6); a
 // short reduction takes 2, so that several CTAs fit on an SM.
@@ -163,7 +170,7 @@ struct Config {
 
 // grid: (N / BN, M / BM, ksplit); K tiles of this CTA: the z-th slice.
 template <int BN, int ST = (BN == 256 ? 4 : 6)>
-__global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(192, 4) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, int K, Epilogue ep,
                                                       int32_t *d_status) {
     using Cfg = Config<BN, ST>;
@@ -255,25 +262,63 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CU
                 }
                 if (ep.mask) {
                     const __nv_bfloat16 *mr = ep.mask + (int64_t)m * ep.ldm + nb;
+                    if (ep.vec_mask) {
+                        uint4 w[2];
+                        w[0] = *reinterpret_cast<const uint4 *>(mr);
+                        w[1] = *reinterpret_cast<const uint4 *>(mr + 8);
+                        const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(w);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (!(__bfloat162float(mr[j]) > 0.0f)) v[j] = 0.0f;
+                        for (int j = 0; j < 16; ++j)
+                            if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (!(__bfloat162float(mr[j]) > 0.0f)) v[j] = 0.0f;
+                    }
                 }
                 if (ep.out_bf16) {
                     __nv_bfloat16 *o = ep.out_bf16 + (int64_t)m * ep.ldo + nb;
+                    if (ep.vec_out) {
+                        uint4 w[2];
+                        __nv_bfloat162 *wb = reinterpret_cast<__nv_bfloat162 *>(w);
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) *reinterpret_cast<__nv_bfloat162 *>(o + j) =
-                        __floats2bfloat162_rn(v[j], v[j + 1]);
+                        for (int j = 0; j < 16; j += 2) wb[j / 2] = __floats2bfloat162_rn(v[j], v[j + 1]);
+                        *reinterpret_cast<uint4 *>(o) = w[0];
+                        *reinterpret_cast<uint4 *>(o + 8) = w[1];
+                    } else {  // any row stride: one element at a time
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16_rn(v[j]);
+                    }
                 }
                 if (ep.out_bf16_t) {
+                    if (ep.vec_t) {
+                        // the ring's shared memory is free once every MMA has completed:
+                        // column j of the warp's block goes to staging row j, then each
+                        // lane stores 8 consecutive rows of one column as one 16-byte word
+                        __nv_bfloat16 *stg = reinterpret_cast<__nv_bfloat16 *>(smem) + q * 16 * kTStride;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) ep.out_bf16_t[(int64_t)(nb + j) * ep.ldt + m] = __float2bfloat16_rn(v[j]);
+                        for (int j = 0; j < 16; ++j) stg[j * kTStride + lane] = __float2bfloat16_rn(v[j]);
+                        __syncwarp();
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int c = 8 * i + (lane >> 2), r8 = 8 * (lane & 3);
+                            const uint4 w = *reinterpret_cast<const uint4 *>(stg + c * kTStride + r8);
+                            *reinterpret_cast<uint4 *>(ep.out_bf16_t + (int64_t)(nb + c) * ep.ldt + (m0 + 32 * q + r8)) = w;
+                        }
+                        __syncwarp();
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            ep.out_bf16_t[(int64_t)(nb + j) * ep.ldt + m] = __float2bfloat16_rn(v[j]);
+                    }
                 }
                 if (ep.out_f32) {
                     float *o = ep.out_f32 + (int64_t)m * ep.ldf + nb;
                     if (ep.atomic_f32) {
+                        // vector reductions (16-byte aligned: ldf % 4 == 0, nb % 16 == 0)
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) atomicAdd(o + j, v[j]);
+                        for (int j = 0; j < 16; j += 4)
+                            atomicAdd(reinterpret_cast<float4 *>(o + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
                     } else {
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(o + j) =

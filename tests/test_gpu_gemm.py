@@ -23,19 +23,25 @@ def _p(t):
 
 
 def _gemm(A, B, *, bias=None, relu=0, mask=None, out="f32", transposed=False, colsum=None, valid=None, ksplit=1,
-          atomic=0):
+          atomic=0, pad=0):
+    """pad: extra elements per row of the mask, the BF16 outputs and the
+    transposed output (pad % 8 != 0 takes the epilogue's unvectorised paths)."""
     M, K = A.shape
     N = B.shape[0]
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     of = torch.zeros(M, N, device="cuda") if out == "f32" else None
-    ob = torch.zeros(M, N, dtype=torch.bfloat16, device="cuda") if out == "bf16" else None
-    ot = torch.zeros(N, M, dtype=torch.bfloat16, device="cuda") if transposed else None
-    L.gsr_gemm_bf16(_p(A), K, _p(B), K, M, N, K, _p(bias), relu, _p(mask), N, _p(ob), N, _p(ot), M, _p(of), N,
-                    atomic, _p(colsum), M if valid is None else valid, ksplit, _p(status), st)
+    ob = torch.zeros(M, N + pad, dtype=torch.bfloat16, device="cuda") if out == "bf16" else None
+    ot = torch.zeros(N, M + pad, dtype=torch.bfloat16, device="cuda") if transposed else None
+    mk = None
+    if mask is not None:
+        mk = torch.zeros(M, N + pad, dtype=torch.bfloat16, device="cuda")
+        mk[:, :N] = mask
+    L.gsr_gemm_bf16(_p(A), K, _p(B), K, M, N, K, _p(bias), relu, _p(mk), N + pad, _p(ob), N + pad, _p(ot), M + pad,
+                    _p(of), N, atomic, _p(colsum), M if valid is None else valid, ksplit, _p(status), st)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
-    return of, ob, ot
+    return of, None if ob is None else ob[:, :N], None if ot is None else ot[:, :M]
 
 
 def _operands(M, N, K, seed):
@@ -59,12 +65,13 @@ def test_gemm_fp32_output(M, N, K):
     assert (err <= bound).all(), f"max err/bound {(err / bound).max():.3f}"
 
 
-def test_gemm_epilogue_bias_relu_bf16_transposed_colsum():
+@pytest.mark.parametrize("pad", [0, 3])
+def test_gemm_epilogue_bias_relu_bf16_transposed_colsum(pad):
     M, N, K = 256, 128, 192
     At, Bt, a64, b64 = _operands(M, N, K, seed=9)
     bias = torch.tensor(np.random.default_rng(10).standard_normal(N).astype(np.float32), device="cuda")
     colsum = torch.zeros(N, device="cuda")
-    _, ob, ot = _gemm(At, Bt, bias=bias, relu=1, out="bf16", transposed=True, colsum=colsum, valid=200)
+    _, ob, ot = _gemm(At, Bt, bias=bias, relu=1, out="bf16", transposed=True, colsum=colsum, valid=200, pad=pad)
     ref = np.maximum(a64 @ b64.T + bias.cpu().numpy().astype(np.float64), 0)
     bound = K * 2.0 ** -24 * (np.abs(a64) @ np.abs(b64).T) + np.abs(bias.cpu().numpy())[None] * 2 ** -24
     got = ob.float().cpu().numpy()
@@ -76,11 +83,12 @@ def test_gemm_epilogue_bias_relu_bf16_transposed_colsum():
     np.testing.assert_allclose(colsum.cpu().numpy(), ref[:200].sum(0), rtol=1e-5, atol=1e-3)
 
 
-def test_gemm_relu_mask_and_split_k():
+@pytest.mark.parametrize("pad", [0, 3])
+def test_gemm_relu_mask_and_split_k(pad):
     M, N, K = 128, 64, 1024
     At, Bt, a64, b64 = _operands(M, N, K, seed=5)
     mask = torch.randn(M, N, device="cuda").to(torch.bfloat16)
-    of, _, _ = _gemm(At, Bt, mask=mask)
+    of, _, _ = _gemm(At, Bt, mask=mask, pad=pad)
     ref = (a64 @ b64.T) * (mask.float().cpu().numpy() > 0)
     bound = K * 2.0 ** -24 * (np.abs(a64) @ np.abs(b64).T) + 1e-30
     assert (np.abs(of.cpu().numpy() - ref) <= bound).all()
