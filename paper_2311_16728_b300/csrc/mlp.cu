@@ -201,29 +201,53 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(const __nv_bfloat16
 // ---------------------------------------------------------------- loss (MSE)
 // dy = 2 w (y - t) / M on the first 56 columns of valid rows (BF16, both
 // layouts), gb3 += sum_m dy (FP32), loss += sum w (y - t)^2 / M.
+constexpr int kLossRows = 64;    // rows of one tile
+constexpr int kLossTStride = 72; // row stride (BF16) of the transposed tile in shared memory
+
 __global__ void __launch_bounds__(256) mlp_loss_kernel(const float *__restrict__ y, const float *__restrict__ t,
                                                        const float *__restrict__ w, int64_t M, int64_t Mpad,
                                                        __nv_bfloat16 *__restrict__ dy, __nv_bfloat16 *__restrict__ dyT,
                                                        float *__restrict__ gb3, float *__restrict__ d_loss) {
-    // thread: column j = tid % 64 of rows 4 k + tid / 64, grid-striding over
-    // the rows; the column sums and the loss stay in registers until one
-    // reduction and one atomic per column (and one for the loss) per block
+    // tiles of 64 rows, grid-striding: thread = column j = tid % 64 of rows
+    // 4 k + tid / 64 (row-major loads and dy stores coalesced); the tile's
+    // gradient goes transposed through shared memory so that dyT is written
+    // as 16-byte words along the rows.  Column sums and the loss stay in
+    // registers until one reduction and one atomic per column (and one for
+    // the loss) per block.
+    __shared__ __align__(16) __nv_bfloat16 s_t[kN3 * kLossTStride];
+    __shared__ float s_g[256], s_l[256];
     const int j = (int)(threadIdx.x & 63), r0 = (int)(threadIdx.x >> 6);
     float lsum = 0.0f, gsum = 0.0f;
-    const float wj = j < kOut ? w[j] : 0.0f;
-    for (int64_t m = 4 * (int64_t)blockIdx.x + r0; m < Mpad; m += 4 * (int64_t)gridDim.x) {
-        const int64_t e = m * kN3 + j;
-        float g = 0.0f;
-        if (m < M && j < kOut) {
-            const float d = y[e] - t[e];
-            lsum += wj * d * d / (float)M;
-            g = 2.0f * wj * d / (float)M;
+    const float wj = j < kOut ? w[j] : 0.0f, inv_m = 1.0f / (float)M;
+    constexpr int kPer = kLossRows / 4;
+    for (int64_t m0 = (int64_t)kLossRows * blockIdx.x; m0 < Mpad; m0 += (int64_t)kLossRows * gridDim.x) {
+        float d[kPer];  // every load of the tile in flight before the first use
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int64_t m = m0 + r0 + 4 * i, e = m * kN3 + j;
+            d[i] = (m < M && j < kOut) ? y[e] - t[e] : 0.0f;
         }
-        gsum += g;
-        dy[e] = __float2bfloat16_rn(g);
-        dyT[(int64_t)j * Mpad + m] = __float2bfloat16_rn(g);
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int rr = r0 + 4 * i;
+            const int64_t e = (m0 + rr) * kN3 + j;
+            lsum += wj * d[i] * d[i] * inv_m;
+            const float g = 2.0f * wj * d[i] * inv_m;
+            gsum += g;
+            const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+            dy[e] = gb;
+            s_t[j * kLossTStride + rr] = gb;
+        }
+        __syncthreads();
+        {  // column c = tid / 4, rows 16 (tid % 4) .. + 15 of the tile: two 16-byte words
+            const int c = (int)(threadIdx.x >> 2), q = 16 * (int)(threadIdx.x & 3);
+            const uint4 *src = reinterpret_cast<const uint4 *>(s_t + c * kLossTStride + q);
+            uint4 *dst = reinterpret_cast<uint4 *>(dyT + (int64_t)c * Mpad + m0 + q);
+            dst[0] = src[0];
+            dst[1] = src[1];
+        }
+        __syncthreads();
     }
-    __shared__ float s_g[256], s_l[256];
     s_g[threadIdx.x] = gsum;
     s_l[threadIdx.x] = lsum;
     __syncthreads();
@@ -561,7 +585,7 @@ extern "C" int32_t gsr_mlp_train_step(const gsr_mlp_weights *w, const gsr_mlp_we
         cudaMemsetAsync(d_loss, 0, sizeof(float), st) != cudaSuccess)
         return check_launch("mlp memset");
     if ((rc = mlp_forward_ws(w, x, Mpad, y, ws, L, true, d_status, st))) return rc;
-    const int64_t loss_blocks = Mpad / 4 < 2 * 148 ? Mpad / 4 : 2 * 148;
+    const int64_t loss_blocks = Mpad / kLossRows < 2 * 148 ? Mpad / kLossRows : 2 * 148;
     mlp_loss_kernel<<<(unsigned)loss_blocks, 256, 0, st>>>(y, target, out_weight, M, Mpad, bf(L.dy), bf(L.dyt),
                                                            f32(L.gb3), d_loss);
     if ((rc = check_launch("mlp loss"))) return rc;
