@@ -884,7 +884,7 @@ def run_pose(args):
                                    "and pose chain in one CUDA graph (fixed pose)",
                        "visible": nv, "pairs": vb.pairs_needed(), "map_order": args.order},
             "roofline": {"kernel": "pose_bwd_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "alg_bytes": alg,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": NCU_TRAFFIC_POSE if args.order == "morton" else None, "alg_bytes": alg,
                          "ms": ms_chain, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "refinement": {"steps": n_ref, "steps_per_s": n_ref / (w1 - w0), "rot_err_deg": [e0[0], e1[0]],
                            "trans_err_m": [e0[1], e1[1]], "loss": [losses[0], losses[-1]],
@@ -1162,6 +1162,8 @@ def main():
 NCU_TRAFFIC = {"preprocess": 15.452416e6, "bin_sort": 21.101056e6, "render_fwd": 4.218880e6, "loss": 69.143808e6,
                "blend_bwd": 20.784896e6, "preprocess_bwd": 12.432128e6, "adam": 393.195520e6}
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
+# the pose chain (profiles/pose_bwd_300k_1200x680.md)
+NCU_TRAFFIC_POSE = 15.037952e6
 NCU_TRAFFIC_WINDOW_ITERATE = 604.977152e6
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
