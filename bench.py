@@ -1159,12 +1159,12 @@ def main():
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
 # with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
 # loss stage is its two SSIM passes, the binning stage its seven kernels).
-NCU_TRAFFIC = {"preprocess": 15.452416e6, "bin_sort": 21.101056e6, "render_fwd": 4.218880e6, "loss": 69.143808e6,
-               "blend_bwd": 20.784896e6, "preprocess_bwd": 12.432128e6, "adam": 393.195520e6}
-# the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
+NCU_TRAFFIC = {"preprocess": 15.454464e6, "bin_sort": 21.094912e6, "render_fwd": 4.217856e6, "loss": 69.083904e6,
+               "blend_bwd": 20.793600e6, "preprocess_bwd": 12.432640e6, "adam": 393.139456e6}
 # the pose chain (profiles/pose_bwd_300k_1200x680.md)
 NCU_TRAFFIC_POSE = 15.037952e6
-NCU_TRAFFIC_WINDOW_ITERATE = 604.977152e6
+# the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
+NCU_TRAFFIC_WINDOW_ITERATE = 604.692224e6
 
 # FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
 FLOPS_PER_BLEND_FWD = 20

@@ -78,6 +78,34 @@ __device__ __forceinline__ uint2 quad_box_lanes(int x0, int x1, int y0, int y1, 
 // tiles, quadrant warps): s_lanes[w] also receives, for every warp w that
 // can see it, the lanes whose pixels lie in its pixel box, so the blend
 // loops test one bit instead of the box.
+// Whether some pixel of the rectangle [rx0, rx1] x [ry0, ry1] (pixel
+// indices) can reach alpha >= 1/255, i.e. d^T Q d <= tau: a lower bound on
+// the continuous minimum of the quadratic form over the rectangle (0 when it
+// holds the mean, else the least of its four edges, each at its clamped 1D
+// vertex, less a bound on the rounding of the terms) against tau with a
+// margin far above the FP32 error of this test and of the per-pixel alpha.
+// Only warps that cannot see the splat are dropped; the per-pixel test
+// decides every blend, so the image does not depend on this test.
+__device__ __forceinline__ bool rect_may_see(float u, float v, float A, float B, float C, float tau, float rx0,
+                                             float rx1, float ry0, float ry1) {
+    if (u >= rx0 && u <= rx1 && v >= ry0 && v <= ry1) return true;
+    float lb = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float dx, dy;
+        if (e < 2) {  // vertical edges: dy at the edge's vertex, clamped to the rectangle
+            dx = (e ? rx1 : rx0) - u;
+            dy = fminf(fmaxf(-__fdividef(B * dx, C), ry0 - v), ry1 - v);
+        } else {      // horizontal edges
+            dy = (e == 3 ? ry1 : ry0) - v;
+            dx = fminf(fmaxf(-__fdividef(B * dy, A), rx0 - u), rx1 - u);
+        }
+        const float t1 = A * dx * dx, t2 = 2.0f * B * dx * dy, t3 = C * dy * dy;
+        lb = fminf(lb, (t1 + t2 + t3) - 1e-5f * (fabsf(t1) + fabsf(t2) + fabsf(t3)));
+    }
+    return lb <= tau * 1.001f + 1e-3f;
+}
+
 template <bool kQuad>
 __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, int ox, int oy, int nwarps,
                                             float4 &s_xy, float4 &s_cb, float4 &s_rgb, uint32_t &s_mask,
@@ -104,7 +132,9 @@ __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, i
             const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
             const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
             const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
-            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey) {
+            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey &&
+                rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1), (float)max(ry0, y0),
+                             (float)min(ry1, y1))) {
                 mask |= 1u << w;
                 if constexpr (kQuad) s_lanes[w] = quad_box_lanes(x0, x1, y0, y1, rx0, ry0);
             }

@@ -47,7 +47,11 @@ __device__ __forceinline__ uint4 q4_box_lanes(int x0, int x1, int y0, int y1, in
 
 // Stages Gaussian gid as stage_splat does, for the two 16 x 8 warps: the
 // mask of warps that can see it and, for those, the lanes of each pixel slot
-// inside its pixel box.
+// inside its pixel box.  kExact adds the rectangle test of rect_may_see to
+// the ellipse's bounding box (the persistent window kernel, whose register
+// budget other phases set; in the one-view kernel the extra registers cost
+// more than the dropped warps save).
+template <bool kExact>
 __device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int ox, int oy, float4 &s_xy,
                                          float4 &s_cb, float4 &s_rgb, uint32_t &s_mask, uint4 *s_lanes) {
     const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
@@ -70,7 +74,9 @@ __device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int 
             const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
             const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
             const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
-            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey) {
+            if (boxes && fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey &&
+                (!kExact || rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1),
+                                         (float)max(ry0, y0), (float)min(ry1, y1)))) {
                 mask |= 1u << w;
                 s_lanes[w] = q4_box_lanes(x0, x1, y0, y1, ox, ry0);
             }
@@ -154,7 +160,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
         if (idx < bend) {
             const uint32_t gid = a.vals[idx];
             s_gid[ti] = gid;
-            q4_stage(a, gid, ox, oy, s_xy[ti], s_cb[ti], s_rgb[ti], s_mask[ti], s_lanes + 2 * ti);
+            q4_stage<kHalf>(a, gid, ox, oy, s_xy[ti], s_cb[ti], s_rgb[ti], s_mask[ti], s_lanes + 2 * ti);
         } else {
             s_mask[ti] = 0u;
         }
