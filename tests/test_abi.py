@@ -168,3 +168,19 @@ def test_default_init_sizes_and_arguments(gsr):
     # slots beyond the map
     rc = L.gsr_default_init.raw(16, 100, 80, 16, 10, ctypes.byref(cam), ctypes.byref(buf), 5, 0, 16, 1 << 20, None)
     assert rc == L.GSR_ERR_INVALID_ARG
+
+
+def test_build_script_loads_without_the_package():
+    """build() compiles before anything imports the package (whose import
+    fails loudly without the library): its build script loads by path alone."""
+    import subprocess
+    import sys
+    code = ("import importlib.util, os, sys; root = os.getcwd(); "
+            "spec = importlib.util.spec_from_file_location('gsr_build', "
+            "os.path.join(root, 'paper_2311_16728_b300', '_build.py')); "
+            "mod = importlib.util.module_from_spec(spec); spec.loader.exec_module(mod); "
+            "assert callable(mod.build) and mod.sources(); "
+            "assert 'paper_2311_16728_b300' not in sys.modules")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
