@@ -544,6 +544,29 @@ int32_t gsr_adam_step_touched(const gsr_param_buffers *params, const gsr_param_b
                               const gsr_adam_config *cfg, const uint32_t *touched, int32_t *d_step,
                               gsr_stream_t stream);
 
+/* ---------------------------------------------------------------- autotuner */
+
+/* Actions of the autotuner's callback. */
+enum { GSR_AUTOTUNE_SETUP = 0, GSR_AUTOTUNE_STEP = 1, GSR_AUTOTUNE_RELEASE = 2 };
+
+/* Callback of gsr_autotune: for candidate `candidate`, SETUP builds its
+ * state (and may check that it renders what the others render), STEP
+ * enqueues one step of it on the stream given to gsr_autotune, RELEASE frees
+ * its state.  Returns GSR_OK, or an error code that stops the tuning. */
+typedef int32_t (*gsr_autotune_fn)(int32_t candidate, int32_t action, void *ctx);
+
+/* Timing driver of the tiling autotuner (the tile shape, which fixes the
+ * staging batch and the threads per tile, is a pure performance choice: the
+ * image does not depend on it).  For each of ncand candidates in order:
+ * SETUP, `warmup` STEPs, a synchronisation, then `steps` STEPs each
+ * bracketed by CUDA events on `stream`, then RELEASE.  ms[c] (host, ncand
+ * floats) = the median step time of candidate c in milliseconds; *best (host)
+ * = the fastest candidate.  A callback error or a CUDA error stops the run
+ * (after the failing candidate's RELEASE when its SETUP succeeded), is
+ * returned, and leaves *best = -1. */
+int32_t gsr_autotune(int32_t ncand, gsr_autotune_fn fn, void *ctx, int32_t warmup, int32_t steps,
+                     gsr_stream_t stream, float *ms, int32_t *best);
+
 /* ---------------------------------------------------------------- map order */
 
 /* Bytes of scratch for gsr_spatial_order over n Gaussians. */

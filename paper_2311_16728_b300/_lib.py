@@ -66,6 +66,9 @@ class gsr_adam_config(ctypes.Structure):
 
 
 P = POINTER
+# gsr_autotune_fn: (candidate, action, ctx) -> status
+AUTOTUNE_FN = ctypes.CFUNCTYPE(c_int32, c_int32, c_int32, c_void_p)
+GSR_AUTOTUNE_SETUP, GSR_AUTOTUNE_STEP, GSR_AUTOTUNE_RELEASE = 0, 1, 2
 _SIGNATURES = {
     "gsr_version": ([], c_char_p),
     "gsr_last_error": ([], c_char_p),
@@ -81,6 +84,7 @@ _SIGNATURES = {
                        c_void_p, c_void_p, P(gsr_grad2d), c_void_p], c_int32),
     "gsr_preprocess_bwd": ([P(gsr_gaussians), P(gsr_proj), P(gsr_camera), P(gsr_tiling), P(gsr_grad2d),
                             P(gsr_param_buffers), c_void_p, c_void_p, c_void_p], c_int32),
+    "gsr_autotune": ([c_int32, AUTOTUNE_FN, c_void_p, c_int32, c_int32, c_void_p, P(c_float), P(c_int32)], c_int32),
     "gsr_spatial_order_workspace_size": ([c_int64, P(c_size_t)], c_int32),
     "gsr_spatial_order": ([P(gsr_gaussians), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
     "gsr_permute": ([P(gsr_param_buffers), P(gsr_param_buffers), c_void_p, c_int64, c_void_p], c_int32),
@@ -190,6 +194,7 @@ gsr_blend_bwd = _wrap("gsr_blend_bwd")
 gsr_preprocess_bwd = _wrap("gsr_preprocess_bwd")
 gsr_preprocess_bwd_store = _wrap("gsr_preprocess_bwd_store")
 gsr_pose_bwd = _wrap("gsr_pose_bwd")
+gsr_autotune = _wrap("gsr_autotune")
 gsr_spatial_order_workspace_size = _wrap("gsr_spatial_order_workspace_size")
 gsr_spatial_order = _wrap("gsr_spatial_order")
 gsr_permute = _wrap("gsr_permute")

@@ -5,19 +5,23 @@ its own pixel box, and the tile cull never drops a pair that blends), so the
 tile shape -- which also fixes the staging batch (one record per thread per
 batch) and the threads per tile (one per two pixels) -- is a pure performance
 choice.  The tuner times a few captured iterations of each candidate on the
-caller's workload, checks that every candidate renders a bit-identical image,
-and caches the winner per (GPU, width, height, Gaussian-count bucket).
+caller's workload (the library's timing driver, gsr_autotune, calls back to
+set up, step and release each candidate and times the steps with CUDA
+events), checks that every candidate renders a bit-identical image, and
+caches the winner per (GPU, width, height, Gaussian-count bucket).
 """
 from __future__ import annotations
 
 import json
 import math
 import os
-import statistics
 from typing import Optional, Sequence, Tuple
+
+import ctypes
 
 import torch
 
+from . import _lib as L
 from .raster import Gaussians, MappingStep, ViewBuffers, camera_from, ensure_capacity, tiling_struct
 
 # (tile_w, tile_h): every shape the blend kernels accept with 64..512 threads
@@ -33,6 +37,32 @@ def _clone(g: Gaussians) -> Gaussians:
     return Gaussians(*(t.clone() for t in g.tensors()), g.sh_degree)
 
 
+def _tune(n: int, setup, step, release, warmup: int, steps: int):
+    """Times candidates 0 .. n-1 with the native driver (gsr_autotune) on the
+    current stream; setup / step / release(c) are called back for candidate
+    c.  Returns (median ms per candidate, index of the fastest)."""
+    errors = []
+
+    def callback(c, action, _ctx):
+        try:
+            (setup, step, release)[action](c)
+            return 0
+        except BaseException as e:  # re-raised below, after the driver returns
+            errors.append(e)
+            return L.GSR_ERR_INVALID_ARG
+
+    fn = L.AUTOTUNE_FN(callback)
+    ms = (ctypes.c_float * n)()
+    best = ctypes.c_int32(-1)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.gsr_autotune.raw(n, fn, None, warmup, steps, stream, ms, ctypes.byref(best))
+    if errors:
+        raise errors[0]
+    if rc != 0:
+        raise RuntimeError(f"gsr_autotune: {L.gsr_last_error().decode()}")
+    return [float(v) for v in ms], int(best.value)
+
+
 def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int, int]] = CANDIDATES,
              steps: int = 10, warmup: int = 3, cache_path: Optional[str] = None, verbose: bool = False):
     """Returns ((tile_w, tile_h), report).  `views` = [(camera, gt image)] as for
@@ -45,40 +75,36 @@ def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int,
             cache = json.load(f)
         if key in cache:
             return tuple(cache[key]["tile"]), cache[key]
-    ref_img = None
     report = {"key": key, "ms_per_step": {}, "identical_image": {}}
-    for tw, th in candidates:
+    state = {"ref": None, "ms": None}
+
+    def setup(c):
+        tw, th = candidates[c]
         tiling = tiling_struct(tw, th)
         # image check on the first view, untouched parameters
         vb = ViewBuffers(params.n, cam0, tiling, 1024)
         ensure_capacity(vb, params)
         vb.forward(params)
         img = vb.img.clone()
-        if ref_img is None:
-            ref_img = img
-        same = bool(torch.equal(img, ref_img))
+        if state["ref"] is None:
+            state["ref"] = img
+        same = bool(torch.equal(img, state["ref"]))
         report["identical_image"][f"{tw}x{th}"] = same
         if not same:
             raise RuntimeError(f"tiling {tw}x{th} changed the rendered image")
         del vb
         # timing on a copy of the parameters
-        ms = MappingStep(_clone(params), views, tiling)
-        ms.capture()
-        for _ in range(warmup):
-            ms.step()
-        torch.cuda.synchronize()
-        times = []
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ms.step()
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        report["ms_per_step"][f"{tw}x{th}"] = statistics.median(times)
+        state["ms"] = MappingStep(_clone(params), views, tiling)
+        state["ms"].capture()
+
+    def release(c):
+        state["ms"] = None
+
+    times, _ = _tune(len(candidates), setup, lambda c: state["ms"].step(), release, warmup, steps)
+    for (tw, th), t in zip(candidates, times):
+        report["ms_per_step"][f"{tw}x{th}"] = t
         if verbose:
-            print(f"autotune {tw}x{th}: {report['ms_per_step'][f'{tw}x{th}']:.4f} ms/step")
-        del ms
+            print(f"autotune {tw}x{th}: {t:.4f} ms/step")
     best = min(report["ms_per_step"], key=report["ms_per_step"].get)
     tile = tuple(int(v) for v in best.split("x"))
     report["tile"] = list(tile)
@@ -109,41 +135,39 @@ def autotune_window(params: Gaussians, keyframes: Sequence, levels: int = 3,
             cache = json.load(f)
         if key in cache:
             return tuple(cache[key]["tile"]), cache[key]
-    ref = None
     report = {"key": key, "ms_per_step": {}, "identical_image": {}}
-    for tw, th in candidates:
+    state = {"ref": None, "bw": None}
+
+    def setup(c):
+        tw, th = candidates[c]
         bw = BatchedWindow(_clone(params), keyframes, levels=levels, tiling=tiling_struct(tw, th))
         bw.preprocess()
         bw.bin_sort()
         bw.iterate()
         torch.cuda.synchronize()
         imgs = [t.clone() for t in bw.imgs]
-        if ref is None:
-            ref = imgs
-        same = all(torch.equal(a, b) for a, b in zip(imgs, ref))
+        if state["ref"] is None:
+            state["ref"] = imgs
+        same = all(torch.equal(a, b) for a, b in zip(imgs, state["ref"]))
         report["identical_image"][f"{tw}x{th}"] = same
         if not same:
             raise RuntimeError(f"tiling {tw}x{th} changed a rendered view")
         # the eager pass above left screen-space gradients behind: clear them
         bw.g2.zero_()
         bw.capture()
-        for _ in range(warmup):
-            bw.step()
-        torch.cuda.synchronize()
-        times = []
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            bw.step()
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        if bw.status.item() != 0:
+        state["bw"] = bw
+
+    def release(c):
+        bw, state["bw"] = state["bw"], None
+        if bw is not None and bw.status.item() != 0:
+            tw, th = candidates[c]
             raise RuntimeError(f"tiling {tw}x{th}: device status {bw.status.item():#x}")
-        report["ms_per_step"][f"{tw}x{th}"] = statistics.median(times)
+
+    times, _ = _tune(len(candidates), setup, lambda c: state["bw"].step(), release, warmup, steps)
+    for (tw, th), t in zip(candidates, times):
+        report["ms_per_step"][f"{tw}x{th}"] = t
         if verbose:
-            print(f"autotune window {tw}x{th}: {report['ms_per_step'][f'{tw}x{th}']:.4f} ms/step")
-        del bw
+            print(f"autotune window {tw}x{th}: {t:.4f} ms/step")
     best = min(report["ms_per_step"], key=report["ms_per_step"].get)
     tile = tuple(int(v) for v in best.split("x"))
     report["tile"] = list(tile)

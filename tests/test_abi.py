@@ -184,3 +184,15 @@ def test_build_script_loads_without_the_package():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_autotune_driver_rejects_bad_arguments(gsr):
+    """Checked before any CUDA call: no candidates, no callback, no steps."""
+    L = gsr._lib
+    fn = L.AUTOTUNE_FN(lambda c, a, ctx: 0)
+    ms = (ctypes.c_float * 2)()
+    best = ctypes.c_int32(7)
+    assert L.gsr_autotune.raw(0, fn, None, 1, 1, None, ms, ctypes.byref(best)) == L.GSR_ERR_INVALID_ARG
+    assert L.gsr_autotune.raw(2, L.AUTOTUNE_FN(), None, 1, 1, None, ms, ctypes.byref(best)) == L.GSR_ERR_INVALID_ARG
+    assert L.gsr_autotune.raw(2, fn, None, 1, 0, None, ms, ctypes.byref(best)) == L.GSR_ERR_INVALID_ARG
+    assert b"gsr_autotune" in L.gsr_last_error()
