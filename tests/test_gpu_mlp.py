@@ -75,7 +75,9 @@ def _load(li, x):
     li.xT.copy_(li.x.t())
 
 
-@pytest.mark.parametrize("M", [100, 300])
+# 100 / 300 rows: short tiles; 20,000: the benchmark's batch, whose 2368-deep
+# first layer runs 128 x 128 tiles on the 2-stage ring
+@pytest.mark.parametrize("M", [100, 300, 20000])
 def test_forward_matches_oracle(M):
     p, x, t = _batch(M)
     li = LearnedInit(p, M)
@@ -93,8 +95,11 @@ def test_forward_matches_oracle(M):
     assert np.linalg.norm(err) / np.linalg.norm(fw["y"]) < 1e-3
 
 
-def test_training_gradients_match_oracle():
-    M = 200
+# 200 rows: short tiles; 2,048 and 20,000: the benchmark's batches (20,000
+# runs the 2-stage 128 x 128 forward tiles and the 3-stage split-K weight
+# gradient of the first layer)
+@pytest.mark.parametrize("M", [200, 2048, 20000])
+def test_training_gradients_match_oracle(M):
     p, x, t = _batch(M, seed=7)
     li = LearnedInit(p, M, lr=1e-4)
     _load(li, x)

@@ -412,6 +412,28 @@ def test_full_size_keys_and_sampled_rows(order):
     assert ok.all(), f"{(~ok).sum()} gradient elements out of tolerance"
 
 
+def test_large_scene_keys_and_sampled_rows():
+    """The densify workload's frame: 1M Gaussians in the Morton-ordered store,
+    1920 x 1080, fx = fy = 1000: keys, order and ranges bit-exact over the
+    whole frame; the image on sampled rows within the image bar."""
+    p = morton_permuted(S.perturb(S.room_scene(1_000_000, seed=0), 0.05, seed=1), S.ROOM_LO, S.ROOM_HI)
+    pos, yaw = S.trajectory(0)
+    cam = S.pose_camera(pos, yaw, 1000.0, 1000.0, 1920, 1080)
+    vb, g = gpu_view(p, cam)
+    ca = cam.as_array()
+    dec = oracle.decide(p.mean_op, p.quat, p.logscale, ca, cam.width, cam.height)
+    ks, vs, rg = oracle.keys(dec, cam.width, cam.height)
+    _check_keys(vb, dec, (ks, vs, rg))
+    sc = oracle_scene(p)
+    gi = vb.img.cpu().numpy()
+    for r in [(0, 2), (539, 541), (1078, 1080)]:
+        img, _, _, mg = oracle.render(sc, ca, cam.width, cam.height, dec, rows=r)
+        fl = mg[r[0]:r[1]] < MARGIN_FLAG
+        err = np.abs(gi[:, r[0]:r[1]] - img[:, r[0]:r[1]]).max(0)
+        assert err[~fl].max() <= IMG_ATOL, r
+    print(f"large scene: {len(ks)} pairs, {int((dec.visible > 0).sum())} visible")
+
+
 def test_graph_replay_matches_eager():
     """The captured per-stage graphs do what the eager calls do: bit-identical
     render, gradients equal up to float-atomic ordering, and the same loss
