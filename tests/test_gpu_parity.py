@@ -135,7 +135,9 @@ def test_image_independent_of_tiling():
             assert np.array_equal(im, ref), f"tiling {tile} changes the image"
 
 
-@pytest.mark.parametrize("H,W", [(120, 160), (37, 53), (11, 300)])
+# ragged small frames, and the mapping (1200 x 680) and densify (1920 x 1080)
+# workloads' frames
+@pytest.mark.parametrize("H,W", [(120, 160), (37, 53), (11, 300), (680, 1200), (1080, 1920)])
 def test_loss_matches_oracle(H, W):
     x = S.random_image(3, H, W, seed=1)
     y = S.random_image(3, H, W, seed=2)
@@ -492,7 +494,8 @@ def test_long_tile_segments_bit_exact(n):
     _check_keys(vb, dec, keys_ref)
 
 
-@pytest.mark.parametrize("H,W", [(120, 160), (37, 53)])
+# small frames and the stereo workload's 752 x 480 views
+@pytest.mark.parametrize("H,W", [(120, 160), (37, 53), (480, 752)])
 def test_luma_loss_matches_oracle(H, W):
     """Grayscale target: Eq. 4 on the luminance, gradient spread over RGB by
     the luminance weights."""
