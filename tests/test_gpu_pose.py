@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import MARGIN_FLAG, gpu_view, grad_check, oracle_scene, to_gpu
+from parity_helpers import MARGIN_FLAG, gpu_view, grad_check, morton_permuted, oracle_scene, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -99,6 +99,38 @@ def test_pose_gradient_end_to_end_matches_oracle():
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"pose end to end: normwise {rel:.2e}, worst err/bound {worst:.3f} ({used} use the allowance), "
           f"flagged pixels {(mg < MARGIN_FLAG).sum()}\n got {got}\n ref {ref}")
+    assert ok.all()
+    assert rel <= 1e-3
+
+
+def test_pose_gradient_full_size():
+    """The pose workload: 300k Gaussians in the Morton-ordered store, 1200 x
+    680, target rendered by the oracle from the true pose, camera 1 degree /
+    3 cm off; the 15 pose values against the oracle's within the gradient
+    bar and 1e-3 normwise."""
+    base = morton_permuted(S.room_scene(300_000, seed=0), S.ROOM_LO, S.ROOM_HI)
+    true_cam = S.replica_camera(0)
+    tca = true_cam.as_array()
+    sc = oracle_scene(base)
+    dec0 = oracle.decide(base.mean_op, base.quat, base.logscale, tca, true_cam.width, true_cam.height)
+    gt, _, _, _ = oracle.render(sc, tca, true_cam.width, true_cam.height, dec0)
+    R0 = gsr.so3_exp([0.01, -0.012, 0.006]) @ true_cam.R
+    t0 = true_cam.t + np.array([0.02, -0.015, 0.012])
+    cam = S.Camera(R0, t0, true_cam.fx, true_cam.fy, true_cam.cx, true_cam.cy, true_cam.width, true_cam.height)
+    ca = cam.as_array()
+    dec = oracle.decide(base.mean_op, base.quat, base.logscale, ca, cam.width, cam.height)
+    img, _, _, mg = oracle.render(sc, ca, cam.width, cam.height, dec)
+    _, dimg = oracle.loss(img, gt, 0.2)
+    dimg[:, mg < MARGIN_FLAG] = 0.0
+    _, g2ref, mag2d = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, dimg, with_magnitude=True)
+    ref = oracle.pose_grad(sc, ca, cam.width, cam.height, dec, g2ref)
+    cond = _pose_condition(sc, ca, cam.width, cam.height, dec, mag2d)
+    vb, g = gpu_view(base, cam)
+    vb.blend_bwd(dimg=torch.tensor(dimg, dtype=torch.float32, device="cuda"))
+    got = _gpu_pose(vb, g)
+    ok, used, worst = grad_check(got[None], ref[None], cond[None])
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"pose full size: normwise {rel:.2e}, worst err/bound {worst:.3f} ({used} use the allowance)")
     assert ok.all()
     assert rel <= 1e-3
 
