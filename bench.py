@@ -25,7 +25,10 @@ iterations (uneven Gaussian counts); --mode stereo maps 752 x 480 grayscale
 stereo pairs (0.11 m baseline, luminance loss); --mode gp_ablation compares
 the final PSNR of the plain path with 1 to 4 pyramid levels (Sec. 4.4,
 Tab. 4); --mode pose times the camera pose gradient pass and a photometric
-pose refinement.  The default (mapping) line is the headline.
+pose refinement.  The default (mapping) line is the headline; after its
+throughput figure it also carries the batched window's rate (`window`) and a
+bounded time-to-PSNR run (`ttp`: the learned initialiser trained on the GPU
+inside the run, two held-out scenes), the two halves of the headline metric.
 """
 from __future__ import annotations
 
@@ -138,88 +141,169 @@ def oracle_sample(start, target_imgs_rows, cams, pose: int, rows: int, row0: int
 
 
 def run_reference(args):
+    """The oracle on the host cores, every one of the K steps a bounded sample
+    of one mapping iteration: decide + Adam over all Gaussians, render, loss
+    and backward on a band of rows, the band's time scaled to the frame.
+    ms_per_step is the measured time of a sampled step (so K x ms_per_step is
+    the timed region); value is the full-frame rate that the samples
+    extrapolate to."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     import synthetic as S
     target, start, cams = _scene()
-    rows = args.ref_rows
-    # target band: the oracle renders the unperturbed set on the same rows
-    per_step = []
-    detail = None
+    # bands of consecutive rows that tile the frame over the K timed steps
+    # (image rows differ in cost, so the steps together sample every row)
+    rows = args.ref_rows if args.ref_rows > 0 else min(HEIGHT, max(8, -(-HEIGHT // args.steps)))
     tgt_cache = {}
-    # bounded: at most 3 timed steps after 1 warm-up (a full-frame oracle
-    # step takes seconds), each on a band of `rows` rows extrapolated to the
-    # frame; the mean of the timed steps is the per-step time
-    n_warm, n_timed = min(args.warmup, 1), max(1, min(args.steps, 3))
-    for k in range(n_warm + n_timed):
+    n_warm = min(args.warmup, 1)
+    full, measured = [], []
+    t_region = None
+    for k in range(n_warm + args.steps):
+        if k == n_warm:
+            t_region = time.perf_counter()
         pose = k % N_POSES
-        row0 = (97 * k) % (HEIGHT - rows)
+        row0 = min(((k - n_warm) % max(1, -(-HEIGHT // rows))) * rows, HEIGHT - rows)
         key = (pose, row0)
-        if key not in tgt_cache:
+        if key not in tgt_cache:  # the target band (untimed): the oracle's render of the unperturbed set
             cam = cams[pose]
             dt = oracle.decide(target.mean_op, target.quat, target.logscale, cam.as_array(), WIDTH, HEIGHT)
             st = oracle.Scene64(target.mean_op, target.quat, target.logscale, target.sh)
             im, _, _, _ = oracle.render(st, cam.as_array(), WIDTH, HEIGHT, dt, rows=(row0, row0 + rows))
             tgt_cache = {key: im[:, row0:row0 + rows].copy()}
-        full, detail = oracle_sample(start, tgt_cache[key], cams, pose, rows, row0)
+        f, det = oracle_sample(start, tgt_cache[key], cams, pose, rows, row0)
         if k >= n_warm:
-            per_step.append(full)
-    sec = statistics.mean(per_step)
+            full.append(f)
+            measured.append(det["measured_s"])
+    timed_s = time.perf_counter() - t_region
+    sec_full = statistics.mean(full)
     cores = oracle.num_threads()
-    sample = (f"oracle (FP64, OpenMP), {n_timed} timed step(s) after {n_warm} warm-up: decide+Adam over all "
-              f"{N_GAUSS} Gaussians, render+loss+backward on a {rows}-row band of the 1200x680 frame, extrapolated "
-              f"to the full frame")
-    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / sec, "unit": "iters/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(),
-            "cpu_baseline": {"value": 1.0 / sec, "unit": "iters/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": 1.0 / sec, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    sample = (f"oracle (FP64, OpenMP), {args.steps} timed steps after {n_warm} warm-up, each a sample of one "
+              f"iteration: decide + Adam over all {N_GAUSS} Gaussians, render + loss + backward on a {rows}-row band "
+              f"of the 1200x680 frame, the steps' bands tiling the frame ({statistics.mean(measured):.2f} s measured "
+              f"per step); value = the full-frame rate, each band's share scaled by {HEIGHT}/{rows} "
+              f"({sec_full:.2f} s per full iteration, mean over the steps)")
+    value = 1.0 / sec_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(measured) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(), "timed_steps": args.steps, "timed_s": timed_s, "extrapolated": True,
+            "full_frame_ms_per_step": sec_full * 1e3,
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- GPU arm
 class ClockSampler:
-    def __init__(self):
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.p = None
+    """SM clock, power and clock-event reasons of the benchmarked GPU, sampled
+    every few milliseconds by a background thread through NVML's read-only
+    queries (nvidia-smi's 100 ms loop as the fallback).  Started before the
+    warm-up and stopped after the last measured loop, so it also covers timed
+    regions far shorter than its period; `mark` records which samples fall
+    inside the headline's timed region."""
+
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
+
+    def __init__(self, device=None, period_s: float = 0.004):
+        import threading
+        self.device, self.period = device, period_s
+        self.samples = []  # (t, sm_mhz, max_mhz, power_w, reason bits)
+        self.marks = {}
+        self.stop_ev = threading.Event()
+        self.thread = None
+        self.smi = None
+        self.source = None
+
+    def _nvml_handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        if self.device is None:
+            self.device = torch.cuda.current_device()
+        uuid = str(torch.cuda.get_device_properties(self.device).uuid)
+        try:
+            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+        except pynvml.NVMLError:
+            props = torch.cuda.get_device_properties(self.device)
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
 
     def start(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
+        import threading
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms",
-                                       "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            nv, h = self._nvml_handle()
+        except Exception:
+            nv = None
+        if nv is None:
+            self._start_smi()
+            return
+        self.source = "NVML"
+
+        def run():
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons",
+                                  getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons", None))
+            while not self.stop_ev.is_set():
+                try:
+                    self.samples.append((time.perf_counter(), float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)),
+                                         float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)),
+                                         nv.nvmlDeviceGetPowerUsage(h) / 1000.0, int(get_reasons(h))))
+                except Exception:
+                    pass
+                self.stop_ev.wait(self.period)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+
+    def _start_smi(self):
+        self.source = "nvidia-smi -lms 100"
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active")
+        try:
+            self.smi = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms",
+                                         "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
-            self.p = None
+            self.smi = None
+
+    def mark(self, name: str):
+        self.marks[name] = time.perf_counter()
 
     def stop(self, gpu_index: int):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        self.p.wait()
-        self.f.flush()
-        self.f.seek(0)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join()
+        elif self.smi is not None:
+            self.smi.terminate()
+            self.smi.wait()
+            self.f.flush()
+            self.f.seek(0)
+            for line in self.f.read().splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 5 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+                    continue
+                try:
+                    self.samples.append((0.0, float(parts[1]), float(parts[2]), float(parts[3]), int(parts[4], 16)))
+                except ValueError:
+                    continue
+            os.unlink(self.f.name)
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
+        sm = [x[1] for x in self.samples]
+        bits = 0
+        for x in self.samples:
+            bits |= x[4]
+        t0, t1 = self.marks.get("timed_start"), self.marks.get("timed_end")
+        inside = [x[1] for x in self.samples if t0 is not None and t1 is not None and t0 <= x[0] <= t1]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(x[2] for x in self.samples) if self.samples else None,
+                "reasons": sorted(nm for nm, b in self.REASONS if bits & b),
+                "samples": len(sm), "source": self.source, "period_ms": self.period * 1e3,
+                "power_w_max": max(x[3] for x in self.samples) if self.samples else None,
+                "samples_in_timed_region": len(inside),
+                "sm_mhz_timed_region": statistics.median(inside) if inside else None,
+                "window": "warm-up, the timed steps, the stage-timing and e2e loops"}
 
 
 def count_kernel_nodes(graphs) -> int:
@@ -259,13 +343,15 @@ def _peaks():
     return json.load(open(path)) if os.path.exists(path) else {}
 
 
-def run_window(args):
+def _window_setup(args):
+    """The window workload (setup, untimed): targets rendered from the true
+    map, the perturbed map in the store order --order names, the tile shape
+    chosen by the autotuner (or --tile), the window captured as one graph."""
     import torch
     import synthetic as S
     import paper_2311_16728_b300 as gsr
     from paper_2311_16728_b300.autotune import autotune_window
     from paper_2311_16728_b300.batched import BatchedWindow
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     target = S.room_scene(WIN_N, seed=0)
     start = S.perturb(target, 0.05, seed=1)
     cams = [S.tum_camera(k * N_POSES // WIN_KF) for k in range(WIN_KF)]
@@ -286,6 +372,37 @@ def run_window(args):
         report = {"ms_per_step": {}}
     bw = BatchedWindow(params, kf, levels=WIN_LEVELS, tiling=gsr.tiling_struct(*tile))
     bw.capture()
+    return bw, tile, report, kf, params
+
+
+def window_figure(args, steps: int = 200):
+    """The window's throughput for the headline line: `steps` whole-iteration
+    graph replays timed by CUDA events after a warm-up."""
+    import torch
+    bw, tile, report, _, _ = _window_setup(args)
+    for _ in range(max(args.warmup, 3)):
+        bw.step()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(steps):
+        bw.step()
+    t1.record()
+    torch.cuda.synchronize()
+    if bw.status.item() != 0:
+        raise RuntimeError(f"window: device status {bw.status.item():#x}")
+    ms = t0.elapsed_time(t1) / steps
+    return {"workload": f"{WIN_N // 1000}k Gaussians, {WIN_KF} keyframes 640x480 x {WIN_LEVELS} levels = {bw.V} "
+                        "views, one persistent launch per iteration, whole iteration in one CUDA graph",
+            "iters_per_s": 1000.0 / ms, "views_per_s": bw.V * 1000.0 / ms, "ms_per_step": ms, "steps": steps,
+            "tile": f"{tile[0]}x{tile[1]}", "autotune": report.get("chosen", report.get("ms_per_step"))}
+
+
+def run_window(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2311_16728_b300 as gsr
+    bw, tile, report, kf, params = _window_setup(args)
     for _ in range(args.warmup):
         bw.step()
     torch.cuda.synchronize()
@@ -391,7 +508,7 @@ def run_window(args):
         pl["blend_bwd_ms"] += ev[2].elapsed_time(ev[3])
         del vbv
     peaks = _peaks()
-    mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    mhz, mhz_src = _fp32_clock(clk, peaks)
     fp32 = 148 * 128 * 2 * mhz * 1e6 / 1e12
     flops = (FLOPS_PER_BLEND_FWD + FLOPS_PER_BLEND_BWD) * blends
     it_s = stage_ms["iterate"] * 1e-3
@@ -414,7 +531,9 @@ def run_window(args):
                          "frac": flops / it_s / 1e12 / fp32,
                          "traffic": NCU_TRAFFIC_WINDOW_ITERATE if (tile == (16, 16) and args.order == "morton") else None,
                          "alg_per_launch": flops,
-                         "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"},
+                         "alg_rule": f"({FLOPS_PER_BLEND_FWD} + {FLOPS_PER_BLEND_BWD}) FP32 per (pixel, Gaussian) "
+                                     "evaluation x blends over all views",
+                         "peak_source": f"FP32 148 SMs x 128 lanes x 2 flops x {mhz:.0f} MHz, {mhz_src}"},
             "stages_ms": stage_ms, "iterate_phases_ms": phases,
             "one_view_kernels_ms": single, "per_level": per_level, "work": {"blends": blends, "views": bw.V},
             "gpu_launches": launches_per_iter * args.steps, "clocks": clk,
@@ -515,10 +634,21 @@ def _ttp_setup(seed, gsr, torch):
     return truth, keyframes, [torch.tensor(k, device="cuda") for k in kps], offsets
 
 
+TTP_SMOOTH = 3  # evaluations in the running mean that decides a crossing
+
+
+def _smoothed_reached(curve, target, k=TTP_SMOOTH):
+    """Whether the mean PSNR of the last k evaluations (fewer at the start
+    only once the run has ended) has reached `target`."""
+    tail = [ps for _, _, ps in curve[-k:]]
+    return len(tail) == k and statistics.mean(tail) >= target
+
+
 def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, every, gsr, torch):
     """One arm: fresh map = truth with the held-out primitives initialised by
-    `init`; iterate until `target` PSNR (if given) or `budget` iterations.
-    Returns the PSNR curve [(iterations, training ms, PSNR)]."""
+    `init`; iterate until the running mean of the last TTP_SMOOTH evaluations
+    reaches `target` PSNR (if given) or for `budget` iterations.  Returns the
+    PSNR curve [(iterations, training ms, PSNR)]."""
     from paper_2311_16728_b300.batched import BatchedWindow
     from paper_2311_16728_b300.mapping import Evaluator, PlainMapper, densify_default, densify_learned
     params = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
@@ -532,7 +662,7 @@ def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, eve
     curve = [(0, 0.0, ev(params))]
     it, wall = 0, 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    while it < budget and not (target is not None and curve[-1][2] >= target):
+    while it < budget and not (target is not None and _smoothed_reached(curve, target)):
         k = min(every, budget - it)
         e0.record()
         for _ in range(k):
@@ -548,45 +678,56 @@ def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, eve
     return curve
 
 
-def _first_at(curve, target):
-    for it, ms, ps in curve:
-        if ps >= target:
-            return it, ms
+def _first_at(curve, target, k=TTP_SMOOTH):
+    """(iterations, training ms) at the first evaluation where the running
+    mean of the last k evaluations reaches `target`, or (None, None)."""
+    for i in range(k - 1, len(curve)):
+        if statistics.mean(ps for _, _, ps in curve[i - k + 1:i + 1]) >= target:
+            return curve[i][0], curve[i][1]
     return None, None
 
 
-def run_ttp(args):
+def ttp_experiment(eval_seeds, train_seeds=TTP_TRAIN_SEEDS, harvest_iters=TTP_HARVEST_ITERS,
+                   mlp_steps=TTP_MLP_STEPS, budget=TTP_BUDGET):
+    """Time to PSNR (the second half of the headline metric).  The learned
+    initialiser is trained inside the run, on the GPU, from (patch, converged
+    parameter) pairs harvested from window runs on the training scenes; then
+    on every held-out scene the plain path (single view, sequential pyramid
+    schedule, default initialisation) runs `budget` iterations and fixes the
+    target PSNR (the mean of its last TTP_SMOOTH evaluations), and the
+    batched window with the learned and with the default initialisation run
+    until the running mean of their evaluations reaches it.  Returns
+    (per-seed results, training summary)."""
     import torch
     import paper_2311_16728_b300 as gsr
     from paper_2311_16728_b300.batched import BatchedWindow
     from paper_2311_16728_b300.learned_init import LearnedInit, init_weights
     from paper_2311_16728_b300.mapping import densify_default, harvest, train_initialiser
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.time()
     li = LearnedInit(init_weights(3), TTP_NEW, lr=1e-3)  # batches of up to one keyframe's new primitives
-    # ---- harvest (patch, converged parameter) pairs from window runs on training scenes
     batches = []
-    for seed in TTP_TRAIN_SEEDS:
+    for seed in train_seeds:
         truth, keyframes, kps, offsets = _ttp_setup(seed, gsr, torch)
         params = gsr.Gaussians.from_arrays(truth.mean_op, truth.quat, truth.logscale, truth.sh)
         densify_default(params, keyframes, kps, offsets)
         initial = gsr.Gaussians(*(t.clone() for t in params.tensors()), params.sh_degree)
         bw = BatchedWindow(params, keyframes)
         bw.capture()
-        for _ in range(TTP_HARVEST_ITERS):
+        for _ in range(harvest_iters):
             bw.step()
         torch.cuda.synchronize()
         batches += harvest(li, params, initial, keyframes, kps, offsets)
         del bw, params, initial
-    losses = train_initialiser(li, batches, TTP_MLP_STEPS)
-    t_train = time.time() - t0
-    # ---- held-out scenes: plain + default init fixes the target, then the window arms race to it
-    seeds = [int(x) for x in args.ttp_seeds.split(",") if x]
+    losses = train_initialiser(li, batches, mlp_steps)
+    training = {"train_seeds": list(train_seeds), "harvest": f"{harvest_iters} window iterations per training "
+                f"scene, {sum(b.M for b in batches)} pairs", "mlp_steps": mlp_steps,
+                "mlp_loss_first_last": [losses[0], losses[-1]] if losses else None,
+                "setup_s": round(time.time() - t0, 1)}
     per_seed = []
-    for seed in seeds:
+    for seed in eval_seeds:
         truth, keyframes, kps, offsets = _ttp_setup(seed, gsr, torch)
-        plain = _ttp_run("plain", truth, keyframes, kps, offsets, "default", li, TTP_BUDGET, None, 100, gsr, torch)
-        target = plain[-1][2]
+        plain = _ttp_run("plain", truth, keyframes, kps, offsets, "default", li, budget, None, 100, gsr, torch)
+        target = statistics.mean(ps for _, _, ps in plain[-TTP_SMOOTH:])
         res = {"seed": seed, "target_psnr": target, "plain": {"curve": plain},
                "new": sum(int(k.shape[0]) for k in kps)}
         res["plain"]["iters"], res["plain"]["ms"] = _first_at(plain, target)
@@ -596,33 +737,51 @@ def run_ttp(args):
             res[name] = {"curve": c, "iters": it, "ms": ms, "psnr0": c[0][2]}
         res["plain"]["psnr0"] = plain[0][2]
         per_seed.append(res)
-    speed = [r["plain"]["ms"] / r["window_learned"]["ms"] for r in per_seed if r["window_learned"]["ms"]]
-    speed_def = [r["plain"]["ms"] / r["window_default"]["ms"] for r in per_seed if r["window_default"]["ms"]]
-    summary = [{"seed": r["seed"], "new_primitives": r["new"], "target_psnr": r["target_psnr"],
-                "plain_ms": r["plain"]["ms"], "plain_iters": r["plain"]["iters"],
-                "learned_window_ms": r["window_learned"]["ms"], "learned_window_iters": r["window_learned"]["iters"],
-                "default_window_ms": r["window_default"]["ms"], "default_window_iters": r["window_default"]["iters"],
-                "psnr0": {"default": r["plain"]["psnr0"], "learned": r["window_learned"]["psnr0"]}}
-               for r in per_seed]
+    return per_seed, training
+
+
+def ttp_summary(per_seed) -> dict:
+    """Per-seed iterations and training time to the target PSNR, and the
+    speed-ups (plain ms / window ms) with their spread across seeds."""
+    def spread(xs):
+        return {"mean": statistics.mean(xs), "min": min(xs), "max": max(xs)} if xs else None
+
+    sp_l = [r["plain"]["ms"] / r["window_learned"]["ms"] for r in per_seed
+            if r["window_learned"]["ms"] and r["plain"]["ms"]]
+    sp_d = [r["plain"]["ms"] / r["window_default"]["ms"] for r in per_seed
+            if r["window_default"]["ms"] and r["plain"]["ms"]]
+    seeds = [{"seed": r["seed"], "new_primitives": r["new"], "target_psnr": r["target_psnr"],
+              "plain": {"iters": r["plain"]["iters"], "ms": r["plain"]["ms"]},
+              "learned_window": {"iters": r["window_learned"]["iters"], "ms": r["window_learned"]["ms"]},
+              "default_window": {"iters": r["window_default"]["iters"], "ms": r["window_default"]["ms"]},
+              "psnr0": {"default": r["plain"]["psnr0"], "learned": r["window_learned"]["psnr0"]}}
+             for r in per_seed]
+    return {"speedup_learned_window": spread(sp_l), "speedup_default_window": spread(sp_d), "per_seed": seeds}
+
+
+TTP_WORKLOAD = (f"{TTP_N} Gaussians in a 6x3x4 m room, {TTP_KF} keyframes 640x480 fx=fy=525, every Gaussian whose "
+                f"centre a keyframe sees (at most {TTP_NEW} per keyframe) re-created at its keypoint (known depth, "
+                "unknown shape, opacity and colour); target = the plain path's PSNR (default init, sequential pyramid, "
+                f"tau_u 30; mean of its last {TTP_SMOOTH} evaluations) after {TTP_BUDGET} iterations; an arm reaches "
+                f"it when the mean of its last {TTP_SMOOTH} evaluations does; time = CUDA-event time of the training "
+                "iterations (evaluation excluded)")
+
+
+def run_ttp(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    seeds = [int(x) for x in args.ttp_seeds.split(",") if x]
+    per_seed, training = ttp_experiment(seeds)
+    summ = ttp_summary(per_seed)
+    sl = summ["speedup_learned_window"]
     line = {"metric": "time-to-PSNR speed-up, learned initialiser + batched window vs plain single-view path",
-            "value": statistics.mean(speed) if speed else None, "unit": "x (plain ms / learned+batched ms)",
+            "value": sl["mean"] if sl else None, "unit": "x (plain ms / learned+batched ms)",
             "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; held-out scenes)",
-            "config": {"workload": f"{TTP_N} Gaussians in a 6x3x4 m room, {TTP_KF} keyframes 640x480 fx=fy=525, "
-                                   "every Gaussian whose centre a keyframe sees (at most "
-                                   f"{TTP_NEW} per keyframe) re-created at its keypoint (known depth, unknown shape, "
-                                   "opacity and colour); target = PSNR of the plain path (default init, sequential "
-                                   f"pyramid, tau_u 30) after {TTP_BUDGET} iterations; wall time = CUDA-event time "
-                                   "of the training iterations (evaluation excluded)",
-                       "train_seeds": list(TTP_TRAIN_SEEDS), "eval_seeds": seeds,
-                       "harvest": f"{TTP_HARVEST_ITERS} window iterations per training scene, "
-                                  f"{sum(b.M for b in batches)} pairs", "mlp_steps": TTP_MLP_STEPS,
-                       "mlp_loss_first_last": [losses[0], losses[-1]] if losses else None,
-                       "setup_s": round(t_train, 1)},
-            "speedup_default_window": statistics.mean(speed_def) if speed_def else None,
-            "per_seed": summary, "curves": {str(r["seed"]): {k: r[k]["curve"] for k in
-                                                            ("plain", "window_learned", "window_default")}
-                                           for r in per_seed}}
+            "config": {"workload": TTP_WORKLOAD, "eval_seeds": seeds, **training},
+            **summ, "curves": {str(r["seed"]): {k: r[k]["curve"] for k in ("plain", "window_learned",
+                                                                         "window_default")}
+                               for r in per_seed}}
     print(json.dumps(line), flush=True)
 
 
@@ -944,12 +1103,17 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-rows", type=int, default=64, help="image rows per oracle step (reference arm)")
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="image rows per oracle step (reference arm; default: bands that tile the frame over --steps)")
     ap.add_argument("--cpu-rows", type=int, default=680, help="image rows of the cpu_baseline sample")
     ap.add_argument("--mode", default="mapping",
                     choices=["mapping", "window", "mlp", "ttp", "densify", "stereo", "gp_ablation", "pose"])
     ap.add_argument("--ttp-seeds", default="100,101,102,103,104", help="ttp mode: held-out evaluation scenes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="mapping mode: leave out the window figure and the bounded time-to-PSNR run")
+    ap.add_argument("--headline-ttp-seeds", default="100,101",
+                    help="mapping mode: held-out scenes of the bounded time-to-PSNR run in the headline line")
     ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
     ap.add_argument("--profile", action="store_true",
                     help="run --steps iterations between cudaProfilerStart/Stop after the warm-up and exit "
@@ -1012,10 +1176,13 @@ def main():
     params = _ordered(gsr, gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh), args)
     ms = gsr.MappingStep(params, list(zip(cams, gts)), tiling)
     ms.capture()
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         ms.step()
     torch.cuda.synchronize()
     if args.profile:
+        clocks.stop(local)
         _profile_steps(ms.step, args.steps)
         return
     if world > 1:
@@ -1023,26 +1190,25 @@ def main():
 
     # ---- timed region: K whole iterations, one graph replay each
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler()
-    clocks.start()
     torch.cuda.synchronize()
+    clocks.mark("timed_start")
     t_start.record()
     for k in range(args.steps):
         ms.step()
     t_end.record()
     torch.cuda.synchronize()
+    clocks.mark("timed_end")
     if world > 1:
         dist.barrier()
     ms_total = t_start.elapsed_time(t_end)
     # ---- stage times: the same iterations replayed one graph per stage,
     # events between the stages (live, on the launching stream)
     nst = len(gsr.STAGES)
-    k_st = min(args.steps, 300)
+    k_st = min(max(args.steps, 50), 300)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)] for _ in range(k_st)]
     for k in range(k_st):
         ms.step(events=evs[k])
     torch.cuda.synchronize()
-    clk = clocks.stop(local)
     stage_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, name in enumerate(gsr.STAGES)}
     status = ms.status()
     pairs = int(ms.vb.num_pairs.item())
@@ -1086,6 +1252,7 @@ def main():
         host_loss.copy_(ms.vb.loss, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop(local)
     e2e_ms = e0.elapsed_time(e1) / args.steps
     e2e_ms = max_over_ranks(e2e_ms, "cuda")
 
@@ -1150,6 +1317,18 @@ def main():
                                           f"Gaussians, render+loss+backward on rows {row0}-{row0 + rows} of 680"
                                           + (", extrapolated to the full frame" if rows < HEIGHT else "")
                                           + f" ({measured:.1f} s measured)"}
+    if world == 1 and not args.no_extras and args.scene == "room":
+        # the rest of the headline metric, after the throughput figure: the
+        # batched window's rate and a bounded time-to-PSNR run (the learned
+        # initialiser trained on the GPU inside this run, two held-out scenes)
+        del ms, params
+        torch.cuda.empty_cache()
+        t_x = time.time()
+        line["window"] = window_figure(args)
+        seeds = [int(x) for x in args.headline_ttp_seeds.split(",") if x]
+        per_seed, training = ttp_experiment(seeds)
+        line["ttp"] = {"workload": TTP_WORKLOAD, "eval_seeds": seeds, **training, **ttp_summary(per_seed)}
+        line["extras_s"] = round(time.time() - t_x, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -1166,60 +1345,84 @@ NCU_TRAFFIC_POSE = 15.037952e6
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
 NCU_TRAFFIC_WINDOW_ITERATE = 604.692224e6
 
-# FP32 work per blended (pixel, Gaussian) pair and algorithmic bytes per unit.
-FLOPS_PER_BLEND_FWD = 20
-FLOPS_PER_BLEND_BWD = 60
+# Algorithmic work per unit (the hot-path scope table's measurement figures;
+# the implementation's own DRAM bytes are the ncu `traffic` above, never the
+# algorithmic figure): FP32 operations per (pixel, Gaussian) evaluation in the
+# forward and backward blends.
+FLOPS_PER_BLEND_FWD = 16
+FLOPS_PER_BLEND_BWD = 55
 
 
-def stage_rooflines(stage_ms, work, peaks, clk, traffic):
+def _fp32_clock(clk, peaks):
+    """SM clock for the FP32 peak and where it came from."""
+    if clk.get("sm_mhz"):
+        return clk["sm_mhz"], f"median SM clock sampled during the run ({clk.get('source')})"
+    if "sm_max_mhz" in peaks:
+        return peaks["sm_max_mhz"], "MEASURED_PEAKS.json sm_max_mhz (no clock samples)"
+    return 2032.0, "nominal maximum 2032 MHz (no clock samples, no MEASURED_PEAKS.json)"
+
+
+def sort_passes(tiles: int) -> int:
+    """8-bit radix passes of a global LSD sort on 32 depth bits + ceil(log2 T) tile bits."""
+    return -(-(32 + max(1, (tiles - 1).bit_length())) // 8)
+
+
+def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None):
     """Roofline entry of each stage's dominant kernel: algorithmic work per
-    launch / measured stage time against the measured HBM copy bandwidth or
-    the FP32 peak (148 SMs x 128 lanes x 2 flops x median SM clock)."""
+    launch (per-unit figure x the units of one launch) / measured stage time,
+    against the measured HBM copy bandwidth or the FP32 peak (148 SMs x 128
+    lanes x 2 flops x SM clock, the clock sampled during the run when there
+    are samples, else MEASURED_PEAKS.json's maximum)."""
     hbm = peaks.get("hbm_gbs", 6400.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6400 GB/s (of fallback)"
-    mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    mhz, mhz_src = _fp32_clock(clk, peaks)
     fp32 = 148 * 128 * 2 * mhz * 1e6 / 1e12
     n, nv, K, E = N_GAUSS, work["visible"], work["pairs"], work["blends"]
+    T = tiles if tiles is not None else -(-WIDTH // 16) * -(-HEIGHT // 16)
     px = 3 * WIDTH * HEIGHT
 
-    def hbm_entry(kernel, alg):
+    def hbm_entry(kernel, alg, rule):
         sec = stage_ms[st] * 1e-3
         return {"kernel": kernel, "bound": "hbm", "achieved": alg / sec / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": alg / sec / 1e9 / hbm, "traffic": traffic.get(st), "alg_per_launch": alg,
+                "frac": alg / sec / 1e9 / hbm, "traffic": traffic.get(st), "alg_per_launch": alg, "alg_rule": rule,
                 "peak_source": hbm_src}
 
-    def alu_entry(kernel, flops):
+    def alu_entry(kernel, flops, rule):
         sec = stage_ms[st] * 1e-3
         return {"kernel": kernel, "bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32, "unit": "TFLOP/s",
                 "frac": flops / sec / 1e12 / fp32, "traffic": traffic.get(st), "alg_per_launch": flops,
-                "peak_source": f"FP32 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz (sampled median clock)"}
+                "alg_rule": rule, "peak_source": f"FP32 148 SMs x 128 lanes x 2 flops x {mhz:.0f} MHz, {mhz_src}"}
 
     out = {}
     for st in stage_ms:
         if st == "preprocess":
-            # the frustum test reads the mean (16 B) and every Gaussian's tile
-            # count is written (4 B); a visible Gaussian also reads rotation
-            # and scale (32 B) and SH (192 B) and writes its record (48 B)
-            out[st] = hbm_entry("preprocess_fwd_kernel", (16 + 4) * n + (32 + 192 + 48) * nv)
+            out[st] = hbm_entry("preprocess_fwd_kernel", 12 * n + (228 + 48) * nv,
+                                "12 B per Gaussian (cull read) + 228 B read + 48 B written per visible")
         elif st == "bin_sort":
-            # depth passes 4 x 16 B per visible, tile passes 2 x 16 B per pair, keys + values out 12 B per pair
-            out[st] = hbm_entry("binning + radix passes", 4 * 16 * nv + 2 * 16 * K + 12 * K)
+            P = sort_passes(T)
+            out[st] = hbm_entry("binning + per-tile sorts", 12 * K + 4 * n + 24 * P * K + 8 * K,
+                                f"keys + values 12 B per pair + scan 4 B per Gaussian + {P} radix passes x 24 B per "
+                                f"pair (32 depth + ceil(log2 {T}) tile bits) + ranges 8 B per pair")
         elif st == "render_fwd":
-            out[st] = alu_entry("render_fwd_kernel", FLOPS_PER_BLEND_FWD * E)
+            out[st] = alu_entry("render_fwd_kernel", FLOPS_PER_BLEND_FWD * E,
+                                f"{FLOPS_PER_BLEND_FWD} FP32 per (pixel, Gaussian) evaluation x blends")
         elif st == "loss":
-            # x, y read twice, three maps written and read, dL/dx written
-            out[st] = hbm_entry("ssim_pass1/2_kernel", 4 * px * (2 + 3 + 3 + 2 + 1))
+            out[st] = hbm_entry("ssim kernels", 12 * px,
+                                "rendered + target read (2 x 4 B) and dL/dI written (4 B) per pixel-channel")
         elif st == "blend_bwd":
-            out[st] = alu_entry("render_bwd_q4_kernel", FLOPS_PER_BLEND_BWD * E)
+            out[st] = alu_entry("render_bwd_q4_kernel", FLOPS_PER_BLEND_BWD * E,
+                                f"{FLOPS_PER_BLEND_BWD} FP32 per (pixel, Gaussian) evaluation x blends")
         elif st == "preprocess_bwd":
-            # per visible Gaussian: parameters 240 B and screen-space gradient
-            # 48 B read, gradients 240 B stored (they are zero before the pass),
-            # densify statistic and count 16 B; visibility word 4 B per Gaussian
-            out[st] = hbm_entry("preprocess_bwd_kernel", (240 + 48 + 240 + 16) * nv + 4 * n)
+            out[st] = hbm_entry("preprocess_bwd_kernel", (236 + 236) * nv,
+                                "236 B read + 236 B written per visible Gaussian")
         elif st == "adam":
-            # 15 float4 planes: param, m, v read + written for every Gaussian, the
-            # gradient read + zeroed only where the view flag (4 B) is set
-            out[st] = hbm_entry("adam_kernel", (15 * 16 * 6 + 4) * n + 15 * 16 * 2 * nv)
+            # 59 parameters: p, m, v read and written for every Gaussian; the
+            # gradient read and zeroed only where a view flag (4 B) says the
+            # view saw the Gaussian (an unseen Gaussian's gradient is zero)
+            out[st] = hbm_entry("adam_kernel", 59 * 4 * 6 * n + 4 * n + 59 * 4 * 2 * nv,
+                                "59 parameters x (p, m, v read + written) per Gaussian + view flag 4 B + gradient "
+                                "read + zeroed per visible Gaussian (the dense step's 32 B per parameter less the "
+                                "unseen Gaussians' zero gradients)")
     return out
 
 

@@ -14,7 +14,9 @@
  *  - Every pointer named d_* or documented "device" is CUDA device memory
  *    owned by the caller.  No entry point allocates, frees or synchronises the
  *    device; scratch memory is a caller buffer sized by the matching
- *    *_workspace_size query.  Structs and scalars are read on the host during
+ *    *_workspace_size query.  The one exception is gsr_autotune, a set-up
+ *    call outside the iteration: it creates and destroys CUDA events and
+ *    synchronises the stream it times (never inside a stream capture).  Structs and scalars are read on the host during
  *    the call and may be freed on return.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *    stream) and runs asynchronously; outputs are valid once the stream has
@@ -275,15 +277,22 @@ int32_t gsr_render_bwd(const gsr_gaussians *g, const gsr_proj *proj, const uint3
  *
  * Computes exactly what gsr_loss_fwd_bwd computes (same kernels), but its
  * scratch lives in one fixed array in device memory that the library defines
- * (29.6 MB, held by every GPU that loads the library until the process
- * exits).  Limits: C * H * W <= 2,457,600 values (a 3 x 1200 x 680 frame fits)
- * and at most 16,384 blocks of 32 x 32 pixels summed over channels; larger
- * images return GSR_ERR_CAPACITY with a message and enqueue nothing.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  It never calls cudaMalloc or cudaFree.
- * All calls on a device share the array and it keeps the last call's
- * contents (nothing in it needs clearing between calls): calls whose work
+ * (29.6 MB).  The array is allocated on a device when the library's loss
+ * module is first loaded there (CUDA loads modules lazily: the first call on
+ * that device of any loss entry point, this one or gsr_loss_fwd_bwd /
+ * gsr_loss_luma_fwd_bwd, or the address lookup below) and is held until the
+ * process exits.  Limits: C * H * W <= 2,457,600 values (a 3 x 1200 x 680
+ * frame fits) and at most 16,384 blocks of 32 x 32 pixels summed over
+ * channels; larger images return GSR_ERR_CAPACITY with a message and enqueue
+ * nothing.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and caches it for
+ * the process: make that first call, and so the module load, before any
+ * stream capture, and do not use this entry point across a cudaDeviceReset
+ * (or any other teardown of the device's primary context) in the same
+ * process, after which the cached address is stale.  It never calls
+ * cudaMalloc or cudaFree.  All calls on a device share the array and it keeps
+ * the last call's contents; every entry a call reads is written earlier in
+ * the same call, so nothing needs clearing between calls.  Calls whose work
  * overlaps on the GPU -- on different streams, or from different host
  * threads -- race on it and must be serialised by the caller. */
 int32_t gsr_loss_fwd_bwd_static(const float *img, const float *gt, int32_t C, int32_t H, int32_t W,
@@ -561,7 +570,10 @@ typedef int32_t (*gsr_autotune_fn)(int32_t candidate, int32_t action, void *ctx)
  * SETUP, `warmup` STEPs, a synchronisation, then `steps` STEPs each
  * bracketed by CUDA events on `stream`, then RELEASE.  ms[c] (host, ncand
  * floats) = the median step time of candidate c in milliseconds; *best (host)
- * = the fastest candidate.  A callback error or a CUDA error stops the run
+ * = the fastest candidate.  Unlike every other entry point this one
+ * synchronises `stream` (after the warm-up and after the timed steps, to
+ * read the events) and creates its own events: call it outside any stream
+ * capture.  A callback error or a CUDA error stops the run
  * (after the failing candidate's RELEASE when its SETUP succeeded), is
  * returned, and leaves *best = -1. */
 int32_t gsr_autotune(int32_t ncand, gsr_autotune_fn fn, void *ctx, int32_t warmup, int32_t steps,

@@ -1,0 +1,82 @@
+"""Element-wise error bounds for the learned initialiser's tensor-core MLP
+against its FP64 oracle (test infrastructure; no method arithmetic of the
+product lives here).
+
+The GPU and the oracle round the same operands to BF16 at the same places,
+so the two sides differ only where an FP32 sum (GEMM accumulation order) and
+its FP64 counterpart round to different BF16 neighbours, one BF16 ulp
+(2^-8 relative, 8 significant bits) apart, and through what such a
+difference moves downstream.  The forward test bounds the output by
+2^-7 |W3| |h2|: every operand of the last GEMM within 2^-7 (two BF16 ulps)
+of the oracle's.  The gradients get the same kind of bound, built on the
+magnitude of each gradient's own GEMM or column sum:
+
+  gW3 = dy^T h2          2 x 2^-7 |dy|^T |h2|          (both operands rounded)
+  gW2 = dpre2^T h1       2 x 2^-7 |dpre2|^T |h1|
+  gW1 = dpre1^T x        2^-7 |dpre1|^T |x|            (x is the same on both sides)
+  gb3, gb2, gb1          2^-7 sum_m |d|                (FP32 column sums)
+
+plus the FP32 summation bound gamma_M sum |a b| (gamma_n = n u / (1 - n u),
+u = 2^-24).  Like the forward's, this is a model bound (each operand element
+within two BF16 ulps of the oracle's), not a worst case over every possible
+cascade of roundings; `tests/test_mlp_bounds.py` pins it on the CPU against
+an FP32 / BF16 simulation of the tensor-core arithmetic and shows that a
+planted mistake leaves it.  For the Adam step that follows, `adam_bounds`
+carries a gradient bound through the update by the mean value theorem.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U32 = 2.0 ** -24
+TWO_ULPS = 2.0 ** -7
+
+
+def gamma(n: int) -> float:
+    return n * U32 / (1.0 - n * U32)
+
+
+def gradient_bounds(fw: dict, dy: np.ndarray, g_ref: dict) -> dict:
+    """Per-element bounds of the six gradients, from the oracle's forward
+    dict (oracle.mlp.forward), dL/dy (oracle.mlp.loss_and_dy) and its
+    gradients (oracle.mlp.backward, whose BF16 operands it recomputes)."""
+    from oracle import mlp as omlp
+    M = dy.shape[0]
+    dyb = np.abs(omlp.bf16_round(dy))
+    dh2 = omlp.bf16_round(dy) @ fw["W3"]
+    dpre2 = dh2 * (fw["pre2"] > 0)
+    dh1 = omlp.bf16_round(dpre2) @ fw["W2"]
+    dpre1 = dh1 * (fw["pre1"] > 0)
+    a2, a1 = np.abs(omlp.bf16_round(dpre2)), np.abs(omlp.bf16_round(dpre1))
+    h1, h2, x = np.abs(fw["h1"]), np.abs(fw["h2"]), np.abs(fw["xb"])
+    s = gamma(M)
+    out = {"W3": (2 * TWO_ULPS + s) * (dyb.T @ h2),
+           "W2": (2 * TWO_ULPS + s) * (a2.T @ h1),
+           "W1": (TWO_ULPS + s) * (a1.T @ x),
+           "b3": (TWO_ULPS + s) * np.abs(dy).sum(0),
+           "b2": (TWO_ULPS + s) * np.abs(dpre2).sum(0),
+           "b1": (TWO_ULPS + s) * np.abs(dpre1).sum(0)}
+    for k in out:
+        assert out[k].shape == np.shape(g_ref[k]), k
+    return out
+
+
+def adam_bounds(p0, m0, v0, g, e_g, lr, t, b1, b2, eps):
+    """Bounds on |GPU - oracle| of one Adam step's new parameter, first and
+    second moment, given the gradient bound e_g (the oracle's g).  Mean value
+    theorem on the update lr m_hat / (sqrt(v_hat) + eps) over the interval
+    |g' - g| <= e_g, with sqrt(v_hat) >= sqrt(b2 v0 / bc2) there, plus the
+    FP32 rounding of the step (a few ulps of each quantity)."""
+    bc1, bc2 = 1.0 - b1 ** t, 1.0 - b2 ** t
+    ag = np.abs(g) + e_g
+    m = b1 * m0 + (1.0 - b1) * g
+    v = b2 * v0 + (1.0 - b2) * g * g
+    s_min = np.sqrt(b2 * v0 / bc2)
+    am = np.abs(b1 * m0) + (1.0 - b1) * ag
+    d_dg = (1.0 - b1) / bc1 / (s_min + eps) + (am / bc1) * ((1.0 - b2) * ag / bc2) / (
+        np.maximum(s_min, 1e-300) * (s_min + eps) ** 2)
+    step = lr * (np.abs(m) / bc1) / (np.sqrt(v / bc2) + eps)
+    e_p = lr * d_dg * e_g + 2.0 * U32 * np.abs(p0) + 16.0 * U32 * (step + lr * d_dg * e_g)
+    e_m = (1.0 - b1) * e_g + 3.0 * U32 * (np.abs(m) + (1.0 - b1) * e_g)
+    e_v = (1.0 - b2) * (2.0 * np.abs(g) + e_g) * e_g + 4.0 * U32 * (v + (1.0 - b2) * ag * ag)
+    return e_p, e_m, e_v

@@ -7,16 +7,18 @@ FP32 rounding; with several views, each view's loss and weighted pixel
 gradient match its single-view evaluation and the parameter gradient equals
 the sum of the single-view backward passes (normwise 1e-5: only the order of
 FP32 atomic additions differs); against the FP64 oracle, per-view losses
-within 1e-5 relative and the summed gradient normwise within 1e-3, as for
-the single-view end-to-end test.
+within 1e-5 relative and the summed gradient per element within the
+gradient bar, as for the single-view end-to-end test; at the benchmark's
+size, keys of all 24 views bit-exact and their whole images within the image
+bar.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import (IMG_ATOL, MARGIN_FLAG, grad_planes_gpu, grad_report, morton_permuted, oracle_scene,
-                            to_gpu)
+from parity_helpers import (IMG_ATOL, MARGIN_FLAG, assert_grad_bar, colour_clamp_waiver, grad_planes_gpu, grad_report,
+                            morton_permuted, near_flagged, oracle_scene, param_condition, to_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -138,22 +140,29 @@ def test_window_matches_oracle_tiny():
     _run_once(bw)
     gt_l = gt0
     gref = np.zeros((p.n, 60))
+    cond = np.zeros((p.n, 60))
+    waive = np.zeros((p.n, 60), bool)
     for lvl in range(levels):
         if lvl:
             gt_l = oracle.pyramid_down(gt_l)
         cl = S.camera_at_level(cam, lvl)
         ca = cl.as_array()
         dec = oracle.decide(p.mean_op, p.quat, p.logscale, ca, cl.width, cl.height)
-        img, _, _, _ = oracle.render(sc, ca, cl.width, cl.height, dec)
+        img, _, _, mg = oracle.render(sc, ca, cl.width, cl.height, dec)
         L_ref, dimg = oracle.loss(img, gt_l, 0.2)
-        gv, _ = oracle.render_bwd(sc, ca, cl.width, cl.height, dec, dimg)
+        gv, _, mag = oracle.render_bwd(sc, ca, cl.width, cl.height, dec, dimg, with_magnitude=True)
         gref += gv
+        cond += param_condition(sc, ca, cl.width, cl.height, dec, mag)
+        waive |= colour_clamp_waiver(oracle.project(sc, ca, cl.width, cl.height, dec.visible))
+        waive[near_flagged(dec, mg < MARGIN_FLAG)] = True
         L = float(bw.losses[[v[2] for v in bw.views].index(lvl)].item())
-        print(f"level {lvl}: loss {L:.7f} vs oracle {L_ref:.7f}")
+        print(f"level {lvl}: loss {L:.7f} vs oracle {L_ref:.7f}; flagged pixels {int((mg < MARGIN_FLAG).sum())}")
         assert abs(L - L_ref) <= 1e-5 * L_ref
-    _, _, norms = grad_report(grad_planes_gpu(bw.grads), gref)
-    print(f"summed gradient normwise error vs oracle {norms}")
-    assert max(norms.values()) <= 1e-3
+    # the views' losses are mean-reduced: scale by the level-0 view's 3HW (a
+    # sum-reduced loss) so that the 1e-6 floor does not pass everything
+    s = 3 * cam.width * cam.height
+    assert_grad_bar("window (2 levels, x 3HW), summed parameter gradients", s * grad_planes_gpu(bw.grads), s * gref,
+                    s * cond, waive=waive)
 
 
 def test_window_graph_replay_matches_eager():
@@ -177,12 +186,12 @@ def test_window_graph_replay_matches_eager():
     assert le[-1] < le[0], "window loss did not decrease"
 
 
-def test_window_full_size_keys_and_sampled_rows():
+def test_window_full_size_keys_and_images():
     """The window as the benchmark runs it: 500k Gaussians in the Morton-ordered
     store, 8 keyframes 640 x 480 x 3 levels, 16 x 16 tiles.  Keys, order and
     ranges bit-exact against the oracle for all 24 views (values mapped back
-    from compact positions to Gaussian ids); images on sampled rows of one
-    view per level within the image bar."""
+    from compact positions to Gaussian ids); the whole image of every view
+    within the image bar."""
     n = 500_000
     p = morton_permuted(S.perturb(S.room_scene(n, seed=0), 0.05, seed=1), S.ROOM_LO, S.ROOM_HI)
     cams = [S.tum_camera(k * 50 // 8) for k in range(8)]
@@ -201,7 +210,7 @@ def test_window_full_size_keys_and_sampled_rows():
     c2rec = np.zeros(len(vis_rec), np.int64)
     c2rec[r2c[vis_rec]] = vis_rec
     sc = oracle_scene(p)
-    toff, pos, sampled = 0, 0, set()
+    toff, pos, worst, nflag = 0, 0, 0.0, 0
     for v, (_, _, lvl, k) in enumerate(bw.views):
         cl = S.camera_at_level(cams[k], lvl)
         ca = cl.as_array()
@@ -218,16 +227,15 @@ def test_window_full_size_keys_and_sampled_rows():
         assert np.array_equal(wr[0::2] == wr[1::2], empty), f"view {v}: empty tiles differ"
         assert np.array_equal((wr[0::2] - pos)[~empty], rr[0::2][~empty].astype(np.int64))
         assert np.array_equal((wr[1::2] - pos)[~empty], rr[1::2][~empty].astype(np.int64))
-        if lvl not in sampled and k == 3 * lvl:  # one view per level, from different keyframes
-            sampled.add(lvl)
-            gi = bw.imgs[v].cpu().numpy()
-            H = cl.height
-            for r in [(0, 2), (H // 2 - 1, H // 2 + 1), (H - 2, H)]:
-                img, _, _, mg = oracle.render(sc, ca, cl.width, H, dec, rows=r)
-                fl = mg[r[0]:r[1]] < MARGIN_FLAG
-                err = np.abs(gi[:, r[0]:r[1]] - img[:, r[0]:r[1]]).max(0)
-                assert err[~fl].max() <= IMG_ATOL, (v, r, err.max())
+        gi = bw.imgs[v].cpu().numpy()
+        img, _, _, mg = oracle.render(sc, ca, cl.width, cl.height, dec)
+        fl = mg < MARGIN_FLAG
+        err = np.abs(gi - img).max(0)
+        worst = max(worst, float(err[~fl].max()))
+        nflag += int(fl.sum())
+        assert err[~fl].max() <= IMG_ATOL, (v, err.max())
         toff += T
         pos += m
-    assert pos == npairs and toff == bw.tiles and sampled == {0, 1, 2}
-    print(f"window full size: {bw.V} views, {npairs} pairs, {len(vis_rec)} visible records")
+    assert pos == npairs and toff == bw.tiles
+    print(f"window full size: {bw.V} views, {npairs} pairs, {len(vis_rec)} visible records; whole images of every "
+          f"view: max err {worst:.2e} ({nflag} flagged pixels)")

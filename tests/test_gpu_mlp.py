@@ -2,7 +2,9 @@
 import numpy as np
 import pytest
 
+import oracle
 import synthetic as S
+from mlp_bounds import adam_bounds, gradient_bounds
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
@@ -99,25 +101,70 @@ def test_forward_matches_oracle(M):
 # runs the 2-stage 128 x 128 forward tiles and the 3-stage split-K weight
 # gradient of the first layer)
 @pytest.mark.parametrize("M", [200, 2048, 20000])
-def test_training_gradients_match_oracle(M):
+def test_training_gradients_and_adam_match_oracle(M):
+    """One training step (Adam step 5 from seeded moments) against the FP64
+    oracle: the loss within 1e-3 relative; every element of the six
+    gradients within its bound (tests/mlp_bounds.py: each operand of the
+    gradient's GEMM within two BF16 ulps, plus the FP32 summation bound), the
+    normwise error and the share of elements within 1e-3 relative printed per
+    tensor; then the fused Adam update of every master weight and both
+    moments against oracle.adam on the oracle's gradients, within the bound
+    that carries the gradient bound through the update."""
     p, x, t = _batch(M, seed=7)
-    li = LearnedInit(p, M, lr=1e-4)
+    lr, b1, b2, eps, step = 1e-4, 0.9, 0.999, 1e-8, 5
+    f32 = lambda v: float(np.float32(v))  # the kernel receives FP32 hyper-parameters
+    fw = omlp.forward(p, x)
+    L_ref, dy = omlp.loss_and_dy(fw["y"], t, np.ones(omlp.N3))
+    g_ref = omlp.backward(fw, dy)
+    bounds = gradient_bounds(fw, dy, g_ref)
+    names = ("W1", "b1", "W2", "b2", "W3", "b3")
+    li = LearnedInit(p, M, lr=lr)
     _load(li, x)
+    rng = np.random.default_rng(11)
+    p0, m0, v0 = {}, {}, {}
+    for k in names:
+        rms = max(float(np.sqrt(np.mean(g_ref[k] ** 2))), 1e-6)
+        shape = li.w.t[k].shape
+        m0[k] = rng.normal(0.0, rms, shape).astype(np.float32)
+        v0[k] = (rng.uniform(0.5, 2.0, shape) * rms * rms).astype(np.float32)
+        li.m.t[k].copy_(torch.tensor(m0[k]))
+        li.v.t[k].copy_(torch.tensor(v0[k]))
+        p0[k] = li.w.t[k].cpu().numpy()
+    li.step_count.fill_(step - 1)
     target = torch.zeros(li.mpad, omlp.N3, device="cuda")
     target[:M] = torch.tensor(t, device="cuda")
     li.train_step(target, M)
     torch.cuda.synchronize()
     assert int(li.status.item()) == 0
-    fw = omlp.forward(p, x)
-    L_ref, dy = omlp.loss_and_dy(fw["y"], t, np.ones(omlp.N3))
-    g_ref = omlp.backward(fw, dy)
-    assert float(li.loss.item()) == pytest.approx(L_ref, rel=1e-3)
+    L = float(li.loss.item())
+    print(f"M {M}: loss {L:.6f} vs {L_ref:.6f} (rel {abs(L - L_ref) / L_ref:.1e})")
+    assert L == pytest.approx(L_ref, rel=1e-3)
     g = {k: v.cpu().numpy().astype(np.float64) for k, v in li.gradients().items()}
-    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+    for k in names:
+        err = np.abs(g[k] - g_ref[k])
         rel = np.linalg.norm(g[k] - g_ref[k]) / max(np.linalg.norm(g_ref[k]), 1e-30)
+        within = float(np.mean(err <= np.maximum(1e-3 * np.abs(g_ref[k]), 1e-9)))
+        print(f"  grad {k}: normwise {rel:.2e}, worst err/bound {float((err / (bounds[k] + 1e-300)).max()):.3f}, "
+              f"{100 * within:.1f} % of elements within 1e-3 relative")
+        assert (err <= bounds[k]).all(), (k, int((err > bounds[k]).sum()))
         assert rel < 2e-2, (k, rel)
-    # one Adam step moved the masters and refreshed the BF16 copies
-    assert int(li.step_count.item()) == 1
+    for k in names:
+        lr_a = np.full(p0[k].shape, f32(lr))
+        p1, m1, v1 = oracle.adam(p0[k], g_ref[k], m0[k], v0[k], lr_a, step, f32(b1), f32(b2), f32(eps))
+        e_p, e_m, e_v = adam_bounds(p0[k], m0[k], v0[k], g_ref[k], bounds[k], f32(lr), step, f32(b1), f32(b2),
+                                    f32(eps))
+        w1 = li.w.t[k].cpu().numpy().astype(np.float64)
+        gm = li.m.t[k].cpu().numpy().astype(np.float64)
+        gv = li.v.t[k].cpu().numpy().astype(np.float64)
+        moved = np.abs(p1 - p0[k])
+        print(f"  adam {k}: param err / bound {float((np.abs(w1 - p1) / e_p).max()):.3f} (step {moved.mean():.1e}, "
+              f"err {np.abs(w1 - p1).mean():.1e} mean), m {float((np.abs(gm - m1) / e_m).max()):.3f}, "
+              f"v {float((np.abs(gv - v1) / e_v).max()):.3f}")
+        assert (np.abs(w1 - p1) <= e_p).all(), k
+        assert (np.abs(gm - m1) <= e_m).all(), k
+        assert (np.abs(gv - v1) <= e_v).all(), k
+    # the step counter advanced and the BF16 copies are the updated masters
+    assert int(li.step_count.item()) == step
     assert torch.equal(li.w.h["W1h"], li.w.t["W1"].to(torch.bfloat16))
     assert torch.equal(li.w.h["W3hT"], li.w.t["W3"].t().contiguous().to(torch.bfloat16))
 

@@ -2,22 +2,28 @@
 
 Bars: tile keys, sort order, per-tile ranges, cull set, depth bits and pixel
 boxes bit-exact; image <= 1e-4 max abs; gradients per element
-|g - g*| <= max(1e-3 |g*|, 1e-6) + 2^-15 C, where C is the element's
-condition magnitude (the oracle's sum of |terms|): the allowance only
-matters where the exact sum cancels, and the number of elements that use it
-is printed.  Pixels where an alpha / transmittance
-decision lies within 1e-5 (relative) of its threshold may legitimately flip
-between FP32 and FP64: the oracle flags them, the tests count them and keep
-them out of the element-wise image bar (their upstream gradient is zeroed in
-the gradient checks, which removes their influence exactly).
+|g - g*| <= max(1e-3 |g*|, 1e-6).  The upstream gradients of the
+render-backward tests are N(0, 1) per pixel (the scale of a sum-reduced loss,
+where the 1e-6 floor is not vacuous); the end-to-end test scales the
+mean-reduced Eq. 4 gradients by 3HW for the same reason.  An element that
+misses the bar is accepted only as a cancellation case (its exact value at
+most 1 % of the sum C of its terms' magnitudes, the error within 2^-15 C, at
+most 0.1 % of the elements), counted and printed (parity_helpers.
+assert_grad_bar).  Pixels where an alpha / transmittance decision lies within
+1e-5 (relative) of its threshold may legitimately flip between FP32 and FP64:
+the oracle flags them, the tests count them and keep them out of the
+element-wise image bar (their upstream gradient is zeroed in the gradient
+checks, which removes their influence exactly).  Where a Gaussian's raw colour
+lies within 1e-4 of the clamp at 0, the elements that decision changes (that
+channel's SH, the mean) are waived and counted; the rest are checked.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import (GRAD_TAU, IMG_ATOL, MARGIN_FLAG, gpu_view, grad_check, grad_planes_gpu, grad_report,
-                            morton_permuted, oracle_scene, param_condition, to_gpu, unpack_box)
+from parity_helpers import (IMG_ATOL, MARGIN_FLAG, assert_grad_bar, colour_clamp_waiver, gpu_view, grad_planes_gpu,
+                            morton_permuted, near_flagged, oracle_scene, param_condition, to_gpu, unpack_box)
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +68,12 @@ def _check_keys(vb, dec, keys_ref):
     assert np.array_equal(unpack_box(cb[vis]), dec.box[vis]), "pixel boxes differ"
 
 
+def _screen_grads(vb):
+    """The GPU's screen-space gradients (u, v, A, B, C, opacity, r, g, b) in the oracle's (N, 9) layout."""
+    g2 = vb.g2.cpu().numpy()
+    return np.concatenate([g2[0], g2[1], g2[2][:, :1]], 1).astype(np.float64)
+
+
 @pytest.mark.parametrize("tile", TILINGS)
 def test_keys_order_ranges_bit_exact_tiny(tile):
     p, cam = S.tiny_scene(), S.tiny_camera()
@@ -99,14 +111,12 @@ def test_thin_surface_gaussians_keys_image_and_gradients():
     grads = g.zeros_like()
     vb.render_bwd(g, grads, dimg=torch.tensor(dimg, device="cuda"))
     torch.cuda.synchronize()
-    g2 = vb.g2.cpu().numpy()
-    g2gpu = np.concatenate([g2[0], g2[1], g2[2][:, :1]], 1).astype(np.float64)
-    ok2, used2, worst2 = grad_check(g2gpu, g2ref, mag)
-    _, _, norms = grad_report(grad_planes_gpu(grads), gref)
-    print(f"thin surfaces: {int(dec.visible.sum())} visible, flagged pixels {int(flagged.sum())}, screen-space "
-          f"worst err/bound {worst2:.3f}, parameter gradients normwise {norms}")
-    assert ok2.all()
-    assert max(norms.values()) <= 1e-3
+    g2gpu = _screen_grads(vb)
+    print(f"thin surfaces: {int(dec.visible.sum())} visible, flagged pixels {int(flagged.sum())}")
+    assert_grad_bar("thin surfaces, screen-space gradients", g2gpu, g2ref, mag)
+    pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
+    assert_grad_bar("thin surfaces, parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
 
 
 def test_render_matches_oracle_tiny():
@@ -173,23 +183,22 @@ def test_render_backward_matches_oracle_tiny(tile):
     grads = g.zeros_like()
     vb.render_bwd(g, grads, dimg=torch.tensor(dimg, device="cuda"))
     torch.cuda.synchronize()
-    g2 = vb.g2.cpu().numpy()
-    g2gpu = np.concatenate([g2[0], g2[1], g2[2][:, :1]], 1).astype(np.float64)
-    ok2, used2, worst2 = grad_check(g2gpu, g2ref, mag)
+    assert_grad_bar(f"tile {tile}, screen-space gradients", _screen_grads(vb), g2ref, mag)
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
-    near_clamp = (np.abs(pr[:, 13:16]) < 1e-4).any(1)
-    gg = grad_planes_gpu(grads)
-    ok, used, worst = grad_check(gg, gref, param_condition(sc, ca, cam.width, cam.height, dec, mag))
-    ok[near_clamp] = True
-    _, _, norms = grad_report(gg, gref)
-    print(f"screen-space grads: worst err/bound {worst2:.3f} ({used2} of {g2gpu.size} use the FP32 allowance); "
-          f"param grads worst {worst:.3f} ({used} use it), normwise {norms}; "
-          f"colour-clamp-adjacent Gaussians excluded: {near_clamp.sum()}")
-    assert ok2.all(), f"{(~ok2).sum()} screen-space gradient elements out of tolerance"
-    assert ok.all(), f"{(~ok).sum()} of {ok.size} parameter gradient elements out of tolerance"
+    assert_grad_bar(f"tile {tile}, parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
 
 
 def test_end_to_end_loss_and_gradients_tiny():
+    """Render, Eq. 4 loss and its gradient, backward, all on the GPU, against
+    the oracle's: the loss within 1e-5 relative and every parameter gradient
+    element within the bar.  The Eq. 4 gradient is mean-reduced (each pixel
+    term ~1 / 3HW), so both sides are scaled by 3HW (the sum-reduced loss)
+    before the per-element check, which keeps the 1e-6 floor from passing
+    everything.  The GPU's dL/dI comes from its own image; near a flagged
+    pixel (a decision FP32 and FP64 may take differently) it can differ by far
+    more than rounding within the 11 x 11 SSIM window, so Gaussians whose
+    pixel box reaches a flagged pixel's window are waived and counted."""
     base = S.tiny_scene()
     cam = S.tiny_camera()
     ca = cam.as_array()
@@ -198,7 +207,7 @@ def test_end_to_end_loss_and_gradients_tiny():
     p = S.perturb(base)
     dec, _, sc, (img, T, nc, mg) = _oracle_all(p, cam)
     L_ref, dimg_ref = oracle.loss(img, gt, 0.2)
-    gref, _ = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, dimg_ref)
+    gref, _, mag = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, dimg_ref, with_magnitude=True)
     vb, g = gpu_view(p, cam)
     gt_t = torch.tensor(gt, dtype=torch.float32, device="cuda")
     vb.loss_fwd_bwd(gt_t, 0.2)
@@ -206,12 +215,14 @@ def test_end_to_end_loss_and_gradients_tiny():
     vb.render_bwd(g, grads)
     torch.cuda.synchronize()
     L = float(vb.loss.item())
-    flagged = int((mg < MARGIN_FLAG).sum())
-    gg = grad_planes_gpu(grads)
-    _, worst, norms = grad_report(gg, gref)
-    print(f"loss {L:.7f} vs {L_ref:.7f}; flagged pixels {flagged}; normwise grad err {norms}")
+    flagged = mg < MARGIN_FLAG
+    waive = colour_clamp_waiver(oracle.project(sc, ca, cam.width, cam.height, dec.visible))
+    waive[near_flagged(dec, flagged)] = True
+    scale = 3 * cam.width * cam.height
+    print(f"loss {L:.7f} vs {L_ref:.7f} (rel {abs(L - L_ref) / L_ref:.1e}); flagged pixels {int(flagged.sum())}")
     assert abs(L - L_ref) <= 1e-5 * L_ref
-    assert max(norms.values()) <= 1e-3
+    assert_grad_bar("end to end (x 3HW), parameter gradients", scale * grad_planes_gpu(grads), scale * gref,
+                    scale * param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=waive)
 
 
 def test_sh_degrees_and_background():
@@ -310,10 +321,12 @@ def test_autograd_function_matches_oracle_gradient():
     w = S.random_grad_image(3, cam.height, cam.width, seed=9)
     w[:, mg < MARGIN_FLAG] = 0.0
     (img * torch.tensor(w, device="cuda")).sum().backward()
-    gref, _ = oracle.render_bwd(sc, cam.as_array(), cam.width, cam.height, dec, w.astype(np.float64))
+    ca = cam.as_array()
+    gref, _, mag = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, w.astype(np.float64), with_magnitude=True)
     grads = gsr.Gaussians(*(t.grad for t in leaves))
-    _, worst, norms = grad_report(grad_planes_gpu(grads), gref)
-    assert max(norms.values()) <= 1e-4, norms
+    pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
+    assert_grad_bar("autograd.Function, parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
 
 
 def test_capacity_overflow_is_reported_not_written():
@@ -367,57 +380,49 @@ def test_empty_and_degenerate_inputs():
 
 
 @pytest.mark.parametrize("order", ["morton", "input"])
-def test_full_size_keys_and_sampled_rows(order):
-    """300k Gaussians, 1200 x 680, in the launch configuration the benchmark times
-    (store in Morton order of the means, as the benchmark keeps it, or in the
-    generator's order): keys bit-exact over the whole frame; image and
-    gradients on sampled rows."""
+def test_full_size_frame(order):
+    """300k Gaussians, 1200 x 680, in the launch configuration the benchmark
+    times (store in Morton order of the means, as the benchmark keeps it, or in
+    the generator's order): keys bit-exact, and the image and every parameter
+    gradient over the whole frame (all 680 rows; the oracle takes ~10 s of
+    host time for it) within their bars."""
     p = S.perturb(S.room_scene(300_000))
     if order == "morton":
         p = morton_permuted(p, S.ROOM_LO, S.ROOM_HI)
     cam = S.replica_camera(0)
     vb, g = gpu_view(p, cam)
-    rows = [(0, 2), (339, 341), (678, 680)]
     ca = cam.as_array()
     dec = oracle.decide(p.mean_op, p.quat, p.logscale, ca, cam.width, cam.height)
     ks, vs, rg = oracle.keys(dec, cam.width, cam.height)
     _check_keys(vb, dec, (ks, vs, rg))
     sc = oracle_scene(p)
-    gi = vb.img.cpu().numpy()
-    w = np.zeros((3, cam.height, cam.width), np.float32)
-    wr = S.random_grad_image(3, cam.height, cam.width, seed=12)
-    for r in rows:
-        img, T, nc, mg = oracle.render(sc, ca, cam.width, cam.height, dec, rows=r)
-        fl = mg[r[0]:r[1]] < MARGIN_FLAG
-        err = np.abs(gi[:, r[0]:r[1]] - img[:, r[0]:r[1]]).max(0)
-        assert err[~fl].max() <= IMG_ATOL, r
-        ww = wr[:, r[0]:r[1]].copy()
-        ww[:, fl] = 0
-        w[:, r[0]:r[1]] = ww
-    gref = np.zeros((p.n, 60))
-    mag = np.zeros((p.n, 9))
-    for r in rows:
-        gr, _, mg2 = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, w.astype(np.float64), rows=r,
-                                       with_magnitude=True)
-        gref += gr
-        mag += mg2
+    img, T, nc, mg = oracle.render(sc, ca, cam.width, cam.height, dec)
+    flagged = mg < MARGIN_FLAG
+    err = np.abs(vb.img.cpu().numpy() - img).max(0)
+    terr = np.abs(vb.T_final.cpu().numpy() - T)
+    print(f"full frame ({order}): pairs {len(ks)}, visible {int(dec.visible.sum())}, image max err "
+          f"{err[~flagged].max():.2e}, T_final max err {terr[~flagged].max():.2e}, flagged pixels {int(flagged.sum())}")
+    assert flagged.sum() <= 0.002 * flagged.size
+    assert err[~flagged].max() <= IMG_ATOL
+    assert terr[~flagged].max() <= IMG_ATOL
+    w = S.random_grad_image(3, cam.height, cam.width, seed=12)
+    w[:, flagged] = 0.0
+    gref, g2ref, mag = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, w.astype(np.float64),
+                                         with_magnitude=True)
     grads = g.zeros_like()
     vb.render_bwd(g, grads, dimg=torch.tensor(w, device="cuda"))
     torch.cuda.synchronize()
+    assert_grad_bar(f"full frame ({order}), screen-space gradients", _screen_grads(vb), g2ref, mag)
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
-    gg = grad_planes_gpu(grads)
-    ok, used, worst = grad_check(gg, gref, param_condition(sc, ca, cam.width, cam.height, dec, mag))
-    ok[(np.abs(pr[:, 13:16]) < 1e-4).any(1)] = True
-    _, _, norms = grad_report(gg, gref)
-    print(f"full size: pairs {len(ks)}, grad worst err/bound {worst:.3f} ({used} use the FP32 allowance), "
-          f"normwise {norms}")
-    assert ok.all(), f"{(~ok).sum()} gradient elements out of tolerance"
+    assert_grad_bar(f"full frame ({order}), parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
 
 
-def test_large_scene_keys_and_sampled_rows():
+def test_large_scene_frame():
     """The densify workload's frame: 1M Gaussians in the Morton-ordered store,
-    1920 x 1080, fx = fy = 1000: keys, order and ranges bit-exact over the
-    whole frame; the image on sampled rows within the image bar."""
+    1920 x 1080, fx = fy = 1000: keys, order and ranges bit-exact, and the
+    image and every parameter gradient over the whole frame within their
+    bars."""
     p = morton_permuted(S.perturb(S.room_scene(1_000_000, seed=0), 0.05, seed=1), S.ROOM_LO, S.ROOM_HI)
     pos, yaw = S.trajectory(0)
     cam = S.pose_camera(pos, yaw, 1000.0, 1000.0, 1920, 1080)
@@ -427,13 +432,24 @@ def test_large_scene_keys_and_sampled_rows():
     ks, vs, rg = oracle.keys(dec, cam.width, cam.height)
     _check_keys(vb, dec, (ks, vs, rg))
     sc = oracle_scene(p)
-    gi = vb.img.cpu().numpy()
-    for r in [(0, 2), (539, 541), (1078, 1080)]:
-        img, _, _, mg = oracle.render(sc, ca, cam.width, cam.height, dec, rows=r)
-        fl = mg[r[0]:r[1]] < MARGIN_FLAG
-        err = np.abs(gi[:, r[0]:r[1]] - img[:, r[0]:r[1]]).max(0)
-        assert err[~fl].max() <= IMG_ATOL, r
-    print(f"large scene: {len(ks)} pairs, {int((dec.visible > 0).sum())} visible")
+    img, _, _, mg = oracle.render(sc, ca, cam.width, cam.height, dec)
+    flagged = mg < MARGIN_FLAG
+    err = np.abs(vb.img.cpu().numpy() - img).max(0)
+    print(f"large scene: {len(ks)} pairs, {int((dec.visible > 0).sum())} visible, image max err "
+          f"{err[~flagged].max():.2e}, flagged pixels {int(flagged.sum())}")
+    assert flagged.sum() <= 0.002 * flagged.size
+    assert err[~flagged].max() <= IMG_ATOL
+    w = S.random_grad_image(3, cam.height, cam.width, seed=13)
+    w[:, flagged] = 0.0
+    gref, g2ref, mag = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, w.astype(np.float64),
+                                         with_magnitude=True)
+    grads = g.zeros_like()
+    vb.render_bwd(g, grads, dimg=torch.tensor(w, device="cuda"))
+    torch.cuda.synchronize()
+    assert_grad_bar("large scene, screen-space gradients", _screen_grads(vb), g2ref, mag)
+    pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
+    assert_grad_bar("large scene, parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
 
 
 def test_graph_replay_matches_eager():

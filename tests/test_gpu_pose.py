@@ -1,17 +1,19 @@
 """Camera pose gradient (gsr_pose_bwd) against the FP64 oracle, and a
 photometric pose refinement that uses it.
 
-Bars: per element |g - g*| <= max(1e-3 |g*|, 1e-6) + 2^-15 C, C the
-element's condition magnitude (the oracle's per-Gaussian parts pushed through
-the absolute value of their Jacobian in the screen-space gradients, times
-those gradients' own condition magnitudes), as for the parameter gradients.
+Bars: per element |g - g*| <= max(1e-3 |g*|, 1e-6), with the loss-driven
+cases scaled by 3HW (sum-reduced loss); a miss is accepted only as a
+cancellation case within 2^-15 C, C the element's condition magnitude (the
+oracle's per-Gaussian parts pushed through the absolute value of their
+Jacobian in the screen-space gradients, times those gradients' own
+condition magnitudes), as for the parameter gradients.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import MARGIN_FLAG, gpu_view, grad_check, morton_permuted, oracle_scene, to_gpu
+from parity_helpers import MARGIN_FLAG, assert_grad_bar, gpu_view, morton_permuted, oracle_scene, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -68,9 +70,8 @@ def test_pose_chain_matches_oracle():
     got = _gpu_pose(vb, g)
     ref = oracle.pose_grad(sc, ca, cam.width, cam.height, dec, g2)
     cond = _pose_condition(sc, ca, cam.width, cam.height, dec, np.abs(g2))
-    ok, used, worst = grad_check(got[None], ref[None], cond[None])
-    print(f"pose chain: worst err/bound {worst:.3f} ({used} use the FP32 allowance)\n got {got}\n ref {ref}")
-    assert ok.all()
+    print(f"pose chain:\n got {got}\n ref {ref}")
+    assert_grad_bar("pose chain, 15 pose values", got[None], ref[None], cond[None])
 
 
 def test_pose_gradient_end_to_end_matches_oracle():
@@ -95,11 +96,11 @@ def test_pose_gradient_end_to_end_matches_oracle():
     vb, g = gpu_view(base, cam)
     vb.blend_bwd(dimg=torch.tensor(dimg, dtype=torch.float32, device="cuda"))
     got = _gpu_pose(vb, g)
-    ok, used, worst = grad_check(got[None], ref[None], cond[None])
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    print(f"pose end to end: normwise {rel:.2e}, worst err/bound {worst:.3f} ({used} use the allowance), "
-          f"flagged pixels {(mg < MARGIN_FLAG).sum()}\n got {got}\n ref {ref}")
-    assert ok.all()
+    print(f"pose end to end: normwise {rel:.2e}, flagged pixels {(mg < MARGIN_FLAG).sum()}\n got {got}\n ref {ref}")
+    # mean-reduced loss: scaled by 3HW (the sum-reduced loss) for the per-element bar
+    s = 3 * cam.width * cam.height
+    assert_grad_bar("pose end to end (x 3HW), 15 pose values", s * got[None], s * ref[None], s * cond[None])
     assert rel <= 1e-3
 
 
@@ -128,10 +129,10 @@ def test_pose_gradient_full_size():
     vb, g = gpu_view(base, cam)
     vb.blend_bwd(dimg=torch.tensor(dimg, dtype=torch.float32, device="cuda"))
     got = _gpu_pose(vb, g)
-    ok, used, worst = grad_check(got[None], ref[None], cond[None])
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    print(f"pose full size: normwise {rel:.2e}, worst err/bound {worst:.3f} ({used} use the allowance)")
-    assert ok.all()
+    print(f"pose full size: normwise {rel:.2e}")
+    s = 3 * cam.width * cam.height
+    assert_grad_bar("pose full size (x 3HW), 15 pose values", s * got[None], s * ref[None], s * cond[None])
     assert rel <= 1e-3
 
 

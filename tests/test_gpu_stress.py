@@ -2,15 +2,16 @@
 nearly opaque Gaussians on the optical axis (opacity up to the 0.99 alpha
 clamp), where T_i = T_{i+1} / (1 - alpha_i) divides by numbers down to 0.01.
 The gradient bar is the same as for the plain tiny scene: per element
-|g - g*| <= max(1e-3 |g*|, 1e-6) + 2^-15 C and normwise <= 1e-3 per group,
-against the FP64 oracle; the image within 1e-4 outside flagged pixels."""
+|g - g*| <= max(1e-3 |g*|, 1e-6) against the FP64 oracle, cancellation cases
+counted and bounded (parity_helpers.assert_grad_bar); the image within 1e-4
+outside flagged pixels."""
 import numpy as np
 import pytest
 
 import oracle
 import synthetic as S
-from parity_helpers import (IMG_ATOL, MARGIN_FLAG, gpu_view, grad_check, grad_planes_gpu, grad_report, oracle_scene,
-                            param_condition)
+from parity_helpers import (IMG_ATOL, MARGIN_FLAG, assert_grad_bar, colour_clamp_waiver, gpu_view, grad_planes_gpu,
+                            oracle_scene, param_condition)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,15 +55,9 @@ def test_stacked_opaque_gaussians(logit):
     vb.render_bwd(g, grads, dimg=torch.tensor(dimg, device="cuda"))
     torch.cuda.synchronize()
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
-    near_clamp = (np.abs(pr[:, 13:16]) < 1e-4).any(1)
-    gg = grad_planes_gpu(grads)
-    ok, used, worst = grad_check(gg, gref, param_condition(sc, ca, cam.width, cam.height, dec, mag))
-    ok[near_clamp] = True
-    _, _, norms = grad_report(gg, gref)
     clamped = int((pr[:, 5] >= 0.99).sum())
     print(f"logit {logit}: image err {err[~flagged].max():.2e} ({flagged.sum()} flagged); min T "
-          f"{T.min():.2e}; Gaussians at the alpha clamp {clamped}; grad worst err/bound {worst:.3f} "
-          f"({used} use the FP32 allowance); normwise {norms}")
+          f"{T.min():.2e}; Gaussians at the alpha clamp {clamped}")
     assert err[~flagged].max() <= IMG_ATOL
-    assert ok.all(), f"{(~ok).sum()} gradient elements out of tolerance"
-    assert max(norms.values()) <= 1e-3
+    assert_grad_bar(f"stack logit {logit}, parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
