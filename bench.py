@@ -196,6 +196,74 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+class _NvmlCtypes:
+    """The few read-only NVML queries the clock sampler makes, through ctypes
+    on libnvidia-ml (for hosts without the pynvml module)."""
+    NVML_CLOCK_SM = 1
+
+    class NVMLError(Exception):
+        pass
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc):
+        if rc != 0:
+            raise self.NVMLError(f"NVML error {rc}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2())
+
+    def nvmlDeviceGetCount(self):
+        n = self.c.c_uint()
+        self._ok(self.lib.nvmlDeviceGetCount_v2(self.c.byref(n)))
+        return n.value
+
+    def nvmlDeviceGetHandleByIndex(self, k):
+        h = self.c.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.c.c_uint(k), self.c.byref(h)))
+        return h
+
+    def nvmlDeviceGetUUID(self, h):
+        buf = self.c.create_string_buffer(96)
+        self._ok(self.lib.nvmlDeviceGetUUID(h, buf, self.c.c_uint(96)))
+        return buf.value.decode()
+
+    def nvmlDeviceGetPciInfo(self, h):
+        raise self.NVMLError("PCI info not queried through ctypes")
+
+    def _uint(self, fn, h, *args):
+        v = self.c.c_uint()
+        self._ok(fn(h, *args, self.c.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._uint(self.lib.nvmlDeviceGetClockInfo, h, self.c.c_int(kind))
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._uint(self.lib.nvmlDeviceGetMaxClockInfo, h, self.c.c_int(kind))
+
+    def nvmlDeviceGetPowerUsage(self, h):
+        return self._uint(self.lib.nvmlDeviceGetPowerUsage, h)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.c.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._ok(fn(h, self.c.byref(v)))
+        return v.value
+
+
+def _nvml_module():
+    try:
+        import pynvml
+        return pynvml
+    except ImportError:
+        return _NvmlCtypes()
+
+
 class ClockSampler:
     """SM clock, power and clock-event reasons of the benchmarked GPU, sampled
     every few milliseconds by a background thread through NVML's read-only
@@ -216,31 +284,43 @@ class ClockSampler:
         self.thread = None
         self.smi = None
         self.source = None
+        self.nvml_error = None
 
     def _nvml_handle(self):
-        import pynvml
+        """NVML handle of the CUDA device: NVML numbers every GPU of the node,
+        so the device is found by its UUID (else its PCI bus id)."""
         import torch
+        pynvml = _nvml_module()
         pynvml.nvmlInit()
         if self.device is None:
             self.device = torch.cuda.current_device()
-        uuid = str(torch.cuda.get_device_properties(self.device).uuid)
-        try:
-            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
-        except pynvml.NVMLError:
-            props = torch.cuda.get_device_properties(self.device)
-            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
-            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+        props = torch.cuda.get_device_properties(self.device)
+        want = str(props.uuid).lower().replace("gpu-", "")
+        bus = (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        for k in range(pynvml.nvmlDeviceGetCount()):
+            h = pynvml.nvmlDeviceGetHandleByIndex(k)
+            uuid = pynvml.nvmlDeviceGetUUID(h)
+            uuid = (uuid.decode() if isinstance(uuid, bytes) else str(uuid)).lower().replace("gpu-", "")
+            if uuid == want:
+                return pynvml, h
+            try:
+                pci = pynvml.nvmlDeviceGetPciInfo(h)
+            except Exception:
+                continue
+            if (pci.domain, pci.bus, pci.device) == bus:
+                return pynvml, h
+        raise RuntimeError(f"no NVML device with UUID {want} or PCI {bus}")
 
     def start(self):
         import threading
         try:
             nv, h = self._nvml_handle()
-        except Exception:
-            nv = None
+        except Exception as e:  # recorded in the clock record; nvidia-smi is the fallback
+            nv, self.nvml_error = None, f"{type(e).__name__}: {e}"[:200]
         if nv is None:
             self._start_smi()
             return
-        self.source = "NVML"
+        self.source = "NVML (read-only queries, " + ("ctypes" if isinstance(nv, _NvmlCtypes) else "pynvml") + ")"
 
         def run():
             get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons",
@@ -259,6 +339,7 @@ class ClockSampler:
 
     def _start_smi(self):
         self.source = "nvidia-smi -lms 100"
+        self.period = 0.1
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active")
         try:
@@ -303,7 +384,8 @@ class ClockSampler:
                 "power_w_max": max(x[3] for x in self.samples) if self.samples else None,
                 "samples_in_timed_region": len(inside),
                 "sm_mhz_timed_region": statistics.median(inside) if inside else None,
-                "window": "warm-up, the timed steps, the stage-timing and e2e loops"}
+                "window": "warm-up, the timed steps, the stage-timing and e2e loops",
+                **({"nvml_error": self.nvml_error} if self.nvml_error else {})}
 
 
 def count_kernel_nodes(graphs) -> int:

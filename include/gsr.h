@@ -107,12 +107,21 @@ typedef struct {
  *                     box y (u32 bits: y0 | y1 << 16); inclusive pixel box
  *   rgb_depth float4  r, g, b (SH colour, clamped at 0), camera depth z
  *   ntiles    u32     tiles the box touches; 0 = culled
+ *   uv_lo     float2  optional (NULL: not used): the residuals u64 - u and
+ *                     v64 - v of the projected mean evaluated in FP64 (the
+ *                     camera widened), so that u + uv_lo.x is the mean to
+ *                     about 1e-6 pixel where the FP32 u alone is good to an
+ *                     ulp of u (~1e-4 pixel at u ~ 1000).  u, v, the conic
+ *                     and the box stay the FP32 decision chain's (keys and
+ *                     culling are unchanged); when uv_lo is set, the blends
+ *                     evaluate alpha at the FP64 position.  8-byte aligned.
  * Records of culled Gaussians (ntiles == 0) are left unwritten. */
 typedef struct {
     float *xy_conic;
     float *c_op_box;
     float *rgb_depth;
     uint32_t *ntiles;
+    float *uv_lo;
 } gsr_proj;
 
 /* Screen-space gradient buffer (caller-owned, 3 float4 per Gaussian):

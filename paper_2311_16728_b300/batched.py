@@ -49,12 +49,14 @@ class BatchedWindow:
         self.c_op_box = torch.empty(m, 4, **f32)
         self.rgb_depth = torch.empty(m, 4, **f32)
         self.ntiles = torch.zeros(m, dtype=torch.int32, device=dev)
+        self.uv_lo = torch.zeros(m, 2, **f32)
         # the visible records gathered densely by the binning (the pairs'
         # values index these; rec_to_c maps a record to its position), so the
         # persistent launch and the chain rule touch arrays that stay in L2
         self.cxy = torch.empty(m, 4, **f32)
         self.ccb = torch.empty(m, 4, **f32)
         self.crd = torch.empty(m, 4, **f32)
+        self.cuv = torch.zeros(m, 2, **f32)
         self.rec_to_c = torch.zeros(m, dtype=torch.int32, device=dev)
         self.tiles = sum(n_tiles(v[0], self.tiling) for v in views)
         self.ranges = torch.zeros(self.tiles, 2, dtype=torch.int32, device=dev)
@@ -108,10 +110,11 @@ class BatchedWindow:
 
     def proj(self) -> L.gsr_proj:
         return L.gsr_proj(self.xy_conic.data_ptr(), self.c_op_box.data_ptr(), self.rgb_depth.data_ptr(),
-                          self.ntiles.data_ptr())
+                          self.ntiles.data_ptr(), self.uv_lo.data_ptr())
 
     def compact(self) -> L.gsr_proj:
-        return L.gsr_proj(self.cxy.data_ptr(), self.ccb.data_ptr(), self.crd.data_ptr(), self.rec_to_c.data_ptr())
+        return L.gsr_proj(self.cxy.data_ptr(), self.ccb.data_ptr(), self.crd.data_ptr(), self.rec_to_c.data_ptr(),
+                          self.cuv.data_ptr())
 
     def grad2d(self) -> L.gsr_grad2d:
         return L.gsr_grad2d(self.g2[0].data_ptr(), self.g2[1].data_ptr(), self.g2[2].data_ptr())

@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(128) batched_preprocess_kernel(GaussK g, const
                                                                  float4 *__restrict__ xy_conic,
                                                                  float4 *__restrict__ c_op_box,
                                                                  float4 *__restrict__ rgb_depth,
-                                                                 uint32_t *__restrict__ ntiles) {
+                                                                 uint32_t *__restrict__ ntiles,
+                                                                 float2 *__restrict__ uv_lo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(128) batched_preprocess_kernel(GaussK g, const
             xy_conic[r] = make_float4(c.u, c.v, A, B);
             c_op_box[r] = make_float4(C, op, __uint_as_float(bx), __uint_as_float(by));
             rgb_depth[r] = make_float4(rgb[0], rgb[1], rgb[2], c.zc);
+            if (uv_lo) uv_lo[r] = uv_residual(mo, cam, c.u, c.v);
             ntiles[r] = (uint32_t)((c.x1 / cam.tw - c.x0 / cam.tw + 1) * (c.y1 / cam.th - c.y0 / cam.th + 1));
         }
     }
@@ -135,6 +137,7 @@ struct IterView {
 
 struct IterArgs {
     const float4 *xy, *cb, *rd;
+    const float2 *uv;  // position residuals of the records (NULL: none)
     const uint32_t *vals;
     const uint2 *ranges;
     int tw, th;
@@ -221,6 +224,7 @@ __device__ __forceinline__ RenderArgs view_args(const IterArgs &a, const IterVie
     r.xy_conic = a.xy;
     r.c_op_box = a.cb;
     r.rgb_depth = a.rd;
+    r.uv_lo = a.uv;
     r.vals = a.vals;
     r.ranges = a.ranges;
     r.W = v.W;
@@ -512,11 +516,15 @@ extern "C" int32_t gsr_batched_preprocess(const gsr_gaussians *g, const gsr_came
         set_error("gsr_batched_preprocess: output records must be non-NULL and 16-byte aligned");
         return GSR_ERR_INVALID_ARG;
     }
+    if (out->uv_lo && (reinterpret_cast<uintptr_t>(out->uv_lo) & 7u)) {
+        set_error("gsr_batched_preprocess: uv_lo must be 8-byte aligned");
+        return GSR_ERR_INVALID_ARG;
+    }
     PoseGroups PG;
     pose_groups(cams, nviews, PG);
     batched_preprocess_kernel<<<(unsigned)((g->n + 127) / 128), 128, 0, as_cuda(stream)>>>(
         make_gk(g), V, PG, reinterpret_cast<float4 *>(out->xy_conic), reinterpret_cast<float4 *>(out->c_op_box),
-        reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles);
+        reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles, reinterpret_cast<float2 *>(out->uv_lo));
     return check_launch("batched_preprocess_kernel");
 }
 
@@ -564,6 +572,7 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     a.xy = reinterpret_cast<const float4 *>(proj->xy_conic);
     a.cb = reinterpret_cast<const float4 *>(proj->c_op_box);
     a.rd = reinterpret_cast<const float4 *>(proj->rgb_depth);
+    a.uv = reinterpret_cast<const float2 *>(proj->uv_lo);
     a.vals = vals;
     a.ranges = reinterpret_cast<const uint2 *>(tile_ranges);
     a.tw = tiling->tile_w;

@@ -167,6 +167,8 @@ struct Gather {
     const float4 *xy, *cb, *rd;
     float4 *cxy, *ccb, *crd;
     uint32_t *rec_to_c;
+    const float2 *uv;  // position residuals (both NULL: none)
+    float2 *cuv;
 };
 
 // Pass 2: the visible records in index order (order[]), the first candidate
@@ -233,6 +235,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) compact_kernel(const uint32_t
                 gt.cxy[p] = __ldg(gt.xy + e);
                 gt.ccb[p] = __ldg(gt.cb + e);
                 gt.crd[p] = __ldg(gt.rd + e);
+                if (gt.cuv) gt.cuv[p] = __ldg(gt.uv + e);
                 gt.rec_to_c[e] = (uint32_t)p;
             }
         }
@@ -952,6 +955,10 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
         set_error("gsr_batched_bin_sort: compact record arrays must be non-NULL and 16-byte aligned");
         return GSR_ERR_INVALID_ARG;
     }
+    if (compact && proj->uv_lo && (!compact->uv_lo || (reinterpret_cast<uintptr_t>(compact->uv_lo) & 7u))) {
+        set_error("gsr_batched_bin_sort: records with uv_lo need an 8-byte aligned compact uv_lo");
+        return GSR_ERR_INVALID_ARG;
+    }
     const gsr_proj *rp = compact ? compact : proj;  // the records the pairs index
     const float4 *xy = reinterpret_cast<const float4 *>(rp->xy_conic);
     const float4 *cb = reinterpret_cast<const float4 *>(rp->c_op_box);
@@ -966,7 +973,8 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
         gt = Gather{reinterpret_cast<const float4 *>(proj->xy_conic), reinterpret_cast<const float4 *>(proj->c_op_box),
                     reinterpret_cast<const float4 *>(proj->rgb_depth), reinterpret_cast<float4 *>(compact->xy_conic),
                     reinterpret_cast<float4 *>(compact->c_op_box), reinterpret_cast<float4 *>(compact->rgb_depth),
-                    compact->ntiles};
+                    compact->ntiles, reinterpret_cast<const float2 *>(proj->uv_lo),
+                    proj->uv_lo ? reinterpret_cast<float2 *>(compact->uv_lo) : nullptr};
     auto compact_k = L.scan_items == kScanItems ? compact_kernel<kScanItems> : compact_kernel<kScanItemsBig>;
     compact_k<<<sb, kScanThreads, 0, st>>>(proj->ntiles, n, vis_sums, cand_sums, L.scan_blocks, order, coff, d_nvis,
                                            d_ncand, d_status, gt);

@@ -230,6 +230,64 @@ __device__ __forceinline__ void chain_conic_opacity(const Chain &c, float logit,
     op = FD(1.0f, FA(1.0f, chain_exp(-logit)));
 }
 
+// The projected mean beyond FP32: the chain's u, v carry an error of about
+// an ulp of u (~1e-4 pixel at u ~ 1000), which moves alpha by ~1e-4 relative
+// for a splat a pixel wide.  The same projection, u = fx X / Z + cx with
+// X = R mean + t from the FP32 inputs, is evaluated in double-float
+// arithmetic (each value an unevaluated sum hi + lo of two floats, ~2^-44
+// relative): products split exactly by FMA (TwoProduct), sums by Knuth's
+// TwoSum, the division by one correction step, as in Dekker (1971).  The
+// residuals against the chain's u, v let the blends evaluate alpha at the
+// mean to ~1e-6 pixel; the chain keeps deciding boxes, keys and culling.
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+    s = FA(a, b);
+    const float bb = FS(s, a);
+    e = FA(FS(a, FS(s, bb)), FS(b, bb));
+}
+
+// (hi, lo) += a b
+__device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float b) {
+    const float p = FM(a, b), pe = __fmaf_rn(a, b, -p);
+    float s, se;
+    df_two_sum(hi, p, s, se);
+    hi = s;
+    lo = FA(lo, FA(se, pe));
+}
+
+// R[3 r .. 3 r + 2] . mean + t[r] as hi + lo
+__device__ __forceinline__ void df_row(const float *R, float t, const float4 mo, float &hi, float &lo) {
+    hi = t;
+    lo = 0.0f;
+    df_add_prod(hi, lo, R[0], mo.x);
+    df_add_prod(hi, lo, R[1], mo.y);
+    df_add_prod(hi, lo, R[2], mo.z);
+    const float s = FA(hi, lo);  // renormalise
+    lo = FS(lo, FS(s, hi));
+    hi = s;
+}
+
+// residual of f (X / Z) + c against the FP32 value w (near it)
+__device__ __forceinline__ float df_screen_residual(float f, float c, float xh, float xl, float zh, float zl,
+                                                    float w) {
+    const float q1 = FD(xh, zh);
+    const float p = FM(q1, zh), pe = __fmaf_rn(q1, zh, -p);
+    const float r = FA(FS(FS(xh, p), pe), FS(xl, FM(q1, zl)));  // X - q1 Z
+    const float q2 = FD(r, zh);                                 // X / Z = q1 + q2
+    const float m = FM(f, q1), me = __fmaf_rn(f, q1, -m);
+    float s, se;
+    df_two_sum(m, c, s, se);
+    return FA(FS(s, w), FA(FA(se, me), FM(f, q2)));
+}
+
+__device__ __forceinline__ float2 uv_residual(const float4 mo, const CamK &cam, float u, float v) {
+    float xh, xl, yh, yl, zh, zl;
+    df_row(cam.R, cam.t[0], mo, xh, xl);
+    df_row(cam.R + 3, cam.t[1], mo, yh, yl);
+    df_row(cam.R + 6, cam.t[2], mo, zh, zl);
+    return make_float2(df_screen_residual(cam.fx, cam.cx, xh, xl, zh, zl, u),
+                       df_screen_residual(cam.fy, cam.cy, yh, yl, zh, zl, v));
+}
+
 // Tile cull.  A (Gaussian, tile) pair is kept when opacity exp(-q_min / 2)
 // >= 0.5 / 255, q_min being the continuous minimum of d^T Sigma'^-1 d over
 // R = tile x pixel box (0 when the mean lies in R, else the least of R's four

@@ -13,7 +13,8 @@ namespace gsr {
 __global__ void __launch_bounds__(256, 3) preprocess_fwd_kernel(GaussK g, CamK cam, float4 *__restrict__ xy_conic,
                                                              float4 *__restrict__ c_op_box,
                                                              float4 *__restrict__ rgb_depth,
-                                                             uint32_t *__restrict__ ntiles) {
+                                                             uint32_t *__restrict__ ntiles,
+                                                             float2 *__restrict__ uv_lo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < g.n;
     Chain c;
@@ -23,6 +24,7 @@ __global__ void __launch_bounds__(256, 3) preprocess_fwd_kernel(GaussK g, CamK c
         const float4 mo = __ldg(g.mean_op + i), q = __ldg(g.quat + i), ls = __ldg(g.logscale + i);
         vis = decide_chain(mo, q, ls, cam, c);
         if (vis) {
+            if (uv_lo) uv_lo[i] = uv_residual(mo, cam, c.u, c.v);
             float A, B, C, op;
             chain_conic_opacity(c, mo.w, A, B, C, op);
             // colour: SH at the unit view direction (mean - camera centre)
@@ -150,12 +152,16 @@ extern "C" int32_t gsr_preprocess(const gsr_gaussians *g, const gsr_camera *cam,
         set_error("gsr_preprocess: output record pointers must be non-NULL and 16-byte aligned");
         return GSR_ERR_INVALID_ARG;
     }
+    if (out->uv_lo && (reinterpret_cast<uintptr_t>(out->uv_lo) & 7u)) {
+        set_error("gsr_preprocess: uv_lo must be 8-byte aligned");
+        return GSR_ERR_INVALID_ARG;
+    }
     const CamK ck = make_camk(cam, tiling);
     const int threads = 256;
     const int64_t blocks = (g->n + threads - 1) / threads;
     preprocess_fwd_kernel<<<(unsigned)blocks, threads, 0, as_cuda(stream)>>>(
         make_gk(g), ck, reinterpret_cast<float4 *>(out->xy_conic), reinterpret_cast<float4 *>(out->c_op_box),
-        reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles);
+        reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles, reinterpret_cast<float2 *>(out->uv_lo));
     return check_launch("preprocess_fwd_kernel");
 }
 

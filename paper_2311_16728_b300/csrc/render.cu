@@ -56,6 +56,7 @@ static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const ui
     a.xy_conic = reinterpret_cast<const float4 *>(proj->xy_conic);
     a.c_op_box = reinterpret_cast<const float4 *>(proj->c_op_box);
     a.rgb_depth = reinterpret_cast<const float4 *>(proj->rgb_depth);
+    a.uv_lo = reinterpret_cast<const float2 *>(proj->uv_lo);
     a.vals = vals;
     a.ranges = reinterpret_cast<const uint2 *>(ranges);
     a.W = cam->width;
@@ -90,6 +91,8 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
     auto kernel = n_blended ? (quad ? render_fwd_kernel<true, true> : render_fwd_kernel<true, false>)
                             : (quad ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
+    // (per device and cheap, not a stream operation: fine during capture)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_fwd_smem(nthr));
     kernel<<<tiles, nthr, render_fwd_smem(nthr), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
     return check_launch("render_fwd_kernel");
 }
@@ -126,6 +129,7 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
         return check_launch("render_bwd_q4_kernel");
     }
     auto kernel = render_bwd_kernel<false>;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_bwd_smem(nthr));
     kernel<<<tiles, nthr, render_bwd_smem(nthr), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
                                                                   grad2d->g1, grad2d->g2);
     return check_launch("render_bwd_kernel");

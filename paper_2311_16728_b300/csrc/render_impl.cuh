@@ -10,6 +10,7 @@ namespace gsr {
 
 struct RenderArgs {
     const float4 *xy_conic, *c_op_box, *rgb_depth;
+    const float2 *uv_lo;  // residuals of the FP64 projected mean (NULL: the FP32 u, v)
     const uint32_t *vals;
     const uint2 *ranges;  // indexed by tile_off + local tile
     int W, H, tw, th, gx, tile_off;
@@ -72,6 +73,16 @@ __device__ __forceinline__ uint2 quad_box_lanes(int x0, int x1, int y0, int y1, 
     return make_uint2(m0, m1);
 }
 
+// Residual of the FP64 projected mean (zero without residuals).  The blends
+// take a pixel's offset as (px - u) - u_lo: px - u is exact or within an ulp
+// of the offset itself near the mean, and subtracting the residual keeps the
+// mean to ~1e-6 pixel where the FP32 u alone carries an ulp of u (~1e-4 pixel
+// at u ~ 1000).  The offset depends on the pixel and the Gaussian only, not
+// on the tiling, so the image stays independent of the tile shape.
+__device__ __forceinline__ float2 mean_residual(const RenderArgs &a, uint32_t gid) {
+    return a.uv_lo ? __ldg(a.uv_lo + gid) : make_float2(0.0f, 0.0f);
+}
+
 // Stages Gaussian gid: exponent coefficients pre-scaled so that
 // exponent_2 = a2 dx^2 + b2 dx dy + c2 dy^2 (= -log2(e) d^T Q d / 2), and the
 // mask of warps (of a block of nwarps) that can see it.  kQuad (16 x 16
@@ -108,10 +119,11 @@ __device__ __forceinline__ bool rect_may_see(float u, float v, float A, float B,
 
 template <bool kQuad>
 __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, int ox, int oy, int nwarps,
-                                            float4 &s_xy, float4 &s_cb, float4 &s_rgb, uint32_t &s_mask,
-                                            uint2 *s_lanes) {
+                                            float4 &s_xy, float4 &s_cb, float4 &s_rgb, float2 &s_lo,
+                                            uint32_t &s_mask, uint2 *s_lanes) {
     const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
     s_rgb = __ldg(a.rgb_depth + gid);
+    s_lo = mean_residual(a, gid);
     const float A = g.z, B = g.w, C = c.x, op = c.y;
     s_xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
     s_cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
@@ -183,39 +195,53 @@ __device__ __forceinline__ void in_box(const float4 cb, const uint2 *lanes, int 
     }
 }
 
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// The exponent and alpha at the thread's two pixels run as one pair in
+// Blackwell's packed FP32 instructions (FFMA2 / FMUL2 / FADD2: each lane
+// rounded to nearest exactly like the scalar operation), one issue slot for
+// both pixels.
 template <bool kQuad>
-__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, const uint2 *lanes, int px,
-                                                 float fpx, float fpy0, float fpy1, int py0, PixAlpha &r) {
+__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, const float2 lo, const uint2 *lanes,
+                                                 int px, float fpx, float2 fpy, int py0, PixAlpha &r) {
     bool b0, b1;
     in_box<kQuad>(cb, lanes, px, py0, b0, b1);
-    const float dx = fpx - g.x;
+    const float dx = FS(FS(fpx, g.x), lo.x);
     const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
-    const float dy0 = fpy0 - g.y, dy1 = fpy1 - g.y;
-    const float e0 = __fmaf_rn(FM(cb.x, dy0), dy0, __fmaf_rn(bdx, dy0, t));
-    const float e1 = __fmaf_rn(FM(cb.x, dy1), dy1, __fmaf_rn(bdx, dy1, t));
-    Eval v0, v1;
-    r.ok0 = b0 && splat_alpha(e0, cb.y, v0);
-    r.ok1 = b1 && splat_alpha(e1, cb.y, v1);
-    r.a0 = v0.alpha;
-    r.a1 = v1.alpha;
+    const float2 dy = __fadd2_rn(__fadd2_rn(fpy, f2(-g.y)), f2(-lo.y));
+    const float2 e = __ffma2_rn(__fmul2_rn(f2(cb.x), dy), dy, __ffma2_rn(f2(bdx), dy, f2(t)));
+    const float2 raw = __fmul2_rn(f2(cb.y), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+    r.a0 = fminf(kAlphaMax, raw.x);
+    r.a1 = fminf(kAlphaMax, raw.y);
+    r.ok0 = b0 && e.x <= 0.0f && r.a0 >= kAlphaMin;
+    r.ok1 = b1 && e.y <= 0.0f && r.a1 >= kAlphaMin;
 }
 
-// front-to-back blend of one evaluated splat into one pixel's state
-__device__ __forceinline__ void blend_fwd(bool ok, float alpha, const float4 &col, uint32_t pos, bool &done,
-                                          float &T, float &C0, float &C1, float &C2, uint32_t &last, uint32_t &nb) {
-    if (!ok || done) return;
-    const float tn = FM(T, FS(1.0f, alpha));
-    if (tn < kTMin) {
-        done = true;
-        return;
-    }
-    const float w = alpha * T;
-    C0 += col.x * w;
-    C1 += col.y * w;
-    C2 += col.z * w;
-    T = tn;
-    last = pos;
-    ++nb;
+// Front-to-back blend of one evaluated splat into the thread's two pixels
+// (a pair: T, C0, C1, C2 hold pixel 0 in .x and pixel 1 in .y), packed like
+// pixel_pair_alpha; a pixel that takes no part (not ok, or already done)
+// keeps its state exactly.
+struct PairFwd {
+    float2 T, C0, C1, C2;
+    uint32_t last0, last1, nb0, nb1;
+    bool done0, done1;
+};
+
+__device__ __forceinline__ void blend_fwd_pair(PairFwd &p, bool ok0, bool ok1, float a0, float a1,
+                                               const float4 &col, uint32_t pos) {
+    bool l0 = ok0 && !p.done0, l1 = ok1 && !p.done1;
+    if (!(l0 || l1)) return;
+    const float2 tn = __fmul2_rn(p.T, __fadd2_rn(f2(1.0f), make_float2(-a0, -a1)));
+    if (l0 && tn.x < kTMin) { p.done0 = true; l0 = false; }
+    if (l1 && tn.y < kTMin) { p.done1 = true; l1 = false; }
+    const float2 w = __fmul2_rn(make_float2(l0 ? a0 : 0.0f, l1 ? a1 : 0.0f), p.T);
+    p.C0 = __ffma2_rn(f2(col.x), w, p.C0);
+    p.C1 = __ffma2_rn(f2(col.y), w, p.C1);
+    p.C2 = __ffma2_rn(f2(col.z), w, p.C2);
+    p.T = make_float2(l0 ? tn.x : p.T.x, l1 ? tn.y : p.T.y);
+    if (l0) { p.last0 = pos; ++p.nb0; }
+    if (l1) { p.last1 = pos; ++p.nb1; }
 }
 
 // ---------------------------------------------------------------- K5
@@ -226,7 +252,8 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
                                                 uint32_t *__restrict__ n_blended, float4 *smem) {
     const int nthr = blockDim.x, nwarps = nthr >> 5;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    uint2 *s_lanes = reinterpret_cast<uint2 *>(smem + 3 * nthr);  // 4 per staged splat (kQuad)
+    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * nthr);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + nthr);  // 4 per staged splat (kQuad)
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * nthr);
     int px, py0, ox, oy;
     thread_pixels(a, tile, px, py0, ox, oy);
@@ -234,22 +261,27 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
     const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py0 + 1 < a.H;
     const uint2 rg = a.ranges[a.tile_off + tile];
     const int begin = (int)rg.x, end = (int)rg.y;
-    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)(py0 + 1);
-    float T0 = 1.0f, T1 = 1.0f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
-    uint32_t last0 = 0, last1 = 0, nb0 = 0, nb1 = 0;
-    bool done0 = !in0, done1 = !in1;
+    const float fpx = (float)px;
+    const float2 fpy = make_float2((float)py0, (float)(py0 + 1));
+    PairFwd p;
+    p.T = make_float2(1.0f, 1.0f);
+    p.C0 = p.C1 = p.C2 = make_float2(0.0f, 0.0f);
+    p.last0 = p.last1 = p.nb0 = p.nb1 = 0u;
+    p.done0 = !in0;
+    p.done1 = !in1;
     for (int base = begin; base < end; base += nthr) {
         // stop the whole tile once every pixel has terminated
-        if (__syncthreads_count(done0 && done1) == nthr) break;
+        if (__syncthreads_count(p.done0 && p.done1) == nthr) break;
         const int idx = base + (int)threadIdx.x;
         if (idx < end) stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x],
-                                          s_rgb[threadIdx.x], s_mask[threadIdx.x], s_lanes + 4 * threadIdx.x);
+                                          s_rgb[threadIdx.x], s_lo[threadIdx.x], s_mask[threadIdx.x],
+                                          s_lanes + 4 * threadIdx.x);
         else s_mask[threadIdx.x] = 0u;
         __syncthreads();
         const int cnt = min(nthr, end - base);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             // warp-ballot early termination: leave once no pixel of the warp accumulates
-            if (__all_sync(0xffffffffu, done0 && done1)) break;
+            if (__all_sync(0xffffffffu, p.done0 && p.done1)) break;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
             // two splats per round: their alphas are independent, so both are
             // evaluated before they are blended in list order
@@ -260,36 +292,33 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
                 const int jb = has_b ? c0 + __ffs(bits) - 1 : ja;
                 if (has_b) bits &= bits - 1;
                 PixAlpha pa, pb;
-                pixel_pair_alpha<kQuad>(s_xy[ja], s_cb[ja], s_lanes + 4 * ja, px, fpx, fpy0, fpy1, py0, pa);
-                pixel_pair_alpha<kQuad>(s_xy[jb], s_cb[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0, pb);
+                pixel_pair_alpha<kQuad>(s_xy[ja], s_cb[ja], s_lo[ja], s_lanes + 4 * ja, px, fpx, fpy, py0, pa);
+                pixel_pair_alpha<kQuad>(s_xy[jb], s_cb[jb], s_lo[jb], s_lanes + 4 * jb, px, fpx, fpy, py0, pb);
                 if (!has_b) pb.ok0 = pb.ok1 = false;
                 const uint32_t posa = (uint32_t)(base - begin + ja + 1), posb = (uint32_t)(base - begin + jb + 1);
-                const float4 cola = s_rgb[ja], colb = s_rgb[jb];
-                blend_fwd(pa.ok0, pa.a0, cola, posa, done0, T0, C00, C01, C02, last0, nb0);
-                blend_fwd(pb.ok0, pb.a0, colb, posb, done0, T0, C00, C01, C02, last0, nb0);
-                blend_fwd(pa.ok1, pa.a1, cola, posa, done1, T1, C10, C11, C12, last1, nb1);
-                blend_fwd(pb.ok1, pb.a1, colb, posb, done1, T1, C10, C11, C12, last1, nb1);
+                blend_fwd_pair(p, pa.ok0, pa.ok1, pa.a0, pa.a1, s_rgb[ja], posa);
+                blend_fwd_pair(p, pb.ok0, pb.ok1, pb.a0, pb.a1, s_rgb[jb], posb);
             }
         }
     }
     const int64_t plane = (int64_t)a.W * a.H;
     if (in0) {
         const int64_t pix = (int64_t)py0 * a.W + px;
-        img[pix] = C00 + T0 * a.bg0;
-        img[plane + pix] = C01 + T0 * a.bg1;
-        img[2 * plane + pix] = C02 + T0 * a.bg2;
-        T_final[pix] = T0;
-        n_contrib[pix] = last0;
-        if (n_blended) n_blended[pix] = nb0;
+        img[pix] = p.C0.x + p.T.x * a.bg0;
+        img[plane + pix] = p.C1.x + p.T.x * a.bg1;
+        img[2 * plane + pix] = p.C2.x + p.T.x * a.bg2;
+        T_final[pix] = p.T.x;
+        n_contrib[pix] = p.last0;
+        if (n_blended) n_blended[pix] = p.nb0;
     }
     if (in1) {
         const int64_t pix = (int64_t)(py0 + 1) * a.W + px;
-        img[pix] = C10 + T1 * a.bg0;
-        img[plane + pix] = C11 + T1 * a.bg1;
-        img[2 * plane + pix] = C12 + T1 * a.bg2;
-        T_final[pix] = T1;
-        n_contrib[pix] = last1;
-        if (n_blended) n_blended[pix] = nb1;
+        img[pix] = p.C0.y + p.T.y * a.bg0;
+        img[plane + pix] = p.C1.y + p.T.y * a.bg1;
+        img[2 * plane + pix] = p.C2.y + p.T.y * a.bg2;
+        T_final[pix] = p.T.y;
+        n_contrib[pix] = p.last1;
+        if (n_blended) n_blended[pix] = p.nb1;
     }
 }
 
@@ -345,15 +374,15 @@ __device__ __forceinline__ void pixel_bwd_update(PixelBwd &p, const Eval &ev, co
 }
 
 template <bool kQuad>
-__device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, const uint2 *lanes, int px,
-                                               float fpx, float fpy0, float fpy1, int py0, bool live0, bool live1,
-                                               SplatBwd &r) {
+__device__ __forceinline__ void splat_bwd_eval(const float4 g, const float4 cb, const float2 lo, const uint2 *lanes,
+                                               int px, float fpx, float fpy0, float fpy1, int py0, bool live0,
+                                               bool live1, SplatBwd &r) {
     bool b0, b1;
     in_box<kQuad>(cb, lanes, px, py0, b0, b1);
-    r.dx = fpx - g.x;
+    r.dx = FS(FS(fpx, g.x), lo.x);
     const float t = FM(FM(g.z, r.dx), r.dx), bdx = FM(g.w, r.dx);
-    r.dy0 = fpy0 - g.y;
-    r.dy1 = fpy1 - g.y;
+    r.dy0 = FS(FS(fpy0, g.y), lo.y);
+    r.dy1 = FS(FS(fpy1, g.y), lo.y);
     const float e0 = __fmaf_rn(FM(cb.x, r.dy0), r.dy0, __fmaf_rn(bdx, r.dy0, t));
     const float e1 = __fmaf_rn(FM(cb.x, r.dy1), r.dy1, __fmaf_rn(bdx, r.dy1, t));
     r.A = g.z * (1.0f / kHalfLog2e);
@@ -403,7 +432,8 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                                                 float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
     const int nthr = blockDim.x, nwarps = nthr >> 5;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    uint2 *s_lanes = reinterpret_cast<uint2 *>(smem + 3 * nthr);  // 4 per staged splat (kQuad)
+    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * nthr);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + nthr);  // 4 per staged splat (kQuad)
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * nthr);
     uint32_t *s_gid = s_mask + nthr;
     uint32_t *s_max = s_gid + nthr;  // 32 entries
@@ -457,7 +487,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
             const uint32_t gid = a.vals[idx];
             s_gid[threadIdx.x] = gid;
             stage_splat<kQuad>(a, gid, ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x],
-                               s_mask[threadIdx.x], s_lanes + 4 * threadIdx.x);
+                               s_lo[threadIdx.x], s_mask[threadIdx.x], s_lanes + 4 * threadIdx.x);
         } else {
             s_mask[threadIdx.x] = 0u;
         }
@@ -475,9 +505,9 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                 if (has_b) bits &= ~(1u << (jb - c0));
                 const uint32_t posa = (uint32_t)(bstart + ja - begin), posb = (uint32_t)(bstart + jb - begin);
                 SplatBwd sa, sb;
-                splat_bwd_eval<kQuad>(s_xy[ja], s_cb[ja], s_lanes + 4 * ja, px, fpx, fpy0, fpy1, py0,
+                splat_bwd_eval<kQuad>(s_xy[ja], s_cb[ja], s_lo[ja], s_lanes + 4 * ja, px, fpx, fpy0, fpy1, py0,
                                       posa < p0.last, posa < p1.last, sa);
-                splat_bwd_eval<kQuad>(s_xy[jb], s_cb[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0,
+                splat_bwd_eval<kQuad>(s_xy[jb], s_cb[jb], s_lo[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0,
                                       has_b && posb < p0.last, has_b && posb < p1.last, sb);
                 float va[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float vb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -512,10 +542,11 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
 
 // dynamic shared memory of the two tile routines for `nthr` threads
 __host__ __device__ inline size_t render_fwd_smem(int nthr) {
-    return (3 * sizeof(float4) + 4 * sizeof(uint2) + sizeof(uint32_t)) * nthr;
+    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + sizeof(uint32_t)) * nthr;
 }
 __host__ __device__ inline size_t render_bwd_smem(int nthr) {
-    return (3 * sizeof(float4) + 4 * sizeof(uint2) + 2 * sizeof(uint32_t)) * nthr + 32 * sizeof(uint32_t);
+    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + 2 * sizeof(uint32_t)) * nthr +
+           32 * sizeof(uint32_t);
 }
 
 }  // namespace gsr

@@ -53,9 +53,11 @@ __device__ __forceinline__ uint4 q4_box_lanes(int x0, int x1, int y0, int y1, in
 // more than the dropped warps save).
 template <bool kExact>
 __device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int ox, int oy, float4 &s_xy,
-                                         float4 &s_cb, float4 &s_rgb, uint32_t &s_mask, uint4 *s_lanes) {
+                                         float4 &s_cb, float4 &s_rgb, float2 &s_lo, uint32_t &s_mask,
+                                         uint4 *s_lanes) {
     const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
     s_rgb = __ldg(a.rgb_depth + gid);
+    s_lo = mean_residual(a, gid);
     const float A = g.z, B = g.w, C = c.x, op = c.y;
     s_xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
     s_cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
@@ -107,6 +109,19 @@ struct Q4Group {
 };
 
 // ---------------------------------------------------------------- K7
+// The thread's four pixels are two vertical pairs (pixels 2h, 2h + 1 of
+// rows py0 + 2h, py0 + 2h + 1), and each pair runs the per-pixel arithmetic
+// of pixel_bwd_update in Blackwell's packed FP32 instructions (FFMA2 /
+// FADD2 / FMUL2: two independent lanes, each rounded to nearest like the
+// scalar operation), so one issue slot does two pixels' work.  A pixel that
+// has no contribution from the splat takes the same instructions with
+// alpha = 0, G = 0 and a reciprocal of 1, which leave its state and the
+// gradient sums exactly unchanged.  Each of the nine gradient sums is kept
+// as a pair over the splat's four pixels and folded once.
+struct PairBwd {
+    float2 T, accd, dC0, dC1, dC2;
+};
+
 template <bool kHalf = false>
 __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile, const float *__restrict__ T_final,
                                                    const uint32_t *__restrict__ n_contrib,
@@ -115,7 +130,8 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     using G = Q4Group<kHalf>;
     constexpr int nthr = kQ4Threads;
     float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    uint4 *s_lanes = reinterpret_cast<uint4 *>(smem + 3 * nthr);
+    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * nthr);
+    uint4 *s_lanes = reinterpret_cast<uint4 *>(s_lo + nthr);
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 2 * nthr);
     uint32_t *s_gid = s_mask + nthr;
     uint32_t *s_max = s_gid + nthr;  // 2 entries
@@ -126,22 +142,34 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     const uint2 rg = a.ranges[a.tile_off + tile];
     const int begin = (int)rg.x;
     const int64_t plane = (int64_t)a.W * a.H;
-    PixelBwd p[4];
+    PairBwd p[2];
+    uint32_t last[4];
     uint32_t mlast = 0u;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        p[k] = PixelBwd{0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-        if (px < a.W && py0 + k < a.H) {
-            const int64_t pix = (int64_t)(py0 + k) * a.W + px;
-            p[k].T = T_final[pix];
-            p[k].last = n_contrib[pix];
-            p[k].dC0 = dL_dimg[pix];
-            p[k].dC1 = dL_dimg[plane + pix];
-            p[k].dC2 = dL_dimg[2 * plane + pix];
-            // behind the last contributor: the background
-            p[k].accd = p[k].dC0 * a.bg0 + p[k].dC1 * a.bg1 + p[k].dC2 * a.bg2;
+    for (int h = 0; h < 2; ++h) {
+        float v[2][5];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k = 2 * h + q;
+            v[q][0] = v[q][1] = v[q][2] = v[q][3] = v[q][4] = 0.f;
+            last[k] = 0u;
+            if (px < a.W && py0 + k < a.H) {
+                const int64_t pix = (int64_t)(py0 + k) * a.W + px;
+                v[q][0] = T_final[pix];
+                last[k] = n_contrib[pix];
+                v[q][2] = dL_dimg[pix];
+                v[q][3] = dL_dimg[plane + pix];
+                v[q][4] = dL_dimg[2 * plane + pix];
+                // behind the last contributor: the background
+                v[q][1] = v[q][2] * a.bg0 + v[q][3] * a.bg1 + v[q][4] * a.bg2;
+            }
+            mlast = max(mlast, last[k]);
         }
-        mlast = max(mlast, p[k].last);
+        p[h].T = make_float2(v[0][0], v[1][0]);
+        p[h].accd = make_float2(v[0][1], v[1][1]);
+        p[h].dC0 = make_float2(v[0][2], v[1][2]);
+        p[h].dC1 = make_float2(v[0][3], v[1][3]);
+        p[h].dC2 = make_float2(v[0][4], v[1][4]);
     }
     // block-wide max of n_contrib: positions at or beyond it are never used
     const uint32_t m = __reduce_max_sync(0xffffffffu, mlast);
@@ -150,6 +178,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     // never past the tile's own list, whatever n_contrib holds
     const int stop = min(begin + (int)max(s_max[0], s_max[1]), (int)rg.y);
     const float fpx = (float)px;
+    const float2 fpy[2] = {make_float2((float)py0, (float)(py0 + 1)), make_float2((float)(py0 + 2), (float)(py0 + 3))};
     // value k of the transposed reduction lands in lane 4k: its gradient slot
     const int kval = (lane >> 2) & 7;
     float *const gk = (kval < 4 ? g0 : g1) + (kval & 3);
@@ -160,7 +189,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
         if (idx < bend) {
             const uint32_t gid = a.vals[idx];
             s_gid[ti] = gid;
-            q4_stage<kHalf>(a, gid, ox, oy, s_xy[ti], s_cb[ti], s_rgb[ti], s_mask[ti], s_lanes + 2 * ti);
+            q4_stage<kHalf>(a, gid, ox, oy, s_xy[ti], s_cb[ti], s_rgb[ti], s_lo[ti], s_mask[ti], s_lanes + 2 * ti);
         } else {
             s_mask[ti] = 0u;
         }
@@ -173,35 +202,74 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                 bits &= ~(1u << (j - c0));
                 const uint32_t pos = (uint32_t)(bstart + j - begin);
                 const float4 g = s_xy[j], cb = s_cb[j];
+                const float2 lo = s_lo[j];
                 const uint4 lm = s_lanes[2 * j + wid];
-                SplatBwd s;
-                s.dx = fpx - g.x;
-                const float t = FM(FM(g.z, s.dx), s.dx), bdx = FM(g.w, s.dx);
-                s.A = g.z * (1.0f / kHalfLog2e);
-                s.B = g.w * (0.5f / kHalfLog2e);
-                s.C = cb.x * (1.0f / kHalfLog2e);
-                s.Adx = s.A * s.dx;
-                s.Bdx = s.B * s.dx;
-                s.hdx2 = -0.5f * s.dx * s.dx;
-                Eval ev[4];
-                float dy[4];
-                bool ok[4];
+                const float dx = FS(FS(fpx, g.x), lo.x);
+                const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
+                // alpha at the four pixels, a pair at a time
+                float2 dy[2], al[2], gs[2];
+                bool ok[4], cl[4];
                 bool any = false;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    dy[k] = (float)(py0 + k) - g.y;
-                    const float e = __fmaf_rn(FM(cb.x, dy[k]), dy[k], __fmaf_rn(bdx, dy[k], t));
-                    ok[k] = pos < p[k].last && ((q4_lane_bits(lm, k) >> lane) & 1u) && splat_alpha(e, cb.y, ev[k]);
-                    any = any || ok[k];
+                for (int h = 0; h < 2; ++h) {
+                    dy[h] = __fadd2_rn(__fadd2_rn(fpy[h], f2(-g.y)), f2(-lo.y));
+                    const float2 e = __ffma2_rn(__fmul2_rn(f2(cb.x), dy[h]), dy[h],
+                                                __ffma2_rn(f2(bdx), dy[h], f2(t)));
+                    gs[h] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                    const float2 raw = __fmul2_rn(f2(cb.y), gs[h]);
+                    al[h] = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                    cl[2 * h] = raw.x > kAlphaMax;
+                    cl[2 * h + 1] = raw.y > kAlphaMax;
+                    ok[2 * h] = pos < last[2 * h] && ((q4_lane_bits(lm, 2 * h) >> lane) & 1u) && e.x <= 0.0f &&
+                                al[h].x >= kAlphaMin;
+                    ok[2 * h + 1] = pos < last[2 * h + 1] && ((q4_lane_bits(lm, 2 * h + 1) >> lane) & 1u) &&
+                                    e.y <= 0.0f && al[h].y >= kAlphaMin;
+                    any = any || ok[2 * h] || ok[2 * h + 1];
                 }
-                float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float2 v2[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) v2[q] = make_float2(0.f, 0.f);
                 if (any) {
                     const float4 col = s_rgb[j];
+                    const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
+                    const float C = cb.x * (1.0f / kHalfLog2e);
+                    const float Adx = A * dx, Bdx = B * dx, hdx2 = -0.5f * dx * dx;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (ok[k]) pixel_bwd_update(p[k], ev[k], s, dy[k], col, v);
+                    for (int h = 0; h < 2; ++h) {
+                        const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
+                        if (!(o0 || o1)) continue;
+                        const bool q0 = o0 && !cl[2 * h], q1 = o1 && !cl[2 * h + 1];
+                        // alpha of a pixel without a contribution is 0: every update below leaves it unchanged
+                        const float2 al_e = make_float2(o0 ? al[h].x : 0.f, o1 ? al[h].y : 0.f);
+                        const float2 al_g = make_float2(q0 ? al[h].x : 0.f, q1 ? al[h].y : 0.f);
+                        const float2 g_g = make_float2(q0 ? gs[h].x : 0.f, q1 ? gs[h].y : 0.f);
+                        const float2 one_m = __fadd2_rn(f2(1.0f), neg2(al_e));
+                        const float2 rc = make_float2(o0 ? __fdividef(1.0f, one_m.x) : 1.0f,
+                                                      o1 ? __fdividef(1.0f, one_m.y) : 1.0f);
+                        PairBwd &P = p[h];
+                        P.T = __fmul2_rn(P.T, rc);  // transmittance in front of this Gaussian
+                        const float2 aT = __fmul2_rn(al_e, P.T);
+                        v2[6] = __ffma2_rn(P.dC0, aT, v2[6]);
+                        v2[7] = __ffma2_rn(P.dC1, aT, v2[7]);
+                        v2[8] = __ffma2_rn(P.dC2, aT, v2[8]);
+                        float2 dc = __fmul2_rn(P.dC0, f2(col.x));
+                        dc = __ffma2_rn(P.dC1, f2(col.y), dc);
+                        dc = __ffma2_rn(P.dC2, f2(col.z), dc);
+                        const float2 dalpha = __fmul2_rn(P.T, __fadd2_rn(dc, neg2(P.accd)));
+                        P.accd = __ffma2_rn(dc, al_e, __fmul2_rn(P.accd, one_m));
+                        const float2 dpow = __fmul2_rn(dalpha, al_g);
+                        v2[5] = __ffma2_rn(dalpha, g_g, v2[5]);
+                        v2[0] = __ffma2_rn(dpow, __ffma2_rn(f2(B), dy[h], f2(Adx)), v2[0]);
+                        v2[1] = __ffma2_rn(dpow, __ffma2_rn(f2(C), dy[h], f2(Bdx)), v2[1]);
+                        v2[2] = __ffma2_rn(dpow, f2(hdx2), v2[2]);
+                        v2[3] = __ffma2_rn(__fmul2_rn(dpow, f2(-dx)), dy[h], v2[3]);
+                        v2[4] = __ffma2_rn(dpow, __fmul2_rn(__fmul2_rn(f2(-0.5f), dy[h]), dy[h]), v2[4]);
+                    }
                 }
                 if (__any_sync(0xffffffffu, any)) {
+                    float v[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
                     float v8;
                     const float y = warp_transpose_sum(v, v8);
                     const uint32_t gid = s_gid[j];
@@ -215,8 +283,8 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
 
 // shared memory of one tile's 64 threads (a multiple of 16 bytes)
 __host__ __device__ inline size_t render_q4_smem() {
-    return ((3 * sizeof(float4) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * kQ4Threads + 2 * sizeof(uint32_t) + 15) /
-           16 * 16;
+    return ((3 * sizeof(float4) + sizeof(float2) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * kQ4Threads +
+            2 * sizeof(uint32_t) + 15) / 16 * 16;
 }
 
 }  // namespace gsr

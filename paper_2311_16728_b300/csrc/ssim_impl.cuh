@@ -81,6 +81,14 @@ __device__ __forceinline__ void stage_region(const float *__restrict__ src, int 
 constexpr size_t kPass1Floats = 2 * kRH * kRS + 5 * kRH * kLTW;
 constexpr size_t kPass2Floats = 3 * kRH * kRS + 3 * kRH * kLTW;
 
+__device__ __forceinline__ float2 f2w(float x) { return make_float2(x, x); }
+
+// The separable blurs run two of their maps as one pair in Blackwell's
+// packed FP32 instructions (FFMA2 / FMUL2: each lane rounded to nearest like
+// the scalar operation), so one issue slot advances two maps: the moments
+// (mean x, mean y) and (E x^2, E y^2) as pairs and E xy alone in pass 1, the
+// partials (a, b) as a pair and c alone in pass 2.
+
 // Pass 1 on the 32 x 32 output block (bx, by) of channel c: windowed moments
 // (separable: rows then columns, kRun outputs per thread from kRun + 10
 // staged values), SSIM map, its partials (a, b, c) and the block's sums of
@@ -92,7 +100,10 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
                                                  float *__restrict__ part, int bx, int by, int c, float *sm,
                                                  float *s_red) {
     float *sX = sm, *sY = sm + kRH * kRS;
-    float *sH = sm + 2 * kRH * kRS;  // [5][kRH][kLTW]
+    // row-blurred moments: (mean x, mean y) and (E x^2, E y^2) pairs, then E xy
+    float2 *sM2 = reinterpret_cast<float2 *>(sm + 2 * kRH * kRS);  // [kRH][kLTW]
+    float2 *sS2 = sM2 + kRH * kLTW;                                 // [kRH][kLTW]
+    float *sXY = reinterpret_cast<float *>(sS2 + kRH * kLTW);       // [kRH][kLTW]
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     __syncthreads();  // the previous block's readers of sm are done
@@ -101,35 +112,29 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
     __syncthreads();
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
         const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
-        // values and their products once per staged column, then five
-        // fused multiply-adds per tap
-        float a[kRun + 10], b[kRun + 10], aa[kRun + 10], bb[kRun + 10], ab[kRun + 10];
+        // values and their products once per staged column
+        float2 v[kRun + 10], q[kRun + 10];
+        float xy[kRun + 10];
 #pragma unroll
         for (int k = 0; k < kRun + 10; ++k) {
-            a[k] = sX[r * kRS + j0 + k];
-            b[k] = sY[r * kRS + j0 + k];
-            aa[k] = a[k] * a[k];
-            bb[k] = b[k] * b[k];
-            ab[k] = a[k] * b[k];
+            v[k] = make_float2(sX[r * kRS + j0 + k], sY[r * kRS + j0 + k]);
+            q[k] = __fmul2_rn(v[k], v[k]);
+            xy[k] = v[k].x * v[k].y;
         }
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
-            float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+            float2 m = make_float2(0.f, 0.f), sq = make_float2(0.f, 0.f);
+            float sxy = 0.f;
 #pragma unroll
             for (int k = 0; k < 11; ++k) {
                 const float w = win.w[k];
-                mx = __fmaf_rn(w, a[o + k], mx);
-                my = __fmaf_rn(w, b[o + k], my);
-                xx = __fmaf_rn(w, aa[o + k], xx);
-                yy = __fmaf_rn(w, bb[o + k], yy);
-                xy = __fmaf_rn(w, ab[o + k], xy);
+                m = __ffma2_rn(f2w(w), v[o + k], m);
+                sq = __ffma2_rn(f2w(w), q[o + k], sq);
+                sxy = __fmaf_rn(w, xy[o + k], sxy);
             }
-            float *h = sH + r * kLTW + j0 + o;
-            h[0] = mx;
-            h[kRH * kLTW] = my;
-            h[2 * kRH * kLTW] = xx;
-            h[3 * kRH * kLTW] = yy;
-            h[4 * kRH * kLTW] = xy;
+            sM2[r * kLTW + j0 + o] = m;
+            sS2[r * kLTW + j0 + o] = sq;
+            sXY[r * kLTW + j0 + o] = sxy;
         }
     }
     __syncthreads();
@@ -138,26 +143,39 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
     // columns: virtual thread = (column, run of kRun rows); 256 of them
     for (int vt = threadIdx.x; vt < kLTW * (kLTH / kRun); vt += NT) {
         const int tx = vt % kLTW, i0 = (vt / kLTW) * kRun;
-        float m[5][kRun];
+        float2 mm[kRun], ss[kRun];
+        float sxyv[kRun];
+        {
+            float2 cm[kRun + 10], cs[kRun + 10];
+            float cx[kRun + 10];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            float col[kRun + 10];
-#pragma unroll
-            for (int k = 0; k < kRun + 10; ++k) col[k] = sH[q * kRH * kLTW + (i0 + k) * kLTW + tx];
+            for (int k = 0; k < kRun + 10; ++k) {
+                cm[k] = sM2[(i0 + k) * kLTW + tx];
+                cs[k] = sS2[(i0 + k) * kLTW + tx];
+                cx[k] = sXY[(i0 + k) * kLTW + tx];
+            }
 #pragma unroll
             for (int o = 0; o < kRun; ++o) {
-                float s = 0.f;
+                float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+                float e = 0.f;
 #pragma unroll
-                for (int k = 0; k < 11; ++k) s += win.w[k] * col[o + k];
-                m[q][o] = s;
+                for (int k = 0; k < 11; ++k) {
+                    const float w = win.w[k];
+                    a = __ffma2_rn(f2w(w), cm[o + k], a);
+                    b = __ffma2_rn(f2w(w), cs[o + k], b);
+                    e = __fmaf_rn(w, cx[o + k], e);
+                }
+                mm[o] = a;
+                ss[o] = b;
+                sxyv[o] = e;
             }
         }
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
             const int gx = ox + tx, gy = oy + i0 + o;
             if (gx < W && gy < H) {
-                const float mx = m[0][o], my = m[1][o];
-                const float sxx = m[2][o] - mx * mx, syy = m[3][o] - my * my, sxy = m[4][o] - mx * my;
+                const float mx = mm[o].x, my = mm[o].y;
+                const float sxx = ss[o].x - mx * mx, syy = ss[o].y - my * my, sxy = sxyv[o] - mx * my;
                 const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
                 const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
                 const float iB = 1.0f / (B1 * B2);
@@ -193,8 +211,9 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
                                                  const float *__restrict__ mapB, const float *__restrict__ mapC,
                                                  float lambda, float scale, float *__restrict__ dx_out, int bx, int by,
                                                  int c, float *sm) {
-    float *sM = sm;                  // [3][kRH][kRS]
-    float *sH = sm + 3 * kRH * kRS;  // [3][kRH][kLTW]
+    float *sM = sm;                                                  // [3][kRH][kRS]
+    float2 *sAB = reinterpret_cast<float2 *>(sm + 3 * kRH * kRS);    // [kRH][kLTW] row-blurred (a, b)
+    float *sCh = reinterpret_cast<float *>(sAB + kRH * kLTW);        // [kRH][kLTW] row-blurred c
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     const float inv_n = (float)((double)scale / ((double)C * (double)plane));
@@ -203,18 +222,26 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
     stage_region<NT>(mapB + cb, H, W, ox, oy, sM + kRH * kRS);
     stage_region<NT>(mapC + cb, H, W, ox, oy, sM + 2 * kRH * kRS);
     __syncthreads();
-    for (int item = threadIdx.x; item < 3 * kRH * (kLTW / kRun); item += NT) {
-        const int q = item / (kRH * (kLTW / kRun)), rem = item % (kRH * (kLTW / kRun));
-        const int r = rem / (kLTW / kRun), j0 = (rem % (kLTW / kRun)) * kRun;
-        float a[kRun + 10];
+    for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
+        const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
+        float2 ab[kRun + 10];
+        float cc[kRun + 10];
 #pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) a[k] = sM[q * kRH * kRS + r * kRS + j0 + k];
+        for (int k = 0; k < kRun + 10; ++k) {
+            ab[k] = make_float2(sM[r * kRS + j0 + k], sM[kRH * kRS + r * kRS + j0 + k]);
+            cc[k] = sM[2 * kRH * kRS + r * kRS + j0 + k];
+        }
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
-            float s = 0.f;
+            float2 s2 = make_float2(0.f, 0.f);
+            float s1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 11; ++k) s += win.w[k] * a[o + k];
-            sH[q * kRH * kLTW + r * kLTW + j0 + o] = s;
+            for (int k = 0; k < 11; ++k) {
+                s2 = __ffma2_rn(f2w(win.w[k]), ab[o + k], s2);
+                s1 = __fmaf_rn(win.w[k], cc[o + k], s1);
+            }
+            sAB[r * kLTW + j0 + o] = s2;
+            sCh[r * kLTW + j0 + o] = s1;
         }
     }
     __syncthreads();
@@ -230,18 +257,27 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
             xs[o] = x[idx];
             ys[o] = y[idx];
         }
-        float g[3][kRun];
+        float2 gab[kRun];
+        float gc[kRun];
+        {
+            float2 cab[kRun + 10];
+            float ccc[kRun + 10];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            float col[kRun + 10];
-#pragma unroll
-            for (int k = 0; k < kRun + 10; ++k) col[k] = sH[q * kRH * kLTW + (i0 + k) * kLTW + tx];
+            for (int k = 0; k < kRun + 10; ++k) {
+                cab[k] = sAB[(i0 + k) * kLTW + tx];
+                ccc[k] = sCh[(i0 + k) * kLTW + tx];
+            }
 #pragma unroll
             for (int o = 0; o < kRun; ++o) {
-                float s = 0.f;
+                float2 s2 = make_float2(0.f, 0.f);
+                float s1 = 0.f;
 #pragma unroll
-                for (int k = 0; k < 11; ++k) s += win.w[k] * col[o + k];
-                g[q][o] = s;
+                for (int k = 0; k < 11; ++k) {
+                    s2 = __ffma2_rn(f2w(win.w[k]), cab[o + k], s2);
+                    s1 = __fmaf_rn(win.w[k], ccc[o + k], s1);
+                }
+                gab[o] = s2;
+                gc[o] = s1;
             }
         }
 #pragma unroll
@@ -252,7 +288,7 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
                 const float xv = xs[o], yv = ys[o];
                 const float d = xv - yv;
                 const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-                dx_out[idx] = ((1.f - lambda) * sg - lambda * (g[0][o] + 2.f * xv * g[1][o] + yv * g[2][o])) * inv_n;
+                dx_out[idx] = ((1.f - lambda) * sg - lambda * (gab[o].x + 2.f * xv * gab[o].y + yv * gc[o])) * inv_n;
             }
         }
     }

@@ -138,6 +138,7 @@ class ViewBuffers:
         self.c_op_box = torch.empty(m, 4, **f32)
         self.rgb_depth = torch.empty(m, 4, **f32)
         self.ntiles = torch.zeros(m, dtype=torch.int32, device=device)
+        self.uv_lo = torch.zeros(m, 2, **f32)
         self.tiles = n_tiles(cam, tiling)
         self.ranges = torch.zeros(self.tiles, 2, dtype=torch.int32, device=device)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=device)
@@ -165,7 +166,7 @@ class ViewBuffers:
 
     def proj_struct(self) -> L.gsr_proj:
         return L.gsr_proj(self.xy_conic.data_ptr(), self.c_op_box.data_ptr(), self.rgb_depth.data_ptr(),
-                          self.ntiles.data_ptr())
+                          self.ntiles.data_ptr(), self.uv_lo.data_ptr())
 
     def grad2d_struct(self) -> L.gsr_grad2d:
         return L.gsr_grad2d(self.g2[0].data_ptr(), self.g2[1].data_ptr(), self.g2[2].data_ptr())

@@ -17,9 +17,14 @@ magnitude of each gradient's own GEMM or column sum:
   gb3, gb2, gb1          2^-7 sum_m |d|                (FP32 column sums)
 
 plus the FP32 summation bound gamma_M sum |a b| (gamma_n = n u / (1 - n u),
-u = 2^-24).  Like the forward's, this is a model bound (each operand element
-within two BF16 ulps of the oracle's), not a worst case over every possible
-cascade of roundings; `tests/test_mlp_bounds.py` pins it on the CPU against
+u = 2^-24).  A ReLU mask can differ where the oracle's pre-activation lies
+within its own bound of 0 (two BF16 ulps of every input of its GEMM, plus
+the FP32 summation bound): there the masked gradient may be present on one
+side only, so its whole magnitude joins the |d| of the bound, and the
+activation the oracle has as 0 may be as large as that bound on the other
+side, which joins the |h| of the next layer's weight gradient.  Like the
+forward's, this is a model bound (each operand element within two BF16 ulps
+of the oracle's), not a worst case over every possible cascade of roundings; `tests/test_mlp_bounds.py` pins it on the CPU against
 an FP32 / BF16 simulation of the tensor-core arithmetic and shows that a
 planted mistake leaves it.  For the Adam step that follows, `adam_bounds`
 carries a gradient bound through the update by the mean value theorem.
@@ -42,20 +47,28 @@ def gradient_bounds(fw: dict, dy: np.ndarray, g_ref: dict) -> dict:
     gradients (oracle.mlp.backward, whose BF16 operands it recomputes)."""
     from oracle import mlp as omlp
     M = dy.shape[0]
+    K0, H = fw["W1"].shape[1], fw["W2"].shape[0]
     dyb = np.abs(omlp.bf16_round(dy))
+    h1, h2, x = np.abs(fw["h1"]), np.abs(fw["h2"]), np.abs(fw["xb"])
+    # pre-activations whose sign the two sides may see differently, and how
+    # large the activation the oracle has as 0 can then be on the other side
+    e_pre1 = gamma(K0 + 1) * (x @ np.abs(fw["W1"]).T)
+    e_pre2 = (2 * TWO_ULPS + gamma(H + 1)) * (h1 @ np.abs(fw["W2"]).T)
+    unsure1, unsure2 = np.abs(fw["pre1"]) <= e_pre1, np.abs(fw["pre2"]) <= e_pre2
+    h1x, h2x = (1 + TWO_ULPS) * e_pre1 * unsure1, (1 + TWO_ULPS) * e_pre2 * unsure2
     dh2 = omlp.bf16_round(dy) @ fw["W3"]
     dpre2 = dh2 * (fw["pre2"] > 0)
+    a2 = np.abs(omlp.bf16_round(dpre2)) + np.abs(dh2) * unsure2
     dh1 = omlp.bf16_round(dpre2) @ fw["W2"]
     dpre1 = dh1 * (fw["pre1"] > 0)
-    a2, a1 = np.abs(omlp.bf16_round(dpre2)), np.abs(omlp.bf16_round(dpre1))
-    h1, h2, x = np.abs(fw["h1"]), np.abs(fw["h2"]), np.abs(fw["xb"])
+    a1 = np.abs(omlp.bf16_round(dpre1)) + np.abs(dh1) * unsure1
     s = gamma(M)
-    out = {"W3": (2 * TWO_ULPS + s) * (dyb.T @ h2),
-           "W2": (2 * TWO_ULPS + s) * (a2.T @ h1),
+    out = {"W3": (2 * TWO_ULPS + s) * (dyb.T @ h2) + (1 + TWO_ULPS + s) * (dyb.T @ h2x),
+           "W2": (2 * TWO_ULPS + s) * (a2.T @ h1) + (1 + TWO_ULPS + s) * (a2.T @ h1x),
            "W1": (TWO_ULPS + s) * (a1.T @ x),
            "b3": (TWO_ULPS + s) * np.abs(dy).sum(0),
-           "b2": (TWO_ULPS + s) * np.abs(dpre2).sum(0),
-           "b1": (TWO_ULPS + s) * np.abs(dpre1).sum(0)}
+           "b2": (TWO_ULPS + s) * (np.abs(dpre2) + np.abs(dh2) * unsure2).sum(0),
+           "b1": (TWO_ULPS + s) * (np.abs(dpre1) + np.abs(dh1) * unsure1).sum(0)}
     for k in out:
         assert out[k].shape == np.shape(g_ref[k]), k
     return out

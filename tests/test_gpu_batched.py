@@ -153,7 +153,7 @@ def test_window_matches_oracle_tiny():
         gv, _, mag = oracle.render_bwd(sc, ca, cl.width, cl.height, dec, dimg, with_magnitude=True)
         gref += gv
         cond += param_condition(sc, ca, cl.width, cl.height, dec, mag)
-        waive |= colour_clamp_waiver(oracle.project(sc, ca, cl.width, cl.height, dec.visible))
+        waive |= colour_clamp_waiver(oracle.project(sc, ca, cl.width, cl.height, dec.visible), dec.visible)
         waive[near_flagged(dec, mg < MARGIN_FLAG)] = True
         L = float(bw.losses[[v[2] for v in bw.views].index(lvl)].item())
         print(f"level {lvl}: loss {L:.7f} vs oracle {L_ref:.7f}; flagged pixels {int((mg < MARGIN_FLAG).sum())}")

@@ -146,6 +146,18 @@ def test_training_gradients_and_adam_match_oracle(M):
         within = float(np.mean(err <= np.maximum(1e-3 * np.abs(g_ref[k]), 1e-9)))
         print(f"  grad {k}: normwise {rel:.2e}, worst err/bound {float((err / (bounds[k] + 1e-300)).max()):.3f}, "
               f"{100 * within:.1f} % of elements within 1e-3 relative")
+        if not (err <= bounds[k]).all():
+            bad = np.argwhere(err > bounds[k])
+            for ix in bad[np.argsort(-(err / bounds[k])[err > bounds[k]])][:4]:
+                ix = tuple(int(v) for v in ix)
+                info = f"    {k}{ix}: g {g[k][ix]:.6e} g* {g_ref[k][ix]:.6e} err {err[ix]:.2e} bound {bounds[k][ix]:.2e}"
+                if k in ("W2", "W3"):
+                    act, prev = ("pre2", "h1") if k == "W2" else (None, "h2")
+                    j, c = ix
+                    info += f"; |{prev}[:, {c}]| sum {np.abs(fw[prev][:, c]).sum():.3e} nonzero {(fw[prev][:, c] != 0).sum()}"
+                    if act:
+                        info += f"; rows with {act}[:, {j}] > 0: {(fw[act][:, j] > 0).sum()}"
+                print(info)
         assert (err <= bounds[k]).all(), (k, int((err > bounds[k]).sum()))
         assert rel < 2e-2, (k, rel)
     for k in names:

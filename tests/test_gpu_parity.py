@@ -116,7 +116,7 @@ def test_thin_surface_gaussians_keys_image_and_gradients():
     assert_grad_bar("thin surfaces, screen-space gradients", g2gpu, g2ref, mag)
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
     assert_grad_bar("thin surfaces, parameter gradients", grad_planes_gpu(grads), gref,
-                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
 
 
 def test_render_matches_oracle_tiny():
@@ -186,7 +186,7 @@ def test_render_backward_matches_oracle_tiny(tile):
     assert_grad_bar(f"tile {tile}, screen-space gradients", _screen_grads(vb), g2ref, mag)
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
     assert_grad_bar(f"tile {tile}, parameter gradients", grad_planes_gpu(grads), gref,
-                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
 
 
 def test_end_to_end_loss_and_gradients_tiny():
@@ -216,7 +216,7 @@ def test_end_to_end_loss_and_gradients_tiny():
     torch.cuda.synchronize()
     L = float(vb.loss.item())
     flagged = mg < MARGIN_FLAG
-    waive = colour_clamp_waiver(oracle.project(sc, ca, cam.width, cam.height, dec.visible))
+    waive = colour_clamp_waiver(oracle.project(sc, ca, cam.width, cam.height, dec.visible), dec.visible)
     waive[near_flagged(dec, flagged)] = True
     scale = 3 * cam.width * cam.height
     print(f"loss {L:.7f} vs {L_ref:.7f} (rel {abs(L - L_ref) / L_ref:.1e}); flagged pixels {int(flagged.sum())}")
@@ -326,7 +326,7 @@ def test_autograd_function_matches_oracle_gradient():
     grads = gsr.Gaussians(*(t.grad for t in leaves))
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
     assert_grad_bar("autograd.Function, parameter gradients", grad_planes_gpu(grads), gref,
-                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
 
 
 def test_capacity_overflow_is_reported_not_written():
@@ -415,7 +415,7 @@ def test_full_size_frame(order):
     assert_grad_bar(f"full frame ({order}), screen-space gradients", _screen_grads(vb), g2ref, mag)
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
     assert_grad_bar(f"full frame ({order}), parameter gradients", grad_planes_gpu(grads), gref,
-                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
 
 
 def test_large_scene_frame():
@@ -449,7 +449,7 @@ def test_large_scene_frame():
     assert_grad_bar("large scene, screen-space gradients", _screen_grads(vb), g2ref, mag)
     pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
     assert_grad_bar("large scene, parameter gradients", grad_planes_gpu(grads), gref,
-                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr))
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
 
 
 def test_graph_replay_matches_eager():
