@@ -51,11 +51,11 @@ WIDTH, HEIGHT, FOCAL = 1200, 680, 600.0
 N_POSES = 50
 METRIC = "fwd+bwd iters/s @300k Gaussians 1200x680"
 WORKLOAD = ("single-view mapping step (Replica-shaped): 300k Gaussians in a 6x3x4 m room, 1200x680, fx=fy=600, "
-            "50-pose seeded trajectory, 16x16 tiles, L1+D-SSIM (lambda 0.2), Adam, FP32")
+            "50-pose seeded trajectory, autotuned tiling, L1+D-SSIM (lambda 0.2), Adam, FP32")
 
 
 def _config(extra=None):
-    c = {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT, "tile": "16x16",
+    c = {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
          "poses": N_POSES, "sh_degree": 3,
          "l2": "inputs larger than L2: params + grads + Adam moments (4 x 72 MB) stream through HBM every step",
          "parallelism": "replicas (no data-path collective)"}
@@ -425,6 +425,19 @@ def _peaks():
     return json.load(open(path)) if os.path.exists(path) else {}
 
 
+def parse_tiling(spec: str):
+    """'WxH[/depth/bwd_threads]' -> (tile_w, tile_h, batch_depth, bwd_threads)."""
+    parts = spec.split("/")
+    tw, th = (int(x) for x in parts[0].split("x"))
+    rest = [int(x) for x in parts[1:]] + [0, 0]
+    return (tw, th, rest[0], rest[1])
+
+
+def label(tile) -> str:
+    from paper_2311_16728_b300.autotune import label as _label
+    return _label(tuple(tile) + (0,) * (4 - len(tile)))
+
+
 def _window_setup(args):
     """The window workload (setup, untimed): targets rendered from the true
     map, the perturbed map in the store order --order names, the tile shape
@@ -450,8 +463,8 @@ def _window_setup(args):
     if args.tile == "auto":
         tile, report = autotune_window(params, kf, levels=WIN_LEVELS, steps=5, warmup=2)
     else:
-        tile = tuple(int(x) for x in args.tile.split("x"))
-        report = {"ms_per_step": {}}
+        tile = parse_tiling(args.tile)
+        report = {"ms_per_step": {}, "chosen": label(tile)}
     bw = BatchedWindow(params, kf, levels=WIN_LEVELS, tiling=gsr.tiling_struct(*tile))
     bw.capture()
     return bw, tile, report, kf, params
@@ -477,7 +490,8 @@ def window_figure(args, steps: int = 200):
     return {"workload": f"{WIN_N // 1000}k Gaussians, {WIN_KF} keyframes 640x480 x {WIN_LEVELS} levels = {bw.V} "
                         "views, one persistent launch per iteration, whole iteration in one CUDA graph",
             "iters_per_s": 1000.0 / ms, "views_per_s": bw.V * 1000.0 / ms, "ms_per_step": ms, "steps": steps,
-            "tile": f"{tile[0]}x{tile[1]}", "autotune": report.get("chosen", report.get("ms_per_step"))}
+            "tiling": label(tile), "autotune": report.get("chosen"),
+            "autotune_candidates": len(report.get("ms_per_step", {}))}
 
 
 def run_window(args):
@@ -604,14 +618,14 @@ def run_window(args):
                                    f"{WIN_KF} keyframes 640x480 fx=fy=525 x {WIN_LEVELS} levels = {bw.V} views, "
                                    f"{bw.tiles} tiles, {px} px; one persistent launch per iteration; whole "
                                    "iteration (preprocess, binning, persistent fwd/loss/bwd, chain, Adam) in one "
-                                   "CUDA graph", "tile": f"{tile[0]}x{tile[1]}" + (" (autotuned)" if args.tile == "auto" else " (given)"),
+                                   "CUDA graph", "tiling": label(tile) + (" (autotuned)" if args.tile == "auto" else " (given)"),
                        "autotune_ms": report["ms_per_step"], "pairs": int(bw.num_pairs.item()),
                        "map_order": args.order,
                        "l2": "inputs larger than L2 (4 x 120 MB of params, grads, moments per step)"},
             "roofline": {"kernel": "batched_iterate_kernel (fwd + bwd blends)", "bound": "alu",
                          "achieved": flops / it_s / 1e12, "peak": fp32, "unit": "TFLOP/s",
                          "frac": flops / it_s / 1e12 / fp32,
-                         "traffic": NCU_TRAFFIC_WINDOW_ITERATE if (tile == (16, 16) and args.order == "morton") else None,
+                         "traffic": NCU_TRAFFIC_WINDOW_ITERATE if (tuple(tile) == (16, 16, 0, 0) and args.order == "morton") else None,
                          "alg_per_launch": flops,
                          "alg_rule": f"({FLOPS_PER_BLEND_FWD} + {FLOPS_PER_BLEND_BWD}) FP32 per (pixel, Gaussian) "
                                      "evaluation x blends over all views",
@@ -1196,7 +1210,8 @@ def main():
                     help="mapping mode: leave out the window figure and the bounded time-to-PSNR run")
     ap.add_argument("--headline-ttp-seeds", default="100,101",
                     help="mapping mode: held-out scenes of the bounded time-to-PSNR run in the headline line")
-    ap.add_argument("--tile", default="auto", help="window mode: WxH tile shape instead of the autotuner's choice")
+    ap.add_argument("--tile", default="auto",
+                    help="mapping and window modes: WxH[/batch_depth/bwd_threads] instead of the autotuner's choice")
     ap.add_argument("--profile", action="store_true",
                     help="run --steps iterations between cudaProfilerStart/Stop after the warm-up and exit "
                          "(for ncu --profile-from-start off); prints no bench line")
@@ -1246,7 +1261,7 @@ def main():
 
     # targets: renders of the unperturbed set at every pose (setup, untimed)
     g_tgt = gsr.Gaussians.from_arrays(target.mean_op, target.quat, target.logscale, target.sh)
-    tiling = gsr.tiling_struct(16, 16)
+    tiling = gsr.tiling_struct(16, 16)  # the targets' renders (the image does not depend on the tiling)
     vb = gsr.ViewBuffers(N_GAUSS, gsr.camera_from(cams[0]), tiling, 1024)
     gts = []
     for cam in cams:
@@ -1256,6 +1271,14 @@ def main():
         gts.append(vb.img.clone())
     del vb, g_tgt
     params = _ordered(gsr, gsr.Gaussians.from_arrays(start.mean_op, start.quat, start.logscale, start.sh), args)
+    # tile shape, staging batch depth and backward threads per tile: the
+    # autotuner's choice on the first poses (setup, untimed), or --tile
+    if args.tile == "auto":
+        from paper_2311_16728_b300.autotune import autotune
+        tile, tune = autotune(params, list(zip(cams, gts))[:4], steps=8, warmup=2)
+    else:
+        tile, tune = parse_tiling(args.tile), None
+    tiling = gsr.tiling_struct(*tile)
     ms = gsr.MappingStep(params, list(zip(cams, gts)), tiling)
     ms.capture()
     clocks = ClockSampler(local)
@@ -1362,9 +1385,12 @@ def main():
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     # the captured DRAM traffic is the room scene's in the Morton-ordered
-    # store; other scenes and orders report none
-    traffic = NCU_TRAFFIC if (args.scene == "room" and args.order == "morton") else {}
-    stages = stage_rooflines(stage_ms, work, peaks, clk, traffic)
+    # store with the default launch shape; other configurations report none
+    traffic = NCU_TRAFFIC if (args.scene == "room" and args.order == "morton" and
+                              tuple(tile) == (16, 16, 0, 0)) else {}
+    stages = stage_rooflines(stage_ms, work, peaks, clk, traffic,
+                             bwd_kernel="render_bwd_q4_kernel" if (tile[:2] == (16, 16) and tile[3] != 128)
+                             else "render_bwd_kernel")
     dom = max(stage_ms, key=stage_ms.get)
     roof = dict(stages[dom])
 
@@ -1373,6 +1399,11 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; Replica-shaped)",
             "config": _config({"pairs_last_step": pairs, "poses": len(cams), "scene": args.scene,
                                "map_order": args.order,
+                               "tile": label(tile) + (" (autotuned)" if tune else " (given)"),
+                               **({"autotune": {"candidates": len(tune["ms_per_step"]),
+                                                "ms_per_step_best": min(tune["ms_per_step"].values()),
+                                                "ms_per_step_default": tune["ms_per_step"].get(
+                                                    label((16, 16, 0, 0)))}} if tune else {}),
                                **({"workload": WORKLOAD_WALLS} if args.scene == "walls" else {})}),
             "roofline": roof, "stages_ms": stage_ms, "stage_rooflines": stages, "work": work,
             "gpu_launches": launches, "clocks": clk,
@@ -1449,7 +1480,7 @@ def sort_passes(tiles: int) -> int:
     return -(-(32 + max(1, (tiles - 1).bit_length())) // 8)
 
 
-def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None):
+def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None, bwd_kernel="render_bwd_q4_kernel"):
     """Roofline entry of each stage's dominant kernel: algorithmic work per
     launch (per-unit figure x the units of one launch) / measured stage time,
     against the measured HBM copy bandwidth or the FP32 peak (148 SMs x 128
@@ -1492,7 +1523,7 @@ def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None):
             out[st] = hbm_entry("ssim kernels", 12 * px,
                                 "rendered + target read (2 x 4 B) and dL/dI written (4 B) per pixel-channel")
         elif st == "blend_bwd":
-            out[st] = alu_entry("render_bwd_q4_kernel", FLOPS_PER_BLEND_BWD * E,
+            out[st] = alu_entry(bwd_kernel, FLOPS_PER_BLEND_BWD * E,
                                 f"{FLOPS_PER_BLEND_BWD} FP32 per (pixel, Gaussian) evaluation x blends")
         elif st == "preprocess_bwd":
             out[st] = hbm_entry("preprocess_bwd_kernel", (236 + 236) * nv,

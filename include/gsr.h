@@ -91,13 +91,22 @@ typedef struct {
     int32_t width, height;
 } gsr_camera;
 
-/* Screen tiling.  tile_w x tile_h pixels per tile: tile_h even, tile_w a
- * divisor or a multiple of 32, tile_w * tile_h a multiple of 64 and at most
- * 1024 (the blend kernels run one thread per two vertically adjacent pixels).
- * The rendered image does not depend on the tiling: each Gaussian only
- * reaches the pixels of its own 3-sigma pixel box. */
+/* Screen tiling and the blend kernels' launch shape, all pure performance
+ * choices (the autotuner's knobs): the rendered image does not depend on
+ * them, since each Gaussian only reaches the pixels of its own 3-sigma pixel
+ * box and the per-pixel arithmetic is the same in every shape.
+ *  - tile_w x tile_h pixels per tile: tile_h even, tile_w a divisor or a
+ *    multiple of 32, tile_w * tile_h a multiple of 64 and at most 1024.
+ *  - batch_depth: depth-ordered records staged in shared memory per round by
+ *    the blend kernels; 0 = one per thread, else a multiple of 32 up to 512.
+ *  - bwd_threads: threads per tile of the backward blend; 0 = the default
+ *    (64, four pixels a thread, for 16 x 16 tiles; tile_w * tile_h / 2
+ *    otherwise), 128 for 16 x 16 tiles = two pixels a thread, else
+ *    tile_w * tile_h / 2.  The forward always runs two pixels a thread. */
 typedef struct {
     int32_t tile_w, tile_h;
+    int32_t batch_depth;
+    int32_t bwd_threads;
 } gsr_tiling;
 
 /* Per-Gaussian screen-space record written by gsr_preprocess (caller-owned,

@@ -39,7 +39,7 @@ class gsr_camera(ctypes.Structure):
 
 
 class gsr_tiling(ctypes.Structure):
-    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32)]
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch_depth", c_int32), ("bwd_threads", c_int32)]
 
 
 class gsr_proj(ctypes.Structure):

@@ -1,14 +1,17 @@
-"""Autotuner for the screen tiling of the mapping iteration.
+"""Autotuner for the screen tiling and launch shape of the mapping iteration.
 
 The rendered image does not depend on the tiling (each Gaussian reaches only
-its own pixel box, and the tile cull never drops a pair that blends), so the
-tile shape -- which also fixes the staging batch (one record per thread per
-batch) and the threads per tile (one per two pixels) -- is a pure performance
-choice.  The tuner times a few captured iterations of each candidate on the
-caller's workload (the library's timing driver, gsr_autotune, calls back to
-set up, step and release each candidate and times the steps with CUDA
-events), checks that every candidate renders a bit-identical image, and
-caches the winner per (GPU, width, height, Gaussian-count bucket).
+its own pixel box, and the tile cull never drops a pair that blends) nor on
+the blend kernels' launch shape, so all three knobs are pure performance
+choices: the tile shape, the staging batch depth (depth-ordered records
+staged in shared memory per round: one per thread, or 32 .. 256) and the
+backward blend's threads per tile (for 16 x 16 tiles: 64 threads of four
+pixels, or 128 of two).  The tuner times a few captured iterations of every
+(tile, depth, threads) candidate on the caller's workload (the library's
+timing driver, gsr_autotune, calls back to set up, step and release each
+candidate and times the steps with CUDA events), checks that every candidate
+renders a bit-identical image, and caches the winner per (GPU, width,
+height, Gaussian-count bucket).
 """
 from __future__ import annotations
 
@@ -25,7 +28,29 @@ from . import _lib as L
 from .raster import Gaussians, MappingStep, ViewBuffers, camera_from, ensure_capacity, tiling_struct
 
 # (tile_w, tile_h): every shape the blend kernels accept with 64..512 threads
-CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (8, 32), (16, 8), (32, 16), (16, 32), (32, 32))
+TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (8, 32), (16, 8), (32, 16), (16, 32), (32, 32))
+# staging batch depths (0: one record per thread of each kernel)
+DEPTHS: Tuple[int, ...] = (0, 32, 64, 128, 256)
+
+
+def grid(tiles: Sequence[Tuple[int, int]], depths: Sequence[int] = DEPTHS) -> Tuple[Tuple[int, int, int, int], ...]:
+    """(tile_w, tile_h, batch_depth, bwd_threads) candidates: every tile x
+    depth, and for 16 x 16 tiles both backward launch shapes (0 = 64 threads
+    of four pixels, 128 = two pixels a thread)."""
+    out = []
+    for tw, th in tiles:
+        for d in depths:
+            for bt in ((0, 128) if (tw, th) == (16, 16) else (0,)):
+                out.append((tw, th, d, bt))
+    return tuple(out)
+
+
+def label(c) -> str:
+    tw, th, d, bt = c
+    return f"{tw}x{th}/depth{d or 'T'}/bwd{bt or 'default'}"
+
+
+CANDIDATES = grid(TILES)
 
 
 def _key(width: int, height: int, n: int) -> str:
@@ -63,10 +88,11 @@ def _tune(n: int, setup, step, release, warmup: int, steps: int):
     return [float(v) for v in ms], int(best.value)
 
 
-def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int, int]] = CANDIDATES,
+def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int, int, int, int]] = CANDIDATES,
              steps: int = 10, warmup: int = 3, cache_path: Optional[str] = None, verbose: bool = False):
-    """Returns ((tile_w, tile_h), report).  `views` = [(camera, gt image)] as for
-    MappingStep; the caller's parameters are not modified."""
+    """Returns ((tile_w, tile_h, batch_depth, bwd_threads), report).  `views` =
+    [(camera, gt image)] as for MappingStep; the caller's parameters are not
+    modified."""
     cam0 = camera_from(views[0][0])
     key = _key(cam0.width, cam0.height, params.n)
     cache = {}
@@ -79,8 +105,7 @@ def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int,
     state = {"ref": None, "ms": None}
 
     def setup(c):
-        tw, th = candidates[c]
-        tiling = tiling_struct(tw, th)
+        tiling = tiling_struct(*candidates[c])
         # image check on the first view, untouched parameters
         vb = ViewBuffers(params.n, cam0, tiling, 1024)
         ensure_capacity(vb, params)
@@ -89,9 +114,9 @@ def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int,
         if state["ref"] is None:
             state["ref"] = img
         same = bool(torch.equal(img, state["ref"]))
-        report["identical_image"][f"{tw}x{th}"] = same
+        report["identical_image"][label(candidates[c])] = same
         if not same:
-            raise RuntimeError(f"tiling {tw}x{th} changed the rendered image")
+            raise RuntimeError(f"tiling {label(candidates[c])} changed the rendered image")
         del vb
         # timing on a copy of the parameters
         state["ms"] = MappingStep(_clone(params), views, tiling)
@@ -100,14 +125,14 @@ def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int,
     def release(c):
         state["ms"] = None
 
-    times, _ = _tune(len(candidates), setup, lambda c: state["ms"].step(), release, warmup, steps)
-    for (tw, th), t in zip(candidates, times):
-        report["ms_per_step"][f"{tw}x{th}"] = t
+    times, best = _tune(len(candidates), setup, lambda c: state["ms"].step(), release, warmup, steps)
+    for c, t in zip(candidates, times):
+        report["ms_per_step"][label(c)] = t
         if verbose:
-            print(f"autotune {tw}x{th}: {t:.4f} ms/step")
-    best = min(report["ms_per_step"], key=report["ms_per_step"].get)
-    tile = tuple(int(v) for v in best.split("x"))
+            print(f"autotune {label(c)}: {t:.4f} ms/step")
+    tile = tuple(int(v) for v in candidates[best])
     report["tile"] = list(tile)
+    report["chosen"] = label(tile)
     if cache_path:
         cache[key] = report
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
@@ -117,15 +142,18 @@ def autotune(params: Gaussians, views: Sequence, candidates: Sequence[Tuple[int,
 
 
 # tile shapes the persistent window kernel accepts (256 pixels, 128 threads)
-WINDOW_CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (8, 32))
+WINDOW_TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (8, 32))
+WINDOW_CANDIDATES = grid(WINDOW_TILES)
 
 
 def autotune_window(params: Gaussians, keyframes: Sequence, levels: int = 3,
-                    candidates: Sequence[Tuple[int, int]] = WINDOW_CANDIDATES, steps: int = 10, warmup: int = 3,
-                    cache_path: Optional[str] = None, verbose: bool = False):
-    """Tile shape of the batched pyramid window: every candidate must render
-    every view bit-identically; the fastest captured iteration wins.  Returns
-    ((tile_w, tile_h), report); the caller's parameters are not modified."""
+                    candidates: Sequence[Tuple[int, int, int, int]] = WINDOW_CANDIDATES, steps: int = 10,
+                    warmup: int = 3, cache_path: Optional[str] = None, verbose: bool = False):
+    """Tile shape, staging batch depth and backward threads per tile of the
+    batched pyramid window: every candidate must render every view
+    bit-identically; the fastest captured iteration wins.  Returns
+    ((tile_w, tile_h, batch_depth, bwd_threads), report); the caller's
+    parameters are not modified."""
     from .batched import BatchedWindow
     cam0 = camera_from(keyframes[0][0])
     key = "window|" + _key(cam0.width, cam0.height, params.n) + f"|kf{len(keyframes)}|l{levels}"
@@ -139,8 +167,7 @@ def autotune_window(params: Gaussians, keyframes: Sequence, levels: int = 3,
     state = {"ref": None, "bw": None}
 
     def setup(c):
-        tw, th = candidates[c]
-        bw = BatchedWindow(_clone(params), keyframes, levels=levels, tiling=tiling_struct(tw, th))
+        bw = BatchedWindow(_clone(params), keyframes, levels=levels, tiling=tiling_struct(*candidates[c]))
         bw.preprocess()
         bw.bin_sort()
         bw.iterate()
@@ -149,9 +176,9 @@ def autotune_window(params: Gaussians, keyframes: Sequence, levels: int = 3,
         if state["ref"] is None:
             state["ref"] = imgs
         same = all(torch.equal(a, b) for a, b in zip(imgs, state["ref"]))
-        report["identical_image"][f"{tw}x{th}"] = same
+        report["identical_image"][label(candidates[c])] = same
         if not same:
-            raise RuntimeError(f"tiling {tw}x{th} changed a rendered view")
+            raise RuntimeError(f"tiling {label(candidates[c])} changed a rendered view")
         # the eager pass above left screen-space gradients behind: clear them
         bw.g2.zero_()
         bw.capture()
@@ -160,17 +187,16 @@ def autotune_window(params: Gaussians, keyframes: Sequence, levels: int = 3,
     def release(c):
         bw, state["bw"] = state["bw"], None
         if bw is not None and bw.status.item() != 0:
-            tw, th = candidates[c]
-            raise RuntimeError(f"tiling {tw}x{th}: device status {bw.status.item():#x}")
+            raise RuntimeError(f"tiling {label(candidates[c])}: device status {bw.status.item():#x}")
 
-    times, _ = _tune(len(candidates), setup, lambda c: state["bw"].step(), release, warmup, steps)
-    for (tw, th), t in zip(candidates, times):
-        report["ms_per_step"][f"{tw}x{th}"] = t
+    times, best = _tune(len(candidates), setup, lambda c: state["bw"].step(), release, warmup, steps)
+    for c, t in zip(candidates, times):
+        report["ms_per_step"][label(c)] = t
         if verbose:
-            print(f"autotune window {tw}x{th}: {t:.4f} ms/step")
-    best = min(report["ms_per_step"], key=report["ms_per_step"].get)
-    tile = tuple(int(v) for v in best.split("x"))
+            print(f"autotune window {label(c)}: {t:.4f} ms/step")
+    tile = tuple(int(v) for v in candidates[best])
     report["tile"] = list(tile)
+    report["chosen"] = label(tile)
     if cache_path:
         cache[key] = report
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)

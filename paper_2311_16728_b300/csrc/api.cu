@@ -59,6 +59,16 @@ int32_t validate_tiling(const gsr_tiling *t) {
                   "of 64, at most 1024");
         return GSR_ERR_INVALID_ARG;
     }
+    if (t->batch_depth < 0 || t->batch_depth > 512 || t->batch_depth % 32 != 0) {
+        set_error("tiling: batch_depth must be 0 or a multiple of 32 up to 512");
+        return GSR_ERR_INVALID_ARG;
+    }
+    const int half = t->tile_w * t->tile_h / 2;
+    const bool q16 = t->tile_w == 16 && t->tile_h == 16;
+    if (!(t->bwd_threads == 0 || t->bwd_threads == half || (q16 && t->bwd_threads == 64))) {
+        set_error("tiling: bwd_threads must be 0, tile_w * tile_h / 2, or 64 for 16 x 16 tiles");
+        return GSR_ERR_INVALID_ARG;
+    }
     return GSR_OK;
 }
 

@@ -141,6 +141,7 @@ struct IterArgs {
     const uint32_t *vals;
     const uint2 *ranges;
     int tw, th;
+    int depth;  // staging batch of the blend phases (0: one record per thread)
     float bg0, bg1, bg2;
     int nviews, tiles_total, loss_items;
     float lambda;
@@ -231,6 +232,7 @@ __device__ __forceinline__ RenderArgs view_args(const IterArgs &a, const IterVie
     r.H = v.H;
     r.tw = a.tw;
     r.th = a.th;
+    r.depth = a.depth;
     r.gx = v.gx;
     r.tile_off = v.tile_off;
     r.bg0 = a.bg0;
@@ -253,7 +255,7 @@ __device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
 
 // kQuad: the views' tiles are 16 x 16 (quadrant warps; box tests from staged
 // lane masks), one instance per tiling so the blend loops carry no branch
-template <bool kQuad>
+template <bool kQuad, bool kQ4>
 __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const __grid_constant__ IterArgs a) {
     extern __shared__ float4 smem4[];
     float *smf = reinterpret_cast<float *>(smem4);
@@ -300,9 +302,9 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
     phase_stamp(a.sync, 3);
     // ---- phase 4: backward blend of every (view, tile); 16 x 16 tiles run two
     // at a time, one per 64-thread half of the CTA (four pixels per thread)
-    if constexpr (kQuad) {
+    if constexpr (kQ4) {
         const int half = (int)(threadIdx.x >> 6);
-        float4 *sm = smem4 + half * (render_q4_smem() / sizeof(float4));
+        float4 *sm = smem4 + half * (render_q4_smem(a.depth > 0 ? a.depth : kQ4Threads) / sizeof(float4));
         for (int it = next_item_half(a.sync + 3, &s_item2[half]); it < a.tiles_total;
              it = next_item_half(a.sync + 3, &s_item2[half])) {
             const int v = view_of_tile(a, it);
@@ -314,16 +316,16 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
         for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
             const int v = view_of_tile(a, it);
             const IterView &w = a.view[v];
-            render_bwd_tile<false>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
+            render_bwd_tile<kQuad>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
                                    a.g2, smem4);
         }
     }
 }
 
-static size_t iterate_smem() {
-    size_t s = render_bwd_smem(kIterThreads);
-    if (2 * render_q4_smem() > s) s = 2 * render_q4_smem();
-    if (render_fwd_smem(kIterThreads) > s) s = render_fwd_smem(kIterThreads);
+static size_t iterate_smem(int depth, bool q4) {
+    size_t s = render_bwd_smem(depth > 0 ? depth : kIterThreads);
+    if (q4 && 2 * render_q4_smem(depth > 0 ? depth : kQ4Threads) > s) s = 2 * render_q4_smem(depth > 0 ? depth : kQ4Threads);
+    if (render_fwd_smem(depth > 0 ? depth : kIterThreads) > s) s = render_fwd_smem(depth > 0 ? depth : kIterThreads);
     if (sizeof(float) * kPass1Floats > s) s = sizeof(float) * kPass1Floats;
     if (sizeof(float) * kPass2Floats > s) s = sizeof(float) * kPass2Floats;
     return s;
@@ -577,6 +579,7 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     a.ranges = reinterpret_cast<const uint2 *>(tile_ranges);
     a.tw = tiling->tile_w;
     a.th = tiling->tile_h;
+    a.depth = tiling->batch_depth;
     a.bg0 = bg ? bg[0] : 0.f;
     a.bg1 = bg ? bg[1] : 0.f;
     a.bg2 = bg ? bg[2] : 0.f;
@@ -632,9 +635,13 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     a.loss_items = items;
     cudaStream_t st = as_cuda(stream);
     if (cudaMemsetAsync(a.sync, 0, 8 * sizeof(unsigned), st) != cudaSuccess) return check_launch("memset sync");
-    const size_t smem = iterate_smem();
-    auto kernel = tiling->tile_w == 16 && tiling->tile_h == 16 ? batched_iterate_kernel<true>
-                                                               : batched_iterate_kernel<false>;
+    // 16 x 16 tiles: the backward phase runs two tiles per CTA, one per
+    // 64-thread half (four pixels a thread), unless bwd_threads asks for 128
+    const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
+    const bool q4 = quad && tiling->bwd_threads != kIterThreads;
+    const size_t smem = iterate_smem(tiling->batch_depth, q4);
+    auto kernel = q4 ? batched_iterate_kernel<true, true>
+                     : (quad ? batched_iterate_kernel<true, false> : batched_iterate_kernel<false, false>);
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

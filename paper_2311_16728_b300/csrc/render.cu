@@ -65,6 +65,7 @@ static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const ui
     a.th = t->tile_h;
     a.gx = grid_x(cam, t);
     a.tile_off = 0;
+    a.depth = t->batch_depth;
     a.bg0 = bg ? bg[0] : 0.f;
     a.bg1 = bg ? bg[1] : 0.f;
     a.bg2 = bg ? bg[2] : 0.f;
@@ -87,13 +88,14 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     }
     const RenderArgs a = make_args(proj, vals, tile_ranges, cam, tiling, bg);
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
+    const int depth = a.depth > 0 ? a.depth : nthr;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
     auto kernel = n_blended ? (quad ? render_fwd_kernel<true, true> : render_fwd_kernel<true, false>)
                             : (quad ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
     // (per device and cheap, not a stream operation: fine during capture)
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_fwd_smem(nthr));
-    kernel<<<tiles, nthr, render_fwd_smem(nthr), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_fwd_smem(depth));
+    kernel<<<tiles, nthr, render_fwd_smem(depth), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
     return check_launch("render_fwd_kernel");
 }
 
@@ -123,15 +125,20 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
     const RenderArgs a = make_args(proj, vals, tile_ranges, cam, tiling, bg);
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
-    if (tiling->tile_w == 16 && tiling->tile_h == 16) {
-        render_bwd_q4_kernel<<<tiles, kQ4Threads, render_q4_smem(), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
-                                                                          grad2d->g1, grad2d->g2);
+    const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
+    if (quad && tiling->bwd_threads != nthr) {  // 64 threads, four pixels each (the default)
+        const int depth = a.depth > 0 ? a.depth : kQ4Threads;
+        cudaFuncSetAttribute(render_bwd_q4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)render_q4_smem(depth));
+        render_bwd_q4_kernel<<<tiles, kQ4Threads, render_q4_smem(depth), st>>>(a, T_final, n_contrib, dL_dimg,
+                                                                               grad2d->g0, grad2d->g1, grad2d->g2);
         return check_launch("render_bwd_q4_kernel");
     }
-    auto kernel = render_bwd_kernel<false>;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_bwd_smem(nthr));
-    kernel<<<tiles, nthr, render_bwd_smem(nthr), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0,
-                                                                  grad2d->g1, grad2d->g2);
+    const int depth = a.depth > 0 ? a.depth : nthr;
+    auto kernel = quad ? render_bwd_kernel<true> : render_bwd_kernel<false>;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_bwd_smem(depth));
+    kernel<<<tiles, nthr, render_bwd_smem(depth), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0, grad2d->g1,
+                                                        grad2d->g2);
     return check_launch("render_bwd_kernel");
 }
 

@@ -14,6 +14,7 @@ struct RenderArgs {
     const uint32_t *vals;
     const uint2 *ranges;  // indexed by tile_off + local tile
     int W, H, tw, th, gx, tile_off;
+    int depth;  // records staged per round (0: one per thread)
     float bg0, bg1, bg2;
 };
 
@@ -250,11 +251,11 @@ template <bool kQuad>
 __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, float *__restrict__ img,
                                                 float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
                                                 uint32_t *__restrict__ n_blended, float4 *smem) {
-    const int nthr = blockDim.x, nwarps = nthr >> 5;
-    float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * nthr);
-    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + nthr);  // 4 per staged splat (kQuad)
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * nthr);
+    const int nthr = blockDim.x, nwarps = nthr >> 5, D = a.depth > 0 ? a.depth : nthr;
+    float4 *s_xy = smem, *s_cb = smem + D, *s_rgb = smem + 2 * D;
+    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * D);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + D);  // 4 per staged splat (kQuad)
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * D);
     int px, py0, ox, oy;
     thread_pixels(a, tile, px, py0, ox, oy);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -269,16 +270,17 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
     p.last0 = p.last1 = p.nb0 = p.nb1 = 0u;
     p.done0 = !in0;
     p.done1 = !in1;
-    for (int base = begin; base < end; base += nthr) {
+    for (int base = begin; base < end; base += D) {
         // stop the whole tile once every pixel has terminated
         if (__syncthreads_count(p.done0 && p.done1) == nthr) break;
-        const int idx = base + (int)threadIdx.x;
-        if (idx < end) stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x],
-                                          s_rgb[threadIdx.x], s_lo[threadIdx.x], s_mask[threadIdx.x],
-                                          s_lanes + 4 * threadIdx.x);
-        else s_mask[threadIdx.x] = 0u;
+        for (int sl = (int)threadIdx.x; sl < D; sl += nthr) {
+            const int idx = base + sl;
+            if (idx < end) stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_xy[sl], s_cb[sl], s_rgb[sl],
+                                              s_lo[sl], s_mask[sl], s_lanes + 4 * sl);
+            else s_mask[sl] = 0u;
+        }
         __syncthreads();
-        const int cnt = min(nthr, end - base);
+        const int cnt = min(D, end - base);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             // warp-ballot early termination: leave once no pixel of the warp accumulates
             if (__all_sync(0xffffffffu, p.done0 && p.done1)) break;
@@ -430,13 +432,13 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                                                 const uint32_t *__restrict__ n_contrib,
                                                 const float *__restrict__ dL_dimg, float *__restrict__ g0,
                                                 float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
-    const int nthr = blockDim.x, nwarps = nthr >> 5;
-    float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * nthr);
-    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + nthr);  // 4 per staged splat (kQuad)
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * nthr);
-    uint32_t *s_gid = s_mask + nthr;
-    uint32_t *s_max = s_gid + nthr;  // 32 entries
+    const int nthr = blockDim.x, nwarps = nthr >> 5, D = a.depth > 0 ? a.depth : nthr;
+    float4 *s_xy = smem, *s_cb = smem + D, *s_rgb = smem + 2 * D;
+    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * D);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + D);  // 4 per staged splat (kQuad)
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * D);
+    uint32_t *s_gid = s_mask + D;
+    uint32_t *s_max = s_gid + D;  // 32 entries
     int px, py0, ox, oy;
     thread_pixels(a, tile, px, py0, ox, oy);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -479,17 +481,19 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
     // value k of the transposed reduction lands in lane 4k: its gradient slot
     const int kval = (lane >> 2) & 7;
     float *const gk = (kval < 4 ? g0 : g1) + (kval & 3);
-    for (int bend = stop; bend > begin; bend -= nthr) {
-        const int bstart = max(begin, bend - nthr);
+    for (int bend = stop; bend > begin; bend -= D) {
+        const int bstart = max(begin, bend - D);
         __syncthreads();
-        const int idx = bstart + (int)threadIdx.x;
-        if (idx < bend) {
-            const uint32_t gid = a.vals[idx];
-            s_gid[threadIdx.x] = gid;
-            stage_splat<kQuad>(a, gid, ox, oy, nwarps, s_xy[threadIdx.x], s_cb[threadIdx.x], s_rgb[threadIdx.x],
-                               s_lo[threadIdx.x], s_mask[threadIdx.x], s_lanes + 4 * threadIdx.x);
-        } else {
-            s_mask[threadIdx.x] = 0u;
+        for (int sl = (int)threadIdx.x; sl < D; sl += nthr) {
+            const int idx = bstart + sl;
+            if (idx < bend) {
+                const uint32_t gid = a.vals[idx];
+                s_gid[sl] = gid;
+                stage_splat<kQuad>(a, gid, ox, oy, nwarps, s_xy[sl], s_cb[sl], s_rgb[sl], s_lo[sl], s_mask[sl],
+                                   s_lanes + 4 * sl);
+            } else {
+                s_mask[sl] = 0u;
+            }
         }
         __syncthreads();
         const int cnt = bend - bstart;
@@ -540,12 +544,13 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
 }
 
 
-// dynamic shared memory of the two tile routines for `nthr` threads
-__host__ __device__ inline size_t render_fwd_smem(int nthr) {
-    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + sizeof(uint32_t)) * nthr;
+// dynamic shared memory of the two tile routines for a staging batch of
+// `depth` records
+__host__ __device__ inline size_t render_fwd_smem(int depth) {
+    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + sizeof(uint32_t)) * depth;
 }
-__host__ __device__ inline size_t render_bwd_smem(int nthr) {
-    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + 2 * sizeof(uint32_t)) * nthr +
+__host__ __device__ inline size_t render_bwd_smem(int depth) {
+    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + 2 * sizeof(uint32_t)) * depth +
            32 * sizeof(uint32_t);
 }
 

@@ -129,12 +129,13 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                                                    float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
     using G = Q4Group<kHalf>;
     constexpr int nthr = kQ4Threads;
-    float4 *s_xy = smem, *s_cb = smem + nthr, *s_rgb = smem + 2 * nthr;
-    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * nthr);
-    uint4 *s_lanes = reinterpret_cast<uint4 *>(s_lo + nthr);
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 2 * nthr);
-    uint32_t *s_gid = s_mask + nthr;
-    uint32_t *s_max = s_gid + nthr;  // 2 entries
+    const int D = a.depth > 0 ? a.depth : nthr;
+    float4 *s_xy = smem, *s_cb = smem + D, *s_rgb = smem + 2 * D;
+    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * D);
+    uint4 *s_lanes = reinterpret_cast<uint4 *>(s_lo + D);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 2 * D);
+    uint32_t *s_gid = s_mask + D;
+    uint32_t *s_max = s_gid + D;  // 2 entries
     const int ti = G::tid();
     int px, py0, ox, oy;
     q4_pixels(a, tile, ti, px, py0, ox, oy);
@@ -182,16 +183,19 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     // value k of the transposed reduction lands in lane 4k: its gradient slot
     const int kval = (lane >> 2) & 7;
     float *const gk = (kval < 4 ? g0 : g1) + (kval & 3);
-    for (int bend = stop; bend > begin; bend -= nthr) {
-        const int bstart = max(begin, bend - nthr);
+    for (int bend = stop; bend > begin; bend -= D) {
+        const int bstart = max(begin, bend - D);
         G::sync();
-        const int idx = bstart + ti;
-        if (idx < bend) {
-            const uint32_t gid = a.vals[idx];
-            s_gid[ti] = gid;
-            q4_stage<kHalf>(a, gid, ox, oy, s_xy[ti], s_cb[ti], s_rgb[ti], s_lo[ti], s_mask[ti], s_lanes + 2 * ti);
-        } else {
-            s_mask[ti] = 0u;
+        for (int sl = ti; sl < D; sl += nthr) {
+            const int idx = bstart + sl;
+            if (idx < bend) {
+                const uint32_t gid = a.vals[idx];
+                s_gid[sl] = gid;
+                q4_stage<kHalf>(a, gid, ox, oy, s_xy[sl], s_cb[sl], s_rgb[sl], s_lo[sl], s_mask[sl],
+                                s_lanes + 2 * sl);
+            } else {
+                s_mask[sl] = 0u;
+            }
         }
         G::sync();
         const int cnt = bend - bstart;
@@ -281,9 +285,10 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     }
 }
 
-// shared memory of one tile's 64 threads (a multiple of 16 bytes)
-__host__ __device__ inline size_t render_q4_smem() {
-    return ((3 * sizeof(float4) + sizeof(float2) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * kQ4Threads +
+// shared memory of one tile's 64 threads for a staging batch of `depth`
+// records (a multiple of 16 bytes)
+__host__ __device__ inline size_t render_q4_smem(int depth = kQ4Threads) {
+    return ((3 * sizeof(float4) + sizeof(float2) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * depth +
             2 * sizeof(uint32_t) + 15) / 16 * 16;
 }
 

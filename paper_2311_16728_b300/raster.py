@@ -113,8 +113,10 @@ def camera_at_level(cam: L.gsr_camera, level: int) -> L.gsr_camera:
     return out
 
 
-def tiling_struct(tile_w: int = 16, tile_h: int = 16) -> L.gsr_tiling:
-    return L.gsr_tiling(int(tile_w), int(tile_h))
+def tiling_struct(tile_w: int = 16, tile_h: int = 16, batch_depth: int = 0, bwd_threads: int = 0) -> L.gsr_tiling:
+    """Tile shape and the blend kernels' staging batch depth and backward
+    threads per tile (0 = the defaults); none of them changes the image."""
+    return L.gsr_tiling(int(tile_w), int(tile_h), int(batch_depth), int(bwd_threads))
 
 
 def n_tiles(cam: L.gsr_camera, tiling: L.gsr_tiling) -> int:

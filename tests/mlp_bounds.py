@@ -26,8 +26,15 @@ side, which joins the |h| of the next layer's weight gradient.  Like the
 forward's, this is a model bound (each operand element within two BF16 ulps
 of the oracle's), not a worst case over every possible cascade of roundings; `tests/test_mlp_bounds.py` pins it on the CPU against
 an FP32 / BF16 simulation of the tensor-core arithmetic and shows that a
-planted mistake leaves it.  For the Adam step that follows, `adam_bounds`
-carries a gradient bound through the update by the mean value theorem.
+planted mistake leaves it.  The model misses one kind of element: sums
+over units that are almost never active, or of activations whose FP32
+pre-activation cancels to near 0, where another valid summation order moves
+the value by far more than two BF16 ulps.  `order_spread` measures that per
+element: n simulations of the GPU's arithmetic with independently permuted
+summation orders; the test's tolerance is the model bound plus
+SPREAD_FACTOR times the largest deviation among them.  For the Adam step
+that follows, `adam_bounds` carries a gradient bound through the update by
+the mean value theorem.
 """
 from __future__ import annotations
 
@@ -72,6 +79,68 @@ def gradient_bounds(fw: dict, dy: np.ndarray, g_ref: dict) -> dict:
     for k in out:
         assert out[k].shape == np.shape(g_ref[k]), k
     return out
+
+
+def _bf(a):
+    from oracle import mlp as omlp
+    return omlp.bf16_round(a).astype(np.float32)
+
+
+def simulate(params: dict, x: np.ndarray, t: np.ndarray, weight: np.ndarray, rng=None) -> dict:
+    """The MLP's training-step gradients in the GPU's arithmetic on the CPU:
+    BF16 operands, FP32 sums (numpy's float32 GEMMs), BF16 roundings of the
+    activations and gradients where the GPU makes them, FP32 column sums for
+    the biases.  With `rng`, every reduction (the K inputs of layer 1, the
+    hidden units of layers 2 and 3 and of the backward products, the M rows
+    of the weight gradients and bias sums) runs in an independently permuted
+    order: another, equally valid FP32 summation order."""
+    f = np.float32
+    M, K0 = x.shape
+    H, N3 = params["W2"].shape[0], params["W3"].shape[0]
+    pk = rng.permutation(K0) if rng is not None else np.arange(K0)
+    ph1 = rng.permutation(H) if rng is not None else np.arange(H)
+    ph2 = rng.permutation(H) if rng is not None else np.arange(H)
+    pn = rng.permutation(N3) if rng is not None else np.arange(N3)
+    pm = rng.permutation(M) if rng is not None else np.arange(M)
+    xb, W1, W2, W3 = _bf(x), _bf(params["W1"]), _bf(params["W2"]), _bf(params["W3"])
+    pre1 = (xb[:, pk] @ W1[:, pk].T).astype(f) + params["b1"]
+    h1 = _bf(np.maximum(pre1, 0))
+    pre2 = (h1[:, ph1] @ W2[:, ph1].T).astype(f) + params["b2"]
+    h2 = _bf(np.maximum(pre2, 0))
+    y = (h2[:, ph2] @ W3[:, ph2].T).astype(f) + params["b3"]
+    w = np.asarray(weight, f)[None, :]
+    dy = (f(2.0) * ((y - t) * w) * (f(1.0) / f(M))).astype(f)
+    dyb = _bf(dy)
+    g = {"W3": (dyb[pm].T @ h2[pm]).astype(f), "b3": dy[pm].sum(0, dtype=f)}
+    dpre2 = (dyb[:, pn] @ W3[pn]).astype(f) * (h2 > 0)
+    g["W2"] = (_bf(dpre2)[pm].T @ h1[pm]).astype(f)
+    g["b2"] = dpre2[pm].sum(0, dtype=f)
+    dpre1 = (_bf(dpre2)[:, ph1] @ W2[ph1]).astype(f) * (h1 > 0)
+    g["W1"] = (_bf(dpre1)[pm].T @ xb[pm]).astype(f)
+    g["b1"] = dpre1[pm].sum(0, dtype=f)
+    return {k: v.astype(np.float64) for k, v in g.items()}
+
+
+def order_spread(params: dict, x: np.ndarray, t: np.ndarray, weight: np.ndarray, g_ref: dict, n: int = 3,
+                 seed: int = 0) -> dict:
+    """Per element, the largest deviation from the FP64 oracle among n
+    simulations in the GPU's arithmetic with independently permuted summation
+    orders: how far a valid FP32 / BF16 evaluation of that element can land
+    from the oracle.  It is large exactly where the model bound is optimistic
+    (units that are almost never active, pre-activations that cancel to near
+    0, ReLU masks that flip), and stays at rounding level elsewhere."""
+    rng = np.random.default_rng(seed)
+    out = {k: np.zeros_like(np.asarray(v, np.float64)) for k, v in g_ref.items()}
+    for _ in range(n):
+        gs = simulate(params, x, t, weight, rng)
+        for k in out:
+            out[k] = np.maximum(out[k], np.abs(gs[k] - g_ref[k]))
+    return out
+
+
+# the tolerance of an MLP gradient element: the model bound plus this many
+# times the summation-order spread
+SPREAD_FACTOR = 4.0
 
 
 def adam_bounds(p0, m0, v0, g, e_g, lr, t, b1, b2, eps):

@@ -99,6 +99,16 @@ def test_bad_arguments_are_rejected_on_the_host(gsr):
     rc = L.gsr_preprocess.raw(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(bad_tiling), ctypes.byref(proj),
                               None, None)
     assert rc == L.GSR_ERR_INVALID_ARG
+    # launch shapes: staging batch a multiple of 32 up to 512; backward
+    # threads 0, two pixels a thread, or 64 for 16 x 16 tiles
+    for bad in [(16, 16, 48, 0), (16, 16, 1024, 0), (16, 16, -32, 0), (32, 8, 0, 64), (16, 16, 0, 256)]:
+        rc = L.gsr_preprocess.raw(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(gsr.tiling_struct(*bad)),
+                                  ctypes.byref(proj), None, None)
+        assert rc == L.GSR_ERR_INVALID_ARG, bad
+    sz = ctypes.c_size_t()
+    for ok in [(16, 16, 32, 0), (16, 16, 512, 128), (16, 16, 0, 64), (32, 8, 256, 128), (8, 32, 64, 0)]:
+        assert L.gsr_bin_sort_workspace_size.raw(10, 16, ctypes.byref(cam), ctypes.byref(gsr.tiling_struct(*ok)),
+                                                 ctypes.byref(sz)) == 0, ok
     # workspace too small
     rc = L.gsr_bin_sort.raw(ctypes.byref(proj), 10, ctypes.byref(cam), ctypes.byref(good_tiling), 16, 16, 100, 16, 16,
                             16, 1, None, None)

@@ -126,7 +126,9 @@ def test_window_gradient_is_sum_of_single_views(size2):
     assert max(norms.values()) <= 1e-5
 
 
-def test_window_matches_oracle_tiny():
+# the default launch shape, and the batch depth / backward threads knobs
+@pytest.mark.parametrize("tiling", [(16, 16, 0, 0), (16, 16, 32, 128), (32, 8, 256, 0)])
+def test_window_matches_oracle_tiny(tiling):
     base = S.tiny_scene()
     cam = S.tiny_camera()
     ca0 = cam.as_array()
@@ -136,7 +138,7 @@ def test_window_matches_oracle_tiny():
     sc = oracle_scene(p)
     levels = 2
     gt_t = torch.tensor(gt0, dtype=torch.float32, device="cuda")
-    bw = BatchedWindow(to_gpu(p), [(cam, gt_t)], levels=levels)
+    bw = BatchedWindow(to_gpu(p), [(cam, gt_t)], levels=levels, tiling=gsr.tiling_struct(*tiling))
     _run_once(bw)
     gt_l = gt0
     gref = np.zeros((p.n, 60))
@@ -161,7 +163,7 @@ def test_window_matches_oracle_tiny():
     # the views' losses are mean-reduced: scale by the level-0 view's 3HW (a
     # sum-reduced loss) so that the 1e-6 floor does not pass everything
     s = 3 * cam.width * cam.height
-    assert_grad_bar("window (2 levels, x 3HW), summed parameter gradients", s * grad_planes_gpu(bw.grads), s * gref,
+    assert_grad_bar(f"window {tiling} (2 levels, x 3HW), summed parameter gradients", s * grad_planes_gpu(bw.grads), s * gref,
                     s * cond, waive=waive)
 
 

@@ -134,15 +134,18 @@ def test_render_matches_oracle_tiny():
 
 
 def test_image_independent_of_tiling():
+    """Every (tile shape, staging batch depth, backward threads) the autotuner
+    may pick renders the same image, bit for bit."""
+    from paper_2311_16728_b300.autotune import CANDIDATES, label
     p, cam = S.tiny_scene(seed=5), S.tiny_camera()
     ref = None
-    for tile in TILINGS:
+    for tile in CANDIDATES:
         vb, _ = gpu_view(p, cam, tile)
         im = vb.img.cpu().numpy()
         if ref is None:
             ref = im
         else:
-            assert np.array_equal(im, ref), f"tiling {tile} changes the image"
+            assert np.array_equal(im, ref), f"tiling {label(tile)} changes the image"
 
 
 # ragged small frames, and the mapping (1200 x 680) and densify (1920 x 1080)
@@ -168,10 +171,12 @@ def test_loss_matches_oracle(H, W):
     assert np.abs(d - d_ref).max() <= 1e-4 * scale
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32), (16, 16, 32, 0), (16, 16, 256, 128), (16, 16, 0, 128),
+                                  (32, 8, 64, 0), (32, 32, 512, 0)])
 def test_render_backward_matches_oracle_tiny(tile):
-    """16 x 16 tiles take the quadrant-warp path (staged lane masks), the
-    others the per-pixel box test."""
+    """16 x 16 tiles take the quadrant-warp path (staged lane masks; 64
+    threads of four pixels, or 128 of two), the others the per-pixel box
+    test; staging batches of 32 .. 512 records."""
     p, cam = S.perturb(S.tiny_scene()), S.tiny_camera()
     vb, g = gpu_view(p, cam, tile=tile)
     ca = cam.as_array()

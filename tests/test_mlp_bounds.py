@@ -74,6 +74,23 @@ def test_fp32_simulation_inside_the_bounds():
             assert np.linalg.norm(err) <= 0.1 * np.linalg.norm(bb[k]), k
 
 
+def test_order_spread_covers_another_order_and_not_a_mistake():
+    """The tolerance (model bound + SPREAD_FACTOR x the spread of six
+    permuted-order simulations) covers two more simulations in yet other
+    orders, and a planted mistake leaves it."""
+    from mlp_bounds import SPREAD_FACTOR, order_spread, simulate
+    p, x, t, w, fw, g_ref, bb = _setup(6, 640)
+    sp = order_spread(p, x, t, w, g_ref, n=6, seed=1)
+    for seed in (98, 99):
+        g4 = simulate(p, x, t, w, np.random.default_rng(seed))
+        for k in g_ref:
+            tol = bb[k] + SPREAD_FACTOR * sp[k]
+            assert (np.abs(g4[k] - g_ref[k]) <= tol).all(), (seed, k)
+    _, gm = _simulate(p, x, t, w, drop_mask=True)
+    tol = bb["W2"] + SPREAD_FACTOR * sp["W2"]
+    assert (np.abs(gm["W2"] - g_ref["W2"]) > tol).any()
+
+
 def test_planted_mistake_leaves_the_bounds():
     p, x, t, w, fw, g_ref, bb = _setup(4, 96)
     _, g = _simulate(p, x, t, w, drop_mask=True)  # the layer-2 ReLU mask forgotten
