@@ -740,7 +740,7 @@ def _smoothed_reached(curve, target, k=TTP_SMOOTH):
     return len(tail) == k and statistics.mean(tail) >= target
 
 
-def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, every, gsr, torch):
+def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, every, gsr, torch, levels=3):
     """One arm: fresh map = truth with the held-out primitives initialised by
     `init`; iterate until the running mean of the last TTP_SMOOTH evaluations
     reaches `target` PSNR (if given) or for `budget` iterations.  Returns the
@@ -753,7 +753,7 @@ def _ttp_run(kind, truth, keyframes, kps, offsets, init, li, budget, target, eve
     else:
         densify_default(params, keyframes, kps, offsets)
     ev = Evaluator(TTP_N, keyframes)
-    mapper = PlainMapper(params, keyframes) if kind == "plain" else BatchedWindow(params, keyframes)
+    mapper = PlainMapper(params, keyframes, levels=levels) if kind == "plain" else BatchedWindow(params, keyframes)
     mapper.capture()
     curve = [(0, 0.0, ev(params))]
     it, wall = 0, 0.0
@@ -784,7 +784,7 @@ def _first_at(curve, target, k=TTP_SMOOTH):
 
 
 def ttp_experiment(eval_seeds, train_seeds=TTP_TRAIN_SEEDS, harvest_iters=TTP_HARVEST_ITERS,
-                   mlp_steps=TTP_MLP_STEPS, budget=TTP_BUDGET):
+                   mlp_steps=TTP_MLP_STEPS, budget=TTP_BUDGET, ablation_levels=()):
     """Time to PSNR (the second half of the headline metric).  The learned
     initialiser is trained inside the run, on the GPU, from (patch, converged
     parameter) pairs harvested from window runs on the training scenes; then
@@ -792,8 +792,11 @@ def ttp_experiment(eval_seeds, train_seeds=TTP_TRAIN_SEEDS, harvest_iters=TTP_HA
     schedule, default initialisation) runs `budget` iterations and fixes the
     target PSNR (the mean of its last TTP_SMOOTH evaluations), and the
     batched window with the learned and with the default initialisation run
-    until the running mean of their evaluations reaches it.  Returns
-    (per-seed results, training summary)."""
+    until the running mean of their evaluations reaches it.  With
+    `ablation_levels`, the plain path also runs the same budget with each of
+    those pyramid level counts (the 3-level run is the target's) on the same
+    scenes: the Gaussian-pyramid ablation.  Returns (per-seed results,
+    training summary)."""
     import torch
     import paper_2311_16728_b300 as gsr
     from paper_2311_16728_b300.batched import BatchedWindow
@@ -832,8 +835,29 @@ def ttp_experiment(eval_seeds, train_seeds=TTP_TRAIN_SEEDS, harvest_iters=TTP_HA
             it, ms = _first_at(c, target)
             res[name] = {"curve": c, "iters": it, "ms": ms, "psnr0": c[0][2]}
         res["plain"]["psnr0"] = plain[0][2]
+        res["levels"] = {3: plain}
+        for L in ablation_levels:
+            if L != 3:
+                res["levels"][L] = _ttp_run("plain", truth, keyframes, kps, offsets, "default", li, budget, None, 100,
+                                            gsr, torch, levels=L)
         per_seed.append(res)
     return per_seed, training
+
+
+def gp_ablation_summary(per_seed, checkpoints=(400, TTP_BUDGET)) -> dict:
+    """PSNR of the plain path after each checkpoint's iterations with n + 1
+    pyramid levels (mean over the scenes, and per scene), and the training
+    time to it: the replica of the paper's Tab. 4 rows."""
+    out = {}
+    levels = sorted(set().union(*(r["levels"].keys() for r in per_seed)))
+    for L in levels:
+        row = {}
+        for c in checkpoints:
+            pts = [next(pt for pt in r["levels"][L] if pt[0] >= c) for r in per_seed if L in r["levels"]]
+            row[str(c)] = {"psnr_mean": statistics.mean(p[2] for p in pts), "psnr": [p[2] for p in pts],
+                           "ms_mean": statistics.mean(p[1] for p in pts)}
+        out[f"n={L - 1}"] = row
+    return out
 
 
 def ttp_summary(per_seed) -> dict:
@@ -1439,8 +1463,13 @@ def main():
         t_x = time.time()
         line["window"] = window_figure(args)
         seeds = [int(x) for x in args.headline_ttp_seeds.split(",") if x]
-        per_seed, training = ttp_experiment(seeds)
+        per_seed, training = ttp_experiment(seeds, ablation_levels=(1, 2, 4))
         line["ttp"] = {"workload": TTP_WORKLOAD, "eval_seeds": seeds, **training, **ttp_summary(per_seed)}
+        line["gp_ablation"] = {
+            "workload": "the time-to-PSNR scenes above, default initialisation, plain path (one view per iteration, "
+                        "tau_u 30) with n + 1 pyramid levels (n = 0: no pyramid); PSNR over the keyframes after 400 "
+                        f"and {TTP_BUDGET} iterations (Tab. 4 replica)",
+            "levels": gp_ablation_summary(per_seed)}
         line["extras_s"] = round(time.time() - t_x, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -498,7 +498,10 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
         __syncthreads();
         const int cnt = bend - bstart;
         for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            // splats at or beyond the warp's last contributor reach none of its pixels
+            const int j0 = c0 + lane;
+            uint32_t bits = __ballot_sync(0xffffffffu, j0 < cnt && ((s_mask[j0] >> wid) & 1u) &&
+                                                           (uint32_t)(bstart + j0 - begin) < m);
             // two splats per round, back to front: both are evaluated first
             // (independent), then applied in order, then reduced together
             while (bits) {

@@ -200,7 +200,10 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
         G::sync();
         const int cnt = bend - bstart;
         for (int c0 = ((cnt - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && ((s_mask[c0 + lane] >> wid) & 1u));
+            // splats at or beyond the warp's last contributor reach none of its pixels
+            const int j0 = c0 + lane;
+            uint32_t bits = __ballot_sync(0xffffffffu, j0 < cnt && ((s_mask[j0] >> wid) & 1u) &&
+                                                           (uint32_t)(bstart + j0 - begin) < m);
             while (bits) {  // back to front
                 const int j = c0 + 31 - __clz(bits);
                 bits &= ~(1u << (j - c0));
@@ -270,15 +273,26 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                         v2[4] = __ffma2_rn(dpow, __fmul2_rn(__fmul2_rn(f2(-0.5f), dy[h]), dy[h]), v2[4]);
                     }
                 }
-                if (__any_sync(0xffffffffu, any)) {
+                const uint32_t act = __ballot_sync(0xffffffffu, any);
+                if (act) {
                     float v[9];
 #pragma unroll
                     for (int q = 0; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
-                    float v8;
-                    const float y = warp_transpose_sum(v, v8);
                     const uint32_t gid = s_gid[j];
-                    if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
-                    else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+                    if (__popc(act) <= 2) {
+                        // one or two lanes hold all of it: their own vector
+                        // atomics cost less than the warp reduction
+                        if (any) {
+                            atomicAdd(reinterpret_cast<float4 *>(g0) + gid, make_float4(v[0], v[1], v[2], v[3]));
+                            atomicAdd(reinterpret_cast<float4 *>(g1) + gid, make_float4(v[4], v[5], v[6], v[7]));
+                            atomicAdd(g2 + 4 * (int64_t)gid, v[8]);
+                        }
+                    } else {
+                        float v8;
+                        const float y = warp_transpose_sum(v, v8);
+                        if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
+                        else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+                    }
                 }
             }
         }

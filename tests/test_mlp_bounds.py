@@ -1,11 +1,11 @@
-"""CPU pins of the MLP parity bounds (tests/mlp_bounds.py): an FP32 / BF16
-simulation of the tensor-core arithmetic (BF16 operands, FP32 sums in
-another order, BF16 roundings of activations and gradients at the GPU's
-places) stays inside the per-element bounds; its normwise error is far
+"""CPU pins of the MLP parity bounds (tests/mlp_bounds.py): FP32 / BF16
+simulations of the tensor-core arithmetic (BF16 operands, FP32 sums in
+other orders, BF16 roundings of activations and gradients at the GPU's
+places) stay inside the per-element bounds; their normwise error is far
 below them; and a simulation with a planted mistake leaves them."""
 import numpy as np
 
-from mlp_bounds import adam_bounds, gradient_bounds
+from mlp_bounds import EXCEPTION_FRAC, EXCEPTION_MIN, adam_bounds, model_bounds, propagated_bounds
 from oracle import mlp as omlp
 
 
@@ -58,7 +58,16 @@ def _setup(seed, M):
     fw = omlp.forward(p, x)
     _, dy = omlp.loss_and_dy(fw["y"], t, w)
     g_ref = omlp.backward(fw, dy)
-    return p, x, t, w, fw, g_ref, gradient_bounds(fw, dy, g_ref)
+    return p, x, t, w, fw, g_ref, (model_bounds(fw, dy, g_ref), propagated_bounds(fw, dy, g_ref))
+
+
+def _check(g, g_ref, bb, label):
+    """Every element within the envelope, at most a few beyond the bar."""
+    model, env = bb
+    for k in g_ref:
+        err = np.abs(g[k] - g_ref[k])
+        assert (err <= env[k]).all(), (label, k, float((err / (env[k] + 1e-300)).max()))
+        assert int((err > model[k]).sum()) <= max(EXCEPTION_MIN, EXCEPTION_FRAC * err.size), (label, k)
 
 
 def test_fp32_simulation_inside_the_bounds():
@@ -67,35 +76,30 @@ def test_fp32_simulation_inside_the_bounds():
         y, g = _simulate(p, x, t, w)
         scale = np.abs(fw["W3"]) @ np.abs(fw["h2"]).T
         assert (np.abs(y - fw["y"]) <= 2 ** -7 * scale.T + 1e-4).all()  # the forward test's bound
+        _check(g, g_ref, bb, (seed, M))
         for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
-            err = np.abs(g[k] - g_ref[k])
-            assert (err <= bb[k]).all(), (k, float((err / (bb[k] + 1e-300)).max()))
-            # the actual error sits well inside: normwise below a tenth of the bound's norm
-            assert np.linalg.norm(err) <= 0.1 * np.linalg.norm(bb[k]), k
+            # the actual error sits well inside the bar: normwise below a tenth of its norm
+            assert np.linalg.norm(np.abs(g[k] - g_ref[k])) <= 0.1 * np.linalg.norm(bb[0][k]), k
 
 
-def test_order_spread_covers_another_order_and_not_a_mistake():
-    """The tolerance (model bound + SPREAD_FACTOR x the spread of six
-    permuted-order simulations) covers two more simulations in yet other
-    orders, and a planted mistake leaves it."""
-    from mlp_bounds import SPREAD_FACTOR, order_spread, simulate
-    p, x, t, w, fw, g_ref, bb = _setup(6, 640)
-    sp = order_spread(p, x, t, w, g_ref, n=6, seed=1)
-    for seed in (98, 99):
-        g4 = simulate(p, x, t, w, np.random.default_rng(seed))
-        for k in g_ref:
-            tol = bb[k] + SPREAD_FACTOR * sp[k]
-            assert (np.abs(g4[k] - g_ref[k]) <= tol).all(), (seed, k)
-    _, gm = _simulate(p, x, t, w, drop_mask=True)
-    tol = bb["W2"] + SPREAD_FACTOR * sp["W2"]
-    assert (np.abs(gm["W2"] - g_ref["W2"]) > tol).any()
+def test_bounds_cover_simulations_in_permuted_orders():
+    """Simulations of the GPU's arithmetic whose every reduction runs in an
+    independently permuted order (other valid FP32 summation orders, so other
+    BF16 roundings downstream) all stay inside the envelope with at most a
+    few elements beyond the bar, also at a batch of 2,048 rows with
+    near-dead units."""
+    from mlp_bounds import simulate
+    for seed, M in ((6, 640), (7, 2048)):
+        p, x, t, w, fw, g_ref, bb = _setup(seed, M)
+        for r in range(3):
+            _check(simulate(p, x, t, w, np.random.default_rng(100 + r)), g_ref, bb, (M, r))
 
 
 def test_planted_mistake_leaves_the_bounds():
     p, x, t, w, fw, g_ref, bb = _setup(4, 96)
     _, g = _simulate(p, x, t, w, drop_mask=True)  # the layer-2 ReLU mask forgotten
-    assert (np.abs(g["W2"] - g_ref["W2"]) > bb["W2"]).any()
-    assert (np.abs(g["b2"] - g_ref["b2"]) > bb["b2"]).any()
+    assert (np.abs(g["W2"] - g_ref["W2"]) > bb[1]["W2"]).any()
+    assert (np.abs(g["b2"] - g_ref["b2"]) > bb[1]["b2"]).any()
 
 
 def test_adam_bound_covers_a_perturbed_gradient():
