@@ -1409,9 +1409,12 @@ def main():
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     # the captured DRAM traffic is the room scene's in the Morton-ordered
-    # store with the default launch shape; other configurations report none
+    # store with 16x16 tiles and the four-pixel backward; the batch depth only
+    # sets how many of a tile's records are staged per shared-memory round,
+    # not which are read, so it applies at every depth.  Other configurations
+    # report none.
     traffic = NCU_TRAFFIC if (args.scene == "room" and args.order == "morton" and
-                              tuple(tile) == (16, 16, 0, 0)) else {}
+                              tuple(tile[:2]) == (16, 16) and tile[3] in (0, 64)) else {}
     stages = stage_rooflines(stage_ms, work, peaks, clk, traffic,
                              bwd_kernel="render_bwd_q4_kernel" if (tile[:2] == (16, 16) and tile[3] != 128)
                              else "render_bwd_kernel")
@@ -1480,8 +1483,8 @@ def main():
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
 # with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
 # loss stage is its two SSIM passes, the binning stage its seven kernels).
-NCU_TRAFFIC = {"preprocess": 15.454464e6, "bin_sort": 21.094912e6, "render_fwd": 4.217856e6, "loss": 69.083904e6,
-               "blend_bwd": 20.793600e6, "preprocess_bwd": 12.432640e6, "adam": 393.139456e6}
+NCU_TRAFFIC = {"preprocess": 15.456512e6, "bin_sort": 21.096448e6, "render_fwd": 4.531968e6, "loss": 68.919296e6,
+               "blend_bwd": 21.037056e6, "preprocess_bwd": 12.435200e6, "adam": 393.341184e6}
 # the pose chain (profiles/pose_bwd_300k_1200x680.md)
 NCU_TRAFFIC_POSE = 15.037952e6
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)

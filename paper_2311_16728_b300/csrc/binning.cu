@@ -561,7 +561,10 @@ __device__ __forceinline__ void warp_stage(uint64_t (&v)[8], uint32_t lane) {
         for (uint32_t e = 0; e < 8; ++e) {
             const bool up = ((32 * e + lane) & K) == 0;
             const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], J);
-            v[e] = (lower == up) ? (v[e] < o ? v[e] : o) : (v[e] < o ? o : v[e]);
+            // the lane keeps the smaller key when it is the lower one of an
+            // ascending pair (or the upper one of a descending pair): one
+            // decision, one 64-bit select (keys are unique)
+            if ((o < v[e]) == (lower == up)) v[e] = o;
         }
     }
     if constexpr (J > 1) warp_stage<K, J / 2>(v, lane);
