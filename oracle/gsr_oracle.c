@@ -318,8 +318,9 @@ int orc_decide(int64_t n, const float *mean_op, const float *quat, const float *
  * Pixels of a dropped pair would all have alpha < 1/255 by a factor-two
  * margin, so they are skipped by the per-pixel rule anyway: the image does
  * not change and stays independent of the tile shape.  q_min is 0 when the
- * projected mean lies in R, else the smallest value over R's four edges,
- * each minimised in closed form (the 1D quadratic's vertex, clamped). */
+ * projected mean lies in R, else the smallest value over the edges of R that
+ * face the mean (one or two), each minimised in closed form (the 1D
+ * quadratic's vertex, clamped). */
 #define ORC_TILE_ALPHA_MIN 0x1.010102p-9f /* 0.5 / 255 in binary32 */
 
 static float qform32(float A, float B, float C, float dx, float dy) {
@@ -333,18 +334,22 @@ static int tile_keep(float u, float v, const float *conic, float op, float x0, f
     if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
         q = 0.0f;
     } else {
+        /* The minimum lies on the edges that face the mean: a ray from the
+           mean to any other boundary point enters the rectangle through one
+           of them first, and the form grows along a ray from the mean.  So
+           only the vertical edge on the mean's side (when u is outside
+           [x0, x1]) and the horizontal edge on its side (when v is outside
+           [y0, y1]) are evaluated. */
         q = INFINITY;
-        for (int e = 0; e < 2; ++e) {
-            const float xe = e ? x1 : x0;
-            const float dx = xe - u;
+        if (u < x0 || u > x1) {
+            const float dx = (u < x0 ? x0 : x1) - u;
             float ys = v - (B * dx) / C;
             ys = fminf(fmaxf(ys, y0), y1);
             const float dy = ys - v;
-            q = fminf(q, qform32(A, B, C, dx, dy));
+            q = qform32(A, B, C, dx, dy);
         }
-        for (int e = 0; e < 2; ++e) {
-            const float ye = e ? y1 : y0;
-            const float dy = ye - v;
+        if (v < y0 || v > y1) {
+            const float dy = (v < y0 ? y0 : y1) - v;
             float xs = u - (B * dy) / A;
             xs = fminf(fmaxf(xs, x0), x1);
             const float dx = xs - u;

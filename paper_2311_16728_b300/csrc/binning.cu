@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(
 
 // ---------------------------------------------------------------- tile scan
 constexpr int kTileScanThreads = 1024;
-constexpr uint32_t kWarpTile = 256;      // segments this short are sorted by one warp, in registers
+constexpr uint32_t kWarpTile = 512;      // segments this short are sorted by one warp, in registers
 constexpr uint32_t kSmallTile = 1024;    // longest segment of the one-block shared-memory sort
 constexpr uint32_t kLargeTile = 16384;   // longest segment sorted in shared memory
 
@@ -537,44 +537,72 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *s, uint32_t P) {
     }
 }
 
-// The same network over 256 entries held in one warp's registers: entry
-// i = 32 e + lane sits in v[e] of that lane, so partners at distance J < 32
-// are a lane apart (shuffle) and partners at J >= 32 are registers of the
-// same lane.  Stages are unrolled at compile time; sizes above P are skipped.
-template <uint32_t K, uint32_t J>
-__device__ __forceinline__ void warp_stage(uint64_t (&v)[8], uint32_t lane) {
-    if constexpr (J >= 32) {
-        constexpr uint32_t EJ = J / 32;
+// The same network over P <= 32 E entries held in one warp's registers,
+// lane-major: entry i = E lane + e sits in v[e] of that lane, so partners at
+// distance J < E are registers of the same lane and partners at J >= E are
+// J / E lanes apart (one shuffle each).  With E = P / 32 the first log2(E)
+// merge levels and the short stages of every later level stay in registers.
+// Stages are unrolled at compile time; sizes above P are skipped.
+template <int E, uint32_t K, uint32_t J>
+__device__ __forceinline__ void warp_stage(uint64_t (&v)[E], uint32_t lane) {
+    if constexpr (J < (uint32_t)E) {
 #pragma unroll
-        for (uint32_t e = 0; e < 8; ++e)
-            if ((e & EJ) == 0) {
-                const bool up = ((32 * e + lane) & K) == 0;
-                const uint64_t a = v[e], b = v[e | EJ];
+        for (uint32_t e = 0; e < (uint32_t)E; ++e)
+            if ((e & J) == 0) {
+                // ascending when bit K of the entry's index E lane + e is clear
+                bool up;
+                if constexpr (K < (uint32_t)E) up = (e & K) == 0;
+                else up = (lane & (K / E)) == 0;
+                const uint64_t a = v[e], b = v[e | J];
                 if ((a > b) == up) {
                     v[e] = b;
-                    v[e | EJ] = a;
+                    v[e | J] = a;
                 }
             }
     } else {
-        const bool lower = (lane & J) == 0;
+        // K >= 2 J >= 2 E: the direction and the pair's order depend on the lane only
+        const bool keep_min = ((lane & (J / E)) == 0) == ((lane & (K / E)) == 0);
 #pragma unroll
-        for (uint32_t e = 0; e < 8; ++e) {
-            const bool up = ((32 * e + lane) & K) == 0;
-            const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], J);
+        for (uint32_t e = 0; e < (uint32_t)E; ++e) {
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], J / E);
             // the lane keeps the smaller key when it is the lower one of an
             // ascending pair (or the upper one of a descending pair): one
             // decision, one 64-bit select (keys are unique)
-            if ((o < v[e]) == (lower == up)) v[e] = o;
+            if ((o < v[e]) == keep_min) v[e] = o;
         }
     }
-    if constexpr (J > 1) warp_stage<K, J / 2>(v, lane);
+    if constexpr (J > 1) warp_stage<E, K, J / 2>(v, lane);
 }
 
-template <uint32_t K>
-__device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[8], uint32_t lane, uint32_t P) {
+template <int E, uint32_t K>
+__device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[E], uint32_t lane, uint32_t P) {
     if (K > P) return;
-    warp_stage<K, K / 2>(v, lane);
-    if constexpr (K < 256) warp_sort_regs<2 * K>(v, lane, P);
+    warp_stage<E, K, K / 2>(v, lane);
+    if constexpr (K < 32u * E) warp_sort_regs<E, 2 * K>(v, lane, P);
+}
+
+// Tile t's segment seg[b, b + L) (L <= 32 E) sorted by one warp in
+// registers and emitted: loaded coalesced (the input order is free), stored
+// from the lane-major sorted order.
+template <int E>
+__device__ __forceinline__ void warp_tile_sort(const uint64_t *__restrict__ seg, uint32_t t, uint32_t b, uint32_t L,
+                                               uint32_t P, uint32_t lane, uint64_t *__restrict__ keys,
+                                               uint32_t *__restrict__ vals) {
+    uint64_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = 32u * e + lane;
+        v[e] = i < L ? seg[b + i] : ~0ull;
+    }
+    warp_sort_regs<E, 2>(v, lane, P);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)E * lane + e;
+        if (i < L) {
+            keys[b + i] = ((uint64_t)t << 32) | (v[e] >> 32);
+            vals[b + i] = (uint32_t)v[e];
+        }
+    }
 }
 
 // sorted (depth << 32 | index) of tile t -> keys (tile << 32 | depth), vals
@@ -750,21 +778,12 @@ __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uin
         const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
         uint32_t P = 1;
         while (P < L) P <<= 1;
-        uint64_t v[8];
-#pragma unroll
-        for (uint32_t q = 0; q < 8; ++q) {
-            const uint32_t i = 32 * q + lane;
-            v[q] = i < L ? seg[b + i] : ~0ull;
-        }
-        warp_sort_regs<2>(v, lane, P);
-#pragma unroll
-        for (uint32_t q = 0; q < 8; ++q) {
-            const uint32_t i = 32 * q + lane;
-            if (i < L) {
-                keys[b + i] = ((uint64_t)t << 32) | (v[q] >> 32);
-                vals[b + i] = (uint32_t)v[q];
-            }
-        }
+        // E = P / 32 entries a lane (at least one)
+        if (P <= 32) warp_tile_sort<1>(seg, t, b, L, P, lane, keys, vals);
+        else if (P <= 64) warp_tile_sort<2>(seg, t, b, L, P, lane, keys, vals);
+        else if (P <= 128) warp_tile_sort<4>(seg, t, b, L, P, lane, keys, vals);
+        else if (P <= 256) warp_tile_sort<8>(seg, t, b, L, P, lane, keys, vals);
+        else warp_tile_sort<16>(seg, t, b, L, P, lane, keys, vals);
     }
     for (uint32_t e = blockIdx.x; e < n_block; e += gridDim.x) {
         const uint32_t t = list2[e];

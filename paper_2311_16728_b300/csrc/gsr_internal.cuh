@@ -290,10 +290,14 @@ __device__ __forceinline__ float2 uv_residual(const float4 mo, const CamK &cam, 
 
 // Tile cull.  A (Gaussian, tile) pair is kept when opacity exp(-q_min / 2)
 // >= 0.5 / 255, q_min being the continuous minimum of d^T Sigma'^-1 d over
-// R = tile x pixel box (0 when the mean lies in R, else the least of R's four
-// edges, each minimised at its clamped 1D vertex).  A dropped pair has alpha
-// < 1/255 at every pixel by a factor-two margin, so the per-pixel skip would
-// drop it anyway: the image does not depend on this cull or on the tiling.
+// R = tile x pixel box: 0 when the mean lies in R, else the least over the
+// edges of R that face the mean (the vertical one on the mean's side when u
+// is outside [x0, x1], the horizontal one when v is outside [y0, y1]; a ray
+// from the mean to any other boundary point enters R through one of them
+// first, and the form grows along the ray), each minimised at its clamped 1D
+// vertex.  A dropped pair has alpha < 1/255 at every pixel by a factor-two
+// margin, so the per-pixel skip would drop it anyway: the image does not
+// depend on this cull or on the tiling.
 constexpr float kTileAlphaMin = 0x1.010102p-9f;  // 0.5 / 255 in binary32
 
 __device__ __forceinline__ float qform32(float A, float B, float C, float dx, float dy) {
@@ -307,16 +311,14 @@ __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, fl
         q = 0.0f;
     } else {
         q = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float dx = FS(e ? x1 : x0, u);
+        if (u < x0 || u > x1) {
+            const float dx = FS(u < x0 ? x0 : x1, u);
             float ys = FS(v, FD(FM(B, dx), C));
             ys = fminf(fmaxf(ys, y0), y1);
-            q = fminf(q, qform32(A, B, C, dx, FS(ys, v)));
+            q = qform32(A, B, C, dx, FS(ys, v));
         }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float dy = FS(e ? y1 : y0, v);
+        if (v < y0 || v > y1) {
+            const float dy = FS(v < y0 ? y0 : y1, v);
             float xs = FS(u, FD(FM(B, dy), A));
             xs = fminf(fmaxf(xs, x0), x1);
             q = fminf(q, qform32(A, B, C, FS(xs, u), dy));

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kQ4Threads) render_bwd_q4_kernel(RenderArgs a,
                                                                    float *__restrict__ g0, float *__restrict__ g1,
                                                                    float *__restrict__ g2) {
     extern __shared__ float4 smem[];
-    render_bwd_tile_q4(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
+    render_bwd_tile_q4<false, true>(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
 static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const uint32_t *ranges,

@@ -93,23 +93,28 @@ __device__ __forceinline__ float2 mean_residual(const RenderArgs &a, uint32_t gi
 // Whether some pixel of the rectangle [rx0, rx1] x [ry0, ry1] (pixel
 // indices) can reach alpha >= 1/255, i.e. d^T Q d <= tau: a lower bound on
 // the continuous minimum of the quadratic form over the rectangle (0 when it
-// holds the mean, else the least of its four edges, each at its clamped 1D
-// vertex, less a bound on the rounding of the terms) against tau with a
-// margin far above the FP32 error of this test and of the per-pixel alpha.
+// holds the mean, else the least over the one or two edges that face the
+// mean -- the same minimum as over all four, since a ray from the mean
+// reaches every other boundary point through them and the form grows along
+// it -- each at its clamped 1D vertex, less a bound on the rounding of the
+// terms) against tau with a margin far above the FP32 error of this test and
+// of the per-pixel alpha.
 // Only warps that cannot see the splat are dropped; the per-pixel test
 // decides every blend, so the image does not depend on this test.
 __device__ __forceinline__ bool rect_may_see(float u, float v, float A, float B, float C, float tau, float rx0,
                                              float rx1, float ry0, float ry1) {
-    if (u >= rx0 && u <= rx1 && v >= ry0 && v <= ry1) return true;
+    const bool out_x = u < rx0 || u > rx1, out_y = v < ry0 || v > ry1;
+    if (!(out_x || out_y)) return true;
     float lb = __int_as_float(0x7f800000);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
+        if (!(e ? out_y : out_x)) continue;
         float dx, dy;
-        if (e < 2) {  // vertical edges: dy at the edge's vertex, clamped to the rectangle
-            dx = (e ? rx1 : rx0) - u;
+        if (e == 0) {  // the vertical edge on the mean's side: dy at its vertex, clamped to the rectangle
+            dx = (u < rx0 ? rx0 : rx1) - u;
             dy = fminf(fmaxf(-__fdividef(B * dx, C), ry0 - v), ry1 - v);
-        } else {      // horizontal edges
-            dy = (e == 3 ? ry1 : ry0) - v;
+        } else {       // the horizontal edge on the mean's side
+            dy = (v < ry0 ? ry0 : ry1) - v;
             dx = fminf(fmaxf(-__fdividef(B * dy, A), rx0 - u), rx1 - u);
         }
         const float t1 = A * dx * dx, t2 = 2.0f * B * dx * dy, t3 = C * dy * dy;

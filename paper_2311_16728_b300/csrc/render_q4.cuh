@@ -122,7 +122,7 @@ struct PairBwd {
     float2 T, accd, dC0, dC1, dC2;
 };
 
-template <bool kHalf = false>
+template <bool kHalf = false, bool kExact = kHalf>
 __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile, const float *__restrict__ T_final,
                                                    const uint32_t *__restrict__ n_contrib,
                                                    const float *__restrict__ dL_dimg, float *__restrict__ g0,
@@ -191,7 +191,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
             if (idx < bend) {
                 const uint32_t gid = a.vals[idx];
                 s_gid[sl] = gid;
-                q4_stage<kHalf>(a, gid, ox, oy, s_xy[sl], s_cb[sl], s_rgb[sl], s_lo[sl], s_mask[sl],
+                q4_stage<kExact>(a, gid, ox, oy, s_xy[sl], s_cb[sl], s_rgb[sl], s_lo[sl], s_mask[sl],
                                 s_lanes + 2 * sl);
             } else {
                 s_mask[sl] = 0u;
@@ -273,26 +273,15 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                         v2[4] = __ffma2_rn(dpow, __fmul2_rn(__fmul2_rn(f2(-0.5f), dy[h]), dy[h]), v2[4]);
                     }
                 }
-                const uint32_t act = __ballot_sync(0xffffffffu, any);
-                if (act) {
+                if (__any_sync(0xffffffffu, any)) {
                     float v[9];
 #pragma unroll
                     for (int q = 0; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
+                    float v8;
+                    const float y = warp_transpose_sum(v, v8);
                     const uint32_t gid = s_gid[j];
-                    if (__popc(act) <= 2) {
-                        // one or two lanes hold all of it: their own vector
-                        // atomics cost less than the warp reduction
-                        if (any) {
-                            atomicAdd(reinterpret_cast<float4 *>(g0) + gid, make_float4(v[0], v[1], v[2], v[3]));
-                            atomicAdd(reinterpret_cast<float4 *>(g1) + gid, make_float4(v[4], v[5], v[6], v[7]));
-                            atomicAdd(g2 + 4 * (int64_t)gid, v[8]);
-                        }
-                    } else {
-                        float v8;
-                        const float y = warp_transpose_sum(v, v8);
-                        if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
-                        else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
-                    }
+                    if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
+                    else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
                 }
             }
         }

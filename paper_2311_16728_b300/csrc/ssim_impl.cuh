@@ -14,6 +14,8 @@ constexpr int kLTW = 32, kLTH = 32, kLR = 5;       // output tile and window rad
 constexpr int kRW = kLTW + 2 * kLR, kRH = kLTH + 2 * kLR;
 constexpr int kRS = 45;                            // row stride of the staged region (conflict-free)
 constexpr int kRun = 4;                            // outputs per thread along a row / column
+constexpr int kMS = kLTW + 1;                      // row stride of the row-blurred maps (odd: fewer
+                                                   // bank conflicts on the row pass's stores)
 constexpr int kLThreads = 256;
 
 struct Win {
@@ -78,8 +80,8 @@ __device__ __forceinline__ void stage_region(const float *__restrict__ src, int 
     }
 }
 
-constexpr size_t kPass1Floats = 2 * kRH * kRS + 5 * kRH * kLTW;
-constexpr size_t kPass2Floats = 3 * kRH * kRS + 3 * kRH * kLTW;
+constexpr size_t kPass1Floats = 2 * kRH * kRS + 5 * kRH * kMS;
+constexpr size_t kPass2Floats = 3 * kRH * kRS + 3 * kRH * kMS;
 
 __device__ __forceinline__ float2 f2w(float x) { return make_float2(x, x); }
 
@@ -101,9 +103,9 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
                                                  float *s_red) {
     float *sX = sm, *sY = sm + kRH * kRS;
     // row-blurred moments: (mean x, mean y) and (E x^2, E y^2) pairs, then E xy
-    float2 *sM2 = reinterpret_cast<float2 *>(sm + 2 * kRH * kRS);  // [kRH][kLTW]
-    float2 *sS2 = sM2 + kRH * kLTW;                                 // [kRH][kLTW]
-    float *sXY = reinterpret_cast<float *>(sS2 + kRH * kLTW);       // [kRH][kLTW]
+    float2 *sM2 = reinterpret_cast<float2 *>(sm + 2 * kRH * kRS);  // [kRH][kMS]
+    float2 *sS2 = sM2 + kRH * kMS;                                  // [kRH][kMS]
+    float *sXY = reinterpret_cast<float *>(sS2 + kRH * kMS);        // [kRH][kMS]
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     __syncthreads();  // the previous block's readers of sm are done
@@ -111,6 +113,9 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
     stage_region<NT>(y + cb, H, W, ox, oy, sY);
     __syncthreads();
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
+        // a warp covers four rows of eight runs: the staged loads (row
+        // stride kRS) hit distinct banks, the row-blurred stores (odd row
+        // stride kMS) at most two lanes a bank
         const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
         // values and their products once per staged column
         float2 v[kRun + 10], q[kRun + 10];
@@ -132,9 +137,9 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
                 sq = __ffma2_rn(f2w(w), q[o + k], sq);
                 sxy = __fmaf_rn(w, xy[o + k], sxy);
             }
-            sM2[r * kLTW + j0 + o] = m;
-            sS2[r * kLTW + j0 + o] = sq;
-            sXY[r * kLTW + j0 + o] = sxy;
+            sM2[r * kMS + j0 + o] = m;
+            sS2[r * kMS + j0 + o] = sq;
+            sXY[r * kMS + j0 + o] = sxy;
         }
     }
     __syncthreads();
@@ -150,9 +155,9 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
             float cx[kRun + 10];
 #pragma unroll
             for (int k = 0; k < kRun + 10; ++k) {
-                cm[k] = sM2[(i0 + k) * kLTW + tx];
-                cs[k] = sS2[(i0 + k) * kLTW + tx];
-                cx[k] = sXY[(i0 + k) * kLTW + tx];
+                cm[k] = sM2[(i0 + k) * kMS + tx];
+                cs[k] = sS2[(i0 + k) * kMS + tx];
+                cx[k] = sXY[(i0 + k) * kMS + tx];
             }
 #pragma unroll
             for (int o = 0; o < kRun; ++o) {
@@ -212,8 +217,8 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
                                                  float lambda, float scale, float *__restrict__ dx_out, int bx, int by,
                                                  int c, float *sm) {
     float *sM = sm;                                                  // [3][kRH][kRS]
-    float2 *sAB = reinterpret_cast<float2 *>(sm + 3 * kRH * kRS);    // [kRH][kLTW] row-blurred (a, b)
-    float *sCh = reinterpret_cast<float *>(sAB + kRH * kLTW);        // [kRH][kLTW] row-blurred c
+    float2 *sAB = reinterpret_cast<float2 *>(sm + 3 * kRH * kRS);    // [kRH][kMS] row-blurred (a, b)
+    float *sCh = reinterpret_cast<float *>(sAB + kRH * kMS);         // [kRH][kMS] row-blurred c
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     const float inv_n = (float)((double)scale / ((double)C * (double)plane));
@@ -223,6 +228,9 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
     stage_region<NT>(mapC + cb, H, W, ox, oy, sM + 2 * kRH * kRS);
     __syncthreads();
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
+        // a warp covers four rows of eight runs: the staged loads (row
+        // stride kRS) hit distinct banks, the row-blurred stores (odd row
+        // stride kMS) at most two lanes a bank
         const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
         float2 ab[kRun + 10];
         float cc[kRun + 10];
@@ -240,8 +248,8 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
                 s2 = __ffma2_rn(f2w(win.w[k]), ab[o + k], s2);
                 s1 = __fmaf_rn(win.w[k], cc[o + k], s1);
             }
-            sAB[r * kLTW + j0 + o] = s2;
-            sCh[r * kLTW + j0 + o] = s1;
+            sAB[r * kMS + j0 + o] = s2;
+            sCh[r * kMS + j0 + o] = s1;
         }
     }
     __syncthreads();
@@ -264,8 +272,8 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
             float ccc[kRun + 10];
 #pragma unroll
             for (int k = 0; k < kRun + 10; ++k) {
-                cab[k] = sAB[(i0 + k) * kLTW + tx];
-                ccc[k] = sCh[(i0 + k) * kLTW + tx];
+                cab[k] = sAB[(i0 + k) * kMS + tx];
+                ccc[k] = sCh[(i0 + k) * kMS + tx];
             }
 #pragma unroll
             for (int o = 0; o < kRun; ++o) {
