@@ -456,26 +456,49 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
         if (overflow) raise_status(d_status, GSR_ERR_CAPACITY);
     }
     __syncthreads();
-    const uint32_t per = (T + kTileScanThreads - 1) / kTileScanThreads;
-    const uint32_t t0 = threadIdx.x * per, t1 = min(T, t0 + per);
-    uint32_t sum = 0;
-    if (!overflow)
-        for (uint32_t t = t0; t < t1; ++t) sum += ranges[2 * (size_t)t];
-    const uint32_t incl = block_incl_scan_1024(sum, s_warp);
-    uint32_t off = incl - sum;
-    for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t c = overflow ? 0u : ranges[2 * (size_t)t];
-        if (c == 0u) {
-            ranges[2 * (size_t)t] = 0u;
-            ranges[2 * (size_t)t + 1] = 0u;
-            continue;
+    // rounds of kTileScanThreads x 4 tiles: each thread loads its four
+    // tiles' counts at once (two 16-byte words when aligned), one block scan
+    // per round, the running total carried between rounds
+    constexpr uint32_t kPer = 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(ranges) & 15u) == 0u;
+    uint32_t carried = 0;
+    for (uint32_t r0 = 0; r0 < T; r0 += kTileScanThreads * kPer) {
+        const uint32_t t0 = r0 + threadIdx.x * kPer;
+        uint32_t c[kPer] = {0u, 0u, 0u, 0u};
+        if (!overflow) {
+            if (vec && t0 + kPer <= T) {
+                const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(ranges + 2 * (size_t)t0));
+                const uint4 b = __ldcg(reinterpret_cast<const uint4 *>(ranges + 2 * (size_t)t0 + 4));
+                c[0] = a.x;
+                c[1] = a.z;
+                c[2] = b.x;
+                c[3] = b.z;
+            } else {
+#pragma unroll
+                for (uint32_t k = 0; k < kPer; ++k)
+                    if (t0 + k < T) c[k] = ranges[2 * (size_t)(t0 + k)];
+            }
         }
-        ranges[2 * (size_t)t] = off;
-        ranges[2 * (size_t)t + 1] = off + c;
-        if (c <= kWarpTile) list[atomicAdd(&s_small, 1u)] = t;
-        else if (c <= kSmallTile) list2[atomicAdd(&s_mid, 1u)] = t;
-        else list[(size_t)cap - 1 - atomicAdd(&s_large, 1u)] = t;
-        off += c;
+        const uint32_t sum = c[0] + c[1] + c[2] + c[3];
+        const uint32_t incl = block_incl_scan_1024(sum, s_warp);
+        const uint32_t round_total = s_warp[31];
+        uint32_t off = carried + incl - sum;
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+            const uint32_t t = t0 + k;
+            if (t >= T) break;
+            const uint32_t n = c[k];
+            ranges[2 * (size_t)t] = n ? off : 0u;
+            ranges[2 * (size_t)t + 1] = n ? off + n : 0u;
+            if (n) {
+                if (n <= kWarpTile) list[atomicAdd(&s_small, 1u)] = t;
+                else if (n <= kSmallTile) list2[atomicAdd(&s_mid, 1u)] = t;
+                else list[(size_t)cap - 1 - atomicAdd(&s_large, 1u)] = t;
+            }
+            off += n;
+        }
+        carried += round_total;
+        __syncthreads();  // s_warp is rewritten by the next round's scan
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -485,18 +508,32 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     }
 }
 
-// every stored kept pair goes to its tile's segment at its rank
+// every stored kept pair goes to its tile's segment at its rank; a thread
+// takes four pairs a round (a grid stride apart), all loads issued first
 __global__ void __launch_bounds__(256) scatter_kernel(const uint64_t *__restrict__ kept_ts,
                                                       const uint64_t *__restrict__ kept_sk,
                                                       const int64_t *__restrict__ d_written, int64_t cap,
                                                       const uint32_t *__restrict__ ranges,
                                                       uint64_t *__restrict__ seg) {
+    constexpr int kU = 4;
     const int64_t w = *d_written;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < w; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t ts = kept_ts[i];
-        const uint32_t t = (uint32_t)(ts >> 32);
-        const uint64_t pos = (uint64_t)ranges[2 * (size_t)t] + (uint32_t)ts;
-        if (pos < (uint64_t)cap) seg[pos] = kept_sk[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < w; i0 += kU * stride) {
+        uint64_t ts[kU], sk[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t i = i0 + k * stride;
+            ts[k] = i < w ? kept_ts[i] : 0ull;
+            sk[k] = i < w ? kept_sk[i] : 0ull;
+        }
+        uint32_t b[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) b[k] = i0 + k * stride < w ? ranges[2 * (size_t)(ts[k] >> 32)] : 0u;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const uint64_t pos = (uint64_t)b[k] + (uint32_t)ts[k];
+            if (i0 + k * stride < w && pos < (uint64_t)cap) seg[pos] = sk[k];
+        }
     }
 }
 

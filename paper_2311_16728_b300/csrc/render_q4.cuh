@@ -233,14 +233,17 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                                     e.y <= 0.0f && al[h].y >= kAlphaMin;
                     any = any || ok[2 * h] || ok[2 * h + 1];
                 }
+                // v2[0 .. 2]: the lane's dpow-weighted moments in dy (sum dpow,
+                // sum dpow dy, sum dpow dy^2), from which the five conic and
+                // mean sums follow once per lane (dx is the lane's own);
+                // v2[5 .. 8]: the opacity and colour sums
                 float2 v2[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) v2[q] = make_float2(0.f, 0.f);
+                const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
+                const float C = cb.x * (1.0f / kHalfLog2e);
                 if (any) {
                     const float4 col = s_rgb[j];
-                    const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
-                    const float C = cb.x * (1.0f / kHalfLog2e);
-                    const float Adx = A * dx, Bdx = B * dx, hdx2 = -0.5f * dx * dx;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
@@ -266,17 +269,22 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                         P.accd = __ffma2_rn(dc, al_e, __fmul2_rn(P.accd, one_m));
                         const float2 dpow = __fmul2_rn(dalpha, al_g);
                         v2[5] = __ffma2_rn(dalpha, g_g, v2[5]);
-                        v2[0] = __ffma2_rn(dpow, __ffma2_rn(f2(B), dy[h], f2(Adx)), v2[0]);
-                        v2[1] = __ffma2_rn(dpow, __ffma2_rn(f2(C), dy[h], f2(Bdx)), v2[1]);
-                        v2[2] = __ffma2_rn(dpow, f2(hdx2), v2[2]);
-                        v2[3] = __ffma2_rn(__fmul2_rn(dpow, f2(-dx)), dy[h], v2[3]);
-                        v2[4] = __ffma2_rn(dpow, __fmul2_rn(__fmul2_rn(f2(-0.5f), dy[h]), dy[h]), v2[4]);
+                        const float2 tdy = __fmul2_rn(dpow, dy[h]);
+                        v2[0] = __fadd2_rn(v2[0], dpow);
+                        v2[1] = __fadd2_rn(v2[1], tdy);
+                        v2[2] = __ffma2_rn(tdy, dy[h], v2[2]);
                     }
                 }
                 if (__any_sync(0xffffffffu, any)) {
                     float v[9];
+                    const float S0 = v2[0].x + v2[0].y, S1 = v2[1].x + v2[1].y, S2 = v2[2].x + v2[2].y;
+                    v[0] = __fmaf_rn(B, S1, (A * dx) * S0);  // dL/du: sum dpow (A dx + B dy)
+                    v[1] = __fmaf_rn(C, S1, (B * dx) * S0);  // dL/dv: sum dpow (B dx + C dy)
+                    v[2] = (-0.5f * dx * dx) * S0;           // dL/dA: sum dpow (-dx^2 / 2)
+                    v[3] = -dx * S1;                         // dL/dB: sum dpow (-dx dy)
+                    v[4] = -0.5f * S2;                       // dL/dC: sum dpow (-dy^2 / 2)
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
+                    for (int q = 5; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
                     float v8;
                     const float y = warp_transpose_sum(v, v8);
                     const uint32_t gid = s_gid[j];

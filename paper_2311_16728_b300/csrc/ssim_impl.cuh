@@ -183,7 +183,7 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
                 const float sxx = ss[o].x - mx * mx, syy = ss[o].y - my * my, sxy = sxyv[o] - mx * my;
                 const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
                 const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-                const float iB = 1.0f / (B1 * B2);
+                const float iB = __fdividef(1.0f, B1 * B2);  // B1 B2 >= C1 C2 > 0: the fast reciprocal (2 ulp)
                 const float S = A1 * A2 * iB;
                 // 1 / B1 = B2 iB and 1 / B2 = B1 iB: one division per pixel
                 const float dS_dmx = 2.f * my * A2 * iB - S * 2.f * mx * (B2 * iB);
