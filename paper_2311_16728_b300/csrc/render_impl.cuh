@@ -123,16 +123,31 @@ __device__ __forceinline__ bool rect_may_see(float u, float v, float A, float B,
     return lb <= tau * 1.001f + 1e-3f;
 }
 
+// One staged splat: everything a warp reads per splat in the blend loops, in
+// one 96-byte record (one address per splat, the fields at immediate
+// offsets).  The warp masks stay in their own array (the ballot reads 32
+// consecutive ones).
+struct __align__(16) Staged {
+    float4 xy;       // mean (u, v), pre-scaled conic terms a2, b2
+    float4 cb;       // pre-scaled c2, opacity, packed pixel box
+    float4 rgb;      // colour, depth
+    float2 lo;       // position residual
+    uint32_t gid, pad;
+    uint4 lanes[2];  // box lane masks: 4 x uint2 (quadrant warps) or 2 x uint4 (16 x 8 half warps)
+};
+static_assert(sizeof(Staged) == 96, "staged splat record");
+
 template <bool kQuad>
 __device__ __forceinline__ void stage_splat(const RenderArgs &a, uint32_t gid, int ox, int oy, int nwarps,
-                                            float4 &s_xy, float4 &s_cb, float4 &s_rgb, float2 &s_lo,
-                                            uint32_t &s_mask, uint2 *s_lanes) {
+                                            Staged &st, uint32_t &s_mask) {
     const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
-    s_rgb = __ldg(a.rgb_depth + gid);
-    s_lo = mean_residual(a, gid);
+    st.rgb = __ldg(a.rgb_depth + gid);
+    st.lo = mean_residual(a, gid);
+    st.gid = gid;
     const float A = g.z, B = g.w, C = c.x, op = c.y;
-    s_xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
-    s_cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
+    st.xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
+    st.cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
+    uint2 *s_lanes = reinterpret_cast<uint2 *>(st.lanes);
     uint32_t mask = 0u;
     const float tau = 2.0f * __logf(255.0f * op);  // alpha >= 1/255  <=>  d^T Q d <= tau
     if (tau > 0.0f) {
@@ -257,10 +272,8 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
                                                 float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
                                                 uint32_t *__restrict__ n_blended, float4 *smem) {
     const int nthr = blockDim.x, nwarps = nthr >> 5, D = a.depth > 0 ? a.depth : nthr;
-    float4 *s_xy = smem, *s_cb = smem + D, *s_rgb = smem + 2 * D;
-    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * D);
-    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + D);  // 4 per staged splat (kQuad)
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * D);
+    Staged *s_st = reinterpret_cast<Staged *>(smem);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_st + D);
     int px, py0, ox, oy;
     thread_pixels(a, tile, px, py0, ox, oy);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -280,8 +293,7 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
         if (__syncthreads_count(p.done0 && p.done1) == nthr) break;
         for (int sl = (int)threadIdx.x; sl < D; sl += nthr) {
             const int idx = base + sl;
-            if (idx < end) stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_xy[sl], s_cb[sl], s_rgb[sl],
-                                              s_lo[sl], s_mask[sl], s_lanes + 4 * sl);
+            if (idx < end) stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_st[sl], s_mask[sl]);
             else s_mask[sl] = 0u;
         }
         __syncthreads();
@@ -299,12 +311,15 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
                 const int jb = has_b ? c0 + __ffs(bits) - 1 : ja;
                 if (has_b) bits &= bits - 1;
                 PixAlpha pa, pb;
-                pixel_pair_alpha<kQuad>(s_xy[ja], s_cb[ja], s_lo[ja], s_lanes + 4 * ja, px, fpx, fpy, py0, pa);
-                pixel_pair_alpha<kQuad>(s_xy[jb], s_cb[jb], s_lo[jb], s_lanes + 4 * jb, px, fpx, fpy, py0, pb);
+                const Staged &sa = s_st[ja], &sb = s_st[jb];
+                pixel_pair_alpha<kQuad>(sa.xy, sa.cb, sa.lo, reinterpret_cast<const uint2 *>(sa.lanes), px, fpx, fpy,
+                                        py0, pa);
+                pixel_pair_alpha<kQuad>(sb.xy, sb.cb, sb.lo, reinterpret_cast<const uint2 *>(sb.lanes), px, fpx, fpy,
+                                        py0, pb);
                 if (!has_b) pb.ok0 = pb.ok1 = false;
                 const uint32_t posa = (uint32_t)(base - begin + ja + 1), posb = (uint32_t)(base - begin + jb + 1);
-                blend_fwd_pair(p, pa.ok0, pa.ok1, pa.a0, pa.a1, s_rgb[ja], posa);
-                blend_fwd_pair(p, pb.ok0, pb.ok1, pb.a0, pb.a1, s_rgb[jb], posb);
+                blend_fwd_pair(p, pa.ok0, pa.ok1, pa.a0, pa.a1, sa.rgb, posa);
+                blend_fwd_pair(p, pb.ok0, pb.ok1, pb.a0, pb.a1, sb.rgb, posb);
             }
         }
     }
@@ -438,12 +453,9 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                                                 const float *__restrict__ dL_dimg, float *__restrict__ g0,
                                                 float *__restrict__ g1, float *__restrict__ g2, float4 *smem) {
     const int nthr = blockDim.x, nwarps = nthr >> 5, D = a.depth > 0 ? a.depth : nthr;
-    float4 *s_xy = smem, *s_cb = smem + D, *s_rgb = smem + 2 * D;
-    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * D);
-    uint2 *s_lanes = reinterpret_cast<uint2 *>(s_lo + D);  // 4 per staged splat (kQuad)
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 4 * D);
-    uint32_t *s_gid = s_mask + D;
-    uint32_t *s_max = s_gid + D;  // 32 entries
+    Staged *s_st = reinterpret_cast<Staged *>(smem);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_st + D);
+    uint32_t *s_max = s_mask + D;  // 32 entries
     int px, py0, ox, oy;
     thread_pixels(a, tile, px, py0, ox, oy);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -492,10 +504,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
         for (int sl = (int)threadIdx.x; sl < D; sl += nthr) {
             const int idx = bstart + sl;
             if (idx < bend) {
-                const uint32_t gid = a.vals[idx];
-                s_gid[sl] = gid;
-                stage_splat<kQuad>(a, gid, ox, oy, nwarps, s_xy[sl], s_cb[sl], s_rgb[sl], s_lo[sl], s_mask[sl],
-                                   s_lanes + 4 * sl);
+                stage_splat<kQuad>(a, a.vals[idx], ox, oy, nwarps, s_st[sl], s_mask[sl]);
             } else {
                 s_mask[sl] = 0u;
             }
@@ -517,14 +526,15 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                 if (has_b) bits &= ~(1u << (jb - c0));
                 const uint32_t posa = (uint32_t)(bstart + ja - begin), posb = (uint32_t)(bstart + jb - begin);
                 SplatBwd sa, sb;
-                splat_bwd_eval<kQuad>(s_xy[ja], s_cb[ja], s_lo[ja], s_lanes + 4 * ja, px, fpx, fpy0, fpy1, py0,
-                                      posa < p0.last, posa < p1.last, sa);
-                splat_bwd_eval<kQuad>(s_xy[jb], s_cb[jb], s_lo[jb], s_lanes + 4 * jb, px, fpx, fpy0, fpy1, py0,
-                                      has_b && posb < p0.last, has_b && posb < p1.last, sb);
+                const Staged &ra = s_st[ja], &rb = s_st[jb];
+                splat_bwd_eval<kQuad>(ra.xy, ra.cb, ra.lo, reinterpret_cast<const uint2 *>(ra.lanes), px, fpx, fpy0,
+                                      fpy1, py0, posa < p0.last, posa < p1.last, sa);
+                splat_bwd_eval<kQuad>(rb.xy, rb.cb, rb.lo, reinterpret_cast<const uint2 *>(rb.lanes), px, fpx, fpy0,
+                                      fpy1, py0, has_b && posb < p0.last, has_b && posb < p1.last, sb);
                 float va[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float vb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (sa.ok0 || sa.ok1 || sb.ok0 || sb.ok1) {
-                    const float4 cola = s_rgb[ja], colb = s_rgb[jb];
+                    const float4 cola = ra.rgb, colb = rb.rgb;
                     if (sa.ok0) pixel_bwd_update(p0, sa.e0, sa, sa.dy0, cola, va);
                     if (sb.ok0) pixel_bwd_update(p0, sb.e0, sb, sb.dy0, colb, vb);
                     if (sa.ok1) pixel_bwd_update(p1, sa.e1, sa, sa.dy1, cola, va);
@@ -535,14 +545,14 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
                 if (anya) {
                     float v8;
                     const float y = warp_transpose_sum(va, v8);
-                    const uint32_t gid = s_gid[ja];
+                    const uint32_t gid = ra.gid;
                     if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
                     else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
                 }
                 if (anyb) {
                     float v8;
                     const float y = warp_transpose_sum(vb, v8);
-                    const uint32_t gid = s_gid[jb];
+                    const uint32_t gid = rb.gid;
                     if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
                     else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
                 }
@@ -555,11 +565,10 @@ __device__ __forceinline__ void render_bwd_tile(const RenderArgs &a, int tile, c
 // dynamic shared memory of the two tile routines for a staging batch of
 // `depth` records
 __host__ __device__ inline size_t render_fwd_smem(int depth) {
-    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + sizeof(uint32_t)) * depth;
+    return (sizeof(Staged) + sizeof(uint32_t)) * depth;
 }
 __host__ __device__ inline size_t render_bwd_smem(int depth) {
-    return (3 * sizeof(float4) + sizeof(float2) + 4 * sizeof(uint2) + 2 * sizeof(uint32_t)) * depth +
-           32 * sizeof(uint32_t);
+    return (sizeof(Staged) + sizeof(uint32_t)) * depth + 32 * sizeof(uint32_t);
 }
 
 }  // namespace gsr

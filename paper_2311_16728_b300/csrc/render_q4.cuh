@@ -52,15 +52,15 @@ __device__ __forceinline__ uint4 q4_box_lanes(int x0, int x1, int y0, int y1, in
 // budget other phases set; in the one-view kernel the extra registers cost
 // more than the dropped warps save).
 template <bool kExact>
-__device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int ox, int oy, float4 &s_xy,
-                                         float4 &s_cb, float4 &s_rgb, float2 &s_lo, uint32_t &s_mask,
-                                         uint4 *s_lanes) {
+__device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int ox, int oy, Staged &st,
+                                         uint32_t &s_mask) {
     const float4 g = __ldg(a.xy_conic + gid), c = __ldg(a.c_op_box + gid);
-    s_rgb = __ldg(a.rgb_depth + gid);
-    s_lo = mean_residual(a, gid);
+    st.rgb = __ldg(a.rgb_depth + gid);
+    st.lo = mean_residual(a, gid);
+    st.gid = gid;
     const float A = g.z, B = g.w, C = c.x, op = c.y;
-    s_xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
-    s_cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
+    st.xy = make_float4(g.x, g.y, A * kHalfLog2e, B * (2.0f * kHalfLog2e));
+    st.cb = make_float4(C * kHalfLog2e, op, c.z, c.w);
     uint32_t mask = 0u;
     const float tau = 2.0f * __logf(255.0f * op);  // alpha >= 1/255  <=>  d^T Q d <= tau
     if (tau > 0.0f) {
@@ -80,7 +80,7 @@ __device__ __forceinline__ void q4_stage(const RenderArgs &a, uint32_t gid, int 
                 (!kExact || rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1),
                                          (float)max(ry0, y0), (float)min(ry1, y1)))) {
                 mask |= 1u << w;
-                s_lanes[w] = q4_box_lanes(x0, x1, y0, y1, ox, ry0);
+                st.lanes[w] = q4_box_lanes(x0, x1, y0, y1, ox, ry0);
             }
         }
     }
@@ -130,12 +130,9 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
     using G = Q4Group<kHalf>;
     constexpr int nthr = kQ4Threads;
     const int D = a.depth > 0 ? a.depth : nthr;
-    float4 *s_xy = smem, *s_cb = smem + D, *s_rgb = smem + 2 * D;
-    float2 *s_lo = reinterpret_cast<float2 *>(smem + 3 * D);
-    uint4 *s_lanes = reinterpret_cast<uint4 *>(s_lo + D);
-    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_lanes + 2 * D);
-    uint32_t *s_gid = s_mask + D;
-    uint32_t *s_max = s_gid + D;  // 2 entries
+    Staged *s_st = reinterpret_cast<Staged *>(smem);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_st + D);
+    uint32_t *s_max = s_mask + D;  // 2 entries
     const int ti = G::tid();
     int px, py0, ox, oy;
     q4_pixels(a, tile, ti, px, py0, ox, oy);
@@ -189,10 +186,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
         for (int sl = ti; sl < D; sl += nthr) {
             const int idx = bstart + sl;
             if (idx < bend) {
-                const uint32_t gid = a.vals[idx];
-                s_gid[sl] = gid;
-                q4_stage<kExact>(a, gid, ox, oy, s_xy[sl], s_cb[sl], s_rgb[sl], s_lo[sl], s_mask[sl],
-                                s_lanes + 2 * sl);
+                q4_stage<kExact>(a, a.vals[idx], ox, oy, s_st[sl], s_mask[sl]);
             } else {
                 s_mask[sl] = 0u;
             }
@@ -208,9 +202,10 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                 const int j = c0 + 31 - __clz(bits);
                 bits &= ~(1u << (j - c0));
                 const uint32_t pos = (uint32_t)(bstart + j - begin);
-                const float4 g = s_xy[j], cb = s_cb[j];
-                const float2 lo = s_lo[j];
-                const uint4 lm = s_lanes[2 * j + wid];
+                const Staged &sj = s_st[j];
+                const float4 g = sj.xy, cb = sj.cb;
+                const float2 lo = sj.lo;
+                const uint4 lm = sj.lanes[wid];
                 const float dx = FS(FS(fpx, g.x), lo.x);
                 const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
                 // alpha at the four pixels, a pair at a time
@@ -243,7 +238,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                 const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
                 const float C = cb.x * (1.0f / kHalfLog2e);
                 if (any) {
-                    const float4 col = s_rgb[j];
+                    const float4 col = sj.rgb;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
@@ -287,7 +282,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
                     for (int q = 5; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
                     float v8;
                     const float y = warp_transpose_sum(v, v8);
-                    const uint32_t gid = s_gid[j];
+                    const uint32_t gid = sj.gid;
                     if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
                     else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
                 }
@@ -299,8 +294,7 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
 // shared memory of one tile's 64 threads for a staging batch of `depth`
 // records (a multiple of 16 bytes)
 __host__ __device__ inline size_t render_q4_smem(int depth = kQ4Threads) {
-    return ((3 * sizeof(float4) + sizeof(float2) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t)) * depth +
-            2 * sizeof(uint32_t) + 15) / 16 * 16;
+    return ((sizeof(Staged) + sizeof(uint32_t)) * depth + 2 * sizeof(uint32_t) + 15) / 16 * 16;
 }
 
 }  // namespace gsr

