@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kLThreads) ssim_pass1_kernel(const float *__re
                                 blockIdx.z, sm, s_red);
 }
 
-__global__ void __launch_bounds__(kLThreads) ssim_pass2_kernel(const float *__restrict__ x, const float *__restrict__ y,
+__global__ void __launch_bounds__(kLThreads, 5) ssim_pass2_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                                                int H, int W, Win win, const float *__restrict__ mapA,
                                                                const float *__restrict__ mapB,
                                                                const float *__restrict__ mapC,

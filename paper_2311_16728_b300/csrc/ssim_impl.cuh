@@ -50,32 +50,37 @@ __device__ __forceinline__ float block_sum(float v, float *s_red) {
     return r;  // valid in thread 0
 }
 
-// Stages a (kRH x kRW) region of plane `src` around the tile (zero outside):
-// a thread's loads are issued in batches of up to 7 before the batch's
-// shared-memory stores (one memory round trip per batch: one for 256
-// threads, two for 128); a region inside the image skips the bounds tests.
-template <int NT>
-__device__ __forceinline__ void stage_region(const float *__restrict__ src, int H, int W, int ox, int oy, float *dst) {
+// Stages a (kRH x kRW) region of each of the NP planes src[p] around the
+// tile (zero outside) into dst + p kRH kRS: a thread's loads for all planes
+// are issued in batches of up to 7 positions before the batch's shared-memory
+// stores (one memory round trip per batch: one for 256 threads, two for
+// 128); a region inside the image skips the bounds tests.
+template <int NT, int NP>
+__device__ __forceinline__ void stage_planes(const float *const (&src)[NP], int H, int W, int ox, int oy,
+                                             float *dst) {
     constexpr int kN = kRH * kRW, kPer = (kN + NT - 1) / NT, kBatch = 7;
     const int gx0 = ox - kLR, gy0 = oy - kLR;
     const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + kRW <= W && gy0 + kRH <= H;
 #pragma unroll
     for (int j0 = 0; j0 < kPer; j0 += kBatch) {
-        float v[kBatch];
+        float v[NP][kBatch];
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) {
             const int idx = (int)threadIdx.x + (j0 + j) * NT;
             const int r = idx / kRW, q = idx - r * kRW;
             const int gy = gy0 + r, gx = gx0 + q;
-            v[j] = (j0 + j < kPer && idx < kN && (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)))
-                       ? src[(int64_t)gy * W + gx]
-                       : 0.f;
+            const bool ok = j0 + j < kPer && idx < kN && (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W));
+#pragma unroll
+            for (int pl = 0; pl < NP; ++pl) v[pl][j] = ok ? src[pl][(int64_t)gy * W + gx] : 0.f;
         }
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) {
             const int idx = (int)threadIdx.x + (j0 + j) * NT;
             const int r = idx / kRW, q = idx - r * kRW;
-            if (j0 + j < kPer && idx < kN) dst[r * kRS + q] = v[j];
+            if (j0 + j < kPer && idx < kN) {
+#pragma unroll
+                for (int pl = 0; pl < NP; ++pl) dst[pl * kRH * kRS + r * kRS + q] = v[pl][j];
+            }
         }
     }
 }
@@ -109,8 +114,10 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     __syncthreads();  // the previous block's readers of sm are done
-    stage_region<NT>(x + cb, H, W, ox, oy, sX);
-    stage_region<NT>(y + cb, H, W, ox, oy, sY);
+    {
+        const float *const planes[2] = {x + cb, y + cb};
+        stage_planes<NT, 2>(planes, H, W, ox, oy, sX);  // sY = sX + kRH kRS
+    }
     __syncthreads();
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
         // a warp covers four rows of eight runs: the staged loads (row
@@ -223,9 +230,10 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     const float inv_n = (float)((double)scale / ((double)C * (double)plane));
     __syncthreads();
-    stage_region<NT>(mapA + cb, H, W, ox, oy, sM);
-    stage_region<NT>(mapB + cb, H, W, ox, oy, sM + kRH * kRS);
-    stage_region<NT>(mapC + cb, H, W, ox, oy, sM + 2 * kRH * kRS);
+    {
+        const float *const planes[3] = {mapA + cb, mapB + cb, mapC + cb};
+        stage_planes<NT, 3>(planes, H, W, ox, oy, sM);
+    }
     __syncthreads();
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
         // a warp covers four rows of eight runs: the staged loads (row
