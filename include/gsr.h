@@ -124,6 +124,17 @@ typedef struct {
  *                     and the box stay the FP32 decision chain's (keys and
  *                     culling are unchanged); when uv_lo is set, the blends
  *                     evaluate alpha at the FP64 position.  8-byte aligned.
+ *   tile_order u32    optional (NULL: not used), one entry per tile of the
+ *                     view: written by gsr_bin_sort with the tiles in
+ *                     decreasing order of their pair counts (a permutation;
+ *                     ties in any order), read by gsr_render_fwd,
+ *                     gsr_blend_bwd and gsr_render_bwd, whose CTA b then
+ *                     renders tile tile_order[b], so the longest lists start
+ *                     first and the short ones fill the last wave.  The
+ *                     image and gradients do not depend on it.  Entries of
+ *                     tile_order must be valid tile indices (those outside
+ *                     the view are skipped); set it only with buffers that
+ *                     gsr_bin_sort filled for the same camera and tiling.
  * Records of culled Gaussians (ntiles == 0) are left unwritten. */
 typedef struct {
     float *xy_conic;
@@ -131,6 +142,7 @@ typedef struct {
     float *rgb_depth;
     uint32_t *ntiles;
     float *uv_lo;
+    uint32_t *tile_order;
 } gsr_proj;
 
 /* Screen-space gradient buffer (caller-owned, 3 float4 per Gaussian):

@@ -409,6 +409,9 @@ constexpr int kTileScanThreads = 1024;
 constexpr uint32_t kWarpTile = 512;      // segments this short are sorted by one warp, in registers
 constexpr uint32_t kSmallTile = 1024;    // longest segment of the one-block shared-memory sort
 constexpr uint32_t kLargeTile = 16384;   // longest segment sorted in shared memory
+// length classes of the heavy-first tile order: 16 pairs each, the last open
+constexpr int kOrderBuckets = 64;
+__device__ __forceinline__ int order_bucket(uint32_t n) { return (int)min((n + 15u) >> 4, (uint32_t)kOrderBuckets - 1u); }
 
 __device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s_warp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -442,11 +445,14 @@ __device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s
 __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     uint32_t *__restrict__ ranges, uint32_t T, const unsigned long long *__restrict__ d_kept, int64_t cap,
     uint32_t *__restrict__ list, uint32_t *__restrict__ list2, uint32_t *__restrict__ list_counts,
-    int64_t *__restrict__ d_written, int64_t *__restrict__ d_num_pairs, int32_t *__restrict__ d_status) {
+    int64_t *__restrict__ d_written, int64_t *__restrict__ d_num_pairs, int32_t *__restrict__ d_status,
+    uint32_t *__restrict__ order) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_small, s_large, s_mid;
+    __shared__ uint32_t s_bucket[kOrderBuckets];
     const unsigned long long K = *d_kept;
     const bool overflow = K > (unsigned long long)cap;
+    for (int b = threadIdx.x; b < kOrderBuckets; b += kTileScanThreads) s_bucket[b] = 0u;
     if (threadIdx.x == 0) {
         s_small = 0u;
         s_large = 0u;
@@ -495,6 +501,7 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
                 else if (n <= kSmallTile) list2[atomicAdd(&s_mid, 1u)] = t;
                 else list[(size_t)cap - 1 - atomicAdd(&s_large, 1u)] = t;
             }
+            if (order) atomicAdd(&s_bucket[order_bucket(n)], 1u);
             off += n;
         }
         carried += round_total;
@@ -506,6 +513,28 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
         list_counts[1] = s_large;
         list_counts[2] = s_mid;
     }
+    if (!order) return;
+    // tiles by decreasing pair count for the blend kernels: a counting sort
+    // on kOrderBuckets length classes, the longest class first
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = kOrderBuckets - 1; b >= 0; --b) {
+            const uint32_t c = s_bucket[b];
+            s_bucket[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < T; t += kTileScanThreads) {
+        const uint2 r = __ldcg(reinterpret_cast<const uint2 *>(ranges) + t);
+        order[atomicAdd(&s_bucket[order_bucket(r.y - r.x)], 1u)] = t;
+    }
+}
+
+// the tile order of a view without pairs
+__global__ void identity_order_kernel(uint32_t *__restrict__ order, uint32_t T) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) order[t] = t;
 }
 
 // every stored kept pair goes to its tile's segment at its rank; a thread
@@ -993,6 +1022,10 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
         if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st) != cudaSuccess ||
             cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st) != cudaSuccess)
             return check_launch("memset ranges and pair count");
+        if (proj->tile_order && tiles > 0) {
+            identity_order_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(proj->tile_order, (uint32_t)tiles);
+            return check_launch("identity_order_kernel");
+        }
         return GSR_OK;
     }
     uint32_t *order = reinterpret_cast<uint32_t *>(ws + L.order);
@@ -1045,7 +1078,8 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     if ((rc = check_launch("pair expansion"))) return rc;
     // 4-6. ranges, scatter into tile segments, sort each segment
     tile_scan_kernel<<<1, kTileScanThreads, 0, st>>>(tile_ranges, (uint32_t)tiles, d_kept, pair_capacity, list,
-                                                      list2, list_counts, d_written, d_num_pairs, d_status);
+                                                      list2, list_counts, d_written, d_num_pairs, d_status,
+                                                      proj->tile_order);
     if (pair_capacity == 0) return check_launch("tile_scan_kernel");
     scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_ts, kept_sk, d_written, pair_capacity, tile_ranges, seg);
     sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list2, list_counts, tile_ranges, seg, keys,

@@ -22,32 +22,48 @@ namespace gsr {
 // kCount: also write the per-pixel number of blended Gaussians (a work
 // counter); without it the counting is compiled out
 // kQuad: 16 x 16 tiles (quadrant warps, box tests from staged lane masks)
+// The tile CTA b renders: order[b] when the binning wrote the heavy-first
+// tile order (gsr_proj.tile_order), else b; -1 for an entry outside the view.
+__device__ __forceinline__ int cta_tile(const uint32_t *__restrict__ order) {
+    if (!order) return (int)blockIdx.x;
+    const uint32_t t = __ldg(order + blockIdx.x);
+    return t < gridDim.x ? (int)t : -1;
+}
+
 template <bool kCount, bool kQuad>
-__global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, float *__restrict__ img,
-                                                         float *__restrict__ T_final,
+__global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                         float *__restrict__ img, float *__restrict__ T_final,
                                                          uint32_t *__restrict__ n_contrib,
                                                          uint32_t *__restrict__ n_blended) {
     extern __shared__ float4 smem[];
-    render_fwd_tile<kQuad>(a, blockIdx.x, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem);
+    const int tile = cta_tile(order);
+    if (tile < 0) return;
+    render_fwd_tile<kQuad>(a, tile, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem);
 }
 
 template <bool kQuad>
-__global__ void __maxnreg__(80) render_bwd_kernel(RenderArgs a, const float *__restrict__ T_final,
-                                                         const uint32_t *__restrict__ n_contrib,
-                                                         const float *__restrict__ dL_dimg, float *__restrict__ g0,
-                                                         float *__restrict__ g1, float *__restrict__ g2) {
+__global__ void __maxnreg__(80) render_bwd_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                  const float *__restrict__ T_final,
+                                                  const uint32_t *__restrict__ n_contrib,
+                                                  const float *__restrict__ dL_dimg, float *__restrict__ g0,
+                                                  float *__restrict__ g1, float *__restrict__ g2) {
     extern __shared__ float4 smem[];
-    render_bwd_tile<kQuad>(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
+    const int tile = cta_tile(order);
+    if (tile < 0) return;
+    render_bwd_tile<kQuad>(a, tile, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
 // 16 x 16 tiles: the backward with four pixels per thread (render_q4.cuh)
-__global__ void __launch_bounds__(kQ4Threads) render_bwd_q4_kernel(RenderArgs a, const float *__restrict__ T_final,
+__global__ void __launch_bounds__(kQ4Threads) render_bwd_q4_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                                   const float *__restrict__ T_final,
                                                                    const uint32_t *__restrict__ n_contrib,
                                                                    const float *__restrict__ dL_dimg,
                                                                    float *__restrict__ g0, float *__restrict__ g1,
                                                                    float *__restrict__ g2) {
     extern __shared__ float4 smem[];
-    render_bwd_tile_q4<false, true>(a, blockIdx.x, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
+    const int tile = cta_tile(order);
+    if (tile < 0) return;
+    render_bwd_tile_q4<false, true>(a, tile, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
 static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const uint32_t *ranges,
@@ -95,7 +111,8 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
                             : (quad ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
     // (per device and cheap, not a stream operation: fine during capture)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_fwd_smem(depth));
-    kernel<<<tiles, nthr, render_fwd_smem(depth), as_cuda(stream)>>>(a, img, T_final, n_contrib, n_blended);
+    kernel<<<tiles, nthr, render_fwd_smem(depth), as_cuda(stream)>>>(a, proj->tile_order, img, T_final, n_contrib,
+                                                                      n_blended);
     return check_launch("render_fwd_kernel");
 }
 
@@ -130,15 +147,15 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
         const int depth = a.depth > 0 ? a.depth : kQ4Threads;
         cudaFuncSetAttribute(render_bwd_q4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)render_q4_smem(depth));
-        render_bwd_q4_kernel<<<tiles, kQ4Threads, render_q4_smem(depth), st>>>(a, T_final, n_contrib, dL_dimg,
-                                                                               grad2d->g0, grad2d->g1, grad2d->g2);
+        render_bwd_q4_kernel<<<tiles, kQ4Threads, render_q4_smem(depth), st>>>(
+            a, proj->tile_order, T_final, n_contrib, dL_dimg, grad2d->g0, grad2d->g1, grad2d->g2);
         return check_launch("render_bwd_q4_kernel");
     }
     const int depth = a.depth > 0 ? a.depth : nthr;
     auto kernel = quad ? render_bwd_kernel<true> : render_bwd_kernel<false>;
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_bwd_smem(depth));
-    kernel<<<tiles, nthr, render_bwd_smem(depth), st>>>(a, T_final, n_contrib, dL_dimg, grad2d->g0, grad2d->g1,
-                                                        grad2d->g2);
+    kernel<<<tiles, nthr, render_bwd_smem(depth), st>>>(a, proj->tile_order, T_final, n_contrib, dL_dimg, grad2d->g0,
+                                                        grad2d->g1, grad2d->g2);
     return check_launch("render_bwd_kernel");
 }
 
