@@ -352,7 +352,9 @@ int32_t gsr_batched_preprocess(const gsr_gaussians *g, const gsr_camera *cams, i
  * c-th visible record at position c), compact->ntiles[r] receives record r's
  * position c (for records with proj->ntiles[r] > 0), and the pairs' values are
  * these positions: the window's later passes then read records and
- * accumulate gradients in dense arrays (the order of the pairs is the same). */
+ * accumulate gradients in dense arrays (the order of the pairs is the same).
+ * proj->tile_order (optional) receives all views' tiles (window numbering)
+ * by decreasing pair count. */
 int32_t gsr_batched_bin_sort(const gsr_proj *proj, int64_t n_per_view, const gsr_camera *cams, int32_t nviews,
                              const gsr_tiling *tiling, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
                              uint32_t *tile_ranges, int64_t *d_num_pairs, const gsr_proj *compact, void *workspace,
@@ -374,6 +376,8 @@ int32_t gsr_batched_iterate_workspace_size(const gsr_camera *cams, int32_t nview
  * *d_status and the launch winds down.  img, T_final, n_contrib, gt, dL_dimg
  * are arrays of nviews device pointers (host arrays); weights (host, may be
  * NULL = all 1).  Tiles must hold 256 pixels (16 x 16, 32 x 8 or 8 x 32).
+ * With proj->tile_order set (by gsr_batched_bin_sort, window numbering) the
+ * blend phases take their queue items in that order, longest lists first.
  * The last 256 bytes of the workspace hold the launch's queue and barrier
  * words; its bytes 64 .. 95 receive four uint64 global-timer stamps (ns) taken
  * by block 0 at entry and after each of the three barriers (phase split). */

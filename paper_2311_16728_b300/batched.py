@@ -60,6 +60,8 @@ class BatchedWindow:
         self.rec_to_c = torch.zeros(m, dtype=torch.int32, device=dev)
         self.tiles = sum(n_tiles(v[0], self.tiling) for v in views)
         self.ranges = torch.zeros(self.tiles, 2, dtype=torch.int32, device=dev)
+        # tiles of all views by decreasing pair count (binning writes it, the persistent launch reads it)
+        self.tile_order = torch.arange(self.tiles, dtype=torch.int32, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.imgs = [torch.empty(3, v[0].height, v[0].width, **f32) for v in views]
@@ -110,11 +112,11 @@ class BatchedWindow:
 
     def proj(self) -> L.gsr_proj:
         return L.gsr_proj(self.xy_conic.data_ptr(), self.c_op_box.data_ptr(), self.rgb_depth.data_ptr(),
-                          self.ntiles.data_ptr(), self.uv_lo.data_ptr())
+                          self.ntiles.data_ptr(), self.uv_lo.data_ptr(), self.tile_order.data_ptr())
 
     def compact(self) -> L.gsr_proj:
         return L.gsr_proj(self.cxy.data_ptr(), self.ccb.data_ptr(), self.crd.data_ptr(), self.rec_to_c.data_ptr(),
-                          self.cuv.data_ptr())
+                          self.cuv.data_ptr(), self.tile_order.data_ptr())
 
     def grad2d(self) -> L.gsr_grad2d:
         return L.gsr_grad2d(self.g2[0].data_ptr(), self.g2[1].data_ptr(), self.g2[2].data_ptr())

@@ -140,6 +140,7 @@ struct IterArgs {
     const float2 *uv;  // position residuals of the records (NULL: none)
     const uint32_t *vals;
     const uint2 *ranges;
+    const uint32_t *order;  // tiles by decreasing pair count (NULL: natural order)
     int tw, th;
     int depth;  // staging batch of the blend phases (0: one record per thread)
     float bg0, bg1, bg2;
@@ -247,6 +248,14 @@ __device__ __forceinline__ int view_of_tile(const IterArgs &a, int t) {
     return v;
 }
 
+// The tile of queue item it: the heavy-first order when the binning wrote
+// one (the longest lists start first), else it; -1 outside the window.
+__device__ __forceinline__ int ordered_tile(const IterArgs &a, int it) {
+    if (!a.order) return it;
+    const uint32_t t = __ldg(a.order + it);
+    return t < (uint32_t)a.tiles_total ? (int)t : -1;
+}
+
 __device__ __forceinline__ int view_of_loss(const IterArgs &a, int t) {
     int v = 0;
     while (v + 1 < a.nviews && a.view[v + 1].loss_off <= t) ++v;
@@ -266,9 +275,11 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
     phase_stamp(a.sync, 0);
     // ---- phase 1: forward blend of every (view, tile)
     for (int it = next_item(a.sync + 0, &s_item); it < a.tiles_total; it = next_item(a.sync + 0, &s_item)) {
-        const int v = view_of_tile(a, it);
+        const int t = ordered_tile(a, it);
+        if (t < 0) continue;
+        const int v = view_of_tile(a, t);
         const IterView &w = a.view[v];
-        render_fwd_tile<kQuad>(view_args(a, w), it - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
+        render_fwd_tile<kQuad>(view_args(a, w), t - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
     phase_stamp(a.sync, 1);
@@ -307,16 +318,20 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
         float4 *sm = smem4 + half * (render_q4_smem(a.depth > 0 ? a.depth : kQ4Threads) / sizeof(float4));
         for (int it = next_item_half(a.sync + 3, &s_item2[half]); it < a.tiles_total;
              it = next_item_half(a.sync + 3, &s_item2[half])) {
-            const int v = view_of_tile(a, it);
+            const int t = ordered_tile(a, it);
+            if (t < 0) continue;
+            const int v = view_of_tile(a, t);
             const IterView &w = a.view[v];
-            render_bwd_tile_q4<true>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
+            render_bwd_tile_q4<true>(view_args(a, w), t - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
                                      a.g2, sm);
         }
     } else {
         for (int it = next_item(a.sync + 3, &s_item); it < a.tiles_total; it = next_item(a.sync + 3, &s_item)) {
-            const int v = view_of_tile(a, it);
+            const int t = ordered_tile(a, it);
+            if (t < 0) continue;
+            const int v = view_of_tile(a, t);
             const IterView &w = a.view[v];
-            render_bwd_tile<kQuad>(view_args(a, w), it - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
+            render_bwd_tile<kQuad>(view_args(a, w), t - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
                                    a.g2, smem4);
         }
     }
@@ -577,6 +592,7 @@ extern "C" int32_t gsr_batched_iterate(const gsr_proj *proj, const uint32_t *val
     a.uv = reinterpret_cast<const float2 *>(proj->uv_lo);
     a.vals = vals;
     a.ranges = reinterpret_cast<const uint2 *>(tile_ranges);
+    a.order = proj->tile_order;
     a.tw = tiling->tile_w;
     a.th = tiling->tile_h;
     a.depth = tiling->batch_depth;
