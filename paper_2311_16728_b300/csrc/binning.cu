@@ -264,7 +264,7 @@ __device__ __forceinline__ int64_t warp_upper_index(const uint32_t *a, int64_t n
 constexpr int kExpandThreads = 256;
 constexpr int kExpandItems = 4;
 constexpr int kExpandTile = kExpandThreads * kExpandItems;
-constexpr int kExpandGrid = 148 * 8;  // grid-stride over chunks of kExpandTile candidates
+constexpr int kExpandGrid = 148 * 4;  // one wave at four CTAs per SM (56 registers), grid-stride over chunks
 constexpr int kExpandGroup = 16;      // chunks of a block whose ends are searched together
 
 // Kept pairs: kept_ts[p] = global tile << 32 | rank of the pair within its
