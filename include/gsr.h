@@ -135,6 +135,11 @@ typedef struct {
  *                     tile_order must be valid tile indices (those outside
  *                     the view are skipped); set it only with buffers that
  *                     gsr_bin_sort filled for the same camera and tiling.
+ *   tile_work u32     optional (NULL: not used; needs tile_order), one entry
+ *                     per tile: gsr_render_fwd writes each tile's largest
+ *                     n_contrib (how deep into its list the backward walks),
+ *                     and gsr_blend_bwd / gsr_render_bwd first reorder
+ *                     tile_order by it, deepest first, for their own launch.
  * Records of culled Gaussians (ntiles == 0) are left unwritten. */
 typedef struct {
     float *xy_conic;
@@ -143,6 +148,7 @@ typedef struct {
     uint32_t *ntiles;
     float *uv_lo;
     uint32_t *tile_order;
+    uint32_t *tile_work;
 } gsr_proj;
 
 /* Screen-space gradient buffer (caller-owned, 3 float4 per Gaussian):

@@ -44,7 +44,8 @@ class gsr_tiling(ctypes.Structure):
 
 class gsr_proj(ctypes.Structure):
     _fields_ = [("xy_conic", c_void_p), ("c_op_box", c_void_p), ("rgb_depth", c_void_p), ("ntiles", c_void_p),
-                ("uv_lo", c_void_p), ("tile_order", c_void_p)]
+                ("uv_lo", c_void_p), ("tile_order", c_void_p),
+                ("tile_work", c_void_p)]
 
 
 class gsr_grad2d(ctypes.Structure):

@@ -34,11 +34,36 @@ template <bool kCount, bool kQuad>
 __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, const uint32_t *__restrict__ order,
                                                          float *__restrict__ img, float *__restrict__ T_final,
                                                          uint32_t *__restrict__ n_contrib,
-                                                         uint32_t *__restrict__ n_blended) {
+                                                         uint32_t *__restrict__ n_blended,
+                                                         uint32_t *__restrict__ tile_work) {
     extern __shared__ float4 smem[];
     const int tile = cta_tile(order);
     if (tile < 0) return;
-    render_fwd_tile<kQuad>(a, tile, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem);
+    render_fwd_tile<kQuad>(a, tile, img, T_final, n_contrib, kCount ? n_blended : nullptr, smem, tile_work);
+}
+
+// The backward's tile order: tiles by decreasing tile_work (the depth of
+// list each walks), a counting sort on 16-entry classes by one CTA.
+constexpr int kWorkOrderThreads = 1024, kWorkClasses = 64;
+__global__ void __launch_bounds__(kWorkOrderThreads) work_order_kernel(const uint32_t *__restrict__ work, uint32_t T,
+                                                                       uint32_t *__restrict__ order) {
+    __shared__ uint32_t s_cls[kWorkClasses];
+    for (int c = threadIdx.x; c < kWorkClasses; c += kWorkOrderThreads) s_cls[c] = 0u;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
+        atomicAdd(&s_cls[min((work[t] + 15u) >> 4, (uint32_t)kWorkClasses - 1u)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int c = kWorkClasses - 1; c >= 0; --c) {
+            const uint32_t n = s_cls[c];
+            s_cls[c] = run;
+            run += n;
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
+        order[atomicAdd(&s_cls[min((work[t] + 15u) >> 4, (uint32_t)kWorkClasses - 1u)], 1u)] = t;
 }
 
 template <bool kQuad>
@@ -111,8 +136,8 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
                             : (quad ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
     // (per device and cheap, not a stream operation: fine during capture)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_fwd_smem(depth));
-    kernel<<<tiles, nthr, render_fwd_smem(depth), as_cuda(stream)>>>(a, proj->tile_order, img, T_final, n_contrib,
-                                                                      n_blended);
+    kernel<<<tiles, nthr, render_fwd_smem(depth), as_cuda(stream)>>>(
+        a, proj->tile_order, img, T_final, n_contrib, n_blended, proj->tile_order ? proj->tile_work : nullptr);
     return check_launch("render_fwd_kernel");
 }
 
@@ -143,6 +168,10 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
     const int nthr = tiling->tile_w * tiling->tile_h / 2;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
+    if (proj->tile_order && proj->tile_work) {  // deepest lists first (what the forward measured)
+        work_order_kernel<<<1, kWorkOrderThreads, 0, st>>>(proj->tile_work, (uint32_t)tiles, proj->tile_order);
+        if ((rc = check_launch("work_order_kernel"))) return rc;
+    }
     if (quad && tiling->bwd_threads != nthr) {  // 64 threads, four pixels each (the default)
         const int depth = a.depth > 0 ? a.depth : kQ4Threads;
         cudaFuncSetAttribute(render_bwd_q4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

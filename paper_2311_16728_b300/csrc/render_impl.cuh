@@ -267,10 +267,13 @@ __device__ __forceinline__ void blend_fwd_pair(PairFwd &p, bool ok0, bool ok1, f
 
 // ---------------------------------------------------------------- K5
 // One tile (local index `tile` of the view in `a`), by the whole block.
+// tile_work (may be NULL): receives the tile's largest n_contrib, the depth
+// of list its backward walks (the cost proxy of the backward's tile order).
 template <bool kQuad>
 __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, float *__restrict__ img,
                                                 float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
-                                                uint32_t *__restrict__ n_blended, float4 *smem) {
+                                                uint32_t *__restrict__ n_blended, float4 *smem,
+                                                uint32_t *__restrict__ tile_work = nullptr) {
     const int nthr = blockDim.x, nwarps = nthr >> 5, D = a.depth > 0 ? a.depth : nthr;
     Staged *s_st = reinterpret_cast<Staged *>(smem);
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_st + D);
@@ -341,6 +344,15 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int tile, f
         T_final[pix] = p.T.y;
         n_contrib[pix] = p.last1;
         if (n_blended) n_blended[pix] = p.nb1;
+    }
+    if (tile_work) {  // every thread is past the blend loop (its exit is block-uniform)
+        __shared__ uint32_t s_work;
+        if (threadIdx.x == 0) s_work = 0u;
+        __syncthreads();
+        const uint32_t m = __reduce_max_sync(0xffffffffu, max(p.last0, p.last1));
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_work, m);
+        __syncthreads();
+        if (threadIdx.x == 0) tile_work[tile] = s_work;
     }
 }
 

@@ -145,6 +145,8 @@ class ViewBuffers:
         self.ranges = torch.zeros(self.tiles, 2, dtype=torch.int32, device=device)
         # tiles by decreasing pair count (binning writes it, the blends read it)
         self.tile_order = torch.arange(self.tiles, dtype=torch.int32, device=device)
+        # per-tile depth of list the backward walks (the forward writes it; the backward's order)
+        self.tile_work = torch.zeros(self.tiles, dtype=torch.int32, device=device)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         H, W = cam.height, cam.width
@@ -170,7 +172,8 @@ class ViewBuffers:
 
     def proj_struct(self) -> L.gsr_proj:
         return L.gsr_proj(self.xy_conic.data_ptr(), self.c_op_box.data_ptr(), self.rgb_depth.data_ptr(),
-                          self.ntiles.data_ptr(), self.uv_lo.data_ptr(), self.tile_order.data_ptr())
+                          self.ntiles.data_ptr(), self.uv_lo.data_ptr(), self.tile_order.data_ptr(),
+                          self.tile_work.data_ptr())
 
     def grad2d_struct(self) -> L.gsr_grad2d:
         return L.gsr_grad2d(self.g2[0].data_ptr(), self.g2[1].data_ptr(), self.g2[2].data_ptr())
