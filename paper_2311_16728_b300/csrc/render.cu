@@ -43,15 +43,15 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, const uin
 }
 
 // The backward's tile order: tiles by decreasing tile_work (the depth of
-// list each walks), a counting sort on 16-entry classes by one CTA.
-constexpr int kWorkOrderThreads = 1024, kWorkClasses = 64;
+// list each walks), a counting sort on 8-entry classes by one CTA.
+constexpr int kWorkOrderThreads = 1024, kWorkClasses = 128;
 __global__ void __launch_bounds__(kWorkOrderThreads) work_order_kernel(const uint32_t *__restrict__ work, uint32_t T,
                                                                        uint32_t *__restrict__ order) {
     __shared__ uint32_t s_cls[kWorkClasses];
     for (int c = threadIdx.x; c < kWorkClasses; c += kWorkOrderThreads) s_cls[c] = 0u;
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
-        atomicAdd(&s_cls[min((work[t] + 15u) >> 4, (uint32_t)kWorkClasses - 1u)], 1u);
+        atomicAdd(&s_cls[min((work[t] + 7u) >> 3, (uint32_t)kWorkClasses - 1u)], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kWorkOrderThreads) work_order_kernel(const uin
     }
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
-        order[atomicAdd(&s_cls[min((work[t] + 15u) >> 4, (uint32_t)kWorkClasses - 1u)], 1u)] = t;
+        order[atomicAdd(&s_cls[min((work[t] + 7u) >> 3, (uint32_t)kWorkClasses - 1u)], 1u)] = t;
 }
 
 template <bool kQuad>
