@@ -98,7 +98,11 @@ typedef struct {
  *  - tile_w x tile_h pixels per tile: tile_h even, tile_w a divisor or a
  *    multiple of 32, tile_w * tile_h a multiple of 64 and at most 1024.
  *  - batch_depth: depth-ordered records staged in shared memory per round by
- *    the blend kernels; 0 = one per thread, else a multiple of 32 up to 512.
+ *    the blend kernels, a multiple of 32 up to 512, for the whole tile; 0 =
+ *    each kernel's default: for 16 x 16 tiles the one-view blends and the
+ *    batched window's forward let every warp stage its own 32 records a
+ *    round (only those it can see, no barrier between the warps of a tile);
+ *    elsewhere one record per thread.
  *  - bwd_threads: threads per tile of the backward blend; 0 = the default
  *    (64, four pixels a thread, for 16 x 16 tiles; tile_w * tile_h / 2
  *    otherwise), 128 for 16 x 16 tiles = two pixels a thread, else

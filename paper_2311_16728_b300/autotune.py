@@ -4,7 +4,8 @@ The rendered image does not depend on the tiling (each Gaussian reaches only
 its own pixel box, and the tile cull never drops a pair that blends) nor on
 the blend kernels' launch shape, so all three knobs are pure performance
 choices: the tile shape, the staging batch depth (depth-ordered records
-staged in shared memory per round: one per thread, or 32 .. 256) and the
+staged in shared memory per round: 32 .. 256 for the whole tile, or 0 =
+every warp its own 32 for 16 x 16 tiles, one per thread otherwise) and the
 backward blend's threads per tile (for 16 x 16 tiles: 64 threads of four
 pixels, or 128 of two).  The tuner times a few captured iterations of every
 (tile, depth, threads) candidate on the caller's workload (the library's
@@ -29,7 +30,7 @@ from .raster import Gaussians, MappingStep, ViewBuffers, camera_from, ensure_cap
 
 # (tile_w, tile_h): every shape the blend kernels accept with 64..512 threads
 TILES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (8, 32), (16, 8), (32, 16), (16, 32), (32, 32))
-# staging batch depths (0: one record per thread of each kernel)
+# staging batch depths (0: warp-private for 16 x 16 tiles, else one record per thread)
 DEPTHS: Tuple[int, ...] = (0, 32, 64, 128, 256)
 
 
@@ -47,7 +48,8 @@ def grid(tiles: Sequence[Tuple[int, int]], depths: Sequence[int] = DEPTHS) -> Tu
 
 def label(c) -> str:
     tw, th, d, bt = c
-    return f"{tw}x{th}/depth{d or 'T'}/bwd{bt or 'default'}"
+    dl = d or ("W" if (tw, th) == (16, 16) else "T")  # W: warp-private staging, T: one record per thread
+    return f"{tw}x{th}/depth{dl}/bwd{bt or 'default'}"
 
 
 CANDIDATES = grid(TILES)

@@ -21,6 +21,7 @@
 #include "chain_impl.cuh"
 #include "render_impl.cuh"
 #include "render_q4.cuh"
+#include "render_warp.cuh"
 #include "ssim_impl.cuh"
 
 namespace gsr {
@@ -279,7 +280,11 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
         if (t < 0) continue;
         const int v = view_of_tile(a, t);
         const IterView &w = a.view[v];
-        render_fwd_tile<kQuad>(view_args(a, w), t - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
+        if (kQuad && a.depth == 0)  // each warp stages for itself (render_warp.cuh)
+            render_fwd_tile_warp<false>(view_args(a, w), t - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr,
+                                        reinterpret_cast<Staged *>(smem4), nullptr);
+        else
+            render_fwd_tile<kQuad>(view_args(a, w), t - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
     phase_stamp(a.sync, 1);
@@ -322,6 +327,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
             if (t < 0) continue;
             const int v = view_of_tile(a, t);
             const IterView &w = a.view[v];
+            // (block-staged: warp-private staging measured slower in this phase)
             render_bwd_tile_q4<true>(view_args(a, w), t - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
                                      a.g2, sm);
         }
@@ -341,6 +347,7 @@ static size_t iterate_smem(int depth, bool q4) {
     size_t s = render_bwd_smem(depth > 0 ? depth : kIterThreads);
     if (q4 && 2 * render_q4_smem(depth > 0 ? depth : kQ4Threads) > s) s = 2 * render_q4_smem(depth > 0 ? depth : kQ4Threads);
     if (render_fwd_smem(depth > 0 ? depth : kIterThreads) > s) s = render_fwd_smem(depth > 0 ? depth : kIterThreads);
+    if (depth == 0 && render_warp_smem(kIterThreads) > s) s = render_warp_smem(kIterThreads);
     if (sizeof(float) * kPass1Floats > s) s = sizeof(float) * kPass1Floats;
     if (sizeof(float) * kPass2Floats > s) s = sizeof(float) * kPass2Floats;
     return s;

@@ -608,43 +608,72 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *s, uint32_t P) {
 // distance J < E are registers of the same lane and partners at J >= E are
 // J / E lanes apart (one shuffle each).  With E = P / 32 the first log2(E)
 // merge levels and the short stages of every later level stay in registers.
-// Stages are unrolled at compile time; sizes above P are skipped.
-template <int E, uint32_t K, uint32_t J>
-__device__ __forceinline__ void warp_stage(uint64_t (&v)[E], uint32_t lane) {
-    if constexpr (J < (uint32_t)E) {
+// Only the in-register stages are unrolled at compile time (their register
+// indices must be constants); the levels beyond E and their shuffle stages
+// are runtime loops, which keeps the code of the five E instances small
+// (the warps of one launch run all of them at once).
+
+// In-register stages J, J / 2, .., 1 of a level K >= E: the direction of
+// every pair is the lane's (ascending when bit K / E of the lane is clear).
+template <int E, uint32_t J>
+__device__ __forceinline__ void reg_stages(uint64_t (&v)[E], bool up) {
+    if constexpr (J >= 1) {
 #pragma unroll
         for (uint32_t e = 0; e < (uint32_t)E; ++e)
             if ((e & J) == 0) {
-                // ascending when bit K of the entry's index E lane + e is clear
-                bool up;
-                if constexpr (K < (uint32_t)E) up = (e & K) == 0;
-                else up = (lane & (K / E)) == 0;
                 const uint64_t a = v[e], b = v[e | J];
                 if ((a > b) == up) {
                     v[e] = b;
                     v[e | J] = a;
                 }
             }
-    } else {
-        // K >= 2 J >= 2 E: the direction and the pair's order depend on the lane only
-        const bool keep_min = ((lane & (J / E)) == 0) == ((lane & (K / E)) == 0);
-#pragma unroll
-        for (uint32_t e = 0; e < (uint32_t)E; ++e) {
-            const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], J / E);
-            // the lane keeps the smaller key when it is the lower one of an
-            // ascending pair (or the upper one of a descending pair): one
-            // decision, one 64-bit select (keys are unique)
-            if ((o < v[e]) == keep_min) v[e] = o;
-        }
+        if constexpr (J > 1) reg_stages<E, J / 2>(v, up);
     }
-    if constexpr (J > 1) warp_stage<E, K, J / 2>(v, lane);
+}
+
+// Levels K = 2 .. E / 2, all in registers: the direction of a pair is bit K
+// of its entries' in-lane index e (from level E on it is a bit of the lane).
+template <int E, uint32_t K, uint32_t J>
+__device__ __forceinline__ void reg_level(uint64_t (&v)[E]) {
+#pragma unroll
+    for (uint32_t e = 0; e < (uint32_t)E; ++e)
+        if ((e & J) == 0) {
+            const bool up = (e & K) == 0;
+            const uint64_t a = v[e], b = v[e | J];
+            if ((a > b) == up) {
+                v[e] = b;
+                v[e | J] = a;
+            }
+        }
+    if constexpr (J > 1) reg_level<E, K, J / 2>(v);
 }
 
 template <int E, uint32_t K>
+__device__ __forceinline__ void reg_levels(uint64_t (&v)[E]) {
+    if constexpr (K < (uint32_t)E) {
+        reg_level<E, K, K / 2>(v);
+        reg_levels<E, 2 * K>(v);
+    }
+}
+
+template <int E>
 __device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[E], uint32_t lane, uint32_t P) {
-    if (K > P) return;
-    warp_stage<E, K, K / 2>(v, lane);
-    if constexpr (K < 32u * E) warp_sort_regs<E, 2 * K>(v, lane, P);
+    reg_levels<E, 2>(v);
+    for (uint32_t k = E > 1 ? (uint32_t)E : 2u; k <= P; k <<= 1) {
+        const uint32_t kl = k / (uint32_t)E;
+        for (uint32_t jl = kl >> 1; jl >= 1; jl >>= 1) {  // stages J = K / 2 .. E, J / E lanes apart
+            // the lane keeps the smaller key when it is the lower one of an
+            // ascending pair (or the upper one of a descending pair): one
+            // decision, one 64-bit select (keys are unique)
+            const bool keep_min = ((lane & jl) == 0) == ((lane & kl) == 0);
+#pragma unroll
+            for (uint32_t e = 0; e < (uint32_t)E; ++e) {
+                const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], jl);
+                if ((o < v[e]) == keep_min) v[e] = o;
+            }
+        }
+        reg_stages<E, (uint32_t)E / 2>(v, (lane & kl) == 0);
+    }
 }
 
 // Tile t's segment seg[b, b + L) (L <= 32 E) sorted by one warp in
@@ -660,7 +689,7 @@ __device__ __forceinline__ void warp_tile_sort(const uint64_t *__restrict__ seg,
         const uint32_t i = 32u * e + lane;
         v[e] = i < L ? seg[b + i] : ~0ull;
     }
-    warp_sort_regs<E, 2>(v, lane, P);
+    warp_sort_regs<E>(v, lane, P);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const uint32_t i = (uint32_t)E * lane + e;

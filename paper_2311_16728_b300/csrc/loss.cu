@@ -13,34 +13,49 @@
 // partial sums in a fixed order.
 #include <math.h>
 
+#include <string.h>
+
 #include <mutex>
 
 #include "ssim_impl.cuh"
 
 namespace gsr {
 
-__global__ void __launch_bounds__(kLThreads) ssim_pass1_kernel(const float *__restrict__ x, const float *__restrict__ y,
+// kTma: the staged regions come by TMA (tensor maps tx, ty / ta, tb, tc of
+// the C x H x W planes; W a multiple of 4); else the threads stage them.
+template <bool kTma>
+__global__ void __launch_bounds__(kLThreads, kTma ? 5 : 1) ssim_pass1_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                                                int H, int W, Win win, float *__restrict__ mapA,
                                                                float *__restrict__ mapB, float *__restrict__ mapC,
-                                                               float *__restrict__ partials) {
-    extern __shared__ float sm[];
+                                                               float *__restrict__ partials,
+                                                               const __grid_constant__ CUtensorMap tx,
+                                                               const __grid_constant__ CUtensorMap ty) {
+    extern __shared__ __align__(128) float sm[];
     __shared__ float s_red[32];
+    __shared__ uint64_t s_bar;
+    if (kTma) stage_tma_init(&s_bar);
     const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    ssim_pass1_block<kLThreads>(x, y, H, W, win, mapA, mapB, mapC, partials + 2 * b, blockIdx.x, blockIdx.y,
-                                blockIdx.z, sm, s_red);
+    ssim_pass1_block<kLThreads, kTma>(x, y, H, W, win, mapA, mapB, mapC, partials + 2 * b, blockIdx.x, blockIdx.y,
+                                      blockIdx.z, sm, s_red, &tx, &ty, &s_bar, 0u);
 }
 
+template <bool kTma>
 __global__ void __launch_bounds__(kLThreads, 5) ssim_pass2_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                                                int H, int W, Win win, const float *__restrict__ mapA,
                                                                const float *__restrict__ mapB,
                                                                const float *__restrict__ mapC,
                                                                const float *__restrict__ partials, int64_t npartials,
                                                                float lambda, float *__restrict__ d_loss,
-                                                               float *__restrict__ dx_out) {
-    extern __shared__ float sm[];
+                                                               float *__restrict__ dx_out,
+                                                               const __grid_constant__ CUtensorMap ta,
+                                                               const __grid_constant__ CUtensorMap tb,
+                                                               const __grid_constant__ CUtensorMap tc) {
+    extern __shared__ __align__(128) float sm[];
     __shared__ double s_dbl[2 * kLThreads];
-    ssim_pass2_block<kLThreads>(x, y, H, W, gridDim.z, win, mapA, mapB, mapC, lambda, 1.0f, dx_out, blockIdx.x,
-                                blockIdx.y, blockIdx.z, sm);
+    __shared__ uint64_t s_bar;
+    if (kTma) stage_tma_init(&s_bar);
+    ssim_pass2_block<kLThreads, kTma>(x, y, H, W, gridDim.z, win, mapA, mapB, mapC, lambda, 1.0f, dx_out,
+                                      blockIdx.x, blockIdx.y, blockIdx.z, sm, &ta, &tb, &tc, &s_bar, 0u);
     // the first CTA folds the per-CTA partial sums, always in the same order
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
         const float L = loss_from_partials<kLThreads>(partials, npartials, (double)gridDim.z * H * W, lambda, s_dbl);
@@ -48,20 +63,43 @@ __global__ void __launch_bounds__(kLThreads, 5) ssim_pass2_kernel(const float *_
     }
 }
 
-constexpr size_t kPass1Smem = sizeof(float) * kPass1Floats;
-constexpr size_t kPass2Smem = sizeof(float) * kPass2Floats;
+template <bool kTma> constexpr size_t pass1_smem() { return sizeof(float) * pass1_floats<kTma>(); }
+template <bool kTma> constexpr size_t pass2_smem() { return sizeof(float) * pass2_floats<kTma>(); }
+
+// Tensor map of a C x H x W FP32 plane stack for the staging box (48 x 42 x
+// 1), zero fill outside; false when TMA cannot take it (W not a multiple of
+// 4, a base not 16-byte aligned, no encoder) and the threads stage instead.
+static bool plane_map(CUtensorMap *m, const float *base, int C, int H, int W) {
+    auto enc = tensor_map_encoder();
+    if (!enc || W % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kRP, (cuuint32_t)kRH, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 static void launch_ssim(const float *img, const float *gt, int C, int H, int W, float lambda, float *d_loss,
                         float *dL_dimg, float *mA, float *mB, float *mC, float *part, int64_t nblocks,
                         cudaStream_t st) {
-    // (per device, cheap, and not a stream operation: fine during capture)
-    cudaFuncSetAttribute(ssim_pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem);
-    cudaFuncSetAttribute(ssim_pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass2Smem);
     const Win win = ssim_window();
     const dim3 grid((W + kLTW - 1) / kLTW, (H + kLTH - 1) / kLTH, C);
-    ssim_pass1_kernel<<<grid, kLThreads, kPass1Smem, st>>>(img, gt, H, W, win, mA, mB, mC, part);
-    ssim_pass2_kernel<<<grid, kLThreads, kPass2Smem, st>>>(img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda,
-                                                            d_loss, dL_dimg);
+    CUtensorMap t[5];
+    const bool tma = plane_map(&t[0], img, C, H, W) && plane_map(&t[1], gt, C, H, W) &&
+                     plane_map(&t[2], mA, C, H, W) && plane_map(&t[3], mB, C, H, W) && plane_map(&t[4], mC, C, H, W);
+    auto k1 = tma ? ssim_pass1_kernel<true> : ssim_pass1_kernel<false>;
+    auto k2 = tma ? ssim_pass2_kernel<true> : ssim_pass2_kernel<false>;
+    if (!tma) memset(t, 0, sizeof(t));  // unused by the kernels that stage themselves
+    // (per device, cheap, and not a stream operation: fine during capture)
+    const size_t s1 = tma ? pass1_smem<true>() : pass1_smem<false>();
+    const size_t s2 = tma ? pass2_smem<true>() : pass2_smem<false>();
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+    cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+    k1<<<grid, kLThreads, s1, st>>>(img, gt, H, W, win, mA, mB, mC, part, t[0], t[1]);
+    k2<<<grid, kLThreads, s2, st>>>(img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda, d_loss, dL_dimg, t[2],
+                                    t[3], t[4]);
 }
 
 // ---------------------------------------------------------------- PSNR

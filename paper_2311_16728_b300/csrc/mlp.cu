@@ -4,8 +4,6 @@
 // 256 -> 56 ReLU MLP over multi-level image patches, in BF16 with FP32
 // accumulation on the tcgen05 tensor cores (umma_gemm.cuh), trained by MSE
 // with Adam on FP32 master weights.
-#include <cudaTypedefs.h>
-
 #include <mutex>
 
 #include "umma_gemm.cuh"
@@ -13,20 +11,6 @@
 namespace gsr {
 
 // ---------------------------------------------------------------- tensor maps
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void *p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
 // K-major BF16 matrix [rows x K] (K contiguous, row stride ld elements), box
 // of 64 (K) x box_rows rows, 128-byte swizzle.
 static int32_t make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t K, int64_t ld, int box_rows) {

@@ -10,12 +10,15 @@
 // thread per batch; while staging, each record gets a bit mask of the warps
 // whose pixel rectangle can see it at all (pixel box intersected with the
 // bounding box of its alpha >= 1/255 ellipse, conservatively widened), and
-// each warp then visits only its set bits.  The per-pixel decisions (box,
+// each warp then visits only its set bits.  For 16 x 16 tiles at the default
+// staging depth (0) every warp stages for itself instead (render_warp.cuh:
+// no block-wide barrier between the warps of a tile).  The per-pixel decisions (box,
 // exponent sign, 1/255 skip, 0.99 clamp, 1e-4 stop) are evaluated with the
 // same instructions in both kernels, so the backward replays exactly the
 // forward's choices.
 #include "render_impl.cuh"
 #include "render_q4.cuh"
+#include "render_warp.cuh"
 
 namespace gsr {
 
@@ -91,6 +94,32 @@ __global__ void __launch_bounds__(kQ4Threads) render_bwd_q4_kernel(RenderArgs a,
     render_bwd_tile_q4<false, true>(a, tile, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
+// 16 x 16 tiles with warp-private staging (render_warp.cuh)
+template <bool kCount>
+__global__ void __launch_bounds__(kWarpFwdThreads) render_fwd_warp_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                                        float *__restrict__ img,
+                                                                        float *__restrict__ T_final,
+                                                                        uint32_t *__restrict__ n_contrib,
+                                                                        uint32_t *__restrict__ n_blended,
+                                                                        uint32_t *__restrict__ tile_work) {
+    __shared__ Staged s_buf[kWarpFwdThreads];  // 32 records per warp
+    const int tile = cta_tile(order);
+    if (tile < 0) return;
+    render_fwd_tile_warp<kCount>(a, tile, img, T_final, n_contrib, n_blended, s_buf, tile_work);
+}
+
+__global__ void __launch_bounds__(kWarpBwdThreads) render_bwd_warp_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                                        const float *__restrict__ T_final,
+                                                                        const uint32_t *__restrict__ n_contrib,
+                                                                        const float *__restrict__ dL_dimg,
+                                                                        float *__restrict__ g0, float *__restrict__ g1,
+                                                                        float *__restrict__ g2) {
+    __shared__ Staged s_buf[kWarpBwdThreads];  // 32 records per warp
+    const int tile = cta_tile(order);
+    if (tile < 0) return;
+    render_bwd_tile_warp(a, tile, T_final, n_contrib, dL_dimg, g0, g1, g2, s_buf);
+}
+
 static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const uint32_t *ranges,
                             const gsr_camera *cam, const gsr_tiling *t, const float *bg) {
     RenderArgs a;
@@ -132,6 +161,12 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const int depth = a.depth > 0 ? a.depth : nthr;
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
+    if (quad && a.depth == 0) {  // warp-private staging (the default for 16 x 16 tiles)
+        auto wk = n_blended ? render_fwd_warp_kernel<true> : render_fwd_warp_kernel<false>;
+        wk<<<tiles, kWarpFwdThreads, 0, as_cuda(stream)>>>(a, proj->tile_order, img, T_final, n_contrib, n_blended,
+                                                           proj->tile_order ? proj->tile_work : nullptr);
+        return check_launch("render_fwd_warp_kernel");
+    }
     auto kernel = n_blended ? (quad ? render_fwd_kernel<true, true> : render_fwd_kernel<true, false>)
                             : (quad ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
     // (per device and cheap, not a stream operation: fine during capture)
@@ -172,8 +207,13 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
         work_order_kernel<<<1, kWorkOrderThreads, 0, st>>>(proj->tile_work, (uint32_t)tiles, proj->tile_order);
         if ((rc = check_launch("work_order_kernel"))) return rc;
     }
-    if (quad && tiling->bwd_threads != nthr) {  // 64 threads, four pixels each (the default)
-        const int depth = a.depth > 0 ? a.depth : kQ4Threads;
+    if (quad && tiling->bwd_threads != nthr && a.depth == 0) {  // warp-private staging, four pixels a thread
+        render_bwd_warp_kernel<<<tiles, kWarpBwdThreads, 0, st>>>(a, proj->tile_order, T_final, n_contrib, dL_dimg,
+                                                                  grad2d->g0, grad2d->g1, grad2d->g2);
+        return check_launch("render_bwd_warp_kernel");
+    }
+    if (quad && tiling->bwd_threads != nthr) {  // 64 threads, four pixels each, block-staged batches
+        const int depth = a.depth;
         cudaFuncSetAttribute(render_bwd_q4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)render_q4_smem(depth));
         render_bwd_q4_kernel<<<tiles, kQ4Threads, render_q4_smem(depth), st>>>(

@@ -223,11 +223,9 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // Blackwell's packed FP32 instructions (FFMA2 / FMUL2 / FADD2: each lane
 // rounded to nearest exactly like the scalar operation), one issue slot for
 // both pixels.
-template <bool kQuad>
-__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, const float2 lo, const uint2 *lanes,
-                                                 int px, float fpx, float2 fpy, int py0, PixAlpha &r) {
-    bool b0, b1;
-    in_box<kQuad>(cb, lanes, px, py0, b0, b1);
+// b0, b1: whether the two pixels lie in the splat's pixel box
+__device__ __forceinline__ void pair_alpha(const float4 g, const float4 cb, const float2 lo, float fpx, float2 fpy,
+                                           bool b0, bool b1, PixAlpha &r) {
     const float dx = FS(FS(fpx, g.x), lo.x);
     const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
     const float2 dy = __fadd2_rn(__fadd2_rn(fpy, f2(-g.y)), f2(-lo.y));
@@ -237,6 +235,14 @@ __device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb
     r.a1 = fminf(kAlphaMax, raw.y);
     r.ok0 = b0 && e.x <= 0.0f && r.a0 >= kAlphaMin;
     r.ok1 = b1 && e.y <= 0.0f && r.a1 >= kAlphaMin;
+}
+
+template <bool kQuad>
+__device__ __forceinline__ void pixel_pair_alpha(const float4 g, const float4 cb, const float2 lo, const uint2 *lanes,
+                                                 int px, float fpx, float2 fpy, int py0, PixAlpha &r) {
+    bool b0, b1;
+    in_box<kQuad>(cb, lanes, px, py0, b0, b1);
+    pair_alpha(g, cb, lo, fpx, fpy, b0, b1, r);
 }
 
 // Front-to-back blend of one evaluated splat into the thread's two pixels

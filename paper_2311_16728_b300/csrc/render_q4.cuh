@@ -122,6 +122,97 @@ struct PairBwd {
     float2 T, accd, dC0, dC1, dC2;
 };
 
+// The contribution of one staged splat (list position pos, the warp's box
+// lane masks lm) to this thread's four pixels and, reduced over the warp, to
+// the splat's screen-space gradient: the pixels' alphas a pair at a time,
+// their back-to-front updates, and the warp's transposed reduction with its
+// atomics into g0 / g1 (lane 4k: value k at gk) and g2.
+__device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, const uint4 lm, int lane, float fpx,
+                                             const float2 (&fpy)[2], const uint32_t (&last)[4], PairBwd (&p)[2],
+                                             float *gk, float *__restrict__ g2) {
+    const float4 g = sj.xy, cb = sj.cb;
+    const float2 lo = sj.lo;
+    const float dx = FS(FS(fpx, g.x), lo.x);
+    const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
+    // alpha at the four pixels, a pair at a time
+    float2 dy[2], al[2], gs[2];
+    bool ok[4], cl[4];
+    bool any = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        dy[h] = __fadd2_rn(__fadd2_rn(fpy[h], f2(-g.y)), f2(-lo.y));
+        const float2 e = __ffma2_rn(__fmul2_rn(f2(cb.x), dy[h]), dy[h], __ffma2_rn(f2(bdx), dy[h], f2(t)));
+        gs[h] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+        const float2 raw = __fmul2_rn(f2(cb.y), gs[h]);
+        al[h] = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+        cl[2 * h] = raw.x > kAlphaMax;
+        cl[2 * h + 1] = raw.y > kAlphaMax;
+        ok[2 * h] = pos < last[2 * h] && ((q4_lane_bits(lm, 2 * h) >> lane) & 1u) && e.x <= 0.0f &&
+                    al[h].x >= kAlphaMin;
+        ok[2 * h + 1] = pos < last[2 * h + 1] && ((q4_lane_bits(lm, 2 * h + 1) >> lane) & 1u) && e.y <= 0.0f &&
+                        al[h].y >= kAlphaMin;
+        any = any || ok[2 * h] || ok[2 * h + 1];
+    }
+    // v2[0 .. 2]: the lane's dpow-weighted moments in dy (sum dpow,
+    // sum dpow dy, sum dpow dy^2), from which the five conic and
+    // mean sums follow once per lane (dx is the lane's own);
+    // v2[5 .. 8]: the opacity and colour sums
+    float2 v2[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v2[q] = make_float2(0.f, 0.f);
+    const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
+    const float C = cb.x * (1.0f / kHalfLog2e);
+    if (any) {
+        const float4 col = sj.rgb;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
+            if (!(o0 || o1)) continue;
+            const bool q0 = o0 && !cl[2 * h], q1 = o1 && !cl[2 * h + 1];
+            // alpha of a pixel without a contribution is 0: every update below leaves it unchanged
+            const float2 al_e = make_float2(o0 ? al[h].x : 0.f, o1 ? al[h].y : 0.f);
+            const float2 al_g = make_float2(q0 ? al[h].x : 0.f, q1 ? al[h].y : 0.f);
+            const float2 g_g = make_float2(q0 ? gs[h].x : 0.f, q1 ? gs[h].y : 0.f);
+            const float2 one_m = __fadd2_rn(f2(1.0f), neg2(al_e));
+            const float2 rc = make_float2(o0 ? __fdividef(1.0f, one_m.x) : 1.0f,
+                                          o1 ? __fdividef(1.0f, one_m.y) : 1.0f);
+            PairBwd &P = p[h];
+            P.T = __fmul2_rn(P.T, rc);  // transmittance in front of this Gaussian
+            const float2 aT = __fmul2_rn(al_e, P.T);
+            v2[6] = __ffma2_rn(P.dC0, aT, v2[6]);
+            v2[7] = __ffma2_rn(P.dC1, aT, v2[7]);
+            v2[8] = __ffma2_rn(P.dC2, aT, v2[8]);
+            float2 dc = __fmul2_rn(P.dC0, f2(col.x));
+            dc = __ffma2_rn(P.dC1, f2(col.y), dc);
+            dc = __ffma2_rn(P.dC2, f2(col.z), dc);
+            const float2 dalpha = __fmul2_rn(P.T, __fadd2_rn(dc, neg2(P.accd)));
+            P.accd = __ffma2_rn(dc, al_e, __fmul2_rn(P.accd, one_m));
+            const float2 dpow = __fmul2_rn(dalpha, al_g);
+            v2[5] = __ffma2_rn(dalpha, g_g, v2[5]);
+            const float2 tdy = __fmul2_rn(dpow, dy[h]);
+            v2[0] = __fadd2_rn(v2[0], dpow);
+            v2[1] = __fadd2_rn(v2[1], tdy);
+            v2[2] = __ffma2_rn(tdy, dy[h], v2[2]);
+        }
+    }
+    if (__any_sync(0xffffffffu, any)) {
+        float v[9];
+        const float S0 = v2[0].x + v2[0].y, S1 = v2[1].x + v2[1].y, S2 = v2[2].x + v2[2].y;
+        v[0] = __fmaf_rn(B, S1, (A * dx) * S0);  // dL/du: sum dpow (A dx + B dy)
+        v[1] = __fmaf_rn(C, S1, (B * dx) * S0);  // dL/dv: sum dpow (B dx + C dy)
+        v[2] = (-0.5f * dx * dx) * S0;           // dL/dA: sum dpow (-dx^2 / 2)
+        v[3] = -dx * S1;                         // dL/dB: sum dpow (-dx dy)
+        v[4] = -0.5f * S2;                       // dL/dC: sum dpow (-dy^2 / 2)
+#pragma unroll
+        for (int q = 5; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
+        float v8;
+        const float y = warp_transpose_sum(v, v8);
+        const uint32_t gid = sj.gid;
+        if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
+        else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+    }
+}
+
 template <bool kHalf = false, bool kExact = kHalf>
 __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile, const float *__restrict__ T_final,
                                                    const uint32_t *__restrict__ n_contrib,
@@ -201,91 +292,8 @@ __device__ __forceinline__ void render_bwd_tile_q4(const RenderArgs &a, int tile
             while (bits) {  // back to front
                 const int j = c0 + 31 - __clz(bits);
                 bits &= ~(1u << (j - c0));
-                const uint32_t pos = (uint32_t)(bstart + j - begin);
                 const Staged &sj = s_st[j];
-                const float4 g = sj.xy, cb = sj.cb;
-                const float2 lo = sj.lo;
-                const uint4 lm = sj.lanes[wid];
-                const float dx = FS(FS(fpx, g.x), lo.x);
-                const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
-                // alpha at the four pixels, a pair at a time
-                float2 dy[2], al[2], gs[2];
-                bool ok[4], cl[4];
-                bool any = false;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    dy[h] = __fadd2_rn(__fadd2_rn(fpy[h], f2(-g.y)), f2(-lo.y));
-                    const float2 e = __ffma2_rn(__fmul2_rn(f2(cb.x), dy[h]), dy[h],
-                                                __ffma2_rn(f2(bdx), dy[h], f2(t)));
-                    gs[h] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                    const float2 raw = __fmul2_rn(f2(cb.y), gs[h]);
-                    al[h] = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
-                    cl[2 * h] = raw.x > kAlphaMax;
-                    cl[2 * h + 1] = raw.y > kAlphaMax;
-                    ok[2 * h] = pos < last[2 * h] && ((q4_lane_bits(lm, 2 * h) >> lane) & 1u) && e.x <= 0.0f &&
-                                al[h].x >= kAlphaMin;
-                    ok[2 * h + 1] = pos < last[2 * h + 1] && ((q4_lane_bits(lm, 2 * h + 1) >> lane) & 1u) &&
-                                    e.y <= 0.0f && al[h].y >= kAlphaMin;
-                    any = any || ok[2 * h] || ok[2 * h + 1];
-                }
-                // v2[0 .. 2]: the lane's dpow-weighted moments in dy (sum dpow,
-                // sum dpow dy, sum dpow dy^2), from which the five conic and
-                // mean sums follow once per lane (dx is the lane's own);
-                // v2[5 .. 8]: the opacity and colour sums
-                float2 v2[9];
-#pragma unroll
-                for (int q = 0; q < 9; ++q) v2[q] = make_float2(0.f, 0.f);
-                const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
-                const float C = cb.x * (1.0f / kHalfLog2e);
-                if (any) {
-                    const float4 col = sj.rgb;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
-                        if (!(o0 || o1)) continue;
-                        const bool q0 = o0 && !cl[2 * h], q1 = o1 && !cl[2 * h + 1];
-                        // alpha of a pixel without a contribution is 0: every update below leaves it unchanged
-                        const float2 al_e = make_float2(o0 ? al[h].x : 0.f, o1 ? al[h].y : 0.f);
-                        const float2 al_g = make_float2(q0 ? al[h].x : 0.f, q1 ? al[h].y : 0.f);
-                        const float2 g_g = make_float2(q0 ? gs[h].x : 0.f, q1 ? gs[h].y : 0.f);
-                        const float2 one_m = __fadd2_rn(f2(1.0f), neg2(al_e));
-                        const float2 rc = make_float2(o0 ? __fdividef(1.0f, one_m.x) : 1.0f,
-                                                      o1 ? __fdividef(1.0f, one_m.y) : 1.0f);
-                        PairBwd &P = p[h];
-                        P.T = __fmul2_rn(P.T, rc);  // transmittance in front of this Gaussian
-                        const float2 aT = __fmul2_rn(al_e, P.T);
-                        v2[6] = __ffma2_rn(P.dC0, aT, v2[6]);
-                        v2[7] = __ffma2_rn(P.dC1, aT, v2[7]);
-                        v2[8] = __ffma2_rn(P.dC2, aT, v2[8]);
-                        float2 dc = __fmul2_rn(P.dC0, f2(col.x));
-                        dc = __ffma2_rn(P.dC1, f2(col.y), dc);
-                        dc = __ffma2_rn(P.dC2, f2(col.z), dc);
-                        const float2 dalpha = __fmul2_rn(P.T, __fadd2_rn(dc, neg2(P.accd)));
-                        P.accd = __ffma2_rn(dc, al_e, __fmul2_rn(P.accd, one_m));
-                        const float2 dpow = __fmul2_rn(dalpha, al_g);
-                        v2[5] = __ffma2_rn(dalpha, g_g, v2[5]);
-                        const float2 tdy = __fmul2_rn(dpow, dy[h]);
-                        v2[0] = __fadd2_rn(v2[0], dpow);
-                        v2[1] = __fadd2_rn(v2[1], tdy);
-                        v2[2] = __ffma2_rn(tdy, dy[h], v2[2]);
-                    }
-                }
-                if (__any_sync(0xffffffffu, any)) {
-                    float v[9];
-                    const float S0 = v2[0].x + v2[0].y, S1 = v2[1].x + v2[1].y, S2 = v2[2].x + v2[2].y;
-                    v[0] = __fmaf_rn(B, S1, (A * dx) * S0);  // dL/du: sum dpow (A dx + B dy)
-                    v[1] = __fmaf_rn(C, S1, (B * dx) * S0);  // dL/dv: sum dpow (B dx + C dy)
-                    v[2] = (-0.5f * dx * dx) * S0;           // dL/dA: sum dpow (-dx^2 / 2)
-                    v[3] = -dx * S1;                         // dL/dB: sum dpow (-dx dy)
-                    v[4] = -0.5f * S2;                       // dL/dC: sum dpow (-dy^2 / 2)
-#pragma unroll
-                    for (int q = 5; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
-                    float v8;
-                    const float y = warp_transpose_sum(v, v8);
-                    const uint32_t gid = sj.gid;
-                    if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
-                    else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
-                }
+                q4_splat_bwd(sj, (uint32_t)(bstart + j - begin), sj.lanes[wid], lane, fpx, fpy, last, p, gk, g2);
             }
         }
     }

@@ -6,13 +6,26 @@
 
 #include <math.h>
 
-#include "gsr_internal.cuh"
+#include "tma.cuh"
 
 namespace gsr {
 
 constexpr int kLTW = 32, kLTH = 32, kLR = 5;       // output tile and window radius
 constexpr int kRW = kLTW + 2 * kLR, kRH = kLTH + 2 * kLR;
-constexpr int kRS = 45;                            // row stride of the staged region (conflict-free)
+// Staged planes, two layouts of rows oy - 5 .. oy + 36:
+//  - staged by the threads: columns ox - 5 .. ox + 36, row stride kRS = 45
+//    (the row pass's scalar loads hit distinct banks);
+//  - staged by TMA: columns ox - 8 .. ox + 39, row stride kRP = 48 floats (a
+//    TMA box starts on a 16-byte column boundary; the window's halo starts at
+//    column kRC = 3), read by the row pass in 16-byte loads.
+constexpr int kRS = 45;
+constexpr int kRP = 48, kRX = 8, kRC = kRX - kLR;
+template <bool kTma> struct Region {
+    static constexpr int pitch = kTma ? kRP : kRS;    // row stride
+    static constexpr int col0 = kTma ? kRX : kLR;     // column of the tile's first output column
+    static constexpr int plane = kRH * pitch;         // floats of one staged plane
+};
+constexpr int kPlane = Region<true>::plane;        // TMA plane: 8064 bytes, a 128-byte multiple
 constexpr int kRun = 4;                            // outputs per thread along a row / column
 constexpr int kMS = kLTW + 1;                      // row stride of the row-blurred maps (odd: fewer
                                                    // bank conflicts on the row pass's stores)
@@ -85,8 +98,39 @@ __device__ __forceinline__ void stage_planes(const float *const (&src)[NP], int 
     }
 }
 
-constexpr size_t kPass1Floats = 2 * kRH * kRS + 5 * kRH * kMS;
-constexpr size_t kPass2Floats = 3 * kRH * kRS + 3 * kRH * kMS;
+// The same regions, copied by the Tensor Memory Accelerator: plane p of the
+// C x H x W tensor maps[p] (FP32, zero outside the image), box 48 x 42 x 1
+// at column ox - 8 (a multiple of 4: the 16-byte rule of the box's first
+// column), row oy - 5, channel c, into dst + p kPlane (128-byte aligned).
+// Thread 0 issues the copies on the mbarrier `bar` (one phase per call:
+// `parity` alternates between calls); every thread waits, with a bound.
+// Returns false, in every thread, when the wait gave up.
+template <int NP>
+__device__ __forceinline__ bool stage_planes_tma(const CUtensorMap *const (&maps)[NP], int ox, int oy, int c,
+                                                 float *dst, uint64_t *bar, uint32_t parity) {
+    if (threadIdx.x == 0) {
+        tma::mbar_expect_tx(bar, (uint32_t)(NP * kPlane * sizeof(float)));
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) tma::load_3d(dst + pl * kPlane, maps[pl], ox - kRX, oy - kLR, c, bar);
+    }
+    const bool ok = tma::mbar_wait(bar, parity);
+    return __syncthreads_or(!ok) == 0;
+}
+
+// One-time set-up of the staging mbarrier of a CTA (before its first
+// stage_planes_tma; every thread calls it).
+__device__ __forceinline__ void stage_tma_init(uint64_t *bar) {
+    if (threadIdx.x == 0) {
+        tma::mbar_init(bar, 1);
+        tma::fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+template <bool kTma> constexpr size_t pass1_floats() { return 2 * Region<kTma>::plane + 5 * kRH * kMS; }
+template <bool kTma> constexpr size_t pass2_floats() { return 3 * Region<kTma>::plane + 3 * kRH * kMS; }
+constexpr size_t kPass1Floats = pass1_floats<false>();  // the thread-staged layout
+constexpr size_t kPass2Floats = pass2_floats<false>();
 
 __device__ __forceinline__ float2 f2w(float x) { return make_float2(x, x); }
 
@@ -100,53 +144,111 @@ __device__ __forceinline__ float2 f2w(float x) { return make_float2(x, x); }
 // (separable: rows then columns, kRun outputs per thread from kRun + 10
 // staged values), SSIM map, its partials (a, b, c) and the block's sums of
 // |x - y| and SSIM into part[0], part[1].
-template <int NT>
+// kTma: x and y come by TMA (tensor maps tmx, tmy, the CTA's mbarrier `bar`
+// and its phase parity), else the threads stage them.
+template <int NT, bool kTma = false>
 __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                  int W, const Win &win, float *__restrict__ mapA,
                                                  float *__restrict__ mapB, float *__restrict__ mapC,
                                                  float *__restrict__ part, int bx, int by, int c, float *sm,
-                                                 float *s_red) {
-    float *sX = sm, *sY = sm + kRH * kRS;
+                                                 float *s_red, const CUtensorMap *tmx = nullptr,
+                                                 const CUtensorMap *tmy = nullptr, uint64_t *bar = nullptr,
+                                                 uint32_t parity = 0u) {
+    using Rg = Region<kTma>;
+    float *sX = sm, *sY = sm + Rg::plane;
     // row-blurred moments: (mean x, mean y) and (E x^2, E y^2) pairs, then E xy
-    float2 *sM2 = reinterpret_cast<float2 *>(sm + 2 * kRH * kRS);  // [kRH][kMS]
-    float2 *sS2 = sM2 + kRH * kMS;                                  // [kRH][kMS]
-    float *sXY = reinterpret_cast<float *>(sS2 + kRH * kMS);        // [kRH][kMS]
+    float2 *sM2 = reinterpret_cast<float2 *>(sm + 2 * Rg::plane);  // [kRH][kMS]
+    float2 *sS2 = sM2 + kRH * kMS;                              // [kRH][kMS]
+    float *sXY = reinterpret_cast<float *>(sS2 + kRH * kMS);    // [kRH][kMS]
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     __syncthreads();  // the previous block's readers of sm are done
-    {
+    if constexpr (kTma) {
+        const CUtensorMap *const maps[2] = {tmx, tmy};
+        if (!stage_planes_tma<2>(maps, ox, oy, c, sX, bar, parity)) {
+            if (threadIdx.x == 0) part[0] = part[1] = __int_as_float(0x7fc00000);  // the loss reads NaN
+            return;
+        }
+    } else {
         const float *const planes[2] = {x + cb, y + cb};
         stage_planes<NT, 2>(planes, H, W, ox, oy, sX);  // sY = sX + kRH kRS
+        __syncthreads();
     }
-    __syncthreads();
+    // a warp covers four rows of eight runs: its staged loads hit distinct
+    // banks (16-byte loads: in each quarter warp), the row-blurred stores
+    // (odd row stride kMS) at most two lanes a bank
+    if constexpr (!kTma)
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
-        // a warp covers four rows of eight runs: the staged loads (row
-        // stride kRS) hit distinct banks, the row-blurred stores (odd row
-        // stride kMS) at most two lanes a bank
         const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
-        // values and their products once per staged column
-        float2 v[kRun + 10], q[kRun + 10];
-        float xy[kRun + 10];
+        {
+            // values and their products once per staged column
+            float2 v[kRun + 10], q[kRun + 10];
+            float xy[kRun + 10];
 #pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) {
-            v[k] = make_float2(sX[r * kRS + j0 + k], sY[r * kRS + j0 + k]);
-            q[k] = __fmul2_rn(v[k], v[k]);
-            xy[k] = v[k].x * v[k].y;
+            for (int k = 0; k < kRun + 10; ++k) {
+                v[k] = make_float2(sX[r * kRS + j0 + k], sY[r * kRS + j0 + k]);
+                q[k] = __fmul2_rn(v[k], v[k]);
+                xy[k] = v[k].x * v[k].y;
+            }
+#pragma unroll
+            for (int o = 0; o < kRun; ++o) {
+                float2 m = make_float2(0.f, 0.f), sq = make_float2(0.f, 0.f);
+                float sxy = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) {
+                    const float w = win.w[k];
+                    m = __ffma2_rn(f2w(w), v[o + k], m);
+                    sq = __ffma2_rn(f2w(w), q[o + k], sq);
+                    sxy = __fmaf_rn(w, xy[o + k], sxy);
+                }
+                sM2[r * kMS + j0 + o] = m;
+                sS2[r * kMS + j0 + o] = sq;
+                sXY[r * kMS + j0 + o] = sxy;
+            }
+        }
+    }
+    else
+    for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
+        const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
+        // streamed over the staged columns: five 16-byte loads a plane
+        // (columns j0 .. j0 + 19 of the staged row, of which kRC .. kRC + 13
+        // are used); each value and its products update the outputs whose
+        // window holds it, every sum in ascending tap order
+        float2 m[kRun], sq[kRun];
+        float sxy[kRun];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            m[o] = sq[o] = make_float2(0.f, 0.f);
+            sxy[o] = 0.f;
+        }
+        const float4 *px4 = reinterpret_cast<const float4 *>(sX + r * kRP + j0);
+        const float4 *py4 = reinterpret_cast<const float4 *>(sY + r * kRP + j0);
+#pragma unroll
+        for (int m4 = 0; m4 < 5; ++m4) {
+            const float4 a = px4[m4], b = py4[m4];
+            const float ax[4] = {a.x, a.y, a.z, a.w}, by[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * m4 + i - kRC;  // staged column k of the window run
+                if (k < 0 || k >= kRun + 10) continue;
+                const float2 v = make_float2(ax[i], by[i]);
+                const float2 q = __fmul2_rn(v, v);
+                const float xy = v.x * v.y;
+#pragma unroll
+                for (int o = 0; o < kRun; ++o) {
+                    if (k - o < 0 || k - o > 10) continue;
+                    const float w = win.w[k - o];
+                    m[o] = __ffma2_rn(f2w(w), v, m[o]);
+                    sq[o] = __ffma2_rn(f2w(w), q, sq[o]);
+                    sxy[o] = __fmaf_rn(w, xy, sxy[o]);
+                }
+            }
         }
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
-            float2 m = make_float2(0.f, 0.f), sq = make_float2(0.f, 0.f);
-            float sxy = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                const float w = win.w[k];
-                m = __ffma2_rn(f2w(w), v[o + k], m);
-                sq = __ffma2_rn(f2w(w), q[o + k], sq);
-                sxy = __fmaf_rn(w, xy[o + k], sxy);
-            }
-            sM2[r * kMS + j0 + o] = m;
-            sS2[r * kMS + j0 + o] = sq;
-            sXY[r * kMS + j0 + o] = sxy;
+            sM2[r * kMS + j0 + o] = m[o];
+            sS2[r * kMS + j0 + o] = sq[o];
+            sXY[r * kMS + j0 + o] = sxy[o];
         }
     }
     __syncthreads();
@@ -200,8 +302,8 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
                 mapA[idx] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
                 mapB[idx] = dS_dsxx;
                 mapC[idx] = dS_dsxy;
-                const int rr = i0 + o + kLR, qq = tx + kLR;
-                l1 += fabsf(sX[rr * kRS + qq] - sY[rr * kRS + qq]);
+                const int rr = i0 + o + kLR, qq = tx + Rg::col0;
+                l1 += fabsf(sX[rr * Rg::pitch + qq] - sY[rr * Rg::pitch + qq]);
                 ssim += S;
             }
         }
@@ -217,47 +319,100 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
 // Pass 2 on block (bx, by) of channel c: blur (a, b, c) (the adjoint of the
 // symmetric window), then
 // dL/dx = scale ((1 - lambda) sign(x - y) - lambda (G*a + 2 x G*b + y G*c)) / (C H W).
-template <int NT>
+// kTma: (a, b, c) come by TMA (tensor maps tma_a, tma_b, tma_c, the CTA's
+// mbarrier `bar` and its phase parity), else the threads stage them.
+template <int NT, bool kTma = false>
 __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                  int W, int C, const Win &win, const float *__restrict__ mapA,
                                                  const float *__restrict__ mapB, const float *__restrict__ mapC,
                                                  float lambda, float scale, float *__restrict__ dx_out, int bx, int by,
-                                                 int c, float *sm) {
-    float *sM = sm;                                                  // [3][kRH][kRS]
-    float2 *sAB = reinterpret_cast<float2 *>(sm + 3 * kRH * kRS);    // [kRH][kMS] row-blurred (a, b)
-    float *sCh = reinterpret_cast<float *>(sAB + kRH * kMS);         // [kRH][kMS] row-blurred c
+                                                 int c, float *sm, const CUtensorMap *tma_a = nullptr,
+                                                 const CUtensorMap *tma_b = nullptr,
+                                                 const CUtensorMap *tma_c = nullptr, uint64_t *bar = nullptr,
+                                                 uint32_t parity = 0u) {
+    using Rg = Region<kTma>;
+    float *sM = sm;                                                  // [3][kRH][pitch]
+    float2 *sAB = reinterpret_cast<float2 *>(sm + 3 * Rg::plane);    // [kRH][kMS] row-blurred (a, b)
+    float *sCh = reinterpret_cast<float *>(sAB + kRH * kMS);      // [kRH][kMS] row-blurred c
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     const float inv_n = (float)((double)scale / ((double)C * (double)plane));
     __syncthreads();
-    {
+    if constexpr (kTma) {
+        const CUtensorMap *const maps[3] = {tma_a, tma_b, tma_c};
+        if (!stage_planes_tma<3>(maps, ox, oy, c, sM, bar, parity)) {
+            for (int k = threadIdx.x; k < kLTW * kLTH; k += NT) {  // the gradient reads NaN
+                const int gx = ox + k % kLTW, gy = oy + k / kLTW;
+                if (gx < W && gy < H) dx_out[cb + (int64_t)gy * W + gx] = __int_as_float(0x7fc00000);
+            }
+            return;
+        }
+    } else {
         const float *const planes[3] = {mapA + cb, mapB + cb, mapC + cb};
         stage_planes<NT, 3>(planes, H, W, ox, oy, sM);
+        __syncthreads();
     }
-    __syncthreads();
+    // a warp covers four rows of eight runs (as in pass 1)
+    if constexpr (!kTma)
     for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
-        // a warp covers four rows of eight runs: the staged loads (row
-        // stride kRS) hit distinct banks, the row-blurred stores (odd row
-        // stride kMS) at most two lanes a bank
         const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
-        float2 ab[kRun + 10];
-        float cc[kRun + 10];
+        {
+            float2 ab[kRun + 10];
+            float cc[kRun + 10];
 #pragma unroll
-        for (int k = 0; k < kRun + 10; ++k) {
-            ab[k] = make_float2(sM[r * kRS + j0 + k], sM[kRH * kRS + r * kRS + j0 + k]);
-            cc[k] = sM[2 * kRH * kRS + r * kRS + j0 + k];
+            for (int k = 0; k < kRun + 10; ++k) {
+                ab[k] = make_float2(sM[r * kRS + j0 + k], sM[kRH * kRS + r * kRS + j0 + k]);
+                cc[k] = sM[2 * kRH * kRS + r * kRS + j0 + k];
+            }
+#pragma unroll
+            for (int o = 0; o < kRun; ++o) {
+                float2 s2 = make_float2(0.f, 0.f);
+                float s1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) {
+                    s2 = __ffma2_rn(f2w(win.w[k]), ab[o + k], s2);
+                    s1 = __fmaf_rn(win.w[k], cc[o + k], s1);
+                }
+                sAB[r * kMS + j0 + o] = s2;
+                sCh[r * kMS + j0 + o] = s1;
+            }
+        }
+    }
+    else
+    for (int item = threadIdx.x; item < kRH * (kLTW / kRun); item += NT) {
+        const int r = item / (kLTW / kRun), j0 = (item % (kLTW / kRun)) * kRun;
+        // streamed over the staged columns as in pass 1
+        float2 s2[kRun];
+        float s1[kRun];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            s2[o] = make_float2(0.f, 0.f);
+            s1[o] = 0.f;
+        }
+        const float4 *pa4 = reinterpret_cast<const float4 *>(sM + r * kRP + j0);
+        const float4 *pb4 = reinterpret_cast<const float4 *>(sM + kPlane + r * kRP + j0);
+        const float4 *pc4 = reinterpret_cast<const float4 *>(sM + 2 * kPlane + r * kRP + j0);
+#pragma unroll
+        for (int m4 = 0; m4 < 5; ++m4) {
+            const float4 a = pa4[m4], b = pb4[m4], c4 = pc4[m4];
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * m4 + i - kRC;
+                if (k < 0 || k >= kRun + 10) continue;
+                const float2 ab = make_float2(av[i], bv[i]);
+#pragma unroll
+                for (int o = 0; o < kRun; ++o) {
+                    if (k - o < 0 || k - o > 10) continue;
+                    s2[o] = __ffma2_rn(f2w(win.w[k - o]), ab, s2[o]);
+                    s1[o] = __fmaf_rn(win.w[k - o], cv[i], s1[o]);
+                }
+            }
         }
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
-            float2 s2 = make_float2(0.f, 0.f);
-            float s1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                s2 = __ffma2_rn(f2w(win.w[k]), ab[o + k], s2);
-                s1 = __fmaf_rn(win.w[k], cc[o + k], s1);
-            }
-            sAB[r * kMS + j0 + o] = s2;
-            sCh[r * kMS + j0 + o] = s1;
+            sAB[r * kMS + j0 + o] = s2[o];
+            sCh[r * kMS + j0 + o] = s1[o];
         }
     }
     __syncthreads();
