@@ -468,9 +468,11 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     constexpr uint32_t kPer = 4;
     const bool vec = (reinterpret_cast<uintptr_t>(ranges) & 15u) == 0u;
     uint32_t carried = 0;
+    uint32_t c[kPer];  // the last round's counts stay for the tile order (one round: every tile's)
     for (uint32_t r0 = 0; r0 < T; r0 += kTileScanThreads * kPer) {
         const uint32_t t0 = r0 + threadIdx.x * kPer;
-        uint32_t c[kPer] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) c[k] = 0u;
         if (!overflow) {
             if (vec && t0 + kPer <= T) {
                 const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(ranges + 2 * (size_t)t0));
@@ -516,15 +518,15 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     if (!order) return;
     // tiles by decreasing pair count for the blend kernels: a counting sort
     // on kOrderBuckets length classes, the longest class first
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = kOrderBuckets - 1; b >= 0; --b) {
-            const uint32_t c = s_bucket[b];
-            s_bucket[b] = run;
-            run += c;
-        }
-    }
+    desc_class_bases<kOrderBuckets>(s_bucket);
     __syncthreads();
+    if (T <= kTileScanThreads * kPer) {  // one round: the counts are still in registers
+        const uint32_t t0 = threadIdx.x * kPer;
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k)
+            if (t0 + k < T) order[atomicAdd(&s_bucket[order_bucket(overflow ? 0u : c[k])], 1u)] = t0 + k;
+        return;
+    }
     for (uint32_t t = threadIdx.x; t < T; t += kTileScanThreads) {
         const uint2 r = __ldcg(reinterpret_cast<const uint2 *>(ranges) + t);
         order[atomicAdd(&s_bucket[order_bucket(r.y - r.x)], 1u)] = t;

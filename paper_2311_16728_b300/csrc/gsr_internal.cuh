@@ -29,6 +29,36 @@ __device__ __forceinline__ void raise_status(int32_t *d_status, int code) {
     if (d_status) atomicOr(d_status, 1 << code);
 }
 
+// Counting-sort bases of NB classes ordered from the last class down: c[b]
+// <- sum of c[b'] over b' > b, by the first warp of the block (the other
+// threads return at once; the caller synchronises afterwards).
+template <int NB>
+__device__ __forceinline__ void desc_class_bases(uint32_t *c) {
+    if (threadIdx.x >= 32) return;
+    constexpr int K = (NB + 31) / 32;
+    const int lane = (int)threadIdx.x;
+    uint32_t v[K], sum = 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {  // lane l takes the classes NB - 1 - (l K + k)
+        const int r = lane * K + k;
+        v[k] = r < NB ? c[NB - 1 - r] : 0u;
+        sum += v[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int r = lane * K + k;
+        if (r < NB) c[NB - 1 - r] = run;
+        run += v[k];
+    }
+}
+
 // ---------------------------------------------------------------- constants
 constexpr float kNear = 0.2f;        // near plane (reading; the paper names none)
 constexpr float kAlphaMax = 0.99f;   // alpha clamp

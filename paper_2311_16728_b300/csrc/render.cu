@@ -50,21 +50,36 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, const uin
 constexpr int kWorkOrderThreads = 1024, kWorkClasses = 128;
 __global__ void __launch_bounds__(kWorkOrderThreads) work_order_kernel(const uint32_t *__restrict__ work, uint32_t T,
                                                                        uint32_t *__restrict__ order) {
+    constexpr uint32_t kPer = 4;  // tiles a thread keeps in registers between the two passes
     __shared__ uint32_t s_cls[kWorkClasses];
     for (int c = threadIdx.x; c < kWorkClasses; c += kWorkOrderThreads) s_cls[c] = 0u;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
-        atomicAdd(&s_cls[min((work[t] + 7u) >> 3, (uint32_t)kWorkClasses - 1u)], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int c = kWorkClasses - 1; c >= 0; --c) {
-            const uint32_t n = s_cls[c];
-            s_cls[c] = run;
-            run += n;
-        }
+    const bool regs = T <= kWorkOrderThreads * kPer;
+    uint32_t cls[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        const uint32_t t = threadIdx.x + k * kWorkOrderThreads;
+        cls[k] = t < T ? min((__ldg(work + t) + 7u) >> 3, (uint32_t)kWorkClasses - 1u) : 0u;
+    }
+    if (regs) {
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k)
+            if (threadIdx.x + k * kWorkOrderThreads < T) atomicAdd(&s_cls[cls[k]], 1u);
+    } else {
+        for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
+            atomicAdd(&s_cls[min((work[t] + 7u) >> 3, (uint32_t)kWorkClasses - 1u)], 1u);
     }
     __syncthreads();
+    desc_class_bases<kWorkClasses>(s_cls);
+    __syncthreads();
+    if (regs) {
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+            const uint32_t t = threadIdx.x + k * kWorkOrderThreads;
+            if (t < T) order[atomicAdd(&s_cls[cls[k]], 1u)] = t;
+        }
+        return;
+    }
     for (uint32_t t = threadIdx.x; t < T; t += kWorkOrderThreads)
         order[atomicAdd(&s_cls[min((work[t] + 7u) >> 3, (uint32_t)kWorkClasses - 1u)], 1u)] = t;
 }
