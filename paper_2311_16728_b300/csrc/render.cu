@@ -208,7 +208,11 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
     }
     cudaStream_t st = as_cuda(stream);
     const size_t g2bytes = sizeof(float4) * (size_t)n;
-    if (n > 0) {
+    const char *b0 = reinterpret_cast<const char *>(grad2d->g0);
+    if (n > 0 && reinterpret_cast<const char *>(grad2d->g1) == b0 + g2bytes &&
+        reinterpret_cast<const char *>(grad2d->g2) == b0 + 2 * g2bytes) {  // one contiguous block: one memset
+        if (cudaMemsetAsync(grad2d->g0, 0, 3 * g2bytes, st) != cudaSuccess) return check_launch("memset grad2d");
+    } else if (n > 0) {
         if (cudaMemsetAsync(grad2d->g0, 0, g2bytes, st) != cudaSuccess ||
             cudaMemsetAsync(grad2d->g1, 0, g2bytes, st) != cudaSuccess ||
             cudaMemsetAsync(grad2d->g2, 0, g2bytes, st) != cudaSuccess)
