@@ -1409,15 +1409,15 @@ def main():
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     # the captured DRAM traffic is the room scene's in the Morton-ordered
-    # store with 16x16 tiles and the four-pixel backward; the batch depth only
-    # sets how many of a tile's records are staged per shared-memory round,
-    # not which are read, so it applies at every depth.  Other configurations
-    # report none.
+    # store with 16x16 tiles at the default staging (warp-private) and the
+    # four-pixel backward; other configurations report none
     traffic = NCU_TRAFFIC if (args.scene == "room" and args.order == "morton" and
-                              tuple(tile[:2]) == (16, 16) and tile[3] in (0, 64)) else {}
+                              tuple(tile[:2]) == (16, 16) and tile[2] == 0 and tile[3] in (0, 64)) else {}
     stages = stage_rooflines(stage_ms, work, peaks, clk, traffic,
-                             bwd_kernel="render_bwd_q4_kernel" if (tile[:2] == (16, 16) and tile[3] != 128)
-                             else "render_bwd_kernel")
+                             bwd_kernel=("render_bwd_warp_kernel" if tile[2] == 0 else "render_bwd_q4_kernel")
+                             if (tuple(tile[:2]) == (16, 16) and tile[3] != 128) else "render_bwd_kernel",
+                             fwd_kernel="render_fwd_warp_kernel" if (tuple(tile[:2]) == (16, 16) and tile[2] == 0)
+                             else "render_fwd_kernel")
     dom = max(stage_ms, key=stage_ms.get)
     roof = dict(stages[dom])
 
@@ -1482,9 +1482,11 @@ def main():
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload
 # with the current kernels (profiles/mapping_kernels_300k_1200x680.md; the
-# loss stage is its two SSIM passes, the binning stage its seven kernels).
-NCU_TRAFFIC = {"preprocess": 15.456512e6, "bin_sort": 21.096448e6, "render_fwd": 4.531968e6, "loss": 68.919296e6,
-               "blend_bwd": 21.037056e6, "preprocess_bwd": 12.435200e6, "adam": 393.341184e6}
+# loss stage is its two SSIM passes, the binning stage its seven kernels, the
+# backward stage its tile reorder and blend, the Adam stage its step and
+# counter kernels).
+NCU_TRAFFIC = {"preprocess": 15.462e6, "bin_sort": 21.090e6, "render_fwd": 3.987e6, "loss": 68.999e6,
+               "blend_bwd": 21.058e6, "preprocess_bwd": 12.433e6, "adam": 393.420e6}
 # the pose chain (profiles/pose_bwd_300k_1200x680.md)
 NCU_TRAFFIC_POSE = 15.037952e6
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
@@ -1512,7 +1514,8 @@ def sort_passes(tiles: int) -> int:
     return -(-(32 + max(1, (tiles - 1).bit_length())) // 8)
 
 
-def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None, bwd_kernel="render_bwd_q4_kernel"):
+def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None, bwd_kernel="render_bwd_warp_kernel",
+                    fwd_kernel="render_fwd_warp_kernel"):
     """Roofline entry of each stage's dominant kernel: algorithmic work per
     launch (per-unit figure x the units of one launch) / measured stage time,
     against the measured HBM copy bandwidth or the FP32 peak (148 SMs x 128
@@ -1549,7 +1552,7 @@ def stage_rooflines(stage_ms, work, peaks, clk, traffic, tiles=None, bwd_kernel=
                                 f"keys + values 12 B per pair + scan 4 B per Gaussian + {P} radix passes x 24 B per "
                                 f"pair (32 depth + ceil(log2 {T}) tile bits) + ranges 8 B per pair")
         elif st == "render_fwd":
-            out[st] = alu_entry("render_fwd_kernel", FLOPS_PER_BLEND_FWD * E,
+            out[st] = alu_entry(fwd_kernel, FLOPS_PER_BLEND_FWD * E,
                                 f"{FLOPS_PER_BLEND_FWD} FP32 per (pixel, Gaussian) evaluation x blends")
         elif st == "loss":
             out[st] = hbm_entry("ssim kernels", 12 * px,
