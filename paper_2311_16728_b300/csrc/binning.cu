@@ -412,6 +412,9 @@ constexpr uint32_t kLargeTile = 16384;   // longest segment sorted in shared mem
 // length classes of the heavy-first tile order: 16 pairs each, the last open
 constexpr int kOrderBuckets = 64;
 __device__ __forceinline__ int order_bucket(uint32_t n) { return (int)min((n + 15u) >> 4, (uint32_t)kOrderBuckets - 1u); }
+// the warp-sorted segments (1 .. kWarpTile pairs) are whole length classes of
+// that order, the last non-empty ones
+static_assert(kWarpTile % 16 == 0 && kWarpTile / 16 < kOrderBuckets - 1, "warp segments end on a class boundary");
 
 __device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s_warp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -860,6 +863,7 @@ constexpr int kSortGrid = 148 * 8;
 // over the whole grid.
 __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uint32_t *__restrict__ list,
                                                                        const uint32_t *__restrict__ list2,
+                                                                       const uint32_t *__restrict__ order,
                                                                        const uint32_t *__restrict__ list_counts,
                                                                        const uint32_t *__restrict__ ranges,
                                                                        const uint64_t *__restrict__ seg,
@@ -870,6 +874,9 @@ __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uin
     __shared__ uint32_t s_hist[256], s_wcnt[kWarps * 256], s_tmp[9];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t n_warp = list_counts[0], n_block = list_counts[2];
+    // with the heavy-first tile order, the warp segments (1 .. kWarpTile
+    // pairs) are its entries after the longer segments: the longest go first
+    if (order) list = order + list_counts[1] + list_counts[2];
     for (uint32_t e = blockIdx.x * kWarps + wid; e < n_warp; e += gridDim.x * kWarps) {
         const uint32_t t = list[e];
         const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
@@ -1113,8 +1120,8 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
                                                       proj->tile_order);
     if (pair_capacity == 0) return check_launch("tile_scan_kernel");
     scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_ts, kept_sk, d_written, pair_capacity, tile_ranges, seg);
-    sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list2, list_counts, tile_ranges, seg, keys,
-                                                                 vals);
+    sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list2, proj->tile_order, list_counts,
+                                                                 tile_ranges, seg, keys, vals);
     const size_t big = sizeof(uint64_t) * kLargeTile + sizeof(uint32_t) * (kLargeSortThreads / 32) * 256;
     static_assert(sizeof(uint64_t) * kLargeTile >= sizeof(uint32_t) * (kLargeSortThreads / 32) * kRadix,
                   "the long-segment sort reuses the shared array for its per-warp counts");
