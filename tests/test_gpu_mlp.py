@@ -156,7 +156,7 @@ def test_training_gradients_and_adam_match_oracle(M):
               f"{float((err / (envelope[k] + 1e-300)).max()):.3f}), {100 * within:.1f} % within 1e-3 relative")
         if not (err <= bounds[k]).all():
             bad = np.argwhere(err > bounds[k])
-            for ix in bad[np.argsort(-(err / bounds[k])[err > bounds[k]])][:4]:
+            for ix in bad[np.argsort(-(err / (bounds[k] + 1e-300))[err > bounds[k]])][:4]:
                 ix = tuple(int(v) for v in ix)
                 info = f"    {k}{ix}: g {g[k][ix]:.6e} g* {g_ref[k][ix]:.6e} err {err[ix]:.2e} bound {bounds[k][ix]:.2e}"
                 if k in ("W2", "W3"):
