@@ -140,8 +140,9 @@ typedef struct {
  *                     the view are skipped); set it only with buffers that
  *                     gsr_bin_sort filled for the same camera and tiling.
  *   tile_work u32     optional (NULL: not used; needs tile_order), one entry
- *                     per tile: gsr_render_fwd writes each tile's largest
- *                     n_contrib (how deep into its list the backward walks),
+ *                     per tile: gsr_bin_sort zeroes it and gsr_render_fwd
+ *                     raises each entry to the tile's largest n_contrib (how
+ *                     deep into its list the backward walks),
  *                     and gsr_blend_bwd / gsr_render_bwd first reorder
  *                     tile_order by it, deepest first, for their own launch.
  * Records of culled Gaussians (ntiles == 0) are left unwritten. */

@@ -445,11 +445,12 @@ __device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t v, uint32_t *s
 // empty tile.  Non-empty tiles are listed for the sort by length: up to
 // kWarpTile from the front of `list`, up to kSmallTile in `list2`, longer
 // ones from the back of `list`.  On pair overflow every range is empty.
+// tile_work (may be NULL) is zeroed for the forward blend to raise.
 __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     uint32_t *__restrict__ ranges, uint32_t T, const unsigned long long *__restrict__ d_kept, int64_t cap,
     uint32_t *__restrict__ list, uint32_t *__restrict__ list2, uint32_t *__restrict__ list_counts,
     int64_t *__restrict__ d_written, int64_t *__restrict__ d_num_pairs, int32_t *__restrict__ d_status,
-    uint32_t *__restrict__ order) {
+    uint32_t *__restrict__ order, uint32_t *__restrict__ tile_work) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_small, s_large, s_mid;
     __shared__ uint32_t s_bucket[kOrderBuckets];
@@ -501,6 +502,7 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
             const uint32_t n = c[k];
             ranges[2 * (size_t)t] = n ? off : 0u;
             ranges[2 * (size_t)t + 1] = n ? off + n : 0u;
+            if (tile_work) tile_work[t] = 0u;  // raised by the forward blend
             if (n) {
                 if (n <= kWarpTile) list[atomicAdd(&s_small, 1u)] = t;
                 else if (n <= kSmallTile) list2[atomicAdd(&s_mid, 1u)] = t;
@@ -1117,7 +1119,7 @@ int32_t bin_sort_impl(const gsr_proj *proj, int64_t n, const ViewTiles &vt, int6
     // 4-6. ranges, scatter into tile segments, sort each segment
     tile_scan_kernel<<<1, kTileScanThreads, 0, st>>>(tile_ranges, (uint32_t)tiles, d_kept, pair_capacity, list,
                                                       list2, list_counts, d_written, d_num_pairs, d_status,
-                                                      proj->tile_order);
+                                                      proj->tile_order, proj->tile_order ? proj->tile_work : nullptr);
     if (pair_capacity == 0) return check_launch("tile_scan_kernel");
     scatter_kernel<<<kSortGrid, 256, 0, st>>>(kept_ts, kept_sk, d_written, pair_capacity, tile_ranges, seg);
     sort_small_kernel<<<kSortGrid, kSmallSortThreads, 0, st>>>(list, list2, proj->tile_order, list_counts,

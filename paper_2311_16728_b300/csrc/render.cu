@@ -109,30 +109,41 @@ __global__ void __launch_bounds__(kQ4Threads) render_bwd_q4_kernel(RenderArgs a,
     render_bwd_tile_q4<false, true>(a, tile, T_final, n_contrib, dL_dimg, g0, g1, g2, smem);
 }
 
-// 16 x 16 tiles with warp-private staging (render_warp.cuh)
-template <bool kCount>
-__global__ void __launch_bounds__(kWarpFwdThreads) render_fwd_warp_kernel(RenderArgs a, const uint32_t *__restrict__ order,
-                                                                        float *__restrict__ img,
-                                                                        float *__restrict__ T_final,
-                                                                        uint32_t *__restrict__ n_contrib,
-                                                                        uint32_t *__restrict__ n_blended,
-                                                                        uint32_t *__restrict__ tile_work) {
-    __shared__ Staged s_buf[kWarpFwdThreads];  // 32 records per warp
-    const int tile = cta_tile(order);
-    if (tile < 0) return;
-    render_fwd_tile_warp<kCount>(a, tile, img, T_final, n_contrib, n_blended, s_buf, tile_work);
+// 16 x 16 tiles with warp-private staging (render_warp.cuh), one warp per
+// CTA: CTA b renders warp part b % P of tile order[b / P] (P = 4 quadrants
+// forward, 2 halves backward), so the parts of the heaviest tiles start first.
+__device__ __forceinline__ int cta_tile_part(const uint32_t *__restrict__ order, int parts, int &part) {
+    const int b = (int)blockIdx.x / parts, nt = (int)gridDim.x / parts;
+    part = (int)blockIdx.x - b * parts;
+    if (!order) return b;
+    const uint32_t t = __ldg(order + b);
+    return t < (uint32_t)nt ? (int)t : -1;
 }
 
-__global__ void __launch_bounds__(kWarpBwdThreads) render_bwd_warp_kernel(RenderArgs a, const uint32_t *__restrict__ order,
-                                                                        const float *__restrict__ T_final,
-                                                                        const uint32_t *__restrict__ n_contrib,
-                                                                        const float *__restrict__ dL_dimg,
-                                                                        float *__restrict__ g0, float *__restrict__ g1,
-                                                                        float *__restrict__ g2) {
-    __shared__ Staged s_buf[kWarpBwdThreads];  // 32 records per warp
-    const int tile = cta_tile(order);
+template <bool kCount>
+__global__ void __launch_bounds__(32) render_fwd_warp_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                             float *__restrict__ img, float *__restrict__ T_final,
+                                                             uint32_t *__restrict__ n_contrib,
+                                                             uint32_t *__restrict__ n_blended,
+                                                             uint32_t *__restrict__ tile_work) {
+    __shared__ Staged s_buf[32];
+    int part;
+    const int tile = cta_tile_part(order, 4, part);
     if (tile < 0) return;
-    render_bwd_tile_warp(a, tile, T_final, n_contrib, dL_dimg, g0, g1, g2, s_buf);
+    render_fwd_quadrant<kCount>(a, tile, part, img, T_final, n_contrib, n_blended, s_buf, tile_work);
+}
+
+__global__ void __launch_bounds__(32) render_bwd_warp_kernel(RenderArgs a, const uint32_t *__restrict__ order,
+                                                             const float *__restrict__ T_final,
+                                                             const uint32_t *__restrict__ n_contrib,
+                                                             const float *__restrict__ dL_dimg,
+                                                             float *__restrict__ g0, float *__restrict__ g1,
+                                                             float *__restrict__ g2) {
+    __shared__ Staged s_buf[32];
+    int part;
+    const int tile = cta_tile_part(order, 2, part);
+    if (tile < 0) return;
+    render_bwd_tile_warp(a, tile, part, T_final, n_contrib, dL_dimg, g0, g1, g2, s_buf);
 }
 
 static RenderArgs make_args(const gsr_proj *proj, const uint32_t *vals, const uint32_t *ranges,
@@ -178,8 +189,8 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
     if (quad && a.depth == 0) {  // warp-private staging (the default for 16 x 16 tiles)
         auto wk = n_blended ? render_fwd_warp_kernel<true> : render_fwd_warp_kernel<false>;
-        wk<<<tiles, kWarpFwdThreads, 0, as_cuda(stream)>>>(a, proj->tile_order, img, T_final, n_contrib, n_blended,
-                                                           proj->tile_order ? proj->tile_work : nullptr);
+        wk<<<4 * tiles, 32, 0, as_cuda(stream)>>>(a, proj->tile_order, img, T_final, n_contrib, n_blended,
+                                                  proj->tile_order ? proj->tile_work : nullptr);
         return check_launch("render_fwd_warp_kernel");
     }
     auto kernel = n_blended ? (quad ? render_fwd_kernel<true, true> : render_fwd_kernel<true, false>)
@@ -227,8 +238,8 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
         if ((rc = check_launch("work_order_kernel"))) return rc;
     }
     if (quad && tiling->bwd_threads != nthr && a.depth == 0) {  // warp-private staging, four pixels a thread
-        render_bwd_warp_kernel<<<tiles, kWarpBwdThreads, 0, st>>>(a, proj->tile_order, T_final, n_contrib, dL_dimg,
-                                                                  grad2d->g0, grad2d->g1, grad2d->g2);
+        render_bwd_warp_kernel<<<2 * tiles, 32, 0, st>>>(a, proj->tile_order, T_final, n_contrib, dL_dimg,
+                                                         grad2d->g0, grad2d->g1, grad2d->g2);
         return check_launch("render_bwd_warp_kernel");
     }
     if (quad && tiling->bwd_threads != nthr) {  // 64 threads, four pixels each, block-staged batches

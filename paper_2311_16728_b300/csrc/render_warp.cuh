@@ -15,15 +15,17 @@
 // routines' (render_impl.cuh, render_q4.cuh), so the image, T_final and
 // n_contrib are bit-identical to theirs.
 //
-// Forward: 128 threads, warp w an 8 x 8 quadrant, two pixels a lane.
-// Backward: 64 threads, warp w rows 8 w .. 8 w + 7, four pixels a lane.
+// Forward: warp w an 8 x 8 quadrant, two pixels a lane; backward: warp w
+// rows 8 w .. 8 w + 7, four pixels a lane.  The one-view kernels run every
+// warp as a CTA of its own, so a warp that finishes early frees its slot for
+// another tile's warp at once.
 #pragma once
 
 #include "render_q4.cuh"
 
 namespace gsr {
 
-constexpr int kWarpFwdThreads = 128, kWarpBwdThreads = 64;
+constexpr int kWarpFwdThreads = 128, kWarpBwdThreads = 64;  // threads of a tile
 
 // Whether the warp whose pixels span [rx0, rx1] x [ry0, ry1] can see the
 // splat at all (the test stage_splat applies per warp); x0, x1, y0, y1
@@ -65,17 +67,19 @@ __device__ __forceinline__ void warp_stage(const RenderArgs &a, uint32_t gid, ui
 }
 
 // ---------------------------------------------------------------- K5
+// Quadrant `wid` of the tile, by one warp with its 32-record buffer `buf`;
+// tile_work (may be NULL): raised (atomic max) to the quadrant's largest
+// n_contrib.
 template <bool kCount>
-__device__ __forceinline__ void render_fwd_tile_warp(const RenderArgs &a, int tile, float *__restrict__ img,
-                                                     float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
-                                                     uint32_t *__restrict__ n_blended, Staged *s_buf,
-                                                     uint32_t *__restrict__ tile_work) {
-    int px, py0, ox, oy;
-    thread_pixels(a, tile, px, py0, ox, oy);  // quadrant warps
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__device__ __forceinline__ void render_fwd_quadrant(const RenderArgs &a, int tile, int wid, float *__restrict__ img,
+                                                    float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
+                                                    uint32_t *__restrict__ n_blended, Staged *buf,
+                                                    uint32_t *__restrict__ tile_work) {
+    const int lane = threadIdx.x & 31;
+    const int ox = (tile % a.gx) * a.tw, oy = (tile / a.gx) * a.th;
+    const int px = ox + 8 * (wid & 1) + (lane & 7), py0 = oy + 8 * (wid >> 1) + 2 * (lane >> 3);
     int rx0, rx1, ry0, ry1;
     warp_rect(a, wid, ox, oy, rx0, rx1, ry0, ry1);
-    Staged *buf = s_buf + 32 * wid;
     const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py0 + 1 < a.H;
     const uint2 rg = a.ranges[a.tile_off + tile];
     const int begin = (int)rg.x, end = (int)rg.y;
@@ -143,30 +147,36 @@ __device__ __forceinline__ void render_fwd_tile_warp(const RenderArgs &a, int ti
         n_contrib[pix] = p.last1;
         if (kCount) n_blended[pix] = p.nb1;
     }
-    if (tile_work) {  // the tile's largest n_contrib: one barrier, after every warp's loop
-        __shared__ uint32_t s_work;
-        if (threadIdx.x == 0) s_work = 0u;
-        __syncthreads();
+    if (tile_work) {
         const uint32_t mx = __reduce_max_sync(0xffffffffu, max(p.last0, p.last1));
-        if (lane == 0) atomicMax(&s_work, mx);
-        __syncthreads();
-        if (threadIdx.x == 0) tile_work[tile] = s_work;
+        if (lane == 0 && mx) atomicMax(&tile_work[tile], mx);
     }
+}
+
+// The whole tile by a CTA of four warps (warp w: quadrant w).
+template <bool kCount>
+__device__ __forceinline__ void render_fwd_tile_warp(const RenderArgs &a, int tile, float *__restrict__ img,
+                                                     float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
+                                                     uint32_t *__restrict__ n_blended, Staged *s_buf,
+                                                     uint32_t *__restrict__ tile_work) {
+    const int wid = threadIdx.x >> 5;
+    render_fwd_quadrant<kCount>(a, tile, wid, img, T_final, n_contrib, n_blended, s_buf + 32 * wid, tile_work);
 }
 
 // ---------------------------------------------------------------- K7
 // Back to front from the warp's own largest n_contrib; per visible splat the
 // arithmetic of render_bwd_tile_q4 (q4_splat_bwd).
-__device__ __forceinline__ void render_bwd_tile_warp(const RenderArgs &a, int tile, const float *__restrict__ T_final,
+// Half `wid` (rows 8 wid .. 8 wid + 7) of the tile, by one warp with its
+// 32-record buffer `buf`.
+__device__ __forceinline__ void render_bwd_tile_warp(const RenderArgs &a, int tile, int wid,
+                                                     const float *__restrict__ T_final,
                                                      const uint32_t *__restrict__ n_contrib,
                                                      const float *__restrict__ dL_dimg, float *__restrict__ g0,
-                                                     float *__restrict__ g1, float *__restrict__ g2, Staged *s_buf) {
-    const int ti = (int)threadIdx.x;
+                                                     float *__restrict__ g1, float *__restrict__ g2, Staged *buf) {
+    const int lane = (int)(threadIdx.x & 31u), ti = 32 * wid + lane;
     int px, py0, ox, oy;
     q4_pixels(a, tile, ti, px, py0, ox, oy);
-    const int lane = ti & 31, wid = ti >> 5;
     const int rx0 = ox, rx1 = ox + 15, ry0 = oy + 8 * wid, ry1 = ry0 + 7;
-    Staged *buf = s_buf + 32 * wid;
     const uint2 rg = a.ranges[a.tile_off + tile];
     const int begin = (int)rg.x;
     const int64_t plane = (int64_t)a.W * a.H;
@@ -234,7 +244,7 @@ __device__ __forceinline__ void render_bwd_tile_warp(const RenderArgs &a, int ti
     }
 }
 
-// shared memory of the warp-staged kernels: 32 records per warp
+// shared memory of warp-staged tiles: 32 records per warp
 __host__ __device__ inline size_t render_warp_smem(int threads) { return sizeof(Staged) * 32 * (threads / 32); }
 
 }  // namespace gsr
