@@ -99,9 +99,9 @@ typedef struct {
  *    multiple of 32, tile_w * tile_h a multiple of 64 and at most 1024.
  *  - batch_depth: depth-ordered records staged in shared memory per round by
  *    the blend kernels, a multiple of 32 up to 512, for the whole tile; 0 =
- *    each kernel's default: for 16 x 16 tiles the one-view blends and the
- *    batched window's forward let every warp stage its own 32 records a
- *    round (only those it can see, no barrier between the warps of a tile);
+ *    each kernel's default: for 16 x 16 tiles every warp of the blends (one
+ *    view or the batched window) stages its own 32 records a round (only
+ *    those it can see; no barrier ties the warps of a tile together);
  *    elsewhere one record per thread.
  *  - bwd_threads: threads per tile of the backward blend; 0 = the default
  *    (64, four pixels a thread, for 16 x 16 tiles; tile_w * tile_h / 2

@@ -275,16 +275,32 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
     const unsigned nb = gridDim.x;
     phase_stamp(a.sync, 0);
     // ---- phase 1: forward blend of every (view, tile)
-    for (int it = next_item(a.sync + 0, &s_item); it < a.tiles_total; it = next_item(a.sync + 0, &s_item)) {
-        const int t = ordered_tile(a, it);
-        if (t < 0) continue;
-        const int v = view_of_tile(a, t);
-        const IterView &w = a.view[v];
-        if (kQuad && a.depth == 0)  // each warp stages for itself (render_warp.cuh)
-            render_fwd_tile_warp<false>(view_args(a, w), t - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr,
-                                        reinterpret_cast<Staged *>(smem4), nullptr);
-        else
+    if (kQuad && a.depth == 0) {
+        // every warp takes its own items, one 8 x 8 quadrant of a tile each
+        // (render_warp.cuh: it stages for itself), so no CTA barrier ties
+        // four quadrants of unequal work together
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        Staged *buf = reinterpret_cast<Staged *>(smem4) + 32 * wid;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = (int)atomicAdd(a.sync + 0, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= 4 * a.tiles_total) break;
+            const int t = ordered_tile(a, it >> 2);
+            if (t < 0) continue;
+            const int v = view_of_tile(a, t);
+            const IterView &w = a.view[v];
+            render_fwd_quadrant<false>(view_args(a, w), t - w.tile_off, it & 3, w.img, w.T_final, w.n_contrib,
+                                       nullptr, buf, nullptr);
+        }
+    } else {
+        for (int it = next_item(a.sync + 0, &s_item); it < a.tiles_total; it = next_item(a.sync + 0, &s_item)) {
+            const int t = ordered_tile(a, it);
+            if (t < 0) continue;
+            const int v = view_of_tile(a, t);
+            const IterView &w = a.view[v];
             render_fwd_tile<kQuad>(view_args(a, w), t - w.tile_off, w.img, w.T_final, w.n_contrib, nullptr, smem4);
+        }
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
     phase_stamp(a.sync, 1);
@@ -316,9 +332,27 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
     }
     if (!grid_barrier(a.sync, nb, a.d_status, &s_ok)) return;
     phase_stamp(a.sync, 3);
-    // ---- phase 4: backward blend of every (view, tile); 16 x 16 tiles run two
-    // at a time, one per 64-thread half of the CTA (four pixels per thread)
-    if constexpr (kQ4) {
+    // ---- phase 4: backward blend of every (view, tile); 16 x 16 tiles run at
+    // four pixels per thread, as per-warp halves (default staging) or two
+    // tiles at a time, one per 64-thread half of the CTA (staging depths)
+    if (kQ4 && a.depth == 0) {
+        // every warp takes its own items, one 16 x 8 half of a tile each,
+        // staging for itself (render_warp.cuh)
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        Staged *buf = reinterpret_cast<Staged *>(smem4) + 32 * wid;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = (int)atomicAdd(a.sync + 3, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= 2 * a.tiles_total) break;
+            const int t = ordered_tile(a, it >> 1);
+            if (t < 0) continue;
+            const int v = view_of_tile(a, t);
+            const IterView &w = a.view[v];
+            render_bwd_tile_warp(view_args(a, w), t - w.tile_off, it & 1, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
+                                 a.g2, buf);
+        }
+    } else if constexpr (kQ4) {
         const int half = (int)(threadIdx.x >> 6);
         float4 *sm = smem4 + half * (render_q4_smem(a.depth > 0 ? a.depth : kQ4Threads) / sizeof(float4));
         for (int it = next_item_half(a.sync + 3, &s_item2[half]); it < a.tiles_total;
@@ -327,7 +361,6 @@ __global__ void __launch_bounds__(kIterThreads, 5) batched_iterate_kernel(const 
             if (t < 0) continue;
             const int v = view_of_tile(a, t);
             const IterView &w = a.view[v];
-            // (block-staged: warp-private staging measured slower in this phase)
             render_bwd_tile_q4<true>(view_args(a, w), t - w.tile_off, w.T_final, w.n_contrib, w.dimg, a.g0, a.g1,
                                      a.g2, sm);
         }
