@@ -1490,7 +1490,7 @@ NCU_TRAFFIC = {"preprocess": 15.462e6, "bin_sort": 21.090e6, "render_fwd": 3.987
 # the pose chain (profiles/pose_bwd_300k_1200x680.md)
 NCU_TRAFFIC_POSE = 15.037952e6
 # the persistent window kernel (profiles/window_kernels_500k_8x640x480x3.md)
-NCU_TRAFFIC_WINDOW_ITERATE = 596.922e6
+NCU_TRAFFIC_WINDOW_ITERATE = 597.489e6
 
 # Algorithmic work per unit (the hot-path scope table's measurement figures;
 # the implementation's own DRAM bytes are the ncu `traffic` above, never the
