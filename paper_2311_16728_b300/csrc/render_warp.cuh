@@ -28,8 +28,13 @@ namespace gsr {
 constexpr int kWarpFwdThreads = 128, kWarpBwdThreads = 64;  // threads of a tile
 
 // Whether the warp whose pixels span [rx0, rx1] x [ry0, ry1] can see the
-// splat at all (the test stage_splat applies per warp); x0, x1, y0, y1
-// receive its pixel box once the alpha test has passed.
+// splat at all: the pixel box against the rectangle, then the minimum of the
+// quadratic form over their overlap against the alpha threshold (the test
+// stage_splat applies per warp, without its prefilter on the alpha
+// ellipse's bounding box, which the minimum implies: the two square roots
+// and divisions cost more per staged record than the records it drops
+// earlier); x0, x1, y0, y1 receive its pixel box once the alpha test has
+// passed.
 __device__ __forceinline__ bool warp_may_see(const float4 g, const float4 c, int rx0, int rx1, int ry0, int ry1,
                                              int &x0, int &x1, int &y0, int &y1) {
     const float A = g.z, B = g.w, C = c.x, op = c.y;
@@ -41,14 +46,7 @@ __device__ __forceinline__ bool warp_may_see(const float4 g, const float4 c, int
     y0 = (int)(by & 0xffffu);
     y1 = (int)(by >> 16);
     if (!(x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0)) return false;
-    const float bb = B * B;
-    const float det = __fmaf_rn(A, C, -bb) + __fmaf_rn(-B, B, bb);
-    const float ex = sqrtf(tau * C / det) * 1.001f + 0.01f;
-    const float ey = sqrtf(tau * A / det) * 1.001f + 0.01f;
-    const float cx = fminf(fmaxf(g.x, (float)rx0), (float)rx1);
-    const float cy = fminf(fmaxf(g.y, (float)ry0), (float)ry1);
-    return fabsf(cx - g.x) <= ex && fabsf(cy - g.y) <= ey &&
-           rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1), (float)max(ry0, y0),
+    return rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1), (float)max(ry0, y0),
                         (float)min(ry1, y1));
 }
 
