@@ -683,13 +683,22 @@ __device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[E], uint32_t lane, 
     }
 }
 
+// The warp's transpose buffer: entry i at word i + i / 32, so that both the
+// lane-major writes (entry E lane + e, any E <= 16) and the row reads (entry
+// 32 e + lane) hit 32 distinct banks.
+constexpr uint32_t kTransposeWords = kWarpTile + kWarpTile / 32;
+__device__ __forceinline__ uint32_t transpose_word(uint32_t i) { return i + (i >> 5); }
+
 // Tile t's segment seg[b, b + L) (L <= 32 E) sorted by one warp in
-// registers and emitted: loaded coalesced (the input order is free), stored
-// from the lane-major sorted order.
+// registers and emitted: loaded coalesced (the input order is free); the
+// lane-major sorted order goes through the warp's shared buffer `tr`
+// (kTransposeWords words), the depth halves and then the index halves, so
+// that every store of keys and vals covers 32 consecutive entries.
 template <int E>
 __device__ __forceinline__ void warp_tile_sort(const uint64_t *__restrict__ seg, uint32_t t, uint32_t b, uint32_t L,
                                                uint32_t P, uint32_t lane, uint64_t *__restrict__ keys,
-                                               uint32_t *__restrict__ vals) {
+                                               uint32_t *__restrict__ vals, uint32_t *tr) {
+    static_assert(32 * E <= (int)kWarpTile, "a warp segment fits the transpose buffer");
     uint64_t v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -698,12 +707,21 @@ __device__ __forceinline__ void warp_tile_sort(const uint64_t *__restrict__ seg,
     }
     warp_sort_regs<E>(v, lane, P);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const uint32_t i = (uint32_t)E * lane + e;
-        if (i < L) {
-            keys[b + i] = ((uint64_t)t << 32) | (v[e] >> 32);
-            vals[b + i] = (uint32_t)v[e];
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            tr[transpose_word((uint32_t)E * lane + e)] = half ? (uint32_t)v[e] : (uint32_t)(v[e] >> 32);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t i = 32u * e + lane;
+            if (i < L) {
+                const uint32_t w = tr[transpose_word(i)];
+                if (half) vals[b + i] = w;
+                else keys[b + i] = ((uint64_t)t << 32) | w;
+            }
         }
+        __syncwarp();  // the buffer is free again
     }
 }
 
@@ -872,9 +890,16 @@ __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uin
                                                                        uint64_t *__restrict__ keys,
                                                                        uint32_t *__restrict__ vals) {
     constexpr int kWarps = kSmallSortThreads / 32;
-    __shared__ uint64_t s_a[kSmallTile], s_b[kSmallTile];
-    __shared__ uint32_t s_hist[256], s_wcnt[kWarps * 256], s_tmp[9];
+    // the warps' transpose buffers share the block sort's arrays: the block
+    // segments start after a barrier that ends every warp segment
+    constexpr size_t kBlockBytes = sizeof(uint64_t) * 2 * kSmallTile + sizeof(uint32_t) * (1 + kWarps) * 256;
+    static_assert(sizeof(uint32_t) * kWarps * kTransposeWords <= kBlockBytes, "transpose buffers fit");
+    __shared__ __align__(16) unsigned char s_raw[kBlockBytes];
+    __shared__ uint32_t s_tmp[9];
+    uint64_t *const s_a = reinterpret_cast<uint64_t *>(s_raw), *const s_b = s_a + kSmallTile;
+    uint32_t *const s_hist = reinterpret_cast<uint32_t *>(s_b + kSmallTile), *const s_wcnt = s_hist + 256;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t *const s_tr = reinterpret_cast<uint32_t *>(s_raw) + wid * kTransposeWords;
     const uint32_t n_warp = list_counts[0], n_block = list_counts[2];
     // with the heavy-first tile order, the warp segments (1 .. kWarpTile
     // pairs) are its entries after the longer segments: the longest go first
@@ -885,12 +910,13 @@ __global__ void __launch_bounds__(kSmallSortThreads) sort_small_kernel(const uin
         uint32_t P = 1;
         while (P < L) P <<= 1;
         // E = P / 32 entries a lane (at least one)
-        if (P <= 32) warp_tile_sort<1>(seg, t, b, L, P, lane, keys, vals);
-        else if (P <= 64) warp_tile_sort<2>(seg, t, b, L, P, lane, keys, vals);
-        else if (P <= 128) warp_tile_sort<4>(seg, t, b, L, P, lane, keys, vals);
-        else if (P <= 256) warp_tile_sort<8>(seg, t, b, L, P, lane, keys, vals);
-        else warp_tile_sort<16>(seg, t, b, L, P, lane, keys, vals);
+        if (P <= 32) warp_tile_sort<1>(seg, t, b, L, P, lane, keys, vals, s_tr);
+        else if (P <= 64) warp_tile_sort<2>(seg, t, b, L, P, lane, keys, vals, s_tr);
+        else if (P <= 128) warp_tile_sort<4>(seg, t, b, L, P, lane, keys, vals, s_tr);
+        else if (P <= 256) warp_tile_sort<8>(seg, t, b, L, P, lane, keys, vals, s_tr);
+        else warp_tile_sort<16>(seg, t, b, L, P, lane, keys, vals, s_tr);
     }
+    if (blockIdx.x < n_block) __syncthreads();  // the transpose buffers are free
     for (uint32_t e = blockIdx.x; e < n_block; e += gridDim.x) {
         const uint32_t t = list2[e];
         const uint32_t b = ranges[2 * (size_t)t], L = ranges[2 * (size_t)t + 1] - b;
