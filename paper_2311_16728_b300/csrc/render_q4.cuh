@@ -126,7 +126,9 @@ struct PairBwd {
 // lane masks lm) to this thread's four pixels and, reduced over the warp, to
 // the splat's screen-space gradient: the pixels' alphas a pair at a time,
 // their back-to-front updates, and the warp's transposed reduction with its
-// atomics into g0 / g1 (lane 4k: value k at gk) and g2.
+// atomics into g0 / g1 (lane 4k: value k at gk) and g2.  kPosTest false:
+// the caller knows pos lies below every one of the thread's n_contrib.
+template <bool kPosTest = true>
 __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, const uint4 lm, int lane, float fpx,
                                              const float2 (&fpy)[2], const uint32_t (&last)[4], PairBwd (&p)[2],
                                              float *gk, float *__restrict__ g2) {
@@ -147,10 +149,10 @@ __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, con
         al[h] = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
         cl[2 * h] = raw.x > kAlphaMax;
         cl[2 * h + 1] = raw.y > kAlphaMax;
-        ok[2 * h] = pos < last[2 * h] && ((q4_lane_bits(lm, 2 * h) >> lane) & 1u) && e.x <= 0.0f &&
+        ok[2 * h] = (!kPosTest || pos < last[2 * h]) && ((q4_lane_bits(lm, 2 * h) >> lane) & 1u) && e.x <= 0.0f &&
                     al[h].x >= kAlphaMin;
-        ok[2 * h + 1] = pos < last[2 * h + 1] && ((q4_lane_bits(lm, 2 * h + 1) >> lane) & 1u) && e.y <= 0.0f &&
-                        al[h].y >= kAlphaMin;
+        ok[2 * h + 1] = (!kPosTest || pos < last[2 * h + 1]) && ((q4_lane_bits(lm, 2 * h + 1) >> lane) & 1u) &&
+                        e.y <= 0.0f && al[h].y >= kAlphaMin;
         any = any || ok[2 * h] || ok[2 * h + 1];
     }
     // v2[0 .. 2]: the lane's dpow-weighted moments in dy (sum dpow,

@@ -234,9 +234,18 @@ __device__ __forceinline__ void render_bwd_tile_warp(const RenderArgs &a, int ti
             warp_stage(a, gid, (uint32_t)(idx - begin), g, c, q4_box_lanes(x0, x1, y0, y1, ox, ry0),
                        buf[__popc(bits & ((1u << lane) - 1u))]);
         __syncwarp();
-        for (int j = __popc(bits) - 1; j >= 0; --j) {  // back to front
-            const Staged &sj = buf[j];
-            q4_splat_bwd(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+        // every position of the round below every pixel's n_contrib: no
+        // per-splat position test
+        if (__all_sync(0xffffffffu, min(min(last[0], last[1]), min(last[2], last[3])) >= (uint32_t)(bend - begin))) {
+            for (int j = __popc(bits) - 1; j >= 0; --j) {  // back to front
+                const Staged &sj = buf[j];
+                q4_splat_bwd<false>(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+            }
+        } else {
+            for (int j = __popc(bits) - 1; j >= 0; --j) {
+                const Staged &sj = buf[j];
+                q4_splat_bwd(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+            }
         }
         __syncwarp();
     }
