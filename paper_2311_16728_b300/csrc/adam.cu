@@ -39,6 +39,7 @@ __device__ __forceinline__ float adam_delta(float lr, float m, float v, float ib
 
 __global__ void __launch_bounds__(kAdamThreads) adam_kernel(AdamK a, const int32_t *__restrict__ d_step,
                                                             const uint32_t *__restrict__ touched) {
+    chain_enter();
     __shared__ float s_bc[2];
     if (threadIdx.x == 0) {
         const int t = *d_step + 1;
@@ -92,7 +93,10 @@ __global__ void __launch_bounds__(kAdamThreads) adam_kernel(AdamK a, const int32
     }
 }
 
-__global__ void step_advance_kernel(int32_t *d_step) { *d_step += 1; }
+__global__ void step_advance_kernel(int32_t *d_step) {
+    chain_enter();
+    *d_step += 1;
+}
 
 __device__ __forceinline__ int reflect101(int i, int n) {
     if (n == 1) return 0;
@@ -162,10 +166,10 @@ static int32_t adam_step(const gsr_param_buffers *params, const gsr_param_buffer
         a.lr_mean = cfg->lr_mean; a.lr_opacity = cfg->lr_opacity; a.lr_quat = cfg->lr_quat;
         a.lr_scale = cfg->lr_scale; a.lr_sh = cfg->lr_sh;
         a.b1 = cfg->beta1; a.b2 = cfg->beta2; a.eps = cfg->eps;
-        adam_kernel<<<dim3((unsigned)((n + kAdamThreads * kAdamPer - 1) / (kAdamThreads * kAdamPer)), 15),
-                      kAdamThreads, 0, st>>>(a, d_step, touched);
+        launch_chained(adam_kernel, dim3((unsigned)((n + kAdamThreads * kAdamPer - 1) / (kAdamThreads * kAdamPer)), 15),
+                       dim3(kAdamThreads), 0, st, a, d_step, touched);
     }
-    step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+    launch_chained(step_advance_kernel, dim3(1), dim3(1), 0, st, d_step);
     return check_launch("adam_kernel");
 }
 

@@ -24,6 +24,40 @@ int32_t validate_tiling(const gsr_tiling *t);
 inline int grid_x(const gsr_camera *c, const gsr_tiling *t) { return (c->width + t->tile_w - 1) / t->tile_w; }
 inline int grid_y(const gsr_camera *c, const gsr_tiling *t) { return (c->height + t->tile_h - 1) / t->tile_h; }
 
+// ---------------------------------------------------------------- chained launches
+// The kernels of one mapping iteration run back to back on one stream.  A
+// kernel launched by launch_chained may be scheduled while the kernel before
+// it in the stream is still finishing (programmatic dependent launch): its
+// CTAs take SM slots that the predecessor's last wave leaves free and get
+// through their launch before the predecessor has ended.  Every such kernel
+// calls chain_enter() first, before it touches global memory:
+// griddepcontrol.wait returns once every grid it depends on has completed
+// and its memory operations are visible (at once when the kernel was
+// launched without the attribute, or after a non-kernel node), so what the
+// kernel computes is what a plainly serialised launch computes.  chain_enter
+// then lets the next chained kernel be scheduled (griddepcontrol.
+// launch_dependents); that kernel in turn waits for this one to complete.
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_chained(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  A &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // status bit set by kernels in the caller's device status word
 __device__ __forceinline__ void raise_status(int32_t *d_status, int code) {
     if (d_status) atomicOr(d_status, 1 << code);

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kLThreads, kTma ? 5 : 1) ssim_pass1_kernel(con
                                                                float *__restrict__ partials,
                                                                const __grid_constant__ CUtensorMap tx,
                                                                const __grid_constant__ CUtensorMap ty) {
+    chain_enter();
     extern __shared__ __align__(128) float sm[];
     __shared__ float s_red[32];
     __shared__ uint64_t s_bar;
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(kLThreads, 5) ssim_pass2_kernel(const float *_
                                                                const __grid_constant__ CUtensorMap ta,
                                                                const __grid_constant__ CUtensorMap tb,
                                                                const __grid_constant__ CUtensorMap tc) {
+    chain_enter();
     extern __shared__ __align__(128) float sm[];
     __shared__ double s_dbl[2 * kLThreads];
     __shared__ uint64_t s_bar;
@@ -97,9 +99,9 @@ static void launch_ssim(const float *img, const float *gt, int C, int H, int W, 
     const size_t s2 = tma ? pass2_smem<true>() : pass2_smem<false>();
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
     cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
-    k1<<<grid, kLThreads, s1, st>>>(img, gt, H, W, win, mA, mB, mC, part, t[0], t[1]);
-    k2<<<grid, kLThreads, s2, st>>>(img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda, d_loss, dL_dimg, t[2],
-                                    t[3], t[4]);
+    launch_chained(k1, dim3(grid), dim3(kLThreads), s1, st, img, gt, H, W, win, mA, mB, mC, part, t[0], t[1]);
+    launch_chained(k2, dim3(grid), dim3(kLThreads), s2, st, img, gt, H, W, win, mA, mB, mC, part, nblocks, lambda,
+                   d_loss, dL_dimg, t[2], t[3], t[4]);
 }
 
 // ---------------------------------------------------------------- PSNR

@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(256, 3) preprocess_fwd_kernel(GaussK g, CamK c
                                                              float4 *__restrict__ rgb_depth,
                                                              uint32_t *__restrict__ ntiles,
                                                              float2 *__restrict__ uv_lo) {
+    chain_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < g.n;
     Chain c;
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(GaussK g, C
                                                                      float4 *__restrict__ d_ls, float4 *__restrict__ d_sh,
                                                                      float *__restrict__ dstat,
                                                                      float *__restrict__ dcount) {
+    chain_enter();
     __shared__ uint32_t s_idx[kBwdChunk];
     __shared__ uint32_t s_cnt;
     if (threadIdx.x == 0) s_cnt = 0u;
@@ -159,7 +161,7 @@ extern "C" int32_t gsr_preprocess(const gsr_gaussians *g, const gsr_camera *cam,
     const CamK ck = make_camk(cam, tiling);
     const int threads = 256;
     const int64_t blocks = (g->n + threads - 1) / threads;
-    preprocess_fwd_kernel<<<(unsigned)blocks, threads, 0, as_cuda(stream)>>>(
+    launch_chained(preprocess_fwd_kernel, dim3((unsigned)blocks), dim3(threads), 0, as_cuda(stream),
         make_gk(g), ck, reinterpret_cast<float4 *>(out->xy_conic), reinterpret_cast<float4 *>(out->c_op_box),
         reinterpret_cast<float4 *>(out->rgb_depth), out->ntiles, reinterpret_cast<float2 *>(out->uv_lo));
     return check_launch("preprocess_fwd_kernel");
@@ -184,7 +186,7 @@ static int32_t preprocess_bwd(const gsr_gaussians *g, const gsr_proj *proj, cons
     const CamK ck = make_camk(cam, tiling);
     const int64_t blocks = (g->n + kBwdChunk - 1) / kBwdChunk;
     auto kernel = store ? preprocess_bwd_kernel<true> : preprocess_bwd_kernel<false>;
-    kernel<<<(unsigned)blocks, kBwdThreads, 0, as_cuda(stream)>>>(
+    launch_chained(kernel, dim3((unsigned)blocks), dim3(kBwdThreads), 0, as_cuda(stream),
         make_gk(g), ck, proj->ntiles, reinterpret_cast<const float4 *>(g2d->g0),
         reinterpret_cast<const float4 *>(g2d->g1), reinterpret_cast<const float4 *>(g2d->g2),
         reinterpret_cast<float4 *>(grads->mean_op), reinterpret_cast<float4 *>(grads->quat),

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(512) render_fwd_kernel(RenderArgs a, const uin
 constexpr int kWorkOrderThreads = 1024, kWorkClasses = 128;
 __global__ void __launch_bounds__(kWorkOrderThreads) work_order_kernel(const uint32_t *__restrict__ work, uint32_t T,
                                                                        uint32_t *__restrict__ order) {
+    chain_enter();
     constexpr uint32_t kPer = 4;  // tiles a thread keeps in registers between the two passes
     __shared__ uint32_t s_cls[kWorkClasses];
     for (int c = threadIdx.x; c < kWorkClasses; c += kWorkOrderThreads) s_cls[c] = 0u;
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(32) render_fwd_warp_kernel(RenderArgs a, const
                                                              uint32_t *__restrict__ n_contrib,
                                                              uint32_t *__restrict__ n_blended,
                                                              uint32_t *__restrict__ tile_work) {
+    chain_enter();
     __shared__ Staged s_buf[32];
     int part;
     const int tile = cta_tile_part(order, 4, part);
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(32) render_bwd_warp_kernel(RenderArgs a, const
                                                              const float *__restrict__ dL_dimg,
                                                              float *__restrict__ g0, float *__restrict__ g1,
                                                              float *__restrict__ g2) {
+    chain_enter();
     __shared__ Staged s_buf[32];
     int part;
     const int tile = cta_tile_part(order, 2, part);
@@ -189,8 +192,8 @@ extern "C" int32_t gsr_render_fwd(const gsr_proj *proj, const uint32_t *vals, co
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
     if (quad && a.depth == 0) {  // warp-private staging (the default for 16 x 16 tiles)
         auto wk = n_blended ? render_fwd_warp_kernel<true> : render_fwd_warp_kernel<false>;
-        wk<<<4 * tiles, 32, 0, as_cuda(stream)>>>(a, proj->tile_order, img, T_final, n_contrib, n_blended,
-                                                  proj->tile_order ? proj->tile_work : nullptr);
+        launch_chained(wk, dim3(4 * tiles), dim3(32), 0, as_cuda(stream), a, proj->tile_order, img, T_final,
+                       n_contrib, n_blended, proj->tile_order ? proj->tile_work : nullptr);
         return check_launch("render_fwd_warp_kernel");
     }
     auto kernel = n_blended ? (quad ? render_fwd_kernel<true, true> : render_fwd_kernel<true, false>)
@@ -234,12 +237,13 @@ extern "C" int32_t gsr_blend_bwd(const gsr_proj *proj, int64_t n, const uint32_t
     const int tiles = grid_x(cam, tiling) * grid_y(cam, tiling);
     const bool quad = tiling->tile_w == 16 && tiling->tile_h == 16;
     if (proj->tile_order && proj->tile_work) {  // deepest lists first (what the forward measured)
-        work_order_kernel<<<1, kWorkOrderThreads, 0, st>>>(proj->tile_work, (uint32_t)tiles, proj->tile_order);
+        launch_chained(work_order_kernel, dim3(1), dim3(kWorkOrderThreads), 0, st, proj->tile_work, (uint32_t)tiles,
+                       proj->tile_order);
         if ((rc = check_launch("work_order_kernel"))) return rc;
     }
     if (quad && tiling->bwd_threads != nthr && a.depth == 0) {  // warp-private staging, four pixels a thread
-        render_bwd_warp_kernel<<<2 * tiles, 32, 0, st>>>(a, proj->tile_order, T_final, n_contrib, dL_dimg,
-                                                         grad2d->g0, grad2d->g1, grad2d->g2);
+        launch_chained(render_bwd_warp_kernel, dim3(2 * tiles), dim3(32), 0, st, a, proj->tile_order, T_final,
+                       n_contrib, dL_dimg, grad2d->g0, grad2d->g1, grad2d->g2);
         return check_launch("render_bwd_warp_kernel");
     }
     if (quad && tiling->bwd_threads != nthr) {  // 64 threads, four pixels each, block-staged batches

@@ -134,6 +134,7 @@ __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, con
                                              float *gk, float *__restrict__ g2) {
     const float4 g = sj.xy, cb = sj.cb;
     const float2 lo = sj.lo;
+    const uint32_t lbit = 1u << lane;  // this lane's bit in the box lane masks
     const float dx = FS(FS(fpx, g.x), lo.x);
     const float t = FM(FM(g.z, dx), dx), bdx = FM(g.w, dx);
     // alpha at the four pixels, a pair at a time
@@ -149,9 +150,9 @@ __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, con
         al[h] = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
         cl[2 * h] = raw.x > kAlphaMax;
         cl[2 * h + 1] = raw.y > kAlphaMax;
-        ok[2 * h] = (!kPosTest || pos < last[2 * h]) && ((q4_lane_bits(lm, 2 * h) >> lane) & 1u) && e.x <= 0.0f &&
+        ok[2 * h] = (!kPosTest || pos < last[2 * h]) && (q4_lane_bits(lm, 2 * h) & lbit) != 0u && e.x <= 0.0f &&
                     al[h].x >= kAlphaMin;
-        ok[2 * h + 1] = (!kPosTest || pos < last[2 * h + 1]) && ((q4_lane_bits(lm, 2 * h + 1) >> lane) & 1u) &&
+        ok[2 * h + 1] = (!kPosTest || pos < last[2 * h + 1]) && (q4_lane_bits(lm, 2 * h + 1) & lbit) != 0u &&
                         e.y <= 0.0f && al[h].y >= kAlphaMin;
         any = any || ok[2 * h] || ok[2 * h + 1];
     }
@@ -164,38 +165,35 @@ __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, con
     for (int q = 0; q < 9; ++q) v2[q] = make_float2(0.f, 0.f);
     const float A = g.z * (1.0f / kHalfLog2e), B = g.w * (0.5f / kHalfLog2e);
     const float C = cb.x * (1.0f / kHalfLog2e);
-    if (any) {
-        const float4 col = sj.rgb;
+    const float4 col = sj.rgb;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
-            if (!(o0 || o1)) continue;
-            const bool q0 = o0 && !cl[2 * h], q1 = o1 && !cl[2 * h + 1];
-            // alpha of a pixel without a contribution is 0: every update below leaves it unchanged
-            const float2 al_e = make_float2(o0 ? al[h].x : 0.f, o1 ? al[h].y : 0.f);
-            const float2 al_g = make_float2(q0 ? al[h].x : 0.f, q1 ? al[h].y : 0.f);
-            const float2 g_g = make_float2(q0 ? gs[h].x : 0.f, q1 ? gs[h].y : 0.f);
-            const float2 one_m = __fadd2_rn(f2(1.0f), neg2(al_e));
-            const float2 rc = make_float2(o0 ? __fdividef(1.0f, one_m.x) : 1.0f,
-                                          o1 ? __fdividef(1.0f, one_m.y) : 1.0f);
-            PairBwd &P = p[h];
-            P.T = __fmul2_rn(P.T, rc);  // transmittance in front of this Gaussian
-            const float2 aT = __fmul2_rn(al_e, P.T);
-            v2[6] = __ffma2_rn(P.dC0, aT, v2[6]);
-            v2[7] = __ffma2_rn(P.dC1, aT, v2[7]);
-            v2[8] = __ffma2_rn(P.dC2, aT, v2[8]);
-            float2 dc = __fmul2_rn(P.dC0, f2(col.x));
-            dc = __ffma2_rn(P.dC1, f2(col.y), dc);
-            dc = __ffma2_rn(P.dC2, f2(col.z), dc);
-            const float2 dalpha = __fmul2_rn(P.T, __fadd2_rn(dc, neg2(P.accd)));
-            P.accd = __ffma2_rn(dc, al_e, __fmul2_rn(P.accd, one_m));
-            const float2 dpow = __fmul2_rn(dalpha, al_g);
-            v2[5] = __ffma2_rn(dalpha, g_g, v2[5]);
-            const float2 tdy = __fmul2_rn(dpow, dy[h]);
-            v2[0] = __fadd2_rn(v2[0], dpow);
-            v2[1] = __fadd2_rn(v2[1], tdy);
-            v2[2] = __ffma2_rn(tdy, dy[h], v2[2]);
-        }
+    for (int h = 0; h < 2; ++h) {
+        const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
+        const bool q0 = o0 && !cl[2 * h], q1 = o1 && !cl[2 * h + 1];
+        // alpha of a pixel without a contribution is 0: every update below leaves it unchanged
+        const float2 al_e = make_float2(o0 ? al[h].x : 0.f, o1 ? al[h].y : 0.f);
+        const float2 al_g = make_float2(q0 ? al[h].x : 0.f, q1 ? al[h].y : 0.f);
+        const float2 g_g = make_float2(q0 ? gs[h].x : 0.f, q1 ? gs[h].y : 0.f);
+        const float2 one_m = __fadd2_rn(f2(1.0f), neg2(al_e));
+        const float2 rc = make_float2(o0 ? __fdividef(1.0f, one_m.x) : 1.0f,
+                                      o1 ? __fdividef(1.0f, one_m.y) : 1.0f);
+        PairBwd &P = p[h];
+        P.T = __fmul2_rn(P.T, rc);  // transmittance in front of this Gaussian
+        const float2 aT = __fmul2_rn(al_e, P.T);
+        v2[6] = __ffma2_rn(P.dC0, aT, v2[6]);
+        v2[7] = __ffma2_rn(P.dC1, aT, v2[7]);
+        v2[8] = __ffma2_rn(P.dC2, aT, v2[8]);
+        float2 dc = __fmul2_rn(P.dC0, f2(col.x));
+        dc = __ffma2_rn(P.dC1, f2(col.y), dc);
+        dc = __ffma2_rn(P.dC2, f2(col.z), dc);
+        const float2 dalpha = __fmul2_rn(P.T, __fadd2_rn(dc, neg2(P.accd)));
+        P.accd = __ffma2_rn(dc, al_e, __fmul2_rn(P.accd, one_m));
+        const float2 dpow = __fmul2_rn(dalpha, al_g);
+        v2[5] = __ffma2_rn(dalpha, g_g, v2[5]);
+        const float2 tdy = __fmul2_rn(dpow, dy[h]);
+        v2[0] = __fadd2_rn(v2[0], dpow);
+        v2[1] = __fadd2_rn(v2[1], tdy);
+        v2[2] = __ffma2_rn(tdy, dy[h], v2[2]);
     }
     if (__any_sync(0xffffffffu, any)) {
         float v[9];

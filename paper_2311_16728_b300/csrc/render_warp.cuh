@@ -83,6 +83,7 @@ __device__ __forceinline__ void render_fwd_quadrant(const RenderArgs &a, int til
     const int begin = (int)rg.x, end = (int)rg.y;
     const float fpx = (float)px;
     const float2 fpy = make_float2((float)py0, (float)(py0 + 1));
+    const uint32_t lbit = 1u << lane;  // this lane's bit in the box lane masks
     PairFwd p;
     p.T = make_float2(1.0f, 1.0f);
     p.C0 = p.C1 = p.C2 = make_float2(0.0f, 0.0f);
@@ -118,8 +119,8 @@ __device__ __forceinline__ void render_fwd_quadrant(const RenderArgs &a, int til
             const Staged &sa = buf[j], &sb = buf[has_b ? j + 1 : j];
             PixAlpha pa, pb;
             const uint2 ma = *reinterpret_cast<const uint2 *>(sa.lanes), mb = *reinterpret_cast<const uint2 *>(sb.lanes);
-            pair_alpha(sa.xy, sa.cb, sa.lo, fpx, fpy, (ma.x >> lane) & 1u, (ma.y >> lane) & 1u, pa);
-            pair_alpha(sb.xy, sb.cb, sb.lo, fpx, fpy, (mb.x >> lane) & 1u, (mb.y >> lane) & 1u, pb);
+            pair_alpha(sa.xy, sa.cb, sa.lo, fpx, fpy, (ma.x & lbit) != 0u, (ma.y & lbit) != 0u, pa);
+            pair_alpha(sb.xy, sb.cb, sb.lo, fpx, fpy, (mb.x & lbit) != 0u, (mb.y & lbit) != 0u, pb);
             if (!has_b) pb.ok0 = pb.ok1 = false;
             blend_fwd_pair(p, pa.ok0, pa.ok1, pa.a0, pa.a1, sa.rgb, sa.pad);
             blend_fwd_pair(p, pb.ok0, pb.ok1, pb.a0, pb.a1, sb.rgb, sb.pad);
