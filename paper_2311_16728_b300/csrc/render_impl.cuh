@@ -104,23 +104,21 @@ __device__ __forceinline__ float2 mean_residual(const RenderArgs &a, uint32_t gi
 __device__ __forceinline__ bool rect_may_see(float u, float v, float A, float B, float C, float tau, float rx0,
                                              float rx1, float ry0, float ry1) {
     const bool out_x = u < rx0 || u > rx1, out_y = v < ry0 || v > ry1;
-    if (!(out_x || out_y)) return true;
-    float lb = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        if (!(e ? out_y : out_x)) continue;
-        float dx, dy;
-        if (e == 0) {  // the vertical edge on the mean's side: dy at its vertex, clamped to the rectangle
-            dx = (u < rx0 ? rx0 : rx1) - u;
-            dy = fminf(fmaxf(-__fdividef(B * dx, C), ry0 - v), ry1 - v);
-        } else {       // the horizontal edge on the mean's side
-            dy = (v < ry0 ? ry0 : ry1) - v;
-            dx = fminf(fmaxf(-__fdividef(B * dy, A), rx0 - u), rx1 - u);
-        }
-        const float t1 = A * dx * dx, t2 = 2.0f * B * dx * dy, t3 = C * dy * dy;
-        lb = fminf(lb, (t1 + t2 + t3) - 1e-5f * (fabsf(t1) + fabsf(t2) + fabsf(t3)));
-    }
-    return lb <= tau * 1.001f + 1e-3f;
+    // both edges are evaluated on every lane (no divergent branch); an edge
+    // that does not face the mean does not enter the minimum
+    // the vertical edge on the mean's side: dy at its vertex, clamped to the rectangle
+    const float dxv = (u < rx0 ? rx0 : rx1) - u;
+    const float dyv = fminf(fmaxf(-__fdividef(B * dxv, C), ry0 - v), ry1 - v);
+    // the horizontal edge on the mean's side
+    const float dyh = (v < ry0 ? ry0 : ry1) - v;
+    const float dxh = fminf(fmaxf(-__fdividef(B * dyh, A), rx0 - u), rx1 - u);
+    const float t1v = A * dxv * dxv, t2v = 2.0f * B * dxv * dyv, t3v = C * dyv * dyv;
+    const float t1h = A * dxh * dxh, t2h = 2.0f * B * dxh * dyh, t3h = C * dyh * dyh;
+    const float lv = (t1v + t2v + t3v) - 1e-5f * (fabsf(t1v) + fabsf(t2v) + fabsf(t3v));
+    const float lh = (t1h + t2h + t3h) - 1e-5f * (fabsf(t1h) + fabsf(t2h) + fabsf(t3h));
+    const float inf = __int_as_float(0x7f800000);
+    const float lb = fminf(out_x ? lv : inf, out_y ? lh : inf);
+    return !(out_x || out_y) || lb <= tau * 1.001f + 1e-3f;
 }
 
 // One staged splat: everything a warp reads per splat in the blend loops, in

@@ -33,21 +33,22 @@ constexpr int kWarpFwdThreads = 128, kWarpBwdThreads = 64;  // threads of a tile
 // stage_splat applies per warp, without its prefilter on the alpha
 // ellipse's bounding box, which the minimum implies: the two square roots
 // and divisions cost more per staged record than the records it drops
-// earlier); x0, x1, y0, y1 receive its pixel box once the alpha test has
-// passed.
+// earlier); x0, x1, y0, y1 receive its pixel box.  Every test runs on every
+// lane (no divergent early exit).
 __device__ __forceinline__ bool warp_may_see(const float4 g, const float4 c, int rx0, int rx1, int ry0, int ry1,
                                              int &x0, int &x1, int &y0, int &y1) {
     const float A = g.z, B = g.w, C = c.x, op = c.y;
     const float tau = 2.0f * __logf(255.0f * op);  // alpha >= 1/255  <=>  d^T Q d <= tau
-    if (!(tau > 0.0f)) return false;
     const uint32_t bx = __float_as_uint(c.z), by = __float_as_uint(c.w);
     x0 = (int)(bx & 0xffffu);
     x1 = (int)(bx >> 16);
     y0 = (int)(by & 0xffffu);
     y1 = (int)(by >> 16);
-    if (!(x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0)) return false;
-    return rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1), (float)max(ry0, y0),
-                        (float)min(ry1, y1));
+    // every test on every lane, combined without short-circuit branches
+    const bool boxes = x0 <= rx1 && x1 >= rx0 && y0 <= ry1 && y1 >= ry0;
+    const bool near = rect_may_see(g.x, g.y, A, B, C, tau, (float)max(rx0, x0), (float)min(rx1, x1),
+                                   (float)max(ry0, y0), (float)min(ry1, y1));
+    return (tau > 0.0f) & boxes & near;
 }
 
 // The record of a visible splat in the warp's buffer: pre-scaled exponent

@@ -46,21 +46,34 @@ inline Win ssim_window() {
     return k;
 }
 
+// The block sums of a and b (warp shuffles, then the warps' totals by the
+// first warp), both in one shared-memory round of two barriers.
 template <int NT>
-__device__ __forceinline__ float block_sum(float v, float *s_red) {
+__device__ __forceinline__ float2 block_sum2(float a, float b, float *s_red) {
     constexpr int kW = NT / 32;
+    static_assert(2 * kW <= 32, "two partial sums per warp in s_red[32]");
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float r = 0.f;
-    if (threadIdx.x < 32) {
-        r = threadIdx.x < kW ? s_red[threadIdx.x] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_red[threadIdx.x >> 5] = a;
+        s_red[kW + (threadIdx.x >> 5)] = b;
     }
     __syncthreads();
-    return r;  // valid in thread 0
+    float ra = 0.f, rb = 0.f;
+    if (threadIdx.x < 32) {
+        ra = threadIdx.x < kW ? s_red[threadIdx.x] : 0.f;
+        rb = threadIdx.x < kW ? s_red[kW + threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ra += __shfl_xor_sync(0xffffffffu, ra, o);
+            rb += __shfl_xor_sync(0xffffffffu, rb, o);
+        }
+    }
+    __syncthreads();
+    return make_float2(ra, rb);  // valid in thread 0
 }
 
 // Stages a (kRH x kRW) region of each of the NP planes src[p] around the
@@ -308,11 +321,10 @@ __device__ __forceinline__ void ssim_pass1_block(const float *__restrict__ x, co
             }
         }
     }
-    const float s1 = block_sum<NT>(l1, s_red);
-    const float s2 = block_sum<NT>(ssim, s_red);
+    const float2 s12 = block_sum2<NT>(l1, ssim, s_red);
     if (threadIdx.x == 0) {
-        part[0] = s1;
-        part[1] = s2;
+        part[0] = s12.x;
+        part[1] = s12.y;
     }
 }
 
