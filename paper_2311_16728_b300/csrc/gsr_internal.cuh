@@ -370,24 +370,19 @@ __device__ __forceinline__ float qform32(float A, float B, float C, float dx, fl
 
 __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, float C, float op, float x0, float x1,
                                           float y0, float y1) {
-    float q;
-    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
-        q = 0.0f;
-    } else {
-        q = __int_as_float(0x7f800000);
-        if (u < x0 || u > x1) {
-            const float dx = FS(u < x0 ? x0 : x1, u);
-            float ys = FS(v, FD(FM(B, dx), C));
-            ys = fminf(fmaxf(ys, y0), y1);
-            q = qform32(A, B, C, dx, FS(ys, v));
-        }
-        if (v < y0 || v > y1) {
-            const float dy = FS(v < y0 ? y0 : y1, v);
-            float xs = FS(u, FD(FM(B, dy), A));
-            xs = fminf(fmaxf(xs, x0), x1);
-            q = fminf(q, qform32(A, B, C, FS(xs, u), dy));
-        }
-    }
+    // both edges on every lane, no divergent branch: the lanes of a warp
+    // test different tiles and Gaussians; edges that do not face the mean
+    // (and the mean inside) are selected away
+    const bool out_x = u < x0 || u > x1, out_y = v < y0 || v > y1;
+    const float dx = FS(u < x0 ? x0 : x1, u);
+    const float ys = fminf(fmaxf(FS(v, FD(FM(B, dx), C)), y0), y1);
+    const float qx = qform32(A, B, C, dx, FS(ys, v));
+    const float dy = FS(v < y0 ? y0 : y1, v);
+    const float xs = fminf(fmaxf(FS(u, FD(FM(B, dy), A)), x0), x1);
+    const float qy = qform32(A, B, C, FS(xs, u), dy);
+    float q = out_x ? qx : __int_as_float(0x7f800000);
+    q = out_y ? fminf(q, qy) : q;
+    q = (u >= x0 && u <= x1 && v >= y0 && v <= y1) ? 0.0f : q;
     return FM(op, chain_exp(FM(-0.5f, q))) >= kTileAlphaMin;
 }
 

@@ -207,9 +207,10 @@ __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, con
         for (int q = 5; q < 9; ++q) v[q] = v2[q].x + v2[q].y;
         float v8;
         const float y = warp_transpose_sum(v, v8);
+        // one atomic instruction, predicated on the lanes that hold a total
         const uint32_t gid = sj.gid;
-        if ((lane & 3) == 0) atomicAdd(gk + 4 * (int64_t)gid, y);
-        else if (lane == 1) atomicAdd(g2 + 4 * (int64_t)gid, v8);
+        const bool g0g1 = (lane & 3) == 0;
+        if (g0g1 || lane == 1) atomicAdd((g0g1 ? gk : g2) + 4 * (int64_t)gid, g0g1 ? y : v8);
     }
 }
 
