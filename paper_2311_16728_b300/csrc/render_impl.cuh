@@ -131,7 +131,8 @@ struct __align__(16) Staged {
     float4 rgb;      // colour, depth
     float2 lo;       // position residual
     uint32_t gid, pad;
-    uint4 lanes[2];  // box lane masks: 4 x uint2 (quadrant warps) or 2 x uint4 (16 x 8 half warps)
+    uint4 lanes[2];  // box lane masks: 4 x uint2 (quadrant warps) or 2 x uint4 (16 x 8 half warps);
+                     // warp-private staging: lanes[0] the warp's masks, lanes[1].x its fast-path flag
 };
 static_assert(sizeof(Staged) == 96, "staged splat record");
 
@@ -221,7 +222,13 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // Blackwell's packed FP32 instructions (FFMA2 / FMUL2 / FADD2: each lane
 // rounded to nearest exactly like the scalar operation), one issue slot for
 // both pixels.
-// b0, b1: whether the two pixels lie in the splat's pixel box
+// b0, b1: whether the two pixels lie in the splat's pixel box.
+// kUnclamped: the caller knows opacity <= kOpNoClamp, so opacity G < 0.99
+// and the clamp is the identity (G = 2^e <= 1 up to the 2^-22 error of
+// ex2.approx for e <= 0, and a pixel with e > 0 is skipped anyway).
+constexpr float kOpNoClamp = 0.98f;
+
+template <bool kUnclamped = false>
 __device__ __forceinline__ void pair_alpha(const float4 g, const float4 cb, const float2 lo, float fpx, float2 fpy,
                                            bool b0, bool b1, PixAlpha &r) {
     const float dx = FS(FS(fpx, g.x), lo.x);
@@ -229,8 +236,8 @@ __device__ __forceinline__ void pair_alpha(const float4 g, const float4 cb, cons
     const float2 dy = __fadd2_rn(__fadd2_rn(fpy, f2(-g.y)), f2(-lo.y));
     const float2 e = __ffma2_rn(__fmul2_rn(f2(cb.x), dy), dy, __ffma2_rn(f2(bdx), dy, f2(t)));
     const float2 raw = __fmul2_rn(f2(cb.y), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-    r.a0 = fminf(kAlphaMax, raw.x);
-    r.a1 = fminf(kAlphaMax, raw.y);
+    r.a0 = kUnclamped ? raw.x : fminf(kAlphaMax, raw.x);
+    r.a1 = kUnclamped ? raw.y : fminf(kAlphaMax, raw.y);
     r.ok0 = b0 && e.x <= 0.0f && r.a0 >= kAlphaMin;
     r.ok1 = b1 && e.y <= 0.0f && r.a1 >= kAlphaMin;
 }

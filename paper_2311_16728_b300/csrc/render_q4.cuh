@@ -128,7 +128,10 @@ struct PairBwd {
 // their back-to-front updates, and the warp's transposed reduction with its
 // atomics into g0 / g1 (lane 4k: value k at gk) and g2.  kPosTest false:
 // the caller knows pos lies below every one of the thread's n_contrib.
-template <bool kPosTest = true>
+// kFast: the splat's pixel box holds all of the warp's pixels and its
+// opacity cannot reach the clamp (the staged fast-path flag), so the box and
+// clamp tests are dropped; decisions and arithmetic are the general path's.
+template <bool kPosTest = true, bool kFast = false>
 __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, const uint4 lm, int lane, float fpx,
                                              const float2 (&fpy)[2], const uint32_t (&last)[4], PairBwd (&p)[2],
                                              float *gk, float *__restrict__ g2) {
@@ -147,13 +150,13 @@ __device__ __forceinline__ void q4_splat_bwd(const Staged &sj, uint32_t pos, con
         const float2 e = __ffma2_rn(__fmul2_rn(f2(cb.x), dy[h]), dy[h], __ffma2_rn(f2(bdx), dy[h], f2(t)));
         gs[h] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
         const float2 raw = __fmul2_rn(f2(cb.y), gs[h]);
-        al[h] = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
-        cl[2 * h] = raw.x > kAlphaMax;
-        cl[2 * h + 1] = raw.y > kAlphaMax;
-        ok[2 * h] = (!kPosTest || pos < last[2 * h]) && (q4_lane_bits(lm, 2 * h) & lbit) != 0u && e.x <= 0.0f &&
-                    al[h].x >= kAlphaMin;
-        ok[2 * h + 1] = (!kPosTest || pos < last[2 * h + 1]) && (q4_lane_bits(lm, 2 * h + 1) & lbit) != 0u &&
-                        e.y <= 0.0f && al[h].y >= kAlphaMin;
+        al[h] = kFast ? raw : make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+        cl[2 * h] = !kFast && raw.x > kAlphaMax;
+        cl[2 * h + 1] = !kFast && raw.y > kAlphaMax;
+        ok[2 * h] = (!kPosTest || pos < last[2 * h]) && (kFast || (q4_lane_bits(lm, 2 * h) & lbit) != 0u) &&
+                    e.x <= 0.0f && al[h].x >= kAlphaMin;
+        ok[2 * h + 1] = (!kPosTest || pos < last[2 * h + 1]) &&
+                        (kFast || (q4_lane_bits(lm, 2 * h + 1) & lbit) != 0u) && e.y <= 0.0f && al[h].y >= kAlphaMin;
         any = any || ok[2 * h] || ok[2 * h + 1];
     }
     // v2[0 .. 2]: the lane's dpow-weighted moments in dy (sum dpow,

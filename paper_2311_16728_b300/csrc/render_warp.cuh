@@ -53,9 +53,14 @@ __device__ __forceinline__ bool warp_may_see(const float4 g, const float4 c, int
 
 // The record of a visible splat in the warp's buffer: pre-scaled exponent
 // terms as stage_splat writes them, `pad` = the splat's 0-based position in
-// the tile's list, lanes[0] = the warp's box lane masks.
+// the tile's list, lanes[0] = the warp's box lane masks, lanes[1].x = 1 when
+// the blend may take its fast path for this splat: the pixel box holds every
+// pixel of the warp (`full`) and the opacity cannot reach the alpha clamp.
+// The flag is the same for every lane of the warp, so the branch on it
+// never diverges; the fast path drops the per-pixel box and clamp tests that
+// cannot fail, with the same decisions and arithmetic as the general one.
 __device__ __forceinline__ void warp_stage(const RenderArgs &a, uint32_t gid, uint32_t pos, const float4 g,
-                                           const float4 c, const uint4 lanes, Staged &st) {
+                                           const float4 c, const uint4 lanes, bool full, Staged &st) {
     st.xy = make_float4(g.x, g.y, g.z * kHalfLog2e, g.w * (2.0f * kHalfLog2e));
     st.cb = make_float4(c.x * kHalfLog2e, c.y, c.z, c.w);
     st.rgb = __ldg(a.rgb_depth + gid);
@@ -63,6 +68,7 @@ __device__ __forceinline__ void warp_stage(const RenderArgs &a, uint32_t gid, ui
     st.gid = gid;
     st.pad = pos;
     st.lanes[0] = lanes;
+    st.lanes[1] = make_uint4((full && c.y <= kOpNoClamp) ? 1u : 0u, 0u, 0u, 0u);
 }
 
 // ---------------------------------------------------------------- K5
@@ -109,7 +115,7 @@ __device__ __forceinline__ void render_fwd_quadrant(const RenderArgs &a, int til
         if (vis) {
             const uint2 m = quad_box_lanes(x0, x1, y0, y1, rx0, ry0);
             warp_stage(a, gid, (uint32_t)(idx - begin + 1), g, c, make_uint4(m.x, m.y, 0u, 0u),
-                       buf[__popc(bits & ((1u << lane) - 1u))]);
+                       (m.x & m.y) == 0xffffffffu, buf[__popc(bits & ((1u << lane) - 1u))]);
         }
         __syncwarp();
         const int n = __popc(bits);
@@ -119,9 +125,15 @@ __device__ __forceinline__ void render_fwd_quadrant(const RenderArgs &a, int til
             const bool has_b = j + 1 < n;
             const Staged &sa = buf[j], &sb = buf[has_b ? j + 1 : j];
             PixAlpha pa, pb;
-            const uint2 ma = *reinterpret_cast<const uint2 *>(sa.lanes), mb = *reinterpret_cast<const uint2 *>(sb.lanes);
-            pair_alpha(sa.xy, sa.cb, sa.lo, fpx, fpy, (ma.x & lbit) != 0u, (ma.y & lbit) != 0u, pa);
-            pair_alpha(sb.xy, sb.cb, sb.lo, fpx, fpy, (mb.x & lbit) != 0u, (mb.y & lbit) != 0u, pb);
+            if ((sa.lanes[1].x & sb.lanes[1].x) != 0u) {  // both on the fast path (uniform over the warp)
+                pair_alpha<true>(sa.xy, sa.cb, sa.lo, fpx, fpy, true, true, pa);
+                pair_alpha<true>(sb.xy, sb.cb, sb.lo, fpx, fpy, true, true, pb);
+            } else {
+                const uint2 ma = *reinterpret_cast<const uint2 *>(sa.lanes);
+                const uint2 mb = *reinterpret_cast<const uint2 *>(sb.lanes);
+                pair_alpha(sa.xy, sa.cb, sa.lo, fpx, fpy, (ma.x & lbit) != 0u, (ma.y & lbit) != 0u, pa);
+                pair_alpha(sb.xy, sb.cb, sb.lo, fpx, fpy, (mb.x & lbit) != 0u, (mb.y & lbit) != 0u, pb);
+            }
             if (!has_b) pb.ok0 = pb.ok1 = false;
             blend_fwd_pair(p, pa.ok0, pa.ok1, pa.a0, pa.a1, sa.rgb, sa.pad);
             blend_fwd_pair(p, pb.ok0, pb.ok1, pb.a0, pb.a1, sb.rgb, sb.pad);
@@ -232,21 +244,25 @@ __device__ __forceinline__ void render_bwd_tile_warp(const RenderArgs &a, int ti
             vis = warp_may_see(g, c, rx0, rx1, ry0, ry1, x0, x1, y0, y1);
         }
         const uint32_t bits = __ballot_sync(0xffffffffu, vis);
-        if (vis)
-            warp_stage(a, gid, (uint32_t)(idx - begin), g, c, q4_box_lanes(x0, x1, y0, y1, ox, ry0),
+        if (vis) {
+            const uint4 m = q4_box_lanes(x0, x1, y0, y1, ox, ry0);
+            warp_stage(a, gid, (uint32_t)(idx - begin), g, c, m, (m.x & m.y & m.z & m.w) == 0xffffffffu,
                        buf[__popc(bits & ((1u << lane) - 1u))]);
+        }
         __syncwarp();
         // every position of the round below every pixel's n_contrib: no
         // per-splat position test
         if (__all_sync(0xffffffffu, min(min(last[0], last[1]), min(last[2], last[3])) >= (uint32_t)(bend - begin))) {
             for (int j = __popc(bits) - 1; j >= 0; --j) {  // back to front
                 const Staged &sj = buf[j];
-                q4_splat_bwd<false>(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+                if (sj.lanes[1].x) q4_splat_bwd<false, true>(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+                else q4_splat_bwd<false>(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
             }
         } else {
             for (int j = __popc(bits) - 1; j >= 0; --j) {
                 const Staged &sj = buf[j];
-                q4_splat_bwd(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+                if (sj.lanes[1].x) q4_splat_bwd<true, true>(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
+                else q4_splat_bwd(sj, sj.pad, sj.lanes[0], lane, fpx, fpy, last, p, gk, g2);
             }
         }
         __syncwarp();
