@@ -349,6 +349,21 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
     const int ox = bx * kLTW, oy = by * kLTH;
     const int64_t plane = (int64_t)H * W, cb = (int64_t)c * plane;
     const float inv_n = (float)((double)scale / ((double)C * (double)plane));
+    // one column run per thread: its rendered and target values are loaded
+    // before the staging, in flight during the copy and both blurs
+    constexpr bool kEarly = kTma && NT == kLTW * (kLTH / kRun);
+    float xs[kRun], ys[kRun];
+    if constexpr (kEarly) {
+        const int tx = (int)threadIdx.x % kLTW, i0 = ((int)threadIdx.x / kLTW) * kRun;
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            const int gx = ox + tx, gy = oy + i0 + o;
+            const bool in = gx < W && gy < H;
+            const int64_t idx = cb + (int64_t)(in ? gy : 0) * W + (in ? gx : 0);
+            xs[o] = x[idx];
+            ys[o] = y[idx];
+        }
+    }
     __syncthreads();
     if constexpr (kTma) {
         const CUtensorMap *const maps[3] = {tma_a, tma_b, tma_c};
@@ -431,14 +446,15 @@ __device__ __forceinline__ void ssim_pass2_block(const float *__restrict__ x, co
     for (int vt = threadIdx.x; vt < kLTW * (kLTH / kRun); vt += NT) {
         const int tx = vt % kLTW, i0 = (vt / kLTW) * kRun;
         // this thread's rendered and target values, in flight during the blur
-        float xs[kRun], ys[kRun];
+        if constexpr (!kEarly) {
 #pragma unroll
-        for (int o = 0; o < kRun; ++o) {
-            const int gx = ox + tx, gy = oy + i0 + o;
-            const bool in = gx < W && gy < H;
-            const int64_t idx = cb + (int64_t)(in ? gy : 0) * W + (in ? gx : 0);
-            xs[o] = x[idx];
-            ys[o] = y[idx];
+            for (int o = 0; o < kRun; ++o) {
+                const int gx = ox + tx, gy = oy + i0 + o;
+                const bool in = gx < W && gy < H;
+                const int64_t idx = cb + (int64_t)(in ? gy : 0) * W + (in ? gx : 0);
+                xs[o] = x[idx];
+                ys[o] = y[idx];
+            }
         }
         float2 gab[kRun];
         float gc[kRun];
