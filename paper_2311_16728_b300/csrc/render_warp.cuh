@@ -122,6 +122,9 @@ __device__ __forceinline__ void render_fwd_quadrant(const RenderArgs &a, int til
         // two splats per round: their alphas are independent, so both are
         // evaluated before they are blended in list order
         for (int j = 0; j < n; j += 2) {
+            // and within a round, every eight splats, so that a warp whose
+            // pixels all stopped early in the round skips its remaining splats
+            if ((j & 7) == 0 && j > 0 && __all_sync(0xffffffffu, p.done0 && p.done1)) break;
             const bool has_b = j + 1 < n;
             const Staged &sa = buf[j], &sb = buf[has_b ? j + 1 : j];
             PixAlpha pa, pb;
