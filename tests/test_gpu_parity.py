@@ -194,6 +194,50 @@ def test_render_backward_matches_oracle_tiny(tile):
                     param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_opaque_splats_alpha_clamp_and_fast_path(tile):
+    """Opacity logits N(4, 2): about half the Gaussians have opacity above
+    0.98, where the warp-staged blends take their general path and alpha
+    often meets the clamp at 0.99; the rest take the fast path wherever a
+    splat's pixel box holds all of a warp's pixels.  Image, transmittance
+    and blend counts against the oracle, screen-space and parameter
+    gradients within the bar; 16 x 16 tiles are the warp-staged kernels,
+    32 x 8 the block-staged ones."""
+    p = S.perturb(S.tiny_scene(seed=21))
+    rng = np.random.default_rng(21)
+    p.mean_op[:, 3] = rng.normal(4.0, 2.0, p.n).astype(np.float32)
+    op = 1.0 / (1.0 + np.exp(-p.mean_op[:, 3].astype(np.float64)))
+    assert (op > 0.99).mean() > 0.3 and (op <= 0.98).mean() > 0.2
+    cam = S.tiny_camera()
+    ca = cam.as_array()
+    dec, _, sc, (img, T, nc, mg) = _oracle_all(p, cam)
+    vb, g = gpu_view(p, cam, tile)
+    nb = torch.zeros(cam.height, cam.width, dtype=torch.int32, device="cuda")
+    vb.render_fwd(n_blended=nb)
+    torch.cuda.synchronize()
+    flagged = mg < MARGIN_FLAG
+    err = np.abs(vb.img.cpu().numpy().astype(np.float64) - img).max(axis=0)
+    terr = np.abs(vb.T_final.cpu().numpy().astype(np.float64) - T)
+    nbg = nb.cpu().numpy()
+    print(f"tile {tile}: opacity > 0.99 for {(op > 0.99).mean():.0%}; image err {err[~flagged].max():.2e}, "
+          f"T err {terr[~flagged].max():.2e}, flagged pixels {int(flagged.sum())}")
+    assert flagged.sum() <= 0.01 * flagged.size
+    assert err[~flagged].max() <= IMG_ATOL
+    assert terr[~flagged].max() <= IMG_ATOL
+    assert np.array_equal(nbg[~flagged], nc[~flagged]), "blend counts differ"
+    dimg = S.random_grad_image(3, cam.height, cam.width, seed=22)
+    dimg[:, flagged] = 0.0
+    gref, g2ref, mag = oracle.render_bwd(sc, ca, cam.width, cam.height, dec, dimg.astype(np.float64),
+                                         with_magnitude=True)
+    grads = g.zeros_like()
+    vb.render_bwd(g, grads, dimg=torch.tensor(dimg, device="cuda"))
+    torch.cuda.synchronize()
+    assert_grad_bar(f"opaque splats, tile {tile}, screen-space gradients", _screen_grads(vb), g2ref, mag)
+    pr = oracle.project(sc, ca, cam.width, cam.height, dec.visible)
+    assert_grad_bar(f"opaque splats, tile {tile}, parameter gradients", grad_planes_gpu(grads), gref,
+                    param_condition(sc, ca, cam.width, cam.height, dec, mag), waive=colour_clamp_waiver(pr, dec.visible))
+
+
 def test_end_to_end_loss_and_gradients_tiny():
     """Render, Eq. 4 loss and its gradient, backward, all on the GPU, against
     the oracle's: the loss within 1e-5 relative and every parameter gradient
