@@ -1485,7 +1485,7 @@ def main():
 # loss stage is its two SSIM passes, the binning stage its seven kernels, the
 # backward stage its tile reorder and blend, the Adam stage its step and
 # counter kernels).
-NCU_TRAFFIC = {"preprocess": 15.461e6, "bin_sort": 21.098e6, "render_fwd": 3.996e6, "loss": 69.038e6,
+NCU_TRAFFIC = {"preprocess": 15.461e6, "bin_sort": 21.099e6, "render_fwd": 3.996e6, "loss": 69.038e6,
                "blend_bwd": 21.062e6, "preprocess_bwd": 12.438e6, "adam": 393.483e6}
 # the pose chain (profiles/pose_bwd_300k_1200x680.md)
 NCU_TRAFFIC_POSE = 15.037952e6
