@@ -20,7 +20,14 @@
  *    the call and may be freed on return.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *    stream) and runs asynchronously; outputs are valid once the stream has
- *    reached that point.
+ *    reached that point.  Some kernels are launched with programmatic
+ *    dependent launch (the mapping step's kernels after the binning): each
+ *    waits (griddepcontrol.wait) for the work before it in the stream to
+ *    complete before it touches memory, so stream order holds as for plain
+ *    launches.  A caller's own kernel launched with programmatic stream
+ *    serialization directly after one of ours may start early and must
+ *    itself wait (cudaGridDependencySynchronize) before reading our
+ *    outputs; plainly launched work, copies and events need nothing.
  *  - The return value is a gsr_status.  Argument errors are detected on the
  *    host before anything is enqueued (GSR_ERR_INVALID_ARG) and leave every
  *    output untouched.  GSR_ERR_CUDA means a launch failed; gsr_last_error()
